@@ -1,0 +1,151 @@
+/*
+ * libsinv -- selected inverse of a sparse symmetric matrix on S = pattern(L+D+L^T)
+ * from given incomplete LDL^T factors, on one NVIDIA B300 (sm_103a).
+ *
+ * Method: Akter, Bollhoefer, Schenk, "Scalable Approximate Selected Inversion
+ * Based on Single-Level Incomplete LDL^T Factorization and Spectral Corrections
+ * for Large Sparse Systems".  Section numbers below refer to that paper.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - n is the matrix order; indices are 0-based.  Column indices are int32,
+ *    row pointers int64.
+ *  - L is strictly lower triangular CSR (unit diagonal implied, not stored):
+ *    row i holds the columns j < i of its stored entries, strictly increasing.
+ *    A stored entry is structurally nonzero even when its value is 0.
+ *  - D is block diagonal with 1x1 and 2x2 blocks.  pivot_start[j] = 1 when a
+ *    block starts at j; the block is 2x2 iff pivot_start[j+1] = 0.  Packed
+ *    values D_val list the blocks in order: d for a 1x1 block, (d11, d21, d22)
+ *    for a 2x2 block, so D_val has n + (#2x2 blocks) entries.  The two columns
+ *    of a 2x2 block are coupled only through D: L(j+1, j) must not be stored.
+ *  - S_lo is the lower part of S (Section 1): row i holds the stored columns of
+ *    L row i, then i-1 if (i-1, i) is a 2x2 block, then i.  Every value array
+ *    "on S" (G_S, N_S, M_S, X_S) has |S_lo| entries in this CSR order.
+ *  - Numeric calls take DEVICE pointers, are asynchronous on the given stream,
+ *    and keep no pointer after their stream work completes.  The caller owns
+ *    every buffer it passes; the handle owns everything it allocates.
+ *  - Every call returns a status and never aborts or throws across the ABI.
+ *    Errors found on the device (a singular pivot, a wait that timed out) are
+ *    recorded in a handle-owned status word and returned (and cleared) by
+ *    the next sinv_sync_status, which synchronises with the stream.  The
+ *    handle is not thread safe: one host thread drives it at a time.
+ */
+#ifndef SINV_H
+#define SINV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SINV_OK = 0,
+    SINV_ERR_INVALID_ARG = 1,   /* null pointer, negative size, bad enum      */
+    SINV_ERR_PATTERN = 2,       /* unsorted / duplicate / out-of-range / not
+                                   strictly lower / bad pivot layout          */
+    SINV_ERR_SINGULAR_PIVOT = 3,/* a D block with zero determinant            */
+    SINV_ERR_OOM = 4,           /* host or device allocation failed           */
+    SINV_ERR_CUDA = 5,          /* a CUDA runtime call failed                 */
+    SINV_ERR_TIMEOUT = 6,       /* a bounded device wait gave up              */
+    SINV_ERR_UNSUPPORTED = 7    /* size or option outside what is built       */
+} sinv_status;
+
+/* Arithmetic of a numeric call.  Inputs and outputs stay FP64 in every form. */
+typedef enum {
+    SINV_FP64 = 0,      /* native FP64 throughout                                  */
+    SINV_FP32 = 1       /* FP32 products and sums; pivot inverses and the diagonal
+                           accumulation of each pivot block in FP64                */
+} sinv_precision;
+
+typedef struct sinv_handle_s *sinv_handle;
+
+typedef struct {
+    int32_t supernode_cap;  /* max columns per supernode (1 disables merging); 0 = 16 */
+    int32_t device;         /* CUDA device ordinal the handle lives on; -1 = host-only
+                               analysis (no CUDA call; numeric calls then fail with
+                               SINV_ERR_INVALID_ARG)                                  */
+    int64_t wait_limit;     /* polls before a device wait gives up; 0 = default       */
+} sinv_symbolic_opts;
+
+/* Symbolic analysis (host).  Validates the pattern of L and the pivot layout,
+ * builds S_lo, the pivot blocks, the supernode partition, the dependency levels
+ * and every index map the numeric calls use, and uploads them to the device.
+ *   L_rowptr [n+1], L_col [nnzL], pivot_start [n]: HOST memory, read only.
+ *   opts may be NULL (defaults).  *out receives a new handle (destroy with
+ *   sinv_destroy).  Pattern of S: Section 1; the supernodal ordering of the
+ *   Takahashi recurrence: Section 2.1 and Fig. 2 (block elimination tree). */
+sinv_status sinv_symbolic(int64_t n, const int64_t *L_rowptr, const int32_t *L_col,
+                          const int8_t *pivot_start, const sinv_symbolic_opts *opts,
+                          sinv_handle *out);
+
+/* S_lo on the device (handle-owned, valid until sinv_destroy) and its size. */
+sinv_status sinv_get_pattern(sinv_handle h, const int64_t **S_rowptr, const int32_t **S_col,
+                             int64_t *nnzS_lo);
+
+/* Copies S_lo into caller-owned HOST arrays S_rowptr [n+1] and S_col [|S_lo|]. */
+sinv_status sinv_get_pattern_host(sinv_handle h, int64_t *S_rowptr, int32_t *S_col);
+
+/* Selected inverse on S (Section 2.1, eqs. (2.4)-(2.5)): for every pivot block
+ * from the last to the first, G21 = -G22 L21 restricted to S (entries of G22
+ * outside S read as zero), G11 = D11^{-1} - L21^T G21.  Supernodes of
+ * consecutive pivot blocks with nested structure are processed as one dense
+ * step; supernodes are scheduled by a persistent kernel in dependency order.
+ *   L_val [nnzL] (CSR order of L), D_val (packed), G_S [|S_lo|]: device.
+ * Singular D blocks: SINV_ERR_SINGULAR_PIVOT (reported by sinv_sync_status). */
+sinv_status sinv_selinv(sinv_handle h, const double *L_val, const double *D_val,
+                        sinv_precision prec, double *G_S, void *stream);
+
+/* NInv on S (Section 2.2, eqs. (2.6) and (2.8)): W = sum_{t=0}^{m} E^t with
+ * L = I - E, by m Horner steps W <- I + E W on the fixed pattern of the
+ * truncated series, then N = W^T D^{-1} W evaluated on S only.  0 <= m <= 60.
+ *   L_val, D_val, N_S [|S_lo|]: device.  m > 60: SINV_ERR_UNSUPPORTED. */
+sinv_status sinv_ninv(sinv_handle h, const double *L_val, const double *D_val, int m,
+                      sinv_precision prec, double *N_S, void *stream);
+
+/* Mix (Section 2.3): M_ij = G_ij where |G_ij| > eps, else N_ij, on S.
+ *   G_S, N_S, M_S [|S_lo|]: device (M_S may alias G_S or N_S). */
+sinv_status sinv_mix(sinv_handle h, const double *G_S, const double *N_S, double eps,
+                     double *M_S, void *stream);
+
+/* Low-rank spectral correction on S (Section 2.5, eq. (2.9); its diagonal is
+ * the update formula of Section 2.6): X_ij += sum_{l<k} lambda_l V_il V_jl for
+ * (i, j) in S_lo.
+ *   V [n*k] row-major, lambda [k], X_S [|S_lo|] in/out: device.  k <= 256. */
+sinv_status sinv_lowrank_correct(sinv_handle h, int k, const double *V, const double *lambda,
+                                 sinv_precision prec, double *X_S, void *stream);
+
+/* Wait for the handle's queued work on `stream` and return the first device
+ * error recorded since the last call (then clear it). */
+sinv_status sinv_sync_status(sinv_handle h, void *stream);
+
+/* Statistics of the symbolic analysis (host values). */
+typedef struct {
+    int64_t n, nnz_L, nnz_S_lo, n_blocks, n_2x2, n_supernodes, n_levels;
+    int64_t max_c, hit_pairs, max_width;
+    int64_t nnz_W;        /* pattern of the truncated series, 0 until sinv_ninv ran */
+    int32_t ninv_m;       /* m of that pattern                                        */
+} sinv_stats;
+sinv_status sinv_get_stats(sinv_handle h, sinv_stats *out);
+
+/* Supernode partition and levels (host arrays owned by the handle):
+ * sn_start[n_supernodes+1] (first column of each supernode, then n),
+ * sn_level[n_supernodes]. */
+sinv_status sinv_get_supernodes(sinv_handle h, const int32_t **sn_start, const int32_t **sn_level,
+                                int64_t *n_supernodes);
+
+const char *sinv_status_string(sinv_status s);
+/* Copies the handle's last error message (NUL terminated) into buf. */
+sinv_status sinv_last_error(sinv_handle h, char *buf, size_t len);
+void sinv_destroy(sinv_handle h);
+
+/* Tests the bounded-wait machinery every persistent kernel uses: launches one
+ * warp that waits, with the handle's poll limit, on a device flag that nothing
+ * sets, and returns the status that wait reports (SINV_ERR_TIMEOUT expected). */
+sinv_status sinv_debug_wait_timeout(sinv_handle h, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SINV_H */

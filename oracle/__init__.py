@@ -1,0 +1,45 @@
+"""ORACLE -- test infrastructure only.
+
+Plain, slow, obviously correct FP64 CPU implementations of what the selected-
+inverse path computes, written from the paper (Akter, Bollhoefer, Schenk,
+"Scalable Approximate Selected Inversion Based on Single-Level Incomplete
+LDL^T Factorization and Spectral Corrections"):
+
+* ``symbolic_S``      -- S = {(i,j): (L+D+L^T)_ij != 0}   (Section 1)
+* ``selinv``          -- scalar Takahashi recurrence, eqs. (2.4)-(2.5) with the
+                         restriction to S of Section 2.1       (C, csrc/selinv_ref.c)
+* ``ninv``            -- truncated Neumann series L^{-1} ~ sum_{t<=m} E_L^t,
+                         eq. (2.6), and (L^inv)^T D^{-1} L^inv, eq. (2.8), on S
+* ``mix``             -- Mix approximation (Section 2.3)
+* ``lowrank_correct`` -- A^inv + V_k Lambda_k V_k^T on S, eq. (2.9); diagonal
+                         update formula of Section 2.6
+* ``lanczos_einv``    -- dominant eigenpairs of E_inv = A^{-1} - A^inv
+                         (Section 2.5, Algorithm 1 step 5)
+* measures            -- err_1, fill_fact, fill_inv, DoDD (Sections 2.6, 3.2)
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA
+library: the one thing both sides use is the seeded input generator package
+``workloads`` (matrices, ordering and the ILDL factors, none of the selected-
+inverse arithmetic).
+
+Parity pins: see ``tests/test_oracle_pins.py``.  Every function here is pinned
+by at least one check that is not a re-typing of its own formula.
+"""
+from .core import (  # noqa: F401
+    symbolic_S,
+    selinv,
+    ninv,
+    ninv_W,
+    ninv_entries_sampled,
+    mix,
+    lowrank_correct,
+    lowrank_diag,
+    lanczos_einv,
+    err1,
+    fill_fact,
+    fill_inv,
+    dodd,
+    accept_modes,
+    build_lib,
+)

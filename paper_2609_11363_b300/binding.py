@@ -1,0 +1,225 @@
+"""ctypes binding of libsinv (argument marshalling only).
+
+Numeric calls take CUDA tensors (float64, contiguous) and run on the current
+torch stream unless a stream is given.  Index arrays for the symbolic call are
+host numpy arrays (the symbolic analysis runs on the host).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libsinv.so")
+_lib = None
+
+PREC = {"fp64": 0, "fp32": 1}
+STATUS = {
+    0: "SINV_OK", 1: "SINV_ERR_INVALID_ARG", 2: "SINV_ERR_PATTERN", 3: "SINV_ERR_SINGULAR_PIVOT",
+    4: "SINV_ERR_OOM", 5: "SINV_ERR_CUDA", 6: "SINV_ERR_TIMEOUT", 7: "SINV_ERR_UNSUPPORTED",
+}
+
+# every symbol include/sinv.h declares
+EXPORTS = [
+    "sinv_symbolic", "sinv_get_pattern", "sinv_get_pattern_host", "sinv_selinv", "sinv_ninv", "sinv_mix",
+    "sinv_lowrank_correct", "sinv_sync_status", "sinv_get_stats", "sinv_get_supernodes",
+    "sinv_status_string", "sinv_last_error", "sinv_destroy", "sinv_debug_wait_timeout",
+]
+
+
+class SinvError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = int(status)
+        self.name = STATUS.get(self.status, str(status))
+        super().__init__("%s: %s" % (self.name, msg))
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("supernode_cap", ctypes.c_int32), ("device", ctypes.c_int32), ("wait_limit", ctypes.c_int64)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("n", "nnz_L", "nnz_S_lo", "n_blocks", "n_2x2", "n_supernodes",
+                                              "n_levels", "max_c", "hit_pairs", "max_width", "nnz_W")] + [
+        ("ninv_m", ctypes.c_int32)]
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load_library():
+    """Load libsinv.so (build it first with ``paper_2609_11363_b300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError("libsinv.so not built at %s (run __graft_entry__.build())" % _LIB_PATH)
+    lib = ctypes.CDLL(_LIB_PATH)
+    P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    H = ctypes.c_void_p
+    lib.sinv_symbolic.argtypes = [I64, P, P, P, ctypes.POINTER(_Opts), ctypes.POINTER(H)]
+    lib.sinv_get_pattern.argtypes = [H, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I64)]
+    lib.sinv_get_pattern_host.argtypes = [H, P, P]
+    lib.sinv_selinv.argtypes = [H, P, P, ctypes.c_int, P, P]
+    lib.sinv_ninv.argtypes = [H, P, P, ctypes.c_int, ctypes.c_int, P, P]
+    lib.sinv_mix.argtypes = [H, P, P, D, P, P]
+    lib.sinv_lowrank_correct.argtypes = [H, ctypes.c_int, P, P, ctypes.c_int, P, P]
+    lib.sinv_sync_status.argtypes = [H, P]
+    lib.sinv_get_stats.argtypes = [H, ctypes.POINTER(_Stats)]
+    lib.sinv_get_supernodes.argtypes = [H, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I64)]
+    lib.sinv_status_string.argtypes = [ctypes.c_int]
+    lib.sinv_status_string.restype = ctypes.c_char_p
+    lib.sinv_last_error.argtypes = [H, ctypes.c_char_p, ctypes.c_size_t]
+    lib.sinv_destroy.argtypes = [H]
+    lib.sinv_destroy.restype = None
+    lib.sinv_debug_wait_timeout.argtypes = [H, P]
+    for name in EXPORTS:
+        f = getattr(lib, name)
+        if name not in ("sinv_status_string", "sinv_destroy"):
+            f.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check_tensor(t, name, numel=None, dtype=torch.float64):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch tensor" % name)
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s" % (name, dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if numel is not None and t.numel() != numel:
+        raise ValueError("%s has %d entries, expected %d" % (name, t.numel(), numel))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Handle:
+    """Symbolic analysis of one factor pattern; numeric calls reuse it.
+
+    ``L_rowptr`` (int64, n+1), ``L_col`` (int32), ``pivot_start`` (int8, n) are
+    host arrays describing strictly lower CSR L and the 1x1/2x2 pivot layout.
+    """
+
+    def __init__(self, n, L_rowptr, L_col, pivot_start, supernode_cap=16, device=0, wait_limit=0):
+        self._lib = load_library()
+        self._h = ctypes.c_void_p()
+        self.n = int(n)
+        rp = np.ascontiguousarray(L_rowptr, dtype=np.int64)
+        col = np.ascontiguousarray(L_col, dtype=np.int32)
+        ps = np.ascontiguousarray(pivot_start, dtype=np.int8)
+        if rp.shape != (self.n + 1,) or ps.shape != (self.n,):
+            raise ValueError("L_rowptr must have n+1 and pivot_start n entries")
+        opts = _Opts(int(supernode_cap), int(device), int(wait_limit))
+        self.device = torch.device("cuda", int(device)) if int(device) >= 0 else None
+        st = self._lib.sinv_symbolic(self.n, _np_ptr(rp), _np_ptr(col), _np_ptr(ps), ctypes.byref(opts),
+                                     ctypes.byref(self._h))
+        if st != 0:
+            msg = self.last_error()
+            self.close()
+            raise SinvError(st, msg)
+        s = self.stats()
+        self.nnz_S = s["nnz_S_lo"]
+        self.nnz_L = s["nnz_L"]
+        self.nD = self.n + s["n_2x2"]
+
+    # -- helpers -----------------------------------------------------------
+    def last_error(self) -> str:
+        if not self._h:
+            return ""
+        buf = ctypes.create_string_buffer(4096)
+        self._lib.sinv_last_error(self._h, buf, len(buf))
+        return buf.value.decode(errors="replace")
+
+    def _check(self, st):
+        if st != 0:
+            raise SinvError(st, self.last_error())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sinv_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stats(self) -> dict:
+        s = _Stats()
+        self._check(self._lib.sinv_get_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in _Stats._fields_}
+
+    def pattern_host(self):
+        rp = np.empty(self.n + 1, dtype=np.int64)
+        col = np.empty(max(self.nnz_S, 1), dtype=np.int32)
+        self._check(self._lib.sinv_get_pattern_host(self._h, _np_ptr(rp), _np_ptr(col)))
+        return rp, col[: self.nnz_S]
+
+    def pattern_device_ptrs(self):
+        rp, col, nnz = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int64()
+        self._check(self._lib.sinv_get_pattern(self._h, ctypes.byref(rp), ctypes.byref(col), ctypes.byref(nnz)))
+        return rp.value, col.value, nnz.value
+
+    def supernodes(self):
+        a, b, c = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int64()
+        self._check(self._lib.sinv_get_supernodes(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        ns = c.value
+        start = np.ctypeslib.as_array(ctypes.cast(a, ctypes.POINTER(ctypes.c_int32)), shape=(ns + 1,)).copy()
+        level = np.ctypeslib.as_array(ctypes.cast(b, ctypes.POINTER(ctypes.c_int32)), shape=(max(ns, 1),))[:ns].copy()
+        return start, level
+
+    def _out(self, out):
+        if out is None:
+            out = torch.empty(self.nnz_S, dtype=torch.float64, device=self.device)
+        return out
+
+    # -- numeric calls -----------------------------------------------------
+    def selinv(self, L_val, D_val, prec="fp64", out=None, stream=None):
+        out = self._out(out)
+        self._check(self._lib.sinv_selinv(self._h, _check_tensor(L_val, "L_val", self.nnz_L),
+                                          _check_tensor(D_val, "D_val", self.nD), PREC[prec],
+                                          _check_tensor(out, "G_S", self.nnz_S), _stream_ptr(stream)))
+        return out
+
+    def ninv(self, L_val, D_val, m, prec="fp64", out=None, stream=None):
+        out = self._out(out)
+        self._check(self._lib.sinv_ninv(self._h, _check_tensor(L_val, "L_val", self.nnz_L),
+                                        _check_tensor(D_val, "D_val", self.nD), int(m), PREC[prec],
+                                        _check_tensor(out, "N_S", self.nnz_S), _stream_ptr(stream)))
+        return out
+
+    def mix(self, G, N, eps, out=None, stream=None):
+        out = self._out(out)
+        self._check(self._lib.sinv_mix(self._h, _check_tensor(G, "G_S", self.nnz_S),
+                                       _check_tensor(N, "N_S", self.nnz_S), float(eps),
+                                       _check_tensor(out, "M_S", self.nnz_S), _stream_ptr(stream)))
+        return out
+
+    def lowrank_correct(self, V, lam, X, prec="fp64", stream=None):
+        k = int(lam.numel())
+        self._check(self._lib.sinv_lowrank_correct(self._h, k, _check_tensor(V, "V", self.n * k),
+                                                   _check_tensor(lam, "lambda", k), PREC[prec],
+                                                   _check_tensor(X, "X_S", self.nnz_S), _stream_ptr(stream)))
+        return X
+
+    def sync_status(self, stream=None):
+        self._check(self._lib.sinv_sync_status(self._h, _stream_ptr(stream)))
+
+    def debug_wait_timeout(self, stream=None) -> int:
+        return int(self._lib.sinv_debug_wait_timeout(self._h, _stream_ptr(stream)))

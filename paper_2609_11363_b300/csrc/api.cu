@@ -1,0 +1,469 @@
+// C ABI of libsinv (declared in include/sinv.h): handle management, the host
+// symbolic analysis upload and the numeric entry points.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/sinv.h"
+#include "kernels.h"
+#include "plan.h"
+
+using namespace sinv;
+
+struct sinv_handle_s {
+    int device = 0;
+    int num_sms = 0;
+    HostPlan P;
+    int64_t wait_limit = 4000000;  // polls (64 ns sleep each): a few seconds
+    // device copies of the plan
+    int64_t* dSrp = nullptr;
+    int32_t* dSc = nullptr;
+    int32_t* dSdiag = nullptr;
+    int32_t* dl2s = nullptr;
+    int64_t* dLrp = nullptr;
+    int64_t* dLcp = nullptr;
+    int32_t* dLri = nullptr;
+    int32_t* dLcsr = nullptr;
+    int32_t* ddpos = nullptr;
+    int8_t* dpstart = nullptr;
+    SnInfo* dsn = nullptr;
+    int32_t* dorder = nullptr;
+    int32_t* downer = nullptr;
+    int32_t* dCrow = nullptr;
+    int32_t* dLmap = nullptr;
+    int32_t* dJJl = nullptr;
+    int32_t* dJJs = nullptr;
+    uint32_t* dhit_ik = nullptr;
+    int32_t* dhit_pos = nullptr;
+    uint32_t* ddone = nullptr;
+    uint32_t* depoch = nullptr;
+    int32_t* dticket = nullptr;
+    int32_t* dstatus = nullptr;
+    uint32_t* ddebug_flag = nullptr;
+    double* dscratch = nullptr;
+    void* dwork = nullptr;
+    size_t work_bytes = 0;
+    int grid = 0;
+    // NInv pattern (built by the first sinv_ninv for a given m)
+    NinvPlan W;
+    int64_t* dWcp = nullptr;
+    int32_t* dWr = nullptr;
+    int32_t* dgrp = nullptr;
+    std::string last_error;
+};
+
+namespace {
+
+void set_err(sinv_handle h, const std::string& msg) {
+    if (h) h->last_error = msg;
+}
+
+sinv_status cuda_fail(sinv_handle h, cudaError_t e, const char* where) {
+    set_err(h, std::string(where) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? SINV_ERR_OOM : SINV_ERR_CUDA;
+}
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& src) {
+    size_t bytes = std::max<size_t>(src.size(), 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void**)dst, bytes);
+    if (e != cudaSuccess) return e;
+    if (!src.empty()) e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+void free_all(sinv_handle h) {
+    void* ptrs[] = {h->dSrp, h->dSc, h->dSdiag, h->dl2s, h->dLrp, h->dLcp, h->dLri, h->dLcsr, h->ddpos, h->dpstart,
+                    h->dsn, h->dorder, h->downer, h->dCrow, h->dLmap, h->dJJl, h->dJJs, h->dhit_ik, h->dhit_pos,
+                    h->ddone, h->depoch, h->dticket, h->dstatus, h->ddebug_flag, h->dscratch, h->dwork, h->dWcp,
+                    h->dWr, h->dgrp};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+sinv_status ensure_work(sinv_handle h, size_t bytes) {
+    if (bytes <= h->work_bytes) return SINV_OK;
+    if (h->dwork) cudaFree(h->dwork);
+    h->dwork = nullptr;
+    h->work_bytes = 0;
+    cudaError_t e = cudaMalloc(&h->dwork, bytes);
+    if (e != cudaSuccess) return cuda_fail(h, e, "work buffer");
+    h->work_bytes = bytes;
+    return SINV_OK;
+}
+
+bool valid_prec(int p) { return p == SINV_FP64 || p == SINV_FP32; }
+
+// numeric calls need a handle that lives on a device
+bool on_device(sinv_handle h) {
+    if (h->device >= 0) return true;
+    set_err(h, "handle was analysed host-only (device < 0): numeric calls are not available");
+    return false;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sinv_status_string(sinv_status s) {
+    switch (s) {
+        case SINV_OK: return "ok";
+        case SINV_ERR_INVALID_ARG: return "invalid argument";
+        case SINV_ERR_PATTERN: return "invalid sparsity pattern or pivot layout";
+        case SINV_ERR_SINGULAR_PIVOT: return "singular pivot block in D";
+        case SINV_ERR_OOM: return "out of memory";
+        case SINV_ERR_CUDA: return "CUDA error";
+        case SINV_ERR_TIMEOUT: return "device wait timed out";
+        case SINV_ERR_UNSUPPORTED: return "unsupported size or option";
+    }
+    return "unknown status";
+}
+
+sinv_status sinv_last_error(sinv_handle h, char* buf, size_t len) {
+    if (!h || !buf || len == 0) return SINV_ERR_INVALID_ARG;
+    size_t n = std::min(len - 1, h->last_error.size());
+    memcpy(buf, h->last_error.data(), n);
+    buf[n] = 0;
+    return SINV_OK;
+}
+
+sinv_status sinv_symbolic(int64_t n, const int64_t* L_rowptr, const int32_t* L_col, const int8_t* pivot_start,
+                          const sinv_symbolic_opts* opts, sinv_handle* out) {
+    if (!out) return SINV_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 0 || (n > 0 && (!L_rowptr || !pivot_start)) || (n > 0 && L_rowptr[n] > 0 && !L_col))
+        return SINV_ERR_INVALID_ARG;
+    sinv_handle h = new (std::nothrow) sinv_handle_s();
+    if (!h) return SINV_ERR_OOM;
+    int cap = 16;
+    if (opts) {
+        if (opts->supernode_cap > 0) cap = opts->supernode_cap;
+        h->device = opts->device;
+        if (opts->wait_limit > 0) h->wait_limit = opts->wait_limit;
+    }
+    cap = std::min(cap, selinv_max_width());
+    const bool host_only = h->device < 0;
+    cudaError_t e = cudaSuccess;
+    if (!host_only && (e = cudaSetDevice(h->device)) != cudaSuccess) {
+        sinv_status s = cuda_fail(h, e, "cudaSetDevice");
+        *out = h;  // so that the caller can read the message
+        return s;
+    }
+    std::string err;
+    try {
+        err = build_plan(n, L_rowptr, L_col, pivot_start, cap, h->P);
+    } catch (const std::bad_alloc&) {
+        set_err(h, "host allocation failed in the symbolic analysis");
+        *out = h;
+        return SINV_ERR_OOM;
+    }
+    if (!err.empty()) {
+        set_err(h, err);
+        *out = h;
+        return err.find("not supported") != std::string::npos || err.find("unsupported") != std::string::npos
+                   ? SINV_ERR_UNSUPPORTED
+                   : SINV_ERR_PATTERN;
+    }
+    HostPlan& P = h->P;
+    if (host_only) {
+        *out = h;
+        return SINV_OK;
+    }
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    std::vector<int64_t> Lrp(L_rowptr, L_rowptr + n + 1);
+#define UP(dst, src)                                              \
+    do {                                                          \
+        e = upload(&h->dst, src);                                 \
+        if (e != cudaSuccess) {                                   \
+            *out = h;                                             \
+            return cuda_fail(h, e, "upload " #dst);               \
+        }                                                         \
+    } while (0)
+    UP(dSrp, P.Srp);
+    UP(dSc, P.Sc);
+    UP(dSdiag, P.Sdiag);
+    UP(dl2s, P.l2s);
+    UP(dLrp, Lrp);
+    UP(dLcp, P.Lcp);
+    UP(dLri, P.Lri);
+    UP(dLcsr, P.Lcsr);
+    UP(ddpos, P.dpos);
+    UP(dpstart, P.pstart);
+    UP(dsn, P.sn);
+    UP(dorder, P.order);
+    UP(downer, P.owner);
+    UP(dCrow, P.Crow);
+    UP(dLmap, P.Lmap);
+    UP(dJJl, P.JJl);
+    UP(dJJs, P.JJs);
+    UP(dhit_ik, P.hit_ik);
+    UP(dhit_pos, P.hit_pos);
+#undef UP
+    size_t nsn = std::max<size_t>(P.sn.size(), 1);
+    if ((e = cudaMalloc((void**)&h->ddone, nsn * sizeof(uint32_t))) != cudaSuccess ||
+        (e = cudaMemset(h->ddone, 0, nsn * sizeof(uint32_t))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&h->depoch, 64)) != cudaSuccess || (e = cudaMemset(h->depoch, 0, 64)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&h->dticket, 64)) != cudaSuccess ||
+        (e = cudaMemset(h->dticket, 0, 64)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&h->dstatus, 64)) != cudaSuccess ||
+        (e = cudaMemset(h->dstatus, 0, 64)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&h->ddebug_flag, 64)) != cudaSuccess ||
+        (e = cudaMemset(h->ddebug_flag, 0, 64)) != cudaSuccess) {
+        *out = h;
+        return cuda_fail(h, e, "device state");
+    }
+    if ((e = selinv_configure()) != cudaSuccess || (e = ninv_configure()) != cudaSuccess) {
+        *out = h;
+        return cuda_fail(h, e, "kernel attributes");
+    }
+    h->grid = selinv_grid(h->num_sms);
+    if (P.max_cw > selinv_cw_smem()) {
+        size_t bytes = (size_t)h->grid * selinv_warps_per_cta() * 2 * (size_t)P.max_cw * sizeof(double);
+        if ((e = cudaMalloc((void**)&h->dscratch, bytes)) != cudaSuccess) {
+            *out = h;
+            return cuda_fail(h, e, "selinv scratch");
+        }
+    }
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
+        *out = h;
+        return cuda_fail(h, e, "symbolic upload");
+    }
+    *out = h;
+    return SINV_OK;
+}
+
+sinv_status sinv_get_pattern(sinv_handle h, const int64_t** S_rowptr, const int32_t** S_col, int64_t* nnzS_lo) {
+    if (!h || !S_rowptr || !S_col || !nnzS_lo) return SINV_ERR_INVALID_ARG;
+    *S_rowptr = h->dSrp;
+    *S_col = h->dSc;
+    *nnzS_lo = h->P.nnzS;
+    return SINV_OK;
+}
+
+sinv_status sinv_get_pattern_host(sinv_handle h, int64_t* S_rowptr, int32_t* S_col) {
+    if (!h || !S_rowptr || (!S_col && h->P.nnzS > 0)) return SINV_ERR_INVALID_ARG;
+    memcpy(S_rowptr, h->P.Srp.data(), h->P.Srp.size() * sizeof(int64_t));
+    if (h->P.nnzS > 0) memcpy(S_col, h->P.Sc.data(), h->P.Sc.size() * sizeof(int32_t));
+    return SINV_OK;
+}
+
+sinv_status sinv_get_stats(sinv_handle h, sinv_stats* s) {
+    if (!h || !s) return SINV_ERR_INVALID_ARG;
+    const HostPlan& P = h->P;
+    s->n = P.n;
+    s->nnz_L = P.nnzL;
+    s->nnz_S_lo = P.nnzS;
+    s->n_blocks = P.n_blocks;
+    s->n_2x2 = P.n_2x2;
+    s->n_supernodes = (int64_t)P.sn.size();
+    s->n_levels = P.n_levels;
+    s->max_c = P.max_c;
+    s->hit_pairs = P.hit_pairs;
+    s->max_width = P.max_w;
+    s->nnz_W = h->W.m >= 0 ? h->W.nnzW : 0;
+    s->ninv_m = h->W.m;
+    return SINV_OK;
+}
+
+sinv_status sinv_get_supernodes(sinv_handle h, const int32_t** sn_start, const int32_t** sn_level, int64_t* count) {
+    if (!h || !sn_start || !sn_level || !count) return SINV_ERR_INVALID_ARG;
+    *sn_start = h->P.sn_start.data();
+    *sn_level = h->P.sn_level.data();
+    *count = (int64_t)h->P.sn.size();
+    return SINV_OK;
+}
+
+sinv_status sinv_selinv(sinv_handle h, const double* L_val, const double* D_val, sinv_precision prec, double* G_S,
+                        void* stream) {
+    if (!h || !valid_prec(prec)) return SINV_ERR_INVALID_ARG;
+    if (!on_device(h)) return SINV_ERR_INVALID_ARG;
+    const HostPlan& P = h->P;
+    if (P.n == 0) return SINV_OK;
+    if (!D_val || !G_S || (P.nnzL > 0 && !L_val)) return SINV_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if (prec == SINV_FP32) {
+        sinv_status s = ensure_work(h, (size_t)P.nnzS * sizeof(float) + 256);
+        if (s != SINV_OK) return s;
+    }
+    SelinvArgs a;
+    a.sn = h->dsn;
+    a.order = h->dorder;
+    a.nsn = (int32_t)P.sn.size();
+    a.n = (int32_t)P.n;
+    a.owner = h->downer;
+    a.Crow = h->dCrow;
+    a.Lmap = h->dLmap;
+    a.JJl = h->dJJl;
+    a.JJs = h->dJJs;
+    a.hit_ik = h->dhit_ik;
+    a.hit_pos = h->dhit_pos;
+    a.Sdiag = h->dSdiag;
+    a.l2s = h->dl2s;
+    a.dpos = h->ddpos;
+    a.pstart = h->dpstart;
+    a.Lval = L_val;
+    a.Dval = D_val;
+    a.done = h->ddone;
+    a.epoch = h->depoch;
+    a.ticket = h->dticket;
+    a.status = h->dstatus;
+    a.wait_limit = h->wait_limit;
+    a.scratch = h->dscratch;
+    a.max_cw = P.max_cw;
+    a.nnzS = P.nnzS;
+    a.num_sms = h->num_sms;
+    if ((e = selinv_prepare(h->depoch, h->dticket, st)) != cudaSuccess) return cuda_fail(h, e, "selinv prepare");
+    if ((e = selinv_launch(a, prec == SINV_FP64 ? 0 : 1, h->dwork, G_S, st, h->grid)) != cudaSuccess)
+        return cuda_fail(h, e, "selinv launch");
+    return SINV_OK;
+}
+
+sinv_status sinv_ninv(sinv_handle h, const double* L_val, const double* D_val, int m, sinv_precision prec,
+                      double* N_S, void* stream) {
+    if (!h || !valid_prec(prec) || m < 0) return SINV_ERR_INVALID_ARG;
+    if (!on_device(h)) return SINV_ERR_INVALID_ARG;
+    if (m > 60) {
+        set_err(h, "m > 60 is not supported");
+        return SINV_ERR_UNSUPPORTED;
+    }
+    const HostPlan& P = h->P;
+    if (P.n == 0) return SINV_OK;
+    if (!D_val || !N_S || (P.nnzL > 0 && !L_val)) return SINV_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if (h->W.m != m) {
+        std::string err;
+        try {
+            err = build_ninv_plan(P, m, h->W);
+        } catch (const std::bad_alloc&) {
+            set_err(h, "host allocation failed building the Neumann pattern");
+            return SINV_ERR_OOM;
+        }
+        if (!err.empty()) {
+            h->W.m = -1;
+            set_err(h, err);
+            return SINV_ERR_UNSUPPORTED;
+        }
+        if (h->dWcp) cudaFree(h->dWcp);
+        if (h->dWr) cudaFree(h->dWr);
+        if (h->dgrp) cudaFree(h->dgrp);
+        h->dWcp = nullptr; h->dWr = nullptr; h->dgrp = nullptr;
+        if ((e = upload(&h->dWcp, h->W.Wcp)) != cudaSuccess || (e = upload(&h->dWr, h->W.Wr)) != cudaSuccess ||
+            (e = upload(&h->dgrp, h->W.grp)) != cudaSuccess) {
+            h->W.m = -1;
+            return cuda_fail(h, e, "upload Neumann pattern");
+        }
+    }
+    NinvArgs a;
+    a.n = P.n;
+    a.m = m;
+    a.Lcp = h->dLcp;
+    a.Lri = h->dLri;
+    a.Lcsr = h->dLcsr;
+    a.Wcp = h->dWcp;
+    a.Wr = h->dWr;
+    a.grp = h->dgrp;
+    a.Srp = h->dSrp;
+    a.Sc = h->dSc;
+    a.Lrp = h->dLrp;
+    a.nnzW = h->W.nnzW;
+    a.dpos = h->ddpos;
+    a.pstart = h->dpstart;
+    a.Lval = L_val;
+    a.Dval = D_val;
+    a.max_col = h->W.max_col;
+    a.num_sms = h->num_sms;
+    a.status = h->dstatus;
+    int p = prec == SINV_FP64 ? 0 : 1;
+    sinv_status s = ensure_work(h, ninv_work_bytes(a, p));
+    if (s != SINV_OK) return s;
+    if ((e = ninv_launch(a, p, h->dwork, N_S, st)) != cudaSuccess) return cuda_fail(h, e, "ninv launch");
+    return SINV_OK;
+}
+
+sinv_status sinv_mix(sinv_handle h, const double* G_S, const double* N_S, double eps, double* M_S, void* stream) {
+    if (!h) return SINV_ERR_INVALID_ARG;
+    if (!on_device(h)) return SINV_ERR_INVALID_ARG;
+    if (h->P.nnzS == 0) return SINV_OK;
+    if (!G_S || !N_S || !M_S) return SINV_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if ((e = mix_launch(G_S, N_S, eps, M_S, h->P.nnzS, h->num_sms, (cudaStream_t)stream)) != cudaSuccess)
+        return cuda_fail(h, e, "mix launch");
+    return SINV_OK;
+}
+
+sinv_status sinv_lowrank_correct(sinv_handle h, int k, const double* V, const double* lambda, sinv_precision prec,
+                                 double* X_S, void* stream) {
+    if (!h || k < 0 || !valid_prec(prec)) return SINV_ERR_INVALID_ARG;
+    if (!on_device(h)) return SINV_ERR_INVALID_ARG;
+    if (k > 256) {
+        set_err(h, "k > 256 is not supported");
+        return SINV_ERR_UNSUPPORTED;
+    }
+    if (k == 0 || h->P.n == 0) return SINV_OK;
+    if (!V || !lambda || !X_S) return SINV_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if (prec == SINV_FP32) {
+        sinv_status s = ensure_work(h, ((size_t)h->P.n * k + k) * sizeof(float) + 256);
+        if (s != SINV_OK) return s;
+    }
+    if ((e = lowrank_launch(h->P.n, h->dSrp, h->dSc, k, V, lambda, prec == SINV_FP64 ? 0 : 1, h->dwork, X_S,
+                            h->num_sms, (cudaStream_t)stream)) != cudaSuccess)
+        return cuda_fail(h, e, "lowrank launch");
+    return SINV_OK;
+}
+
+sinv_status sinv_sync_status(sinv_handle h, void* stream) {
+    if (!h) return SINV_ERR_INVALID_ARG;
+    if (!on_device(h)) return SINV_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if ((e = cudaStreamSynchronize((cudaStream_t)stream)) != cudaSuccess) return cuda_fail(h, e, "synchronize");
+    int32_t st = 0;
+    if ((e = cudaMemcpy(&st, h->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(h, e, "read status");
+    if (st != 0) {
+        cudaMemset(h->dstatus, 0, sizeof(int32_t));
+        if (st == SINV_ERR_TIMEOUT) {
+            set_err(h, "a device wait exceeded its poll limit");
+            return SINV_ERR_TIMEOUT;
+        }
+        if (st == SINV_ERR_SINGULAR_PIVOT) {
+            set_err(h, "a pivot block of D is singular");
+            return SINV_ERR_SINGULAR_PIVOT;
+        }
+        set_err(h, "internal device error " + std::to_string(st));
+        return SINV_ERR_CUDA;
+    }
+    return SINV_OK;
+}
+
+sinv_status sinv_debug_wait_timeout(sinv_handle h, void* stream) {
+    if (!h) return SINV_ERR_INVALID_ARG;
+    if (!on_device(h)) return SINV_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    int64_t limit = std::min<int64_t>(h->wait_limit, 200000);
+    if ((e = debug_wait_launch(h->ddebug_flag, h->dstatus, limit, (cudaStream_t)stream)) != cudaSuccess)
+        return cuda_fail(h, e, "debug wait launch");
+    return sinv_sync_status(h, stream);
+}
+
+void sinv_destroy(sinv_handle h) {
+    if (!h) return;
+    if (h->device >= 0) {
+        cudaSetDevice(h->device);
+        free_all(h);
+    }
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// Entry-wise work on S: Mix (Section 2.3) and the low-rank correction applied on
+// S as a sampled dense product (Section 2.5, eq. (2.9)).
+#include "device.cuh"
+#include "kernels.h"
+
+namespace sinv {
+
+namespace {
+
+// (A_Mix)_ij = G_ij if |G_ij| > eps else N_ij.  Streams 3 x 8 B in, 8 B out per entry.
+__global__ void mix_kernel(const double* __restrict__ G, const double* __restrict__ N, double eps,
+                           double* __restrict__ M, int64_t nnz) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool vec = ((((uintptr_t)G) | ((uintptr_t)N) | ((uintptr_t)M)) & 15) == 0;
+    if (vec) {
+        const int64_t n2 = nnz >> 1;
+        const double2* G2 = reinterpret_cast<const double2*>(G);
+        const double2* N2 = reinterpret_cast<const double2*>(N);
+        double2* M2 = reinterpret_cast<double2*>(M);
+        for (int64_t i = i0; i < n2; i += stride) {
+            double2 g = __ldcs(G2 + i), v = __ldcs(N2 + i), r;
+            r.x = fabs(g.x) > eps ? g.x : v.x;
+            r.y = fabs(g.y) > eps ? g.y : v.y;
+            __stcs(M2 + i, r);
+        }
+        if (i0 == 0 && (nnz & 1)) {
+            int64_t i = nnz - 1;
+            M[i] = fabs(G[i]) > eps ? G[i] : N[i];
+        }
+    } else {
+        for (int64_t i = i0; i < nnz; i += stride) M[i] = fabs(G[i]) > eps ? G[i] : N[i];
+    }
+}
+
+constexpr int kLrWarps = 8;
+constexpr int kKMax = 256;
+
+// One warp per row i of S_lo: u = lambda .* V_i staged in shared memory, then
+// every entry (i, j) of the row adds u . V_j.  R is the product type.
+template <class R>
+__global__ void __launch_bounds__(kLrWarps * 32) lowrank_kernel(int64_t n, const int64_t* __restrict__ Srp,
+                                                                const int32_t* __restrict__ Sc, int k,
+                                                                const R* __restrict__ V, const R* __restrict__ lam,
+                                                                double* __restrict__ X) {
+    __shared__ R u_s[kLrWarps][kKMax];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    R* u = u_s[wid];
+    const int64_t nwarps = (int64_t)gridDim.x * kLrWarps;
+    for (int64_t i = (int64_t)blockIdx.x * kLrWarps + wid; i < n; i += nwarps) {
+        for (int l = lane; l < k; l += 32) u[l] = lam[l] * V[i * k + l];
+        __syncwarp();
+        const int64_t e0 = Srp[i], e1 = Srp[i + 1];
+        for (int64_t e = e0 + lane; e < e1; e += 32) {
+            const R* vj = V + (int64_t)Sc[e] * k;
+            R s0 = R(0), s1 = R(0), s2 = R(0), s3 = R(0);
+            int l = 0;
+            for (; l + 4 <= k; l += 4) {
+                s0 += u[l] * vj[l];
+                s1 += u[l + 1] * vj[l + 1];
+                s2 += u[l + 2] * vj[l + 2];
+                s3 += u[l + 3] * vj[l + 3];
+            }
+            for (; l < k; ++l) s0 += u[l] * vj[l];
+            X[e] += (double)((s0 + s1) + (s2 + s3));
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void to_float(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+__global__ void debug_wait_kernel(uint32_t* flag, int32_t* status, int64_t limit) {
+    if (threadIdx.x == 0) wait_flag(flag, 0xFFFFFFFFu, status, limit);
+}
+
+}  // namespace
+
+cudaError_t mix_launch(const double* G, const double* N, double eps, double* M, int64_t nnz, int num_sms,
+                       cudaStream_t st) {
+    if (nnz == 0) return cudaSuccess;
+    int64_t blocks = (nnz / 2 + 255) / 256;
+    int grid = (int)std::min<int64_t>(std::max<int64_t>(blocks, 1), (int64_t)num_sms * 8);
+    mix_kernel<<<grid, 256, 0, st>>>(G, N, eps, M, nnz);
+    return cudaGetLastError();
+}
+
+cudaError_t lowrank_launch(int64_t n, const int64_t* Srp, const int32_t* Sc, int k, const double* V,
+                           const double* lambda, int prec, void* work, double* X, int num_sms,
+                           cudaStream_t st) {
+    if (n == 0 || k == 0) return cudaSuccess;
+    int64_t blocks = (n + kLrWarps - 1) / kLrWarps;
+    int grid = (int)std::min<int64_t>(blocks, (int64_t)num_sms * 16);
+    if (prec == 0) {
+        lowrank_kernel<double><<<grid, kLrWarps * 32, 0, st>>>(n, Srp, Sc, k, V, lambda, X);
+    } else {
+        float* Vf = reinterpret_cast<float*>(work);
+        float* lf = Vf + n * (int64_t)k;
+        to_float<<<num_sms * 4, 256, 0, st>>>(V, Vf, n * (int64_t)k);
+        to_float<<<1, 256, 0, st>>>(lambda, lf, k);
+        lowrank_kernel<float><<<grid, kLrWarps * 32, 0, st>>>(n, Srp, Sc, k, Vf, lf, X);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t debug_wait_launch(uint32_t* flag, int32_t* status, int64_t limit, cudaStream_t st) {
+    debug_wait_kernel<<<1, 32, 0, st>>>(flag, status, limit);
+    return cudaGetLastError();
+}
+
+}  // namespace sinv

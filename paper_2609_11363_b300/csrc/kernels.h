@@ -1,0 +1,85 @@
+// Launch interfaces of the device kernels (internal to libsinv).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "plan.h"
+
+namespace sinv {
+
+struct SelinvArgs {
+    const SnInfo* sn;
+    const int32_t* order;
+    int32_t nsn;
+    int32_t n;
+    const int32_t* owner;
+    const int32_t* Crow;
+    const int32_t* Lmap;
+    const int32_t* JJl;
+    const int32_t* JJs;
+    const uint32_t* hit_ik;
+    const int32_t* hit_pos;
+    const int32_t* Sdiag;
+    const int32_t* l2s;
+    const int32_t* dpos;
+    const int8_t* pstart;
+    const double* Lval;
+    const double* Dval;
+    uint32_t* done;
+    const uint32_t* epoch;  // device word, bumped by selinv_prepare before each launch
+    int32_t* ticket;
+    int32_t* status;
+    int64_t wait_limit;
+    double* scratch;
+    int64_t max_cw;
+    int64_t nnzS;
+    int32_t num_sms;
+};
+
+cudaError_t selinv_configure();
+// epoch += 1 (skipping 0) and ticket = 0, in stream order: keeps the launch graph-capturable
+cudaError_t selinv_prepare(uint32_t* epoch, int32_t* ticket, cudaStream_t st);
+int selinv_grid(int num_sms);
+int selinv_max_width();
+int selinv_cw_smem();
+int selinv_warps_per_cta();
+// prec: 0 = FP64 (writes G_out directly), 1 = FP32 (working copy in `work`, |S_lo| floats)
+cudaError_t selinv_launch(const SelinvArgs& a, int prec, void* work, double* G_out, cudaStream_t st, int grid);
+
+cudaError_t mix_launch(const double* G, const double* N, double eps, double* M, int64_t nnz, int num_sms,
+                       cudaStream_t st);
+
+// X_S += sum_l lambda_l V_il V_jl on S_lo.  prec 0: FP64; 1: FP32 products (V converted
+// once into `work`, n*k floats), FP64 accumulation into X.
+cudaError_t lowrank_launch(int64_t n, const int64_t* Srp, const int32_t* Sc, int k, const double* V,
+                           const double* lambda, int prec, void* work, double* X, int num_sms,
+                           cudaStream_t st);
+
+struct NinvArgs {
+    int64_t n;
+    int m;
+    const int64_t* Lcp;   // E by columns (struct(j)), CSR positions of L values
+    const int32_t* Lri;
+    const int32_t* Lcsr;
+    const int64_t* Wcp;   // P_W by columns, grouped by first power
+    const int32_t* Wr;
+    const int32_t* grp;
+    const int64_t* Srp;   // S_lo
+    const int32_t* Sc;
+    const int64_t* Lrp;   // L row pointers (CSR of the caller's L)
+    int64_t nnzW;
+    const int32_t* dpos;
+    const int8_t* pstart;
+    const double* Lval;
+    const double* Dval;
+    int64_t max_col;
+    int32_t num_sms;
+    int32_t* status;
+};
+cudaError_t ninv_configure();
+size_t ninv_work_bytes(const NinvArgs& a, int prec);
+cudaError_t ninv_launch(const NinvArgs& a, int prec, void* work, double* N_out, cudaStream_t st);
+
+cudaError_t debug_wait_launch(uint32_t* flag, int32_t* status, int64_t limit, cudaStream_t st);
+
+}  // namespace sinv

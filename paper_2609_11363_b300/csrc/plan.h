@@ -1,0 +1,66 @@
+// Internal data layout shared by the host symbolic analysis and the kernels.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace sinv {
+
+// One supernode: consecutive pivot blocks [s0, s0 + w) processed as one dense
+// step of the Takahashi recurrence.  C is the sorted set of rows below the
+// supernode touched by any of its columns (|C| = c).
+struct SnInfo {
+    int32_t s0, w, c, level;
+    int64_t crow_off;  // Crow[crow_off .. +c): global row of each local row
+    int64_t cw_off;    // Lmap[cw_off .. +c*w): CSR position of L(C[i], s0+t), row-major (i, t), or -1
+    int64_t ww_off;    // JJl / JJs [ww_off .. +w*w): within-supernode maps, row-major (a, b)
+    int64_t hit_off;   // hit arrays [hit_off .. +hit_cnt)
+    int64_t hit_cnt;   // pairs (i, k), k < i, with (C[i], C[k]) in S
+};
+
+struct HostPlan {
+    int64_t n = 0, nnzL = 0, nnzS = 0;
+    // S_lo
+    std::vector<int64_t> Srp;
+    std::vector<int32_t> Sc;
+    std::vector<int32_t> Sdiag;   // position of (i, i) in S_lo
+    std::vector<int32_t> l2s;     // S_lo position of each L entry (CSR order)
+    // L by columns (struct(j)), with the CSR position of each entry
+    std::vector<int64_t> Lcp;
+    std::vector<int32_t> Lri;
+    std::vector<int32_t> Lcsr;
+    // pivot blocks
+    std::vector<int8_t> pstart;
+    std::vector<int32_t> dpos;    // per column: offset of its block's first value in D_val
+    int64_t nD = 0, n_blocks = 0, n_2x2 = 0;
+    // supernodes
+    std::vector<SnInfo> sn;
+    std::vector<int32_t> sn_start;   // first column of each supernode, then n
+    std::vector<int32_t> sn_level;
+    std::vector<int32_t> owner;      // supernode of each column
+    std::vector<int32_t> order;      // processing order (level-major)
+    std::vector<int32_t> Crow, Lmap, JJl, JJs;
+    std::vector<uint32_t> hit_ik;    // (i << 16) | k
+    std::vector<int32_t> hit_pos;    // S_lo position of (C[i], C[k])
+    int64_t n_levels = 0, max_c = 0, max_w = 0, max_cw = 0, hit_pairs = 0;
+};
+
+// Neumann-series pattern P_W = pattern(sum_{t<=m} E^t), stored by columns.
+// Column j lists its rows grouped by the first power t that reaches them
+// (t = 0 is row j itself), each group sorted by row; grp[j*(m+2) + t] is the
+// start of group t inside column j (relative to Wcp[j]), grp[j*(m+2)+m+1] its end.
+struct NinvPlan {
+    int m = -1;
+    int64_t nnzW = 0;
+    std::vector<int64_t> Wcp;
+    std::vector<int32_t> Wr;
+    std::vector<int32_t> grp;
+    int64_t max_col = 0;
+};
+
+// Returns an empty string on success, else the reason the pattern is invalid.
+std::string build_plan(int64_t n, const int64_t* L_rowptr, const int32_t* L_col,
+                       const int8_t* pivot_start, int supernode_cap, HostPlan& P);
+std::string build_ninv_plan(const HostPlan& P, int m, NinvPlan& W);
+
+}  // namespace sinv

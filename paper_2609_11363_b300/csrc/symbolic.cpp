@@ -1,0 +1,404 @@
+// Host symbolic analysis: validation of L's pattern and the pivot layout, the
+// pattern S (Section 1), pivot blocks, supernodes of the block elimination tree
+// (Section 2.1, Fig. 2), dependency levels and the index maps of the numeric
+// kernels.  Everything here is integer work and is deterministic.
+#include <algorithm>
+#include <cstring>
+#include <thread>
+
+#include "plan.h"
+
+namespace sinv {
+
+namespace {
+
+int n_threads() {
+    unsigned h = std::thread::hardware_concurrency();
+    return h == 0 ? 4 : (int)std::min(h, 32u);
+}
+
+template <class F>
+void parallel_for(int64_t count, F f) {
+    int T = n_threads();
+    if (count < 4096 || T == 1) {
+        f(0, count);
+        return;
+    }
+    std::vector<std::thread> th;
+    int64_t chunk = (count + T - 1) / T;
+    for (int t = 0; t < T; ++t) {
+        int64_t a = t * chunk, b = std::min(count, a + chunk);
+        if (a >= b) break;
+        th.emplace_back([=, &f] { f(a, b); });
+    }
+    for (auto& x : th) x.join();
+}
+
+// is sorted list a (minus the values in [ex0, ex1)) a subset of sorted list b?
+bool subset_except(const int32_t* a, int64_t na, const int32_t* b, int64_t nb, int32_t ex0, int32_t ex1) {
+    int64_t j = 0;
+    for (int64_t i = 0; i < na; ++i) {
+        int32_t v = a[i];
+        if (v >= ex0 && v < ex1) continue;
+        while (j < nb && b[j] < v) ++j;
+        if (j == nb || b[j] != v) return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+std::string build_plan(int64_t n, const int64_t* Lrp, const int32_t* Lc, const int8_t* ps, int cap,
+                       HostPlan& P) {
+    if (n < 0) return "negative n";
+    if (n > INT32_MAX - 1) return "n does not fit int32 column indices";
+    if (cap <= 0) cap = 16;
+    if (cap > 64) cap = 64;
+    P = HostPlan();
+    P.n = n;
+    if (n == 0) {
+        P.Srp.assign(1, 0);
+        P.sn_start.assign(1, 0);
+        P.Lcp.assign(1, 0);
+        return "";
+    }
+    if (Lrp[0] != 0) return "L_rowptr[0] != 0";
+    for (int64_t i = 0; i < n; ++i)
+        if (Lrp[i + 1] < Lrp[i]) return "L_rowptr not nondecreasing at row " + std::to_string(i);
+    int64_t nnzL = Lrp[n];
+    P.nnzL = nnzL;
+    if (nnzL > INT32_MAX) return "nnz(L) >= 2^31 not supported";
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t q = Lrp[i]; q < Lrp[i + 1]; ++q) {
+            int32_t c = Lc[q];
+            if (c < 0 || c >= i) return "L entry out of the strictly lower triangle at row " + std::to_string(i);
+            if (q > Lrp[i] && Lc[q - 1] >= c) return "L row " + std::to_string(i) + " not strictly increasing";
+        }
+    }
+    // pivot layout
+    P.pstart.assign(ps, ps + n);
+    for (int64_t j = 0; j < n; ++j) {
+        if (ps[j] != 0 && ps[j] != 1) return "pivot_start values must be 0 or 1";
+    }
+    if (ps[0] != 1) return "pivot_start[0] must be 1";
+    for (int64_t j = 1; j < n; ++j) {
+        if (ps[j] == 0) {
+            if (ps[j - 1] == 0) return "pivot block larger than 2x2 at column " + std::to_string(j);
+            // L(j, j-1) must not be stored: last entry of row j is < j-1
+            if (Lrp[j + 1] > Lrp[j] && Lc[Lrp[j + 1] - 1] == j - 1)
+                return "L(j, j-1) stored inside a 2x2 pivot block at row " + std::to_string(j);
+        }
+    }
+    P.dpos.resize(n);
+    {
+        int64_t off = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (ps[j]) {
+                P.n_blocks++;
+                bool two = (j + 1 < n) && ps[j + 1] == 0;
+                P.dpos[j] = (int32_t)off;
+                if (two) {
+                    P.dpos[j + 1] = (int32_t)off;
+                    P.n_2x2++;
+                    off += 3;
+                } else {
+                    off += 1;
+                }
+            }
+        }
+        P.nD = off;
+    }
+    // S_lo: row i = L row i, then (i-1) for the second column of a 2x2 block, then i
+    P.Srp.resize(n + 1);
+    P.Srp[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t len = (Lrp[i + 1] - Lrp[i]) + 1 + ((i > 0 && ps[i] == 0) ? 1 : 0);
+        P.Srp[i + 1] = P.Srp[i] + len;
+    }
+    P.nnzS = P.Srp[n];
+    if (P.nnzS > INT32_MAX) return "|S_lo| >= 2^31 not supported";
+    P.Sc.resize(P.nnzS);
+    P.Sdiag.resize(n);
+    P.l2s.resize(nnzL);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t s = P.Srp[i];
+        for (int64_t q = Lrp[i]; q < Lrp[i + 1]; ++q) {
+            P.l2s[q] = (int32_t)s;
+            P.Sc[s++] = Lc[q];
+        }
+        if (i > 0 && ps[i] == 0) P.Sc[s++] = (int32_t)(i - 1);
+        P.Sdiag[i] = (int32_t)s;
+        P.Sc[s++] = (int32_t)i;
+    }
+    // L by columns
+    P.Lcp.assign(n + 1, 0);
+    for (int64_t q = 0; q < nnzL; ++q) P.Lcp[Lc[q] + 1]++;
+    for (int64_t j = 0; j < n; ++j) P.Lcp[j + 1] += P.Lcp[j];
+    P.Lri.resize(nnzL);
+    P.Lcsr.resize(nnzL);
+    {
+        std::vector<int64_t> fill(P.Lcp.begin(), P.Lcp.end() - 1);
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t q = Lrp[i]; q < Lrp[i + 1]; ++q) {
+                int64_t d = fill[Lc[q]]++;
+                P.Lri[d] = (int32_t)i;
+                P.Lcsr[d] = (int32_t)q;
+            }
+    }
+    const int64_t* Lcp = P.Lcp.data();
+    const int32_t* Lri = P.Lri.data();
+
+    // pivot blocks and their row unions U_P (rows below the block)
+    std::vector<int32_t> bstart;
+    for (int64_t j = 0; j < n; ++j)
+        if (ps[j]) bstart.push_back((int32_t)j);
+    int64_t nb = (int64_t)bstart.size();
+    bstart.push_back((int32_t)n);
+    auto block_union = [&](int64_t b, std::vector<int32_t>& U) {
+        U.clear();
+        int32_t c0 = bstart[b], c1 = bstart[b + 1];
+        for (int32_t c = c0; c < c1; ++c)
+            for (int64_t q = Lcp[c]; q < Lcp[c + 1]; ++q)
+                if (Lri[q] >= c1) U.push_back(Lri[q]);
+        std::sort(U.begin(), U.end());
+        U.erase(std::unique(U.begin(), U.end()), U.end());
+    };
+    // merge rule between consecutive blocks b and b+1 (b+1 joins b's supernode):
+    //  (a) the first column of block b+1 is in U_b (block b+1 is b's parent)
+    //  (b) U_b minus block b+1 is contained in struct(c) for every column c of block b+1
+    //  (c) the supernode stays within the width cap
+    // Under (b) for every consecutive pair, every pair of rows (a, r) that a block of
+    // the supernode reads from a later column a of the same supernode is in S, so the
+    // dense supernodal step equals the scalar recurrence in exact arithmetic.
+    std::vector<char> joins(nb, 0);
+    parallel_for(nb - 1, [&](int64_t a, int64_t b) {
+        std::vector<int32_t> U;
+        for (int64_t q = a; q < b; ++q) {
+            block_union(q, U);
+            int32_t n0 = bstart[q + 1], n1 = bstart[q + 2];
+            if (U.empty() || U[0] != n0) continue;
+            bool ok = true;
+            for (int32_t c = n0; c < n1 && ok; ++c)
+                ok = subset_except(U.data(), (int64_t)U.size(), Lri + Lcp[c], Lcp[c + 1] - Lcp[c], n0, n1);
+            joins[q] = ok;
+        }
+    });
+    P.sn_start.clear();
+    {
+        int64_t b = 0;
+        while (b < nb) {
+            int32_t s0 = bstart[b];
+            int64_t e = b + 1;
+            while (e < nb && joins[e - 1] && (bstart[e + 1] - s0) <= cap) ++e;
+            P.sn_start.push_back(s0);
+            b = e;
+        }
+        P.sn_start.push_back((int32_t)n);
+    }
+    int64_t ns = (int64_t)P.sn_start.size() - 1;
+    P.owner.resize(n);
+    for (int64_t s = 0; s < ns; ++s)
+        for (int32_t c = P.sn_start[s]; c < P.sn_start[s + 1]; ++c) P.owner[c] = (int32_t)s;
+    // C_J per supernode
+    P.sn.resize(ns);
+    std::vector<std::vector<int32_t>> Cs(ns);
+    parallel_for(ns, [&](int64_t a, int64_t b) {
+        for (int64_t s = a; s < b; ++s) {
+            int32_t s0 = P.sn_start[s], s1 = P.sn_start[s + 1];
+            auto& C = Cs[s];
+            for (int32_t c = s0; c < s1; ++c)
+                for (int64_t q = Lcp[c]; q < Lcp[c + 1]; ++q)
+                    if (Lri[q] >= s1) C.push_back(Lri[q]);
+            std::sort(C.begin(), C.end());
+            C.erase(std::unique(C.begin(), C.end()), C.end());
+        }
+    });
+    // levels: 0 if C empty, else 1 + max level of the supernodes owning rows of C
+    P.sn_level.assign(ns, 0);
+    for (int64_t s = ns - 1; s >= 0; --s) {
+        int32_t lv = -1;
+        for (int32_t r : Cs[s]) lv = std::max(lv, P.sn_level[P.owner[r]]);
+        P.sn_level[s] = lv + 1;
+    }
+    int32_t maxlev = 0;
+    for (int64_t s = 0; s < ns; ++s) maxlev = std::max(maxlev, P.sn_level[s]);
+    P.n_levels = ns ? maxlev + 1 : 0;
+    // offsets
+    int64_t crow = 0, cw = 0, ww = 0;
+    for (int64_t s = 0; s < ns; ++s) {
+        SnInfo& I = P.sn[s];
+        I.s0 = P.sn_start[s];
+        I.w = P.sn_start[s + 1] - P.sn_start[s];
+        I.c = (int32_t)Cs[s].size();
+        I.level = P.sn_level[s];
+        if (I.c > 65535) return "a supernode touches more than 65535 rows: unsupported";
+        I.crow_off = crow; crow += I.c;
+        I.cw_off = cw; cw += (int64_t)I.c * I.w;
+        I.ww_off = ww; ww += (int64_t)I.w * I.w;
+        P.max_c = std::max<int64_t>(P.max_c, I.c);
+        P.max_w = std::max<int64_t>(P.max_w, I.w);
+        P.max_cw = std::max<int64_t>(P.max_cw, (int64_t)I.c * I.w);
+    }
+    P.Crow.resize(crow);
+    P.Lmap.assign(cw, -1);
+    P.JJl.assign(ww, -1);
+    P.JJs.assign(ww, -1);
+    // hit pairs: count, then fill
+    std::vector<int64_t> hits(ns, 0);
+    auto S_row_hits = [&](int64_t s, bool fill, uint32_t* ik, int32_t* pos) {
+        const auto& C = Cs[s];
+        int64_t cnt = 0;
+        for (int64_t i = 1; i < (int64_t)C.size(); ++i) {
+            int32_t r = C[i];
+            int64_t q = P.Srp[r], qe = P.Srp[r + 1];
+            int64_t k = 0;
+            while (q < qe && k < i) {
+                int32_t a = P.Sc[q], b = C[k];
+                if (a == b) {
+                    if (fill) {
+                        ik[cnt] = ((uint32_t)i << 16) | (uint32_t)k;
+                        pos[cnt] = (int32_t)q;
+                    }
+                    ++cnt; ++q; ++k;
+                } else if (a < b) {
+                    ++q;
+                } else {
+                    ++k;
+                }
+            }
+        }
+        return cnt;
+    };
+    parallel_for(ns, [&](int64_t a, int64_t b) {
+        for (int64_t s = a; s < b; ++s) hits[s] = S_row_hits(s, false, nullptr, nullptr);
+    });
+    int64_t hoff = 0;
+    for (int64_t s = 0; s < ns; ++s) {
+        P.sn[s].hit_off = hoff;
+        P.sn[s].hit_cnt = hits[s];
+        hoff += hits[s];
+    }
+    P.hit_pairs = hoff;
+    P.hit_ik.resize(hoff);
+    P.hit_pos.resize(hoff);
+    parallel_for(ns, [&](int64_t a, int64_t b) {
+        for (int64_t s = a; s < b; ++s) {
+            SnInfo& I = P.sn[s];
+            S_row_hits(s, true, P.hit_ik.data() + I.hit_off, P.hit_pos.data() + I.hit_off);
+            const auto& C = Cs[s];
+            std::copy(C.begin(), C.end(), P.Crow.begin() + I.crow_off);
+            // Lmap: L(C[i], s0+t)
+            for (int32_t t = 0; t < I.w; ++t) {
+                int32_t col = I.s0 + t;
+                int64_t i = 0;
+                for (int64_t q = Lcp[col]; q < Lcp[col + 1]; ++q) {
+                    int32_t r = Lri[q];
+                    if (r < I.s0 + I.w) {
+                        // inside the supernode: L_JJ(r - s0, t)
+                        P.JJl[I.ww_off + (int64_t)(r - I.s0) * I.w + t] = P.Lcsr[q];
+                        continue;
+                    }
+                    while (C[i] < r) ++i;
+                    P.Lmap[I.cw_off + i * I.w + t] = P.Lcsr[q];
+                }
+            }
+            // JJs: S positions of (s0+a, s0+b), a >= b
+            for (int32_t aa = 0; aa < I.w; ++aa) {
+                int32_t r = I.s0 + aa;
+                for (int64_t q = P.Srp[r]; q < P.Srp[r + 1]; ++q) {
+                    int32_t c = P.Sc[q];
+                    if (c >= I.s0) P.JJs[I.ww_off + (int64_t)aa * I.w + (c - I.s0)] = (int32_t)q;
+                }
+            }
+        }
+    });
+    // processing order: level-major, larger c first inside a level
+    P.order.resize(ns);
+    for (int64_t s = 0; s < ns; ++s) P.order[s] = (int32_t)(ns - 1 - s);
+    std::stable_sort(P.order.begin(), P.order.end(), [&](int32_t a, int32_t b) {
+        if (P.sn[a].level != P.sn[b].level) return P.sn[a].level < P.sn[b].level;
+        return P.sn[a].c > P.sn[b].c;
+    });
+    return "";
+}
+
+// Pattern of sum_{t<=m} E^t by columns: R_t(j) = {j} u union_{k in struct(j)} R_{t-1}(k),
+// computed for t = 1..m, with each row tagged by the first t that reaches it.
+std::string build_ninv_plan(const HostPlan& P, int m, NinvPlan& W) {
+    int64_t n = P.n;
+    W = NinvPlan();
+    W.m = m;
+    const int64_t* Lcp = P.Lcp.data();
+    const int32_t* Lri = P.Lri.data();
+    // dist-tagged columns, built per power: cur[j] = rows of R_t(j) sorted, with tag
+    std::vector<std::vector<int32_t>> rows(n), tags(n);
+    for (int64_t j = 0; j < n; ++j) {
+        rows[j].push_back((int32_t)j);
+        tags[j].push_back(0);
+    }
+    for (int t = 1; t <= m; ++t) {
+        std::vector<std::vector<int32_t>> nrows(n), ntags(n);
+        parallel_for(n, [&](int64_t a, int64_t b) {
+            // per-thread dense markers: mark[r] == j when row r is already in R_t(j)
+            std::vector<int32_t> mark(n, -1), best(n, 0), list;
+            for (int64_t j = a; j < b; ++j) {
+                list.clear();
+                auto add = [&](int32_t r, int32_t tg) {
+                    if (mark[r] != (int32_t)j) {
+                        mark[r] = (int32_t)j;
+                        best[r] = tg;
+                        list.push_back(r);
+                    } else if (tg < best[r]) {
+                        best[r] = tg;
+                    }
+                };
+                for (size_t e = 0; e < rows[j].size(); ++e) add(rows[j][e], tags[j][e]);
+                for (int64_t q = Lcp[j]; q < Lcp[j + 1]; ++q) {
+                    int32_t k = Lri[q];
+                    // rows reached from k within t-1 steps are reached from j within t
+                    const auto& rk = rows[k];
+                    const auto& tk = tags[k];
+                    for (size_t e = 0; e < rk.size(); ++e)
+                        if (tk[e] <= t - 1) add(rk[e], tk[e] + 1);
+                }
+                std::sort(list.begin(), list.end());
+                auto& R = nrows[j];
+                auto& T = ntags[j];
+                R.resize(list.size());
+                T.resize(list.size());
+                for (size_t e = 0; e < list.size(); ++e) {
+                    R[e] = list[e];
+                    T[e] = best[list[e]];
+                }
+            }
+        });
+        rows.swap(nrows);
+        tags.swap(ntags);
+    }
+    W.Wcp.assign(n + 1, 0);
+    for (int64_t j = 0; j < n; ++j) W.Wcp[j + 1] = W.Wcp[j] + (int64_t)rows[j].size();
+    W.nnzW = W.Wcp[n];
+    if (W.nnzW > INT32_MAX) return "pattern of the truncated Neumann series has >= 2^31 entries";
+    W.Wr.resize(W.nnzW);
+    W.grp.assign((size_t)n * (m + 2), 0);
+    parallel_for(n, [&](int64_t a, int64_t b) {
+        std::vector<std::pair<int32_t, int32_t>> buf;
+        for (int64_t j = a; j < b; ++j) {
+            buf.clear();
+            for (size_t e = 0; e < rows[j].size(); ++e) buf.push_back({tags[j][e], rows[j][e]});
+            std::sort(buf.begin(), buf.end());
+            int64_t base = W.Wcp[j];
+            int32_t* g = W.grp.data() + (size_t)j * (m + 2);
+            int t = 0;
+            for (size_t e = 0; e < buf.size(); ++e) {
+                while (t <= buf[e].first) g[t++] = (int32_t)e;
+                W.Wr[base + e] = buf[e].second;
+            }
+            while (t <= m + 1) g[t++] = (int32_t)buf.size();
+        }
+    });
+    for (int64_t j = 0; j < n; ++j) W.max_col = std::max<int64_t>(W.max_col, W.Wcp[j + 1] - W.Wcp[j]);
+    return "";
+}
+
+}  // namespace sinv

@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: FP64 forms within 1e-10 entrywise in the scaled sense
+|x_ij - r_ij| <= 1e-10 (|r_ij| + sqrt|r_ii r_jj|); the pattern S bit-exact;
+Mix bit-exact (it only selects); FP32 forms normwise within the bound stated
+in each test.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from tests.helpers import normwise, sel_rel_err
+from workloads.configs import diff3d, lap2d_32, plant_2x2, random_factors, random_lowrank
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def _handle(f, **kw):
+    from paper_2609_11363_b300 import Handle
+    return Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start, **kw)
+
+
+def _oracle_all(f, m):
+    S = oracle.symbolic_S(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+    G = oracle.selinv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, S)
+    N = oracle.ninv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, m, S)
+    return S, G, N
+
+
+CASES = {
+    "lap2d_tau1e-2": lambda: lap2d_32().factors,
+    "lap2d_exact": lambda: lap2d_32(tau=0.0).factors,
+    "lap2d_planted2x2": lambda: plant_2x2(lap2d_32().factors, 0.3, 11),
+    "random_nonclosed": lambda: random_factors(700, 0.02, 0.15, 5),
+    "random_dense_rows": lambda: random_factors(300, 0.25, 0.1, 6, scale=0.1),
+    "diff3d_12_planted": lambda: plant_2x2(diff3d(12, m=3).factors, 0.05, 13),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request):
+    f = CASES[request.param]()
+    m = 3
+    S, G, N = _oracle_all(f, m)
+    return request.param, f, m, S, G, N
+
+
+def test_pattern_bit_exact(case):
+    name, f, m, S, G, N = case
+    h = _handle(f)
+    rp, col = h.pattern_host()
+    assert np.array_equal(rp, S[0]) and np.array_equal(col, S[1])
+
+
+@pytest.mark.parametrize("cap", [1, 16])
+def test_selinv_fp64(case, cap):
+    name, f, m, S, G, N = case
+    h = _handle(f, supernode_cap=cap)
+    out = h.selinv(_dev(f.L_val), _dev(f.D_packed), "fp64")
+    h.sync_status()
+    err = sel_rel_err(out.cpu().numpy(), G, *S)
+    assert err <= TOL64, (name, err)
+
+
+def test_selinv_repeat_is_deterministic(case):
+    name, f, m, S, G, N = case
+    h = _handle(f)
+    Lv, Dv = _dev(f.L_val), _dev(f.D_packed)
+    a = h.selinv(Lv, Dv).cpu().numpy()
+    b = h.selinv(Lv, Dv).cpu().numpy()
+    h.sync_status()
+    assert sel_rel_err(a, G, *S) <= TOL64 and sel_rel_err(b, G, *S) <= TOL64
+
+
+def test_selinv_fp32(case):
+    name, f, m, S, G, N = case
+    h = _handle(f)
+    out = h.selinv(_dev(f.L_val), _dev(f.D_packed), "fp32")
+    h.sync_status()
+    assert normwise(out.cpu().numpy(), G) <= 1e-5, name
+
+
+@pytest.mark.parametrize("mm", [0, 1, 3])
+def test_ninv_fp64(case, mm):
+    name, f, m, S, G, N = case
+    Nr = N if mm == m else oracle.ninv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, mm, S)
+    h = _handle(f)
+    out = h.ninv(_dev(f.L_val), _dev(f.D_packed), mm, "fp64")
+    h.sync_status()
+    err = sel_rel_err(out.cpu().numpy(), Nr, *S)
+    assert err <= TOL64, (name, mm, err)
+
+
+def test_ninv_fp32(case):
+    name, f, m, S, G, N = case
+    h = _handle(f)
+    out = h.ninv(_dev(f.L_val), _dev(f.D_packed), m, "fp32")
+    h.sync_status()
+    assert normwise(out.cpu().numpy(), N) <= 1e-5, name
+
+
+@pytest.mark.parametrize("eps_rule", ["rel", "inf", "neg", "zero"])
+def test_mix_bit_exact(case, eps_rule):
+    name, f, m, S, G, N = case
+    eps = {"rel": 1e-3 * np.max(np.abs(G[S[0][1:] - 1])), "inf": np.inf, "neg": -1.0, "zero": 0.0}[eps_rule]
+    h = _handle(f)
+    out = h.mix(_dev(G), _dev(N), eps)
+    h.sync_status()
+    assert np.array_equal(out.cpu().numpy(), oracle.mix(G, N, eps))
+
+
+@pytest.mark.parametrize("k", [1, 16, 37])
+def test_lowrank_fp64(case, k):
+    name, f, m, S, G, N = case
+    V, lam = random_lowrank(f.n, k, seed=100 + k)
+    ref = oracle.lowrank_correct(S[0], S[1], G, V, lam)
+    h = _handle(f)
+    X = _dev(G.copy())
+    h.lowrank_correct(_dev(V), _dev(lam), X, "fp64")
+    h.sync_status()
+    assert sel_rel_err(X.cpu().numpy(), ref, *S) <= 1e-12
+
+
+def test_lowrank_fp32(case):
+    name, f, m, S, G, N = case
+    V, lam = random_lowrank(f.n, 16, seed=7)
+    ref = oracle.lowrank_correct(S[0], S[1], G, V, lam)
+    h = _handle(f)
+    X = _dev(G.copy())
+    h.lowrank_correct(_dev(V), _dev(lam), X, "fp32")
+    h.sync_status()
+    corr = ref - G
+    assert normwise(X.cpu().numpy() - G, corr) <= 1e-5
+
+
+def test_singular_pivot_reported():
+    f = lap2d_32().factors
+    h = _handle(f)
+    D = f.D_packed.copy()
+    D[5] = 0.0
+    from paper_2609_11363_b300 import SinvError
+    h.selinv(_dev(f.L_val), _dev(D))
+    with pytest.raises(SinvError) as ei:
+        h.sync_status()
+    assert ei.value.name == "SINV_ERR_SINGULAR_PIVOT"
+    # the handle stays usable
+    out = h.selinv(_dev(f.L_val), _dev(f.D_packed))
+    h.sync_status()
+    S, G, _ = _oracle_all(f, 0)
+    assert sel_rel_err(out.cpu().numpy(), G, *S) <= TOL64
+
+
+def test_bounded_wait_reports_timeout():
+    f = lap2d_32().factors
+    h = _handle(f, wait_limit=20000)
+    assert h.debug_wait_timeout() == 6  # SINV_ERR_TIMEOUT
+    out = h.selinv(_dev(f.L_val), _dev(f.D_packed))
+    h.sync_status()
+    assert torch.isfinite(out).all()
+
+
+def test_empty_and_tiny():
+    from paper_2609_11363_b300 import Handle
+    h = Handle(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int8))
+    assert h.nnz_S == 0
+    f = random_factors(1, 0.0, 0.0, 1)
+    S, G, N = _oracle_all(f, 2)
+    h = _handle(f)
+    out = h.selinv(_dev(f.L_val) if f.nnz_L else torch.zeros(0, dtype=torch.float64, device="cuda"),
+                   _dev(f.D_packed))
+    h.sync_status()
+    assert abs(out.item() - G[0]) <= 1e-15 * abs(G[0])
+
+
+@pytest.mark.slow
+def test_full_size_diff3d_64():
+    """The 64^3 shifted diffusion workload at full size, in the benchmark's launch
+    configuration: SelInv against the full oracle, NInv on sampled entries."""
+    w = diff3d(64)
+    f = plant_2x2(w.factors, 0.02, 2)
+    S = oracle.symbolic_S(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+    G = oracle.selinv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, S)
+    h = _handle(f)
+    Lv, Dv = _dev(f.L_val), _dev(f.D_packed)
+    out = h.selinv(Lv, Dv, "fp64")
+    h.sync_status()
+    assert sel_rel_err(out.cpu().numpy(), G, *S) <= TOL64
+    N = h.ninv(Lv, Dv, w.m, "fp64").cpu().numpy()
+    h.sync_status()
+    rng = np.random.default_rng(0)
+    idx = rng.choice(len(S[1]), 64, replace=False)
+    rows = np.repeat(np.arange(f.n), np.diff(S[0]))
+    pairs = list(zip(rows[idx], S[1][idx]))
+    Nr = oracle.ninv_entries_sampled(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, w.m, pairs)
+    diag = N[S[0][1:] - 1]
+    scale = np.abs(Nr) + np.sqrt(np.abs(diag[rows[idx]] * diag[S[1][idx]]))
+    assert np.max(np.abs(N[idx] - Nr) / scale) <= TOL64
