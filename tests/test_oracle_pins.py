@@ -1,0 +1,331 @@
+"""Pins of the FP64 oracle to facts fixed by the paper and by mathematics.
+
+None of these re-types the oracle's own formula: each compares it with a
+dense LAPACK inverse, a closed form, an invariant, a hand-derived small case
+or a brute-force dense evaluation.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+from workloads import grids
+from workloads.configs import diff3d, lap2d_32
+from workloads.factor import Factors, ildl
+from workloads.nd import nd_perm
+
+
+def _S(f):
+    return oracle.symbolic_S(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+
+
+def _rows(Srp):
+    return np.repeat(np.arange(len(Srp) - 1), np.diff(Srp))
+
+
+def _selinv(f, S=None):
+    return oracle.selinv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, S)
+
+
+def _ninv(f, m, S=None):
+    return oracle.ninv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, m, S)
+
+
+def _dense_LDLt(f):
+    L = (f.L_csr() + sp.identity(f.n)).toarray()
+    return L @ f.D_dense_blocks().toarray() @ L.T
+
+
+def _factors_from_dense(L, dblocks):
+    """Factors from a dense unit-lower L (structural pattern = nonzeros) and a list
+    of D blocks (scalars or 2x2 arrays)."""
+    n = L.shape[0]
+    low = sp.csr_matrix(np.tril(L, -1))
+    low.sort_indices()
+    ps = np.zeros(n, np.int8); dd = np.zeros(n); do = np.zeros(n)
+    j = 0
+    for b in dblocks:
+        ps[j] = 1
+        if np.ndim(b) == 0:
+            dd[j] = b; j += 1
+        else:
+            dd[j], dd[j + 1], do[j] = b[0][0], b[1][1], b[1][0]; j += 2
+    return Factors(n=n, L_rowptr=low.indptr.astype(np.int64), L_col=low.indices.astype(np.int32),
+                   L_val=low.data.astype(np.float64), pivot_start=ps, d_diag=dd, d_off=do)
+
+
+# -- S (Section 1) ----------------------------------------------------------------
+def test_pattern_is_brute_force_pattern_of_L_plus_D_plus_Lt():
+    f = diff3d(6, tau=1e-2, shifted=True).factors
+    f2 = _factors_from_dense((f.L_csr() + sp.identity(f.n)).toarray(),
+                             [f.d_diag[j] if (j + 1 == f.n or f.pivot_start[j + 1]) else
+                              [[f.d_diag[j], f.d_off[j]], [f.d_off[j], f.d_diag[j + 1]]]
+                              for j in range(f.n) if f.pivot_start[j]])
+    Srp, Sc = _S(f2)
+    B = (np.abs((f2.L_csr() + sp.identity(f.n)).toarray()) > 0) | (np.abs(f2.D_dense_blocks().toarray()) > 0)
+    B = B | B.T
+    low = np.tril(B)
+    rows, cols = np.nonzero(low)
+    assert np.array_equal(_rows(Srp), rows) and np.array_equal(Sc, cols)
+
+
+# -- SelInv (Section 2.1) ------------------------------------------------------------
+def test_selinv_exact_factors_equal_dense_inverse_2d():
+    """Exact factors: SelInv coincides with A^{-1} on S (Section 2.1)."""
+    w = lap2d_32(tau=0.0)
+    f = w.factors
+    Srp, Sc = _S(f)
+    G = _selinv(f, (Srp, Sc))
+    Ainv = np.linalg.inv(w.A.toarray())
+    assert np.max(np.abs(G - Ainv[_rows(Srp), Sc])) <= 1e-12 * np.max(np.abs(Ainv))
+
+
+def test_selinv_exact_indefinite_with_2x2_pivot():
+    """Shifted 3D problem, exact factors with a 2x2 pivot chosen by the pivot test."""
+    w = diff3d(6, tau=0.0)
+    f = w.factors
+    assert f.stats["n_2x2"] >= 1
+    Srp, Sc = _S(f)
+    G = _selinv(f, (Srp, Sc))
+    Ainv = np.linalg.inv(w.A.toarray())
+    assert np.max(np.abs(G - Ainv[_rows(Srp), Sc])) <= 1e-10 * np.max(np.abs(Ainv))
+
+
+def test_selinv_identity_GA_diag_is_one():
+    """Exact factors: pattern(A) is inside S, so (G A)_ii = 1 from entries on S only."""
+    w = lap2d_32(tau=0.0)
+    f = w.factors
+    Srp, Sc = _S(f)
+    G = _selinv(f, (Srp, Sc))
+    Gs = oracle.core.sym_from_S(f.n, Srp, Sc, G)
+    A = w.A
+    Sset = set(zip(_rows(Srp).tolist(), Sc.tolist()))
+    Alow = sp.tril(A).tocoo()
+    assert all((int(i), int(j)) in Sset for i, j in zip(Alow.row, Alow.col))
+    d = np.asarray(Gs.multiply(A.T).sum(axis=1)).ravel()
+    assert np.max(np.abs(d - 1.0)) <= 1e-12
+
+
+def test_selinv_1d_closed_form():
+    """tridiag(-1, 2, -1): (A^{-1})_ij = i (n+1-j) / (n+1), 1-based, i <= j."""
+    n = 50
+    A = sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1], format="csr")
+    f = ildl(A, 0.0)
+    Srp, Sc = _S(f)
+    G = _selinv(f, (Srp, Sc))
+    r = _rows(Srp) + 1; c = Sc + 1
+    i, j = np.minimum(r, c), np.maximum(r, c)
+    assert np.max(np.abs(G - i * (n + 1 - j) / (n + 1))) <= 1e-12 * n
+
+
+def test_selinv_2d_diagonal_closed_form_sine_expansion():
+    """lap2d 32x32 + 0.1 I, exact factors: diag(A^{-1}) from the Dirichlet
+    eigenbasis, d(x,y) = sum_pq phi_pq(x,y)^2 / (4 - 2cos(p pi/33) - 2cos(q pi/33) + 0.1)."""
+    w = lap2d_32(tau=0.0)
+    f = w.factors
+    Srp, Sc = _S(f)
+    G = _selinv(f, (Srp, Sc))
+    diag_nd = G[Srp[1:] - 1]
+    perm = w.meta["perm"]  # perm[new] = old natural index
+    k = np.arange(1, 33)
+    lam1 = 2 - 2 * np.cos(k * np.pi / 33)
+    phi = np.sqrt(2 / 33) * np.sin(np.outer(np.arange(1, 33), k) * np.pi / 33)  # phi[x-1, p-1]
+    lam = lam1[:, None] + lam1[None, :] + 0.1
+    # d(x, y) = sum_pq phi[x,p]^2 phi[y,q]^2 / lam[p,q]
+    d = np.einsum("xp,yq,pq->yx", phi ** 2, phi ** 2, 1.0 / lam).ravel()  # natural index y*32 + x
+    assert np.max(np.abs(diag_nd - d[perm])) <= 1e-12
+
+
+def test_selinv_hand_example_nonclosed():
+    """n = 4, L(1,0)=a, L(2,0)=b, L(3,1)=c, L(3,2)=e: (2,1) is not in S.  By hand,
+    the recurrence with the entries outside S discarded gives
+      G33 = 1/d3, G32 = -e/d3, G22 = 1/d2 + e^2/d3, G31 = -c/d3, G11 = 1/d1 + c^2/d3,
+      G10 = -a G11, G20 = -b G22, G00 = 1/d0 + a^2 G11 + b^2 G22,
+    while the exact (LDL^T)^{-1} has G00 larger by 2 a b c e / d3."""
+    a, b, c, e = 0.3, -0.7, 0.45, 0.2
+    d = [2.0, 1.5, -1.25, 3.0]
+    L = np.eye(4); L[1, 0] = a; L[2, 0] = b; L[3, 1] = c; L[3, 2] = e
+    f = _factors_from_dense(L, d)
+    Srp, Sc = _S(f)
+    G = _selinv(f, (Srp, Sc))
+    G33 = 1 / d[3]; G32 = -e / d[3]; G22 = 1 / d[2] + e * e / d[3]; G31 = -c / d[3]; G11 = 1 / d[1] + c * c / d[3]
+    G10 = -a * G11; G20 = -b * G22; G00 = 1 / d[0] + a * a * G11 + b * b * G22
+    want = {(0, 0): G00, (1, 0): G10, (1, 1): G11, (2, 0): G20, (2, 2): G22, (3, 1): G31, (3, 2): G32, (3, 3): G33}
+    got = dict(zip(zip(_rows(Srp), Sc), G))
+    assert set(got) == set(want)
+    for key in want:
+        assert abs(got[key] - want[key]) <= 1e-15 * 10, key
+    exact = np.linalg.inv(_dense_LDLt(f))
+    assert abs(exact[0, 0] - G00 - 2 * a * b * c * e / d[3]) <= 1e-14
+
+
+def test_selinv_2x2_block_with_different_column_structures():
+    """2x2 block {0,1} with struct(0) = {2}, struct(1) = {3} and (3,2) in S: the
+    pattern is closed, so SelInv must equal (LDL^T)^{-1} on S.  This fixes the
+    reading that the block's G11 uses X on the union of the two structures."""
+    L = np.eye(4); L[2, 0] = 0.4; L[3, 1] = -0.6; L[3, 2] = 0.5
+    f = _factors_from_dense(L, [[[1.5, 0.7], [0.7, -2.0]], 1.2, 2.5])
+    Srp, Sc = _S(f)
+    G = _selinv(f, (Srp, Sc))
+    exact = np.linalg.inv(_dense_LDLt(f))
+    assert np.max(np.abs(G - exact[_rows(Srp), Sc])) <= 1e-14
+
+
+def test_selinv_closed_random_pattern_equals_inverse():
+    """Random values on a closed pattern (the exact symbolic factor of a random
+    sparse SPD matrix) and random-sign D: SelInv = (LDL^T)^{-1} on S."""
+    rng = np.random.default_rng(5)
+    n = 60
+    B = sp.random(n, n, density=0.05, random_state=rng)
+    A = (B + B.T + sp.identity(n) * 5).tocsr()
+    f0 = ildl(A, 0.0, allow_2x2=False)
+    # random values on the same (closed) pattern
+    L = (f0.L_csr() + sp.identity(n)).toarray()
+    mask = np.tril(L, -1) != 0
+    L[mask] = rng.uniform(-0.5, 0.5, mask.sum())
+    f = _factors_from_dense(L, list(rng.uniform(1, 2, n) * rng.choice([-1, 1], n)))
+    Srp, Sc = _S(f)
+    G = _selinv(f, (Srp, Sc))
+    exact = np.linalg.inv(_dense_LDLt(f))
+    assert np.max(np.abs(G - exact[_rows(Srp), Sc])) <= 1e-11 * np.max(np.abs(exact))
+
+
+# -- NInv (Section 2.2) ------------------------------------------------------------------
+def _brute_ninv(f, m):
+    n = f.n
+    E = -f.L_csr().toarray()
+    W = sum(np.linalg.matrix_power(E, t) for t in range(m + 1))
+    return W.T @ np.linalg.inv(f.D_dense_blocks().toarray()) @ W
+
+
+@pytest.mark.parametrize("m", [0, 1, 2, 5])
+def test_ninv_equals_dense_truncated_series(m):
+    from workloads.configs import random_factors
+    f = random_factors(120, 0.05, 0.2, 9)
+    Srp, Sc = _S(f)
+    N = _ninv(f, m, (Srp, Sc))
+    ref = _brute_ninv(f, m)[_rows(Srp), Sc]
+    assert np.max(np.abs(N - ref)) <= 1e-13 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_ninv_m0_is_Dinv_on_S():
+    from workloads.configs import random_factors
+    f = random_factors(80, 0.1, 0.3, 2)
+    Srp, Sc = _S(f)
+    N = _ninv(f, 0, (Srp, Sc))
+    Dinv = np.linalg.inv(f.D_dense_blocks().toarray())
+    assert np.array_equal(N == 0, Dinv[_rows(Srp), Sc] == 0)
+    assert np.max(np.abs(N - Dinv[_rows(Srp), Sc])) <= 1e-15 * 4
+
+
+def test_ninv_exact_when_m_reaches_depth():
+    """E is nilpotent: for m >= the longest path in the graph of L the series is
+    L^{-1} exactly, so NInv = (LDL^T)^{-1} on S (Section 2.2)."""
+    w = lap2d_32(tau=0.0)
+    f = w.factors
+    Lc = f.L_csr().tocsc()
+    depth = np.zeros(f.n, int)
+    for j in range(f.n - 1, -1, -1):
+        r = Lc.indices[Lc.indptr[j]:Lc.indptr[j + 1]]
+        if len(r):
+            depth[j] = 1 + depth[r].max()
+    m = int(depth.max())
+    Srp, Sc = _S(f)
+    N = _ninv(f, m, (Srp, Sc))
+    Ainv = np.linalg.inv(w.A.toarray())
+    assert np.max(np.abs(N - Ainv[_rows(Srp), Sc])) <= 1e-11
+    E = -f.L_csr().toarray()
+    assert not np.any(np.linalg.matrix_power(E, m + 1))
+
+
+def test_ninv_sampled_matches_full():
+    w = lap2d_32()
+    f = w.factors
+    Srp, Sc = _S(f)
+    N = _ninv(f, 3, (Srp, Sc))
+    rows = _rows(Srp)
+    idx = np.arange(0, len(Sc), 37)
+    Ns = oracle.ninv_entries_sampled(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, 3,
+                                     list(zip(rows[idx], Sc[idx])))
+    ref = _brute_ninv(f, 3)[rows[idx], Sc[idx]]
+    assert np.max(np.abs(Ns - ref)) <= 1e-13 and np.max(np.abs(N[idx] - ref)) <= 1e-13
+
+
+# -- Mix (Section 2.3) ---------------------------------------------------------------------
+def test_mix_special_cases_and_hand_example():
+    G = np.array([0.5, -1e-4, 2e-3, -0.2, 0.0])
+    N = np.array([0.4, 7.0, 8.0, 9.0, 1.0])
+    assert np.array_equal(oracle.mix(G, N, np.inf), N)
+    assert np.array_equal(oracle.mix(G, N, -1.0), G)
+    assert np.array_equal(oracle.mix(G, N, 1e-3), np.array([0.5, 7.0, 2e-3, -0.2, 1.0]))
+
+
+# -- low-rank correction (Sections 2.5, 2.6) --------------------------------------------------
+def test_lowrank_brute_force_and_diagonal_formula():
+    from workloads.configs import random_factors, random_lowrank
+    f = random_factors(90, 0.08, 0.1, 4)
+    Srp, Sc = _S(f)
+    X = np.random.default_rng(1).standard_normal(len(Sc))
+    V, lam = random_lowrank(f.n, 5, seed=3, orthonormal=False)
+    out = oracle.lowrank_correct(Srp, Sc, X, V, lam)
+    dense = V @ np.diag(lam) @ V.T
+    assert np.max(np.abs(out - X - dense[_rows(Srp), Sc])) <= 1e-14
+    dd = np.diag(dense)
+    # Section 2.6: d_i + sum_j lambda_j v_ij^2
+    diag = oracle.lowrank_diag(X[Srp[1:] - 1], V, lam)
+    assert np.max(np.abs(diag - (X[Srp[1:] - 1] + dd))) <= 1e-14
+    assert np.array_equal(oracle.lowrank_correct(Srp, Sc, X, V[:, :0], lam[:0]), X)
+
+
+def test_lanczos_eigenpairs_and_eckart_young():
+    """Dominant eigenpairs of E_inv = A^{-1} - A^inv (Lanczos, matrix free) agree
+    with a dense eigendecomposition, and the rank-k residual in the 2-norm is
+    |lambda_{k+1}| (Eckart-Young, Section 2.5)."""
+    A0 = grids.laplace2d_5pt(10, 10, 0.1)
+    p = nd_perm((10, 10))
+    A = A0[p][:, p].tocsr()
+    f = ildl(A, 5e-2)
+    Srp, Sc = _S(f)
+    G = _selinv(f, (Srp, Sc))
+    Gs = oracle.core.sym_from_S(f.n, Srp, Sc, G)
+    Einv = np.linalg.inv(A.toarray()) - Gs.toarray()
+    ev = np.linalg.eigvalsh(Einv)
+    ev = ev[np.argsort(-np.abs(ev))]
+    k = 3
+    lam, V = oracle.lanczos_einv(A, Gs, k, steps=100, seed=0)
+    assert np.allclose(np.sort(np.abs(lam)), np.sort(np.abs(ev[:k])), rtol=1e-9, atol=0)
+    R = Einv - V @ np.diag(lam) @ V.T
+    assert abs(np.linalg.norm(R, 2) - abs(ev[k])) <= 1e-8 * abs(ev[0])
+    assert abs(np.linalg.norm(R, "fro") ** 2 - np.sum(ev[k:] ** 2)) <= 1e-8 * np.sum(ev ** 2)
+
+
+def test_acceptance_keeps_only_improving_modes():
+    d = np.array([1.0, 2.0, 3.0])
+    d_hat = np.array([0.9, 2.0, 3.0])
+    V = np.eye(3)[:, :2]
+    lam = np.array([0.1, 0.5])  # mode 0 fixes entry 0, mode 1 spoils entry 1
+    kept, cur = oracle.accept_modes(d, d_hat, V, lam)
+    assert kept == [0] and np.allclose(cur, d)
+
+
+# -- measures (Sections 2.6, 3.2) -----------------------------------------------------------
+def test_measures():
+    assert oracle.err1([1.0, -2.0], [1.0, -2.0]) == 0.0
+    assert oracle.err1([1.0, 3.0], [2.0, 3.0]) == 0.25
+    n = 20
+    A = sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1], format="csr")
+    assert oracle.dodd(A) == 1.0
+    f = ildl(A, 0.0)
+    Srp, Sc = _S(f)
+    assert oracle.fill_fact(2 * len(Sc) - n, A.nnz) == 1.0
+
+
+# -- the input factorisation (generator side) -------------------------------------------------
+def test_ildl_exact_reconstructs_and_keeps_inertia():
+    w = diff3d(6, tau=0.0)
+    f = w.factors
+    R = _dense_LDLt(f) - w.A.toarray()
+    assert np.max(np.abs(R)) <= 1e-12 * np.max(np.abs(w.A.toarray()))
+    neg_A = int(np.sum(np.linalg.eigvalsh(w.A.toarray()) < 0))
+    neg_D = int(np.sum(np.linalg.eigvalsh(f.D_dense_blocks().toarray()) < 0))
+    assert neg_A == neg_D == 1
