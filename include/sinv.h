@@ -67,6 +67,8 @@ typedef struct {
                                analysis (no CUDA call; numeric calls then fail with
                                SINV_ERR_INVALID_ARG)                                  */
     int64_t wait_limit;     /* polls before a device wait gives up; 0 = default       */
+    int64_t big_pairs;      /* supernodes with at least this many entries of S in
+                               C x C are processed by a whole CTA; 0 = default 2048   */
 } sinv_symbolic_opts;
 
 /* Symbolic analysis (host).  Validates the pattern of L and the pivot layout,

@@ -38,7 +38,8 @@ class SinvError(RuntimeError):
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("supernode_cap", ctypes.c_int32), ("device", ctypes.c_int32), ("wait_limit", ctypes.c_int64)]
+    _fields_ = [("supernode_cap", ctypes.c_int32), ("device", ctypes.c_int32), ("wait_limit", ctypes.c_int64),
+                ("big_pairs", ctypes.c_int64)]
 
 
 class _Stats(ctypes.Structure):
@@ -104,8 +105,11 @@ def _check_tensor(t, name, numel=None, dtype=torch.float64):
 
 
 def _stream_ptr(stream):
-    s = stream if stream is not None else torch.cuda.current_stream()
-    return ctypes.c_void_p(s.cuda_stream)
+    if stream is None:
+        if not torch.cuda.is_available():
+            return ctypes.c_void_p(0)  # host-only handles: the library rejects the call itself
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
 
 
 class Handle:
@@ -115,7 +119,7 @@ class Handle:
     host arrays describing strictly lower CSR L and the 1x1/2x2 pivot layout.
     """
 
-    def __init__(self, n, L_rowptr, L_col, pivot_start, supernode_cap=16, device=0, wait_limit=0):
+    def __init__(self, n, L_rowptr, L_col, pivot_start, supernode_cap=16, device=0, wait_limit=0, big_pairs=0):
         self._lib = load_library()
         self._h = ctypes.c_void_p()
         self.n = int(n)
@@ -124,7 +128,7 @@ class Handle:
         ps = np.ascontiguousarray(pivot_start, dtype=np.int8)
         if rp.shape != (self.n + 1,) or ps.shape != (self.n,):
             raise ValueError("L_rowptr must have n+1 and pivot_start n entries")
-        opts = _Opts(int(supernode_cap), int(device), int(wait_limit))
+        opts = _Opts(int(supernode_cap), int(device), int(wait_limit), int(big_pairs))
         self.device = torch.device("cuda", int(device)) if int(device) >= 0 else None
         st = self._lib.sinv_symbolic(self.n, _np_ptr(rp), _np_ptr(col), _np_ptr(ps), ctypes.byref(opts),
                                      ctypes.byref(self._h))

@@ -38,6 +38,8 @@ struct sinv_handle_s {
     int32_t* dJJs = nullptr;
     uint32_t* dhit_ik = nullptr;
     int32_t* dhit_pos = nullptr;
+    int32_t* dhrow = nullptr;
+    WorkItem* ditems = nullptr;
     uint32_t* ddone = nullptr;
     uint32_t* depoch = nullptr;
     int32_t* dticket = nullptr;
@@ -78,7 +80,7 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
 void free_all(sinv_handle h) {
     void* ptrs[] = {h->dSrp, h->dSc, h->dSdiag, h->dl2s, h->dLrp, h->dLcp, h->dLri, h->dLcsr, h->ddpos, h->dpstart,
                     h->dsn, h->dorder, h->downer, h->dCrow, h->dLmap, h->dJJl, h->dJJs, h->dhit_ik, h->dhit_pos,
-                    h->ddone, h->depoch, h->dticket, h->dstatus, h->ddebug_flag, h->dscratch, h->dwork, h->dWcp,
+                    h->dhrow, h->ditems, h->ddone, h->depoch, h->dticket, h->dstatus, h->ddebug_flag, h->dscratch, h->dwork, h->dWcp,
                     h->dWr, h->dgrp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -139,8 +141,10 @@ sinv_status sinv_symbolic(int64_t n, const int64_t* L_rowptr, const int32_t* L_c
     sinv_handle h = new (std::nothrow) sinv_handle_s();
     if (!h) return SINV_ERR_OOM;
     int cap = 16;
+    int64_t big_pairs = 2048;
     if (opts) {
         if (opts->supernode_cap > 0) cap = opts->supernode_cap;
+        if (opts->big_pairs > 0) big_pairs = opts->big_pairs;
         h->device = opts->device;
         if (opts->wait_limit > 0) h->wait_limit = opts->wait_limit;
     }
@@ -154,7 +158,7 @@ sinv_status sinv_symbolic(int64_t n, const int64_t* L_rowptr, const int32_t* L_c
     }
     std::string err;
     try {
-        err = build_plan(n, L_rowptr, L_col, pivot_start, cap, h->P);
+        err = build_plan(n, L_rowptr, L_col, pivot_start, cap, big_pairs, selinv_warps_per_cta(), h->P);
     } catch (const std::bad_alloc&) {
         set_err(h, "host allocation failed in the symbolic analysis");
         *out = h;
@@ -201,6 +205,8 @@ sinv_status sinv_symbolic(int64_t n, const int64_t* L_rowptr, const int32_t* L_c
     UP(dJJs, P.JJs);
     UP(dhit_ik, P.hit_ik);
     UP(dhit_pos, P.hit_pos);
+    UP(dhrow, P.hrow);
+    UP(ditems, P.items);
 #undef UP
     size_t nsn = std::max<size_t>(P.sn.size(), 1);
     if ((e = cudaMalloc((void**)&h->ddone, nsn * sizeof(uint32_t))) != cudaSuccess ||
@@ -221,7 +227,7 @@ sinv_status sinv_symbolic(int64_t n, const int64_t* L_rowptr, const int32_t* L_c
     }
     h->grid = selinv_grid(h->num_sms);
     if (P.max_cw > selinv_cw_smem()) {
-        size_t bytes = (size_t)h->grid * selinv_warps_per_cta() * 2 * (size_t)P.max_cw * sizeof(double);
+        size_t bytes = (size_t)h->grid * selinv_warps_per_cta() * 3 * (size_t)P.max_cw * sizeof(double);
         if ((e = cudaMalloc((void**)&h->dscratch, bytes)) != cudaSuccess) {
             *out = h;
             return cuda_fail(h, e, "selinv scratch");
@@ -293,6 +299,8 @@ sinv_status sinv_selinv(sinv_handle h, const double* L_val, const double* D_val,
     SelinvArgs a;
     a.sn = h->dsn;
     a.order = h->dorder;
+    a.items = h->ditems;
+    a.nitems = (int32_t)P.items.size();
     a.nsn = (int32_t)P.sn.size();
     a.n = (int32_t)P.n;
     a.owner = h->downer;
@@ -302,6 +310,7 @@ sinv_status sinv_selinv(sinv_handle h, const double* L_val, const double* D_val,
     a.JJs = h->dJJs;
     a.hit_ik = h->dhit_ik;
     a.hit_pos = h->dhit_pos;
+    a.hrow = h->dhrow;
     a.Sdiag = h->dSdiag;
     a.l2s = h->dl2s;
     a.dpos = h->ddpos;

@@ -10,6 +10,8 @@ namespace sinv {
 struct SelinvArgs {
     const SnInfo* sn;
     const int32_t* order;
+    const WorkItem* items;
+    int32_t nitems;
     int32_t nsn;
     int32_t n;
     const int32_t* owner;
@@ -19,6 +21,7 @@ struct SelinvArgs {
     const int32_t* JJs;
     const uint32_t* hit_ik;
     const int32_t* hit_pos;
+    const int32_t* hrow;
     const int32_t* Sdiag;
     const int32_t* l2s;
     const int32_t* dpos;

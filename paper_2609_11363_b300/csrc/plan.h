@@ -15,7 +15,18 @@ struct SnInfo {
     int64_t cw_off;    // Lmap[cw_off .. +c*w): CSR position of L(C[i], s0+t), row-major (i, t), or -1
     int64_t ww_off;    // JJl / JJs [ww_off .. +w*w): within-supernode maps, row-major (a, b)
     int64_t hit_off;   // hit arrays [hit_off .. +hit_cnt)
-    int64_t hit_cnt;   // pairs (i, k), k < i, with (C[i], C[k]) in S
+    int64_t hit_cnt;   // pairs (i, k) of C x C (both triangles and the diagonal) with
+                       // (C[i], C[k]) in S, sorted by (i, k)
+    int64_t hrow_off;  // hrow[hrow_off .. +c+1): start of row i's pairs, relative to hit_off
+};
+
+// A unit of the persistent SelInv schedule: either one large supernode that a
+// whole CTA processes, or up to kGroup consecutive small ones, one per warp.
+struct WorkItem {
+    int32_t first;  // index into the processing order
+    int32_t count;  // supernodes in the item
+    int32_t big;    // 1: CTA-cooperative
+    int32_t pad;
 };
 
 struct HostPlan {
@@ -41,7 +52,9 @@ struct HostPlan {
     std::vector<int32_t> order;      // processing order (level-major)
     std::vector<int32_t> Crow, Lmap, JJl, JJs;
     std::vector<uint32_t> hit_ik;    // (i << 16) | k
-    std::vector<int32_t> hit_pos;    // S_lo position of (C[i], C[k])
+    std::vector<int32_t> hit_pos;    // S_lo position of (max, min) of (C[i], C[k])
+    std::vector<int32_t> hrow;       // per supernode c+1 row starts
+    std::vector<WorkItem> items;
     int64_t n_levels = 0, max_c = 0, max_w = 0, max_cw = 0, hit_pairs = 0;
 };
 
@@ -59,8 +72,11 @@ struct NinvPlan {
 };
 
 // Returns an empty string on success, else the reason the pattern is invalid.
+// big_pairs: supernodes with at least this many pairs are processed by a whole CTA;
+// group: small supernodes per work item (one per warp).
 std::string build_plan(int64_t n, const int64_t* L_rowptr, const int32_t* L_col,
-                       const int8_t* pivot_start, int supernode_cap, HostPlan& P);
+                       const int8_t* pivot_start, int supernode_cap, int64_t big_pairs, int group,
+                       HostPlan& P);
 std::string build_ninv_plan(const HostPlan& P, int m, NinvPlan& W);
 
 }  // namespace sinv

@@ -7,16 +7,18 @@
 //     X    = -G~_CC Lh                              (G~ = G on S, 0 off S)
 //     G_JJ = L_JJ^{-T} D_J^{-1} L_JJ^{-1} - Lh^T X
 // and X is stored where (C[i], s0+t) is in S.  The symmetric c x c matrix G~_CC
-// is read through a per-supernode list of the pairs (i, k), k < i, whose
-// entry is in S (the zeros are never touched), plus the diagonal.
+// is read through a per-supernode list of the pairs (i, k) whose entry is in S
+// (both triangles and the diagonal, sorted by i): the zeros of G~ are never
+// touched.  Each row of X is a segmented sum over its pairs, formed by warp
+// shuffles, so no atomic is needed.
 //
-// Scheduling: every warp takes the next supernode from a global ticket counter
-// in level-major order, waits (bounded) until the supernodes owning its rows C
-// have published their results, computes, and publishes with a release store.
-// A warp only ever waits for tickets handed out before its own, all held by
-// running warps, so the schedule cannot deadlock.
-#include <cstdio>
-
+// Scheduling: a CTA takes the next work item from a global ticket counter in
+// level-major order.  An item is either one large supernode (the whole CTA
+// works on it, rows split among the warps) or up to eight small ones (one per
+// warp).  Before computing, the threads wait (bounded) until the supernodes
+// owning the rows C have published their results; a result is published with
+// a release store of the call's epoch.  A CTA only waits for items handed out
+// before its own, all held by running CTAs, so the schedule cannot deadlock.
 #include "device.cuh"
 #include "kernels.h"
 #include "plan.h"
@@ -26,11 +28,10 @@ namespace sinv {
 namespace {
 
 constexpr int kWarps = 8;          // warps per CTA
-constexpr int kCW = 512;           // per-warp shared capacity for c*w values
+constexpr int kCW = 384;           // per-warp shared capacity for c*w values (Lh, X, output positions)
 constexpr int kWMax = 16;          // supernode width limit of this kernel
+constexpr int kBatch = 4;          // chunks of 32 pairs whose G loads are in flight together
 
-// Arithmetic forms.  Storage type of the working copy of G, the type products
-// are formed in, and conversions.
 struct F64 {
     using G = double;
     using R = double;
@@ -49,141 +50,223 @@ struct F32 {
     static __device__ __forceinline__ double to_d(R v) { return (double)v; }
 };
 
+constexpr int kPairs = kWMax * (kWMax + 1) / 2;
+
 struct WarpSmem {
     double lh[kCW];
     double x[kCW];
     double jj[kWMax * kWMax];   // L_JJ, then M = L_JJ^{-1}
-    double t[kWMax * kWMax];    // D_J^{-1} M, then Lh^T X
+    double t[kWMax * kWMax];    // D_J^{-1} M
+    double red[kPairs];         // Lh^T X, lower triangle
+    int32_t xpos[kCW];          // S_lo position of X[i][t] or -1
+};
+// a CTA-cooperative supernode lays Lh, X and the positions out over all warps' regions
+static_assert(sizeof(WarpSmem) * kWarps >= (2 * sizeof(double) + sizeof(int32_t)) * kCW * kWarps, "layout");
+
+struct CtaShared {
+    int item;
+    int stop;
+    double jj[kWMax * kWMax];
+    double t[kWMax * kWMax];
+    double red[kWarps][kPairs];
 };
 
+// A group of threads working on one supernode: one warp, or the whole CTA.
+template <bool kCta>
+struct Group {
+    static __device__ __forceinline__ int size() { return kCta ? kWarps * 32 : 32; }
+    static __device__ __forceinline__ int rank() { return kCta ? (int)threadIdx.x : (int)(threadIdx.x & 31); }
+    static __device__ __forceinline__ int nwarps() { return kCta ? kWarps : 1; }
+    static __device__ __forceinline__ int warp() { return kCta ? (int)(threadIdx.x >> 5) : 0; }
+    static __device__ __forceinline__ void sync() {
+        if (kCta) __syncthreads(); else __syncwarp();
+    }
+    static __device__ __forceinline__ bool any(bool p) {
+        if (kCta) return __syncthreads_or(p) != 0;
+        return __any_sync(0xffffffffu, p);
+    }
+};
+
+// Segmented sum of v over lanes that share `key` (lanes sorted by key): after the
+// call, the last lane of every run holds the run's total.
+template <class R>
+__device__ __forceinline__ R seg_sum(R v, int key, int lane) {
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        R o = __shfl_up_sync(0xffffffffu, v, off);
+        int ko = __shfl_up_sync(0xffffffffu, key, off);
+        if (lane >= off && ko == key) v += o;
+    }
+    return v;
+}
+
+// Pairs of one warp: entries [e0, e1) of the supernode's pair list.  The first
+// batch of (i, k) / position words is loaded before the dependency wait.
+struct PairRange {
+    int64_t e0, e1;
+    uint32_t ik[kBatch];
+    int32_t pos[kBatch];
+};
+
+__device__ __forceinline__ void load_pairs(const uint32_t* __restrict__ hik, const int32_t* __restrict__ hpos,
+                                           int64_t base, int64_t e1, int lane, uint32_t* ik, int32_t* pos) {
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+        const int64_t e = base + u * 32 + lane;
+        ik[u] = e < e1 ? hik[e] : 0xFFFFFFFFu;
+        pos[u] = e < e1 ? hpos[e] : -1;
+    }
+}
+
+// X[i][:] -= sum over the pairs (i, k) of G(C[i], C[k]) Lh[k][:]; one warp.  Rows of
+// different warps are disjoint, and a run of one row inside a chunk of 32 pairs is
+// summed by shuffles and added by its last lane, so no atomic is needed.  Every
+// batch issues the G loads of kBatch chunks and the pair words of the next batch
+// before it computes.
 template <class Form>
-__global__ void __launch_bounds__(kWarps * 32) selinv_persistent(SelinvArgs a, typename Form::G* Gw) {
+__device__ __forceinline__ void accumulate_pairs(PairRange& pr, const uint32_t* __restrict__ hik,
+                                                 const int32_t* __restrict__ hpos, const typename Form::G* Gw,
+                                                 const typename Form::R* lh, typename Form::R* x, int w, int lane) {
     using R = typename Form::R;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    WarpSmem* ws = reinterpret_cast<WarpSmem*>(smem_raw) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    const int64_t gwarp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-    const uint32_t epoch = *a.epoch;
-
-    for (;;) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(a.ticket, 1);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= a.nsn) break;
-        if (ld_volatile(a.status) != ST_OK) break;
-        const int J = a.order[t];
-        const SnInfo I = a.sn[J];
-        const int c = I.c, w = I.w, cw = c * w;
-        const int32_t* Crow = a.Crow + I.crow_off;
-        const int32_t* Lmap = a.Lmap + I.cw_off;
-
-        // wait until every supernode owning a row of C has published
-        bool ok = true;
-        for (int i = lane; i < c; i += 32) {
-            int s = a.owner[Crow[i]];
-            if (!wait_flag(a.done + s, epoch, a.status, a.wait_limit)) ok = false;
+    for (int64_t base = pr.e0; base < pr.e1; base += 32 * kBatch) {
+        R g[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) g[u] = pr.pos[u] >= 0 ? Form::ld(Gw + pr.pos[u]) : R(0);
+        uint32_t ik_n[kBatch];
+        int32_t pos_n[kBatch];
+        load_pairs(hik, hpos, base + 32 * kBatch, pr.e1, lane, ik_n, pos_n);
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            if (base + u * 32 >= pr.e1) break;  // uniform across the warp
+            const bool valid = pr.pos[u] >= 0;
+            const int i = valid ? (int)(pr.ik[u] >> 16) : -1 - lane;
+            const int k = valid ? (int)(pr.ik[u] & 0xffff) : 0;
+            const int inext = __shfl_down_sync(0xffffffffu, i, 1);
+            const bool last = valid && (lane == 31 || inext != i);
+            for (int q = 0; q < w; ++q) {
+                R v = valid ? g[u] * lh[k * w + q] : R(0);
+                v = seg_sum(v, i, lane);
+                if (last) x[i * w + q] -= v;
+            }
+            __syncwarp();
         }
-        if (__any_sync(0xffffffffu, !ok)) break;
-        __syncwarp();
-        __threadfence();
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            pr.ik[u] = ik_n[u];
+            pr.pos[u] = pos_n[u];
+        }
+    }
+}
 
-        R* lh;
-        R* x;
-        if (cw <= kCW) {
+// One supernode on a group (warp or CTA).  Returns false when a wait gave up.
+// Phase A reads only the inputs and the plan (it overlaps the producers of C);
+// phase B waits for them; phase C reads G, forms X and G_JJ and publishes.
+template <class Form, bool kCta>
+__device__ bool process(const SelinvArgs& a, typename Form::G* Gw, int J, uint32_t epoch, WarpSmem* ws,
+                        CtaShared* cs, int64_t gslot) {
+    using R = typename Form::R;
+    using Gr = Group<kCta>;
+    const SnInfo I = a.sn[J];
+    const int c = I.c, w = I.w, cw = c * w;
+    const int tid = Gr::rank(), gsz = Gr::size(), lane = threadIdx.x & 31;
+    const int32_t* Crow = a.Crow + I.crow_off;
+    const int32_t* Lmap = a.Lmap + I.cw_off;
+
+    // ---- phase A ---------------------------------------------------------------------
+    // working arrays: shared memory of this warp (or all warps' regions for the CTA), else global scratch
+    const int cap = kCta ? kCW * kWarps : kCW;
+    R* lh;
+    R* x;
+    int32_t* xpos;
+    if (cw <= cap) {
+        if (kCta) {
+            WarpSmem* w0 = ws - (threadIdx.x >> 5);
+            double* base = reinterpret_cast<double*>(w0);
+            lh = reinterpret_cast<R*>(base);
+            x = reinterpret_cast<R*>(base + cap);
+            xpos = reinterpret_cast<int32_t*>(base + 2 * cap);
+        } else {
             lh = reinterpret_cast<R*>(ws->lh);
             x = reinterpret_cast<R*>(ws->x);
-        } else {
-            lh = reinterpret_cast<R*>(a.scratch + gwarp * 2 * a.max_cw);
-            x = lh + a.max_cw;
+            xpos = ws->xpos;
         }
-        // L_CJ and L_JJ
-        for (int e = lane; e < cw; e += 32) {
-            int q = Lmap[e];
-            lh[e] = q >= 0 ? Form::from_d(a.Lval[q]) : R(0);
-            x[e] = R(0);
-        }
-        for (int e = lane; e < w * w; e += 32) {
-            int q = a.JJl[I.ww_off + e];
-            ws->jj[e] = q >= 0 ? a.Lval[q] : 0.0;
-        }
-        __syncwarp();
-        // Lh = L_CJ L_JJ^{-1}: row by row, columns from the last to the first
-        if (w > 1) {
-            for (int i = lane; i < c; i += 32) {
-                R* row = lh + (int64_t)i * w;
-                for (int q = w - 2; q >= 0; --q) {
-                    R acc = row[q];
-                    for (int p = q + 1; p < w; ++p) acc -= row[p] * Form::from_d(ws->jj[p * w + q]);
-                    row[q] = acc;
-                }
+    } else {
+        double* base = a.scratch + gslot * 3 * a.max_cw;
+        lh = reinterpret_cast<R*>(base);
+        x = reinterpret_cast<R*>(base + a.max_cw);
+        xpos = reinterpret_cast<int32_t*>(base + 2 * a.max_cw);
+    }
+    double* jj = kCta ? cs->jj : ws->jj;
+    double* tt = kCta ? cs->t : ws->t;
+    for (int e = tid; e < cw; e += gsz) {
+        const int q = Lmap[e];
+        lh[e] = q >= 0 ? Form::from_d(a.Lval[q]) : R(0);
+        xpos[e] = q >= 0 ? a.l2s[q] : -1;
+        x[e] = R(0);
+    }
+    for (int e = tid; e < w * w; e += gsz) {
+        const int q = a.JJl[I.ww_off + e];
+        jj[e] = q >= 0 ? a.Lval[q] : 0.0;
+    }
+    // this warp's pairs: the whole list, or a contiguous range of rows balanced by pairs
+    const uint32_t* hik = a.hit_ik + I.hit_off;
+    const int32_t* hpos = a.hit_pos + I.hit_off;
+    PairRange pr;
+    pr.e0 = 0;
+    pr.e1 = I.hit_cnt;
+    if (kCta) {
+        const int32_t* hrow = a.hrow + I.hrow_off;
+        const int64_t E = I.hit_cnt;
+        const int v = Gr::warp();
+        auto row_start_at = [&](int64_t target) -> int64_t {
+            int lo = 0, hi = c;
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (hrow[mid] < target) lo = mid + 1; else hi = mid;
             }
-            __syncwarp();
-        }
-        // X = -G~_CC Lh : diagonal part (conflict free, lane owns row i) ...
-        for (int i = lane; i < c; i += 32) {
-            R g = Form::ld(Gw + a.Sdiag[Crow[i]]);
-            for (int q = 0; q < w; ++q) x[i * w + q] -= g * lh[i * w + q];
-        }
-        __syncwarp();
-        // ... and the off-diagonal pairs of S, each used for (i, k) and (k, i)
-        {
-            const uint32_t* hik = a.hit_ik + I.hit_off;
-            const int32_t* hpos = a.hit_pos + I.hit_off;
-            const int64_t hc = I.hit_cnt;
-            if (w == 1) {
-                for (int64_t h = lane; h < hc; h += 32) {
-                    uint32_t ik = hik[h];
-                    int i = ik >> 16, k = ik & 0xffff;
-                    R g = Form::ld(Gw + hpos[h]);
-                    atomicAdd(x + i, -g * lh[k]);
-                    atomicAdd(x + k, -g * lh[i]);
-                }
-            } else {
-                for (int64_t h = lane; h < hc; h += 32) {
-                    uint32_t ik = hik[h];
-                    int i = ik >> 16, k = ik & 0xffff;
-                    R g = Form::ld(Gw + hpos[h]);
-                    for (int q = 0; q < w; ++q) {
-                        atomicAdd(x + i * w + q, -g * lh[k * w + q]);
-                        atomicAdd(x + k * w + q, -g * lh[i * w + q]);
-                    }
-                }
+            return hrow[lo];
+        };
+        pr.e0 = v == 0 ? 0 : row_start_at(E * v / kWarps);
+        pr.e1 = v == kWarps - 1 ? E : row_start_at(E * (v + 1) / kWarps);
+    }
+    load_pairs(hik, hpos, pr.e0, pr.e1, lane, pr.ik, pr.pos);
+    Gr::sync();
+    // Lh = L_CJ L_JJ^{-1}: row by row, columns from the last to the first
+    if (w > 1) {
+        for (int i = tid; i < c; i += gsz) {
+            R* row = lh + (int64_t)i * w;
+            for (int q = w - 2; q >= 0; --q) {
+                R acc = row[q];
+                for (int p = q + 1; p < w; ++p) acc -= row[p] * Form::from_d(jj[p * w + q]);
+                row[q] = acc;
             }
         }
-        __syncwarp();
-        // store X on S
-        for (int e = lane; e < cw; e += 32) {
-            int q = Lmap[e];
-            if (q >= 0) Form::st(Gw + a.l2s[q], x[e]);
-        }
-        // M = L_JJ^{-1} (unit lower), in place in jj; lane b owns column b
-        if (w > 1) {
-            if (lane < w) {
-                const int b = lane;
-                // column b of M: M[b][b] = 1, M[r][b] = -sum_{b<=p<r} L[r][p] M[p][b]
-                double col[kWMax];
-                for (int r = 0; r < w; ++r) col[r] = 0.0;
-                col[b] = 1.0;
-                for (int r = b + 1; r < w; ++r) {
-                    double acc = 0.0;
-                    for (int p = b; p < r; ++p) acc -= ws->jj[r * w + p] * col[p];
-                    col[r] = acc;
-                }
-                __syncwarp(__activemask());
-                for (int r = 0; r < w; ++r) ws->jj[r * w + b] = col[r];
+    }
+    Gr::sync();
+    // M = L_JJ^{-1} (unit lower) in place in jj (thread b owns column b), then
+    // T = D_J^{-1} M with the FP64 pivot inverses (thread r owns row r)
+    if (tid < 32) {
+        double col[kWMax];
+        if (tid < w) {
+            const int b = tid;
+            for (int r = 0; r < w; ++r) col[r] = 0.0;
+            col[b] = 1.0;
+            for (int r = b + 1; r < w; ++r) {
+                double acc = 0.0;
+                for (int p = b; p < r; ++p) acc -= jj[r * w + p] * col[p];
+                col[r] = acc;
             }
-            __syncwarp();
-        } else {
-            if (lane == 0) ws->jj[0] = 1.0;
-            __syncwarp();
         }
-        // T = D_J^{-1} M (FP64 pivot inverses); lane r owns row r
-        if (lane < w) {
-            const int r = lane;
-            const int col = I.s0 + r;
-            const bool first = a.pstart[col] != 0;
-            const bool two = first ? (col + 1 < a.n && a.pstart[col + 1] == 0) : true;
-            const double* d = a.Dval + a.dpos[col];
+        __syncwarp();
+        if (tid < w)
+            for (int r = 0; r < w; ++r) jj[r * w + tid] = col[r];
+        __syncwarp();
+        if (tid < w) {
+            const int r = tid;
+            const int col_ = I.s0 + r;
+            const bool first = a.pstart[col_] != 0;
+            const bool two = first ? (col_ + 1 < a.n && a.pstart[col_ + 1] == 0) : true;
+            const double* d = a.Dval + a.dpos[col_];
             double i_rr, i_rs = 0.0;
             int partner = -1;
             if (!two) {
@@ -197,31 +280,91 @@ __global__ void __launch_bounds__(kWarps * 32) selinv_persistent(SelinvArgs a, t
                 i_rs = -d[1] / det;
             }
             for (int b = 0; b < w; ++b) {
-                double v = i_rr * ws->jj[r * w + b];
-                if (partner >= 0) v += i_rs * ws->jj[partner * w + b];
-                ws->t[r * w + b] = v;
+                double v = i_rr * jj[r * w + b];
+                if (partner >= 0) v += i_rs * jj[partner * w + b];
+                tt[r * w + b] = v;
             }
         }
-        __syncwarp();
-        // G_JJ[r][b] = sum_p M[p][r] T[p][b] - sum_i Lh[i][r] X[i][b]   (r >= b)
-        for (int r = 0; r < w; ++r) {
-            for (int b = 0; b <= r; ++b) {
-                double s = 0.0;
-                for (int i = lane; i < c; i += 32) s += (double)lh[i * w + r] * (double)x[i * w + b];
+    }
+
+    // ---- phase B: wait until every supernode owning a row of C has published --------
+    bool ok = true;
+    for (int i = tid; i < c; i += gsz) {
+        if (!wait_flag(a.done + a.owner[Crow[i]], epoch, a.status, a.wait_limit)) {
+            ok = false;
+            break;
+        }
+    }
+    if (Gr::any(!ok)) return false;
+    __threadfence();
+
+    // ---- phase C ---------------------------------------------------------------------
+    accumulate_pairs<Form>(pr, hik, hpos, Gw, lh, x, w, lane);
+    Gr::sync();
+    for (int e = tid; e < cw; e += gsz) {
+        const int p = xpos[e];
+        if (p >= 0) Form::st(Gw + p, x[e]);
+    }
+    // G_JJ[r][b] = (M^T T)[r][b] - sum_i Lh[i][r] X[i][b]   (r >= b): FP64 accumulation
+    const int npair = w * (w + 1) / 2;
+    for (int pidx = 0, r = 0; r < w; ++r) {
+        for (int b = 0; b <= r; ++b, ++pidx) {
+            double s = 0.0;
+            for (int i = tid; i < c; i += gsz) s += (double)lh[i * w + r] * (double)x[i * w + b];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                if (lane == 0) {
-                    double m = 0.0;
-                    for (int p = 0; p < w; ++p) m += ws->jj[p * w + r] * ws->t[p * w + b];
-                    int sp = a.JJs[I.ww_off + r * w + b];
-                    if (sp >= 0) Form::st(Gw + sp, Form::from_d(m - s));
-                }
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) {
+                if (kCta) cs->red[threadIdx.x >> 5][pidx] = s;
+                else ws->red[pidx] = s;
             }
         }
-        __syncwarp();
-        if (lane == 0) {
-            __threadfence();
-            st_release(a.done + J, epoch);
+    }
+    Gr::sync();
+    for (int pidx = tid; pidx < npair; pidx += gsz) {
+        int r = 0;
+        while ((r + 1) * (r + 2) / 2 <= pidx) ++r;
+        const int b = pidx - r * (r + 1) / 2;
+        double s = 0.0;
+        if (kCta) {
+            for (int v = 0; v < kWarps; ++v) s += cs->red[v][pidx];
+        } else {
+            s = ws->red[pidx];
+        }
+        double m = 0.0;
+        for (int p = 0; p < w; ++p) m += jj[p * w + r] * tt[p * w + b];
+        const int sp = a.JJs[I.ww_off + r * w + b];
+        if (sp >= 0) Form::st(Gw + sp, Form::from_d(m - s));
+    }
+    Gr::sync();
+    if (tid == 0) {
+        __threadfence();
+        st_release(a.done + J, epoch);
+    }
+    return true;
+}
+
+template <class Form>
+__global__ void __launch_bounds__(kWarps * 32) selinv_persistent(SelinvArgs a, typename Form::G* Gw) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ CtaShared cs;
+    WarpSmem* ws = reinterpret_cast<WarpSmem*>(smem_raw) + (threadIdx.x >> 5);
+    const int warp = threadIdx.x >> 5;
+    const uint32_t epoch = *a.epoch;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            cs.item = atomicAdd(a.ticket, 1);
+            cs.stop = ld_volatile(a.status) != ST_OK;
+        }
+        __syncthreads();
+        const int item = cs.item;
+        if (item >= a.nitems || cs.stop) break;
+        const WorkItem it = a.items[item];
+        if (it.big) {
+            process<Form, true>(a, Gw, a.order[it.first], epoch, ws, &cs, (int64_t)blockIdx.x * kWarps);
+        } else if (warp < it.count) {
+            process<Form, false>(a, Gw, a.order[it.first + warp], epoch, ws, &cs,
+                                 (int64_t)blockIdx.x * kWarps + warp);
         }
     }
 }

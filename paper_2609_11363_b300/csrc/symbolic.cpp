@@ -49,7 +49,7 @@ bool subset_except(const int32_t* a, int64_t na, const int32_t* b, int64_t nb, i
 }  // namespace
 
 std::string build_plan(int64_t n, const int64_t* Lrp, const int32_t* Lc, const int8_t* ps, int cap,
-                       HostPlan& P) {
+                       int64_t big_pairs, int group, HostPlan& P) {
     if (n < 0) return "negative n";
     if (n > INT32_MAX - 1) return "n does not fit int32 column indices";
     if (cap <= 0) cap = 16;
@@ -243,22 +243,25 @@ std::string build_plan(int64_t n, const int64_t* Lrp, const int32_t* Lc, const i
     P.Lmap.assign(cw, -1);
     P.JJl.assign(ww, -1);
     P.JJs.assign(ww, -1);
-    // hit pairs: count, then fill
+    // pairs of C x C in S, both triangles and the diagonal, sorted by (i, k):
+    //   k < i : (C[i], C[k]) in row C[i] of S_lo            (merge with C[0..i))
+    //   k = i : the diagonal of C[i]
+    //   k > i : (C[k], C[i]) with C[k] in struct(C[i]) or the 2x2 partner of C[i]
     std::vector<int64_t> hits(ns, 0);
-    auto S_row_hits = [&](int64_t s, bool fill, uint32_t* ik, int32_t* pos) {
+    auto pairs = [&](int64_t s, bool fill, uint32_t* ik, int32_t* pos, int32_t* hrow) {
         const auto& C = Cs[s];
+        const int64_t c = (int64_t)C.size();
         int64_t cnt = 0;
-        for (int64_t i = 1; i < (int64_t)C.size(); ++i) {
-            int32_t r = C[i];
-            int64_t q = P.Srp[r], qe = P.Srp[r + 1];
+        for (int64_t i = 0; i < c; ++i) {
+            if (fill) hrow[i] = (int32_t)cnt;
+            const int32_t r = C[i];
+            // lower part
+            int64_t q = P.Srp[r], qe = P.Srp[r + 1] - 1;  // exclude the diagonal
             int64_t k = 0;
             while (q < qe && k < i) {
                 int32_t a = P.Sc[q], b = C[k];
                 if (a == b) {
-                    if (fill) {
-                        ik[cnt] = ((uint32_t)i << 16) | (uint32_t)k;
-                        pos[cnt] = (int32_t)q;
-                    }
+                    if (fill) { ik[cnt] = ((uint32_t)i << 16) | (uint32_t)k; pos[cnt] = (int32_t)q; }
                     ++cnt; ++q; ++k;
                 } else if (a < b) {
                     ++q;
@@ -266,25 +269,67 @@ std::string build_plan(int64_t n, const int64_t* Lrp, const int32_t* Lc, const i
                     ++k;
                 }
             }
+            // diagonal
+            if (fill) { ik[cnt] = ((uint32_t)i << 16) | (uint32_t)i; pos[cnt] = P.Sdiag[r]; }
+            ++cnt;
+            // upper part: column r of S below the diagonal
+            const bool two_first = ps[r] != 0 && r + 1 < n && ps[r + 1] == 0;
+            int64_t qq = Lcp[r], qqe = Lcp[r + 1];
+            k = i + 1;
+            bool partner_pending = two_first;
+            while (k < c) {
+                int32_t b = C[k];
+                // next row of column r: the 2x2 partner r+1 comes before struct(r) (all > r+1)
+                int32_t a;
+                int64_t apos;
+                if (partner_pending) {
+                    a = r + 1;
+                    apos = P.Srp[r + 2] - 2;
+                } else if (qq < qqe) {
+                    a = Lri[qq];
+                    apos = P.l2s[P.Lcsr[qq]];
+                } else {
+                    break;
+                }
+                if (a == b) {
+                    if (fill) { ik[cnt] = ((uint32_t)i << 16) | (uint32_t)k; pos[cnt] = (int32_t)apos; }
+                    ++cnt; ++k;
+                    if (partner_pending) partner_pending = false; else ++qq;
+                } else if (a < b) {
+                    if (partner_pending) partner_pending = false; else ++qq;
+                } else {
+                    ++k;
+                }
+            }
         }
+        if (fill) hrow[c] = (int32_t)cnt;
         return cnt;
     };
     parallel_for(ns, [&](int64_t a, int64_t b) {
-        for (int64_t s = a; s < b; ++s) hits[s] = S_row_hits(s, false, nullptr, nullptr);
+        for (int64_t s = a; s < b; ++s) hits[s] = pairs(s, false, nullptr, nullptr, nullptr);
     });
-    int64_t hoff = 0;
+    int64_t hoff = 0, roff = 0;
     for (int64_t s = 0; s < ns; ++s) {
         P.sn[s].hit_off = hoff;
         P.sn[s].hit_cnt = hits[s];
+        P.sn[s].hrow_off = roff;
         hoff += hits[s];
+        roff += P.sn[s].c + 1;
+        if (hits[s] > INT32_MAX) return "a supernode has >= 2^31 pairs: unsupported";
     }
     P.hit_pairs = hoff;
     P.hit_ik.resize(hoff);
     P.hit_pos.resize(hoff);
+    P.hrow.resize(roff);
     parallel_for(ns, [&](int64_t a, int64_t b) {
         for (int64_t s = a; s < b; ++s) {
             SnInfo& I = P.sn[s];
-            S_row_hits(s, true, P.hit_ik.data() + I.hit_off, P.hit_pos.data() + I.hit_off);
+            pairs(s, true, P.hit_ik.data() + I.hit_off, P.hit_pos.data() + I.hit_off, P.hrow.data() + I.hrow_off);
+        }
+    });
+    parallel_for(ns, [&](int64_t a, int64_t b) {
+        for (int64_t s = a; s < b; ++s) {
+            SnInfo& I = P.sn[s];
             const auto& C = Cs[s];
             std::copy(C.begin(), C.end(), P.Crow.begin() + I.crow_off);
             // Lmap: L(C[i], s0+t)
@@ -317,8 +362,28 @@ std::string build_plan(int64_t n, const int64_t* Lrp, const int32_t* Lc, const i
     for (int64_t s = 0; s < ns; ++s) P.order[s] = (int32_t)(ns - 1 - s);
     std::stable_sort(P.order.begin(), P.order.end(), [&](int32_t a, int32_t b) {
         if (P.sn[a].level != P.sn[b].level) return P.sn[a].level < P.sn[b].level;
-        return P.sn[a].c > P.sn[b].c;
+        return P.sn[a].hit_cnt > P.sn[b].hit_cnt;
     });
+    // work items: a large supernode alone (whole CTA), else up to `group` consecutive ones
+    P.items.clear();
+    for (int64_t t = 0; t < ns;) {
+        const SnInfo& I = P.sn[P.order[t]];
+        WorkItem it;
+        it.first = (int32_t)t;
+        it.pad = 0;
+        if (I.hit_cnt >= big_pairs) {
+            it.count = 1;
+            it.big = 1;
+            ++t;
+        } else {
+            int64_t e = t;
+            while (e < ns && e - t < group && P.sn[P.order[e]].hit_cnt < big_pairs) ++e;
+            it.count = (int32_t)(e - t);
+            it.big = 0;
+            t = e;
+        }
+        P.items.push_back(it);
+    }
     return "";
 }
 

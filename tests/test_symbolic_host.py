@@ -1,0 +1,139 @@
+"""Host-side checks of libsinv without a GPU: exported symbols, the symbolic
+analysis (S bit-exact against the oracle, supernode and level invariants) and
+the pattern validation errors."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+from workloads.configs import diff3d, lap2d_32, plant_2x2, random_factors
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2609_11363_b300.build import build_lib
+    build_lib()
+    from paper_2609_11363_b300 import load_library
+    return load_library()
+
+
+def _host_handle(f, **kw):
+    from paper_2609_11363_b300 import Handle
+    return Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start, device=-1, **kw)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    hdr = open(os.path.join(ROOT, "include", "sinv.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    names = sorted(set(re.findall(r"\b(sinv_[a-z_0-9]+)\s*\(", hdr)))
+    assert len(names) >= 14
+    for nm in names:
+        assert hasattr(lib, nm), nm
+    from paper_2609_11363_b300.binding import EXPORTS
+    assert sorted(EXPORTS) == names
+
+
+CASES = {
+    "lap2d": lambda: lap2d_32().factors,
+    "lap2d_exact": lambda: lap2d_32(tau=0.0).factors,
+    "lap2d_2x2": lambda: plant_2x2(lap2d_32().factors, 0.4, 3),
+    "rand": lambda: random_factors(400, 0.03, 0.2, 8),
+    "diff3d_10": lambda: plant_2x2(diff3d(10).factors, 0.05, 4),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_pattern_bit_exact_vs_oracle(lib, name):
+    f = CASES[name]()
+    h = _host_handle(f)
+    rp, col = h.pattern_host()
+    S = oracle.symbolic_S(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+    assert np.array_equal(rp, S[0]) and np.array_equal(col, S[1])
+    st = h.stats()
+    assert st["nnz_S_lo"] == len(S[1]) and st["n_2x2"] == int(np.sum(f.pivot_start == 0))
+
+
+def _structs(f):
+    Lc = f.L_csr().tocsc()
+    Lc.sort_indices()
+    return [set(Lc.indices[Lc.indptr[j]:Lc.indptr[j + 1]].tolist()) for j in range(f.n)]
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("cap", [1, 4, 16])
+def test_supernode_and_level_invariants(lib, name, cap):
+    f = CASES[name]()
+    h = _host_handle(f, supernode_cap=cap)
+    start, level = h.supernodes()
+    n = f.n
+    assert start[0] == 0 and start[-1] == n and np.all(np.diff(start) >= 1) and np.max(np.diff(start)) <= max(cap, 2)
+    ps = f.pivot_start.astype(bool)
+    # a supernode never splits a 2x2 block
+    assert np.all(ps[start[:-1]])
+    st = _structs(f)
+    blocks = [j for j in range(n) if ps[j]] + [n]
+    owner = np.repeat(np.arange(len(start) - 1), np.diff(start))
+    bstart_set = set(start[:-1].tolist())
+    for b in range(len(blocks) - 2):
+        P = range(blocks[b], blocks[b + 1]); Q = range(blocks[b + 1], blocks[b + 2])
+        U = set().union(*[st[p] for p in P]) - set(P) - set(range(blocks[b + 1]))
+        U = {r for r in U if r >= blocks[b + 1]}
+        joined = blocks[b + 1] not in bstart_set
+        rule = (len(U) > 0 and min(U) == Q[0]) and all((U - set(Q)) <= st[c] for c in Q)
+        if joined:
+            assert rule, ("joined blocks violate the merge rule", b)
+        else:
+            width = blocks[b + 2] - start[owner[blocks[b]]]
+            assert (not rule) or width > cap, ("mergeable blocks left apart", b)
+    for s in range(len(start) - 1):
+        cols = range(start[s], start[s + 1])
+        C = set().union(*[st[c] for c in cols]) - set(range(start[s + 1] + 0)) if cols else set()
+        C = {r for r in C if r >= start[s + 1]}
+        want = 0 if not C else 1 + max(level[owner[r]] for r in C)
+        assert level[s] == want
+
+
+def _expect_pattern_error(n, rp, col, ps):
+    from paper_2609_11363_b300 import Handle, SinvError
+    with pytest.raises(SinvError) as ei:
+        Handle(n, np.asarray(rp, np.int64), np.asarray(col, np.int32), np.asarray(ps, np.int8), device=-1)
+    assert ei.value.name == "SINV_ERR_PATTERN"
+
+
+def test_pattern_validation(lib):
+    # rows: 0: -, 1: [0], 2: [0, 1]
+    ok = ([0, 0, 1, 3], [0, 0, 1], [1, 1, 1])
+    from paper_2609_11363_b300 import Handle
+    Handle(3, np.asarray(ok[0], np.int64), np.asarray(ok[1], np.int32), np.asarray(ok[2], np.int8), device=-1)
+    _expect_pattern_error(3, [0, 0, 1, 3], [0, 1, 0], [1, 1, 1])      # unsorted row
+    _expect_pattern_error(3, [0, 0, 1, 3], [0, 0, 0], [1, 1, 1])      # duplicate
+    _expect_pattern_error(3, [0, 0, 1, 3], [0, 0, 2], [1, 1, 1])      # diagonal stored
+    _expect_pattern_error(3, [0, 0, 1, 3], [0, -1, 1], [1, 1, 1])     # negative column
+    _expect_pattern_error(3, [0, 0, 2, 3], [0, 0, 1], [1, 1, 1])      # col >= row via bad rowptr
+    _expect_pattern_error(3, [0, 1, 1, 3], [0, 0, 1], [1, 1, 1])      # row 0 has an entry
+    _expect_pattern_error(3, [0, 0, 1, 1], [0], [0, 1, 1])            # first flag 0
+    _expect_pattern_error(3, [0, 0, 0, 0], [], [1, 0, 0])             # 3x3 block
+    _expect_pattern_error(3, [0, 0, 1, 1], [0], [1, 0, 1])            # L(1,0) inside a 2x2 block
+    _expect_pattern_error(3, [0, 0, 0, 0], [], [1, 2, 1])             # bad flag value
+
+
+def test_host_only_handle_rejects_numeric_calls(lib):
+    from paper_2609_11363_b300 import SinvError
+    f = lap2d_32().factors
+    h = _host_handle(f)
+    with pytest.raises(SinvError) as ei:
+        h.sync_status()
+    assert ei.value.name == "SINV_ERR_INVALID_ARG"
+
+
+def test_status_strings(lib):
+    for code in range(8):
+        s = lib.sinv_status_string(code)
+        assert s and s != b"unknown status"
+    assert lib.sinv_status_string(99) == b"unknown status"
