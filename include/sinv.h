@@ -89,7 +89,7 @@ sinv_status sinv_get_pattern(sinv_handle h, const int64_t **S_rowptr, const int3
 /* Copies S_lo into caller-owned HOST arrays S_rowptr [n+1] and S_col [|S_lo|]. */
 sinv_status sinv_get_pattern_host(sinv_handle h, int64_t *S_rowptr, int32_t *S_col);
 
-/* Selected inverse on S (Section 2.1, eqs. (2.4)-(2.5)): for every pivot block
+/* Selected inverse on S (Section 2.1, Eqs. (4)-(5)): for every pivot block
  * from the last to the first, G21 = -G22 L21 restricted to S (entries of G22
  * outside S read as zero), G11 = D11^{-1} - L21^T G21.  Supernodes of
  * consecutive pivot blocks with nested structure are processed as one dense
@@ -99,7 +99,7 @@ sinv_status sinv_get_pattern_host(sinv_handle h, int64_t *S_rowptr, int32_t *S_c
 sinv_status sinv_selinv(sinv_handle h, const double *L_val, const double *D_val,
                         sinv_precision prec, double *G_S, void *stream);
 
-/* NInv on S (Section 2.2, eqs. (2.6) and (2.8)): W = sum_{t=0}^{m} E^t with
+/* NInv on S (Section 2.2, Eqs. (6) and (8)): W = sum_{t=0}^{m} E^t with
  * L = I - E, by m Horner steps W <- I + E W on the fixed pattern of the
  * truncated series, then N = W^T D^{-1} W evaluated on S only.  0 <= m <= 60.
  *   L_val, D_val, N_S [|S_lo|]: device.  m > 60: SINV_ERR_UNSUPPORTED. */
@@ -111,7 +111,7 @@ sinv_status sinv_ninv(sinv_handle h, const double *L_val, const double *D_val, i
 sinv_status sinv_mix(sinv_handle h, const double *G_S, const double *N_S, double eps,
                      double *M_S, void *stream);
 
-/* Low-rank spectral correction on S (Section 2.5, eq. (2.9); its diagonal is
+/* Low-rank spectral correction on S (Section 2.5, Eq. (9); its diagonal is
  * the update formula of Section 2.6): X_ij += sum_{l<k} lambda_l V_il V_jl for
  * (i, j) in S_lo.
  *   V [n*k] row-major, lambda [k], X_S [|S_lo|] in/out: device.  k <= 256. */
@@ -136,6 +136,20 @@ sinv_status sinv_get_stats(sinv_handle h, sinv_stats *out);
  * sn_level[n_supernodes]. */
 sinv_status sinv_get_supernodes(sinv_handle h, const int32_t **sn_start, const int32_t **sn_level,
                                 int64_t *n_supernodes);
+
+/* Per-kernel timing.  While enabled, every kernel a numeric call launches is
+ * bracketed by CUDA events on the call's stream (small host overhead, no
+ * device synchronisation).  sinv_trace_read waits for the recorded events,
+ * and copies up to max_entries aggregated rows {kernel name, launches, total
+ * milliseconds}; *count receives the number copied.  reset != 0 clears the
+ * totals afterwards. */
+typedef struct {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+} sinv_kernel_time;
+sinv_status sinv_trace_enable(sinv_handle h, int enable);
+sinv_status sinv_trace_read(sinv_handle h, sinv_kernel_time *out, int max_entries, int *count, int reset);
 
 const char *sinv_status_string(sinv_status s);
 /* Copies the handle's last error message (NUL terminated) into buf. */

@@ -6,12 +6,12 @@ inverse path computes, written from the paper (Akter, Bollhoefer, Schenk,
 LDL^T Factorization and Spectral Corrections"):
 
 * ``symbolic_S``      -- S = {(i,j): (L+D+L^T)_ij != 0}   (Section 1)
-* ``selinv``          -- scalar Takahashi recurrence, eqs. (2.4)-(2.5) with the
+* ``selinv``          -- scalar Takahashi recurrence, Eqs. (4)-(5) with the
                          restriction to S of Section 2.1       (C, csrc/selinv_ref.c)
 * ``ninv``            -- truncated Neumann series L^{-1} ~ sum_{t<=m} E_L^t,
-                         eq. (2.6), and (L^inv)^T D^{-1} L^inv, eq. (2.8), on S
+                         Eq. (6), and (L^inv)^T D^{-1} L^inv, Eq. (8), on S
 * ``mix``             -- Mix approximation (Section 2.3)
-* ``lowrank_correct`` -- A^inv + V_k Lambda_k V_k^T on S, eq. (2.9); diagonal
+* ``lowrank_correct`` -- A^inv + V_k Lambda_k V_k^T on S, Eq. (9); diagonal
                          update formula of Section 2.6
 * ``lanczos_einv``    -- dominant eigenpairs of E_inv = A^{-1} - A^inv
                          (Section 2.5, Algorithm 1 step 5)

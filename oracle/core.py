@@ -130,7 +130,7 @@ def _Dinv(n, pivot_start, d_diag, d_off):
 
 
 def ninv_W(n, L_rowptr, L_col, L_val, m):
-    """W = sum_{t=0}^{m} E_L^t (eq. (2.6) truncated after the m-th power)."""
+    """W = sum_{t=0}^{m} E_L^t (Eq. (6) truncated after the m-th power)."""
     E = _E(n, L_rowptr, L_col, L_val)
     I = sp.identity(n, format="csr")
     W = I.copy()
@@ -141,7 +141,7 @@ def ninv_W(n, L_rowptr, L_col, L_val, m):
 
 
 def ninv(n, L_rowptr, L_col, L_val, pivot_start, d_diag, d_off, m, S=None, chunk=1 << 20):
-    """NInv on S: N_ij = (W^T D^{-1} W)_ij for (i, j) in S_lo (eq. (2.8)).
+    """NInv on S: N_ij = (W^T D^{-1} W)_ij for (i, j) in S_lo (Eq. (8)).
 
     W is the exact truncated series (no value dropping); the product is
     evaluated exactly on S, entry by entry as the dot product of column i of W
@@ -192,7 +192,7 @@ def mix(G_S, N_S, eps):
 
 
 def lowrank_correct(Srp, Sc, X_S, V, lam):
-    """(A^inv + V diag(lam) V^T)_ij for (i, j) in S_lo (eq. (2.9))."""
+    """(A^inv + V diag(lam) V^T)_ij for (i, j) in S_lo (Eq. (9))."""
     rows, cols = _S_entries(Srp, Sc)
     V = np.asarray(V, dtype=np.float64).reshape(len(Srp) - 1, -1)
     lam = np.asarray(lam, dtype=np.float64)

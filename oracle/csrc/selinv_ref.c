@@ -3,13 +3,13 @@
  * baseline of the benchmark; never by the product path).
  *
  * Plain FP64 selected inversion by the scalar Takahashi recurrence at pivot-block
- * granularity, Section 2.1, eqs. (2.4)-(2.5):
+ * granularity, Section 2.1, Eqs. (4)-(5):
  *     G21 <- -G22 L21 ,   G11 <- D11^{-1} - L21^T G21 ,
  * processed from the last pivot block to the first, where block 1 is one pivot
- * block P of D (1x1 or 2x2) and block 2 is everything after it.  "The
- * computation of G21 is restricted to the set S and entries outside this
- * pattern are discarded" (Section 2.1): when G22 is read, entries outside S
- * read as zero, and X = G21 is stored only where (r, p) is in S.
+ * block P of D (1x1 or 2x2) and block 2 is everything after it.  Section 2.1
+ * restricts G21 to the pattern S and throws away whatever falls outside it:
+ * here, when G22 is read its entries outside S count as zero, and X = G21 is
+ * stored only where (r, p) is in S.
  *
  * Reading for a 2x2 block whose two columns have different row structure: X is
  * formed on the union U of both structures and G11 uses that unrestricted X, so

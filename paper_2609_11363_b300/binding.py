@@ -27,6 +27,7 @@ EXPORTS = [
     "sinv_symbolic", "sinv_get_pattern", "sinv_get_pattern_host", "sinv_selinv", "sinv_ninv", "sinv_mix",
     "sinv_lowrank_correct", "sinv_sync_status", "sinv_get_stats", "sinv_get_supernodes",
     "sinv_status_string", "sinv_last_error", "sinv_destroy", "sinv_debug_wait_timeout",
+    "sinv_trace_enable", "sinv_trace_read",
 ]
 
 
@@ -40,6 +41,10 @@ class SinvError(RuntimeError):
 class _Opts(ctypes.Structure):
     _fields_ = [("supernode_cap", ctypes.c_int32), ("device", ctypes.c_int32), ("wait_limit", ctypes.c_int64),
                 ("big_pairs", ctypes.c_int64)]
+
+
+class _KTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
 class _Stats(ctypes.Structure):
@@ -78,6 +83,9 @@ def load_library():
     lib.sinv_destroy.argtypes = [H]
     lib.sinv_destroy.restype = None
     lib.sinv_debug_wait_timeout.argtypes = [H, P]
+    lib.sinv_trace_enable.argtypes = [H, ctypes.c_int]
+    lib.sinv_trace_read.argtypes = [H, ctypes.POINTER(_KTime), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                    ctypes.c_int]
     for name in EXPORTS:
         f = getattr(lib, name)
         if name not in ("sinv_status_string", "sinv_destroy"):
@@ -224,6 +232,17 @@ class Handle:
 
     def sync_status(self, stream=None):
         self._check(self._lib.sinv_sync_status(self._h, _stream_ptr(stream)))
+
+    def trace(self, enable=True):
+        """Turn per-kernel event timing on or off."""
+        self._check(self._lib.sinv_trace_enable(self._h, int(bool(enable))))
+
+    def trace_read(self, reset=True) -> dict:
+        """{kernel name: (launches, total ms)} since the last reset (waits for the events)."""
+        buf = (_KTime * 64)()
+        cnt = ctypes.c_int()
+        self._check(self._lib.sinv_trace_read(self._h, buf, 64, ctypes.byref(cnt), int(bool(reset))))
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(cnt.value)}
 
     def debug_wait_timeout(self, stream=None) -> int:
         return int(self._lib.sinv_debug_wait_timeout(self._h, _stream_ptr(stream)))

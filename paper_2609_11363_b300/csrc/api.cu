@@ -4,8 +4,10 @@
 
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/sinv.h"
 #include "kernels.h"
@@ -13,7 +15,81 @@
 
 using namespace sinv;
 
+namespace sinv {
+
+// Event pairs around every kernel launch of a call, aggregated by kernel name.
+struct Tracer {
+    struct Rec {
+        const char* name;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    std::map<std::string, std::pair<int64_t, double>> agg;
+    int open = -1;
+
+    cudaEvent_t get() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void begin(const char* name, cudaStream_t st) {
+        Rec r{name, get(), get()};
+        cudaEventRecord(r.a, st);
+        pending.push_back(r);
+        open = (int)pending.size() - 1;
+    }
+    void end(cudaStream_t st) {
+        if (open >= 0) cudaEventRecord(pending[open].b, st);
+        open = -1;
+    }
+    void collect() {
+        for (auto& r : pending) {
+            float ms = 0.f;
+            if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+                auto& x = agg[r.name];
+                x.first += 1;
+                x.second += ms;
+            }
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        pending.clear();
+    }
+    ~Tracer() {
+        for (auto& r : pending) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+thread_local Tracer* g_tracer = nullptr;
+
+void trace_begin(const char* name, cudaStream_t st) {
+    if (g_tracer) g_tracer->begin(name, st);
+}
+void trace_end(cudaStream_t st) {
+    if (g_tracer) g_tracer->end(st);
+}
+
+// installs the handle's tracer (if any) for the lifetime of a numeric call
+struct TraceScope {
+    Tracer* prev;
+    explicit TraceScope(Tracer* t) : prev(g_tracer) { g_tracer = t; }
+    ~TraceScope() { g_tracer = prev; }
+};
+
+}  // namespace sinv
+
 struct sinv_handle_s {
+    Tracer* tracer = nullptr;
     int device = 0;
     int num_sms = 0;
     HostPlan P;
@@ -156,9 +232,12 @@ sinv_status sinv_symbolic(int64_t n, const int64_t* L_rowptr, const int32_t* L_c
         *out = h;  // so that the caller can read the message
         return s;
     }
+    if (!host_only) cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    const int64_t thin_level = 2 * (int64_t)(h->num_sms > 0 ? h->num_sms : 148);
     std::string err;
     try {
-        err = build_plan(n, L_rowptr, L_col, pivot_start, cap, big_pairs, selinv_warps_per_cta(), h->P);
+        err = build_plan(n, L_rowptr, L_col, pivot_start, cap, big_pairs, selinv_warps_per_cta(), thin_level,
+                         h->P);
     } catch (const std::bad_alloc&) {
         set_err(h, "host allocation failed in the symbolic analysis");
         *out = h;
@@ -176,7 +255,6 @@ sinv_status sinv_symbolic(int64_t n, const int64_t* L_rowptr, const int32_t* L_c
         *out = h;
         return SINV_OK;
     }
-    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     std::vector<int64_t> Lrp(L_rowptr, L_rowptr + n + 1);
 #define UP(dst, src)                                              \
     do {                                                          \
@@ -296,6 +374,7 @@ sinv_status sinv_selinv(sinv_handle h, const double* L_val, const double* D_val,
         sinv_status s = ensure_work(h, (size_t)P.nnzS * sizeof(float) + 256);
         if (s != SINV_OK) return s;
     }
+    TraceScope trace_scope(h->tracer);
     SelinvArgs a;
     a.sn = h->dsn;
     a.order = h->dorder;
@@ -369,6 +448,7 @@ sinv_status sinv_ninv(sinv_handle h, const double* L_val, const double* D_val, i
             return cuda_fail(h, e, "upload Neumann pattern");
         }
     }
+    TraceScope trace_scope(h->tracer);
     NinvArgs a;
     a.n = P.n;
     a.m = m;
@@ -403,6 +483,7 @@ sinv_status sinv_mix(sinv_handle h, const double* G_S, const double* N_S, double
     if (!G_S || !N_S || !M_S) return SINV_ERR_INVALID_ARG;
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    TraceScope trace_scope(h->tracer);
     if ((e = mix_launch(G_S, N_S, eps, M_S, h->P.nnzS, h->num_sms, (cudaStream_t)stream)) != cudaSuccess)
         return cuda_fail(h, e, "mix launch");
     return SINV_OK;
@@ -424,6 +505,7 @@ sinv_status sinv_lowrank_correct(sinv_handle h, int k, const double* V, const do
         sinv_status s = ensure_work(h, ((size_t)h->P.n * k + k) * sizeof(float) + 256);
         if (s != SINV_OK) return s;
     }
+    TraceScope trace_scope(h->tracer);
     if ((e = lowrank_launch(h->P.n, h->dSrp, h->dSc, k, V, lambda, prec == SINV_FP64 ? 0 : 1, h->dwork, X_S,
                             h->num_sms, (cudaStream_t)stream)) != cudaSuccess)
         return cuda_fail(h, e, "lowrank launch");
@@ -466,10 +548,46 @@ sinv_status sinv_debug_wait_timeout(sinv_handle h, void* stream) {
     return sinv_sync_status(h, stream);
 }
 
+sinv_status sinv_trace_enable(sinv_handle h, int enable) {
+    if (!h) return SINV_ERR_INVALID_ARG;
+    if (!on_device(h)) return SINV_ERR_INVALID_ARG;
+    if (enable && !h->tracer) h->tracer = new (std::nothrow) Tracer();
+    if (enable && !h->tracer) return SINV_ERR_OOM;
+    if (!enable && h->tracer) {
+        cudaSetDevice(h->device);
+        delete h->tracer;
+        h->tracer = nullptr;
+    }
+    return SINV_OK;
+}
+
+sinv_status sinv_trace_read(sinv_handle h, sinv_kernel_time* out, int max_entries, int* count, int reset) {
+    if (!h || !count || max_entries < 0 || (max_entries > 0 && !out)) return SINV_ERR_INVALID_ARG;
+    *count = 0;
+    if (!h->tracer) return SINV_OK;
+    cudaSetDevice(h->device);
+    h->tracer->collect();
+    int c = 0;
+    for (auto& kv : h->tracer->agg) {
+        if (c < max_entries) {
+            memset(&out[c], 0, sizeof(out[c]));
+            strncpy(out[c].name, kv.first.c_str(), sizeof(out[c].name) - 1);
+            out[c].launches = kv.second.first;
+            out[c].total_ms = kv.second.second;
+        }
+        ++c;
+    }
+    *count = std::min(c, max_entries);
+    if (reset) h->tracer->agg.clear();
+    return SINV_OK;
+}
+
 void sinv_destroy(sinv_handle h) {
     if (!h) return;
     if (h->device >= 0) {
         cudaSetDevice(h->device);
+        delete h->tracer;
+        h->tracer = nullptr;
         free_all(h);
     }
     delete h;

@@ -35,7 +35,7 @@ __device__ __forceinline__ bool wait_flag(const uint32_t* flag, uint32_t want, i
             set_status(status, ST_TIMEOUT);
             return false;
         }
-        __nanosleep(64);
+        if (it > 16) __nanosleep(32);
     }
     return true;
 }

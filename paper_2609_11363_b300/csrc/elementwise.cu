@@ -1,5 +1,5 @@
 // Entry-wise work on S: Mix (Section 2.3) and the low-rank correction applied on
-// S as a sampled dense product (Section 2.5, eq. (2.9)).
+// S as a sampled dense product (Section 2.5, Eq. (9)).
 #include "device.cuh"
 #include "kernels.h"
 
@@ -84,7 +84,9 @@ cudaError_t mix_launch(const double* G, const double* N, double eps, double* M, 
     if (nnz == 0) return cudaSuccess;
     int64_t blocks = (nnz / 2 + 255) / 256;
     int grid = (int)std::min<int64_t>(std::max<int64_t>(blocks, 1), (int64_t)num_sms * 8);
+    trace_begin("mix", st);
     mix_kernel<<<grid, 256, 0, st>>>(G, N, eps, M, nnz);
+    trace_end(st);
     return cudaGetLastError();
 }
 
@@ -95,13 +97,19 @@ cudaError_t lowrank_launch(int64_t n, const int64_t* Srp, const int32_t* Sc, int
     int64_t blocks = (n + kLrWarps - 1) / kLrWarps;
     int grid = (int)std::min<int64_t>(blocks, (int64_t)num_sms * 16);
     if (prec == 0) {
+        trace_begin("lowrank", st);
         lowrank_kernel<double><<<grid, kLrWarps * 32, 0, st>>>(n, Srp, Sc, k, V, lambda, X);
+        trace_end(st);
     } else {
         float* Vf = reinterpret_cast<float*>(work);
         float* lf = Vf + n * (int64_t)k;
+        trace_begin("lowrank_to_float", st);
         to_float<<<num_sms * 4, 256, 0, st>>>(V, Vf, n * (int64_t)k);
         to_float<<<1, 256, 0, st>>>(lambda, lf, k);
+        trace_end(st);
+        trace_begin("lowrank", st);
         lowrank_kernel<float><<<grid, kLrWarps * 32, 0, st>>>(n, Srp, Sc, k, Vf, lf, X);
+        trace_end(st);
     }
     return cudaGetLastError();
 }

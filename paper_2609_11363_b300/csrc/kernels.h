@@ -7,6 +7,12 @@
 
 namespace sinv {
 
+// Optional per-kernel event timing.  The API installs a tracer for the duration
+// of a numeric call when tracing is enabled on the handle; launch sites bracket
+// every kernel with these two calls (no-ops otherwise).
+void trace_begin(const char* name, cudaStream_t st);
+void trace_end(cudaStream_t st);
+
 struct SelinvArgs {
     const SnInfo* sn;
     const int32_t* order;

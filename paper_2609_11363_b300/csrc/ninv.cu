@@ -1,5 +1,5 @@
-// NInv (Section 2.2): truncated Neumann series of L^{-1}, eq. (2.6), and the
-// product (L^inv)^T D^{-1} L^inv of eq. (2.8), evaluated on S only.
+// NInv (Section 2.2): truncated Neumann series of L^{-1}, Eq. (6), and the
+// product (L^inv)^T D^{-1} L^inv of Eq. (8), evaluated on S only.
 //
 // With L = I - E, W = sum_{t=0}^{m} E^t is built by m Horner steps
 //     W_t = I + E W_{t-1}      (column form: W_t[:, j] = e_j + sum_{k in struct(j)} E_kj W_{t-1}[:, k])
@@ -10,15 +10,17 @@
 //
 // Horner step: one CTA owns one column j.  Its rows go into a shared-memory
 // hash table (row -> slot).  Warp v handles the columns k of struct(j) with
-// k = v mod 4 and accumulates E_kj W_{t-1}[r, k] into its own copy of the
-// column (the lanes of one instruction touch distinct rows, so no atomic is
-// needed); the copies are summed at the end.
+// k = v mod 8 and adds E_kj W_{t-1}[r, k] into the slot of r with shared-memory
+// atomics (native for FP32 and FP64 and as fast as a plain read-modify-write
+// here; the lanes of one instruction always touch distinct rows).
 //
 // Product on S: N_ij = sum_r W_ri (D^{-1} W)_rj for (i, j) in S_lo.  One CTA
-// owns column j: it tabulates y = (D^{-1} W)[:, j] (the 2x2 blocks of D^{-1}
-// couple a row with its partner, which may add rows outside column j's
-// pattern), then one warp per entry (i, j) streams column i of W and sums
-// W_ri y_r over the rows found in the table.
+// owns column j: it tabulates y = (D^{-1} W)[:, j] on the rows of column j,
+// then one warp per entry (i, j) streams column i of W and sums W_ri y_r over
+// the rows found in the table.  The 2x2 blocks of D^{-1} couple a row with its
+// partner: a row of column i outside column j still meets y through its
+// partner; pattern entries carry a flag bit for rows of 2x2 blocks so that only
+// those rows pay for the extra lookup.
 //
 // Columns too long for shared memory use the same code on a per-CTA slice of
 // global scratch, with atomic accumulation.
@@ -31,15 +33,13 @@ namespace sinv {
 
 namespace {
 
-constexpr int kWarpsH = 4;                    // warps per CTA, Horner step
-constexpr int kThreadsH = kWarpsH * 32;
-constexpr int kSlotsH = 4096;                 // hash slots in shared memory
-constexpr int kColH = kSlotsH / 2;            // longest column kept in shared memory
-constexpr int kWarpsP = 8;                    // warps per CTA, product
-constexpr int kThreadsP = kWarpsP * 32;
-constexpr int kSlotsP = 8192;
-constexpr int kEntP = kSlotsP / 2;            // table entries (column rows + partner rows)
+constexpr int kWarps = 8;                     // warps per CTA (Horner step and product)
+constexpr int kThreads = kWarps * 32;
+constexpr int kSlots = 4096;                  // hash slots in shared memory
+constexpr int kEnt = 2730;                    // longest column kept in shared memory (load <= 2/3)
 constexpr int kUnroll = 8;                    // column entries per lane with loads in flight
+constexpr int32_t kRowMask = 0x7FFFFFFF;      // row index bits of a pattern entry
+constexpr int32_t kTwoFlag = (int32_t)0x80000000u;  // set when the row belongs to a 2x2 block of D
 
 __device__ __forceinline__ uint32_t hash_row(int32_t r, uint32_t mask) {
     return ((uint32_t)r * 2654435761u) & mask;
@@ -109,18 +109,18 @@ template <>
 __device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return fmaf(a, b, c); }
 
 struct Scratch {
-    int32_t* keys;   // per CTA: slots int32 keys, slots int32 vals, slots int32 extra rows
-    void* acc;       // per CTA: accumulators / y values
+    int32_t* keys;   // per CTA: slots int32 keys, slots int32 vals
+    void* acc;       // per CTA: accumulators / y values (slots entries of 8 bytes)
     int64_t slots;   // slots per CTA (0 when every column fits shared memory)
 };
 
 template <class T>
-__global__ void __launch_bounds__(kThreadsH) ninv_horner(NinvArgs a, int t, const T* __restrict__ Wp, T* __restrict__ Wn,
+__global__ void __launch_bounds__(kThreads) ninv_horner(NinvArgs a, int t, const T* __restrict__ Wp, T* __restrict__ Wn,
                                                          int32_t* ticket, Scratch gs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int32_t* skeys = reinterpret_cast<int32_t*>(smem_raw);
-    int32_t* svals = skeys + kSlotsH;
-    T* sacc = reinterpret_cast<T*>(svals + kSlotsH);  // kWarpsH copies of kColH
+    int32_t* svals = skeys + kSlots;
+    T* sacc = reinterpret_cast<T*>(svals + kSlots);  // kEnt accumulators
     __shared__ int32_t s_j;
     const int G = a.m + 2;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -132,117 +132,84 @@ __global__ void __launch_bounds__(kThreadsH) ninv_horner(NinvArgs a, int t, cons
         if (j >= a.n) break;
         const int64_t base = a.Wcp[j];
         const int32_t nj = a.grp[j * G + t + 1];  // rows of groups 0..t
-        const bool small = nj <= kColH;
-        const uint32_t mask = small ? (uint32_t)(kSlotsH - 1) : table_mask(nj);
-        int32_t* keys = small ? skeys : gs.keys + (int64_t)blockIdx.x * 3 * gs.slots;
+        const bool small = nj <= kEnt;
+        const uint32_t mask = small ? (uint32_t)(kSlots - 1) : table_mask(nj);
+        int32_t* keys = small ? skeys : gs.keys + (int64_t)blockIdx.x * 2 * gs.slots;
         int32_t* vals = small ? svals : keys + gs.slots;
-        T* gacc = reinterpret_cast<T*>(gs.acc) + (int64_t)blockIdx.x * gs.slots;
-        for (uint32_t s = threadIdx.x; s <= mask; s += kThreadsH) keys[s] = -1;
-        if (small) {
-            for (int32_t e = threadIdx.x; e < kWarpsH * nj; e += kThreadsH) sacc[(e / nj) * kColH + e % nj] = T(0);
-        } else {
-            for (int32_t e = threadIdx.x; e < nj; e += kThreadsH) gacc[e] = T(0);
-        }
+        T* acc = small ? sacc : reinterpret_cast<T*>(gs.acc) + (int64_t)blockIdx.x * gs.slots;
+        for (uint32_t s = threadIdx.x; s <= mask; s += kThreads) keys[s] = -1;
+        for (int32_t e = threadIdx.x; e < nj; e += kThreads) acc[e] = T(0);
         __syncthreads();
-        for (int32_t e = threadIdx.x; e < nj; e += kThreadsH) vals[table_insert(keys, mask, a.Wr[base + e])] = e;
+        for (int32_t e = threadIdx.x; e < nj; e += kThreads)
+            vals[table_insert(keys, mask, a.Wr[base + e] & kRowMask)] = e;
         __syncthreads();
-        T* acc = small ? sacc + wid * kColH : gacc;
-        // sum_k E_kj W_{t-1}[:, k]: warp wid takes k = wid, wid+4, ...; lanes over column k's groups 0..t-1
-        for (int64_t q = a.Lcp[j] + wid; q < a.Lcp[j + 1]; q += kWarpsH) {
+        // sum_k E_kj W_{t-1}[:, k]: warp wid takes k = wid, wid+8, ...; lanes over column k's
+        // groups 0..t-1, kUnroll entries per lane in flight; shared (or global) atomic adds
+        for (int64_t q = a.Lcp[j] + wid; q < a.Lcp[j + 1]; q += kWarps) {
             const int32_t k = a.Lri[q];
             const T ekj = T(-a.Lval[a.Lcsr[q]]);
             const int64_t kb = a.Wcp[k];
             const int32_t nk = a.grp[(int64_t)k * G + t];
-            // kUnroll entries per lane in flight; all rows of one column are distinct, so the
-            // lanes of a batch never touch the same slot
             for (int32_t e0 = 0; e0 < nk; e0 += 32 * kUnroll) {
                 int32_t r[kUnroll];
                 T v[kUnroll];
 #pragma unroll
                 for (int u = 0; u < kUnroll; ++u) {
                     const int32_t e = e0 + u * 32 + lane;
-                    r[u] = e < nk ? a.Wr[kb + e] : -1;
+                    r[u] = e < nk ? (a.Wr[kb + e] & kRowMask) : -1;
                     v[u] = e < nk ? Wp[kb + e] : T(0);
                 }
 #pragma unroll
                 for (int u = 0; u < kUnroll; ++u) {
                     if (r[u] < 0) continue;
                     const int32_t idx = table_find(keys, vals, mask, r[u]);
-                    if (idx >= 0) {
-                        if (small) acc[idx] = fma_t<T>(ekj, v[u], acc[idx]);
-                        else atomicAdd(acc + idx, ekj * v[u]);
-                    } else {
-                        set_status(a.status, ST_INTERNAL);  // row outside the pattern: never expected
-                    }
+                    if (idx >= 0) atomicAdd(acc + idx, ekj * v[u]);
+                    else set_status(a.status, ST_INTERNAL);  // row outside the pattern: never expected
                 }
-                __syncwarp();
             }
         }
         __syncthreads();
-        for (int32_t e = threadIdx.x; e < nj; e += kThreadsH) {
-            T s = e == 0 ? T(1) : T(0);
-            if (small) {
-#pragma unroll
-                for (int v = 0; v < kWarpsH; ++v) s += sacc[v * kColH + e];
-            } else {
-                s += gacc[e];
-            }
-            Wn[base + e] = s;
-        }
+        for (int32_t e = threadIdx.x; e < nj; e += kThreads) Wn[base + e] = acc[e] + (e == 0 ? T(1) : T(0));
         __syncthreads();
     }
 }
 
 template <class T>
-__global__ void __launch_bounds__(kThreadsP) ninv_product(NinvArgs a, const T* __restrict__ W, const double* __restrict__ dr,
-                                                          const double* __restrict__ dp, const int32_t* __restrict__ part,
-                                                          double* __restrict__ N, int32_t* ticket, Scratch gs) {
+__global__ void __launch_bounds__(kThreads) ninv_product(NinvArgs a, const T* __restrict__ W, const double* __restrict__ dr,
+                                                         const double* __restrict__ dp, const int32_t* __restrict__ part,
+                                                         double* __restrict__ N, int32_t* ticket, Scratch gs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int32_t* skeys = reinterpret_cast<int32_t*>(smem_raw);
-    int32_t* svals = skeys + kSlotsP;
-    T* syv = reinterpret_cast<T*>(svals + kSlotsP);          // kEntP y values
-    __shared__ int32_t s_j, s_extra;
-    __shared__ int32_t s_xrow[kEntP / 2];                      // rows of the extra (partner) entries
+    int32_t* svals = skeys + kSlots;
+    T* syv = reinterpret_cast<T*>(svals + kSlots);  // kEnt values of y = (D^{-1} W)[:, j]
+    __shared__ int32_t s_j;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_j = atomicAdd(ticket, 1);
-            s_extra = 0;
-        }
+        if (threadIdx.x == 0) s_j = atomicAdd(ticket, 1);
         __syncthreads();
         const int64_t j = s_j;
         __syncthreads();
         if (j >= a.n) break;
         const int64_t base = a.Wcp[j];
         const int32_t nj = (int32_t)(a.Wcp[j + 1] - base);
-        const bool small = 2 * nj <= kEntP;
-        const uint32_t mask = small ? (uint32_t)(kSlotsP - 1) : table_mask(2 * (int64_t)nj);
-        int32_t* keys = small ? skeys : gs.keys + (int64_t)blockIdx.x * 3 * gs.slots;
+        const bool small = nj <= kEnt;
+        const uint32_t mask = small ? (uint32_t)(kSlots - 1) : table_mask(nj);
+        int32_t* keys = small ? skeys : gs.keys + (int64_t)blockIdx.x * 2 * gs.slots;
         int32_t* vals = small ? svals : keys + gs.slots;
         T* yv = small ? syv : reinterpret_cast<T*>(gs.acc) + (int64_t)blockIdx.x * gs.slots;
-        int32_t* xrow = small ? s_xrow : vals + gs.slots;
-        for (uint32_t s = threadIdx.x; s <= mask; s += kThreadsP) keys[s] = -1;
+        for (uint32_t s = threadIdx.x; s <= mask; s += kThreads) keys[s] = -1;
         __syncthreads();
-        for (int32_t e = threadIdx.x; e < nj; e += kThreadsP) vals[table_insert(keys, mask, a.Wr[base + e])] = e;
+        for (int32_t e = threadIdx.x; e < nj; e += kThreads)
+            vals[table_insert(keys, mask, a.Wr[base + e] & kRowMask)] = e;
         __syncthreads();
-        // partner rows of 2x2 blocks that are not in column j: y is nonzero there too
-        for (int32_t e = threadIdx.x; e < nj; e += kThreadsP) {
-            const int32_t p = part[a.Wr[base + e]];
-            if (p >= 0 && table_find(keys, vals, mask, p) < 0) {
-                int32_t x = atomicAdd(&s_extra, 1);
-                xrow[x] = p;
-                vals[table_insert(keys, mask, p)] = nj + x;
-            }
-        }
-        __syncthreads();
-        const int32_t ntot = nj + s_extra;
-        for (int32_t e = threadIdx.x; e < ntot; e += kThreadsP) {
-            const int32_t r = e < nj ? a.Wr[base + e] : xrow[e - nj];
-            double y = e < nj ? dr[r] * (double)W[base + e] : 0.0;
-            const int32_t p = part[r];
-            if (p >= 0) {
-                const int32_t x = table_find(keys, vals, mask, p);
-                if (x >= 0 && x < nj) y += dp[r] * (double)W[base + x];
+        // y_r = (D^{-1})_rr W_rj + (D^{-1})_{r,p} W_pj for the rows r of column j (p: 2x2 partner)
+        for (int32_t e = threadIdx.x; e < nj; e += kThreads) {
+            const int32_t rf = a.Wr[base + e];
+            const int32_t r = rf & kRowMask;
+            double y = dr[r] * (double)W[base + e];
+            if (rf & kTwoFlag) {
+                const int32_t x = table_find(keys, vals, mask, part[r]);
+                if (x >= 0) y += dp[r] * (double)W[base + x];
             }
             yv[e] = T(y);
         }
@@ -251,7 +218,7 @@ __global__ void __launch_bounds__(kThreadsP) ninv_product(NinvArgs a, const T* _
         const bool two_first = a.pstart[j] != 0 && j + 1 < a.n && a.pstart[j + 1] == 0;
         const int64_t q0 = a.Lcp[j], q1 = a.Lcp[j + 1];
         const int64_t cnt = (q1 - q0) + 1 + (two_first ? 1 : 0);
-        for (int64_t e = wid; e < cnt; e += kWarpsP) {
+        for (int64_t e = wid; e < cnt; e += kWarps) {
             int64_t i, spos;
             if (e == 0) {
                 i = j;
@@ -268,19 +235,26 @@ __global__ void __launch_bounds__(kThreadsP) ninv_product(NinvArgs a, const T* _
             const int64_t ib = a.Wcp[i], ie = a.Wcp[i + 1];
             T s = T(0);
             for (int64_t f0 = ib; f0 < ie; f0 += 32 * kUnroll) {
-                int32_t r[kUnroll];
+                int32_t rf[kUnroll];
                 T wv[kUnroll];
 #pragma unroll
                 for (int u = 0; u < kUnroll; ++u) {
                     const int64_t f = f0 + u * 32 + lane;
-                    r[u] = f < ie ? a.Wr[f] : -1;
+                    rf[u] = f < ie ? a.Wr[f] : -1;
                     wv[u] = f < ie ? W[f] : T(0);
                 }
 #pragma unroll
                 for (int u = 0; u < kUnroll; ++u) {
-                    if (r[u] < 0) continue;
-                    const int32_t x = table_find(keys, vals, mask, r[u]);
-                    if (x >= 0) s = fma_t<T>(wv[u], yv[x], s);
+                    if (rf[u] == -1) continue;
+                    const int32_t r = rf[u] & kRowMask;
+                    const int32_t x = table_find(keys, vals, mask, r);
+                    if (x >= 0) {
+                        s = fma_t<T>(wv[u], yv[x], s);
+                    } else if (rf[u] & kTwoFlag) {
+                        // r is outside column j but its 2x2 partner may be inside: y_r = (D^{-1})_{r,p} W_pj
+                        const int32_t xp = table_find(keys, vals, mask, part[r]);
+                        if (xp >= 0) s = fma_t<T>(wv[u], T(dp[r] * (double)W[base + xp]), s);
+                    }
                 }
             }
 #pragma unroll
@@ -292,30 +266,27 @@ __global__ void __launch_bounds__(kThreadsP) ninv_product(NinvArgs a, const T* _
 }
 
 template <class T>
-constexpr size_t horner_smem() { return kSlotsH * 2 * sizeof(int32_t) + (size_t)kWarpsH * kColH * sizeof(T); }
-template <class T>
-constexpr size_t product_smem() { return kSlotsP * 2 * sizeof(int32_t) + (size_t)kEntP * sizeof(T); }
+constexpr size_t ninv_smem() { return kSlots * 2 * sizeof(int32_t) + (size_t)kEnt * sizeof(T); }
 
 int64_t global_slots(const NinvArgs& a) {
-    // the longest column may hold up to 2 max_col table entries (partner rows)
-    if (a.max_col <= kColH && 2 * a.max_col <= kEntP) return 0;
-    return (int64_t)table_mask(2 * a.max_col) + 1;
+    if (a.max_col <= kEnt) return 0;
+    return (int64_t)table_mask(a.max_col) + 1;
 }
 
 }  // namespace
 
 cudaError_t ninv_configure() {
     cudaError_t e;
-    e = cudaFuncSetAttribute(ninv_horner<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)horner_smem<double>());
+    e = cudaFuncSetAttribute(ninv_horner<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ninv_smem<double>());
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(ninv_horner<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)horner_smem<float>());
+    e = cudaFuncSetAttribute(ninv_horner<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ninv_smem<float>());
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(ninv_product<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)product_smem<double>());
+    e = cudaFuncSetAttribute(ninv_product<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ninv_smem<double>());
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(ninv_product<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)product_smem<float>());
+    return cudaFuncSetAttribute(ninv_product<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ninv_smem<float>());
 }
 
-static int ninv_grid(const NinvArgs& a) { return a.num_sms * 2; }
+static int ninv_grid(const NinvArgs& a) { return a.num_sms * 4; }
 
 size_t ninv_work_bytes(const NinvArgs& a, int prec) {
     size_t ts = prec == 0 ? sizeof(double) : sizeof(float);
@@ -323,7 +294,7 @@ size_t ninv_work_bytes(const NinvArgs& a, int prec) {
     b += (size_t)a.n * (2 * sizeof(double) + sizeof(int32_t)) + 3 * 256;
     b += sizeof(int32_t) * 64 + 256;                            // tickets
     int64_t slots = global_slots(a);
-    if (slots) b += (size_t)ninv_grid(a) * slots * (3 * sizeof(int32_t) + sizeof(double)) + 2 * 256;
+    if (slots) b += (size_t)ninv_grid(a) * slots * (2 * sizeof(int32_t) + sizeof(double)) + 2 * 256;
     return b + 4096;
 }
 
@@ -344,20 +315,28 @@ static cudaError_t ninv_run(const NinvArgs& a, void* work, double* N_out, cudaSt
     const int grid = ninv_grid(a);
     Scratch gs{nullptr, nullptr, global_slots(a)};
     if (gs.slots) {
-        gs.keys = reinterpret_cast<int32_t*>(take((size_t)grid * gs.slots * 3 * sizeof(int32_t)));
+        gs.keys = reinterpret_cast<int32_t*>(take((size_t)grid * gs.slots * 2 * sizeof(int32_t)));
         gs.acc = take((size_t)grid * gs.slots * sizeof(double));
     }
     cudaError_t e = cudaMemsetAsync(tickets, 0, sizeof(int32_t) * 64, st);
     if (e != cudaSuccess) return e;
+    trace_begin("ninv_dinv", st);
     ninv_dinv<<<a.num_sms * 4, 256, 0, st>>>(a.n, a.dpos, a.pstart, a.Dval, dr, dp, part, a.status);
+    trace_end(st);
+    trace_begin("ninv_init", st);
     ninv_init<T><<<a.num_sms * 4, 256, 0, st>>>(a.Wcp, W0, a.n);
+    trace_end(st);
     T* cur = W0;
     T* nxt = W1;
     for (int t = 1; t <= a.m; ++t) {
-        ninv_horner<T><<<grid, kThreadsH, horner_smem<T>(), st>>>(a, t, cur, nxt, tickets + t, gs);
+        trace_begin("ninv_horner", st);
+        ninv_horner<T><<<grid, kThreads, ninv_smem<T>(), st>>>(a, t, cur, nxt, tickets + t, gs);
+        trace_end(st);
         std::swap(cur, nxt);
     }
-    ninv_product<T><<<grid, kThreadsP, product_smem<T>(), st>>>(a, cur, dr, dp, part, N_out, tickets + 63, gs);
+    trace_begin("ninv_product", st);
+    ninv_product<T><<<grid, kThreads, ninv_smem<T>(), st>>>(a, cur, dr, dp, part, N_out, tickets + 63, gs);
+    trace_end(st);
     return cudaGetLastError();
 }
 

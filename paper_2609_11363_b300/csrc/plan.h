@@ -62,6 +62,7 @@ struct HostPlan {
 // Column j lists its rows grouped by the first power t that reaches them
 // (t = 0 is row j itself), each group sorted by row; grp[j*(m+2) + t] is the
 // start of group t inside column j (relative to Wcp[j]), grp[j*(m+2)+m+1] its end.
+// Bit 31 of a row entry is set when that row belongs to a 2x2 block of D.
 struct NinvPlan {
     int m = -1;
     int64_t nnzW = 0;
@@ -73,10 +74,11 @@ struct NinvPlan {
 
 // Returns an empty string on success, else the reason the pattern is invalid.
 // big_pairs: supernodes with at least this many pairs are processed by a whole CTA;
-// group: small supernodes per work item (one per warp).
+// group: small supernodes per work item (one per warp); levels with fewer than
+// thin_level supernodes give every supernode a whole CTA.
 std::string build_plan(int64_t n, const int64_t* L_rowptr, const int32_t* L_col,
                        const int8_t* pivot_start, int supernode_cap, int64_t big_pairs, int group,
-                       HostPlan& P);
+                       int64_t thin_level, HostPlan& P);
 std::string build_ninv_plan(const HostPlan& P, int m, NinvPlan& W);
 
 }  // namespace sinv

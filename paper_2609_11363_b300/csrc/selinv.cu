@@ -1,4 +1,4 @@
-// Supernodal selected inversion (Section 2.1, eqs. (2.4)-(2.5)) as one
+// Supernodal selected inversion (Section 2.1, Eqs. (4)-(5)) as one
 // persistent kernel.
 //
 // For a supernode J (consecutive pivot blocks [s0, s0+w)) with row set C below
@@ -28,7 +28,7 @@ namespace sinv {
 namespace {
 
 constexpr int kWarps = 8;          // warps per CTA
-constexpr int kCW = 384;           // per-warp shared capacity for c*w values (Lh, X, output positions)
+constexpr int kCW = 256;           // per-warp shared capacity for c*w values (Lh, X, output positions)
 constexpr int kWMax = 16;          // supernode width limit of this kernel
 constexpr int kBatch = 4;          // chunks of 32 pairs whose G loads are in flight together
 
@@ -81,9 +81,12 @@ struct Group {
     static __device__ __forceinline__ void sync() {
         if (kCta) __syncthreads(); else __syncwarp();
     }
+    // vote plus a barrier that orders memory among the group's threads
     static __device__ __forceinline__ bool any(bool p) {
         if (kCta) return __syncthreads_or(p) != 0;
-        return __any_sync(0xffffffffu, p);
+        const bool r = __any_sync(0xffffffffu, p);
+        __syncwarp();
+        return r;
     }
 };
 
@@ -295,8 +298,9 @@ __device__ bool process(const SelinvArgs& a, typename Form::G* Gw, int J, uint32
             break;
         }
     }
+    // the acquire loads above, followed by the group barrier inside any(), order
+    // every thread's reads of G after the producers' release stores
     if (Gr::any(!ok)) return false;
-    __threadfence();
 
     // ---- phase C ---------------------------------------------------------------------
     accumulate_pairs<Form>(pr, hik, hpos, Gw, lh, x, w, lane);
@@ -335,11 +339,10 @@ __device__ bool process(const SelinvArgs& a, typename Form::G* Gw, int J, uint32
         const int sp = a.JJs[I.ww_off + r * w + b];
         if (sp >= 0) Form::st(Gw + sp, Form::from_d(m - s));
     }
+    // the barrier orders every thread's writes before thread 0's release store,
+    // which publishes them (release is cumulative over the barrier)
     Gr::sync();
-    if (tid == 0) {
-        __threadfence();
-        st_release(a.done + J, epoch);
-    }
+    if (tid == 0) st_release(a.done + J, epoch);
     return true;
 }
 
@@ -384,11 +387,15 @@ __global__ void widen_to_double(const typename Form::G* __restrict__ src, double
 template <class Form>
 cudaError_t launch_form(const SelinvArgs& a, typename Form::G* Gw, double* G_out, cudaStream_t st, int grid) {
     size_t smem = sizeof(WarpSmem) * kWarps;
+    trace_begin("selinv_persistent", st);
     selinv_persistent<Form><<<grid, kWarps * 32, smem, st>>>(a, Gw);
+    trace_end(st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if ((void*)Gw != (void*)G_out) {
+        trace_begin("selinv_widen", st);
         widen_to_double<Form><<<a.num_sms * 8, 256, 0, st>>>(Gw, G_out, a.nnzS);
+        trace_end(st);
         e = cudaGetLastError();
     }
     return e;
@@ -397,7 +404,9 @@ cudaError_t launch_form(const SelinvArgs& a, typename Form::G* Gw, double* G_out
 }  // namespace
 
 cudaError_t selinv_prepare(uint32_t* epoch, int32_t* ticket, cudaStream_t st) {
+    trace_begin("selinv_prepare", st);
     prepare_kernel<<<1, 1, 0, st>>>(epoch, ticket);
+    trace_end(st);
     return cudaGetLastError();
 }
 

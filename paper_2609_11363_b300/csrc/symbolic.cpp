@@ -49,7 +49,7 @@ bool subset_except(const int32_t* a, int64_t na, const int32_t* b, int64_t nb, i
 }  // namespace
 
 std::string build_plan(int64_t n, const int64_t* Lrp, const int32_t* Lc, const int8_t* ps, int cap,
-                       int64_t big_pairs, int group, HostPlan& P) {
+                       int64_t big_pairs, int group, int64_t thin_level, HostPlan& P) {
     if (n < 0) return "negative n";
     if (n > INT32_MAX - 1) return "n does not fit int32 column indices";
     if (cap <= 0) cap = 16;
@@ -364,20 +364,26 @@ std::string build_plan(int64_t n, const int64_t* Lrp, const int32_t* Lc, const i
         if (P.sn[a].level != P.sn[b].level) return P.sn[a].level < P.sn[b].level;
         return P.sn[a].hit_cnt > P.sn[b].hit_cnt;
     });
-    // work items: a large supernode alone (whole CTA), else up to `group` consecutive ones
+    // work items: a large supernode alone (whole CTA), else up to `group` consecutive ones.
+    // Levels with fewer supernodes than thin_level sit on the critical path of the
+    // dependency chain: each of their supernodes gets a whole CTA to shorten it.
+    std::vector<int64_t> level_size(P.n_levels, 0);
+    for (int64_t s = 0; s < ns; ++s) level_size[P.sn[s].level]++;
     P.items.clear();
     for (int64_t t = 0; t < ns;) {
         const SnInfo& I = P.sn[P.order[t]];
         WorkItem it;
         it.first = (int32_t)t;
         it.pad = 0;
-        if (I.hit_cnt >= big_pairs) {
+        if (I.hit_cnt >= big_pairs || level_size[I.level] < thin_level) {
             it.count = 1;
             it.big = 1;
             ++t;
         } else {
             int64_t e = t;
-            while (e < ns && e - t < group && P.sn[P.order[e]].hit_cnt < big_pairs) ++e;
+            while (e < ns && e - t < group && P.sn[P.order[e]].hit_cnt < big_pairs &&
+                   level_size[P.sn[P.order[e]].level] >= thin_level)
+                ++e;
             it.count = (int32_t)(e - t);
             it.big = 0;
             t = e;
@@ -457,7 +463,9 @@ std::string build_ninv_plan(const HostPlan& P, int m, NinvPlan& W) {
             int t = 0;
             for (size_t e = 0; e < buf.size(); ++e) {
                 while (t <= buf[e].first) g[t++] = (int32_t)e;
-                W.Wr[base + e] = buf[e].second;
+                const int32_t r = buf[e].second;
+                const bool two = !P.pstart[r] || (r + 1 < n && !P.pstart[r + 1]);
+                W.Wr[base + e] = two ? (int32_t)((uint32_t)r | 0x80000000u) : r;
             }
             while (t <= m + 1) g[t++] = (int32_t)buf.size();
         }

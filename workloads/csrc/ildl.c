@@ -3,7 +3,7 @@
  * pivots, plus a solve with the resulting factors.
  *
  * This produces the INPUTS of the selected-inverse path (the paper takes the
- * factors of a block ILDL as given: Section 2, eq. (2.1) "A ~ L D L^T" with L
+ * factors of a block ILDL as given: Section 2, Eq. (1) "A ~ L D L^T" with L
  * block unit lower triangular and D block diagonal).  It computes nothing of
  * the selected inverse itself.
  *

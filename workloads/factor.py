@@ -1,7 +1,7 @@
 """Incomplete LDL^T factors (the inputs of the selected-inverse path).
 
 The paper builds every inverse from a block ILDL with drop tolerance tau
-(Section 2.1, eq. (2.1); Algorithm 1, step 2).  Its JANUS implementation is not
+(Section 2.1, Eq. (1); Algorithm 1, step 2).  Its JANUS implementation is not
 described, so the factorisation here is a stated stand-in:
 
 * symmetric scaling  A_hat = S A S,  S = diag(|a_ii|^{-1/2});
