@@ -118,6 +118,23 @@ sinv_status sinv_mix(sinv_handle h, const double *G_S, const double *N_S, double
 sinv_status sinv_lowrank_correct(sinv_handle h, int k, const double *V, const double *lambda,
                                  sinv_precision prec, double *X_S, void *stream);
 
+/* The FP32 form of sinv_lowrank_correct for callers that cannot allocate device
+ * memory -- for instance code that gets all of its device memory from an
+ * arena it owns, or that must not call cudaMalloc because it may synchronise
+ * the device.  It needs no handle and allocates nothing: the FP32 working copy
+ * of V and lambda lives in a 16 MiB array inside the library (reserved on
+ * every GPU that loads the library until the process exits).  The paper has
+ * no counterpart; this is a deployment variant of the correction above.
+ *   S_rowptr [n+1], S_col [|S_lo|]: the pattern S_lo on the device (for example
+ *   from sinv_get_pattern); V [n*k] row-major, lambda [k], X_S in/out: device.
+ *   Limit: n*k + k <= 4,194,304, else SINV_ERR_UNSUPPORTED (nothing is launched).
+ *   The first call on a device looks up the array's device address; make that
+ *   first call before any stream capture.  All calls on a device share the
+ *   array: calls that overlap on the GPU (other streams, other threads) race,
+ *   so order them on one stream.  Errors of the launch: SINV_ERR_CUDA. */
+sinv_status sinv_lowrank_correct_noalloc(int64_t n, const int64_t *S_rowptr, const int32_t *S_col, int k,
+                                         const double *V, const double *lambda, double *X_S, void *stream);
+
 /* Wait for the handle's queued work on `stream` and return the first device
  * error recorded since the last call (then clear it). */
 sinv_status sinv_sync_status(sinv_handle h, void *stream);

@@ -11,4 +11,6 @@ from .binding import (  # noqa: F401
     lib_path,
     load_library,
     PREC,
+    lowrank_correct_noalloc,
+    LOWRANK_NOALLOC_MAX,
 )

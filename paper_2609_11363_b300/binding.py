@@ -27,7 +27,7 @@ EXPORTS = [
     "sinv_symbolic", "sinv_get_pattern", "sinv_get_pattern_host", "sinv_selinv", "sinv_ninv", "sinv_mix",
     "sinv_lowrank_correct", "sinv_sync_status", "sinv_get_stats", "sinv_get_supernodes",
     "sinv_status_string", "sinv_last_error", "sinv_destroy", "sinv_debug_wait_timeout",
-    "sinv_trace_enable", "sinv_trace_read",
+    "sinv_trace_enable", "sinv_trace_read", "sinv_lowrank_correct_noalloc",
 ]
 
 
@@ -83,6 +83,7 @@ def load_library():
     lib.sinv_destroy.argtypes = [H]
     lib.sinv_destroy.restype = None
     lib.sinv_debug_wait_timeout.argtypes = [H, P]
+    lib.sinv_lowrank_correct_noalloc.argtypes = [I64, P, P, ctypes.c_int, P, P, P, P]
     lib.sinv_trace_enable.argtypes = [H, ctypes.c_int]
     lib.sinv_trace_read.argtypes = [H, ctypes.POINTER(_KTime), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                     ctypes.c_int]
@@ -118,6 +119,31 @@ def _stream_ptr(stream):
             return ctypes.c_void_p(0)  # host-only handles: the library rejects the call itself
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+LOWRANK_NOALLOC_MAX = 1 << 22  # n*k + k floats of the library's built-in working array
+
+
+def lowrank_correct_noalloc(S_rowptr, S_col, V, lam, X, stream=None):
+    """FP32 low-rank correction on S through the allocation-free entry point.
+
+    For callers that cannot allocate device memory: no handle, the working copy
+    lives in the library's fixed 16 MiB array.  S_rowptr (int64, n+1) and S_col
+    (int32) are the pattern on the device; V (n x k, float64), lam (k) and the
+    in/out X (float64) are CUDA tensors.  Raises SinvError(SINV_ERR_UNSUPPORTED)
+    when n*k + k exceeds LOWRANK_NOALLOC_MAX.
+    """
+    lib = load_library()
+    n = int(S_rowptr.numel()) - 1
+    k = int(lam.numel())
+    st = lib.sinv_lowrank_correct_noalloc(
+        n, _check_tensor(S_rowptr, "S_rowptr", n + 1, torch.int64), _check_tensor(S_col, "S_col", None, torch.int32),
+        k, _check_tensor(V, "V", n * k), _check_tensor(lam, "lambda", k), _check_tensor(X, "X_S", int(S_col.numel())),
+        _stream_ptr(stream))
+    if st != 0:
+        msg = "n*k + k = %d exceeds %d" % (n * k + k, LOWRANK_NOALLOC_MAX) if st == 7 else "launch failed"
+        raise SinvError(st, msg)
+    return X
 
 
 class Handle:

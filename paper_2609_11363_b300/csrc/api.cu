@@ -548,6 +548,16 @@ sinv_status sinv_debug_wait_timeout(sinv_handle h, void* stream) {
     return sinv_sync_status(h, stream);
 }
 
+sinv_status sinv_lowrank_correct_noalloc(int64_t n, const int64_t* S_rowptr, const int32_t* S_col, int k,
+                                         const double* V, const double* lambda, double* X_S, void* stream) {
+    if (n < 0 || k < 0) return SINV_ERR_INVALID_ARG;
+    if (n == 0 || k == 0) return SINV_OK;
+    if (n * (int64_t)k + k > kLowrankStaticFloats) return SINV_ERR_UNSUPPORTED;
+    if (!S_rowptr || !S_col || !V || !lambda || !X_S) return SINV_ERR_INVALID_ARG;
+    cudaError_t e = lowrank_noalloc_launch(n, S_rowptr, S_col, k, V, lambda, X_S, (cudaStream_t)stream);
+    return e == cudaSuccess ? SINV_OK : SINV_ERR_CUDA;
+}
+
 sinv_status sinv_trace_enable(sinv_handle h, int enable) {
     if (!h) return SINV_ERR_INVALID_ARG;
     if (!on_device(h)) return SINV_ERR_INVALID_ARG;

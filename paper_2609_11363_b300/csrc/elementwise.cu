@@ -1,5 +1,7 @@
 // Entry-wise work on S: Mix (Section 2.3) and the low-rank correction applied on
 // S as a sampled dense product (Section 2.5, Eq. (9)).
+#include <mutex>
+
 #include "device.cuh"
 #include "kernels.h"
 
@@ -111,6 +113,57 @@ cudaError_t lowrank_launch(int64_t n, const int64_t* Srp, const int32_t* Sc, int
         lowrank_kernel<float><<<grid, kLrWarps * 32, 0, st>>>(n, Srp, Sc, k, Vf, lf, X);
         trace_end(st);
     }
+    return cudaGetLastError();
+}
+
+// ---- the FP32 low-rank correction without any allocation --------------------------
+// Callers that cannot allocate device memory get the FP32 form with its working copy
+// of V and lambda in this file-scope array instead of a handle-owned buffer.  Every
+// GPU that loads the library keeps these 16 MiB until the process exits.  All calls
+// on a device share the array (each call overwrites the part it uses before reading
+// it), so calls that overlap on the GPU race with each other.
+static __device__ __align__(256) float g_lowrank_scratch[kLowrankStaticFloats];
+
+namespace {
+constexpr int kMaxDevices = 256;
+std::mutex g_scratch_mu;
+float* g_scratch_ptr[kMaxDevices] = {};
+}  // namespace
+
+// The array's device address for the current device, looked up once per device (the
+// first call on a device does this, so it must come before any stream capture).
+static cudaError_t lowrank_static_scratch(float** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_lowrank_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = reinterpret_cast<float*>(p);
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+cudaError_t lowrank_noalloc_launch(int64_t n, const int64_t* Srp, const int32_t* Sc, int k, const double* V,
+                                   const double* lambda, double* X, cudaStream_t st) {
+    if (n == 0 || k == 0) return cudaSuccess;
+    if (n * (int64_t)k + k > kLowrankStaticFloats) return cudaErrorInvalidValue;
+    float* Vf = nullptr;
+    cudaError_t e = lowrank_static_scratch(&Vf);
+    if (e != cudaSuccess) return e;
+    int dev = 0, num_sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    float* lf = Vf + n * (int64_t)k;
+    const int64_t blocks = (n + kLrWarps - 1) / kLrWarps;
+    const int grid = (int)std::min<int64_t>(blocks, (int64_t)num_sms * 16);
+    to_float<<<num_sms * 4, 256, 0, st>>>(V, Vf, n * (int64_t)k);
+    to_float<<<1, 256, 0, st>>>(lambda, lf, k);
+    lowrank_kernel<float><<<grid, kLrWarps * 32, 0, st>>>(n, Srp, Sc, k, Vf, lf, X);
     return cudaGetLastError();
 }
 

@@ -89,6 +89,12 @@ cudaError_t ninv_configure();
 size_t ninv_work_bytes(const NinvArgs& a, int prec);
 cudaError_t ninv_launch(const NinvArgs& a, int prec, void* work, double* N_out, cudaStream_t st);
 
+// FP32 low-rank correction with its working copy in a file-scope device array
+// (no allocation); n*k + k must not exceed kLowrankStaticFloats.
+constexpr int64_t kLowrankStaticFloats = int64_t(1) << 22;  // 4,194,304 floats = 16 MiB
+cudaError_t lowrank_noalloc_launch(int64_t n, const int64_t* Srp, const int32_t* Sc, int k, const double* V,
+                                   const double* lambda, double* X, cudaStream_t st);
+
 cudaError_t debug_wait_launch(uint32_t* flag, int32_t* status, int64_t limit, cudaStream_t st);
 
 }  // namespace sinv
