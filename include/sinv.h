@@ -145,6 +145,11 @@ typedef struct {
     int64_t max_c, hit_pairs, max_width;
     int64_t nnz_W;        /* pattern of the truncated series, 0 until sinv_ninv ran */
     int32_t ninv_m;       /* m of that pattern                                        */
+    int32_t pad;
+    int64_t horner_products;  /* E_kj W[r,k] products of the m Horner steps            */
+    int64_t product_stream;   /* entries of W streamed by the product on S             */
+    int64_t selinv_flops;     /* algorithmic flops of one SelInv                        */
+    int64_t selinv_bytes;     /* algorithmic bytes of one SelInv (S read once, L in, X out) */
 } sinv_stats;
 sinv_status sinv_get_stats(sinv_handle h, sinv_stats *out);
 

@@ -37,7 +37,7 @@ def _load():
     if _lib is None:
         lib = ctypes.CDLL(build_lib())
         P = ctypes.c_void_p
-        lib.oracle_selinv.argtypes = [ctypes.c_int64, P, P, P, P, P, P, P, P, P]
+        lib.oracle_selinv.argtypes = [ctypes.c_int64, P, P, P, P, P, P, P, P, P, ctypes.c_int64]
         lib.oracle_selinv.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -82,8 +82,12 @@ def _S_entries(Srp, Sc):
 # --------------------------------------------------------------------------
 # SelInv (Section 2.1)
 # --------------------------------------------------------------------------
-def selinv(n, L_rowptr, L_col, L_val, pivot_start, d_diag, d_off, S=None):
-    """Selected inverse on S by the scalar recurrence (C implementation)."""
+def selinv(n, L_rowptr, L_col, L_val, pivot_start, d_diag, d_off, S=None, stop_col=0):
+    """Selected inverse on S by the scalar recurrence (C implementation).
+
+    ``stop_col > 0`` runs only the pivot blocks starting at or after it (the last
+    part of the recurrence), for timing a bounded sample; other entries stay 0.
+    """
     lib = _load()
     if S is None:
         S = symbolic_S(n, L_rowptr, L_col, pivot_start)
@@ -96,7 +100,7 @@ def selinv(n, L_rowptr, L_col, L_val, pivot_start, d_diag, d_off, S=None):
     do = np.ascontiguousarray(d_off, dtype=np.float64)
     Srp = np.ascontiguousarray(Srp, dtype=np.int64); Sc = np.ascontiguousarray(Sc, dtype=np.int32)
     G = np.zeros(len(Sc))
-    rc = lib.oracle_selinv(n, _p(cp), _p(r), _p(v), _p(ps), _p(dd), _p(do), _p(Srp), _p(Sc), _p(G))
+    rc = lib.oracle_selinv(n, _p(cp), _p(r), _p(v), _p(ps), _p(dd), _p(do), _p(Srp), _p(Sc), _p(G), int(stop_col))
     if rc == -2:
         raise ZeroDivisionError("singular pivot block")
     if rc != 0:

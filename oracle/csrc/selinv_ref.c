@@ -45,10 +45,13 @@ static int cmp_i32(const void *a, const void *b) {
     return (x > y) - (x < y);
 }
 
-/* Returns 0 on success, -1 on allocation failure, -2 on a singular pivot block. */
+/* Returns 0 on success, -1 on allocation failure, -2 on a singular pivot block.
+ * Processes the pivot blocks from the last one down to the block that starts at
+ * or after stop_col (stop_col = 0: all of them); the entries of earlier blocks
+ * are left untouched.  A partial run times a bounded sample of the recurrence. */
 int oracle_selinv(int64_t n, const int64_t *Lcp, const int32_t *Lr, const double *Lv,
                   const int8_t *pivot_start, const double *d_diag, const double *d_off,
-                  const int64_t *Srp, const int32_t *Sc, double *G) {
+                  const int64_t *Srp, const int32_t *Sc, double *G, int64_t stop_col) {
     int32_t *U = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
     int64_t *mark = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
     double *Lu = (double *)malloc(2 * ((size_t)n + 1) * sizeof(double));
@@ -60,6 +63,7 @@ int oracle_selinv(int64_t n, const int64_t *Lcp, const int32_t *Lr, const double
     while (j >= 0) {
         /* pivot block P = {b} or {b, b+1} ending at j */
         int64_t b = pivot_start[j] ? j : j - 1;
+        if (b < stop_col) break;
         int w = (int)(j - b + 1);
         /* U = union of the column structures of P, rows below the block */
         int64_t u = 0;

@@ -50,7 +50,8 @@ class _KTime(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("n", "nnz_L", "nnz_S_lo", "n_blocks", "n_2x2", "n_supernodes",
                                               "n_levels", "max_c", "hit_pairs", "max_width", "nnz_W")] + [
-        ("ninv_m", ctypes.c_int32)]
+        ("ninv_m", ctypes.c_int32), ("pad", ctypes.c_int32), ("horner_products", ctypes.c_int64),
+        ("product_stream", ctypes.c_int64), ("selinv_flops", ctypes.c_int64), ("selinv_bytes", ctypes.c_int64)]
 
 
 def lib_path() -> str:

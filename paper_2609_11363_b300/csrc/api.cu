@@ -349,6 +349,11 @@ sinv_status sinv_get_stats(sinv_handle h, sinv_stats* s) {
     s->max_width = P.max_w;
     s->nnz_W = h->W.m >= 0 ? h->W.nnzW : 0;
     s->ninv_m = h->W.m;
+    s->pad = 0;
+    s->horner_products = h->W.m >= 0 ? h->W.horner_products : 0;
+    s->product_stream = h->W.m >= 0 ? h->W.product_stream : 0;
+    s->selinv_flops = P.selinv_flops;
+    s->selinv_bytes = P.selinv_bytes;
     return SINV_OK;
 }
 

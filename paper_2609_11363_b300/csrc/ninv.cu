@@ -36,7 +36,7 @@ namespace {
 constexpr int kWarps = 8;                     // warps per CTA (Horner step and product)
 constexpr int kThreads = kWarps * 32;
 constexpr int kSlots = 4096;                  // hash slots in shared memory
-constexpr int kEnt = 2730;                    // longest column kept in shared memory (load <= 2/3)
+constexpr int kEnt = 2730;                    // most table entries kept in shared memory (load <= 2/3)
 constexpr int kUnroll = 8;                    // column entries per lane with loads in flight
 constexpr int32_t kRowMask = 0x7FFFFFFF;      // row index bits of a pattern entry
 constexpr int32_t kTwoFlag = (int32_t)0x80000000u;  // set when the row belongs to a 2x2 block of D
@@ -55,11 +55,12 @@ __device__ __forceinline__ uint32_t table_insert(int32_t* keys, uint32_t mask, i
     }
 }
 
-__device__ __forceinline__ int32_t table_find(const int32_t* keys, const int32_t* vals, uint32_t mask, int32_t r) {
+// slot of r, or -1 when r is not in the table
+__device__ __forceinline__ int32_t table_find(const int32_t* keys, uint32_t mask, int32_t r) {
     uint32_t h = hash_row(r, mask);
     for (uint32_t probe = 0; probe <= mask; ++probe) {
         int32_t k = keys[h];
-        if (k == r) return vals[h];
+        if (k == r) return (int32_t)h;
         if (k == -1) return -1;
         h = (h + 1) & mask;
     }
@@ -109,8 +110,8 @@ template <>
 __device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return fmaf(a, b, c); }
 
 struct Scratch {
-    int32_t* keys;   // per CTA: slots int32 keys, slots int32 vals
-    void* acc;       // per CTA: accumulators / y values (slots entries of 8 bytes)
+    int32_t* keys;   // per CTA: slots int32 keys
+    void* acc;       // per CTA: slots accumulators / y values of 8 bytes
     int64_t slots;   // slots per CTA (0 when every column fits shared memory)
 };
 
@@ -118,9 +119,8 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) ninv_horner(NinvArgs a, int t, const T* __restrict__ Wp, T* __restrict__ Wn,
                                                          int32_t* ticket, Scratch gs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    int32_t* skeys = reinterpret_cast<int32_t*>(smem_raw);
-    int32_t* svals = skeys + kSlots;
-    T* sacc = reinterpret_cast<T*>(svals + kSlots);  // kEnt accumulators
+    T* sacc = reinterpret_cast<T*>(smem_raw);                    // kSlots accumulators, one per slot
+    int32_t* skeys = reinterpret_cast<int32_t*>(sacc + kSlots);  // kSlots keys
     __shared__ int32_t s_j;
     const int G = a.m + 2;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -134,17 +134,17 @@ __global__ void __launch_bounds__(kThreads) ninv_horner(NinvArgs a, int t, const
         const int32_t nj = a.grp[j * G + t + 1];  // rows of groups 0..t
         const bool small = nj <= kEnt;
         const uint32_t mask = small ? (uint32_t)(kSlots - 1) : table_mask(nj);
-        int32_t* keys = small ? skeys : gs.keys + (int64_t)blockIdx.x * 2 * gs.slots;
-        int32_t* vals = small ? svals : keys + gs.slots;
+        int32_t* keys = small ? skeys : gs.keys + (int64_t)blockIdx.x * gs.slots;
         T* acc = small ? sacc : reinterpret_cast<T*>(gs.acc) + (int64_t)blockIdx.x * gs.slots;
-        for (uint32_t s = threadIdx.x; s <= mask; s += kThreads) keys[s] = -1;
-        for (int32_t e = threadIdx.x; e < nj; e += kThreads) acc[e] = T(0);
+        for (uint32_t s = threadIdx.x; s <= mask; s += kThreads) {
+            keys[s] = -1;
+            acc[s] = T(0);
+        }
         __syncthreads();
-        for (int32_t e = threadIdx.x; e < nj; e += kThreads)
-            vals[table_insert(keys, mask, a.Wr[base + e] & kRowMask)] = e;
+        for (int32_t e = threadIdx.x; e < nj; e += kThreads) table_insert(keys, mask, a.Wr[base + e] & kRowMask);
         __syncthreads();
         // sum_k E_kj W_{t-1}[:, k]: warp wid takes k = wid, wid+8, ...; lanes over column k's
-        // groups 0..t-1, kUnroll entries per lane in flight; shared (or global) atomic adds
+        // groups 0..t-1, kUnroll entries per lane in flight; atomic adds into the row's slot
         for (int64_t q = a.Lcp[j] + wid; q < a.Lcp[j + 1]; q += kWarps) {
             const int32_t k = a.Lri[q];
             const T ekj = T(-a.Lval[a.Lcsr[q]]);
@@ -162,14 +162,17 @@ __global__ void __launch_bounds__(kThreads) ninv_horner(NinvArgs a, int t, const
 #pragma unroll
                 for (int u = 0; u < kUnroll; ++u) {
                     if (r[u] < 0) continue;
-                    const int32_t idx = table_find(keys, vals, mask, r[u]);
-                    if (idx >= 0) atomicAdd(acc + idx, ekj * v[u]);
+                    const int32_t h = table_find(keys, mask, r[u]);
+                    if (h >= 0) atomicAdd(acc + h, ekj * v[u]);
                     else set_status(a.status, ST_INTERNAL);  // row outside the pattern: never expected
                 }
             }
         }
         __syncthreads();
-        for (int32_t e = threadIdx.x; e < nj; e += kThreads) Wn[base + e] = acc[e] + (e == 0 ? T(1) : T(0));
+        for (int32_t e = threadIdx.x; e < nj; e += kThreads) {
+            const int32_t h = table_find(keys, mask, a.Wr[base + e] & kRowMask);
+            Wn[base + e] = acc[h] + (e == 0 ? T(1) : T(0));
+        }
         __syncthreads();
     }
 }
@@ -179,39 +182,46 @@ __global__ void __launch_bounds__(kThreads) ninv_product(NinvArgs a, const T* __
                                                          const double* __restrict__ dp, const int32_t* __restrict__ part,
                                                          double* __restrict__ N, int32_t* ticket, Scratch gs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    int32_t* skeys = reinterpret_cast<int32_t*>(smem_raw);
-    int32_t* svals = skeys + kSlots;
-    T* syv = reinterpret_cast<T*>(svals + kSlots);  // kEnt values of y = (D^{-1} W)[:, j]
-    __shared__ int32_t s_j;
+    T* syv = reinterpret_cast<T*>(smem_raw);                     // y = (D^{-1} W)[:, j], one per slot
+    int32_t* skeys = reinterpret_cast<int32_t*>(syv + kSlots);
+    __shared__ int32_t s_j, s_flagged;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (;;) {
-        if (threadIdx.x == 0) s_j = atomicAdd(ticket, 1);
+        if (threadIdx.x == 0) {
+            s_j = atomicAdd(ticket, 1);
+            s_flagged = 0;
+        }
         __syncthreads();
         const int64_t j = s_j;
         __syncthreads();
         if (j >= a.n) break;
         const int64_t base = a.Wcp[j];
         const int32_t nj = (int32_t)(a.Wcp[j + 1] - base);
-        const bool small = nj <= kEnt;
-        const uint32_t mask = small ? (uint32_t)(kSlots - 1) : table_mask(nj);
-        int32_t* keys = small ? skeys : gs.keys + (int64_t)blockIdx.x * 2 * gs.slots;
-        int32_t* vals = small ? svals : keys + gs.slots;
+        // the table holds the rows of column j and, for its rows in 2x2 blocks, their partners
+        int flagged = 0;
+        for (int32_t e = threadIdx.x; e < nj; e += kThreads) flagged += (a.Wr[base + e] & kTwoFlag) ? 1 : 0;
+        if (flagged) atomicAdd(&s_flagged, flagged);
+        __syncthreads();
+        const int32_t entries = nj + s_flagged;
+        const bool small = entries <= kEnt;
+        const uint32_t mask = small ? (uint32_t)(kSlots - 1) : table_mask(entries);
+        int32_t* keys = small ? skeys : gs.keys + (int64_t)blockIdx.x * gs.slots;
         T* yv = small ? syv : reinterpret_cast<T*>(gs.acc) + (int64_t)blockIdx.x * gs.slots;
-        for (uint32_t s = threadIdx.x; s <= mask; s += kThreads) keys[s] = -1;
+        for (uint32_t s = threadIdx.x; s <= mask; s += kThreads) {
+            keys[s] = -1;
+            yv[s] = T(0);
+        }
         __syncthreads();
-        for (int32_t e = threadIdx.x; e < nj; e += kThreads)
-            vals[table_insert(keys, mask, a.Wr[base + e] & kRowMask)] = e;
+        for (int32_t e = threadIdx.x; e < nj; e += kThreads) table_insert(keys, mask, a.Wr[base + e] & kRowMask);
         __syncthreads();
-        // y_r = (D^{-1})_rr W_rj + (D^{-1})_{r,p} W_pj for the rows r of column j (p: 2x2 partner)
+        // y_r = sum_{r'} (D^{-1})_{r r'} W_{r' j}: row r adds (D^{-1})_rr W_rj to its own slot and,
+        // in a 2x2 block with partner p, (D^{-1})_pr W_rj to p's slot (inserted if p is not in column j)
         for (int32_t e = threadIdx.x; e < nj; e += kThreads) {
             const int32_t rf = a.Wr[base + e];
             const int32_t r = rf & kRowMask;
-            double y = dr[r] * (double)W[base + e];
-            if (rf & kTwoFlag) {
-                const int32_t x = table_find(keys, vals, mask, part[r]);
-                if (x >= 0) y += dp[r] * (double)W[base + x];
-            }
-            yv[e] = T(y);
+            const double wv = (double)W[base + e];
+            atomicAdd(yv + table_find(keys, mask, r), T(dr[r] * wv));
+            if (rf & kTwoFlag) atomicAdd(yv + table_insert(keys, mask, part[r]), T(dp[r] * wv));
         }
         __syncthreads();
         // entries of S_lo in column j: the diagonal, the 2x2 partner row, struct(j)
@@ -235,26 +245,19 @@ __global__ void __launch_bounds__(kThreads) ninv_product(NinvArgs a, const T* __
             const int64_t ib = a.Wcp[i], ie = a.Wcp[i + 1];
             T s = T(0);
             for (int64_t f0 = ib; f0 < ie; f0 += 32 * kUnroll) {
-                int32_t rf[kUnroll];
+                int32_t r[kUnroll];
                 T wv[kUnroll];
 #pragma unroll
                 for (int u = 0; u < kUnroll; ++u) {
                     const int64_t f = f0 + u * 32 + lane;
-                    rf[u] = f < ie ? a.Wr[f] : -1;
+                    r[u] = f < ie ? (a.Wr[f] & kRowMask) : -1;
                     wv[u] = f < ie ? W[f] : T(0);
                 }
 #pragma unroll
                 for (int u = 0; u < kUnroll; ++u) {
-                    if (rf[u] == -1) continue;
-                    const int32_t r = rf[u] & kRowMask;
-                    const int32_t x = table_find(keys, vals, mask, r);
-                    if (x >= 0) {
-                        s = fma_t<T>(wv[u], yv[x], s);
-                    } else if (rf[u] & kTwoFlag) {
-                        // r is outside column j but its 2x2 partner may be inside: y_r = (D^{-1})_{r,p} W_pj
-                        const int32_t xp = table_find(keys, vals, mask, part[r]);
-                        if (xp >= 0) s = fma_t<T>(wv[u], T(dp[r] * (double)W[base + xp]), s);
-                    }
+                    if (r[u] < 0) continue;
+                    const int32_t h = table_find(keys, mask, r[u]);
+                    if (h >= 0) s = fma_t<T>(wv[u], yv[h], s);
                 }
             }
 #pragma unroll
@@ -266,11 +269,11 @@ __global__ void __launch_bounds__(kThreads) ninv_product(NinvArgs a, const T* __
 }
 
 template <class T>
-constexpr size_t ninv_smem() { return kSlots * 2 * sizeof(int32_t) + (size_t)kEnt * sizeof(T); }
+constexpr size_t ninv_smem() { return (size_t)kSlots * (sizeof(int32_t) + sizeof(T)); }
 
 int64_t global_slots(const NinvArgs& a) {
     if (a.max_col <= kEnt) return 0;
-    return (int64_t)table_mask(a.max_col) + 1;
+    return (int64_t)table_mask(2 * a.max_col) + 1;  // room for the partner rows too
 }
 
 }  // namespace
@@ -294,7 +297,7 @@ size_t ninv_work_bytes(const NinvArgs& a, int prec) {
     b += (size_t)a.n * (2 * sizeof(double) + sizeof(int32_t)) + 3 * 256;
     b += sizeof(int32_t) * 64 + 256;                            // tickets
     int64_t slots = global_slots(a);
-    if (slots) b += (size_t)ninv_grid(a) * slots * (2 * sizeof(int32_t) + sizeof(double)) + 2 * 256;
+    if (slots) b += (size_t)ninv_grid(a) * slots * (sizeof(int32_t) + sizeof(double)) + 2 * 256;
     return b + 4096;
 }
 
@@ -315,7 +318,7 @@ static cudaError_t ninv_run(const NinvArgs& a, void* work, double* N_out, cudaSt
     const int grid = ninv_grid(a);
     Scratch gs{nullptr, nullptr, global_slots(a)};
     if (gs.slots) {
-        gs.keys = reinterpret_cast<int32_t*>(take((size_t)grid * gs.slots * 2 * sizeof(int32_t)));
+        gs.keys = reinterpret_cast<int32_t*>(take((size_t)grid * gs.slots * sizeof(int32_t)));
         gs.acc = take((size_t)grid * gs.slots * sizeof(double));
     }
     cudaError_t e = cudaMemsetAsync(tickets, 0, sizeof(int32_t) * 64, st);

@@ -56,6 +56,9 @@ struct HostPlan {
     std::vector<int32_t> hrow;       // per supernode c+1 row starts
     std::vector<WorkItem> items;
     int64_t n_levels = 0, max_c = 0, max_w = 0, max_cw = 0, hit_pairs = 0;
+    // algorithmic work of one SelInv: 2 w flops per pair of C x C in S, 2 c w^2 for
+    // the diagonal block; bytes: each entry of S in C x C once (8 B) and L_CJ in, X out
+    int64_t selinv_flops = 0, selinv_bytes = 0;
 };
 
 // Neumann-series pattern P_W = pattern(sum_{t<=m} E^t), stored by columns.
@@ -70,6 +73,10 @@ struct NinvPlan {
     std::vector<int32_t> Wr;
     std::vector<int32_t> grp;
     int64_t max_col = 0;
+    // algorithmic work: products E_kj W_{t-1}[r,k] of all m Horner steps, and the
+    // entries of W streamed by the product on S (sum over (i,j) in S_lo of |col i|)
+    int64_t horner_products = 0;
+    int64_t product_stream = 0;
 };
 
 // Returns an empty string on success, else the reason the pattern is invalid.

@@ -318,6 +318,11 @@ std::string build_plan(int64_t n, const int64_t* Lrp, const int32_t* Lc, const i
         if (hits[s] > INT32_MAX) return "a supernode has >= 2^31 pairs: unsupported";
     }
     P.hit_pairs = hoff;
+    for (int64_t s = 0; s < ns; ++s) {
+        const SnInfo& I = P.sn[s];
+        P.selinv_flops += 2 * I.w * hits[s] + 2 * (int64_t)I.c * I.w * I.w;
+        P.selinv_bytes += 8 * ((hits[s] + I.c) / 2) + 16 * (int64_t)I.c * I.w;
+    }
     P.hit_ik.resize(hoff);
     P.hit_pos.resize(hoff);
     P.hrow.resize(roff);
@@ -471,6 +476,19 @@ std::string build_ninv_plan(const HostPlan& P, int m, NinvPlan& W) {
         }
     });
     for (int64_t j = 0; j < n; ++j) W.max_col = std::max<int64_t>(W.max_col, W.Wcp[j + 1] - W.Wcp[j]);
+    // work counts: step t reads groups 0..t-1 of every k in struct(j)
+    const int G = m + 2;
+    for (int64_t j = 0; j < n; ++j) {
+        for (int64_t q = Lcp[j]; q < Lcp[j + 1]; ++q) {
+            const int64_t k = Lri[q];
+            for (int t = 1; t <= m; ++t) W.horner_products += W.grp[(size_t)k * G + t];
+        }
+        // column j of S_lo: j, its 2x2 partner, struct(j); each streams column i of W
+        const bool two_first = P.pstart[j] && j + 1 < n && !P.pstart[j + 1];
+        W.product_stream += W.Wcp[j + 1] - W.Wcp[j];
+        if (two_first) W.product_stream += W.Wcp[j + 2] - W.Wcp[j + 1];
+        for (int64_t q = Lcp[j]; q < Lcp[j + 1]; ++q) W.product_stream += W.Wcp[Lri[q] + 1] - W.Wcp[Lri[q]];
+    }
     return "";
 }
 
