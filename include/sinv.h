@@ -82,6 +82,24 @@ sinv_status sinv_symbolic(int64_t n, const int64_t *L_rowptr, const int32_t *L_c
                           const int8_t *pivot_start, const sinv_symbolic_opts *opts,
                           sinv_handle *out);
 
+/* Batched analysis: nmat matrices (sizes n[b], each with its own L pattern and
+ * pivot layout, HOST arrays) analysed as one block-diagonal matrix.  Every numeric
+ * call then processes all matrices together: one persistent SelInv launch runs the
+ * supernodes of all matrices in one level-major schedule (matrices of uneven size
+ * fill each other's idle levels), and each NInv step is one launch over all
+ * columns.  Value arrays are the concatenations of the per-matrix arrays in matrix
+ * order (L_val, D_val, and every array on S); sinv_batch_layout gives the offsets.
+ * An entry of matrix b must lie inside its own block (SINV_ERR_PATTERN otherwise).
+ * This is the batching of many independent problems; the paper solves one matrix
+ * at a time. */
+sinv_status sinv_batch_symbolic(int32_t nmat, const int64_t *n, const int64_t *const *L_rowptr,
+                                const int32_t *const *L_col, const int8_t *const *pivot_start,
+                                const sinv_symbolic_opts *opts, sinv_handle *out);
+/* nmat (0 for a handle from sinv_symbolic) and, for arrays that are not NULL,
+ * nmat+1 offsets of each matrix's rows, L entries, packed D values and S_lo entries. */
+sinv_status sinv_batch_layout(sinv_handle h, int32_t *nmat, int64_t *n_off, int64_t *L_off, int64_t *D_off,
+                              int64_t *S_off);
+
 /* S_lo on the device (handle-owned, valid until sinv_destroy) and its size. */
 sinv_status sinv_get_pattern(sinv_handle h, const int64_t **S_rowptr, const int32_t **S_col,
                              int64_t *nnzS_lo);

@@ -28,6 +28,7 @@ EXPORTS = [
     "sinv_lowrank_correct", "sinv_sync_status", "sinv_get_stats", "sinv_get_supernodes",
     "sinv_status_string", "sinv_last_error", "sinv_destroy", "sinv_debug_wait_timeout",
     "sinv_trace_enable", "sinv_trace_read", "sinv_lowrank_correct_noalloc",
+    "sinv_batch_symbolic", "sinv_batch_layout",
 ]
 
 
@@ -84,6 +85,8 @@ def load_library():
     lib.sinv_destroy.argtypes = [H]
     lib.sinv_destroy.restype = None
     lib.sinv_debug_wait_timeout.argtypes = [H, P]
+    lib.sinv_batch_symbolic.argtypes = [ctypes.c_int32, P, P, P, P, ctypes.POINTER(_Opts), ctypes.POINTER(H)]
+    lib.sinv_batch_layout.argtypes = [H, ctypes.POINTER(ctypes.c_int32), P, P, P, P]
     lib.sinv_lowrank_correct_noalloc.argtypes = [I64, P, P, ctypes.c_int, P, P, P, P]
     lib.sinv_trace_enable.argtypes = [H, ctypes.c_int]
     lib.sinv_trace_read.argtypes = [H, ctypes.POINTER(_KTime), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -154,19 +157,34 @@ class Handle:
     host arrays describing strictly lower CSR L and the 1x1/2x2 pivot layout.
     """
 
-    def __init__(self, n, L_rowptr, L_col, pivot_start, supernode_cap=16, device=0, wait_limit=0, big_pairs=0):
+    def __init__(self, n, L_rowptr, L_col, pivot_start, supernode_cap=16, device=0, wait_limit=0, big_pairs=0,
+                 _batch=None):
         self._lib = load_library()
         self._h = ctypes.c_void_p()
-        self.n = int(n)
-        rp = np.ascontiguousarray(L_rowptr, dtype=np.int64)
-        col = np.ascontiguousarray(L_col, dtype=np.int32)
-        ps = np.ascontiguousarray(pivot_start, dtype=np.int8)
-        if rp.shape != (self.n + 1,) or ps.shape != (self.n,):
-            raise ValueError("L_rowptr must have n+1 and pivot_start n entries")
         opts = _Opts(int(supernode_cap), int(device), int(wait_limit), int(big_pairs))
         self.device = torch.device("cuda", int(device)) if int(device) >= 0 else None
-        st = self._lib.sinv_symbolic(self.n, _np_ptr(rp), _np_ptr(col), _np_ptr(ps), ctypes.byref(opts),
-                                     ctypes.byref(self._h))
+        if _batch is None:
+            self.n = int(n)
+            rp = np.ascontiguousarray(L_rowptr, dtype=np.int64)
+            col = np.ascontiguousarray(L_col, dtype=np.int32)
+            ps = np.ascontiguousarray(pivot_start, dtype=np.int8)
+            if rp.shape != (self.n + 1,) or ps.shape != (self.n,):
+                raise ValueError("L_rowptr must have n+1 and pivot_start n entries")
+            st = self._lib.sinv_symbolic(self.n, _np_ptr(rp), _np_ptr(col), _np_ptr(ps), ctypes.byref(opts),
+                                         ctypes.byref(self._h))
+        else:
+            ns, rps, cols, pss = _batch
+            nmat = len(ns)
+            keep = [np.ascontiguousarray(x, dtype=dt) for xs, dt in ((rps, np.int64), (cols, np.int32), (pss, np.int8))
+                    for x in xs]
+            rps_a, cols_a, pss_a = keep[:nmat], keep[nmat:2 * nmat], keep[2 * nmat:]
+            n_arr = np.ascontiguousarray(ns, dtype=np.int64)
+            arr = lambda xs: (ctypes.c_void_p * max(nmat, 1))(*[x.ctypes.data for x in xs])  # noqa: E731
+            prp, pcol, pps = arr(rps_a), arr(cols_a), arr(pss_a)
+            self.n = int(n_arr.sum())
+            st = self._lib.sinv_batch_symbolic(nmat, _np_ptr(n_arr), ctypes.cast(prp, ctypes.c_void_p),
+                                               ctypes.cast(pcol, ctypes.c_void_p), ctypes.cast(pps, ctypes.c_void_p),
+                                               ctypes.byref(opts), ctypes.byref(self._h))
         if st != 0:
             msg = self.last_error()
             self.close()
@@ -175,6 +193,28 @@ class Handle:
         self.nnz_S = s["nnz_S_lo"]
         self.nnz_L = s["nnz_L"]
         self.nD = self.n + s["n_2x2"]
+
+    @classmethod
+    def batch(cls, factors, **kw):
+        """One handle over several matrices (block-diagonal concatenation).
+
+        ``factors``: sequence of objects with n, L_rowptr, L_col, pivot_start.
+        Value arrays are concatenated in matrix order; ``layout()`` gives the offsets.
+        """
+        fs = list(factors)
+        return cls(None, None, None, None, _batch=([f.n for f in fs], [f.L_rowptr for f in fs],
+                                                   [f.L_col for f in fs], [f.pivot_start for f in fs]), **kw)
+
+    def layout(self):
+        """{'n', 'L', 'D', 'S'}: nmat+1 offsets each (empty for a single-matrix handle)."""
+        nmat = ctypes.c_int32()
+        self._check(self._lib.sinv_batch_layout(self._h, ctypes.byref(nmat), None, None, None, None))
+        k = nmat.value
+        if k == 0:
+            return {}
+        arrs = [np.zeros(k + 1, dtype=np.int64) for _ in range(4)]
+        self._check(self._lib.sinv_batch_layout(self._h, ctypes.byref(nmat), *[_np_ptr(a) for a in arrs]))
+        return dict(zip(("n", "L", "D", "S"), arrs))
 
     # -- helpers -----------------------------------------------------------
     def last_error(self) -> str:

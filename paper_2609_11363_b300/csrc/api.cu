@@ -127,6 +127,8 @@ struct sinv_handle_s {
     int grid = 0;
     // NInv pattern (built by the first sinv_ninv for a given m)
     NinvPlan W;
+    // batch layout (block-diagonal concatenation of several matrices), nmat+1 offsets each
+    std::vector<int64_t> b_n_off, b_L_off, b_D_off, b_S_off;
     int64_t* dWcp = nullptr;
     int32_t* dWr = nullptr;
     int32_t* dgrp = nullptr;
@@ -316,6 +318,74 @@ sinv_status sinv_symbolic(int64_t n, const int64_t* L_rowptr, const int32_t* L_c
         return cuda_fail(h, e, "symbolic upload");
     }
     *out = h;
+    return SINV_OK;
+}
+
+sinv_status sinv_batch_symbolic(int32_t nmat, const int64_t* n, const int64_t* const* L_rowptr,
+                                const int32_t* const* L_col, const int8_t* const* pivot_start,
+                                const sinv_symbolic_opts* opts, sinv_handle* out) {
+    if (!out || nmat < 0 || (nmat > 0 && (!n || !L_rowptr || !L_col || !pivot_start))) return SINV_ERR_INVALID_ARG;
+    *out = nullptr;
+    std::vector<int64_t> n_off(nmat + 1, 0), L_off(nmat + 1, 0), D_off(nmat + 1, 0);
+    for (int32_t b = 0; b < nmat; ++b) {
+        if (n[b] < 0 || (n[b] > 0 && (!L_rowptr[b] || !pivot_start[b]))) return SINV_ERR_INVALID_ARG;
+        const int64_t nb = n[b];
+        const int64_t nnzb = nb > 0 ? L_rowptr[b][nb] : 0;
+        if (nnzb > 0 && !L_col[b]) return SINV_ERR_INVALID_ARG;
+        n_off[b + 1] = n_off[b] + nb;
+        L_off[b + 1] = L_off[b] + nnzb;
+        int64_t n2 = 0;
+        for (int64_t j = 1; j < nb; ++j) n2 += pivot_start[b][j] == 0;
+        D_off[b + 1] = D_off[b] + nb + n2;
+    }
+    const int64_t N = n_off[nmat], NNZ = L_off[nmat];
+    std::vector<int64_t> rp;
+    std::vector<int32_t> col;
+    std::vector<int8_t> ps;
+    try {
+        rp.assign(N + 1, 0);
+        col.resize(NNZ);
+        ps.resize(N);
+    } catch (const std::bad_alloc&) {
+        return SINV_ERR_OOM;
+    }
+    for (int32_t b = 0; b < nmat; ++b) {
+        const int64_t nb = n[b], r0 = n_off[b], q0 = L_off[b];
+        for (int64_t i = 0; i < nb; ++i) {
+            const int64_t a = L_rowptr[b][i], e = L_rowptr[b][i + 1];
+            if (a < 0 || e < a || e > L_rowptr[b][nb]) return SINV_ERR_PATTERN;
+            for (int64_t q = a; q < e; ++q) {
+                const int32_t c = L_col[b][q];
+                // checked per matrix: an entry must stay inside its own block
+                if (c < 0 || c >= i) return SINV_ERR_PATTERN;
+                col[q0 + q] = (int32_t)(c + r0);
+            }
+            rp[r0 + i + 1] = q0 + e;
+        }
+        if (nb > 0 && (L_rowptr[b][0] != 0 || pivot_start[b][0] != 1)) return SINV_ERR_PATTERN;
+        for (int64_t j = 0; j < nb; ++j) ps[r0 + j] = pivot_start[b][j];
+    }
+    sinv_status st = sinv_symbolic(N, rp.data(), col.data(), ps.data(), opts, out);
+    if (*out) {
+        (*out)->b_n_off = n_off;
+        (*out)->b_L_off = L_off;
+        (*out)->b_D_off = D_off;
+        (*out)->b_S_off.assign(nmat + 1, 0);
+        for (int32_t b = 0; b <= nmat; ++b) (*out)->b_S_off[b] = (*out)->P.Srp.empty() ? 0 : (*out)->P.Srp[n_off[b]];
+    }
+    return st;
+}
+
+sinv_status sinv_batch_layout(sinv_handle h, int32_t* nmat, int64_t* n_off, int64_t* L_off, int64_t* D_off,
+                              int64_t* S_off) {
+    if (!h || !nmat) return SINV_ERR_INVALID_ARG;
+    const int32_t nb = h->b_n_off.empty() ? 0 : (int32_t)h->b_n_off.size() - 1;
+    *nmat = nb;
+    if (nb == 0) return SINV_OK;
+    int64_t* dst[4] = {n_off, L_off, D_off, S_off};
+    const std::vector<int64_t>* src[4] = {&h->b_n_off, &h->b_L_off, &h->b_D_off, &h->b_S_off};
+    for (int t = 0; t < 4; ++t)
+        if (dst[t]) memcpy(dst[t], src[t]->data(), (nb + 1) * sizeof(int64_t));
     return SINV_OK;
 }
 

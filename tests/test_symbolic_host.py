@@ -137,3 +137,32 @@ def test_status_strings(lib):
         s = lib.sinv_status_string(code)
         assert s and s != b"unknown status"
     assert lib.sinv_status_string(99) == b"unknown status"
+
+
+def test_batch_rejects_cross_block_entries():
+    from paper_2609_11363_b300 import Handle, SinvError
+    from workloads.configs import random_factors
+    fs = [random_factors(50, 0.1, 0.0, 1), random_factors(60, 0.1, 0.0, 2)]
+    bad = random_factors(60, 0.1, 0.0, 2)
+    bad.L_col = bad.L_col.copy()
+    bad.L_col[-1] = bad.L_rowptr.shape[0]  # beyond its own row
+    with pytest.raises(SinvError) as ei:
+        Handle.batch([fs[0], bad], device=-1)
+    assert ei.value.name == "SINV_ERR_PATTERN"
+
+
+def test_batch_layout_host(lib):
+    from paper_2609_11363_b300 import Handle
+    from workloads.configs import random_factors
+    fs = [lap2d_32().factors, random_factors(300, 0.05, 0.2, 3), plant_2x2(lap2d_32().factors, 0.2, 5)]
+    h = Handle.batch(fs, device=-1)
+    lay = h.layout()
+    rp, col = h.pattern_host()
+    assert list(np.diff(lay["n"])) == [f.n for f in fs]
+    assert list(np.diff(lay["L"])) == [f.nnz_L for f in fs]
+    assert list(np.diff(lay["D"])) == [len(f.D_packed) for f in fs]
+    for b, f in enumerate(fs):
+        S = oracle.symbolic_S(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+        s0, r0 = lay["S"][b], lay["n"][b]
+        assert np.array_equal(col[s0:lay["S"][b + 1]] - r0, S[1])
+        assert np.array_equal(rp[r0:r0 + f.n + 1] - s0, S[0])
