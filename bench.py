@@ -42,6 +42,10 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
     p.add_argument("--size", type=int, default=64)
+    p.add_argument("--workload", default="diff3d", choices=["diff3d", "batch9pt", "learned"],
+                   help="diff3d: the 64^3 step (default); batch9pt: 256 matrices in one graph-captured launch; "
+                        "learned: the trained NInv->SelInv correction on 128^3")
+    p.add_argument("--batch", type=int, default=256, help="matrices of the batch9pt workload")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -351,6 +355,13 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group(backend="nccl" if args.impl == "ours" else "gloo")
+    if args.workload != "diff3d" and args.impl == "ours":
+        run_extra(args, rank, world)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+        return
     if args.impl == "reference":
         if rank == 0:
             run_reference(args, world)
@@ -397,6 +408,162 @@ def main():
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+
+
+def _gen_batch_member(seed):
+    from workloads.configs import batch9pt_member
+    return batch9pt_member(seed).factors
+
+
+def run_extra(args, rank, world):
+    """The other hot-path rows, one JSON line each (not the default benchmark line).
+
+    batch9pt: 256 random-weight 9-point matrices (n uniform in [2048, 65536], seeds
+    3000+) in one batched handle; the autotuner picks the SelInv schedule; one step
+    = SelInv + NInv (m = 3) in FP32 for all matrices, replayed from a CUDA graph.
+    learned: the NInv -> SelInv correction network trained on 3D diffusion 48^3
+    (seeds 4000+) and applied to 128^3 (seed 4999); one step = NInv stack (m = 3)
+    + features + network, compared with SelInv FP64 on the same matrix.
+    """
+    import multiprocessing as mp
+
+    import torch
+    from paper_2609_11363_b300 import Handle
+    from workloads.configs import diff3d
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    peaks, peak_kind = load_peaks()
+    if args.workload == "batch9pt":
+        from paper_2609_11363_b300.autotune import tune_selinv
+        t0 = time.time()
+        with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+            fs = pool.map(_gen_batch_member, [3000 + i for i in range(args.batch)])
+        t_gen = time.time() - t0
+        torch.cuda.set_device(dev)
+        Lv = torch.as_tensor(np.concatenate([f.L_val for f in fs]), device=dev)
+        Dv = torch.as_tensor(np.concatenate([f.D_packed for f in fs]), device=dev)
+        t0 = time.time()
+        h, best, table = tune_selinv(fs, Lv, Dv, prec="fp32", caps=(1, 4), bigs=(512, 2048), device=dev.index)
+        t_tune = time.time() - t0
+        G = torch.empty(h.nnz_S, dtype=torch.float64, device=dev)
+        N = torch.empty_like(G)
+
+        def step():
+            h.selinv(Lv, Dv, "fp32", out=G)
+            h.ninv(Lv, Dv, 3, "fp32", out=N)
+
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            step()
+            step()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        for _ in range(args.warmup):
+            graph.replay()
+        torch.cuda.synchronize()
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        clocks = ClockSampler(dev.index)
+        clocks.start()
+        ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            graph.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        clk = clocks.stop()
+        h.sync_status()
+        nS = 2 * h.nnz_S - h.n
+        total = float(np.sum(ms))
+        st = h.stats()
+        line = {"metric": "selected-inverse entries/s on S, batched (SelInv + NInv m=3, FP32 accumulation)",
+                "value": world * nS * args.steps / (total / 1e3), "unit": "entries/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": "batch9pt: %d 2D 9-point random-weight Laplacians, n ~ U[2048, 65536], "
+                                       "ILDL tau=1e-2, one CUDA graph per step" % args.batch,
+                           "matrices": len(fs), "n_total": h.n, "S_entries": nS, "levels": st["n_levels"],
+                           "autotuned": best, "autotune_table_ms": [list(r[:3]) for r in table],
+                           "autotune_s": t_tune, "input_gen_s": t_gen, "l2": "flushed between timed steps"},
+                "clocks": clk, "gpu_launches": None}
+        if rank == 0:
+            print(json.dumps(line))
+        return
+    # learned correction
+    from paper_2609_11363_b300.learned import LearnedCorrection
+    torch.cuda.set_device(dev)
+    t0 = time.time()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        train_f = pool.map(_gen_diff_spd48, [4000 + i for i in range(64)])
+    test_w = diff3d(args.size if args.size != 64 else 128, shifted=False, m=3, seed=4999)
+    t_gen = time.time() - t0
+    lc = LearnedCorrection(m=3, seed=1, batch=16384, device=dev.index)
+    sets = []
+    for f in train_f:
+        h = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start, device=dev.index)
+        d = lc.prepare(h, torch.as_tensor(f.L_val, device=dev), torch.as_tensor(f.D_packed, device=dev))
+        sets.append({"X": d["X"], "y": d["y"]})  # keep only what training needs
+        del d
+        h.close()
+    fit = lc.fit(sets, epochs=2, lr=2e-3)
+    del sets
+    f = test_w.factors
+    h = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start, device=dev.index)
+    Lv = torch.as_tensor(f.L_val, device=dev)
+    Dv = torch.as_tensor(f.D_packed, device=dev)
+    d = lc.prepare(h, Lv, Dv)
+    ev = lc.evaluate(d)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        out = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return float(np.median(out))
+
+    def learned_step():
+        Nst = h.ninv_stack(Lv, Dv, 3, "fp64")
+        X, sc = h.mlp_features(Nst, 3, Lv, Dv)
+        lc.mlp.predict(X, sc, Nst[3].contiguous())
+
+    ms_learned = timed(learned_step, args.steps)
+    ms_selinv = timed(lambda: h.selinv(Lv, Dv, "fp64"), args.steps)
+    h.sync_status()
+    nS = 2 * h.nnz_S - h.n
+    line = {"metric": "selected-inverse entries/s on S, learned NInv->SelInv correction (NInv m=3 + BF16 MLP)",
+            "value": nS / (ms_learned / 1e3), "unit": "entries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_learned, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16+f64", "data": "synthetic",
+            "config": {"workload": "learned: 3-layer width-64 BF16 MLP trained on 64 seeds of 3D 7-point "
+                                   "log-normal diffusion 48^3, applied to %d^3 (n=%d), tau=1e-3, m=3" % (
+                                       round(f.n ** (1 / 3)), f.n),
+                       "train_entries": fit["entries"], "train_steps": fit["steps"], "train_s": fit["seconds"],
+                       "err_vs_selinv_ninv": ev["err_ninv"], "err_vs_selinv_learned": ev["err_learned"],
+                       "keep_correction": LearnedCorrection.choose([ev]), "selinv_fp64_ms": ms_selinv,
+                       "input_gen_s": t_gen},
+            "gpu_launches": None}
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def _gen_diff_spd48(seed):
+    from workloads.configs import diff3d
+    return diff3d(48, shifted=False, m=3, seed=seed).factors
 
 
 def run_reference(args, world):

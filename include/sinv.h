@@ -119,10 +119,17 @@ sinv_status sinv_selinv(sinv_handle h, const double *L_val, const double *D_val,
 
 /* NInv on S (Section 2.2, Eqs. (6) and (8)): W = sum_{t=0}^{m} E^t with
  * L = I - E, by m Horner steps W <- I + E W on the fixed pattern of the
- * truncated series, then N = W^T D^{-1} W evaluated on S only.  0 <= m <= 60.
- *   L_val, D_val, N_S [|S_lo|]: device.  m > 60: SINV_ERR_UNSUPPORTED. */
+ * truncated series, then N = W^T D^{-1} W evaluated on S only.  0 <= m <= 30.
+ *   L_val, D_val, N_S [|S_lo|]: device.  m > 30: SINV_ERR_UNSUPPORTED. */
 sinv_status sinv_ninv(sinv_handle h, const double *L_val, const double *D_val, int m,
                       sinv_precision prec, double *N_S, void *stream);
+
+/* NInv on S for every truncation t = 0..m of the series at once (Eq. (6) cut after
+ * t terms, then Eq. (8)): N_stack[t * |S_lo| + e] (device, (m+1) x |S_lo| doubles).
+ * The last slice equals sinv_ninv(m); t = 0 gives D^{-1} on S.  The per-order
+ * differences are inputs of the learned correction. */
+sinv_status sinv_ninv_stack(sinv_handle h, const double *L_val, const double *D_val, int m,
+                            sinv_precision prec, double *N_stack, void *stream);
 
 /* Mix (Section 2.3): M_ij = G_ij where |G_ij| > eps, else N_ij, on S.
  *   G_S, N_S, M_S [|S_lo|]: device (M_S may alias G_S or N_S). */
@@ -152,6 +159,43 @@ sinv_status sinv_lowrank_correct(sinv_handle h, int k, const double *V, const do
  *   so order them on one stream.  Errors of the launch: SINV_ERR_CUDA. */
 sinv_status sinv_lowrank_correct_noalloc(int64_t n, const int64_t *S_rowptr, const int32_t *S_col, int k,
                                          const double *V, const double *lambda, double *X_S, void *stream);
+
+/* Learned correction from NInv towards SelInv (not in the paper: a proposed
+ * addition).  A ReLU network 16 -> 64 -> 64 -> 1 maps features of an entry (i, j)
+ * of S to a correction: N^_ij = N_ij + s_ij f(x_ij), s_ij = sqrt|N_ii N_jj|.  It is
+ * trained on pairs the method itself produces (target (SelInv_ij - N_ij) / s_ij),
+ * with BF16 weights and features, FP32 sums and Adam, by the library's own
+ * forward, backward and optimiser kernels.  SelInv stays the judge: callers keep
+ * the correction only where it lowers the error on held-out matrices.
+ * Parameter vector (FP32, sinv_mlp_param_count() entries): W1[16x64], b1[64],
+ * W2[64x64], b2[64], W3[64], b3. */
+typedef struct sinv_mlp_s *sinv_mlp;
+int32_t sinv_mlp_param_count(void);
+/* Network on `device` with seeded He-uniform weights; max_batch bounds the
+ * mini-batch of sinv_mlp_grad / sinv_mlp_train_step. */
+sinv_status sinv_mlp_create(int32_t device, uint64_t seed, int64_t max_batch, sinv_mlp *out);
+void sinv_mlp_destroy(sinv_mlp m);
+/* Host copies of the FP32 master weights; set also resets the Adam state. */
+sinv_status sinv_mlp_get_params(sinv_mlp m, float *theta);
+sinv_status sinv_mlp_set_params(sinv_mlp m, const float *theta);
+/* Features of every S_lo entry from the NInv stack of sinv_ninv_stack (m <= 9):
+ * X [|S_lo| x 16] BF16, scale [|S_lo|] FP32 (s_ij); all device. */
+sinv_status sinv_mlp_features(sinv_handle h, const double *N_stack, int m, const double *L_val,
+                              const double *D_val, void *X, float *scale, void *stream);
+/* y[e] = (G[e] - N[e]) / scale[e] for count entries (device). */
+sinv_status sinv_mlp_targets(sinv_mlp m, int64_t count, const double *G, const double *N, const float *scale,
+                             float *y, void *stream);
+/* Gradient of the mean squared error over the entries idx[0..count) (idx may be
+ * NULL: entries 0..count-1) into grad [param_count] and the loss into *loss
+ * (both device; grad may be NULL to keep it inside). */
+sinv_status sinv_mlp_grad(sinv_mlp m, const void *X, const float *y, const int64_t *idx, int64_t count,
+                          float *grad, float *loss, void *stream);
+/* sinv_mlp_grad followed by one Adam step (beta 0.9 / 0.999, eps 1e-8) with rate lr. */
+sinv_status sinv_mlp_train_step(sinv_mlp m, const void *X, const float *y, const int64_t *idx, int64_t count,
+                                float lr, float *loss, void *stream);
+/* out[e] = N[e] + scale[e] f(X[e]) for count entries (device). */
+sinv_status sinv_mlp_predict(sinv_mlp m, const void *X, const float *scale, const double *N, int64_t count,
+                             double *out, void *stream);
 
 /* Wait for the handle's queued work on `stream` and return the first device
  * error recorded since the last call (then clear it). */

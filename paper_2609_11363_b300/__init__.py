@@ -13,4 +13,7 @@ from .binding import (  # noqa: F401
     PREC,
     lowrank_correct_noalloc,
     LOWRANK_NOALLOC_MAX,
+    Mlp,
+    MLP_F,
+    MLP_H,
 )

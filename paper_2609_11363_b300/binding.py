@@ -28,7 +28,9 @@ EXPORTS = [
     "sinv_lowrank_correct", "sinv_sync_status", "sinv_get_stats", "sinv_get_supernodes",
     "sinv_status_string", "sinv_last_error", "sinv_destroy", "sinv_debug_wait_timeout",
     "sinv_trace_enable", "sinv_trace_read", "sinv_lowrank_correct_noalloc",
-    "sinv_batch_symbolic", "sinv_batch_layout",
+    "sinv_batch_symbolic", "sinv_batch_layout", "sinv_ninv_stack",
+    "sinv_mlp_param_count", "sinv_mlp_create", "sinv_mlp_destroy", "sinv_mlp_get_params", "sinv_mlp_set_params",
+    "sinv_mlp_features", "sinv_mlp_targets", "sinv_mlp_grad", "sinv_mlp_train_step", "sinv_mlp_predict",
 ]
 
 
@@ -85,6 +87,16 @@ def load_library():
     lib.sinv_destroy.argtypes = [H]
     lib.sinv_destroy.restype = None
     lib.sinv_debug_wait_timeout.argtypes = [H, P]
+    lib.sinv_ninv_stack.argtypes = [H, P, P, ctypes.c_int, ctypes.c_int, P, P]
+    lib.sinv_mlp_create.argtypes = [ctypes.c_int32, ctypes.c_uint64, I64, ctypes.POINTER(H)]
+    lib.sinv_mlp_destroy.argtypes = [H]
+    lib.sinv_mlp_get_params.argtypes = [H, P]
+    lib.sinv_mlp_set_params.argtypes = [H, P]
+    lib.sinv_mlp_features.argtypes = [H, P, ctypes.c_int, P, P, P, P, P]
+    lib.sinv_mlp_targets.argtypes = [H, I64, P, P, P, P, P]
+    lib.sinv_mlp_grad.argtypes = [H, P, P, P, I64, P, P, P]
+    lib.sinv_mlp_train_step.argtypes = [H, P, P, P, I64, ctypes.c_float, P, P]
+    lib.sinv_mlp_predict.argtypes = [H, P, P, P, I64, P, P]
     lib.sinv_batch_symbolic.argtypes = [ctypes.c_int32, P, P, P, P, ctypes.POINTER(_Opts), ctypes.POINTER(H)]
     lib.sinv_batch_layout.argtypes = [H, ctypes.POINTER(ctypes.c_int32), P, P, P, P]
     lib.sinv_lowrank_correct_noalloc.argtypes = [I64, P, P, ctypes.c_int, P, P, P, P]
@@ -93,8 +105,9 @@ def load_library():
                                     ctypes.c_int]
     for name in EXPORTS:
         f = getattr(lib, name)
-        if name not in ("sinv_status_string", "sinv_destroy"):
+        if name not in ("sinv_status_string", "sinv_destroy", "sinv_mlp_destroy"):
             f.restype = ctypes.c_int
+    lib.sinv_mlp_destroy.restype = None
     _lib = lib
     return lib
 
@@ -123,6 +136,88 @@ def _stream_ptr(stream):
             return ctypes.c_void_p(0)  # host-only handles: the library rejects the call itself
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+MLP_F = 16
+MLP_H = 64
+
+
+class Mlp:
+    """The learned NInv -> SelInv correction network (weights live on the GPU)."""
+
+    def __init__(self, seed=0, max_batch=1 << 16, device=0):
+        self._lib = load_library()
+        self._m = ctypes.c_void_p()
+        self.device = torch.device("cuda", int(device))
+        self.max_batch = int(max_batch)
+        st = self._lib.sinv_mlp_create(int(device), ctypes.c_uint64(int(seed)), self.max_batch, ctypes.byref(self._m))
+        if st != 0:
+            raise SinvError(st, "sinv_mlp_create")
+        self.n_params = int(self._lib.sinv_mlp_param_count())
+        self._loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+
+    def close(self):
+        if getattr(self, "_m", None):
+            self._lib.sinv_mlp_destroy(self._m)
+            self._m = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, st, what):
+        if st != 0:
+            raise SinvError(st, what)
+
+    def get_params(self) -> np.ndarray:
+        th = np.empty(self.n_params, dtype=np.float32)
+        self._chk(self._lib.sinv_mlp_get_params(self._m, _np_ptr(th)), "get_params")
+        return th
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        assert th.size == self.n_params
+        self._chk(self._lib.sinv_mlp_set_params(self._m, _np_ptr(th)), "set_params")
+
+    def targets(self, G, N, scale, stream=None):
+        y = torch.empty(G.numel(), dtype=torch.float32, device=self.device)
+        self._chk(self._lib.sinv_mlp_targets(self._m, G.numel(), _check_tensor(G, "G"), _check_tensor(N, "N"),
+                                             _check_tensor(scale, "scale", None, torch.float32),
+                                             _check_tensor(y, "y", None, torch.float32), _stream_ptr(stream)),
+                  "targets")
+        return y
+
+    def grad(self, X, y, idx=None, stream=None):
+        """(gradient [n_params] float32 tensor, loss tensor) over the entries idx (or all)."""
+        count = int(idx.numel()) if idx is not None else int(X.shape[0])
+        g = torch.empty(self.n_params, dtype=torch.float32, device=self.device)
+        self._chk(self._lib.sinv_mlp_grad(self._m, _check_tensor(X, "X", None, torch.bfloat16),
+                                          _check_tensor(y, "y", None, torch.float32),
+                                          _check_tensor(idx, "idx", None, torch.int64) if idx is not None else None,
+                                          count, _check_tensor(g, "grad", None, torch.float32),
+                                          _check_tensor(self._loss, "loss", None, torch.float32), _stream_ptr(stream)),
+                  "grad")
+        return g, self._loss
+
+    def train_step(self, X, y, idx, lr, stream=None):
+        self._chk(self._lib.sinv_mlp_train_step(self._m, _check_tensor(X, "X", None, torch.bfloat16),
+                                                _check_tensor(y, "y", None, torch.float32),
+                                                _check_tensor(idx, "idx", None, torch.int64), int(idx.numel()),
+                                                ctypes.c_float(lr), _check_tensor(self._loss, "loss", None,
+                                                                                  torch.float32),
+                                                _stream_ptr(stream)), "train_step")
+        return self._loss
+
+    def predict(self, X, scale, N, out=None, stream=None):
+        if out is None:
+            out = torch.empty_like(N)
+        self._chk(self._lib.sinv_mlp_predict(self._m, _check_tensor(X, "X", None, torch.bfloat16),
+                                             _check_tensor(scale, "scale", None, torch.float32),
+                                             _check_tensor(N, "N"), int(N.numel()), _check_tensor(out, "out"),
+                                             _stream_ptr(stream)), "predict")
+        return out
 
 
 LOWRANK_NOALLOC_MAX = 1 << 22  # n*k + k floats of the library's built-in working array
@@ -296,6 +391,27 @@ class Handle:
                                                    _check_tensor(lam, "lambda", k), PREC[prec],
                                                    _check_tensor(X, "X_S", self.nnz_S), _stream_ptr(stream)))
         return X
+
+    def ninv_stack(self, L_val, D_val, m, prec="fp64", out=None, stream=None):
+        """NInv on S for the truncations after 0..m terms: tensor [(m+1), |S_lo|]."""
+        if out is None:
+            out = torch.empty((m + 1) * self.nnz_S, dtype=torch.float64, device=self.device)
+        self._check(self._lib.sinv_ninv_stack(self._h, _check_tensor(L_val, "L_val", self.nnz_L),
+                                              _check_tensor(D_val, "D_val", self.nD), int(m), PREC[prec],
+                                              _check_tensor(out, "N_stack", (m + 1) * self.nnz_S),
+                                              _stream_ptr(stream)))
+        return out.view(m + 1, self.nnz_S)
+
+    def mlp_features(self, N_stack, m, L_val, D_val, stream=None):
+        """(X [|S_lo| x 16] bfloat16, scale [|S_lo|] float32) for the learned correction."""
+        X = torch.empty((self.nnz_S, MLP_F), dtype=torch.bfloat16, device=self.device)
+        sc = torch.empty(self.nnz_S, dtype=torch.float32, device=self.device)
+        self._check(self._lib.sinv_mlp_features(
+            self._h, _check_tensor(N_stack.reshape(-1), "N_stack", (m + 1) * self.nnz_S), int(m),
+            _check_tensor(L_val, "L_val", self.nnz_L), _check_tensor(D_val, "D_val", self.nD),
+            _check_tensor(X, "X", None, torch.bfloat16), _check_tensor(sc, "scale", None, torch.float32),
+            _stream_ptr(stream)))
+        return X, sc
 
     def sync_status(self, stream=None):
         self._check(self._lib.sinv_sync_status(self._h, _stream_ptr(stream)))

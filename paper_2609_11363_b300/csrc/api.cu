@@ -486,17 +486,31 @@ sinv_status sinv_selinv(sinv_handle h, const double* L_val, const double* D_val,
     return SINV_OK;
 }
 
+static sinv_status ninv_common(sinv_handle h, const double* L_val, const double* D_val, int m, sinv_precision prec,
+                               double* N_S, double* N_stack, void* stream);
+
 sinv_status sinv_ninv(sinv_handle h, const double* L_val, const double* D_val, int m, sinv_precision prec,
                       double* N_S, void* stream) {
+    return ninv_common(h, L_val, D_val, m, prec, N_S, nullptr, stream);
+}
+
+sinv_status sinv_ninv_stack(sinv_handle h, const double* L_val, const double* D_val, int m, sinv_precision prec,
+                            double* N_stack, void* stream) {
+    if (h && h->P.n > 0 && !N_stack) return SINV_ERR_INVALID_ARG;
+    return ninv_common(h, L_val, D_val, m, prec, nullptr, N_stack, stream);
+}
+
+static sinv_status ninv_common(sinv_handle h, const double* L_val, const double* D_val, int m, sinv_precision prec,
+                               double* N_S, double* N_stack, void* stream) {
     if (!h || !valid_prec(prec) || m < 0) return SINV_ERR_INVALID_ARG;
     if (!on_device(h)) return SINV_ERR_INVALID_ARG;
-    if (m > 60) {
-        set_err(h, "m > 60 is not supported");
+    if (m > 30) {
+        set_err(h, "m > 30 is not supported");
         return SINV_ERR_UNSUPPORTED;
     }
     const HostPlan& P = h->P;
     if (P.n == 0) return SINV_OK;
-    if (!D_val || !N_S || (P.nnzL > 0 && !L_val)) return SINV_ERR_INVALID_ARG;
+    if (!D_val || (!N_S && !N_stack) || (P.nnzL > 0 && !L_val)) return SINV_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
@@ -536,6 +550,7 @@ sinv_status sinv_ninv(sinv_handle h, const double* L_val, const double* D_val, i
     a.Srp = h->dSrp;
     a.Sc = h->dSc;
     a.Lrp = h->dLrp;
+    a.nnzS = P.nnzS;
     a.nnzW = h->W.nnzW;
     a.dpos = h->ddpos;
     a.pstart = h->dpstart;
@@ -547,7 +562,7 @@ sinv_status sinv_ninv(sinv_handle h, const double* L_val, const double* D_val, i
     int p = prec == SINV_FP64 ? 0 : 1;
     sinv_status s = ensure_work(h, ninv_work_bytes(a, p));
     if (s != SINV_OK) return s;
-    if ((e = ninv_launch(a, p, h->dwork, N_S, st)) != cudaSuccess) return cuda_fail(h, e, "ninv launch");
+    if ((e = ninv_launch(a, p, h->dwork, N_S, st, N_stack)) != cudaSuccess) return cuda_fail(h, e, "ninv launch");
     return SINV_OK;
 }
 
@@ -631,6 +646,151 @@ sinv_status sinv_lowrank_correct_noalloc(int64_t n, const int64_t* S_rowptr, con
     if (!S_rowptr || !S_col || !V || !lambda || !X_S) return SINV_ERR_INVALID_ARG;
     cudaError_t e = lowrank_noalloc_launch(n, S_rowptr, S_col, k, V, lambda, X_S, (cudaStream_t)stream);
     return e == cudaSuccess ? SINV_OK : SINV_ERR_CUDA;
+}
+
+// ---- learned correction ------------------------------------------------------------
+struct sinv_mlp_s {
+    int device = 0;
+    int num_sms = 0;
+    int64_t max_batch = 0;
+    int step = 0;
+    float* theta = nullptr;   // FP32 master weights
+    float* mom1 = nullptr;
+    float* mom2 = nullptr;
+    float* grad = nullptr;
+    float* partial = nullptr;
+    float* loss_partial = nullptr;
+};
+
+static uint64_t splitmix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+int32_t sinv_mlp_param_count(void) { return kMlpParams; }
+
+void sinv_mlp_destroy(sinv_mlp m) {
+    if (!m) return;
+    cudaSetDevice(m->device);
+    for (void* p : {(void*)m->theta, (void*)m->mom1, (void*)m->mom2, (void*)m->grad, (void*)m->partial,
+                    (void*)m->loss_partial})
+        if (p) cudaFree(p);
+    delete m;
+}
+
+sinv_status sinv_mlp_create(int32_t device, uint64_t seed, int64_t max_batch, sinv_mlp* out) {
+    if (!out || max_batch <= 0 || device < 0) return SINV_ERR_INVALID_ARG;
+    *out = nullptr;
+    sinv_mlp m = new (std::nothrow) sinv_mlp_s();
+    if (!m) return SINV_ERR_OOM;
+    m->device = device;
+    m->max_batch = max_batch;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, device);
+    const int nblk = mlp_train_blocks(max_batch);
+    const size_t P = kMlpParams * sizeof(float);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->theta, P);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->mom1, P);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->mom2, P);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->grad, P);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->partial, (size_t)nblk * P);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->loss_partial, (size_t)nblk * sizeof(float) + 16);
+    if (e == cudaSuccess) e = mlp_configure();
+    if (e != cudaSuccess) {
+        sinv_mlp_destroy(m);
+        return e == cudaErrorMemoryAllocation ? SINV_ERR_OOM : SINV_ERR_CUDA;
+    }
+    // He-uniform initial weights from a counter-based hash of (seed, index); zero biases;
+    // the output layer is scaled by 0.1 so that the first predictions stay small
+    std::vector<float> th(kMlpParams, 0.f);
+    auto uni = [&](int p) { return (double)(splitmix64(seed * 0x100000001B3ull + (uint64_t)p) >> 11) / 9007199254740992.0; };
+    for (int p = 0; p < kMlpF * kMlpH; ++p) th[kOffW1 + p] = (float)((2 * uni(p) - 1) * sqrt(6.0 / kMlpF));
+    for (int p = 0; p < kMlpH * kMlpH; ++p) th[kOffW2 + p] = (float)((2 * uni(kOffW2 + p) - 1) * sqrt(6.0 / kMlpH));
+    for (int p = 0; p < kMlpH; ++p) th[kOffW3 + p] = (float)(0.1 * (2 * uni(kOffW3 + p) - 1) * sqrt(6.0 / kMlpH));
+    sinv_status st = sinv_mlp_set_params(m, th.data());
+    if (st != SINV_OK) {
+        sinv_mlp_destroy(m);
+        return st;
+    }
+    *out = m;
+    return SINV_OK;
+}
+
+sinv_status sinv_mlp_get_params(sinv_mlp m, float* theta) {
+    if (!m || !theta) return SINV_ERR_INVALID_ARG;
+    cudaSetDevice(m->device);
+    return cudaMemcpy(theta, m->theta, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess
+               ? SINV_OK
+               : SINV_ERR_CUDA;
+}
+
+sinv_status sinv_mlp_set_params(sinv_mlp m, const float* theta) {
+    if (!m || !theta) return SINV_ERR_INVALID_ARG;
+    cudaSetDevice(m->device);
+    const size_t P = kMlpParams * sizeof(float);
+    if (cudaMemcpy(m->theta, theta, P, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(m->mom1, 0, P) != cudaSuccess || cudaMemset(m->mom2, 0, P) != cudaSuccess)
+        return SINV_ERR_CUDA;
+    m->step = 0;
+    return SINV_OK;
+}
+
+sinv_status sinv_mlp_features(sinv_handle h, const double* N_stack, int m, const double* L_val, const double* D_val,
+                              void* X, float* scale, void* stream) {
+    if (!h || m < 0) return SINV_ERR_INVALID_ARG;
+    if (!on_device(h)) return SINV_ERR_INVALID_ARG;
+    if (m > kMlpF - 7) {
+        set_err(h, "the feature layout holds the increments of at most 9 Neumann terms");
+        return SINV_ERR_UNSUPPORTED;
+    }
+    if (h->P.n == 0) return SINV_OK;
+    if (!N_stack || !D_val || !X || !scale || (h->P.nnzL > 0 && !L_val)) return SINV_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    TraceScope trace_scope(h->tracer);
+    if ((e = mlp_features_launch(h->P.n, h->dSrp, h->dSc, h->dLrp, h->dLcp, m, N_stack, h->P.nnzS, L_val, D_val,
+                                 h->ddpos, h->dpstart, X, scale, h->num_sms, (cudaStream_t)stream)) != cudaSuccess)
+        return cuda_fail(h, e, "mlp features");
+    return SINV_OK;
+}
+
+sinv_status sinv_mlp_targets(sinv_mlp m, int64_t count, const double* G, const double* N, const float* scale, float* y,
+                             void* stream) {
+    if (!m || count < 0 || (count > 0 && (!G || !N || !scale || !y))) return SINV_ERR_INVALID_ARG;
+    cudaSetDevice(m->device);
+    return mlp_targets_launch(count, G, N, scale, y, m->num_sms, (cudaStream_t)stream) == cudaSuccess ? SINV_OK
+                                                                                                     : SINV_ERR_CUDA;
+}
+
+sinv_status sinv_mlp_grad(sinv_mlp m, const void* X, const float* y, const int64_t* idx, int64_t count, float* grad,
+                          float* loss, void* stream) {
+    if (!m || !X || !y || count <= 0 || count > m->max_batch) return SINV_ERR_INVALID_ARG;
+    cudaSetDevice(m->device);
+    return mlp_grad_launch(X, y, idx, count, m->theta, m->partial, m->loss_partial, grad ? grad : m->grad, loss,
+                           (cudaStream_t)stream) == cudaSuccess
+               ? SINV_OK
+               : SINV_ERR_CUDA;
+}
+
+sinv_status sinv_mlp_train_step(sinv_mlp m, const void* X, const float* y, const int64_t* idx, int64_t count, float lr,
+                                float* loss, void* stream) {
+    sinv_status s = sinv_mlp_grad(m, X, y, idx, count, nullptr, loss, stream);
+    if (s != SINV_OK) return s;
+    m->step += 1;
+    return mlp_adam_launch(m->theta, m->mom1, m->mom2, m->grad, lr, m->step, (cudaStream_t)stream) == cudaSuccess
+               ? SINV_OK
+               : SINV_ERR_CUDA;
+}
+
+sinv_status sinv_mlp_predict(sinv_mlp m, const void* X, const float* scale, const double* N, int64_t count, double* out,
+                             void* stream) {
+    if (!m || count < 0 || (count > 0 && (!X || !scale || !N || !out))) return SINV_ERR_INVALID_ARG;
+    cudaSetDevice(m->device);
+    return mlp_predict_launch(X, scale, N, count, m->theta, out, m->num_sms, (cudaStream_t)stream) == cudaSuccess
+               ? SINV_OK
+               : SINV_ERR_CUDA;
 }
 
 sinv_status sinv_trace_enable(sinv_handle h, int enable) {

@@ -76,6 +76,7 @@ struct NinvArgs {
     const int64_t* Srp;   // S_lo
     const int32_t* Sc;
     const int64_t* Lrp;   // L row pointers (CSR of the caller's L)
+    int64_t nnzS;
     int64_t nnzW;
     const int32_t* dpos;
     const int8_t* pstart;
@@ -87,7 +88,10 @@ struct NinvArgs {
 };
 cudaError_t ninv_configure();
 size_t ninv_work_bytes(const NinvArgs& a, int prec);
-cudaError_t ninv_launch(const NinvArgs& a, int prec, void* work, double* N_out, cudaStream_t st);
+// N_stack (optional): (m+1) x |S_lo| products of the truncations after 0..m steps;
+// then N_out is not written (the last slice holds the full NInv)
+cudaError_t ninv_launch(const NinvArgs& a, int prec, void* work, double* N_out, cudaStream_t st,
+                        double* N_stack = nullptr);
 
 // FP32 low-rank correction with its working copy in a file-scope device array
 // (no allocation); n*k + k must not exceed kLowrankStaticFloats.
@@ -96,5 +100,29 @@ cudaError_t lowrank_noalloc_launch(int64_t n, const int64_t* Srp, const int32_t*
                                    const double* lambda, double* X, cudaStream_t st);
 
 cudaError_t debug_wait_launch(uint32_t* flag, int32_t* status, int64_t limit, cudaStream_t st);
+
+// ---- learned correction (mlp.cu) ----
+constexpr int kMlpF = 16;  // features per entry (zero padded)
+constexpr int kMlpH = 64;  // hidden width
+constexpr int kOffW1 = 0;
+constexpr int kOffB1 = kOffW1 + kMlpF * kMlpH;
+constexpr int kOffW2 = kOffB1 + kMlpH;
+constexpr int kOffB2 = kOffW2 + kMlpH * kMlpH;
+constexpr int kOffW3 = kOffB2 + kMlpH;
+constexpr int kOffB3 = kOffW3 + kMlpH;
+constexpr int kMlpParams = kOffB3 + 1;
+cudaError_t mlp_configure();
+int mlp_train_blocks(int64_t count);
+cudaError_t mlp_features_launch(int64_t n, const int64_t* Srp, const int32_t* Sc, const int64_t* Lrp,
+                                const int64_t* Lcp, int m, const double* Nst, int64_t nnzS, const double* Lval,
+                                const double* Dval, const int32_t* dpos, const int8_t* pstart, void* X, float* scale,
+                                int num_sms, cudaStream_t st);
+cudaError_t mlp_targets_launch(int64_t count, const double* G, const double* N, const float* scale, float* y,
+                               int num_sms, cudaStream_t st);
+cudaError_t mlp_grad_launch(const void* X, const float* y, const int64_t* idx, int64_t count, const float* theta,
+                            float* partial, float* loss_partial, float* grad, float* loss, cudaStream_t st);
+cudaError_t mlp_adam_launch(float* theta, float* m, float* v, const float* g, float lr, int step, cudaStream_t st);
+cudaError_t mlp_predict_launch(const void* X, const float* scale, const double* N, int64_t count, const float* theta,
+                               double* out, int num_sms, cudaStream_t st);
 
 }  // namespace sinv

@@ -177,10 +177,13 @@ __global__ void __launch_bounds__(kThreads) ninv_horner(NinvArgs a, int t, const
     }
 }
 
+// tlim: use the rows of groups 0..tlim of every column (the truncation after tlim
+// Horner steps; tlim = m is the whole pattern)
 template <class T>
-__global__ void __launch_bounds__(kThreads) ninv_product(NinvArgs a, const T* __restrict__ W, const double* __restrict__ dr,
-                                                         const double* __restrict__ dp, const int32_t* __restrict__ part,
-                                                         double* __restrict__ N, int32_t* ticket, Scratch gs) {
+__global__ void __launch_bounds__(kThreads) ninv_product(NinvArgs a, int tlim, const T* __restrict__ W,
+                                                         const double* __restrict__ dr, const double* __restrict__ dp,
+                                                         const int32_t* __restrict__ part, double* __restrict__ N,
+                                                         int32_t* ticket, Scratch gs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* syv = reinterpret_cast<T*>(smem_raw);                     // y = (D^{-1} W)[:, j], one per slot
     int32_t* skeys = reinterpret_cast<int32_t*>(syv + kSlots);
@@ -195,8 +198,9 @@ __global__ void __launch_bounds__(kThreads) ninv_product(NinvArgs a, const T* __
         const int64_t j = s_j;
         __syncthreads();
         if (j >= a.n) break;
+        const int G = a.m + 2;
         const int64_t base = a.Wcp[j];
-        const int32_t nj = (int32_t)(a.Wcp[j + 1] - base);
+        const int32_t nj = a.grp[j * G + tlim + 1];
         // the table holds the rows of column j and, for its rows in 2x2 blocks, their partners
         int flagged = 0;
         for (int32_t e = threadIdx.x; e < nj; e += kThreads) flagged += (a.Wr[base + e] & kTwoFlag) ? 1 : 0;
@@ -242,7 +246,7 @@ __global__ void __launch_bounds__(kThreads) ninv_product(NinvArgs a, const T* __
                 // row i of S_lo starts with row i of L, so L(i, j) keeps its offset in the row
                 spos = a.Srp[i] + ((int64_t)a.Lcsr[q] - a.Lrp[i]);
             }
-            const int64_t ib = a.Wcp[i], ie = a.Wcp[i + 1];
+            const int64_t ib = a.Wcp[i], ie = ib + a.grp[i * G + tlim + 1];
             T s = T(0);
             for (int64_t f0 = ib; f0 < ie; f0 += 32 * kUnroll) {
                 int32_t r[kUnroll];
@@ -302,7 +306,7 @@ size_t ninv_work_bytes(const NinvArgs& a, int prec) {
 }
 
 template <class T>
-static cudaError_t ninv_run(const NinvArgs& a, void* work, double* N_out, cudaStream_t st) {
+static cudaError_t ninv_run(const NinvArgs& a, void* work, double* N_out, double* N_stack, cudaStream_t st) {
     char* p = reinterpret_cast<char*>(work);
     auto take = [&](size_t bytes) {
         char* r = p;
@@ -331,23 +335,28 @@ static cudaError_t ninv_run(const NinvArgs& a, void* work, double* N_out, cudaSt
     trace_end(st);
     T* cur = W0;
     T* nxt = W1;
+    auto product = [&](int t, double* out, int32_t* tk) {
+        trace_begin("ninv_product", st);
+        ninv_product<T><<<grid, kThreads, ninv_smem<T>(), st>>>(a, t, cur, dr, dp, part, out, tk, gs);
+        trace_end(st);
+    };
+    if (N_stack) product(0, N_stack, tickets + 62 - a.m);
     for (int t = 1; t <= a.m; ++t) {
         trace_begin("ninv_horner", st);
         ninv_horner<T><<<grid, kThreads, ninv_smem<T>(), st>>>(a, t, cur, nxt, tickets + t, gs);
         trace_end(st);
         std::swap(cur, nxt);
+        if (N_stack && t < a.m) product(t, N_stack + (int64_t)t * a.nnzS, tickets + 62 - a.m + t);
     }
-    trace_begin("ninv_product", st);
-    ninv_product<T><<<grid, kThreads, ninv_smem<T>(), st>>>(a, cur, dr, dp, part, N_out, tickets + 63, gs);
-    trace_end(st);
+    product(a.m, N_stack ? N_stack + (int64_t)a.m * a.nnzS : N_out, tickets + 63);
     return cudaGetLastError();
 }
 
-cudaError_t ninv_launch(const NinvArgs& a, int prec, void* work, double* N_out, cudaStream_t st) {
+cudaError_t ninv_launch(const NinvArgs& a, int prec, void* work, double* N_out, cudaStream_t st, double* N_stack) {
     if (a.n == 0) return cudaSuccess;
-    if (a.m > 60) return cudaErrorInvalidValue;
-    if (prec == 0) return ninv_run<double>(a, work, N_out, st);
-    return ninv_run<float>(a, work, N_out, st);
+    if (a.m > 30) return cudaErrorInvalidValue;
+    if (prec == 0) return ninv_run<double>(a, work, N_out, N_stack, st);
+    return ninv_run<float>(a, work, N_out, N_stack, st);
 }
 
 }  // namespace sinv

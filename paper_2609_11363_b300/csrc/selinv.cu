@@ -9,8 +9,8 @@
 // and X is stored where (C[i], s0+t) is in S.  The symmetric c x c matrix G~_CC
 // is read through a per-supernode list of the pairs (i, k) whose entry is in S
 // (both triangles and the diagonal, sorted by i): the zeros of G~ are never
-// touched.  Each row of X is a segmented sum over its pairs, formed by warp
-// shuffles, so no atomic is needed.
+// touched.  The pairs are accumulated with shared-memory atomic adds into
+// distinct rows per instruction (see accumulate_pairs).
 //
 // Scheduling: a CTA takes the next work item from a global ticket counter in
 // level-major order.  An item is either one large supernode (the whole CTA
@@ -90,19 +90,6 @@ struct Group {
     }
 };
 
-// Segmented sum of v over lanes that share `key` (lanes sorted by key): after the
-// call, the last lane of every run holds the run's total.
-template <class R>
-__device__ __forceinline__ R seg_sum(R v, int key, int lane) {
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        R o = __shfl_up_sync(0xffffffffu, v, off);
-        int ko = __shfl_up_sync(0xffffffffu, key, off);
-        if (lane >= off && ko == key) v += o;
-    }
-    return v;
-}
-
 // Pairs of one warp: entries [e0, e1) of the supernode's pair list.  The first
 // batch of (i, k) / position words is loaded before the dependency wait.
 struct PairRange {
@@ -121,9 +108,11 @@ __device__ __forceinline__ void load_pairs(const uint32_t* __restrict__ hik, con
     }
 }
 
-// X[i][:] -= sum over the pairs (i, k) of G(C[i], C[k]) Lh[k][:]; one warp.  Rows of
-// different warps are disjoint, and a run of one row inside a chunk of 32 pairs is
-// summed by shuffles and added by its last lane, so no atomic is needed.  Every
+// X -= G~_CC Lh over the pairs of this warp.  The pair list holds both (i, k) and
+// (k, i), so each pair can add G(C[i], C[k]) Lh[i][:] into row k: the pairs of a
+// chunk share i (sorted by i) and have distinct k, so the shared-memory atomic
+// adds of one instruction hit distinct rows (FP64 and FP32 shared atomics are
+// native), and no chain of dependent additions sits on the critical path.  Every
 // batch issues the G loads of kBatch chunks and the pair words of the next batch
 // before it computes.
 template <class Form>
@@ -140,18 +129,14 @@ __device__ __forceinline__ void accumulate_pairs(PairRange& pr, const uint32_t* 
         load_pairs(hik, hpos, base + 32 * kBatch, pr.e1, lane, ik_n, pos_n);
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
-            if (base + u * 32 >= pr.e1) break;  // uniform across the warp
-            const bool valid = pr.pos[u] >= 0;
-            const int i = valid ? (int)(pr.ik[u] >> 16) : -1 - lane;
-            const int k = valid ? (int)(pr.ik[u] & 0xffff) : 0;
-            const int inext = __shfl_down_sync(0xffffffffu, i, 1);
-            const bool last = valid && (lane == 31 || inext != i);
-            for (int q = 0; q < w; ++q) {
-                R v = valid ? g[u] * lh[k * w + q] : R(0);
-                v = seg_sum(v, i, lane);
-                if (last) x[i * w + q] -= v;
+            if (pr.pos[u] < 0) continue;
+            const int i = (int)(pr.ik[u] >> 16);
+            const int k = (int)(pr.ik[u] & 0xffff);
+            if (w == 1) {
+                atomicAdd(x + k, -g[u] * lh[i]);
+            } else {
+                for (int q = 0; q < w; ++q) atomicAdd(x + k * w + q, -g[u] * lh[i * w + q]);
             }
-            __syncwarp();
         }
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {

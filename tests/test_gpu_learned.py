@@ -1,0 +1,102 @@
+"""Learned correction: NInv truncation stack, BF16 MLP gradients against the FP64
+oracle, one Adam step, and the gain of a trained network over plain NInv on a
+held-out matrix (SelInv as the judge)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import mlp as omlp
+from tests.helpers import sel_rel_err
+from workloads.configs import diff3d, plant_2x2
+
+pytestmark = pytest.mark.gpu
+
+F, H = 16, 64
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def _bf16_round(a):
+    return torch.as_tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def test_ninv_stack_matches_each_truncation():
+    from paper_2609_11363_b300 import Handle
+    f = plant_2x2(diff3d(10, shifted=False, m=3).factors, 0.05, 3)
+    S = oracle.symbolic_S(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+    h = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+    st = h.ninv_stack(_dev(f.L_val), _dev(f.D_packed), 3).cpu().numpy()
+    h.sync_status()
+    for t in range(4):
+        ref = oracle.ninv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, t, S)
+        assert sel_rel_err(st[t], ref, *S) <= 1e-10, t
+
+
+def test_mlp_gradient_matches_oracle_and_adam_step():
+    from paper_2609_11363_b300 import Mlp
+    rng = np.random.default_rng(0)
+    B = 1000
+    Xf = rng.standard_normal((B, F)).astype(np.float32)
+    y = rng.standard_normal(B).astype(np.float32)
+    net = Mlp(seed=7, max_batch=4096)
+    th = net.get_params().astype(np.float64)
+    Xb = torch.as_tensor(Xf).to(torch.bfloat16).cuda()
+    g, loss = net.grad(Xb, _dev(y))
+    torch.cuda.synchronize()
+    # the oracle sees the same BF16-rounded weights and features
+    Xr = Xb.float().cpu().numpy().astype(np.float64)
+    thr = _bf16_round(th)
+    g_ref = omlp.grad(thr, Xr, y.astype(np.float64), F, H)
+    l_ref = omlp.loss(thr, Xr, y.astype(np.float64), F, H)
+    gg = g.cpu().numpy().astype(np.float64)
+    assert abs(float(loss.item()) - l_ref) <= 1e-4 * max(1.0, abs(l_ref))
+    assert np.linalg.norm(gg - g_ref) <= 1e-3 * np.linalg.norm(g_ref)
+    # one Adam step on the FP32 master weights
+    idx = torch.arange(B, dtype=torch.int64, device="cuda")
+    net.train_step(Xb, _dev(y), idx, 1e-3)
+    th1 = net.get_params().astype(np.float64)
+    want, _, _ = omlp.adam(th, gg, np.zeros_like(th), np.zeros_like(th), 1, 1e-3)
+    assert np.max(np.abs(th1 - want)) <= 1e-6
+
+
+def test_features_match_their_definition():
+    from paper_2609_11363_b300 import Handle
+    f = plant_2x2(diff3d(8, shifted=False, m=3).factors, 0.1, 5)
+    S = oracle.symbolic_S(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+    h = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+    Lv, Dv = _dev(f.L_val), _dev(f.D_packed)
+    st = h.ninv_stack(Lv, Dv, 3)
+    X, sc = h.mlp_features(st, 3, Lv, Dv)
+    h.sync_status()
+    X = X.float().cpu().numpy()
+    sc = sc.cpu().numpy()
+    Nst = st.cpu().numpy()
+    rows = np.repeat(np.arange(f.n), np.diff(S[0]))
+    cols = S[1].astype(np.int64)
+    N = Nst[3]
+    diag = N[S[0][1:] - 1]
+    s = np.sqrt(np.abs(diag[rows] * diag[cols]))
+    assert np.allclose(sc, s, rtol=1e-6)
+    assert np.allclose(X[:, 0], _bf16_round(N / s), rtol=1e-2, atol=1e-3)
+    for t in range(1, 4):
+        assert np.allclose(X[:, t], _bf16_round((Nst[t] - Nst[t - 1]) / s), rtol=1e-2, atol=1e-3)
+    assert np.array_equal(X[:, 5], (rows == cols).astype(np.float32))
+
+
+def test_trained_network_beats_plain_ninv_on_held_out_matrix():
+    """Train on three 3D diffusion matrices, judge on a fourth: the corrected NInv is
+    closer to SelInv than NInv itself."""
+    from paper_2609_11363_b300 import Handle
+    from paper_2609_11363_b300.learned import LearnedCorrection
+    lc = LearnedCorrection(m=3, seed=1, batch=4096)
+    sets = []
+    for seed in (4000, 4001, 4002, 4003):
+        f = diff3d(14, shifted=False, m=3, seed=seed).factors
+        h = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+        sets.append(lc.prepare(h, _dev(f.L_val), _dev(f.D_packed)))
+    lc.fit(sets[:3], epochs=12, lr=3e-3)
+    ev = lc.evaluate(sets[3])
+    assert ev["err_learned"] < 0.8 * ev["err_ninv"], ev

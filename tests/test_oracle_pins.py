@@ -329,3 +329,21 @@ def test_ildl_exact_reconstructs_and_keeps_inertia():
     neg_A = int(np.sum(np.linalg.eigvalsh(w.A.toarray()) < 0))
     neg_D = int(np.sum(np.linalg.eigvalsh(f.D_dense_blocks().toarray()) < 0))
     assert neg_A == neg_D == 1
+
+
+# -- the learned correction's network (oracle side of the gradient check) --------------
+def test_mlp_oracle_gradient_matches_finite_differences():
+    from oracle import mlp as omlp
+    F, H = 16, 64
+    rng = np.random.default_rng(3)
+    theta = rng.standard_normal(omlp.n_params(F, H)) * 0.2
+    X = rng.standard_normal((40, F))
+    y = rng.standard_normal(40)
+    g = omlp.grad(theta, X, y, F, H)
+    idx = rng.choice(len(theta), 60, replace=False)
+    fd = omlp.grad_fd(theta, X, y, F, H, idx)
+    assert np.max(np.abs(g[idx] - fd)) <= 1e-6 * max(1.0, np.max(np.abs(fd)))
+    # Adam's first step moves every parameter by lr * sign(g) (bias-corrected moments)
+    t1, m1, v1 = omlp.adam(theta, g, np.zeros_like(g), np.zeros_like(g), 1, 1e-3)
+    big = np.abs(g) > 1e-3
+    assert np.allclose((theta - t1)[big], 1e-3 * np.sign(g[big]), rtol=1e-4)
