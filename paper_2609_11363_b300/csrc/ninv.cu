@@ -9,10 +9,10 @@
 // column k and no step touches a structural zero.
 //
 // Horner step: one CTA owns one column j.  Its rows go into a shared-memory
-// hash table (row -> slot, the accumulator lives in the slot).  The CTA walks the
-// columns k of struct(j) one at a time; its threads split column k's entries,
-// which are distinct rows, so each slot is updated by one fused multiply-add with
-// no atomic, and a barrier separates consecutive k.
+// hash table (row -> slot).  Warp v handles the columns k of struct(j) with
+// k = v mod 8 and adds E_kj W_{t-1}[r, k] into the slot of r with shared-memory
+// atomics (native for FP32 and FP64 and as fast as a plain read-modify-write
+// here; the lanes of one instruction always touch distinct rows).
 //
 // Product on S: N_ij = sum_r W_ri (D^{-1} W)_rj for (i, j) in S_lo.  One CTA
 // owns column j: it tabulates y = (D^{-1} W)[:, j] on the rows of column j,
@@ -37,8 +37,7 @@ constexpr int kWarps = 8;                     // warps per CTA (Horner step and 
 constexpr int kThreads = kWarps * 32;
 constexpr int kSlots = 4096;                  // hash slots in shared memory
 constexpr int kEnt = 2730;                    // most table entries kept in shared memory (load <= 2/3)
-constexpr int kUnroll = 8;                    // column entries per lane with loads in flight (product)
-constexpr int kUnrollH = 2;                   // entries per thread in flight (Horner step, per column k)
+constexpr int kUnroll = 8;                    // column entries per lane with loads in flight
 constexpr int32_t kRowMask = 0x7FFFFFFF;      // row index bits of a pattern entry
 constexpr int32_t kTwoFlag = (int32_t)0x80000000u;  // set when the row belongs to a 2x2 block of D
 
@@ -124,6 +123,7 @@ __global__ void __launch_bounds__(kThreads) ninv_horner(NinvArgs a, int t, const
     int32_t* skeys = reinterpret_cast<int32_t*>(sacc + kSlots);  // kSlots keys
     __shared__ int32_t s_j;
     const int G = a.m + 2;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (;;) {
         if (threadIdx.x == 0) s_j = atomicAdd(ticket, 1);
         __syncthreads();
@@ -143,33 +143,30 @@ __global__ void __launch_bounds__(kThreads) ninv_horner(NinvArgs a, int t, const
         __syncthreads();
         for (int32_t e = threadIdx.x; e < nj; e += kThreads) table_insert(keys, mask, a.Wr[base + e] & kRowMask);
         __syncthreads();
-        // sum_k E_kj W_{t-1}[:, k], one k at a time for the whole CTA: the threads split the
-        // entries of column k's groups 0..t-1, which are distinct rows, so every slot has a
-        // single writer and the update is a plain fused multiply-add (no atomics)
-        const int64_t q0 = a.Lcp[j], q1 = a.Lcp[j + 1];
-        for (int64_t q = q0; q < q1; ++q) {
+        // sum_k E_kj W_{t-1}[:, k]: warp wid takes k = wid, wid+8, ...; lanes over column k's
+        // groups 0..t-1, kUnroll entries per lane in flight; atomic adds into the row's slot
+        for (int64_t q = a.Lcp[j] + wid; q < a.Lcp[j + 1]; q += kWarps) {
             const int32_t k = a.Lri[q];
             const T ekj = T(-a.Lval[a.Lcsr[q]]);
             const int64_t kb = a.Wcp[k];
             const int32_t nk = a.grp[(int64_t)k * G + t];
-            for (int32_t e0 = 0; e0 < nk; e0 += kThreads * kUnrollH) {
-                int32_t r[kUnrollH];
-                T v[kUnrollH];
+            for (int32_t e0 = 0; e0 < nk; e0 += 32 * kUnroll) {
+                int32_t r[kUnroll];
+                T v[kUnroll];
 #pragma unroll
-                for (int u = 0; u < kUnrollH; ++u) {
-                    const int32_t e = e0 + u * kThreads + (int32_t)threadIdx.x;
+                for (int u = 0; u < kUnroll; ++u) {
+                    const int32_t e = e0 + u * 32 + lane;
                     r[u] = e < nk ? (a.Wr[kb + e] & kRowMask) : -1;
                     v[u] = e < nk ? Wp[kb + e] : T(0);
                 }
 #pragma unroll
-                for (int u = 0; u < kUnrollH; ++u) {
+                for (int u = 0; u < kUnroll; ++u) {
                     if (r[u] < 0) continue;
                     const int32_t h = table_find(keys, mask, r[u]);
-                    if (h >= 0) acc[h] = fma_t<T>(ekj, v[u], acc[h]);
+                    if (h >= 0) atomicAdd(acc + h, ekj * v[u]);
                     else set_status(a.status, ST_INTERNAL);  // row outside the pattern: never expected
                 }
             }
-            __syncthreads();
         }
         __syncthreads();
         for (int32_t e = threadIdx.x; e < nj; e += kThreads) {
