@@ -135,13 +135,22 @@ def kernel_rooflines(trace, st, m, k, nS_lo, prec, peaks, steps):
     alu_src = "derived: %d SMs x %d %s flop/clk x %.0f MHz" % (
         N_SMS, FP64_FLOP_PER_CLK_SM if prec == "fp64" else FP32_FLOP_PER_CLK_SM, prec.upper(), mhz)
     hbm = float(peaks["hbm_gbs"])
+    horner = st["horner_products"] / max(m, 1)  # mean products of one Horner step
     work = {
         "selinv_persistent": ("alu", st["selinv_flops"], "flop"),
-        "ninv_horner": ("alu", 2.0 * st["horner_products"] / max(m, 1), "flop"),
+        "ninv_horner": ("alu", 2.0 * horner, "flop"),
         "ninv_product": ("alu", 2.0 * st["product_stream"], "flop"),
         "lowrank": ("alu", 2.0 * k * nS_lo, "flop"),
         "mix": ("hbm", 32.0 * nS_lo, "byte"),
     }
+    if prec == "fp64":
+        work["ninv_gather_horner"] = ("alu", 2.0 * horner, "flop")
+        work["ninv_gather_product"] = ("alu", 2.0 * st["product_hits"], "flop")
+    else:
+        # FP32 gather form: a 4-byte index word and a 4-byte value per product, the
+        # targets written once (Horner); two 4-byte values per product word
+        work["ninv_gather_horner"] = ("hbm", 8.0 * horner + 4.0 * st["nnz_W"], "byte")
+        work["ninv_gather_product"] = ("hbm", 12.0 * st["product_hits"] + 8.0 * nS_lo, "byte")
     out = {}
     for name, (launches, total_ms) in trace.items():
         per_launch_ms = total_ms / launches

@@ -69,6 +69,11 @@ typedef struct {
     int64_t wait_limit;     /* polls before a device wait gives up; 0 = default       */
     int64_t big_pairs;      /* supernodes with at least this many entries of S in
                                C x C are processed by a whole CTA; 0 = default 2048   */
+    int64_t ninv_index_bytes; /* device memory the gather form of NInv may hold (its
+                               index of the series pattern, built by the first
+                               sinv_ninv of an m): 0 = half of the free memory at
+                               that time, > 0 = this many bytes, < 0 = never (the
+                               hash form runs, with no index)                        */
 } sinv_symbolic_opts;
 
 /* Symbolic analysis (host).  Validates the pattern of L and the pivot layout,
@@ -212,6 +217,8 @@ typedef struct {
     int64_t product_stream;   /* entries of W streamed by the product on S             */
     int64_t selinv_flops;     /* algorithmic flops of one SelInv                        */
     int64_t selinv_bytes;     /* algorithmic bytes of one SelInv (S read once, L in, X out) */
+    int64_t ninv_index_bytes; /* device bytes of the NInv gather index, 0 = hash form  */
+    int64_t product_hits;     /* multiply-adds of the product on S (gather form)        */
 } sinv_stats;
 sinv_status sinv_get_stats(sinv_handle h, sinv_stats *out);
 

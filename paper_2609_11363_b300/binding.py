@@ -43,7 +43,7 @@ class SinvError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("supernode_cap", ctypes.c_int32), ("device", ctypes.c_int32), ("wait_limit", ctypes.c_int64),
-                ("big_pairs", ctypes.c_int64)]
+                ("big_pairs", ctypes.c_int64), ("ninv_index_bytes", ctypes.c_int64)]
 
 
 class _KTime(ctypes.Structure):
@@ -54,7 +54,8 @@ class _Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("n", "nnz_L", "nnz_S_lo", "n_blocks", "n_2x2", "n_supernodes",
                                               "n_levels", "max_c", "hit_pairs", "max_width", "nnz_W")] + [
         ("ninv_m", ctypes.c_int32), ("pad", ctypes.c_int32), ("horner_products", ctypes.c_int64),
-        ("product_stream", ctypes.c_int64), ("selinv_flops", ctypes.c_int64), ("selinv_bytes", ctypes.c_int64)]
+        ("product_stream", ctypes.c_int64), ("selinv_flops", ctypes.c_int64), ("selinv_bytes", ctypes.c_int64),
+        ("ninv_index_bytes", ctypes.c_int64), ("product_hits", ctypes.c_int64)]
 
 
 def lib_path() -> str:
@@ -253,10 +254,10 @@ class Handle:
     """
 
     def __init__(self, n, L_rowptr, L_col, pivot_start, supernode_cap=16, device=0, wait_limit=0, big_pairs=0,
-                 _batch=None):
+                 ninv_index_bytes=0, _batch=None):
         self._lib = load_library()
         self._h = ctypes.c_void_p()
-        opts = _Opts(int(supernode_cap), int(device), int(wait_limit), int(big_pairs))
+        opts = _Opts(int(supernode_cap), int(device), int(wait_limit), int(big_pairs), int(ninv_index_bytes))
         self.device = torch.device("cuda", int(device)) if int(device) >= 0 else None
         if _batch is None:
             self.n = int(n)

@@ -27,6 +27,7 @@
 #include <algorithm>
 
 #include "device.cuh"
+#include "hash.cuh"
 #include "kernels.h"
 
 namespace sinv {
@@ -40,38 +41,6 @@ constexpr int kEnt = 2730;                    // most table entries kept in shar
 constexpr int kUnroll = 8;                    // column entries per lane with loads in flight
 constexpr int32_t kRowMask = 0x7FFFFFFF;      // row index bits of a pattern entry
 constexpr int32_t kTwoFlag = (int32_t)0x80000000u;  // set when the row belongs to a 2x2 block of D
-
-__device__ __forceinline__ uint32_t hash_row(int32_t r, uint32_t mask) {
-    return ((uint32_t)r * 2654435761u) & mask;
-}
-
-// insert r (if absent) and return its slot
-__device__ __forceinline__ uint32_t table_insert(int32_t* keys, uint32_t mask, int32_t r) {
-    uint32_t h = hash_row(r, mask);
-    for (;;) {
-        int32_t old = atomicCAS(keys + h, -1, r);
-        if (old == -1 || old == r) return h;
-        h = (h + 1) & mask;
-    }
-}
-
-// slot of r, or -1 when r is not in the table
-__device__ __forceinline__ int32_t table_find(const int32_t* keys, uint32_t mask, int32_t r) {
-    uint32_t h = hash_row(r, mask);
-    for (uint32_t probe = 0; probe <= mask; ++probe) {
-        int32_t k = keys[h];
-        if (k == r) return (int32_t)h;
-        if (k == -1) return -1;
-        h = (h + 1) & mask;
-    }
-    return -1;
-}
-
-__host__ __device__ __forceinline__ uint32_t table_mask(int64_t entries) {
-    uint32_t s = 16;
-    while ((int64_t)s < 2 * entries) s <<= 1;
-    return s - 1;
-}
 
 template <class T>
 __global__ void ninv_init(const int64_t* __restrict__ Wcp, T* __restrict__ W, int64_t n) {
@@ -350,6 +319,10 @@ static cudaError_t ninv_run(const NinvArgs& a, void* work, double* N_out, double
     }
     product(a.m, N_stack ? N_stack + (int64_t)a.m * a.nnzS : N_out, tickets + 63);
     return cudaGetLastError();
+}
+
+void ninv_dinv_launch(const NinvArgs& a, double* dr, double* dp, int32_t* part, cudaStream_t st) {
+    ninv_dinv<<<a.num_sms * 4, 256, 0, st>>>(a.n, a.dpos, a.pstart, a.Dval, dr, dp, part, a.status);
 }
 
 cudaError_t ninv_launch(const NinvArgs& a, int prec, void* work, double* N_out, cudaStream_t st, double* N_stack) {

@@ -87,23 +87,65 @@ def test_selinv_fp32(case):
     assert normwise(out.cpu().numpy(), G) <= 1e-5, name
 
 
+# NInv runs in gather form (index built on the first call, the default) or in hash
+# form (no index); both are checked against the oracle
+FORMS = {"gather": 0, "hash": -1}
+
+
+def _check_form(h, form):
+    st = h.stats()
+    if form == "gather":
+        assert st["ninv_index_bytes"] > 0 and st["product_hits"] > 0
+    else:
+        assert st["ninv_index_bytes"] == 0
+
+
+@pytest.mark.parametrize("form", sorted(FORMS))
 @pytest.mark.parametrize("mm", [0, 1, 3])
-def test_ninv_fp64(case, mm):
+def test_ninv_fp64(case, mm, form):
     name, f, m, S, G, N = case
     Nr = N if mm == m else oracle.ninv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, mm, S)
-    h = _handle(f)
+    h = _handle(f, ninv_index_bytes=FORMS[form])
     out = h.ninv(_dev(f.L_val), _dev(f.D_packed), mm, "fp64")
     h.sync_status()
+    _check_form(h, form)
     err = sel_rel_err(out.cpu().numpy(), Nr, *S)
-    assert err <= TOL64, (name, mm, err)
+    assert err <= TOL64, (name, mm, form, err)
 
 
-def test_ninv_fp32(case):
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_ninv_fp32(case, form):
     name, f, m, S, G, N = case
-    h = _handle(f)
+    h = _handle(f, ninv_index_bytes=FORMS[form])
     out = h.ninv(_dev(f.L_val), _dev(f.D_packed), m, "fp32")
     h.sync_status()
+    _check_form(h, form)
     assert normwise(out.cpu().numpy(), N) <= 1e-5, name
+
+
+def test_ninv_gather_repeat_and_m_change(case):
+    """Numeric reruns on one index are bit-identical; a new m rebuilds the index."""
+    name, f, m, S, G, N = case
+    h = _handle(f)
+    Lv, Dv = _dev(f.L_val), _dev(f.D_packed)
+    a = h.ninv(Lv, Dv, m).cpu().numpy()
+    b = h.ninv(Lv, Dv, m).cpu().numpy()
+    c = h.ninv(Lv, Dv, 1).cpu().numpy()
+    d = h.ninv(Lv, Dv, m).cpu().numpy()
+    h.sync_status()
+    assert np.array_equal(a, b) and np.array_equal(a, d)
+    N1 = oracle.ninv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, 1, S)
+    assert sel_rel_err(c, N1, *S) <= TOL64 and sel_rel_err(a, N, *S) <= TOL64
+
+
+def test_ninv_index_over_budget_runs_hash_form():
+    f = plant_2x2(lap2d_32().factors, 0.3, 11)
+    S, G, N = _oracle_all(f, 3)
+    h = _handle(f, ninv_index_bytes=1)
+    out = h.ninv(_dev(f.L_val), _dev(f.D_packed), 3)
+    h.sync_status()
+    assert h.stats()["ninv_index_bytes"] == 0
+    assert sel_rel_err(out.cpu().numpy(), N, *S) <= TOL64
 
 
 @pytest.mark.parametrize("eps_rule", ["rel", "inf", "neg", "zero"])
@@ -194,6 +236,7 @@ def test_full_size_diff3d_64():
     assert sel_rel_err(out.cpu().numpy(), G, *S) <= TOL64
     N = h.ninv(Lv, Dv, w.m, "fp64").cpu().numpy()
     h.sync_status()
+    assert h.stats()["ninv_index_bytes"] > 0  # the benchmark's form
     rng = np.random.default_rng(0)
     idx = rng.choice(len(S[1]), 64, replace=False)
     rows = np.repeat(np.arange(f.n), np.diff(S[0]))
