@@ -144,13 +144,13 @@ def kernel_rooflines(trace, st, m, k, nS_lo, prec, peaks, steps):
         "mix": ("hbm", 32.0 * nS_lo, "byte"),
     }
     if prec == "fp64":
-        work["ninv_gather_horner"] = ("alu", 2.0 * horner, "flop")
-        work["ninv_gather_product"] = ("alu", 2.0 * st["product_hits"], "flop")
+        work["ninv_map_horner"] = ("alu", 2.0 * horner, "flop")
+        work["ninv_map_product"] = ("alu", 2.0 * st["product_hits"], "flop")
     else:
-        # FP32 gather form: a 4-byte index word and a 4-byte value per product, the
-        # targets written once (Horner); two 4-byte values per product word
-        work["ninv_gather_horner"] = ("hbm", 8.0 * horner + 4.0 * st["nnz_W"], "byte")
-        work["ninv_gather_product"] = ("hbm", 12.0 * st["product_hits"] + 8.0 * nS_lo, "byte")
+        # FP32 map form streams a 2-byte map entry and a 4-byte value per product and
+        # writes its targets (Horner); per product-map entry the same, plus N (8 B)
+        work["ninv_map_horner"] = ("hbm", 6.0 * horner + 4.0 * st["nnz_W"], "byte")
+        work["ninv_map_product"] = ("hbm", 6.0 * st["product_stream"] + 8.0 * nS_lo, "byte")
     out = {}
     for name, (launches, total_ms) in trace.items():
         per_launch_ms = total_ms / launches

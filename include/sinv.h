@@ -69,11 +69,13 @@ typedef struct {
     int64_t wait_limit;     /* polls before a device wait gives up; 0 = default       */
     int64_t big_pairs;      /* supernodes with at least this many entries of S in
                                C x C are processed by a whole CTA; 0 = default 2048   */
-    int64_t ninv_index_bytes; /* device memory the gather form of NInv may hold (its
-                               index of the series pattern, built by the first
-                               sinv_ninv of an m): 0 = half of the free memory at
-                               that time, > 0 = this many bytes, < 0 = never (the
-                               hash form runs, with no index)                        */
+    int64_t ninv_index_bytes; /* device memory the map form of NInv may hold (the
+                               positions of every product in the series pattern,
+                               built by the first sinv_ninv of an m): 0 = half of
+                               the free memory at that time, > 0 = this many bytes,
+                               < 0 = never.  Without maps (also when a column of the
+                               pattern is too long for them) the hash form runs:
+                               same results, slower                                  */
 } sinv_symbolic_opts;
 
 /* Symbolic analysis (host).  Validates the pattern of L and the pivot layout,
@@ -125,7 +127,13 @@ sinv_status sinv_selinv(sinv_handle h, const double *L_val, const double *D_val,
 /* NInv on S (Section 2.2, Eqs. (6) and (8)): W = sum_{t=0}^{m} E^t with
  * L = I - E, by m Horner steps W <- I + E W on the fixed pattern of the
  * truncated series, then N = W^T D^{-1} W evaluated on S only.  0 <= m <= 30.
- *   L_val, D_val, N_S [|S_lo|]: device.  m > 30: SINV_ERR_UNSUPPORTED. */
+ *   L_val, D_val, N_S [|S_lo|]: device.  m > 30: SINV_ERR_UNSUPPORTED.
+ * The first call for an m builds that pattern (host) and its position maps
+ * (device, see sinv_symbolic_opts.ninv_index_bytes) and synchronises the
+ * stream; later calls with the same m only launch kernels (make the first one
+ * before capturing a stream into a CUDA graph).  Sums run in an order that can
+ * change between calls (shared-memory atomics), so repeated calls agree to
+ * rounding, not bit for bit. */
 sinv_status sinv_ninv(sinv_handle h, const double *L_val, const double *D_val, int m,
                       sinv_precision prec, double *N_S, void *stream);
 
@@ -217,8 +225,10 @@ typedef struct {
     int64_t product_stream;   /* entries of W streamed by the product on S             */
     int64_t selinv_flops;     /* algorithmic flops of one SelInv                        */
     int64_t selinv_bytes;     /* algorithmic bytes of one SelInv (S read once, L in, X out) */
-    int64_t ninv_index_bytes; /* device bytes of the NInv gather index, 0 = hash form  */
-    int64_t product_hits;     /* multiply-adds of the product on S (gather form)        */
+    int64_t ninv_index_bytes; /* device bytes of the NInv position maps, 0 = hash form */
+    int64_t product_hits;     /* rows shared by W[:, i] and (D^{-1} W)[:, j] over the
+                                 entries (i, j) of S_lo: the multiply-adds of the
+                                 product (known once the maps exist, else 0)           */
 } sinv_stats;
 sinv_status sinv_get_stats(sinv_handle h, sinv_stats *out);
 

@@ -132,11 +132,11 @@ struct sinv_handle_s {
     int64_t* dWcp = nullptr;
     int32_t* dWr = nullptr;
     int32_t* dgrp = nullptr;
-    // gather form of NInv: index of the current pattern (built at the first call of an m)
-    NinvIndex X;
+    // map form of NInv: maps of the current pattern (built by the first call of an m)
+    NinvMaps X;
     int64_t index_budget = 0;   // < 0: never; 0: half the free device memory; > 0: bytes
     int index_tried_m = -1;     // m for which the index was built or found not to fit
-    std::string index_note;     // why the hash form runs (empty when the index is used)
+    std::string index_note;     // why the hash form runs (empty when the maps are used)
     std::string last_error;
 };
 
@@ -167,7 +167,7 @@ void free_all(sinv_handle h) {
                     h->dWr, h->dgrp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    ninv_index_free(h->X);
+    ninv_maps_free(h->X);
 }
 
 sinv_status ensure_work(sinv_handle h, size_t bytes) {
@@ -309,7 +309,7 @@ sinv_status sinv_symbolic(int64_t n, const int64_t* L_rowptr, const int32_t* L_c
         return cuda_fail(h, e, "device state");
     }
     if ((e = selinv_configure()) != cudaSuccess || (e = ninv_configure()) != cudaSuccess ||
-        (e = ninv_index_configure()) != cudaSuccess) {
+        (e = ninv_maps_configure()) != cudaSuccess) {
         *out = h;
         return cuda_fail(h, e, "kernel attributes");
     }
@@ -433,7 +433,7 @@ sinv_status sinv_get_stats(sinv_handle h, sinv_stats* s) {
     s->selinv_flops = P.selinv_flops;
     s->selinv_bytes = P.selinv_bytes;
     s->ninv_index_bytes = h->X.ready ? h->X.bytes : 0;
-    s->product_hits = h->X.ready ? h->X.nhits : 0;
+    s->product_hits = h->X.ready ? h->X.hits : 0;
     return SINV_OK;
 }
 
@@ -537,7 +537,7 @@ static sinv_status ninv_common(sinv_handle h, const double* L_val, const double*
             set_err(h, err);
             return SINV_ERR_UNSUPPORTED;
         }
-        ninv_index_free(h->X);
+        ninv_maps_free(h->X);
         h->index_tried_m = -1;
         if (h->dWcp) cudaFree(h->dWcp);
         if (h->dWr) cudaFree(h->dWr);
@@ -583,19 +583,19 @@ static sinv_status ninv_common(sinv_handle h, const double* L_val, const double*
                 budget = (int64_t)(free_b / 2);
             }
             try {
-                h->index_note = ninv_index_build(a, P, h->W, budget, h->X, st, e);
+                h->index_note = ninv_maps_build(a, P, h->W, budget, h->X, st, e);
             } catch (const std::bad_alloc&) {
-                ninv_index_free(h->X);
-                h->index_note = "host allocation failed building the index";
+                ninv_maps_free(h->X);
+                h->index_note = "host allocation failed building the maps";
             }
             if (e != cudaSuccess && e != cudaErrorMemoryAllocation) return cuda_fail(h, e, "NInv index");
             cudaGetLastError();  // an allocation that did not fit leaves the hash form in use
         }
     }
     if (h->X.ready) {
-        sinv_status s = ensure_work(h, ninv_gather_work_bytes(a, p));
+        sinv_status s = ensure_work(h, ninv_map_work_bytes(a, p));
         if (s != SINV_OK) return s;
-        if ((e = ninv_gather_launch(a, h->X, p, h->dwork, N_S, st, N_stack)) != cudaSuccess)
+        if ((e = ninv_map_launch(a, h->X, p, h->dwork, N_S, st, N_stack)) != cudaSuccess)
             return cuda_fail(h, e, "ninv launch");
         return SINV_OK;
     }

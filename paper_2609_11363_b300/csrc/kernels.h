@@ -87,34 +87,27 @@ struct NinvArgs {
     int32_t num_sms;
     int32_t* status;
 };
-// Gather form of NInv (ninv_index.cu): index lists built once per pattern and m.
-constexpr int kIdxEnt = 5440;  // longest column of P_W the index build handles
-struct NinvIndex {
+constexpr int kIdxEnt = 5440;  // longest column of P_W (with its partner rows) the maps handle
+// Map form of NInv (ninv_map.cu): per-entry positions resolved once per pattern and m.
+struct NinvMaps {
     bool ready = false;
     int m = -1;
-    int64_t nslices = 0;        // slices of 32 targets (all columns)
-    int64_t nsrc = 0;           // source words (with the padding of the slices)
-    int64_t nhits = 0;          // product words
-    int64_t bytes = 0;          // device memory held
-    int64_t* cs = nullptr;      // n+1: first slice of every column
-    int64_t* sb = nullptr;      // nslices+1: first source word of every slice
-    uint16_t* tloc = nullptr;   // 32 per slice: local position of the lane's target in its column (0xFFFF: none)
-    uint8_t* scnt = nullptr;    // m x (32 per slice): sources of the lane's target used by step t = 1..m
-    uint32_t* src = nullptr;    // source words  slot << 24 | offset in column k
-    int32_t* Srow = nullptr;    // row of every entry of S_lo
-    int64_t* hoff = nullptr;    // |S_lo|+1: first product word of every entry
-    uint32_t* hits = nullptr;   // product words  pos_i | pos_j << 16 | partner << 31
+    int64_t nmap_h = 0, nmap_p = 0, bytes = 0;
+    int64_t hits = 0;           // map entries with y nonzero (multiply-adds of the product)
+    int64_t* moff = nullptr;    // nnz_L+1: start of the Horner map of every entry of E (CSC order)
+    uint16_t* hmap = nullptr;   // position in column j of each row of column k (powers <= m-1)
+    int64_t* poff = nullptr;    // |S_lo|+1: start of the product map of every entry of S_lo
+    uint16_t* pmap = nullptr;   // y-table position of each row of column i (0xFFFF: y is zero)
+    uint16_t* ypart = nullptr;  // nnz_W: y-table position of the partner row (2x2 rows only)
+    int32_t* ynx = nullptr;     // n: extra y-table positions (partner rows outside the column)
 };
-cudaError_t ninv_index_configure();
-// Builds x for the pattern of a (m = a.m).  Returns an empty string on success; else
-// the reason the gather form is not used (x is then empty; err holds a CUDA error,
-// if one caused it).  budget > 0 caps the device bytes the index may hold.
-std::string ninv_index_build(const NinvArgs& a, const HostPlan& P, const NinvPlan& W, int64_t budget,
-                             NinvIndex& x, cudaStream_t st, cudaError_t& err);
-void ninv_index_free(NinvIndex& x);
-size_t ninv_gather_work_bytes(const NinvArgs& a, int prec);
-cudaError_t ninv_gather_launch(const NinvArgs& a, const NinvIndex& x, int prec, void* work, double* N_out,
-                               cudaStream_t st, double* N_stack = nullptr);
+cudaError_t ninv_maps_configure();
+std::string ninv_maps_build(const NinvArgs& a, const HostPlan& P, const NinvPlan& W, int64_t budget,
+                            NinvMaps& x, cudaStream_t st, cudaError_t& err);
+void ninv_maps_free(NinvMaps& x);
+size_t ninv_map_work_bytes(const NinvArgs& a, int prec);
+cudaError_t ninv_map_launch(const NinvArgs& a, const NinvMaps& x, int prec, void* work, double* N_out,
+                            cudaStream_t st, double* N_stack = nullptr);
 // D^{-1} per row (ninv.cu): diagonal, off-diagonal of its 2x2 block, partner row (-1: 1x1)
 void ninv_dinv_launch(const NinvArgs& a, double* dr, double* dp, int32_t* part, cudaStream_t st);
 

@@ -1,0 +1,455 @@
+// NInv in map form (Section 2.2, Eqs. (6) and (8)): the arithmetic of the hash
+// form in ninv.cu, with every hash search replaced by a position resolved once
+// per pattern and m.
+//
+// Horner step W_t[:, j] = e_j + sum_{k in struct(j)} E_kj W_{t-1}[:, k].  One CTA
+// owns column j and accumulates it in shared memory, indexed by the local
+// position of a row in column j.  For every entry E_kj (an entry q of L) the map
+// hmap[moff[q] + e] holds the position in column j of the e-th row of column k;
+// column k's rows of powers <= t - 1 are a prefix of it, so step t streams the
+// prefix of the map beside the prefix of W_{t-1}[:, k] (both coalesced) and adds
+// E_kj W_{t-1}[r, k] at the mapped position with a shared-memory atomic.
+//
+// Product on S: N_ij = sum_r W_ri y_r with y = (D^{-1} W)[:, j].  One CTA owns
+// column j and tabulates y in shared memory: positions [0, |col j|) are the rows
+// of column j, then one extra position for every partner row (2x2 block of D)
+// that is not in column j.  For every entry (i, j) of S_lo the map
+// pmap[poff[e] + f] holds the table position of the f-th row of column i (or
+// 0xFFFF when y is zero there); a warp streams column i with its map and sums
+// W_ri y_r.  ypart holds, for the rows of 2x2 blocks, the table position of the
+// partner row inside their own column's table.
+//
+// The maps are built on the GPU from the same shared-memory tables as the hash
+// form; they need |col j| + extras <= kIdxEnt for every column.
+#include <algorithm>
+#include <vector>
+
+#include "device.cuh"
+#include "hash.cuh"
+#include "kernels.h"
+#include "plan.h"
+
+namespace sinv {
+
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+constexpr int kIdxSlots = 8192;
+constexpr int kUnrollM = 8;
+constexpr int32_t kRowMask = 0x7FFFFFFF;
+constexpr int32_t kTwoFlag = (int32_t)0x80000000u;
+constexpr uint16_t kNone = 0xFFFF;
+
+__device__ __forceinline__ int64_t take_column(int32_t* ticket, int32_t* s_j) {
+    if (threadIdx.x == 0) *s_j = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int64_t j = *s_j;
+    __syncthreads();
+    return j;
+}
+
+struct TableSmem {
+    int32_t keys[kIdxSlots];
+    uint16_t loc[kIdxSlots];
+};
+
+// rows of column j -> local position
+__device__ __forceinline__ void column_table(const NinvArgs& a, int64_t base, int32_t nj, TableSmem& t) {
+    for (int s = threadIdx.x; s < kIdxSlots; s += kThreads) t.keys[s] = -1;
+    __syncthreads();
+    for (int32_t e = threadIdx.x; e < nj; e += kThreads)
+        t.loc[table_insert(t.keys, kIdxSlots - 1, a.Wr[base + e] & kRowMask)] = (uint16_t)e;
+    __syncthreads();
+}
+
+__device__ __forceinline__ uint16_t lookup(const TableSmem& t, int32_t r) {
+    const int32_t h = table_find(t.keys, kIdxSlots - 1, r);
+    return h < 0 ? kNone : t.loc[h];
+}
+
+// Horner maps: hmap[moff[q] + e] = position in column j of row e of column k (e over
+// the powers 0..m-1 of column k), for every entry q = (k, j) of E.
+__global__ void __launch_bounds__(kThreads) hmap_build(NinvArgs a, NinvMaps x, int32_t* ticket) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TableSmem& tb = *reinterpret_cast<TableSmem*>(smem_raw);
+    __shared__ int32_t s_j;
+    const int G = a.m + 2;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (;;) {
+        const int64_t j = take_column(ticket, &s_j);
+        if (j >= a.n) break;
+        const int64_t base = a.Wcp[j];
+        column_table(a, base, (int32_t)(a.Wcp[j + 1] - base), tb);
+        for (int64_t q = a.Lcp[j] + wid; q < a.Lcp[j + 1]; q += kWarps) {
+            const int32_t k = a.Lri[q];
+            const int64_t kb = a.Wcp[k];
+            const int32_t nk = a.grp[(int64_t)k * G + a.m];
+            uint16_t* mp = x.hmap + x.moff[q];
+            for (int32_t e = lane; e < nk; e += 32) {
+                const uint16_t p = lookup(tb, a.Wr[kb + e] & kRowMask);
+                if (p == kNone) set_status(a.status, ST_INTERNAL);
+                mp[e] = p;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// y tables and product maps.
+__global__ void __launch_bounds__(kThreads) pmap_build(NinvArgs a, NinvMaps x, const int32_t* __restrict__ part,
+                                                       int32_t* ticket, unsigned long long* hits) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TableSmem& tb = *reinterpret_cast<TableSmem*>(smem_raw);
+    __shared__ int32_t s_j, s_extra;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long nhit = 0;
+    for (;;) {
+        const int64_t j = take_column(ticket, &s_j);
+        if (j >= a.n) break;
+        const int64_t base = a.Wcp[j];
+        const int32_t nj = (int32_t)(a.Wcp[j + 1] - base);
+        if (threadIdx.x == 0) s_extra = 0;
+        column_table(a, base, nj, tb);
+        // partner rows: in the column, or an extra position (each row has one partner,
+        // so every extra row is inserted by a single thread)
+        for (int32_t e = threadIdx.x; e < nj; e += kThreads) {
+            const int32_t rf = a.Wr[base + e];
+            uint16_t pp = kNone;
+            if (rf & kTwoFlag) {
+                const int32_t p = part[rf & kRowMask];
+                const int32_t h = table_find(tb.keys, kIdxSlots - 1, p);
+                if (h >= 0) {
+                    pp = tb.loc[h];
+                } else {
+                    const int32_t slot = (int32_t)table_insert(tb.keys, kIdxSlots - 1, p);
+                    pp = (uint16_t)(nj + atomicAdd(&s_extra, 1));
+                    tb.loc[slot] = pp;
+                }
+            }
+            x.ypart[base + e] = pp;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) x.ynx[j] = s_extra;
+        const bool two_first = a.pstart[j] != 0 && j + 1 < a.n && a.pstart[j + 1] == 0;
+        const int64_t q0 = a.Lcp[j];
+        const int64_t cnt = (a.Lcp[j + 1] - q0) + 1 + (two_first ? 1 : 0);
+        for (int64_t e = wid; e < cnt; e += kWarps) {
+            int64_t i, spos;
+            if (e == 0) {
+                i = j;
+                spos = a.Srp[j + 1] - 1;
+            } else if (two_first && e == 1) {
+                i = j + 1;
+                spos = a.Srp[j + 2] - 2;
+            } else {
+                const int64_t q = q0 + e - 1 - (two_first ? 1 : 0);
+                i = a.Lri[q];
+                spos = a.Srp[i] + ((int64_t)a.Lcsr[q] - a.Lrp[i]);
+            }
+            const int64_t ib = a.Wcp[i];
+            const int32_t ni = (int32_t)(a.Wcp[i + 1] - ib);
+            uint16_t* mp = x.pmap + x.poff[spos];
+            for (int32_t f = lane; f < ni; f += 32) {
+                const uint16_t p = lookup(tb, a.Wr[ib + f] & kRowMask);
+                mp[f] = p;
+                nhit += p != kNone ? 1 : 0;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nhit += __shfl_xor_sync(0xffffffffu, nhit, o);
+    if (lane == 0 && nhit) atomicAdd(hits, nhit);
+}
+
+__global__ void mmap_partner(int64_t n, const int8_t* __restrict__ pstart, int32_t* __restrict__ part) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const bool first = pstart[r] != 0;
+        const bool two = first ? (r + 1 < n && pstart[r + 1] == 0) : true;
+        part[r] = two ? (int32_t)(first ? r + 1 : r - 1) : -1;
+    }
+}
+
+// ---- numeric kernels ----
+
+template <class T>
+__device__ __forceinline__ T fma_m(T a, T b, T c);
+template <>
+__device__ __forceinline__ double fma_m<double>(double a, double b, double c) { return fma(a, b, c); }
+template <>
+__device__ __forceinline__ float fma_m<float>(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) hm_step(NinvArgs a, NinvMaps x, int t, const T* __restrict__ Wp,
+                                                    T* __restrict__ Wn, int32_t* ticket) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* acc = reinterpret_cast<T*>(smem_raw);
+    __shared__ int32_t s_j;
+    const int G = a.m + 2;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (;;) {
+        const int64_t j = take_column(ticket, &s_j);
+        if (j >= a.n) break;
+        const int64_t base = a.Wcp[j];
+        const int32_t nt = a.grp[j * G + t + 1];  // rows of powers 0..t
+        for (int32_t e = threadIdx.x; e < nt; e += kThreads) acc[e] = T(0);
+        __syncthreads();
+        for (int64_t q = a.Lcp[j] + wid; q < a.Lcp[j + 1]; q += kWarps) {
+            const int32_t k = a.Lri[q];
+            const T ekj = T(-a.Lval[a.Lcsr[q]]);
+            const T* __restrict__ wk = Wp + a.Wcp[k];
+            const uint16_t* __restrict__ mp = x.hmap + x.moff[q];
+            const int32_t nk = a.grp[(int64_t)k * G + t];  // rows of powers 0..t-1
+            for (int32_t e0 = 0; e0 < nk; e0 += 32 * kUnrollM) {
+                uint16_t p[kUnrollM];
+                T v[kUnrollM];
+#pragma unroll
+                for (int u = 0; u < kUnrollM; ++u) {
+                    const int32_t e = e0 + u * 32 + lane;
+                    p[u] = e < nk ? mp[e] : kNone;
+                    v[u] = e < nk ? wk[e] : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < kUnrollM; ++u)
+                    if (p[u] != kNone) atomicAdd(acc + p[u], ekj * v[u]);
+            }
+        }
+        __syncthreads();
+        for (int32_t e = threadIdx.x; e < nt; e += kThreads) Wn[base + e] = acc[e] + (e == 0 ? T(1) : T(0));
+        __syncthreads();
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) pm_product(NinvArgs a, NinvMaps x, int tlim, const T* __restrict__ W,
+                                                       const double* __restrict__ dr, const double* __restrict__ dp,
+                                                       double* __restrict__ N, int32_t* ticket) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* y = reinterpret_cast<T*>(smem_raw);
+    __shared__ int32_t s_j;
+    const int G = a.m + 2;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (;;) {
+        const int64_t j = take_column(ticket, &s_j);
+        if (j >= a.n) break;
+        const int64_t base = a.Wcp[j];
+        const int32_t ny = (int32_t)(a.Wcp[j + 1] - base) + x.ynx[j];
+        const int32_t nt = a.grp[j * G + tlim + 1];
+        for (int32_t e = threadIdx.x; e < ny; e += kThreads) y[e] = T(0);
+        __syncthreads();
+        // y = D^{-1} W[:, j] on the rows of powers <= tlim: two terms at most per position,
+        // so the atomics give the same sum in any order
+        for (int32_t e = threadIdx.x; e < nt; e += kThreads) {
+            const int32_t rf = a.Wr[base + e];
+            const int32_t r = rf & kRowMask;
+            const double w = (double)W[base + e];
+            atomicAdd(y + e, T(dr[r] * w));
+            if (rf & kTwoFlag) atomicAdd(y + x.ypart[base + e], T(dp[r] * w));
+        }
+        __syncthreads();
+        const bool two_first = a.pstart[j] != 0 && j + 1 < a.n && a.pstart[j + 1] == 0;
+        const int64_t q0 = a.Lcp[j];
+        const int64_t cnt = (a.Lcp[j + 1] - q0) + 1 + (two_first ? 1 : 0);
+        for (int64_t e = wid; e < cnt; e += kWarps) {
+            int64_t i, spos;
+            if (e == 0) {
+                i = j;
+                spos = a.Srp[j + 1] - 1;
+            } else if (two_first && e == 1) {
+                i = j + 1;
+                spos = a.Srp[j + 2] - 2;
+            } else {
+                const int64_t q = q0 + e - 1 - (two_first ? 1 : 0);
+                i = a.Lri[q];
+                spos = a.Srp[i] + ((int64_t)a.Lcsr[q] - a.Lrp[i]);
+            }
+            const T* __restrict__ wi = W + a.Wcp[i];
+            const uint16_t* __restrict__ mp = x.pmap + x.poff[spos];
+            const int32_t ni = a.grp[i * G + tlim + 1];
+            T s = T(0);
+            for (int32_t f0 = 0; f0 < ni; f0 += 32 * kUnrollM) {
+                uint16_t p[kUnrollM];
+                T v[kUnrollM];
+#pragma unroll
+                for (int u = 0; u < kUnrollM; ++u) {
+                    const int32_t f = f0 + u * 32 + lane;
+                    p[u] = f < ni ? mp[f] : kNone;
+                    v[u] = f < ni ? wi[f] : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < kUnrollM; ++u)
+                    if (p[u] != kNone) s = fma_m<T>(v[u], y[p[u]], s);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) N[spos] = (double)s;
+        }
+        __syncthreads();
+    }
+}
+
+template <class T>
+__global__ void hm_init(const int64_t* __restrict__ Wcp, T* __restrict__ W, int64_t n) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        W[Wcp[j]] = T(1);
+}
+
+constexpr size_t kTableSmem = sizeof(TableSmem);
+template <class T>
+constexpr size_t map_smem() { return (size_t)kIdxEnt * sizeof(T); }
+
+template <class T>
+cudaError_t map_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N_out, double* N_stack,
+                    cudaStream_t st) {
+    char* p = reinterpret_cast<char*>(work);
+    auto take = [&](size_t bytes) {
+        char* r = p;
+        p += (bytes + 255) & ~(size_t)255;
+        return r;
+    };
+    T* W0 = reinterpret_cast<T*>(take((size_t)a.nnzW * sizeof(T)));
+    T* W1 = reinterpret_cast<T*>(take((size_t)a.nnzW * sizeof(T)));
+    double* dr = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));
+    double* dp = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));
+    int32_t* part = reinterpret_cast<int32_t*>(take((size_t)a.n * sizeof(int32_t)));
+    int32_t* tickets = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 64));
+    cudaError_t e = cudaMemsetAsync(tickets, 0, sizeof(int32_t) * 64, st);
+    if (e != cudaSuccess) return e;
+    trace_begin("ninv_dinv", st);
+    ninv_dinv_launch(a, dr, dp, part, st);
+    trace_end(st);
+    trace_begin("ninv_init", st);
+    hm_init<T><<<a.num_sms * 4, 256, 0, st>>>(a.Wcp, W0, a.n);
+    trace_end(st);
+    const int grid = a.num_sms * 4;
+    T* cur = W0;
+    T* nxt = W1;
+    auto product = [&](int t, double* out, int32_t* tk) {
+        trace_begin("ninv_map_product", st);
+        pm_product<T><<<grid, kThreads, map_smem<T>(), st>>>(a, x, t, cur, dr, dp, out, tk);
+        trace_end(st);
+    };
+    if (N_stack) product(0, N_stack, tickets + 62 - a.m);
+    for (int t = 1; t <= a.m; ++t) {
+        trace_begin("ninv_map_horner", st);
+        hm_step<T><<<grid, kThreads, map_smem<T>(), st>>>(a, x, t, cur, nxt, tickets + t);
+        trace_end(st);
+        std::swap(cur, nxt);
+        if (N_stack && t < a.m) product(t, N_stack + (int64_t)t * a.nnzS, tickets + 62 - a.m + t);
+    }
+    product(a.m, N_stack ? N_stack + (int64_t)a.m * a.nnzS : N_out, tickets + 63);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t ninv_map_work_bytes(const NinvArgs& a, int prec) {
+    const size_t ts = prec == 0 ? sizeof(double) : sizeof(float);
+    return 2 * ((size_t)a.nnzW * ts + 256) + (size_t)a.n * (2 * sizeof(double) + sizeof(int32_t)) + 3 * 256 +
+           sizeof(int32_t) * 64 + 256 + 4096;
+}
+
+cudaError_t ninv_map_launch(const NinvArgs& a, const NinvMaps& x, int prec, void* work, double* N_out,
+                            cudaStream_t st, double* N_stack) {
+    if (a.n == 0) return cudaSuccess;
+    if (prec == 0) return map_run<double>(a, x, work, N_out, N_stack, st);
+    return map_run<float>(a, x, work, N_out, N_stack, st);
+}
+
+void ninv_maps_free(NinvMaps& x) {
+    void* ptrs[] = {x.moff, x.hmap, x.poff, x.pmap, x.ypart, x.ynx};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    x = NinvMaps();
+}
+
+cudaError_t ninv_maps_configure() {
+    cudaError_t e;
+    const void* fs[] = {(const void*)hmap_build, (const void*)pmap_build};
+    for (const void* f : fs)
+        if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTableSmem)) !=
+            cudaSuccess)
+            return e;
+    if ((e = cudaFuncSetAttribute(hm_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)map_smem<double>())) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(hm_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)map_smem<float>())) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(pm_product<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)map_smem<double>())) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(pm_product<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)map_smem<float>());
+}
+
+std::string ninv_maps_build(const NinvArgs& a, const HostPlan& P, const NinvPlan& Wp, int64_t budget,
+                            NinvMaps& x, cudaStream_t st, cudaError_t& err) {
+    err = cudaSuccess;
+    ninv_maps_free(x);
+    const int64_t n = a.n;
+    const int G = a.m + 2;
+    // every column with its partner rows must fit the tables: |col j| + 2x2 rows <= kIdxEnt
+    {
+        int64_t worst = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            int64_t c = 0;
+            for (int64_t e = Wp.Wcp[j]; e < Wp.Wcp[j + 1]; ++e) c += (Wp.Wr[e] & kTwoFlag) ? 1 : 0;
+            worst = std::max<int64_t>(worst, Wp.Wcp[j + 1] - Wp.Wcp[j] + c);
+        }
+        if (worst > kIdxEnt) return "a column of the series pattern exceeds the map tables";
+    }
+    std::vector<int64_t> moff(P.nnzL + 1, 0), poff(P.nnzS + 1, 0);
+    for (int64_t q = 0; q < P.nnzL; ++q) moff[q + 1] = moff[q] + Wp.grp[(int64_t)P.Lri[q] * G + a.m];
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t len = Wp.Wcp[i + 1] - Wp.Wcp[i];
+        for (int64_t q = P.Srp[i]; q < P.Srp[i + 1]; ++q) poff[q + 1] = len;
+    }
+    for (int64_t q = 0; q < P.nnzS; ++q) poff[q + 1] += poff[q];
+    const int64_t bytes = (P.nnzL + 1) * 8 + moff[P.nnzL] * 2 + (P.nnzS + 1) * 8 + poff[P.nnzS] * 2 +
+                          a.nnzW * 2 + n * 4;
+    if (budget > 0 && bytes > budget) return "maps exceed the memory budget";
+    auto alloc = [&](void** ptr, size_t b) { return cudaMalloc(ptr, std::max<size_t>(b, 16)); };
+    int32_t* part = nullptr;
+    int32_t* tk = nullptr;  // 8 column tickets, then the hit counter
+    auto fail = [&](cudaError_t e, const char* what) {
+        err = e;
+        if (part) cudaFree(part);
+        if (tk) cudaFree(tk);
+        ninv_maps_free(x);
+        return std::string(what) + ": " + cudaGetErrorString(e);
+    };
+    cudaError_t e;
+    if ((e = alloc((void**)&x.moff, moff.size() * 8)) != cudaSuccess ||
+        (e = alloc((void**)&x.hmap, moff[P.nnzL] * 2)) != cudaSuccess ||
+        (e = alloc((void**)&x.poff, poff.size() * 8)) != cudaSuccess ||
+        (e = alloc((void**)&x.pmap, poff[P.nnzS] * 2)) != cudaSuccess ||
+        (e = alloc((void**)&x.ypart, a.nnzW * 2)) != cudaSuccess ||
+        (e = alloc((void**)&x.ynx, n * 4)) != cudaSuccess || (e = alloc((void**)&part, n * 4)) != cudaSuccess ||
+        (e = alloc((void**)&tk, 64)) != cudaSuccess)
+        return fail(e, "map alloc");
+    if ((e = cudaMemcpyAsync(x.moff, moff.data(), moff.size() * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(x.poff, poff.data(), poff.size() * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(tk, 0, 64, st)) != cudaSuccess)
+        return fail(e, "map upload");
+    const int grid = a.num_sms * 2;
+    mmap_partner<<<a.num_sms * 4, 256, 0, st>>>(n, a.pstart, part);
+    if (a.m > 0) hmap_build<<<grid, kThreads, kTableSmem, st>>>(a, x, tk);
+    unsigned long long* dhits = reinterpret_cast<unsigned long long*>(tk + 8);
+    pmap_build<<<grid, kThreads, kTableSmem, st>>>(a, x, part, tk + 1, dhits);
+    unsigned long long nh = 0;
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&nh, dhits, sizeof(nh), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return fail(e, "map build");
+    x.hits = (int64_t)nh;
+    cudaFree(part);
+    cudaFree(tk);
+    x.m = a.m;
+    x.nmap_h = moff[P.nnzL];
+    x.nmap_p = poff[P.nnzS];
+    x.bytes = bytes;
+    x.ready = true;
+    return std::string();
+}
+
+}  // namespace sinv
