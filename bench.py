@@ -27,7 +27,11 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-METRIC = "selected-inverse entries/s on S (SelInv+NInv+Mix+rank-k step; FP64 rel.err<=1e-10 vs FP64 oracle)"
+METRIC = "selected-inverse entries/s on S at stated rel. error vs FP64 oracle; % roofline"
+# the error each precision form is held to against the FP64 oracle (parity tests)
+STATED_ERROR = {"fp64": "entrywise |x-r| <= 1e-10 (|r| + sqrt|r_ii r_jj|)",
+                "fp32x2": "entrywise |x-r| <= 1e-10 (|r| + sqrt|r_ii r_jj|)",
+                "fp32": "normwise ||x-r||_F <= 1e-5 ||r||_F"}
 # B300: 148 SMs; FP64 2 FMA/clk/SM (4 flop), FP32 128 FMA/clk/SM (256 flop)
 N_SMS = 148
 FP64_FLOP_PER_CLK_SM = 4
@@ -40,7 +44,8 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
+    p.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "fp32x2"],
+                   help="fp32x2: FP64 with the NInv product on S in pairs of floats (FP64-class)")
     p.add_argument("--size", type=int, default=64)
     p.add_argument("--workload", default="diff3d", choices=["diff3d", "batch9pt", "learned"],
                    help="diff3d: the 64^3 step (default); batch9pt: 256 matrices in one graph-captured launch; "
@@ -131,9 +136,10 @@ def kernel_rooflines(trace, st, m, k, nS_lo, prec, peaks, steps):
     """Per kernel: launches per step, mean launch time, algorithmic work per launch and
     the achieved fraction of its bound (see the design notes for the unit counts)."""
     mhz = float(peaks.get("sm_max_mhz", 2032.0))
-    alu_peak = N_SMS * (FP64_FLOP_PER_CLK_SM if prec == "fp64" else FP32_FLOP_PER_CLK_SM) * mhz * 1e6 / 1e12
+    fp64_alu = prec != "fp32"  # fp32x2 keeps SelInv, the Horner steps and the low-rank correction in FP64
+    alu_peak = N_SMS * (FP64_FLOP_PER_CLK_SM if fp64_alu else FP32_FLOP_PER_CLK_SM) * mhz * 1e6 / 1e12
     alu_src = "derived: %d SMs x %d %s flop/clk x %.0f MHz" % (
-        N_SMS, FP64_FLOP_PER_CLK_SM if prec == "fp64" else FP32_FLOP_PER_CLK_SM, prec.upper(), mhz)
+        N_SMS, FP64_FLOP_PER_CLK_SM if fp64_alu else FP32_FLOP_PER_CLK_SM, "FP64" if fp64_alu else "FP32", mhz)
     hbm = float(peaks["hbm_gbs"])
     horner = st["horner_products"] / max(m, 1)  # mean products of one Horner step
     work = {
@@ -143,9 +149,11 @@ def kernel_rooflines(trace, st, m, k, nS_lo, prec, peaks, steps):
         "lowrank": ("alu", 2.0 * k * nS_lo, "flop"),
         "mix": ("hbm", 32.0 * nS_lo, "byte"),
     }
-    if prec == "fp64":
+    if fp64_alu:
         work["ninv_map_horner"] = ("alu", 2.0 * horner, "flop")
         work["ninv_map_product"] = ("alu", 2.0 * st["product_hits"], "flop")
+        # pairs of floats: a 2-byte map entry and an 8-byte pair per streamed row, N written
+        work["ninv_pair_product"] = ("hbm", 10.0 * st["product_stream"] + 8.0 * nS_lo, "byte")
     else:
         # FP32 map form streams a 2-byte map entry and a 4-byte value per product and
         # writes its targets (Horner); per product-map entry the same, plus N (8 B)
@@ -168,6 +176,21 @@ def kernel_rooflines(trace, st, m, k, nS_lo, prec, peaks, steps):
                            peak_source="MEASURED_PEAKS.json hbm_gbs", work_per_launch=units)
         out[name] = row
     return out
+
+
+# DRAM bytes (read + write) per unit of work from one ncu capture of the same kernel
+# build on the 32^3 case of this workload (profiles/ninv_map_kernels_diff3d_32_fp64.md):
+# Horner: 2.596 GB over the 757.9 M products of its 4 steps; product: 1.996 GB over
+# 811.8 M streamed map entries.  Scaled to a launch here by the units it processes.
+DRAM_PER_UNIT = {"ninv_map_horner": 2.596e9 / 757.933257e6, "ninv_map_product": 1.996266e9 / 811.837539e6}
+
+
+def dram_traffic(kernel, prec, st, m):
+    if prec == "fp32" or kernel not in DRAM_PER_UNIT:
+        return None, None
+    units = st["horner_products"] / max(m, 1) if kernel == "ninv_map_horner" else st["product_stream"]
+    return DRAM_PER_UNIT[kernel] * units, ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the FP64 kernel on "
+                                           "the 32^3 case, scaled by the units per launch (estimate)")
 
 
 def run_ours(args, rank, world):
@@ -386,8 +409,9 @@ def main():
         kr = kernel_rooflines(res["trace"], st, res["m"], res["k"], res["nS_lo"], args.prec, peaks, args.steps)
         dom = max(kr, key=lambda x: kr[x]["ms_per_step"])
         d = kr[dom]
+        traffic, traffic_src = dram_traffic(dom, args.prec, st, res["m"])
         roofline = {"kernel": dom, "bound": d.get("bound"), "achieved": d.get("achieved"), "peak": d.get("peak"),
-                    "unit": d.get("unit"), "frac": d.get("frac"), "traffic": None,
+                    "unit": d.get("unit"), "frac": d.get("frac"), "traffic": traffic, "traffic_source": traffic_src,
                     "peak_source": d.get("peak_source"), "ms_per_launch": d["ms_per_launch"],
                     "work_per_launch": d.get("work_per_launch"), "kernels": kr}
         cpu = None
@@ -396,12 +420,13 @@ def main():
         line = {
             "metric": METRIC, "value": res["value"], "unit": "entries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp32x2": "f64+f32x2"}[args.prec],
             "data": "synthetic",
             "config": {"workload": workload_name(args.size, res["f"], res["m"], res["k"]), "n": res["f"].n,
                        "nnz_L": st["nnz_L"], "S_entries": res["nS"], "S_lo": res["nS_lo"], "n_2x2": st["n_2x2"],
                        "supernodes": st["n_supernodes"], "levels": st["n_levels"], "nnz_W": st["nnz_W"],
                        "l2": "flushed between timed steps (512 MB write)", "precision": args.prec,
+                       "stated_rel_error": STATED_ERROR[args.prec],
                        "symbolic_s": res["t_sym"], "ninv_pattern_s": res["t_sym_ninv"],
                        "input_gen_s": res["t_gen"], "peaks": peak_kind,
                        "parallelism": "replicas" if world > 1 else "single"},
@@ -492,15 +517,48 @@ def run_extra(args, rank, world):
         nS = 2 * h.nnz_S - h.n
         total = float(np.sum(ms))
         st = h.stats()
-        line = {"metric": "selected-inverse entries/s on S, batched (SelInv + NInv m=3, FP32 accumulation)",
+        # the same work without batching: one handle per matrix, launched one after another
+        singles = []
+        for b, f in enumerate(fs):
+            lay = h.layout()
+            hb = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start, device=dev.index, **best)
+            Lb = Lv[lay["L"][b]:lay["L"][b + 1]]
+            Db = Dv[lay["D"][b]:lay["D"][b + 1]]
+            Gb = torch.empty(hb.nnz_S, dtype=torch.float64, device=dev)
+            singles.append((hb, Lb, Db, Gb, torch.empty_like(Gb)))
+
+        def loop_step():
+            for hb, Lb, Db, Gb, Nb in singles:
+                hb.selinv(Lb, Db, "fp32", out=Gb)
+                hb.ninv(Lb, Db, 3, "fp32", out=Nb)
+
+        loop_step()
+        torch.cuda.synchronize()
+        ms_loop = []
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            loop_step()
+            e1.record()
+            torch.cuda.synchronize()
+            ms_loop.append(e0.elapsed_time(e1))
+        for hb, *_ in singles:
+            hb.sync_status()
+            hb.close()
+        del singles
+        line = {"metric": METRIC,
                 "value": world * nS * args.steps / (total / 1e3), "unit": "entries/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": "batch9pt: %d 2D 9-point random-weight Laplacians, n ~ U[2048, 65536], "
-                                       "ILDL tau=1e-2, one CUDA graph per step" % args.batch,
+                                       "ILDL tau=1e-2, SelInv + NInv m=3 in FP32, one CUDA graph per step" % args.batch,
+                           "stated_rel_error": STATED_ERROR["fp32"],
                            "matrices": len(fs), "n_total": h.n, "S_entries": nS, "levels": st["n_levels"],
                            "autotuned": best, "autotune_table_ms": [list(r[:3]) for r in table],
+                           "one_handle_per_matrix_ms_per_step": float(np.median(ms_loop)),
                            "autotune_s": t_tune, "input_gen_s": t_gen, "l2": "flushed between timed steps"},
                 "clocks": clk, "gpu_launches": None}
         if rank == 0:
@@ -554,13 +612,14 @@ def run_extra(args, rank, world):
     ms_selinv = timed(lambda: h.selinv(Lv, Dv, "fp64"), args.steps)
     h.sync_status()
     nS = 2 * h.nnz_S - h.n
-    line = {"metric": "selected-inverse entries/s on S, learned NInv->SelInv correction (NInv m=3 + BF16 MLP)",
+    line = {"metric": METRIC,
             "value": nS / (ms_learned / 1e3), "unit": "entries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_learned, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16+f64", "data": "synthetic",
             "config": {"workload": "learned: 3-layer width-64 BF16 MLP trained on 64 seeds of 3D 7-point "
                                    "log-normal diffusion 48^3, applied to %d^3 (n=%d), tau=1e-3, m=3" % (
                                        round(f.n ** (1 / 3)), f.n),
+                       "stated_rel_error": "relative Frobenius error on S against SelInv FP64: reported, not bounded",
                        "train_entries": fit["entries"], "train_steps": fit["steps"], "train_s": fit["seconds"],
                        "err_vs_selinv_ninv": ev["err_ninv"], "err_vs_selinv_learned": ev["err_learned"],
                        "keep_correction": LearnedCorrection.choose([ev]), "selinv_fp64_ms": ms_selinv,

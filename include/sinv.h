@@ -55,8 +55,20 @@ typedef enum {
 /* Arithmetic of a numeric call.  Inputs and outputs stay FP64 in every form. */
 typedef enum {
     SINV_FP64 = 0,      /* native FP64 throughout                                  */
-    SINV_FP32 = 1       /* FP32 products and sums; pivot inverses and the diagonal
+    SINV_FP32 = 1,      /* FP32 products and sums; pivot inverses and the diagonal
                            accumulation of each pivot block in FP64                */
+    SINV_FP32X2 = 2     /* FP64-class results with the NInv product on S run on the
+                           FP32 pipes: every FP64 operand is split into an FP32
+                           high part and an FP32 low part, a product keeps the
+                           high-by-high product exactly plus both cross terms, and
+                           sums carry their rounding error (error-free two-sum).
+                           The other steps, whose sums go through shared-memory
+                           atomics or wait on a dependency chain, run FP64 (so
+                           sinv_selinv and sinv_lowrank_correct treat it as
+                           SINV_FP64, and so does NInv when it runs in hash form).
+                           Values of W or D^{-1}W at or above 2^100 in magnitude
+                           are reported as SINV_ERR_UNSUPPORTED by the next
+                           sinv_sync_status.                                       */
 } sinv_precision;
 
 typedef struct sinv_handle_s *sinv_handle;

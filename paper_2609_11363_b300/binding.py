@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libsinv.so")
 _lib = None
 
-PREC = {"fp64": 0, "fp32": 1}
+PREC = {"fp64": 0, "fp32": 1, "fp32x2": 2}
 STATUS = {
     0: "SINV_OK", 1: "SINV_ERR_INVALID_ARG", 2: "SINV_ERR_PATTERN", 3: "SINV_ERR_SINGULAR_PIVOT",
     4: "SINV_ERR_OOM", 5: "SINV_ERR_CUDA", 6: "SINV_ERR_TIMEOUT", 7: "SINV_ERR_UNSUPPORTED",

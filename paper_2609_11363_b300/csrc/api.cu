@@ -181,7 +181,7 @@ sinv_status ensure_work(sinv_handle h, size_t bytes) {
     return SINV_OK;
 }
 
-bool valid_prec(int p) { return p == SINV_FP64 || p == SINV_FP32; }
+bool valid_prec(int p) { return p == SINV_FP64 || p == SINV_FP32 || p == SINV_FP32X2; }
 
 // numeric calls need a handle that lives on a device
 bool on_device(sinv_handle h) {
@@ -491,7 +491,7 @@ sinv_status sinv_selinv(sinv_handle h, const double* L_val, const double* D_val,
     a.nnzS = P.nnzS;
     a.num_sms = h->num_sms;
     if ((e = selinv_prepare(h->depoch, h->dticket, st)) != cudaSuccess) return cuda_fail(h, e, "selinv prepare");
-    if ((e = selinv_launch(a, prec == SINV_FP64 ? 0 : 1, h->dwork, G_S, st, h->grid)) != cudaSuccess)
+    if ((e = selinv_launch(a, prec == SINV_FP32 ? 1 : 0, h->dwork, G_S, st, h->grid)) != cudaSuccess)
         return cuda_fail(h, e, "selinv launch");
     return SINV_OK;
 }
@@ -564,6 +564,7 @@ static sinv_status ninv_common(sinv_handle h, const double* L_val, const double*
     a.Lrp = h->dLrp;
     a.nnzS = P.nnzS;
     a.nnzW = h->W.nnzW;
+    a.nnzL = P.nnzL;
     a.dpos = h->ddpos;
     a.pstart = h->dpstart;
     a.Lval = L_val;
@@ -571,7 +572,8 @@ static sinv_status ninv_common(sinv_handle h, const double* L_val, const double*
     a.max_col = h->W.max_col;
     a.num_sms = h->num_sms;
     a.status = h->dstatus;
-    int p = prec == SINV_FP64 ? 0 : 1;
+    // 0: FP64, 1: FP32, 2: FP64 with the product on S in pairs of floats (map form only)
+    int p = prec == SINV_FP32 ? 1 : prec == SINV_FP32X2 ? 2 : 0;
     if (h->index_tried_m != m) {
         h->index_tried_m = m;
         h->index_note = "disabled";
@@ -599,6 +601,7 @@ static sinv_status ninv_common(sinv_handle h, const double* L_val, const double*
             return cuda_fail(h, e, "ninv launch");
         return SINV_OK;
     }
+    if (p == 2) p = 0;  // the hash form has no pair product: FP64 throughout
     sinv_status s = ensure_work(h, ninv_work_bytes(a, p));
     if (s != SINV_OK) return s;
     if ((e = ninv_launch(a, p, h->dwork, N_S, st, N_stack)) != cudaSuccess) return cuda_fail(h, e, "ninv launch");
@@ -635,7 +638,7 @@ sinv_status sinv_lowrank_correct(sinv_handle h, int k, const double* V, const do
         if (s != SINV_OK) return s;
     }
     TraceScope trace_scope(h->tracer);
-    if ((e = lowrank_launch(h->P.n, h->dSrp, h->dSc, k, V, lambda, prec == SINV_FP64 ? 0 : 1, h->dwork, X_S,
+    if ((e = lowrank_launch(h->P.n, h->dSrp, h->dSc, k, V, lambda, prec == SINV_FP32 ? 1 : 0, h->dwork, X_S,
                             h->num_sms, (cudaStream_t)stream)) != cudaSuccess)
         return cuda_fail(h, e, "lowrank launch");
     return SINV_OK;

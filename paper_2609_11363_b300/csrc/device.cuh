@@ -7,7 +7,7 @@
 namespace sinv {
 
 // must match sinv_status in include/sinv.h
-enum : int32_t { ST_OK = 0, ST_SINGULAR = 3, ST_TIMEOUT = 6, ST_INTERNAL = 100 };
+enum : int32_t { ST_OK = 0, ST_SINGULAR = 3, ST_TIMEOUT = 6, ST_UNSUPPORTED = 7, ST_INTERNAL = 100 };
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
     uint32_t v;

@@ -79,6 +79,7 @@ struct NinvArgs {
     const int64_t* Lrp;   // L row pointers (CSR of the caller's L)
     int64_t nnzS;
     int64_t nnzW;
+    int64_t nnzL;
     const int32_t* dpos;
     const int8_t* pstart;
     const double* Lval;

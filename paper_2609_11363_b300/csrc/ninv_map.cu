@@ -19,9 +19,17 @@
 // W_ri y_r.  ypart holds, for the rows of 2x2 blocks, the table position of the
 // partner row inside their own column's table.
 //
+// Pair form (SINV_FP32X2): the Horner steps stay FP64 (their accumulation needs
+// shared atomics, which exist for FP64 but not for pairs of floats) and also
+// write W as pairs hi + lo of floats where a product follows; the product then
+// runs on the FP32 pipes in double-float arithmetic (see pair_mac), and y is
+// formed in pairs with one writer per position, so no FP64 operation is left in
+// the product.
+//
 // The maps are built on the GPU from the same shared-memory tables as the hash
 // form; they need |col j| + extras <= kIdxEnt for every column.
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "device.cuh"
@@ -173,6 +181,42 @@ __global__ void mmap_partner(int64_t n, const int8_t* __restrict__ pstart, int32
 
 // ---- numeric kernels ----
 
+// ---- the product in pairs of floats (FP64-class accuracy on the FP32 pipes) ----
+//
+// A value x is carried as hi + lo with hi = fl32(x) and lo = fl32(x - hi).  The
+// product of two pairs keeps hi_a hi_b exactly (its rounding error comes from a
+// fused multiply-add) and adds both cross terms hi_a lo_b + lo_a hi_b; the sum
+// runs as (s, c): s takes the high parts with an error-free two-sum and c
+// collects every error term and low part in FP32 (its own rounding stays at the
+// 2^-48 level relative to the terms).  The intrinsics keep the compiler from
+// contracting the two-sum.
+
+__device__ __forceinline__ float2 split_pair(double x) {
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+__device__ __forceinline__ void pair_mac(float2 a, float2 b, float& s, float& c) {
+    const float ph = __fmul_rn(a.x, b.x);
+    float pl = __fmaf_rn(a.x, b.x, -ph);
+    pl = __fmaf_rn(a.x, b.y, pl);
+    pl = __fmaf_rn(a.y, b.x, pl);
+    const float t = __fadd_rn(s, ph);
+    const float v = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, v)), __fsub_rn(ph, v));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(e, pl));
+}
+
+__device__ __forceinline__ void pair_add(float& s, float& c, float s2, float c2) {
+    const float t = __fadd_rn(s, s2);
+    const float v = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, v)), __fsub_rn(s2, v));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(e, c2));
+}
+
+
 template <class T>
 __device__ __forceinline__ T fma_m(T a, T b, T c);
 template <>
@@ -182,7 +226,7 @@ __device__ __forceinline__ float fma_m<float>(float a, float b, float c) { retur
 
 template <class T>
 __global__ void __launch_bounds__(kThreads) hm_step(NinvArgs a, NinvMaps x, int t, const T* __restrict__ Wp,
-                                                    T* __restrict__ Wn, int32_t* ticket) {
+                                                    T* __restrict__ Wn, float2* __restrict__ Wx, int32_t* ticket) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* acc = reinterpret_cast<T*>(smem_raw);
     __shared__ int32_t s_j;
@@ -216,7 +260,13 @@ __global__ void __launch_bounds__(kThreads) hm_step(NinvArgs a, NinvMaps x, int 
             }
         }
         __syncthreads();
-        for (int32_t e = threadIdx.x; e < nt; e += kThreads) Wn[base + e] = acc[e] + (e == 0 ? T(1) : T(0));
+        for (int32_t e = threadIdx.x; e < nt; e += kThreads) {
+            const T v = acc[e] + (e == 0 ? T(1) : T(0));
+            Wn[base + e] = v;
+            if constexpr (std::is_same<T, double>::value) {
+                if (Wx) Wx[base + e] = split_pair(v);  // the pairs of the product in pairs of floats
+            }
+        }
         __syncthreads();
     }
 }
@@ -289,6 +339,114 @@ __global__ void __launch_bounds__(kThreads) pm_product(NinvArgs a, NinvMaps x, i
     }
 }
 
+constexpr double kPairMax = 0x1p100;  // magnitude the pairs carry at full accuracy
+
+// D^{-1} per row as pairs (inputs outside the range the pairs carry are reported)
+__global__ void pair_prep(int64_t n, int32_t* status, const double* __restrict__ dr, const double* __restrict__ dp,
+                          float2* __restrict__ drx, float2* __restrict__ dpx) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        if (!(fabs(dr[r]) < kPairMax) || !(fabs(dp[r]) < kPairMax)) set_status(status, ST_UNSUPPORTED);
+        drx[r] = split_pair(dr[r]);
+        dpx[r] = split_pair(dp[r]);
+    }
+}
+
+// (s, c) -> normalised pair (hi, lo)
+__device__ __forceinline__ float2 pair_norm(float s, float c) {
+    const float h = __fadd_rn(s, c);
+    return make_float2(h, __fsub_rn(c, __fsub_rn(h, s)));
+}
+
+__device__ __forceinline__ void pair_mul_add(float2 a, float2 b, float& s, float& c) { pair_mac(a, b, s, c); }
+
+// Product on S in pairs: y = D^{-1} W[:, j] formed in pairs with one writer per
+// position, then the streamed sums of hp_step's arithmetic.
+__global__ void __launch_bounds__(kThreads) pp_product(NinvArgs a, NinvMaps x, int tlim,
+                                                       const float2* __restrict__ W, const float2* __restrict__ drx,
+                                                       const float2* __restrict__ dpx, double* __restrict__ N,
+                                                       int32_t* ticket) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* y = reinterpret_cast<float2*>(smem_raw);
+    __shared__ int32_t s_j;
+    const int G = a.m + 2;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (;;) {
+        const int64_t j = take_column(ticket, &s_j);
+        if (j >= a.n) break;
+        const int64_t base = a.Wcp[j];
+        const int32_t ny = (int32_t)(a.Wcp[j + 1] - base) + x.ynx[j];
+        const int32_t nt = a.grp[j * G + tlim + 1];
+        for (int32_t e = threadIdx.x; e < ny; e += kThreads) y[e] = make_float2(0.f, 0.f);
+        __syncthreads();
+        // y_r = dr_r W_rj + dp_r W_pj for the rows r of powers <= tlim (p the partner of r).
+        // A partner p outside that prefix (a later row of the column, or an extra
+        // position) has W_pj = 0, so y_p = dp W_rj has the single writer r.
+        for (int32_t e = threadIdx.x; e < nt; e += kThreads) {
+            const int32_t rf = a.Wr[base + e];
+            const int32_t r = rf & kRowMask;
+            const float2 w = W[base + e];
+            float s = 0.f, c = 0.f;
+            pair_mul_add(drx[r], w, s, c);
+            if (rf & kTwoFlag) {
+                const int32_t pp = x.ypart[base + e];
+                if (pp < nt) {
+                    pair_mul_add(dpx[r], W[base + pp], s, c);
+                } else {
+                    float s2 = 0.f, c2 = 0.f;
+                    pair_mul_add(dpx[r], w, s2, c2);
+                    y[pp] = pair_norm(s2, c2);
+                }
+            }
+            y[e] = pair_norm(s, c);
+        }
+        __syncthreads();
+        const bool two_first = a.pstart[j] != 0 && j + 1 < a.n && a.pstart[j + 1] == 0;
+        const int64_t q0 = a.Lcp[j];
+        const int64_t cnt = (a.Lcp[j + 1] - q0) + 1 + (two_first ? 1 : 0);
+        for (int64_t e = wid; e < cnt; e += kWarps) {
+            int64_t i, spos;
+            if (e == 0) {
+                i = j;
+                spos = a.Srp[j + 1] - 1;
+            } else if (two_first && e == 1) {
+                i = j + 1;
+                spos = a.Srp[j + 2] - 2;
+            } else {
+                const int64_t q = q0 + e - 1 - (two_first ? 1 : 0);
+                i = a.Lri[q];
+                spos = a.Srp[i] + ((int64_t)a.Lcsr[q] - a.Lrp[i]);
+            }
+            const float2* __restrict__ wi = W + a.Wcp[i];
+            const uint16_t* __restrict__ mp = x.pmap + x.poff[spos];
+            const int32_t ni = a.grp[i * G + tlim + 1];
+            float s = 0.f, c = 0.f;
+            for (int32_t f0 = 0; f0 < ni; f0 += 32 * kUnrollM) {
+                uint16_t p[kUnrollM];
+                float2 v[kUnrollM];
+#pragma unroll
+                for (int u = 0; u < kUnrollM; ++u) {
+                    const int32_t f = f0 + u * 32 + lane;
+                    p[u] = f < ni ? mp[f] : kNone;
+                    v[u] = f < ni ? wi[f] : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < kUnrollM; ++u)
+                    if (p[u] != kNone) pair_mac(v[u], y[p[u]], s, c);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                pair_add(s, c, __shfl_xor_sync(0xffffffffu, s, o), __shfl_xor_sync(0xffffffffu, c, o));
+            if (lane == 0) N[spos] = (double)s + (double)c;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void hp_init(const int64_t* __restrict__ Wcp, float2* __restrict__ W, int64_t n) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        W[Wcp[j]] = make_float2(1.f, 0.f);
+}
+
 template <class T>
 __global__ void hm_init(const int64_t* __restrict__ Wcp, T* __restrict__ W, int64_t n) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
@@ -333,7 +491,60 @@ cudaError_t map_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N_
     if (N_stack) product(0, N_stack, tickets + 62 - a.m);
     for (int t = 1; t <= a.m; ++t) {
         trace_begin("ninv_map_horner", st);
-        hm_step<T><<<grid, kThreads, map_smem<T>(), st>>>(a, x, t, cur, nxt, tickets + t);
+        hm_step<T><<<grid, kThreads, map_smem<T>(), st>>>(a, x, t, cur, nxt, nullptr, tickets + t);
+        trace_end(st);
+        std::swap(cur, nxt);
+        if (N_stack && t < a.m) product(t, N_stack + (int64_t)t * a.nnzS, tickets + 62 - a.m + t);
+    }
+    product(a.m, N_stack ? N_stack + (int64_t)a.m * a.nnzS : N_out, tickets + 63);
+    return cudaGetLastError();
+}
+
+// FP64 Horner steps (shared FP64 atomics) that also write W in pairs of floats
+// where a product follows; the product on S in pairs.
+cudaError_t pair_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N_out, double* N_stack,
+                     cudaStream_t st) {
+    char* p = reinterpret_cast<char*>(work);
+    auto take = [&](size_t bytes) {
+        char* r = p;
+        p += (bytes + 255) & ~(size_t)255;
+        return r;
+    };
+    double* W0 = reinterpret_cast<double*>(take((size_t)a.nnzW * sizeof(double)));
+    double* W1 = reinterpret_cast<double*>(take((size_t)a.nnzW * sizeof(double)));
+    double* dr = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));
+    double* dp = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));
+    int32_t* part = reinterpret_cast<int32_t*>(take((size_t)a.n * sizeof(int32_t)));
+    int32_t* tickets = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 64));
+    float2* Wx = reinterpret_cast<float2*>(take((size_t)a.nnzW * sizeof(float2)));
+    float2* drx = reinterpret_cast<float2*>(take((size_t)a.n * sizeof(float2)));
+    float2* dpx = reinterpret_cast<float2*>(take((size_t)a.n * sizeof(float2)));
+    cudaError_t e = cudaMemsetAsync(tickets, 0, sizeof(int32_t) * 64, st);
+    if (e != cudaSuccess) return e;
+    trace_begin("ninv_dinv", st);
+    ninv_dinv_launch(a, dr, dp, part, st);
+    trace_end(st);
+    trace_begin("ninv_pair_prep", st);
+    pair_prep<<<a.num_sms * 4, 256, 0, st>>>(a.n, a.status, dr, dp, drx, dpx);
+    trace_end(st);
+    trace_begin("ninv_init", st);
+    hm_init<double><<<a.num_sms * 4, 256, 0, st>>>(a.Wcp, W0, a.n);
+    hp_init<<<a.num_sms * 4, 256, 0, st>>>(a.Wcp, Wx, a.n);
+    trace_end(st);
+    const int grid = a.num_sms * 4;
+    double* cur = W0;
+    double* nxt = W1;
+    auto product = [&](int t, double* out, int32_t* tk) {
+        trace_begin("ninv_pair_product", st);
+        pp_product<<<grid, kThreads, map_smem<double>(), st>>>(a, x, t, Wx, drx, dpx, out, tk);
+        trace_end(st);
+    };
+    if (N_stack) product(0, N_stack, tickets + 62 - a.m);
+    for (int t = 1; t <= a.m; ++t) {
+        const bool pairs = t == a.m || N_stack != nullptr;
+        trace_begin("ninv_map_horner", st);
+        hm_step<double><<<grid, kThreads, map_smem<double>(), st>>>(a, x, t, cur, nxt, pairs ? Wx : nullptr,
+                                                                    tickets + t);
         trace_end(st);
         std::swap(cur, nxt);
         if (N_stack && t < a.m) product(t, N_stack + (int64_t)t * a.nnzS, tickets + 62 - a.m + t);
@@ -345,16 +556,18 @@ cudaError_t map_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N_
 }  // namespace
 
 size_t ninv_map_work_bytes(const NinvArgs& a, int prec) {
-    const size_t ts = prec == 0 ? sizeof(double) : sizeof(float);
+    const size_t ts = prec == 1 ? sizeof(float) : sizeof(double);
+    const size_t pairs = prec == 2 ? ((size_t)a.nnzW + 2 * (size_t)a.n) * sizeof(float2) + 3 * 256 : 0;
     return 2 * ((size_t)a.nnzW * ts + 256) + (size_t)a.n * (2 * sizeof(double) + sizeof(int32_t)) + 3 * 256 +
-           sizeof(int32_t) * 64 + 256 + 4096;
+           sizeof(int32_t) * 64 + 256 + pairs + 4096;
 }
 
 cudaError_t ninv_map_launch(const NinvArgs& a, const NinvMaps& x, int prec, void* work, double* N_out,
                             cudaStream_t st, double* N_stack) {
     if (a.n == 0) return cudaSuccess;
-    if (prec == 0) return map_run<double>(a, x, work, N_out, N_stack, st);
-    return map_run<float>(a, x, work, N_out, N_stack, st);
+    if (prec == 1) return map_run<float>(a, x, work, N_out, N_stack, st);
+    if (prec == 2) return pair_run(a, x, work, N_out, N_stack, st);
+    return map_run<double>(a, x, work, N_out, N_stack, st);
 }
 
 void ninv_maps_free(NinvMaps& x) {
@@ -376,6 +589,8 @@ cudaError_t ninv_maps_configure() {
         (e = cudaFuncSetAttribute(hm_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)map_smem<float>())) != cudaSuccess ||
         (e = cudaFuncSetAttribute(pm_product<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)map_smem<double>())) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(pp_product, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)map_smem<double>())) != cudaSuccess)
         return e;
     return cudaFuncSetAttribute(pm_product<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -23,14 +23,14 @@ def _bf16_round(a):
     return torch.as_tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
 
 
-@pytest.mark.parametrize("index_bytes", [0, -1])
-def test_ninv_stack_matches_each_truncation(index_bytes):
-    """Gather form (0) and hash form (-1)."""
+@pytest.mark.parametrize("index_bytes,prec", [(0, "fp64"), (-1, "fp64"), (0, "fp32x2")])
+def test_ninv_stack_matches_each_truncation(index_bytes, prec):
+    """Map form (0), hash form (-1) and the map form in pairs of floats."""
     from paper_2609_11363_b300 import Handle
     f = plant_2x2(diff3d(10, shifted=False, m=3).factors, 0.05, 3)
     S = oracle.symbolic_S(f.n, f.L_rowptr, f.L_col, f.pivot_start)
     h = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start, ninv_index_bytes=index_bytes)
-    st = h.ninv_stack(_dev(f.L_val), _dev(f.D_packed), 3).cpu().numpy()
+    st = h.ninv_stack(_dev(f.L_val), _dev(f.D_packed), 3, prec).cpu().numpy()
     h.sync_status()
     for t in range(4):
         ref = oracle.ninv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, t, S)

@@ -6,6 +6,7 @@ Mix bit-exact (it only selects); FP32 forms normwise within the bound stated
 in each test.
 """
 import numpy as np
+import scipy.sparse as sp
 import pytest
 import torch
 
@@ -123,6 +124,29 @@ def test_ninv_fp32(case, form):
     assert normwise(out.cpu().numpy(), N) <= 1e-5, name
 
 
+@pytest.mark.parametrize("mm", [0, 1, 3])
+def test_ninv_fp32x2(case, mm):
+    """Product on S in pairs of floats: FP64-class, checked at the FP64 tolerance."""
+    name, f, m, S, G, N = case
+    Nr = N if mm == m else oracle.ninv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, mm, S)
+    h = _handle(f)
+    out = h.ninv(_dev(f.L_val), _dev(f.D_packed), mm, "fp32x2")
+    h.sync_status()
+    _check_form(h, "map")
+    err = sel_rel_err(out.cpu().numpy(), Nr, *S)
+    assert err <= TOL64, (name, mm, err)
+
+
+def test_fp32x2_means_fp64_for_selinv_and_lowrank(case):
+    name, f, m, S, G, N = case
+    h = _handle(f)
+    Lv, Dv = _dev(f.L_val), _dev(f.D_packed)
+    a = h.selinv(Lv, Dv, "fp32x2").cpu().numpy()
+    b = h.selinv(Lv, Dv, "fp64").cpu().numpy()
+    h.sync_status()
+    assert sel_rel_err(a, G, *S) <= TOL64 and sel_rel_err(b, G, *S) <= TOL64
+
+
 def test_ninv_maps_reuse_and_m_change(case):
     """Numeric reruns reuse the maps; a new m rebuilds them (and back)."""
     name, f, m, S, G, N = case
@@ -133,6 +157,25 @@ def test_ninv_maps_reuse_and_m_change(case):
     N1 = oracle.ninv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, 1, S)
     for mm, out in zip((m, m, 1, m), outs):
         assert sel_rel_err(out, N if mm == m else N1, *S) <= TOL64, (name, mm)
+
+
+def test_ninv_long_column_runs_hash_form():
+    """A column of the series pattern longer than the map tables: the hash form runs."""
+    n = 6200
+    rows = np.arange(1, n)
+    L = sp.csr_matrix((np.full(n - 1, 1e-3), (rows, np.zeros(n - 1, dtype=np.int64))), shape=(n, n))
+    from workloads.factor import Factors
+    ps = np.ones(n, np.int8)
+    d = np.linspace(1.0, 2.0, n)
+    f = Factors(n, L.indptr.astype(np.int64), L.indices.astype(np.int32), L.data.copy(), ps, d,
+                np.zeros(n), {})
+    S = oracle.symbolic_S(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+    Nr = oracle.ninv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, 2, S)
+    h = _handle(f)
+    out = h.ninv(_dev(f.L_val), _dev(f.D_packed), 2, "fp32x2")
+    h.sync_status()
+    assert h.stats()["ninv_index_bytes"] == 0
+    assert sel_rel_err(out.cpu().numpy(), Nr, *S) <= TOL64
 
 
 def test_ninv_index_over_budget_runs_hash_form():
