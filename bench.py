@@ -193,6 +193,18 @@ def dram_traffic(kernel, prec, st, m):
                                            "the 32^3 case, scaled by the units per launch (estimate)")
 
 
+def aggregate_ranks(total_ms, units_per_step, steps, world, device):
+    """Whole-job throughput of `world` replicas: the slowest rank's time (max over ranks)
+    and the units every rank processed.  Returns (ms per step, units per second)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    return total_ms / steps, world * units_per_step * steps / (total_ms / 1e3)
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2609_11363_b300 import Handle
@@ -269,14 +281,7 @@ def run_ours(args, rank, world):
         for i, p in enumerate(phases):
             per_phase[p].append(ev[i].elapsed_time(ev[i + 1]))
         step_ms.append(ev[0].elapsed_time(ev[4]))
-    total_ms = float(np.sum(step_ms))
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    ms_per_step = total_ms / args.steps
-    value = world * nS * args.steps / (total_ms / 1e3)
+    ms_per_step, value = aggregate_ranks(float(np.sum(step_ms)), nS, args.steps, world, dev)
 
     e2e = None
     if rank == 0:

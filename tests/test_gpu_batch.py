@@ -119,3 +119,42 @@ def test_batch_step_in_cuda_graph(batch):
             Mr = oracle.lowrank_correct(S[0], S[1], oracle.mix(Gr, Nr, eps), V[r0:r0 + f.n], lam)
             assert sel_rel_err(_split(Gh, lay, b), Gr, *S) <= TOL64, (scale, b)
             assert sel_rel_err(_split(Mh, lay, b), Mr, *S) <= TOL64, (scale, b)
+
+
+def _gen_member(seed):
+    return batch9pt_member(seed).factors
+
+
+@pytest.mark.slow
+def test_full_batch_256_sampled_members():
+    """The 256-matrix batched workload at full size (n ~ U[2048, 65536], seeds 3000+),
+    in the benchmark's form (FP32, one handle, m = 3): four members (the smallest, the
+    largest and two seeded picks) against the oracle in full, and the FP64 form of the
+    same members at the FP64 tolerance."""
+    import multiprocessing as mp
+    import os
+
+    from paper_2609_11363_b300 import Handle
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        fs = pool.map(_gen_member, [3000 + i for i in range(256)])
+    h = Handle.batch(fs)
+    lay = h.layout()
+    Lv = _dev(np.concatenate([f.L_val for f in fs]))
+    Dv = _dev(np.concatenate([f.D_packed for f in fs]))
+    G32 = h.selinv(Lv, Dv, "fp32").cpu().numpy()
+    N32 = h.ninv(Lv, Dv, 3, "fp32").cpu().numpy()
+    G64 = h.selinv(Lv, Dv, "fp64").cpu().numpy()
+    N64 = h.ninv(Lv, Dv, 3, "fp64").cpu().numpy()
+    h.sync_status()
+    sizes = np.array([f.n for f in fs])
+    rng = np.random.default_rng(7)
+    picks = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), *rng.choice(256, 2, replace=False).tolist()})
+    for b in picks:
+        f = fs[b]
+        S = oracle.symbolic_S(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+        G = oracle.selinv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, S)
+        N = oracle.ninv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, 3, S)
+        assert normwise(_split(G32, lay, b), G) <= 1e-5, b
+        assert normwise(_split(N32, lay, b), N) <= 1e-5, b
+        assert sel_rel_err(_split(G64, lay, b), G, *S) <= TOL64, b
+        assert sel_rel_err(_split(N64, lay, b), N, *S) <= TOL64, b

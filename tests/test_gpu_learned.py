@@ -102,3 +102,27 @@ def test_trained_network_beats_plain_ninv_on_held_out_matrix():
     lc.fit(sets[:3], epochs=12, lr=3e-3)
     ev = lc.evaluate(sets[3])
     assert ev["err_learned"] < 0.8 * ev["err_ninv"], ev
+
+
+@pytest.mark.slow
+def test_full_size_128_ninv_stack_sampled():
+    """The learned correction's inference matrix at full size (3D diffusion 128^3,
+    n = 2,097,152, m = 3): the NInv truncation stack on sampled entries against the
+    oracle, entry by entry, in the form the benchmark runs."""
+    from paper_2609_11363_b300 import Handle
+    f = diff3d(128, shifted=False, m=3, seed=4999).factors
+    h = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+    Lv, Dv = _dev(f.L_val), _dev(f.D_packed)
+    st = h.ninv_stack(Lv, Dv, 3).cpu().numpy()
+    h.sync_status()
+    S = (h.pattern_host()[0], h.pattern_host()[1])
+    rng = np.random.default_rng(3)
+    idx = rng.choice(len(S[1]), 24, replace=False)
+    rows = np.repeat(np.arange(f.n), np.diff(S[0]))
+    pairs = list(zip(rows[idx], S[1][idx]))
+    for t in (1, 3):
+        ref = oracle.ninv_entries_sampled(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, t,
+                                          pairs)
+        diag = st[t][S[0][1:] - 1]
+        scale = np.abs(ref) + np.sqrt(np.abs(diag[rows[idx]] * diag[S[1][idx]]))
+        assert np.max(np.abs(st[t][idx] - ref) / scale) <= 1e-10, t

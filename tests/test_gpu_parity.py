@@ -12,7 +12,7 @@ import torch
 
 import oracle
 from tests.helpers import normwise, sel_rel_err
-from workloads.configs import diff3d, lap2d_32, plant_2x2, random_factors, random_lowrank
+from workloads.configs import diff3d, elastic3d, lap2d_32, plant_2x2, random_factors, random_lowrank
 
 pytestmark = pytest.mark.gpu
 
@@ -42,6 +42,8 @@ CASES = {
     "random_nonclosed": lambda: random_factors(700, 0.02, 0.15, 5),
     "random_dense_rows": lambda: random_factors(300, 0.25, 0.1, 6, scale=0.1),
     "diff3d_12_planted": lambda: plant_2x2(diff3d(12, m=3).factors, 0.05, 13),
+    # 27-point 3-dof elastic-like operator (dense 3x3 blocks, ~100 entries per row of L)
+    "elastic3d_8_planted": lambda: plant_2x2(elastic3d(8).factors, 0.05, 17),
 }
 
 
