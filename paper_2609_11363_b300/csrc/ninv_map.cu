@@ -271,6 +271,116 @@ __global__ void __launch_bounds__(kThreads) hm_step(NinvArgs a, NinvMaps x, int 
     }
 }
 
+// FP64 Horner step with exact integer accumulation.  Column j of W_t is bounded a
+// priori, |W_t[r, j]| <= B = 1 + sum_k |E_kj| max_r |W_{t-1}[r, k]| (every partial
+// sum too), so with the scale 2^s, s = 61 - ceil(log2 B), each product E_kj W[r, k]
+// is rounded once (by integer operations, fx_round) to an integer multiple of 2^-s
+// and summed with 64-bit integer
+// shared-memory atomics: no overflow, an order-independent (bit-reproducible) sum,
+// absolute error below (|struct(j)| + 1) 2^-s <= 2^-52 B per entry, and one FP64
+// operation per product (the multiply) where an FP64 atomic add would take a second.
+// The step also records max_r |W_t[r, j]| for the next step's bound.
+__device__ __forceinline__ double scale_pow2(double v, int s) {
+    // v * 2^-s for a normal v whose result stays normal, by the exponent field
+    return v == 0.0 ? 0.0 : __longlong_as_double(__double_as_longlong(v) - ((long long)s << 52));
+}
+
+// round(x) for |x| < 2^62 with integer operations only (rounding half away from zero):
+// x = m 2^(e - 1075) with the 53-bit significand m
+__device__ __forceinline__ long long fx_round(double x) {
+    const long long u = __double_as_longlong(x);
+    const int e = (int)((u >> 52) & 0x7FF);
+    if (e < 1022) return 0;  // |x| < 1/2 (zeros and subnormals included)
+    const unsigned long long m = ((unsigned long long)u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = e - 1075;
+    const unsigned long long q = sh >= 0 ? (m << sh) : ((m + (1ull << (-sh - 1))) >> -sh);
+    return u < 0 ? -(long long)q : (long long)q;
+}
+
+__global__ void __launch_bounds__(kThreads) hm_step_fx(NinvArgs a, NinvMaps x, int t, const double* __restrict__ Wp,
+                                                       double* __restrict__ Wn, float2* __restrict__ Wx,
+                                                       const double* __restrict__ Mp, double* __restrict__ Mn,
+                                                       int32_t* ticket) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem_raw);
+    __shared__ int32_t s_j, s_s;
+    __shared__ unsigned long long s_max;
+    const int G = a.m + 2;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (;;) {
+        const int64_t j = take_column(ticket, &s_j);
+        if (j >= a.n) break;
+        const int64_t base = a.Wcp[j];
+        const int32_t nt = a.grp[j * G + t + 1];
+        const int64_t q0 = a.Lcp[j], q1 = a.Lcp[j + 1];
+        if (wid == 0) {
+            double b = 0.0;
+            for (int64_t q = q0 + lane; q < q1; q += 32) b += fabs(a.Lval[a.Lcsr[q]]) * Mp[a.Lri[q]];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+            if (lane == 0) {
+                int ex;
+                frexp(1.0 + b, &ex);  // 1 + b < 2^ex
+                int sc = 61 - ex;
+                if (sc < 0 || !(b < 1e300)) {  // W too large for the fixed-point range
+                    set_status(a.status, ST_UNSUPPORTED);
+                    sc = 0;
+                }
+                s_s = sc;
+                s_max = 0ull;
+            }
+        }
+        __syncthreads();
+        const int sc = s_s;
+        for (int32_t e = threadIdx.x; e < nt; e += kThreads) acc[e] = e == 0 ? (1ull << sc) : 0ull;
+        __syncthreads();
+        for (int64_t q = q0 + wid; q < q1; q += kWarps) {
+            const int32_t k = a.Lri[q];
+            const double ekj = -a.Lval[a.Lcsr[q]] * ldexp(1.0, sc);  // E_kj 2^s (exact)
+            const double* __restrict__ wk = Wp + a.Wcp[k];
+            const uint16_t* __restrict__ mp = x.hmap + x.moff[q];
+            const int32_t nk = a.grp[(int64_t)k * G + t];
+            for (int32_t e0 = 0; e0 < nk; e0 += 32 * kUnrollM) {
+                uint16_t p[kUnrollM];
+                double v[kUnrollM];
+#pragma unroll
+                for (int u = 0; u < kUnrollM; ++u) {
+                    const int32_t e = e0 + u * 32 + lane;
+                    p[u] = e < nk ? mp[e] : kNone;
+                    v[u] = e < nk ? wk[e] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < kUnrollM; ++u)
+                    if (p[u] != kNone) atomicAdd(acc + p[u], (unsigned long long)fx_round(ekj * v[u]));
+            }
+        }
+        __syncthreads();
+        unsigned long long mx = 0ull;
+        for (int32_t e = threadIdx.x; e < nt; e += kThreads) {
+            const long long iv = (long long)acc[e];
+            const unsigned long long av = (unsigned long long)(iv < 0 ? -iv : iv);
+            mx = av > mx ? av : mx;
+            const double v = scale_pow2(__ll2double_rn(iv), sc);
+            Wn[base + e] = v;
+            if (Wx) Wx[base + e] = split_pair(v);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, mx, o);
+            mx = other > mx ? other : mx;
+        }
+        if (lane == 0) atomicMax(&s_max, mx);
+        __syncthreads();
+        if (threadIdx.x == 0) Mn[j] = scale_pow2(__ull2double_ru(s_max), sc);
+        __syncthreads();
+    }
+}
+
+__global__ void fx_init(double* __restrict__ M, int64_t n) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        M[j] = 1.0;  // W_0 = I
+}
+
 template <class T>
 __global__ void __launch_bounds__(kThreads) pm_product(NinvArgs a, NinvMaps x, int tlim, const T* __restrict__ W,
                                                        const double* __restrict__ dr, const double* __restrict__ dp,
@@ -472,6 +582,8 @@ cudaError_t map_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N_
     double* dp = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));
     int32_t* part = reinterpret_cast<int32_t*>(take((size_t)a.n * sizeof(int32_t)));
     int32_t* tickets = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 64));
+    double* M0 = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));  // column bounds (FP64)
+    double* M1 = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));
     cudaError_t e = cudaMemsetAsync(tickets, 0, sizeof(int32_t) * 64, st);
     if (e != cudaSuccess) return e;
     trace_begin("ninv_dinv", st);
@@ -479,6 +591,7 @@ cudaError_t map_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N_
     trace_end(st);
     trace_begin("ninv_init", st);
     hm_init<T><<<a.num_sms * 4, 256, 0, st>>>(a.Wcp, W0, a.n);
+    if constexpr (std::is_same<T, double>::value) fx_init<<<a.num_sms * 4, 256, 0, st>>>(M0, a.n);
     trace_end(st);
     const int grid = a.num_sms * 4;
     T* cur = W0;
@@ -491,7 +604,12 @@ cudaError_t map_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N_
     if (N_stack) product(0, N_stack, tickets + 62 - a.m);
     for (int t = 1; t <= a.m; ++t) {
         trace_begin("ninv_map_horner", st);
-        hm_step<T><<<grid, kThreads, map_smem<T>(), st>>>(a, x, t, cur, nxt, nullptr, tickets + t);
+        if constexpr (std::is_same<T, double>::value) {
+            hm_step_fx<<<grid, kThreads, map_smem<double>(), st>>>(a, x, t, cur, nxt, nullptr, M0, M1, tickets + t);
+            std::swap(M0, M1);
+        } else {
+            hm_step<T><<<grid, kThreads, map_smem<T>(), st>>>(a, x, t, cur, nxt, nullptr, tickets + t);
+        }
         trace_end(st);
         std::swap(cur, nxt);
         if (N_stack && t < a.m) product(t, N_stack + (int64_t)t * a.nnzS, tickets + 62 - a.m + t);
@@ -519,6 +637,8 @@ cudaError_t pair_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N
     float2* Wx = reinterpret_cast<float2*>(take((size_t)a.nnzW * sizeof(float2)));
     float2* drx = reinterpret_cast<float2*>(take((size_t)a.n * sizeof(float2)));
     float2* dpx = reinterpret_cast<float2*>(take((size_t)a.n * sizeof(float2)));
+    double* M0 = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));
+    double* M1 = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));
     cudaError_t e = cudaMemsetAsync(tickets, 0, sizeof(int32_t) * 64, st);
     if (e != cudaSuccess) return e;
     trace_begin("ninv_dinv", st);
@@ -530,6 +650,7 @@ cudaError_t pair_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N
     trace_begin("ninv_init", st);
     hm_init<double><<<a.num_sms * 4, 256, 0, st>>>(a.Wcp, W0, a.n);
     hp_init<<<a.num_sms * 4, 256, 0, st>>>(a.Wcp, Wx, a.n);
+    fx_init<<<a.num_sms * 4, 256, 0, st>>>(M0, a.n);
     trace_end(st);
     const int grid = a.num_sms * 4;
     double* cur = W0;
@@ -543,8 +664,9 @@ cudaError_t pair_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N
     for (int t = 1; t <= a.m; ++t) {
         const bool pairs = t == a.m || N_stack != nullptr;
         trace_begin("ninv_map_horner", st);
-        hm_step<double><<<grid, kThreads, map_smem<double>(), st>>>(a, x, t, cur, nxt, pairs ? Wx : nullptr,
-                                                                    tickets + t);
+        hm_step_fx<<<grid, kThreads, map_smem<double>(), st>>>(a, x, t, cur, nxt, pairs ? Wx : nullptr, M0, M1,
+                                                               tickets + t);
+        std::swap(M0, M1);
         trace_end(st);
         std::swap(cur, nxt);
         if (N_stack && t < a.m) product(t, N_stack + (int64_t)t * a.nnzS, tickets + 62 - a.m + t);
@@ -558,8 +680,9 @@ cudaError_t pair_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N
 size_t ninv_map_work_bytes(const NinvArgs& a, int prec) {
     const size_t ts = prec == 1 ? sizeof(float) : sizeof(double);
     const size_t pairs = prec == 2 ? ((size_t)a.nnzW + 2 * (size_t)a.n) * sizeof(float2) + 3 * 256 : 0;
+    const size_t bounds = 2 * ((size_t)a.n * sizeof(double) + 256);
     return 2 * ((size_t)a.nnzW * ts + 256) + (size_t)a.n * (2 * sizeof(double) + sizeof(int32_t)) + 3 * 256 +
-           sizeof(int32_t) * 64 + 256 + pairs + 4096;
+           sizeof(int32_t) * 64 + 256 + pairs + bounds + 4096;
 }
 
 cudaError_t ninv_map_launch(const NinvArgs& a, const NinvMaps& x, int prec, void* work, double* N_out,
@@ -585,6 +708,8 @@ cudaError_t ninv_maps_configure() {
             cudaSuccess)
             return e;
     if ((e = cudaFuncSetAttribute(hm_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)map_smem<double>())) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(hm_step_fx, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)map_smem<double>())) != cudaSuccess ||
         (e = cudaFuncSetAttribute(hm_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)map_smem<float>())) != cudaSuccess ||

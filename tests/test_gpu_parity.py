@@ -149,6 +149,19 @@ def test_fp32x2_means_fp64_for_selinv_and_lowrank(case):
     assert sel_rel_err(a, G, *S) <= TOL64 and sel_rel_err(b, G, *S) <= TOL64
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32x2"])
+def test_ninv_map_form_is_bit_reproducible(case, prec):
+    """The FP64 Horner steps sum in exact fixed point and the product reduces in a
+    fixed order, so repeated calls agree bit for bit."""
+    name, f, m, S, G, N = case
+    h = _handle(f)
+    Lv, Dv = _dev(f.L_val), _dev(f.D_packed)
+    a = h.ninv(Lv, Dv, m, prec).cpu().numpy()
+    b = h.ninv(Lv, Dv, m, prec).cpu().numpy()
+    h.sync_status()
+    assert np.array_equal(a, b), name
+
+
 def test_ninv_maps_reuse_and_m_change(case):
     """Numeric reruns reuse the maps; a new m rebuilds them (and back)."""
     name, f, m, S, G, N = case
