@@ -19,12 +19,14 @@
 // W_ri y_r.  ypart holds, for the rows of 2x2 blocks, the table position of the
 // partner row inside their own column's table.
 //
-// Pair form (SINV_FP32X2): the Horner steps stay FP64 (their accumulation needs
-// shared atomics, which exist for FP64 but not for pairs of floats) and also
-// write W as pairs hi + lo of floats where a product follows; the product then
-// runs on the FP32 pipes in double-float arithmetic (see pair_mac), and y is
-// formed in pairs with one writer per position, so no FP64 operation is left in
-// the product.
+// The FP64 Horner step (hm_step_fx) sums in exact 64-bit fixed point with integer
+// shared atomics (bit-reproducible; one FP64 multiply per product).
+//
+// Pair form (SINV_FP32X2): W is kept as pairs hi + lo of floats.  The Horner step
+// (hm_step_fx2) forms each product in double-float arithmetic and sums it in the
+// same fixed point; the product on S (pp_product) runs in double-float arithmetic
+// with y formed in pairs, one writer per position.  No FP64 operation is left in
+// either kernel.
 //
 // The maps are built on the GPU from the same shared-memory tables as the hash
 // form; they need |col j| + extras <= kIdxEnt for every column.
@@ -226,7 +228,7 @@ __device__ __forceinline__ float fma_m<float>(float a, float b, float c) { retur
 
 template <class T>
 __global__ void __launch_bounds__(kThreads) hm_step(NinvArgs a, NinvMaps x, int t, const T* __restrict__ Wp,
-                                                    T* __restrict__ Wn, float2* __restrict__ Wx, int32_t* ticket) {
+                                                    T* __restrict__ Wn, int32_t* ticket) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* acc = reinterpret_cast<T*>(smem_raw);
     __shared__ int32_t s_j;
@@ -260,13 +262,7 @@ __global__ void __launch_bounds__(kThreads) hm_step(NinvArgs a, NinvMaps x, int 
             }
         }
         __syncthreads();
-        for (int32_t e = threadIdx.x; e < nt; e += kThreads) {
-            const T v = acc[e] + (e == 0 ? T(1) : T(0));
-            Wn[base + e] = v;
-            if constexpr (std::is_same<T, double>::value) {
-                if (Wx) Wx[base + e] = split_pair(v);  // the pairs of the product in pairs of floats
-            }
-        }
+        for (int32_t e = threadIdx.x; e < nt; e += kThreads) Wn[base + e] = acc[e] + (e == 0 ? T(1) : T(0));
         __syncthreads();
     }
 }
@@ -298,8 +294,8 @@ __device__ __forceinline__ long long fx_round(double x) {
 }
 
 __global__ void __launch_bounds__(kThreads) hm_step_fx(NinvArgs a, NinvMaps x, int t, const double* __restrict__ Wp,
-                                                       double* __restrict__ Wn, float2* __restrict__ Wx,
-                                                       const double* __restrict__ Mp, double* __restrict__ Mn,
+                                                       double* __restrict__ Wn, const double* __restrict__ Mp,
+                                                       double* __restrict__ Mn,
                                                        int32_t* ticket) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem_raw);
@@ -362,7 +358,138 @@ __global__ void __launch_bounds__(kThreads) hm_step_fx(NinvArgs a, NinvMaps x, i
             mx = av > mx ? av : mx;
             const double v = scale_pow2(__ll2double_rn(iv), sc);
             Wn[base + e] = v;
-            if (Wx) Wx[base + e] = split_pair(v);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, mx, o);
+            mx = other > mx ? other : mx;
+        }
+        if (lane == 0) atomicMax(&s_max, mx);
+        __syncthreads();
+        if (threadIdx.x == 0) Mn[j] = scale_pow2(__ull2double_ru(s_max), sc);
+        __syncthreads();
+    }
+}
+
+// round(x) for a float |x| < 2^62, integer operations only (half away from zero)
+__device__ __forceinline__ long long fx_round_f(float x) {
+    const int u = __float_as_int(x);
+    const int e = (u >> 23) & 0xFF;
+    if (e < 126) return 0;  // |x| < 1/2
+    const long long m = (long long)((u & 0x7FFFFF) | 0x800000);
+    const int sh = e - 150;
+    const long long q = sh >= 0 ? (m << sh) : ((m + (1ll << (-sh - 1))) >> -sh);
+    return u < 0 ? -q : q;
+}
+
+// nearest float to a nonzero integer |q| < 2^62 (ties to even), as a float and as the
+// integer it equals; integer operations only
+__device__ __forceinline__ float ll_to_float(long long q, long long& exact) {
+    if (q == 0) {
+        exact = 0;
+        return 0.f;
+    }
+    const bool neg = q < 0;
+    unsigned long long a = neg ? (unsigned long long)(-q) : (unsigned long long)q;
+    const int nb = 64 - __clzll((long long)a);
+    int sh = nb > 24 ? nb - 24 : 0;
+    unsigned long long mnt = a >> sh;
+    if (sh > 0) {
+        const unsigned long long rem = a & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (mnt & 1))) ++mnt;
+        if (mnt == (1ull << 24)) {
+            mnt >>= 1;
+            ++sh;
+        }
+    }
+    const unsigned long long back = mnt << sh;
+    exact = neg ? -(long long)back : (long long)back;
+    const int lead = 63 - __clzll((long long)mnt);  // 23 unless |q| < 2^23
+    const unsigned int bits = ((unsigned int)(127 + lead + sh) << 23) | ((unsigned int)(mnt << (23 - lead)) & 0x7FFFFFu);
+    return __int_as_float((int)(bits | (neg ? 0x80000000u : 0u)));
+}
+
+// Horner step of the pair form: W in pairs of floats, the product E_kj W[r, k] in
+// double-float (exact high product, both cross terms), both parts rounded to the
+// fixed-point grid 2^-s by integer operations and summed with 64-bit integer
+// shared atomics as in hm_step_fx; no FP64 operation.  The result is written as
+// pairs (hi = nearest float, lo = nearest float of the rest).
+__global__ void __launch_bounds__(kThreads) hm_step_fx2(NinvArgs a, NinvMaps x, int t, const float2* __restrict__ Ex,
+                                                        const float2* __restrict__ Wp, float2* __restrict__ Wn,
+                                                        const double* __restrict__ Mp, double* __restrict__ Mn,
+                                                        int32_t* ticket) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem_raw);
+    __shared__ int32_t s_j, s_s;
+    __shared__ unsigned long long s_max;
+    const int G = a.m + 2;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (;;) {
+        const int64_t j = take_column(ticket, &s_j);
+        if (j >= a.n) break;
+        const int64_t base = a.Wcp[j];
+        const int32_t nt = a.grp[j * G + t + 1];
+        const int64_t q0 = a.Lcp[j], q1 = a.Lcp[j + 1];
+        if (wid == 0) {
+            double b = 0.0;
+            for (int64_t q = q0 + lane; q < q1; q += 32) b += fabs(a.Lval[a.Lcsr[q]]) * Mp[a.Lri[q]];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+            if (lane == 0) {
+                int ex;
+                frexp(1.0 + b, &ex);
+                int sc = 61 - ex;
+                if (sc < 0 || !(b < 1e300)) {
+                    set_status(a.status, ST_UNSUPPORTED);
+                    sc = 0;
+                }
+                s_s = sc;
+                s_max = 0ull;
+            }
+        }
+        __syncthreads();
+        const int sc = s_s;
+        for (int32_t e = threadIdx.x; e < nt; e += kThreads) acc[e] = e == 0 ? (1ull << sc) : 0ull;
+        __syncthreads();
+        for (int64_t q = q0 + wid; q < q1; q += kWarps) {
+            const int32_t k = a.Lri[q];
+            const float2 e2 = Ex[q];
+            const float p2 = __int_as_float((127 + sc) << 23);  // 2^s (s <= 60)
+            const float eh = e2.x * p2, el = e2.y * p2;          // E_kj 2^s, exact
+            const float2* __restrict__ wk = Wp + a.Wcp[k];
+            const uint16_t* __restrict__ mp = x.hmap + x.moff[q];
+            const int32_t nk = a.grp[(int64_t)k * G + t];
+            for (int32_t e0 = 0; e0 < nk; e0 += 32 * kUnrollM) {
+                uint16_t p[kUnrollM];
+                float2 v[kUnrollM];
+#pragma unroll
+                for (int u = 0; u < kUnrollM; ++u) {
+                    const int32_t e = e0 + u * 32 + lane;
+                    p[u] = e < nk ? mp[e] : kNone;
+                    v[u] = e < nk ? wk[e] : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < kUnrollM; ++u) {
+                    if (p[u] == kNone) continue;
+                    const float ph = __fmul_rn(eh, v[u].x);
+                    float pl = __fmaf_rn(eh, v[u].x, -ph);
+                    pl = __fmaf_rn(eh, v[u].y, pl);
+                    pl = __fmaf_rn(el, v[u].x, pl);
+                    atomicAdd(acc + p[u], (unsigned long long)(fx_round_f(ph) + fx_round_f(pl)));
+                }
+            }
+        }
+        __syncthreads();
+        unsigned long long mx = 0ull;
+        for (int32_t e = threadIdx.x; e < nt; e += kThreads) {
+            const long long iv = (long long)acc[e];
+            const unsigned long long av = (unsigned long long)(iv < 0 ? -iv : iv);
+            mx = av > mx ? av : mx;
+            long long hi_exact, lo_exact;
+            const float hi = ll_to_float(iv, hi_exact);
+            const float lo = ll_to_float(iv - hi_exact, lo_exact);
+            const float m2 = __int_as_float((127 - sc) << 23);  // 2^-s, a normal float
+            Wn[base + e] = make_float2(hi * m2, lo * m2);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -451,13 +578,22 @@ __global__ void __launch_bounds__(kThreads) pm_product(NinvArgs a, NinvMaps x, i
 
 constexpr double kPairMax = 0x1p100;  // magnitude the pairs carry at full accuracy
 
-// D^{-1} per row as pairs (inputs outside the range the pairs carry are reported)
-__global__ void pair_prep(int64_t n, int32_t* status, const double* __restrict__ dr, const double* __restrict__ dp,
-                          float2* __restrict__ drx, float2* __restrict__ dpx) {
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-        if (!(fabs(dr[r]) < kPairMax) || !(fabs(dp[r]) < kPairMax)) set_status(status, ST_UNSUPPORTED);
-        drx[r] = split_pair(dr[r]);
-        dpx[r] = split_pair(dp[r]);
+// the inputs of the pair form as pairs: E_kj = -L_kj for every entry of E (CSC order)
+// and D^{-1} per row (inputs outside the range the pairs carry are reported)
+__global__ void pair_prep(NinvArgs a, const double* __restrict__ dr, const double* __restrict__ dp,
+                          float2* __restrict__ Ex, float2* __restrict__ drx, float2* __restrict__ dpx) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.nnzL + a.n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        if (q < a.nnzL) {
+            const double v = -a.Lval[a.Lcsr[q]];
+            if (!(fabs(v) < kPairMax)) set_status(a.status, ST_UNSUPPORTED);
+            Ex[q] = split_pair(v);
+        } else {
+            const int64_t r = q - a.nnzL;
+            if (!(fabs(dr[r]) < kPairMax) || !(fabs(dp[r]) < kPairMax)) set_status(a.status, ST_UNSUPPORTED);
+            drx[r] = split_pair(dr[r]);
+            dpx[r] = split_pair(dp[r]);
+        }
     }
 }
 
@@ -605,10 +741,10 @@ cudaError_t map_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N_
     for (int t = 1; t <= a.m; ++t) {
         trace_begin("ninv_map_horner", st);
         if constexpr (std::is_same<T, double>::value) {
-            hm_step_fx<<<grid, kThreads, map_smem<double>(), st>>>(a, x, t, cur, nxt, nullptr, M0, M1, tickets + t);
+            hm_step_fx<<<grid, kThreads, map_smem<double>(), st>>>(a, x, t, cur, nxt, M0, M1, tickets + t);
             std::swap(M0, M1);
         } else {
-            hm_step<T><<<grid, kThreads, map_smem<T>(), st>>>(a, x, t, cur, nxt, nullptr, tickets + t);
+            hm_step<T><<<grid, kThreads, map_smem<T>(), st>>>(a, x, t, cur, nxt, tickets + t);
         }
         trace_end(st);
         std::swap(cur, nxt);
@@ -618,8 +754,8 @@ cudaError_t map_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N_
     return cudaGetLastError();
 }
 
-// FP64 Horner steps (shared FP64 atomics) that also write W in pairs of floats
-// where a product follows; the product on S in pairs.
+// Pair form: W in pairs of floats throughout, the Horner steps in fixed point
+// (hm_step_fx2) and the product on S in double-float arithmetic (pp_product).
 cudaError_t pair_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N_out, double* N_stack,
                      cudaStream_t st) {
     char* p = reinterpret_cast<char*>(work);
@@ -628,13 +764,13 @@ cudaError_t pair_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N
         p += (bytes + 255) & ~(size_t)255;
         return r;
     };
-    double* W0 = reinterpret_cast<double*>(take((size_t)a.nnzW * sizeof(double)));
-    double* W1 = reinterpret_cast<double*>(take((size_t)a.nnzW * sizeof(double)));
+    float2* W0 = reinterpret_cast<float2*>(take((size_t)a.nnzW * sizeof(float2)));
+    float2* W1 = reinterpret_cast<float2*>(take((size_t)a.nnzW * sizeof(float2)));
     double* dr = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));
     double* dp = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));
     int32_t* part = reinterpret_cast<int32_t*>(take((size_t)a.n * sizeof(int32_t)));
     int32_t* tickets = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 64));
-    float2* Wx = reinterpret_cast<float2*>(take((size_t)a.nnzW * sizeof(float2)));
+    float2* Ex = reinterpret_cast<float2*>(take((size_t)std::max<int64_t>(a.nnzL, 1) * sizeof(float2)));
     float2* drx = reinterpret_cast<float2*>(take((size_t)a.n * sizeof(float2)));
     float2* dpx = reinterpret_cast<float2*>(take((size_t)a.n * sizeof(float2)));
     double* M0 = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));
@@ -645,30 +781,27 @@ cudaError_t pair_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N
     ninv_dinv_launch(a, dr, dp, part, st);
     trace_end(st);
     trace_begin("ninv_pair_prep", st);
-    pair_prep<<<a.num_sms * 4, 256, 0, st>>>(a.n, a.status, dr, dp, drx, dpx);
+    pair_prep<<<a.num_sms * 4, 256, 0, st>>>(a, dr, dp, Ex, drx, dpx);
     trace_end(st);
     trace_begin("ninv_init", st);
-    hm_init<double><<<a.num_sms * 4, 256, 0, st>>>(a.Wcp, W0, a.n);
-    hp_init<<<a.num_sms * 4, 256, 0, st>>>(a.Wcp, Wx, a.n);
+    hp_init<<<a.num_sms * 4, 256, 0, st>>>(a.Wcp, W0, a.n);
     fx_init<<<a.num_sms * 4, 256, 0, st>>>(M0, a.n);
     trace_end(st);
     const int grid = a.num_sms * 4;
-    double* cur = W0;
-    double* nxt = W1;
+    float2* cur = W0;
+    float2* nxt = W1;
     auto product = [&](int t, double* out, int32_t* tk) {
         trace_begin("ninv_pair_product", st);
-        pp_product<<<grid, kThreads, map_smem<double>(), st>>>(a, x, t, Wx, drx, dpx, out, tk);
+        pp_product<<<grid, kThreads, map_smem<double>(), st>>>(a, x, t, cur, drx, dpx, out, tk);
         trace_end(st);
     };
     if (N_stack) product(0, N_stack, tickets + 62 - a.m);
     for (int t = 1; t <= a.m; ++t) {
-        const bool pairs = t == a.m || N_stack != nullptr;
-        trace_begin("ninv_map_horner", st);
-        hm_step_fx<<<grid, kThreads, map_smem<double>(), st>>>(a, x, t, cur, nxt, pairs ? Wx : nullptr, M0, M1,
-                                                               tickets + t);
-        std::swap(M0, M1);
+        trace_begin("ninv_pair_horner", st);
+        hm_step_fx2<<<grid, kThreads, map_smem<double>(), st>>>(a, x, t, Ex, cur, nxt, M0, M1, tickets + t);
         trace_end(st);
         std::swap(cur, nxt);
+        std::swap(M0, M1);
         if (N_stack && t < a.m) product(t, N_stack + (int64_t)t * a.nnzS, tickets + 62 - a.m + t);
     }
     product(a.m, N_stack ? N_stack + (int64_t)a.m * a.nnzS : N_out, tickets + 63);
@@ -678,8 +811,8 @@ cudaError_t pair_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N
 }  // namespace
 
 size_t ninv_map_work_bytes(const NinvArgs& a, int prec) {
-    const size_t ts = prec == 1 ? sizeof(float) : sizeof(double);
-    const size_t pairs = prec == 2 ? ((size_t)a.nnzW + 2 * (size_t)a.n) * sizeof(float2) + 3 * 256 : 0;
+    const size_t ts = prec == 1 ? sizeof(float) : sizeof(double);  // a pair of floats is 8 bytes too
+    const size_t pairs = prec == 2 ? ((size_t)a.nnzL + 2 * (size_t)a.n) * sizeof(float2) + 3 * 256 : 0;
     const size_t bounds = 2 * ((size_t)a.n * sizeof(double) + 256);
     return 2 * ((size_t)a.nnzW * ts + 256) + (size_t)a.n * (2 * sizeof(double) + sizeof(int32_t)) + 3 * 256 +
            sizeof(int32_t) * 64 + 256 + pairs + bounds + 4096;
@@ -707,9 +840,9 @@ cudaError_t ninv_maps_configure() {
         if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTableSmem)) !=
             cudaSuccess)
             return e;
-    if ((e = cudaFuncSetAttribute(hm_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(hm_step_fx, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)map_smem<double>())) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(hm_step_fx, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (e = cudaFuncSetAttribute(hm_step_fx2, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)map_smem<double>())) != cudaSuccess ||
         (e = cudaFuncSetAttribute(hm_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)map_smem<float>())) != cudaSuccess ||
