@@ -614,6 +614,7 @@ def run_extra(args, rank, world):
         lc.mlp.predict(X, sc, Nst[3].contiguous())
 
     ms_learned = timed(learned_step, args.steps)
+    ms_stack = timed(lambda: h.ninv_stack(Lv, Dv, 3, "fp64"), args.steps)
     ms_selinv = timed(lambda: h.selinv(Lv, Dv, "fp64"), args.steps)
     h.sync_status()
     nS = 2 * h.nnz_S - h.n
@@ -626,8 +627,10 @@ def run_extra(args, rank, world):
                                        round(f.n ** (1 / 3)), f.n),
                        "stated_rel_error": "relative Frobenius error on S against SelInv FP64: reported, not bounded",
                        "train_entries": fit["entries"], "train_steps": fit["steps"], "train_s": fit["seconds"],
+                       "ninv_form": "map" if h.stats()["ninv_index_bytes"] > 0 else "hash",
                        "err_vs_selinv_ninv": ev["err_ninv"], "err_vs_selinv_learned": ev["err_learned"],
                        "keep_correction": LearnedCorrection.choose([ev]), "selinv_fp64_ms": ms_selinv,
+                       "ninv_stack_ms": ms_stack,
                        "input_gen_s": t_gen},
             "gpu_launches": None}
     if rank == 0:

@@ -22,11 +22,12 @@
 // The FP64 Horner step (hm_step_fx) sums in exact 64-bit fixed point with integer
 // shared atomics (bit-reproducible; one FP64 multiply per product).
 //
-// Pair form (SINV_FP32X2): W is kept as pairs hi + lo of floats.  The Horner step
-// (hm_step_fx2) forms each product in double-float arithmetic and sums it in the
-// same fixed point; the product on S (pp_product) runs in double-float arithmetic
-// with y formed in pairs, one writer per position.  No FP64 operation is left in
-// either kernel.
+// Pair form (SINV_FP32X2): the same fixed-point Horner steps also write W as pairs
+// hi + lo of floats where a product follows, and the product on S (pp_product)
+// runs in double-float arithmetic on the FP32 pipes, with y formed in pairs (one
+// writer per position): no FP64 operation is left in the product.  (A Horner step
+// with double-float products in the same fixed point was slower: its integer
+// rounding of two parts per product outweighed the FP64 multiply it saves.)
 //
 // The maps are built on the GPU from the same shared-memory tables as the hash
 // form; they need |col j| + extras <= kIdxEnt for every column.
@@ -183,6 +184,60 @@ __global__ void mmap_partner(int64_t n, const int8_t* __restrict__ pstart, int32
 
 // ---- numeric kernels ----
 
+// Streams the entries [0, count) of a column beside its map, 32 lanes wide with
+// kUnrollM chunks of loads in flight.  In the last, partial block a chunk that is
+// empty for the whole warp is skipped by a warp-uniform test, so no instruction of
+// apply runs for it (on the FP64 pipe an idle lane costs as much as a busy one).
+// load(e, p, v) reads entry e; apply(p, v) uses it when p != kNone.
+// The same with every block predicated instead (no uniform branches): faster where the
+// apply step is a cheap FP32 operation.
+template <class V, class Load, class Apply>
+__device__ __forceinline__ void stream_column_pred(int32_t count, int lane, Load load, Apply apply) {
+    for (int32_t e0 = 0; e0 < count; e0 += 32 * kUnrollM) {
+        uint16_t p[kUnrollM];
+        V v[kUnrollM];
+#pragma unroll
+        for (int u = 0; u < kUnrollM; ++u) {
+            const int32_t e = e0 + u * 32 + lane;
+            p[u] = kNone;
+            if (e < count) load(e, p[u], v[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnrollM; ++u)
+            if (p[u] != kNone) apply(p[u], v[u]);
+    }
+}
+
+template <class V, class Load, class Apply>
+__device__ __forceinline__ void stream_column(int32_t count, int lane, Load load, Apply apply) {
+    int32_t e0 = 0;
+    for (; e0 + 32 * kUnrollM <= count; e0 += 32 * kUnrollM) {
+        uint16_t p[kUnrollM];
+        V v[kUnrollM];
+#pragma unroll
+        for (int u = 0; u < kUnrollM; ++u) load(e0 + u * 32 + lane, p[u], v[u]);
+#pragma unroll
+        for (int u = 0; u < kUnrollM; ++u)
+            if (p[u] != kNone) apply(p[u], v[u]);
+    }
+    if (e0 < count) {
+        uint16_t p[kUnrollM];
+        V v[kUnrollM];
+#pragma unroll
+        for (int u = 0; u < kUnrollM; ++u) {
+            const int32_t e = e0 + u * 32 + lane;
+            p[u] = kNone;
+            if (e0 + u * 32 < count && e < count) load(e, p[u], v[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnrollM; ++u) {
+            if (e0 + u * 32 >= count) break;  // warp-uniform
+            if (p[u] != kNone) apply(p[u], v[u]);
+        }
+    }
+}
+
+
 // ---- the product in pairs of floats (FP64-class accuracy on the FP32 pipes) ----
 //
 // A value x is carried as hi + lo with hi = fl32(x) and lo = fl32(x - hi).  The
@@ -247,19 +302,13 @@ __global__ void __launch_bounds__(kThreads) hm_step(NinvArgs a, NinvMaps x, int 
             const T* __restrict__ wk = Wp + a.Wcp[k];
             const uint16_t* __restrict__ mp = x.hmap + x.moff[q];
             const int32_t nk = a.grp[(int64_t)k * G + t];  // rows of powers 0..t-1
-            for (int32_t e0 = 0; e0 < nk; e0 += 32 * kUnrollM) {
-                uint16_t p[kUnrollM];
-                T v[kUnrollM];
-#pragma unroll
-                for (int u = 0; u < kUnrollM; ++u) {
-                    const int32_t e = e0 + u * 32 + lane;
-                    p[u] = e < nk ? mp[e] : kNone;
-                    v[u] = e < nk ? wk[e] : T(0);
-                }
-#pragma unroll
-                for (int u = 0; u < kUnrollM; ++u)
-                    if (p[u] != kNone) atomicAdd(acc + p[u], ekj * v[u]);
-            }
+            stream_column<T>(
+                nk, lane,
+                [&](int32_t e, uint16_t& p, T& v) {
+                    p = mp[e];
+                    v = wk[e];
+                },
+                [&](uint16_t p, const T& v) { atomicAdd(acc + p, ekj * v); });
         }
         __syncthreads();
         for (int32_t e = threadIdx.x; e < nt; e += kThreads) Wn[base + e] = acc[e] + (e == 0 ? T(1) : T(0));
@@ -294,8 +343,8 @@ __device__ __forceinline__ long long fx_round(double x) {
 }
 
 __global__ void __launch_bounds__(kThreads) hm_step_fx(NinvArgs a, NinvMaps x, int t, const double* __restrict__ Wp,
-                                                       double* __restrict__ Wn, const double* __restrict__ Mp,
-                                                       double* __restrict__ Mn,
+                                                       double* __restrict__ Wn, float2* __restrict__ Wx,
+                                                       const double* __restrict__ Mp, double* __restrict__ Mn,
                                                        int32_t* ticket) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem_raw);
@@ -336,19 +385,13 @@ __global__ void __launch_bounds__(kThreads) hm_step_fx(NinvArgs a, NinvMaps x, i
             const double* __restrict__ wk = Wp + a.Wcp[k];
             const uint16_t* __restrict__ mp = x.hmap + x.moff[q];
             const int32_t nk = a.grp[(int64_t)k * G + t];
-            for (int32_t e0 = 0; e0 < nk; e0 += 32 * kUnrollM) {
-                uint16_t p[kUnrollM];
-                double v[kUnrollM];
-#pragma unroll
-                for (int u = 0; u < kUnrollM; ++u) {
-                    const int32_t e = e0 + u * 32 + lane;
-                    p[u] = e < nk ? mp[e] : kNone;
-                    v[u] = e < nk ? wk[e] : 0.0;
-                }
-#pragma unroll
-                for (int u = 0; u < kUnrollM; ++u)
-                    if (p[u] != kNone) atomicAdd(acc + p[u], (unsigned long long)fx_round(ekj * v[u]));
-            }
+            stream_column<double>(
+                nk, lane,
+                [&](int32_t e, uint16_t& p, double& v) {
+                    p = mp[e];
+                    v = wk[e];
+                },
+                [&](uint16_t p, const double& v) { atomicAdd(acc + p, (unsigned long long)fx_round(ekj * v)); });
         }
         __syncthreads();
         unsigned long long mx = 0ull;
@@ -358,138 +401,7 @@ __global__ void __launch_bounds__(kThreads) hm_step_fx(NinvArgs a, NinvMaps x, i
             mx = av > mx ? av : mx;
             const double v = scale_pow2(__ll2double_rn(iv), sc);
             Wn[base + e] = v;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long other = __shfl_xor_sync(0xffffffffu, mx, o);
-            mx = other > mx ? other : mx;
-        }
-        if (lane == 0) atomicMax(&s_max, mx);
-        __syncthreads();
-        if (threadIdx.x == 0) Mn[j] = scale_pow2(__ull2double_ru(s_max), sc);
-        __syncthreads();
-    }
-}
-
-// round(x) for a float |x| < 2^62, integer operations only (half away from zero)
-__device__ __forceinline__ long long fx_round_f(float x) {
-    const int u = __float_as_int(x);
-    const int e = (u >> 23) & 0xFF;
-    if (e < 126) return 0;  // |x| < 1/2
-    const long long m = (long long)((u & 0x7FFFFF) | 0x800000);
-    const int sh = e - 150;
-    const long long q = sh >= 0 ? (m << sh) : ((m + (1ll << (-sh - 1))) >> -sh);
-    return u < 0 ? -q : q;
-}
-
-// nearest float to a nonzero integer |q| < 2^62 (ties to even), as a float and as the
-// integer it equals; integer operations only
-__device__ __forceinline__ float ll_to_float(long long q, long long& exact) {
-    if (q == 0) {
-        exact = 0;
-        return 0.f;
-    }
-    const bool neg = q < 0;
-    unsigned long long a = neg ? (unsigned long long)(-q) : (unsigned long long)q;
-    const int nb = 64 - __clzll((long long)a);
-    int sh = nb > 24 ? nb - 24 : 0;
-    unsigned long long mnt = a >> sh;
-    if (sh > 0) {
-        const unsigned long long rem = a & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-        if (rem > half || (rem == half && (mnt & 1))) ++mnt;
-        if (mnt == (1ull << 24)) {
-            mnt >>= 1;
-            ++sh;
-        }
-    }
-    const unsigned long long back = mnt << sh;
-    exact = neg ? -(long long)back : (long long)back;
-    const int lead = 63 - __clzll((long long)mnt);  // 23 unless |q| < 2^23
-    const unsigned int bits = ((unsigned int)(127 + lead + sh) << 23) | ((unsigned int)(mnt << (23 - lead)) & 0x7FFFFFu);
-    return __int_as_float((int)(bits | (neg ? 0x80000000u : 0u)));
-}
-
-// Horner step of the pair form: W in pairs of floats, the product E_kj W[r, k] in
-// double-float (exact high product, both cross terms), both parts rounded to the
-// fixed-point grid 2^-s by integer operations and summed with 64-bit integer
-// shared atomics as in hm_step_fx; no FP64 operation.  The result is written as
-// pairs (hi = nearest float, lo = nearest float of the rest).
-__global__ void __launch_bounds__(kThreads) hm_step_fx2(NinvArgs a, NinvMaps x, int t, const float2* __restrict__ Ex,
-                                                        const float2* __restrict__ Wp, float2* __restrict__ Wn,
-                                                        const double* __restrict__ Mp, double* __restrict__ Mn,
-                                                        int32_t* ticket) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem_raw);
-    __shared__ int32_t s_j, s_s;
-    __shared__ unsigned long long s_max;
-    const int G = a.m + 2;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (;;) {
-        const int64_t j = take_column(ticket, &s_j);
-        if (j >= a.n) break;
-        const int64_t base = a.Wcp[j];
-        const int32_t nt = a.grp[j * G + t + 1];
-        const int64_t q0 = a.Lcp[j], q1 = a.Lcp[j + 1];
-        if (wid == 0) {
-            double b = 0.0;
-            for (int64_t q = q0 + lane; q < q1; q += 32) b += fabs(a.Lval[a.Lcsr[q]]) * Mp[a.Lri[q]];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
-            if (lane == 0) {
-                int ex;
-                frexp(1.0 + b, &ex);
-                int sc = 61 - ex;
-                if (sc < 0 || !(b < 1e300)) {
-                    set_status(a.status, ST_UNSUPPORTED);
-                    sc = 0;
-                }
-                s_s = sc;
-                s_max = 0ull;
-            }
-        }
-        __syncthreads();
-        const int sc = s_s;
-        for (int32_t e = threadIdx.x; e < nt; e += kThreads) acc[e] = e == 0 ? (1ull << sc) : 0ull;
-        __syncthreads();
-        for (int64_t q = q0 + wid; q < q1; q += kWarps) {
-            const int32_t k = a.Lri[q];
-            const float2 e2 = Ex[q];
-            const float p2 = __int_as_float((127 + sc) << 23);  // 2^s (s <= 60)
-            const float eh = e2.x * p2, el = e2.y * p2;          // E_kj 2^s, exact
-            const float2* __restrict__ wk = Wp + a.Wcp[k];
-            const uint16_t* __restrict__ mp = x.hmap + x.moff[q];
-            const int32_t nk = a.grp[(int64_t)k * G + t];
-            for (int32_t e0 = 0; e0 < nk; e0 += 32 * kUnrollM) {
-                uint16_t p[kUnrollM];
-                float2 v[kUnrollM];
-#pragma unroll
-                for (int u = 0; u < kUnrollM; ++u) {
-                    const int32_t e = e0 + u * 32 + lane;
-                    p[u] = e < nk ? mp[e] : kNone;
-                    v[u] = e < nk ? wk[e] : make_float2(0.f, 0.f);
-                }
-#pragma unroll
-                for (int u = 0; u < kUnrollM; ++u) {
-                    if (p[u] == kNone) continue;
-                    const float ph = __fmul_rn(eh, v[u].x);
-                    float pl = __fmaf_rn(eh, v[u].x, -ph);
-                    pl = __fmaf_rn(eh, v[u].y, pl);
-                    pl = __fmaf_rn(el, v[u].x, pl);
-                    atomicAdd(acc + p[u], (unsigned long long)(fx_round_f(ph) + fx_round_f(pl)));
-                }
-            }
-        }
-        __syncthreads();
-        unsigned long long mx = 0ull;
-        for (int32_t e = threadIdx.x; e < nt; e += kThreads) {
-            const long long iv = (long long)acc[e];
-            const unsigned long long av = (unsigned long long)(iv < 0 ? -iv : iv);
-            mx = av > mx ? av : mx;
-            long long hi_exact, lo_exact;
-            const float hi = ll_to_float(iv, hi_exact);
-            const float lo = ll_to_float(iv - hi_exact, lo_exact);
-            const float m2 = __int_as_float((127 - sc) << 23);  // 2^-s, a normal float
-            Wn[base + e] = make_float2(hi * m2, lo * m2);
+            if (Wx) Wx[base + e] = split_pair(v);  // for a product in pairs of floats
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -555,19 +467,13 @@ __global__ void __launch_bounds__(kThreads) pm_product(NinvArgs a, NinvMaps x, i
             const uint16_t* __restrict__ mp = x.pmap + x.poff[spos];
             const int32_t ni = a.grp[i * G + tlim + 1];
             T s = T(0);
-            for (int32_t f0 = 0; f0 < ni; f0 += 32 * kUnrollM) {
-                uint16_t p[kUnrollM];
-                T v[kUnrollM];
-#pragma unroll
-                for (int u = 0; u < kUnrollM; ++u) {
-                    const int32_t f = f0 + u * 32 + lane;
-                    p[u] = f < ni ? mp[f] : kNone;
-                    v[u] = f < ni ? wi[f] : T(0);
-                }
-#pragma unroll
-                for (int u = 0; u < kUnrollM; ++u)
-                    if (p[u] != kNone) s = fma_m<T>(v[u], y[p[u]], s);
-            }
+            auto load = [&](int32_t e, uint16_t& p, T& v) {
+                p = mp[e];
+                v = wi[e];
+            };
+            auto apply = [&](uint16_t p, const T& v) { s = fma_m<T>(v, y[p], s); };
+            if constexpr (std::is_same<T, float>::value) stream_column_pred<T>(ni, lane, load, apply);
+            else stream_column<T>(ni, lane, load, apply);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             if (lane == 0) N[spos] = (double)s;
@@ -578,22 +484,13 @@ __global__ void __launch_bounds__(kThreads) pm_product(NinvArgs a, NinvMaps x, i
 
 constexpr double kPairMax = 0x1p100;  // magnitude the pairs carry at full accuracy
 
-// the inputs of the pair form as pairs: E_kj = -L_kj for every entry of E (CSC order)
-// and D^{-1} per row (inputs outside the range the pairs carry are reported)
-__global__ void pair_prep(NinvArgs a, const double* __restrict__ dr, const double* __restrict__ dp,
-                          float2* __restrict__ Ex, float2* __restrict__ drx, float2* __restrict__ dpx) {
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.nnzL + a.n;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        if (q < a.nnzL) {
-            const double v = -a.Lval[a.Lcsr[q]];
-            if (!(fabs(v) < kPairMax)) set_status(a.status, ST_UNSUPPORTED);
-            Ex[q] = split_pair(v);
-        } else {
-            const int64_t r = q - a.nnzL;
-            if (!(fabs(dr[r]) < kPairMax) || !(fabs(dp[r]) < kPairMax)) set_status(a.status, ST_UNSUPPORTED);
-            drx[r] = split_pair(dr[r]);
-            dpx[r] = split_pair(dp[r]);
-        }
+// D^{-1} per row as pairs (inputs outside the range the pairs carry are reported)
+__global__ void pair_prep(int64_t n, int32_t* status, const double* __restrict__ dr, const double* __restrict__ dp,
+                          float2* __restrict__ drx, float2* __restrict__ dpx) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        if (!(fabs(dr[r]) < kPairMax) || !(fabs(dp[r]) < kPairMax)) set_status(status, ST_UNSUPPORTED);
+        drx[r] = split_pair(dr[r]);
+        dpx[r] = split_pair(dp[r]);
     }
 }
 
@@ -666,19 +563,13 @@ __global__ void __launch_bounds__(kThreads) pp_product(NinvArgs a, NinvMaps x, i
             const uint16_t* __restrict__ mp = x.pmap + x.poff[spos];
             const int32_t ni = a.grp[i * G + tlim + 1];
             float s = 0.f, c = 0.f;
-            for (int32_t f0 = 0; f0 < ni; f0 += 32 * kUnrollM) {
-                uint16_t p[kUnrollM];
-                float2 v[kUnrollM];
-#pragma unroll
-                for (int u = 0; u < kUnrollM; ++u) {
-                    const int32_t f = f0 + u * 32 + lane;
-                    p[u] = f < ni ? mp[f] : kNone;
-                    v[u] = f < ni ? wi[f] : make_float2(0.f, 0.f);
-                }
-#pragma unroll
-                for (int u = 0; u < kUnrollM; ++u)
-                    if (p[u] != kNone) pair_mac(v[u], y[p[u]], s, c);
-            }
+            stream_column<float2>(
+                ni, lane,
+                [&](int32_t e, uint16_t& p, float2& v) {
+                    p = mp[e];
+                    v = wi[e];
+                },
+                [&](uint16_t p, const float2& v) { pair_mac(v, y[p], s, c); });
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
                 pair_add(s, c, __shfl_xor_sync(0xffffffffu, s, o), __shfl_xor_sync(0xffffffffu, c, o));
@@ -741,7 +632,7 @@ cudaError_t map_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N_
     for (int t = 1; t <= a.m; ++t) {
         trace_begin("ninv_map_horner", st);
         if constexpr (std::is_same<T, double>::value) {
-            hm_step_fx<<<grid, kThreads, map_smem<double>(), st>>>(a, x, t, cur, nxt, M0, M1, tickets + t);
+            hm_step_fx<<<grid, kThreads, map_smem<double>(), st>>>(a, x, t, cur, nxt, nullptr, M0, M1, tickets + t);
             std::swap(M0, M1);
         } else {
             hm_step<T><<<grid, kThreads, map_smem<T>(), st>>>(a, x, t, cur, nxt, tickets + t);
@@ -754,8 +645,8 @@ cudaError_t map_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N_
     return cudaGetLastError();
 }
 
-// Pair form: W in pairs of floats throughout, the Horner steps in fixed point
-// (hm_step_fx2) and the product on S in double-float arithmetic (pp_product).
+// Pair form: the FP64 fixed-point Horner steps also write W as pairs of floats
+// where a product follows; the product on S runs in double-float arithmetic.
 cudaError_t pair_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N_out, double* N_stack,
                      cudaStream_t st) {
     char* p = reinterpret_cast<char*>(work);
@@ -764,13 +655,13 @@ cudaError_t pair_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N
         p += (bytes + 255) & ~(size_t)255;
         return r;
     };
-    float2* W0 = reinterpret_cast<float2*>(take((size_t)a.nnzW * sizeof(float2)));
-    float2* W1 = reinterpret_cast<float2*>(take((size_t)a.nnzW * sizeof(float2)));
+    double* W0 = reinterpret_cast<double*>(take((size_t)a.nnzW * sizeof(double)));
+    double* W1 = reinterpret_cast<double*>(take((size_t)a.nnzW * sizeof(double)));
     double* dr = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));
     double* dp = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));
     int32_t* part = reinterpret_cast<int32_t*>(take((size_t)a.n * sizeof(int32_t)));
     int32_t* tickets = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 64));
-    float2* Ex = reinterpret_cast<float2*>(take((size_t)std::max<int64_t>(a.nnzL, 1) * sizeof(float2)));
+    float2* Wx = reinterpret_cast<float2*>(take((size_t)a.nnzW * sizeof(float2)));
     float2* drx = reinterpret_cast<float2*>(take((size_t)a.n * sizeof(float2)));
     float2* dpx = reinterpret_cast<float2*>(take((size_t)a.n * sizeof(float2)));
     double* M0 = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));
@@ -781,24 +672,27 @@ cudaError_t pair_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N
     ninv_dinv_launch(a, dr, dp, part, st);
     trace_end(st);
     trace_begin("ninv_pair_prep", st);
-    pair_prep<<<a.num_sms * 4, 256, 0, st>>>(a, dr, dp, Ex, drx, dpx);
+    pair_prep<<<a.num_sms * 4, 256, 0, st>>>(a.n, a.status, dr, dp, drx, dpx);
     trace_end(st);
     trace_begin("ninv_init", st);
-    hp_init<<<a.num_sms * 4, 256, 0, st>>>(a.Wcp, W0, a.n);
+    hm_init<double><<<a.num_sms * 4, 256, 0, st>>>(a.Wcp, W0, a.n);
+    hp_init<<<a.num_sms * 4, 256, 0, st>>>(a.Wcp, Wx, a.n);
     fx_init<<<a.num_sms * 4, 256, 0, st>>>(M0, a.n);
     trace_end(st);
     const int grid = a.num_sms * 4;
-    float2* cur = W0;
-    float2* nxt = W1;
+    double* cur = W0;
+    double* nxt = W1;
     auto product = [&](int t, double* out, int32_t* tk) {
         trace_begin("ninv_pair_product", st);
-        pp_product<<<grid, kThreads, map_smem<double>(), st>>>(a, x, t, cur, drx, dpx, out, tk);
+        pp_product<<<grid, kThreads, map_smem<double>(), st>>>(a, x, t, Wx, drx, dpx, out, tk);
         trace_end(st);
     };
     if (N_stack) product(0, N_stack, tickets + 62 - a.m);
     for (int t = 1; t <= a.m; ++t) {
-        trace_begin("ninv_pair_horner", st);
-        hm_step_fx2<<<grid, kThreads, map_smem<double>(), st>>>(a, x, t, Ex, cur, nxt, M0, M1, tickets + t);
+        const bool pairs = t == a.m || N_stack != nullptr;
+        trace_begin("ninv_map_horner", st);
+        hm_step_fx<<<grid, kThreads, map_smem<double>(), st>>>(a, x, t, cur, nxt, pairs ? Wx : nullptr, M0, M1,
+                                                               tickets + t);
         trace_end(st);
         std::swap(cur, nxt);
         std::swap(M0, M1);
@@ -812,7 +706,7 @@ cudaError_t pair_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N
 
 size_t ninv_map_work_bytes(const NinvArgs& a, int prec) {
     const size_t ts = prec == 1 ? sizeof(float) : sizeof(double);  // a pair of floats is 8 bytes too
-    const size_t pairs = prec == 2 ? ((size_t)a.nnzL + 2 * (size_t)a.n) * sizeof(float2) + 3 * 256 : 0;
+    const size_t pairs = prec == 2 ? ((size_t)a.nnzW + 2 * (size_t)a.n) * sizeof(float2) + 3 * 256 : 0;
     const size_t bounds = 2 * ((size_t)a.n * sizeof(double) + 256);
     return 2 * ((size_t)a.nnzW * ts + 256) + (size_t)a.n * (2 * sizeof(double) + sizeof(int32_t)) + 3 * 256 +
            sizeof(int32_t) * 64 + 256 + pairs + bounds + 4096;
@@ -842,8 +736,7 @@ cudaError_t ninv_maps_configure() {
             return e;
     if ((e = cudaFuncSetAttribute(hm_step_fx, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)map_smem<double>())) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(hm_step_fx2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)map_smem<double>())) != cudaSuccess ||
+
         (e = cudaFuncSetAttribute(hm_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)map_smem<float>())) != cudaSuccess ||
         (e = cudaFuncSetAttribute(pm_product<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
