@@ -180,13 +180,14 @@ def kernel_rooflines(trace, st, m, k, nS_lo, prec, peaks, steps):
 
 # DRAM bytes (read + write) per unit of work from one ncu capture of the same kernel
 # build on the 32^3 case of this workload (profiles/ninv_map_kernels_diff3d_32_fp64.md):
-# Horner: 2.596 GB over the 757.9 M products of its 4 steps; product: 1.996 GB over
-# 811.8 M streamed map entries.  Scaled to a launch here by the units it processes.
-DRAM_PER_UNIT = {"ninv_map_horner": 2.596e9 / 757.933257e6, "ninv_map_product": 1.996266e9 / 811.837539e6}
+# FP64 Horner (hm_step_fx): 2.599 GB over the 757.9 M products of its 4 steps; FP64
+# product: 1.996 GB over 811.8 M streamed map entries.  Scaled to a launch here by
+# the units it processes.
+DRAM_PER_UNIT = {"ninv_map_horner": 2.5988e9 / 757.933257e6, "ninv_map_product": 1.99613e9 / 811.837539e6}
 
 
 def dram_traffic(kernel, prec, st, m):
-    if prec == "fp32" or kernel not in DRAM_PER_UNIT:
+    if prec != "fp64" or kernel not in DRAM_PER_UNIT:
         return None, None
     units = st["horner_products"] / max(m, 1) if kernel == "ninv_map_horner" else st["product_stream"]
     return DRAM_PER_UNIT[kernel] * units, ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the FP64 kernel on "
