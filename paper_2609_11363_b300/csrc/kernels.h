@@ -88,7 +88,8 @@ struct NinvArgs {
     int32_t num_sms;
     int32_t* status;
 };
-constexpr int kIdxEnt = 5440;  // longest column of P_W (with its partner rows) the maps handle
+constexpr int kIdxEnt = 5440;       // longest short column of P_W (with its partner rows)
+constexpr int kIdxEntLong = 16384;  // longest column the maps handle (large shared tables)
 // Map form of NInv (ninv_map.cu): per-entry positions resolved once per pattern and m.
 struct NinvMaps {
     bool ready = false;
@@ -101,6 +102,8 @@ struct NinvMaps {
     uint16_t* pmap = nullptr;   // y-table position of each row of column i (0xFFFF: y is zero)
     uint16_t* ypart = nullptr;  // nnz_W: y-table position of the partner row (2x2 rows only)
     int32_t* ynx = nullptr;     // n: extra y-table positions (partner rows outside the column)
+    int32_t* cols = nullptr;    // n: the short columns, then the long ones
+    int64_t n_short = 0, n_long = 0;
 };
 cudaError_t ninv_maps_configure();
 std::string ninv_maps_build(const NinvArgs& a, const HostPlan& P, const NinvPlan& W, int64_t budget,

@@ -30,7 +30,9 @@
 // rounding of two parts per product outweighed the FP64 multiply it saves.)
 //
 // The maps are built on the GPU from the same shared-memory tables as the hash
-// form; they need |col j| + extras <= kIdxEnt for every column.
+// form.  A column with its extra partner rows must fit a table: columns up to
+// kIdxEnt rows run several CTAs per SM, longer ones (up to kIdxEntLong) run in a
+// second launch with the large tables, one CTA per SM.
 #include <algorithm>
 #include <type_traits>
 #include <vector>
@@ -46,50 +48,62 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
-constexpr int kIdxSlots = 8192;
+constexpr int kSlotsShort = 8192;     // hash slots of a short column's table (kIdxEnt rows at most)
+constexpr int kSlotsLong = 32768;     // ... of a long column's table (kIdxEntLong rows at most)
 constexpr int kUnrollM = 8;
 constexpr int32_t kRowMask = 0x7FFFFFFF;
 constexpr int32_t kTwoFlag = (int32_t)0x80000000u;
 constexpr uint16_t kNone = 0xFFFF;
 
-__device__ __forceinline__ int64_t take_column(int32_t* ticket, int32_t* s_j) {
+// The columns a launch handles: a list (short columns or long columns, see
+// NinvMaps), taken one per CTA from a ticket counter.  Returns -1 when done.
+struct ColumnList {
+    const int32_t* cols;
+    int64_t count;
+};
+
+__device__ __forceinline__ int64_t take_column(int32_t* ticket, int32_t* s_j, ColumnList cl) {
     if (threadIdx.x == 0) *s_j = atomicAdd(ticket, 1);
     __syncthreads();
-    const int64_t j = *s_j;
+    const int64_t t = *s_j;
     __syncthreads();
-    return j;
+    return t < cl.count ? (int64_t)cl.cols[t] : -1;
 }
 
+template <int kSlots>
 struct TableSmem {
-    int32_t keys[kIdxSlots];
-    uint16_t loc[kIdxSlots];
+    int32_t keys[kSlots];
+    uint16_t loc[kSlots];
 };
 
 // rows of column j -> local position
-__device__ __forceinline__ void column_table(const NinvArgs& a, int64_t base, int32_t nj, TableSmem& t) {
-    for (int s = threadIdx.x; s < kIdxSlots; s += kThreads) t.keys[s] = -1;
+template <int kSlots>
+__device__ __forceinline__ void column_table(const NinvArgs& a, int64_t base, int32_t nj, TableSmem<kSlots>& t) {
+    for (int s = threadIdx.x; s < kSlots; s += kThreads) t.keys[s] = -1;
     __syncthreads();
     for (int32_t e = threadIdx.x; e < nj; e += kThreads)
-        t.loc[table_insert(t.keys, kIdxSlots - 1, a.Wr[base + e] & kRowMask)] = (uint16_t)e;
+        t.loc[table_insert(t.keys, kSlots - 1, a.Wr[base + e] & kRowMask)] = (uint16_t)e;
     __syncthreads();
 }
 
-__device__ __forceinline__ uint16_t lookup(const TableSmem& t, int32_t r) {
-    const int32_t h = table_find(t.keys, kIdxSlots - 1, r);
+template <int kSlots>
+__device__ __forceinline__ uint16_t lookup(const TableSmem<kSlots>& t, int32_t r) {
+    const int32_t h = table_find(t.keys, kSlots - 1, r);
     return h < 0 ? kNone : t.loc[h];
 }
 
 // Horner maps: hmap[moff[q] + e] = position in column j of row e of column k (e over
 // the powers 0..m-1 of column k), for every entry q = (k, j) of E.
-__global__ void __launch_bounds__(kThreads) hmap_build(NinvArgs a, NinvMaps x, int32_t* ticket) {
+template <int kSlots>
+__global__ void __launch_bounds__(kThreads) hmap_build(NinvArgs a, NinvMaps x, ColumnList cl, int32_t* ticket) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TableSmem& tb = *reinterpret_cast<TableSmem*>(smem_raw);
+    TableSmem<kSlots>& tb = *reinterpret_cast<TableSmem<kSlots>*>(smem_raw);
     __shared__ int32_t s_j;
     const int G = a.m + 2;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (;;) {
-        const int64_t j = take_column(ticket, &s_j);
-        if (j >= a.n) break;
+        const int64_t j = take_column(ticket, &s_j, cl);
+        if (j < 0) break;
         const int64_t base = a.Wcp[j];
         column_table(a, base, (int32_t)(a.Wcp[j + 1] - base), tb);
         for (int64_t q = a.Lcp[j] + wid; q < a.Lcp[j + 1]; q += kWarps) {
@@ -108,16 +122,17 @@ __global__ void __launch_bounds__(kThreads) hmap_build(NinvArgs a, NinvMaps x, i
 }
 
 // y tables and product maps.
+template <int kSlots>
 __global__ void __launch_bounds__(kThreads) pmap_build(NinvArgs a, NinvMaps x, const int32_t* __restrict__ part,
-                                                       int32_t* ticket, unsigned long long* hits) {
+                                                       ColumnList cl, int32_t* ticket, unsigned long long* hits) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TableSmem& tb = *reinterpret_cast<TableSmem*>(smem_raw);
+    TableSmem<kSlots>& tb = *reinterpret_cast<TableSmem<kSlots>*>(smem_raw);
     __shared__ int32_t s_j, s_extra;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned long long nhit = 0;
     for (;;) {
-        const int64_t j = take_column(ticket, &s_j);
-        if (j >= a.n) break;
+        const int64_t j = take_column(ticket, &s_j, cl);
+        if (j < 0) break;
         const int64_t base = a.Wcp[j];
         const int32_t nj = (int32_t)(a.Wcp[j + 1] - base);
         if (threadIdx.x == 0) s_extra = 0;
@@ -129,11 +144,11 @@ __global__ void __launch_bounds__(kThreads) pmap_build(NinvArgs a, NinvMaps x, c
             uint16_t pp = kNone;
             if (rf & kTwoFlag) {
                 const int32_t p = part[rf & kRowMask];
-                const int32_t h = table_find(tb.keys, kIdxSlots - 1, p);
+                const int32_t h = table_find(tb.keys, kSlots - 1, p);
                 if (h >= 0) {
                     pp = tb.loc[h];
                 } else {
-                    const int32_t slot = (int32_t)table_insert(tb.keys, kIdxSlots - 1, p);
+                    const int32_t slot = (int32_t)table_insert(tb.keys, kSlots - 1, p);
                     pp = (uint16_t)(nj + atomicAdd(&s_extra, 1));
                     tb.loc[slot] = pp;
                 }
@@ -282,16 +297,16 @@ template <>
 __device__ __forceinline__ float fma_m<float>(float a, float b, float c) { return fmaf(a, b, c); }
 
 template <class T>
-__global__ void __launch_bounds__(kThreads) hm_step(NinvArgs a, NinvMaps x, int t, const T* __restrict__ Wp,
-                                                    T* __restrict__ Wn, int32_t* ticket) {
+__global__ void __launch_bounds__(kThreads) hm_step(NinvArgs a, NinvMaps x, ColumnList cl, int t,
+                                                    const T* __restrict__ Wp, T* __restrict__ Wn, int32_t* ticket) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* acc = reinterpret_cast<T*>(smem_raw);
     __shared__ int32_t s_j;
     const int G = a.m + 2;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (;;) {
-        const int64_t j = take_column(ticket, &s_j);
-        if (j >= a.n) break;
+        const int64_t j = take_column(ticket, &s_j, cl);
+        if (j < 0) break;
         const int64_t base = a.Wcp[j];
         const int32_t nt = a.grp[j * G + t + 1];  // rows of powers 0..t
         for (int32_t e = threadIdx.x; e < nt; e += kThreads) acc[e] = T(0);
@@ -342,7 +357,8 @@ __device__ __forceinline__ long long fx_round(double x) {
     return u < 0 ? -(long long)q : (long long)q;
 }
 
-__global__ void __launch_bounds__(kThreads) hm_step_fx(NinvArgs a, NinvMaps x, int t, const double* __restrict__ Wp,
+__global__ void __launch_bounds__(kThreads) hm_step_fx(NinvArgs a, NinvMaps x, ColumnList cl, int t,
+                                                       const double* __restrict__ Wp,
                                                        double* __restrict__ Wn, float2* __restrict__ Wx,
                                                        const double* __restrict__ Mp, double* __restrict__ Mn,
                                                        int32_t* ticket) {
@@ -353,8 +369,8 @@ __global__ void __launch_bounds__(kThreads) hm_step_fx(NinvArgs a, NinvMaps x, i
     const int G = a.m + 2;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (;;) {
-        const int64_t j = take_column(ticket, &s_j);
-        if (j >= a.n) break;
+        const int64_t j = take_column(ticket, &s_j, cl);
+        if (j < 0) break;
         const int64_t base = a.Wcp[j];
         const int32_t nt = a.grp[j * G + t + 1];
         const int64_t q0 = a.Lcp[j], q1 = a.Lcp[j + 1];
@@ -421,7 +437,8 @@ __global__ void fx_init(double* __restrict__ M, int64_t n) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(kThreads) pm_product(NinvArgs a, NinvMaps x, int tlim, const T* __restrict__ W,
+__global__ void __launch_bounds__(kThreads) pm_product(NinvArgs a, NinvMaps x, ColumnList cl, int tlim,
+                                                       const T* __restrict__ W,
                                                        const double* __restrict__ dr, const double* __restrict__ dp,
                                                        double* __restrict__ N, int32_t* ticket) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -430,8 +447,8 @@ __global__ void __launch_bounds__(kThreads) pm_product(NinvArgs a, NinvMaps x, i
     const int G = a.m + 2;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (;;) {
-        const int64_t j = take_column(ticket, &s_j);
-        if (j >= a.n) break;
+        const int64_t j = take_column(ticket, &s_j, cl);
+        if (j < 0) break;
         const int64_t base = a.Wcp[j];
         const int32_t ny = (int32_t)(a.Wcp[j + 1] - base) + x.ynx[j];
         const int32_t nt = a.grp[j * G + tlim + 1];
@@ -504,7 +521,7 @@ __device__ __forceinline__ void pair_mul_add(float2 a, float2 b, float& s, float
 
 // Product on S in pairs: y = D^{-1} W[:, j] formed in pairs with one writer per
 // position, then the streamed sums of hp_step's arithmetic.
-__global__ void __launch_bounds__(kThreads) pp_product(NinvArgs a, NinvMaps x, int tlim,
+__global__ void __launch_bounds__(kThreads) pp_product(NinvArgs a, NinvMaps x, ColumnList cl, int tlim,
                                                        const float2* __restrict__ W, const float2* __restrict__ drx,
                                                        const float2* __restrict__ dpx, double* __restrict__ N,
                                                        int32_t* ticket) {
@@ -514,8 +531,8 @@ __global__ void __launch_bounds__(kThreads) pp_product(NinvArgs a, NinvMaps x, i
     const int G = a.m + 2;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (;;) {
-        const int64_t j = take_column(ticket, &s_j);
-        if (j >= a.n) break;
+        const int64_t j = take_column(ticket, &s_j, cl);
+        if (j < 0) break;
         const int64_t base = a.Wcp[j];
         const int32_t ny = (int32_t)(a.Wcp[j + 1] - base) + x.ynx[j];
         const int32_t nt = a.grp[j * G + tlim + 1];
@@ -590,9 +607,20 @@ __global__ void hm_init(const int64_t* __restrict__ Wcp, T* __restrict__ W, int6
         W[Wcp[j]] = T(1);
 }
 
-constexpr size_t kTableSmem = sizeof(TableSmem);
+template <int kSlots>
+constexpr size_t table_smem() { return sizeof(TableSmem<kSlots>); }
+// accumulator / y table of a column: short columns, or long ones (one CTA per SM)
 template <class T>
-constexpr size_t map_smem() { return (size_t)kIdxEnt * sizeof(T); }
+constexpr size_t acc_smem(bool lng) { return (size_t)(lng ? kIdxEntLong : kIdxEnt) * sizeof(T); }
+
+// Runs f(list, long?, grid, ticket offset) over the short columns, then the long ones.
+template <class F>
+void for_lists(const NinvMaps& x, int num_sms, F f) {
+    f(ColumnList{x.cols, x.n_short}, false, num_sms * 4, 0);
+    if (x.n_long) f(ColumnList{x.cols + x.n_short, x.n_long}, true, num_sms, 64);
+}
+
+constexpr int kTickets = 128;  // per launch site: [0, 64) short columns, [64, 128) long columns
 
 template <class T>
 cudaError_t map_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N_out, double* N_stack,
@@ -608,10 +636,10 @@ cudaError_t map_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N_
     double* dr = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));
     double* dp = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));
     int32_t* part = reinterpret_cast<int32_t*>(take((size_t)a.n * sizeof(int32_t)));
-    int32_t* tickets = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 64));
+    int32_t* tickets = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * kTickets));
     double* M0 = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));  // column bounds (FP64)
     double* M1 = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));
-    cudaError_t e = cudaMemsetAsync(tickets, 0, sizeof(int32_t) * 64, st);
+    cudaError_t e = cudaMemsetAsync(tickets, 0, sizeof(int32_t) * kTickets, st);
     if (e != cudaSuccess) return e;
     trace_begin("ninv_dinv", st);
     ninv_dinv_launch(a, dr, dp, part, st);
@@ -620,28 +648,32 @@ cudaError_t map_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N_
     hm_init<T><<<a.num_sms * 4, 256, 0, st>>>(a.Wcp, W0, a.n);
     if constexpr (std::is_same<T, double>::value) fx_init<<<a.num_sms * 4, 256, 0, st>>>(M0, a.n);
     trace_end(st);
-    const int grid = a.num_sms * 4;
     T* cur = W0;
     T* nxt = W1;
-    auto product = [&](int t, double* out, int32_t* tk) {
+    auto product = [&](int t, double* out, int tk) {
         trace_begin("ninv_map_product", st);
-        pm_product<T><<<grid, kThreads, map_smem<T>(), st>>>(a, x, t, cur, dr, dp, out, tk);
+        for_lists(x, a.num_sms, [&](ColumnList cl, bool lng, int grid, int off) {
+            pm_product<T><<<grid, kThreads, acc_smem<T>(lng), st>>>(a, x, cl, t, cur, dr, dp, out,
+                                                                    tickets + off + tk);
+        });
         trace_end(st);
     };
-    if (N_stack) product(0, N_stack, tickets + 62 - a.m);
+    if (N_stack) product(0, N_stack, 62 - a.m);
     for (int t = 1; t <= a.m; ++t) {
         trace_begin("ninv_map_horner", st);
-        if constexpr (std::is_same<T, double>::value) {
-            hm_step_fx<<<grid, kThreads, map_smem<double>(), st>>>(a, x, t, cur, nxt, nullptr, M0, M1, tickets + t);
-            std::swap(M0, M1);
-        } else {
-            hm_step<T><<<grid, kThreads, map_smem<T>(), st>>>(a, x, t, cur, nxt, tickets + t);
-        }
+        for_lists(x, a.num_sms, [&](ColumnList cl, bool lng, int grid, int off) {
+            if constexpr (std::is_same<T, double>::value)
+                hm_step_fx<<<grid, kThreads, acc_smem<double>(lng), st>>>(a, x, cl, t, cur, nxt, nullptr, M0, M1,
+                                                                          tickets + off + t);
+            else
+                hm_step<T><<<grid, kThreads, acc_smem<T>(lng), st>>>(a, x, cl, t, cur, nxt, tickets + off + t);
+        });
         trace_end(st);
         std::swap(cur, nxt);
-        if (N_stack && t < a.m) product(t, N_stack + (int64_t)t * a.nnzS, tickets + 62 - a.m + t);
+        std::swap(M0, M1);
+        if (N_stack && t < a.m) product(t, N_stack + (int64_t)t * a.nnzS, 62 - a.m + t);
     }
-    product(a.m, N_stack ? N_stack + (int64_t)a.m * a.nnzS : N_out, tickets + 63);
+    product(a.m, N_stack ? N_stack + (int64_t)a.m * a.nnzS : N_out, 63);
     return cudaGetLastError();
 }
 
@@ -660,13 +692,13 @@ cudaError_t pair_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N
     double* dr = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));
     double* dp = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));
     int32_t* part = reinterpret_cast<int32_t*>(take((size_t)a.n * sizeof(int32_t)));
-    int32_t* tickets = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 64));
+    int32_t* tickets = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * kTickets));
     float2* Wx = reinterpret_cast<float2*>(take((size_t)a.nnzW * sizeof(float2)));
     float2* drx = reinterpret_cast<float2*>(take((size_t)a.n * sizeof(float2)));
     float2* dpx = reinterpret_cast<float2*>(take((size_t)a.n * sizeof(float2)));
     double* M0 = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));
     double* M1 = reinterpret_cast<double*>(take((size_t)a.n * sizeof(double)));
-    cudaError_t e = cudaMemsetAsync(tickets, 0, sizeof(int32_t) * 64, st);
+    cudaError_t e = cudaMemsetAsync(tickets, 0, sizeof(int32_t) * kTickets, st);
     if (e != cudaSuccess) return e;
     trace_begin("ninv_dinv", st);
     ninv_dinv_launch(a, dr, dp, part, st);
@@ -679,26 +711,30 @@ cudaError_t pair_run(const NinvArgs& a, const NinvMaps& x, void* work, double* N
     hp_init<<<a.num_sms * 4, 256, 0, st>>>(a.Wcp, Wx, a.n);
     fx_init<<<a.num_sms * 4, 256, 0, st>>>(M0, a.n);
     trace_end(st);
-    const int grid = a.num_sms * 4;
     double* cur = W0;
     double* nxt = W1;
-    auto product = [&](int t, double* out, int32_t* tk) {
+    auto product = [&](int t, double* out, int tk) {
         trace_begin("ninv_pair_product", st);
-        pp_product<<<grid, kThreads, map_smem<double>(), st>>>(a, x, t, Wx, drx, dpx, out, tk);
+        for_lists(x, a.num_sms, [&](ColumnList cl, bool lng, int grid, int off) {
+            pp_product<<<grid, kThreads, acc_smem<double>(lng), st>>>(a, x, cl, t, Wx, drx, dpx, out,
+                                                                      tickets + off + tk);
+        });
         trace_end(st);
     };
-    if (N_stack) product(0, N_stack, tickets + 62 - a.m);
+    if (N_stack) product(0, N_stack, 62 - a.m);
     for (int t = 1; t <= a.m; ++t) {
         const bool pairs = t == a.m || N_stack != nullptr;
         trace_begin("ninv_map_horner", st);
-        hm_step_fx<<<grid, kThreads, map_smem<double>(), st>>>(a, x, t, cur, nxt, pairs ? Wx : nullptr, M0, M1,
-                                                               tickets + t);
+        for_lists(x, a.num_sms, [&](ColumnList cl, bool lng, int grid, int off) {
+            hm_step_fx<<<grid, kThreads, acc_smem<double>(lng), st>>>(a, x, cl, t, cur, nxt, pairs ? Wx : nullptr,
+                                                                      M0, M1, tickets + off + t);
+        });
         trace_end(st);
         std::swap(cur, nxt);
         std::swap(M0, M1);
-        if (N_stack && t < a.m) product(t, N_stack + (int64_t)t * a.nnzS, tickets + 62 - a.m + t);
+        if (N_stack && t < a.m) product(t, N_stack + (int64_t)t * a.nnzS, 62 - a.m + t);
     }
-    product(a.m, N_stack ? N_stack + (int64_t)a.m * a.nnzS : N_out, tickets + 63);
+    product(a.m, N_stack ? N_stack + (int64_t)a.m * a.nnzS : N_out, 63);
     return cudaGetLastError();
 }
 
@@ -709,7 +745,7 @@ size_t ninv_map_work_bytes(const NinvArgs& a, int prec) {
     const size_t pairs = prec == 2 ? ((size_t)a.nnzW + 2 * (size_t)a.n) * sizeof(float2) + 3 * 256 : 0;
     const size_t bounds = 2 * ((size_t)a.n * sizeof(double) + 256);
     return 2 * ((size_t)a.nnzW * ts + 256) + (size_t)a.n * (2 * sizeof(double) + sizeof(int32_t)) + 3 * 256 +
-           sizeof(int32_t) * 64 + 256 + pairs + bounds + 4096;
+           sizeof(int32_t) * kTickets + 256 + pairs + bounds + 4096;
 }
 
 cudaError_t ninv_map_launch(const NinvArgs& a, const NinvMaps& x, int prec, void* work, double* N_out,
@@ -721,31 +757,32 @@ cudaError_t ninv_map_launch(const NinvArgs& a, const NinvMaps& x, int prec, void
 }
 
 void ninv_maps_free(NinvMaps& x) {
-    void* ptrs[] = {x.moff, x.hmap, x.poff, x.pmap, x.ypart, x.ynx};
+    void* ptrs[] = {x.moff, x.hmap, x.poff, x.pmap, x.ypart, x.ynx, x.cols};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     x = NinvMaps();
 }
 
 cudaError_t ninv_maps_configure() {
-    cudaError_t e;
-    const void* fs[] = {(const void*)hmap_build, (const void*)pmap_build};
-    for (const void* f : fs)
-        if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTableSmem)) !=
-            cudaSuccess)
-            return e;
-    if ((e = cudaFuncSetAttribute(hm_step_fx, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)map_smem<double>())) != cudaSuccess ||
-
-        (e = cudaFuncSetAttribute(hm_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)map_smem<float>())) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(pm_product<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)map_smem<double>())) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(pp_product, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)map_smem<double>())) != cudaSuccess)
-        return e;
-    return cudaFuncSetAttribute(pm_product<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)map_smem<float>());
+    struct {
+        const void* f;
+        size_t bytes;
+    } ks[] = {
+        {(const void*)hmap_build<kSlotsShort>, table_smem<kSlotsShort>()},
+        {(const void*)pmap_build<kSlotsShort>, table_smem<kSlotsShort>()},
+        {(const void*)hmap_build<kSlotsLong>, table_smem<kSlotsLong>()},
+        {(const void*)pmap_build<kSlotsLong>, table_smem<kSlotsLong>()},
+        {(const void*)hm_step_fx, acc_smem<double>(true)},
+        {(const void*)hm_step<float>, acc_smem<float>(true)},
+        {(const void*)pm_product<double>, acc_smem<double>(true)},
+        {(const void*)pm_product<float>, acc_smem<float>(true)},
+        {(const void*)pp_product, acc_smem<double>(true)},
+    };
+    for (const auto& k : ks) {
+        const cudaError_t e = cudaFuncSetAttribute(k.f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.bytes);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 std::string ninv_maps_build(const NinvArgs& a, const HostPlan& P, const NinvPlan& Wp, int64_t budget,
@@ -754,15 +791,15 @@ std::string ninv_maps_build(const NinvArgs& a, const HostPlan& P, const NinvPlan
     ninv_maps_free(x);
     const int64_t n = a.n;
     const int G = a.m + 2;
-    // every column with its partner rows must fit the tables: |col j| + 2x2 rows <= kIdxEnt
-    {
-        int64_t worst = 0;
-        for (int64_t j = 0; j < n; ++j) {
-            int64_t c = 0;
-            for (int64_t e = Wp.Wcp[j]; e < Wp.Wcp[j + 1]; ++e) c += (Wp.Wr[e] & kTwoFlag) ? 1 : 0;
-            worst = std::max<int64_t>(worst, Wp.Wcp[j + 1] - Wp.Wcp[j] + c);
-        }
-        if (worst > kIdxEnt) return "a column of the series pattern exceeds the map tables";
+    // every column with its partner rows must fit a table: |col j| + 2x2 rows <= kIdxEnt
+    // (short columns), else <= kIdxEntLong (long columns, one CTA per SM)
+    std::vector<int32_t> cols_short, cols_long;
+    for (int64_t j = 0; j < n; ++j) {
+        int64_t c = 0;
+        for (int64_t e = Wp.Wcp[j]; e < Wp.Wcp[j + 1]; ++e) c += (Wp.Wr[e] & kTwoFlag) ? 1 : 0;
+        const int64_t need = Wp.Wcp[j + 1] - Wp.Wcp[j] + c;
+        if (need > kIdxEntLong) return "a column of the series pattern exceeds the map tables";
+        (need > kIdxEnt ? cols_long : cols_short).push_back((int32_t)j);
     }
     std::vector<int64_t> moff(P.nnzL + 1, 0), poff(P.nnzS + 1, 0);
     for (int64_t q = 0; q < P.nnzL; ++q) moff[q + 1] = moff[q] + Wp.grp[(int64_t)P.Lri[q] * G + a.m];
@@ -772,11 +809,11 @@ std::string ninv_maps_build(const NinvArgs& a, const HostPlan& P, const NinvPlan
     }
     for (int64_t q = 0; q < P.nnzS; ++q) poff[q + 1] += poff[q];
     const int64_t bytes = (P.nnzL + 1) * 8 + moff[P.nnzL] * 2 + (P.nnzS + 1) * 8 + poff[P.nnzS] * 2 +
-                          a.nnzW * 2 + n * 4;
+                          a.nnzW * 2 + n * 8;
     if (budget > 0 && bytes > budget) return "maps exceed the memory budget";
     auto alloc = [&](void** ptr, size_t b) { return cudaMalloc(ptr, std::max<size_t>(b, 16)); };
     int32_t* part = nullptr;
-    int32_t* tk = nullptr;  // 8 column tickets, then the hit counter
+    int32_t* tk = nullptr;  // 16 column tickets, then the hit counter
     auto fail = [&](cudaError_t e, const char* what) {
         err = e;
         if (part) cudaFree(part);
@@ -790,18 +827,27 @@ std::string ninv_maps_build(const NinvArgs& a, const HostPlan& P, const NinvPlan
         (e = alloc((void**)&x.poff, poff.size() * 8)) != cudaSuccess ||
         (e = alloc((void**)&x.pmap, poff[P.nnzS] * 2)) != cudaSuccess ||
         (e = alloc((void**)&x.ypart, a.nnzW * 2)) != cudaSuccess ||
-        (e = alloc((void**)&x.ynx, n * 4)) != cudaSuccess || (e = alloc((void**)&part, n * 4)) != cudaSuccess ||
-        (e = alloc((void**)&tk, 64)) != cudaSuccess)
+        (e = alloc((void**)&x.ynx, n * 4)) != cudaSuccess || (e = alloc((void**)&x.cols, n * 4)) != cudaSuccess ||
+        (e = alloc((void**)&part, n * 4)) != cudaSuccess || (e = alloc((void**)&tk, 128)) != cudaSuccess)
         return fail(e, "map alloc");
+    x.n_short = (int64_t)cols_short.size();
+    x.n_long = (int64_t)cols_long.size();
+    cols_short.insert(cols_short.end(), cols_long.begin(), cols_long.end());
     if ((e = cudaMemcpyAsync(x.moff, moff.data(), moff.size() * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(x.poff, poff.data(), poff.size() * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(tk, 0, 64, st)) != cudaSuccess)
+        (e = cudaMemcpyAsync(x.cols, cols_short.data(), n * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(tk, 0, 128, st)) != cudaSuccess)
         return fail(e, "map upload");
-    const int grid = a.num_sms * 2;
+    const ColumnList cs{x.cols, x.n_short}, cl{x.cols + x.n_short, x.n_long};
+    unsigned long long* dhits = reinterpret_cast<unsigned long long*>(tk + 16);
     mmap_partner<<<a.num_sms * 4, 256, 0, st>>>(n, a.pstart, part);
-    if (a.m > 0) hmap_build<<<grid, kThreads, kTableSmem, st>>>(a, x, tk);
-    unsigned long long* dhits = reinterpret_cast<unsigned long long*>(tk + 8);
-    pmap_build<<<grid, kThreads, kTableSmem, st>>>(a, x, part, tk + 1, dhits);
+    if (a.m > 0) {
+        hmap_build<kSlotsShort><<<a.num_sms * 2, kThreads, table_smem<kSlotsShort>(), st>>>(a, x, cs, tk);
+        if (x.n_long) hmap_build<kSlotsLong><<<a.num_sms, kThreads, table_smem<kSlotsLong>(), st>>>(a, x, cl, tk + 1);
+    }
+    pmap_build<kSlotsShort><<<a.num_sms * 2, kThreads, table_smem<kSlotsShort>(), st>>>(a, x, part, cs, tk + 2, dhits);
+    if (x.n_long)
+        pmap_build<kSlotsLong><<<a.num_sms, kThreads, table_smem<kSlotsLong>(), st>>>(a, x, part, cl, tk + 3, dhits);
     unsigned long long nh = 0;
     if ((e = cudaGetLastError()) != cudaSuccess ||
         (e = cudaMemcpyAsync(&nh, dhits, sizeof(nh), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||

@@ -174,23 +174,34 @@ def test_ninv_maps_reuse_and_m_change(case):
         assert sel_rel_err(out, N if mm == m else N1, *S) <= TOL64, (name, mm)
 
 
-def test_ninv_long_column_runs_hash_form():
-    """A column of the series pattern longer than the map tables: the hash form runs."""
-    n = 6200
+def _arrow_factors(n, seed):
+    """Column 0 of L full (an arrow): column 0 of the series pattern has n rows, and
+    planted 2x2 blocks further down give it partner rows."""
     rows = np.arange(1, n)
-    L = sp.csr_matrix((np.full(n - 1, 1e-3), (rows, np.zeros(n - 1, dtype=np.int64))), shape=(n, n))
+    rng = np.random.default_rng(seed)
+    L = sp.csr_matrix((rng.uniform(-1e-3, 1e-3, n - 1), (rows, np.zeros(n - 1, dtype=np.int64))), shape=(n, n))
     from workloads.factor import Factors
-    ps = np.ones(n, np.int8)
-    d = np.linspace(1.0, 2.0, n)
-    f = Factors(n, L.indptr.astype(np.int64), L.indices.astype(np.int32), L.data.copy(), ps, d,
-                np.zeros(n), {})
+    f = Factors(n, L.indptr.astype(np.int64), L.indices.astype(np.int32), L.data.copy(), np.ones(n, np.int8),
+                np.linspace(1.0, 2.0, n), np.zeros(n), {})
+    return plant_2x2(f, 0.1, seed)
+
+
+@pytest.mark.parametrize("n,form", [(6200, "map"), (17000, "hash")])
+def test_ninv_long_columns(n, form):
+    """A column longer than the short map tables runs in the long-column launch (map
+    form); one longer than the long tables sends the whole call to the hash form."""
+    f = _arrow_factors(n, 5)
     S = oracle.symbolic_S(f.n, f.L_rowptr, f.L_col, f.pivot_start)
-    Nr = oracle.ninv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, 2, S)
-    h = _handle(f)
-    out = h.ninv(_dev(f.L_val), _dev(f.D_packed), 2, "fp32x2")
-    h.sync_status()
-    assert h.stats()["ninv_index_bytes"] == 0
-    assert sel_rel_err(out.cpu().numpy(), Nr, *S) <= TOL64
+    for prec in ("fp64", "fp32x2", "fp32"):
+        Nr = oracle.ninv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, 2, S)
+        h = _handle(f)
+        out = h.ninv(_dev(f.L_val), _dev(f.D_packed), 2, prec)
+        h.sync_status()
+        _check_form(h, form)
+        if prec == "fp32":
+            assert normwise(out.cpu().numpy(), Nr) <= 1e-5
+        else:
+            assert sel_rel_err(out.cpu().numpy(), Nr, *S) <= TOL64, prec
 
 
 def test_ninv_index_over_budget_runs_hash_form():
