@@ -588,6 +588,7 @@ def run_extra(args, rank, world):
         h.close()
     fit = lc.fit(sets, epochs=2, lr=2e-3)
     del sets
+    torch.cuda.empty_cache()  # the inference matrix's NInv maps take half of the free memory
     f = test_w.factors
     h = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start, device=dev.index)
     Lv = torch.as_tensor(f.L_val, device=dev)
