@@ -74,13 +74,13 @@ typedef enum {
 typedef struct sinv_handle_s *sinv_handle;
 
 typedef struct {
-    int32_t supernode_cap;  /* max columns per supernode (1 disables merging); 0 = 16 */
+    int32_t supernode_cap;  /* max columns per supernode (1 disables merging); 0 = 4  */
     int32_t device;         /* CUDA device ordinal the handle lives on; -1 = host-only
                                analysis (no CUDA call; numeric calls then fail with
                                SINV_ERR_INVALID_ARG)                                  */
     int64_t wait_limit;     /* polls before a device wait gives up; 0 = default       */
     int64_t big_pairs;      /* supernodes with at least this many entries of S in
-                               C x C are processed by a whole CTA; 0 = default 2048   */
+                               C x C are processed by a whole CTA; 0 = default 1024   */
     int64_t ninv_index_bytes; /* device memory the map form of NInv may hold (the
                                positions of every product in the series pattern,
                                built by the first sinv_ninv of an m): 0 = half of

@@ -253,7 +253,7 @@ class Handle:
     host arrays describing strictly lower CSR L and the 1x1/2x2 pivot layout.
     """
 
-    def __init__(self, n, L_rowptr, L_col, pivot_start, supernode_cap=16, device=0, wait_limit=0, big_pairs=0,
+    def __init__(self, n, L_rowptr, L_col, pivot_start, supernode_cap=0, device=0, wait_limit=0, big_pairs=0,
                  ninv_index_bytes=0, _batch=None):
         self._lib = load_library()
         self._h = ctypes.c_void_p()

@@ -224,8 +224,8 @@ sinv_status sinv_symbolic(int64_t n, const int64_t* L_rowptr, const int32_t* L_c
         return SINV_ERR_INVALID_ARG;
     sinv_handle h = new (std::nothrow) sinv_handle_s();
     if (!h) return SINV_ERR_OOM;
-    int cap = 16;
-    int64_t big_pairs = 2048;
+    int cap = 4;
+    int64_t big_pairs = 1024;
     if (opts) {
         if (opts->supernode_cap > 0) cap = opts->supernode_cap;
         if (opts->big_pairs > 0) big_pairs = opts->big_pairs;
