@@ -47,9 +47,11 @@ def parse():
     p.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "fp32x2"],
                    help="fp32x2: FP64 with the NInv product on S in pairs of floats (FP64-class)")
     p.add_argument("--size", type=int, default=64)
-    p.add_argument("--workload", default="diff3d", choices=["diff3d", "batch9pt", "learned"],
+    p.add_argument("--workload", default="diff3d", choices=["diff3d", "batch9pt", "learned", "elastic"],
                    help="diff3d: the 64^3 step (default); batch9pt: 256 matrices in one graph-captured launch; "
-                        "learned: the trained NInv->SelInv correction on 128^3")
+                        "learned: the trained NInv->SelInv correction on 128^3; elastic: the 27-point 3-dof "
+                        "operator (N^3 nodes, --elastic-size N)")
+    p.add_argument("--elastic-size", type=int, default=24)
     p.add_argument("--batch", type=int, default=256, help="matrices of the batch9pt workload")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -570,6 +572,9 @@ def run_extra(args, rank, world):
         if rank == 0:
             print(json.dumps(line))
         return
+    if args.workload == "elastic":
+        run_elastic(args, rank, world, dev, peaks)
+        return
     # learned correction
     from paper_2609_11363_b300.learned import LearnedCorrection
     torch.cuda.set_device(dev)
@@ -633,6 +638,76 @@ def run_extra(args, rank, world):
                        "err_vs_selinv_ninv": ev["err_ninv"], "err_vs_selinv_learned": ev["err_learned"],
                        "keep_correction": LearnedCorrection.choose([ev]), "selinv_fp64_ms": ms_selinv,
                        "ninv_stack_ms": ms_stack,
+                       "input_gen_s": t_gen},
+            "gpu_launches": None}
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def run_elastic(args, rank, world, dev, peaks):
+    """27-point 3-dof elastic-like operator (the 80^3-node configuration's structure,
+    at N^3 nodes: its host ILDL at tau = 1e-4 grows to tens of minutes at 80^3).
+    One step = SelInv (FP32 form) + NInv m = 2 (FP32) + Mix + rank-64 correction
+    (FP32), inputs resident; FP64 SelInv is timed beside it."""
+    import torch
+    from paper_2609_11363_b300 import Handle
+    from workloads.configs import elastic3d, random_lowrank
+    torch.cuda.set_device(dev)
+    t0 = time.time()
+    w = elastic3d(args.elastic_size)
+    f = w.factors
+    V, lam = random_lowrank(f.n, w.k, seed=5)
+    t_gen = time.time() - t0
+    h = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start, device=dev.index)
+    Lv = torch.as_tensor(f.L_val, device=dev)
+    Dv = torch.as_tensor(f.D_packed, device=dev)
+    Vd = torch.as_tensor(V, device=dev)
+    ld = torch.as_tensor(lam, device=dev)
+    G = torch.empty(h.nnz_S, dtype=torch.float64, device=dev)
+    N = torch.empty_like(G)
+    M = torch.empty_like(G)
+    h.selinv(Lv, Dv, "fp64", out=G)
+    eps = 1e-3 * float(G.abs().max())  # the diagonal dominates |G| on this SPD operator
+
+    def step():
+        h.selinv(Lv, Dv, "fp32", out=G)
+        h.ninv(Lv, Dv, w.m, "fp32", out=N)
+        h.mix(G, N, eps, out=M)
+        h.lowrank_correct(Vd, ld, M, "fp32")
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        out = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return float(np.median(out))
+
+    for _ in range(args.warmup):
+        step()
+    ms = timed(step, args.steps)
+    ms_sel64 = timed(lambda: h.selinv(Lv, Dv, "fp64", out=G), args.steps)
+    ms_sel32 = timed(lambda: h.selinv(Lv, Dv, "fp32", out=G), args.steps)
+    ms_ninv = timed(lambda: h.ninv(Lv, Dv, w.m, "fp32", out=N), args.steps)
+    h.sync_status()
+    st = h.stats()
+    nS = 2 * h.nnz_S - h.n
+    line = {"metric": METRIC, "value": world * nS / (ms / 1e3), "unit": "entries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "elastic: 27-point 3-dof lattice-spring operator %d^3 nodes (n=%d), ILDL tau=1e-4, "
+                                   "SelInv + NInv m=%d + Mix + rank-%d correction, FP32 form"
+                                   % (args.elastic_size, f.n, w.m, w.k),
+                       "stated_rel_error": STATED_ERROR["fp32"], "nnz_L": st["nnz_L"], "S_entries": nS,
+                       "supernodes": st["n_supernodes"], "max_width": st["max_width"], "levels": st["n_levels"],
+                       "nnz_W": st["nnz_W"], "ninv_form": "map" if st["ninv_index_bytes"] > 0 else "hash",
+                       "selinv_fp64_ms": ms_sel64, "selinv_fp32_ms": ms_sel32, "ninv_fp32_ms": ms_ninv,
                        "input_gen_s": t_gen},
             "gpu_launches": None}
     if rank == 0:

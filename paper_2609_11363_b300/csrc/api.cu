@@ -116,6 +116,9 @@ struct sinv_handle_s {
     int32_t* dhit_pos = nullptr;
     int32_t* dhrow = nullptr;
     WorkItem* ditems = nullptr;
+    int64_t* dxsum_off = nullptr;
+    double* dxsum = nullptr;
+    uint32_t* darrive = nullptr;
     uint32_t* ddone = nullptr;
     uint32_t* depoch = nullptr;
     int32_t* dticket = nullptr;
@@ -163,7 +166,7 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
 void free_all(sinv_handle h) {
     void* ptrs[] = {h->dSrp, h->dSc, h->dSdiag, h->dl2s, h->dLrp, h->dLcp, h->dLri, h->dLcsr, h->ddpos, h->dpstart,
                     h->dsn, h->dorder, h->downer, h->dCrow, h->dLmap, h->dJJl, h->dJJs, h->dhit_ik, h->dhit_pos,
-                    h->dhrow, h->ditems, h->ddone, h->depoch, h->dticket, h->dstatus, h->ddebug_flag, h->dscratch, h->dwork, h->dWcp,
+                    h->dhrow, h->ditems, h->dxsum_off, h->dxsum, h->darrive, h->ddone, h->depoch, h->dticket, h->dstatus, h->ddebug_flag, h->dscratch, h->dwork, h->dWcp,
                     h->dWr, h->dgrp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -294,10 +297,16 @@ sinv_status sinv_symbolic(int64_t n, const int64_t* L_rowptr, const int32_t* L_c
     UP(dhit_pos, P.hit_pos);
     UP(dhrow, P.hrow);
     UP(ditems, P.items);
+    UP(dxsum_off, P.xsum_off);
 #undef UP
     size_t nsn = std::max<size_t>(P.sn.size(), 1);
+    const size_t nxs = (size_t)std::max<int64_t>(P.xsum_total, 1);
     if ((e = cudaMalloc((void**)&h->ddone, nsn * sizeof(uint32_t))) != cudaSuccess ||
         (e = cudaMemset(h->ddone, 0, nsn * sizeof(uint32_t))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&h->darrive, nsn * sizeof(uint32_t))) != cudaSuccess ||
+        (e = cudaMemset(h->darrive, 0, nsn * sizeof(uint32_t))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&h->dxsum, nxs * sizeof(double))) != cudaSuccess ||
+        (e = cudaMemset(h->dxsum, 0, nxs * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc((void**)&h->depoch, 64)) != cudaSuccess || (e = cudaMemset(h->depoch, 0, 64)) != cudaSuccess ||
         (e = cudaMalloc((void**)&h->dticket, 64)) != cudaSuccess ||
         (e = cudaMemset(h->dticket, 0, 64)) != cudaSuccess ||
@@ -490,7 +499,14 @@ sinv_status sinv_selinv(sinv_handle h, const double* L_val, const double* D_val,
     a.max_cw = P.max_cw;
     a.nnzS = P.nnzS;
     a.num_sms = h->num_sms;
+    a.xsum_off = h->dxsum_off;
+    a.xsum = h->dxsum;
+    a.arrive = h->darrive;
     if ((e = selinv_prepare(h->depoch, h->dticket, st)) != cudaSuccess) return cuda_fail(h, e, "selinv prepare");
+    if (P.xsum_total > 0 &&  // partial sums and arrival counts of the supernodes split over CTAs
+        ((e = cudaMemsetAsync(h->dxsum, 0, (size_t)P.xsum_total * sizeof(double), st)) != cudaSuccess ||
+         (e = cudaMemsetAsync(h->darrive, 0, P.sn.size() * sizeof(uint32_t), st)) != cudaSuccess))
+        return cuda_fail(h, e, "selinv prepare");
     if ((e = selinv_launch(a, prec == SINV_FP32 ? 1 : 0, h->dwork, G_S, st, h->grid)) != cudaSuccess)
         return cuda_fail(h, e, "selinv launch");
     return SINV_OK;

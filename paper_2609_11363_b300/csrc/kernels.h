@@ -44,6 +44,9 @@ struct SelinvArgs {
     int64_t max_cw;
     int64_t nnzS;
     int32_t num_sms;
+    const int64_t* xsum_off;  // per supernode: its partial-sum block when split over CTAs, else -1
+    double* xsum;             // the blocks (zeroed before every launch)
+    uint32_t* arrive;         // per supernode: parts arrived in this call (zeroed before every launch)
 };
 
 cudaError_t selinv_configure();

@@ -24,9 +24,9 @@ struct SnInfo {
 // whole CTA processes, or up to kGroup consecutive small ones, one per warp.
 struct WorkItem {
     int32_t first;  // index into the processing order
-    int32_t count;  // supernodes in the item
-    int32_t big;    // 1: CTA-cooperative
-    int32_t pad;
+    int32_t count;  // supernodes in the item; for a part of a split supernode: the number of parts
+    int32_t big;    // 1: CTA-cooperative; 2: one part of a supernode split over several CTAs
+    int32_t part;   // the part (big == 2)
 };
 
 struct HostPlan {
@@ -55,6 +55,9 @@ struct HostPlan {
     std::vector<int32_t> hit_pos;    // S_lo position of (max, min) of (C[i], C[k])
     std::vector<int32_t> hrow;       // per supernode c+1 row starts
     std::vector<WorkItem> items;
+    // supernodes split over several CTAs: offset of their c*w partial-sum block (-1: not split)
+    std::vector<int64_t> xsum_off;
+    int64_t xsum_total = 0;
     int64_t n_levels = 0, max_c = 0, max_w = 0, max_cw = 0, hit_pairs = 0;
     // algorithmic work of one SelInv: 2 w flops per pair of C x C in S, 2 c w^2 for
     // the diagonal block; bytes: each entry of S in C x C once (8 B) and L_CJ in, X out

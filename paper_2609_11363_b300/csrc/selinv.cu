@@ -66,6 +66,7 @@ static_assert(sizeof(WarpSmem) * kWarps >= (2 * sizeof(double) + sizeof(int32_t)
 struct CtaShared {
     int item;
     int stop;
+    int last;    // this CTA finishes a split supernode
     double jj[kWMax * kWMax];
     double t[kWMax * kWMax];
     double red[kWarps][kPairs];
@@ -149,9 +150,14 @@ __device__ __forceinline__ void accumulate_pairs(PairRange& pr, const uint32_t* 
 // One supernode on a group (warp or CTA).  Returns false when a wait gave up.
 // Phase A reads only the inputs and the plan (it overlaps the producers of C);
 // phase B waits for them; phase C reads G, forms X and G_JJ and publishes.
+// A supernode split over nparts CTAs (nparts > 1, CTA groups only): part `part` takes
+// a range of rows of C balanced by pairs, adds its share of X into the supernode's
+// global block with device atomics, and the last part to arrive (an arrival count,
+// no waiting) reads the complete X back and finishes the supernode.  Blocks and
+// counts are zeroed in stream order before every launch.
 template <class Form, bool kCta>
 __device__ bool process(const SelinvArgs& a, typename Form::G* Gw, int J, uint32_t epoch, WarpSmem* ws,
-                        CtaShared* cs, int64_t gslot) {
+                        CtaShared* cs, int64_t gslot, int part = 0, int nparts = 1) {
     using R = typename Form::R;
     using Gr = Group<kCta>;
     const SnInfo I = a.sn[J];
@@ -214,8 +220,12 @@ __device__ bool process(const SelinvArgs& a, typename Form::G* Gw, int J, uint32
             }
             return hrow[lo];
         };
-        pr.e0 = v == 0 ? 0 : row_start_at(E * v / kWarps);
-        pr.e1 = v == kWarps - 1 ? E : row_start_at(E * (v + 1) / kWarps);
+        // this part's rows, then this warp's share of them
+        const int64_t p0 = part == 0 ? 0 : row_start_at(E * part / nparts);
+        const int64_t p1 = part == nparts - 1 ? E : row_start_at(E * (part + 1) / nparts);
+        pr.e0 = v == 0 ? p0 : row_start_at(p0 + (p1 - p0) * v / kWarps);
+        pr.e1 = v == kWarps - 1 ? p1 : row_start_at(p0 + (p1 - p0) * (v + 1) / kWarps);
+        if (pr.e1 < pr.e0) pr.e1 = pr.e0;
     }
     load_pairs(hik, hpos, pr.e0, pr.e1, lane, pr.ik, pr.pos);
     Gr::sync();
@@ -290,6 +300,22 @@ __device__ bool process(const SelinvArgs& a, typename Form::G* Gw, int J, uint32
     // ---- phase C ---------------------------------------------------------------------
     accumulate_pairs<Form>(pr, hik, hpos, Gw, lh, x, w, lane);
     Gr::sync();
+    if (kCta && nparts > 1) {
+        double* blk = a.xsum + a.xsum_off[J];
+        for (int e = tid; e < cw; e += gsz) {
+            const double v = Form::to_d(x[e]);
+            if (v != 0.0) atomicAdd(blk + e, v);
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) cs->last = atomicAdd(a.arrive + J, 1u) == (uint32_t)(nparts - 1) ? 1 : 0;
+        __syncthreads();
+        if (!cs->last) return true;  // another part finishes the supernode
+        __threadfence();
+        // the last part reads the complete X (the blocks and counts are cleared before each call)
+        for (int e = tid; e < cw; e += gsz) x[e] = Form::from_d(__ldcg(blk + e));
+        Gr::sync();
+    }
     for (int e = tid; e < cw; e += gsz) {
         const int p = xpos[e];
         if (p >= 0) Form::st(Gw + p, x[e]);
@@ -348,7 +374,10 @@ __global__ void __launch_bounds__(kWarps * 32) selinv_persistent(SelinvArgs a, t
         const int item = cs.item;
         if (item >= a.nitems || cs.stop) break;
         const WorkItem it = a.items[item];
-        if (it.big) {
+        if (it.big == 2) {
+            process<Form, true>(a, Gw, a.order[it.first], epoch, ws, &cs, (int64_t)blockIdx.x * kWarps, it.part,
+                                it.count);
+        } else if (it.big) {
             process<Form, true>(a, Gw, a.order[it.first], epoch, ws, &cs, (int64_t)blockIdx.x * kWarps);
         } else if (warp < it.count) {
             process<Form, false>(a, Gw, a.order[it.first + warp], epoch, ws, &cs,

@@ -371,16 +371,36 @@ std::string build_plan(int64_t n, const int64_t* Lrp, const int32_t* Lc, const i
     });
     // work items: a large supernode alone (whole CTA), else up to `group` consecutive ones.
     // Levels with fewer supernodes than thin_level sit on the critical path of the
-    // dependency chain: each of their supernodes gets a whole CTA to shorten it.
+    // dependency chain: each of their supernodes gets a whole CTA to shorten it.  A
+    // supernode with more than 4 big_pairs pairs is split by rows into parts of about
+    // that size (at most kMaxParts), one CTA each: the parts add their share of X into
+    // a global block and the last part to arrive finishes the supernode.
+    constexpr int64_t kMaxParts = 16;
+    const int64_t part_pairs = 4 * big_pairs;
     std::vector<int64_t> level_size(P.n_levels, 0);
     for (int64_t s = 0; s < ns; ++s) level_size[P.sn[s].level]++;
     P.items.clear();
+    P.xsum_off.assign(ns, -1);
+    P.xsum_total = 0;
     for (int64_t t = 0; t < ns;) {
         const SnInfo& I = P.sn[P.order[t]];
         WorkItem it;
         it.first = (int32_t)t;
-        it.pad = 0;
+        it.part = 0;
         if (I.hit_cnt >= big_pairs || level_size[I.level] < thin_level) {
+            const int64_t parts = std::min<int64_t>(kMaxParts, (I.hit_cnt + part_pairs - 1) / part_pairs);
+            if (parts >= 2 && I.c >= 2 * parts) {
+                P.xsum_off[P.order[t]] = P.xsum_total;
+                P.xsum_total += (int64_t)I.c * I.w;
+                for (int64_t q = 0; q < parts; ++q) {
+                    it.count = (int32_t)parts;
+                    it.big = 2;
+                    it.part = (int32_t)q;
+                    P.items.push_back(it);
+                }
+                ++t;
+                continue;
+            }
             it.count = 1;
             it.big = 1;
             ++t;

@@ -72,6 +72,22 @@ def test_selinv_fp64(case, cap):
     assert err <= TOL64, (name, err)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_selinv_split_supernodes(case, prec):
+    """A small whole-CTA threshold splits every supernode with more than 4 x 64 pairs
+    over several CTAs (parts summed in a global block, finished by the last part)."""
+    name, f, m, S, G, N = case
+    h = _handle(f, big_pairs=64)
+    Lv, Dv = _dev(f.L_val), _dev(f.D_packed)
+    for _ in range(2):  # the blocks and counts are cleared before every call
+        out = h.selinv(Lv, Dv, prec).cpu().numpy()
+        h.sync_status()
+        if prec == "fp64":
+            assert sel_rel_err(out, G, *S) <= TOL64, name
+        else:
+            assert normwise(out, G) <= 1e-5, name
+
+
 def test_selinv_repeat_is_deterministic(case):
     name, f, m, S, G, N = case
     h = _handle(f)
