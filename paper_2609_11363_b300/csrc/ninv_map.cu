@@ -333,29 +333,20 @@ __global__ void __launch_bounds__(kThreads) hm_step(NinvArgs a, NinvMaps x, Colu
 
 // FP64 Horner step with exact integer accumulation.  Column j of W_t is bounded a
 // priori, |W_t[r, j]| <= B = 1 + sum_k |E_kj| max_r |W_{t-1}[r, k]| (every partial
-// sum too), so with the scale 2^s, s = 61 - ceil(log2 B), each product E_kj W[r, k]
-// is rounded once (by integer operations, fx_round) to an integer multiple of 2^-s
-// and summed with 64-bit integer
-// shared-memory atomics: no overflow, an order-independent (bit-reproducible) sum,
-// absolute error below (|struct(j)| + 1) 2^-s <= 2^-52 B per entry, and one FP64
-// operation per product (the multiply) where an FP64 atomic add would take a second.
-// The step also records max_r |W_t[r, j]| for the next step's bound.
+// sum too), so on the grid 2^-s with s = 50 - ceil(log2 B) every product and every
+// partial sum stays below 2^50 in grid units.  One fused multiply-add with the
+// constant 1.5 * 2^52 rounds E_kj 2^s W[r, k] to the nearest grid point (a single
+// rounding of the exact product) and leaves that integer in the low bits of the
+// result; the integers are summed with 64-bit integer shared-memory atomics: an
+// order-independent (bit-reproducible) sum, absolute error below
+// (|struct(j)| + 1) 2^-(s+1) <= 2^-50 B per entry, and one FP64 operation per
+// product.  The step also records max_r |W_t[r, j]| for the next step's bound.
 __device__ __forceinline__ double scale_pow2(double v, int s) {
     // v * 2^-s for a normal v whose result stays normal, by the exponent field
     return v == 0.0 ? 0.0 : __longlong_as_double(__double_as_longlong(v) - ((long long)s << 52));
 }
 
-// round(x) for |x| < 2^62 with integer operations only (rounding half away from zero):
-// x = m 2^(e - 1075) with the 53-bit significand m
-__device__ __forceinline__ long long fx_round(double x) {
-    const long long u = __double_as_longlong(x);
-    const int e = (int)((u >> 52) & 0x7FF);
-    if (e < 1022) return 0;  // |x| < 1/2 (zeros and subnormals included)
-    const unsigned long long m = ((unsigned long long)u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = e - 1075;
-    const unsigned long long q = sh >= 0 ? (m << sh) : ((m + (1ull << (-sh - 1))) >> -sh);
-    return u < 0 ? -(long long)q : (long long)q;
-}
+constexpr double kRoundMagic = 6755399441055744.0;  // 1.5 * 2^52: its ulp is 1
 
 __global__ void __launch_bounds__(kThreads) hm_step_fx(NinvArgs a, NinvMaps x, ColumnList cl, int t,
                                                        const double* __restrict__ Wp,
@@ -382,7 +373,7 @@ __global__ void __launch_bounds__(kThreads) hm_step_fx(NinvArgs a, NinvMaps x, C
             if (lane == 0) {
                 int ex;
                 frexp(1.0 + b, &ex);  // 1 + b < 2^ex
-                int sc = 61 - ex;
+                int sc = 50 - ex;
                 if (sc < 0 || !(b < 1e300)) {  // W too large for the fixed-point range
                     set_status(a.status, ST_UNSUPPORTED);
                     sc = 0;
@@ -398,6 +389,7 @@ __global__ void __launch_bounds__(kThreads) hm_step_fx(NinvArgs a, NinvMaps x, C
         for (int64_t q = q0 + wid; q < q1; q += kWarps) {
             const int32_t k = a.Lri[q];
             const double ekj = -a.Lval[a.Lcsr[q]] * ldexp(1.0, sc);  // E_kj 2^s (exact)
+            const long long magic = __double_as_longlong(kRoundMagic);
             const double* __restrict__ wk = Wp + a.Wcp[k];
             const uint16_t* __restrict__ mp = x.hmap + x.moff[q];
             const int32_t nk = a.grp[(int64_t)k * G + t];
@@ -407,7 +399,10 @@ __global__ void __launch_bounds__(kThreads) hm_step_fx(NinvArgs a, NinvMaps x, C
                     p = mp[e];
                     v = wk[e];
                 },
-                [&](uint16_t p, const double& v) { atomicAdd(acc + p, (unsigned long long)fx_round(ekj * v)); });
+                [&](uint16_t p, const double& v) {
+                    const long long q = __double_as_longlong(fma(ekj, v, kRoundMagic)) - magic;
+                    atomicAdd(acc + p, (unsigned long long)q);
+                });
         }
         __syncthreads();
         unsigned long long mx = 0ull;
