@@ -182,10 +182,10 @@ def kernel_rooflines(trace, st, m, k, nS_lo, prec, peaks, steps):
 
 # DRAM bytes (read + write) per unit of work from one ncu capture of the same kernel
 # build on the 32^3 case of this workload (profiles/ninv_map_kernels_diff3d_32_fp64.md):
-# FP64 Horner (hm_step_fx): 2.599 GB over the 757.9 M products of its 4 steps; FP64
+# FP64 Horner (hm_step_fx): 2.600 GB over the 757.9 M products of its 4 steps; FP64
 # product: 1.996 GB over 811.8 M streamed map entries.  Scaled to a launch here by
 # the units it processes.
-DRAM_PER_UNIT = {"ninv_map_horner": 2.5988e9 / 757.933257e6, "ninv_map_product": 1.99613e9 / 811.837539e6}
+DRAM_PER_UNIT = {"ninv_map_horner": 2.59975e9 / 757.933257e6, "ninv_map_product": 1.99553e9 / 811.837539e6}
 
 
 def dram_traffic(kernel, prec, st, m):
