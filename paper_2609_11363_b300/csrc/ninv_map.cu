@@ -260,8 +260,10 @@ __device__ __forceinline__ void stream_column(int32_t count, int lane, Load load
 // fused multiply-add) and adds both cross terms hi_a lo_b + lo_a hi_b; the sum
 // runs as (s, c): s takes the high parts with an error-free two-sum and c
 // collects every error term and low part in FP32 (its own rounding stays at the
-// 2^-48 level relative to the terms).  The intrinsics keep the compiler from
-// contracting the two-sum.
+// 2^-48 level relative to the terms).  These are the error-free transformations
+// of double-word arithmetic: Knuth's two-sum and the product error obtained with
+// a fused multiply-add (Dekker's exact product).  The intrinsics keep the
+// compiler from contracting the two-sum.
 
 __device__ __forceinline__ float2 split_pair(double x) {
     const float h = __double2float_rn(x);
@@ -287,7 +289,6 @@ __device__ __forceinline__ void pair_add(float& s, float& c, float s2, float c2)
     s = t;
     c = __fadd_rn(c, __fadd_rn(e, c2));
 }
-
 
 template <class T>
 __device__ __forceinline__ T fma_m(T a, T b, T c);
@@ -512,8 +513,6 @@ __device__ __forceinline__ float2 pair_norm(float s, float c) {
     return make_float2(h, __fsub_rn(c, __fsub_rn(h, s)));
 }
 
-__device__ __forceinline__ void pair_mul_add(float2 a, float2 b, float& s, float& c) { pair_mac(a, b, s, c); }
-
 // Product on S in pairs: y = D^{-1} W[:, j] formed in pairs with one writer per
 // position, then the streamed sums of hp_step's arithmetic.
 __global__ void __launch_bounds__(kThreads) pp_product(NinvArgs a, NinvMaps x, ColumnList cl, int tlim,
@@ -541,14 +540,14 @@ __global__ void __launch_bounds__(kThreads) pp_product(NinvArgs a, NinvMaps x, C
             const int32_t r = rf & kRowMask;
             const float2 w = W[base + e];
             float s = 0.f, c = 0.f;
-            pair_mul_add(drx[r], w, s, c);
+            pair_mac(drx[r], w, s, c);
             if (rf & kTwoFlag) {
                 const int32_t pp = x.ypart[base + e];
                 if (pp < nt) {
-                    pair_mul_add(dpx[r], W[base + pp], s, c);
+                    pair_mac(dpx[r], W[base + pp], s, c);
                 } else {
                     float s2 = 0.f, c2 = 0.f;
-                    pair_mul_add(dpx[r], w, s2, c2);
+                    pair_mac(dpx[r], w, s2, c2);
                     y[pp] = pair_norm(s2, c2);
                 }
             }
