@@ -245,7 +245,9 @@ sinv_status sinv_symbolic(int64_t n, const int64_t* L_rowptr, const int32_t* L_c
         return s;
     }
     if (!host_only) cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
-    const int64_t thin_level = 2 * (int64_t)(h->num_sms > 0 ? h->num_sms : 148);
+    // levels with fewer supernodes than SMs give each supernode a whole CTA (a sweep over
+    // 0..16 x SMs on the 64^3 diffusion workload put the best at 1 x SMs)
+    const int64_t thin_level = (int64_t)(h->num_sms > 0 ? h->num_sms : 148);
     std::string err;
     try {
         err = build_plan(n, L_rowptr, L_col, pivot_start, cap, big_pairs, selinv_warps_per_cta(), thin_level,
