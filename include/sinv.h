@@ -143,11 +143,23 @@ sinv_status sinv_selinv(sinv_handle h, const double *L_val, const double *D_val,
  * The first call for an m builds that pattern (host) and its position maps
  * (device, see sinv_symbolic_opts.ninv_index_bytes) and synchronises the
  * stream; later calls with the same m only launch kernels (make the first one
- * before capturing a stream into a CUDA graph).  Sums run in an order that can
- * change between calls (shared-memory atomics), so repeated calls agree to
- * rounding, not bit for bit. */
+ * before capturing a stream into a CUDA graph).  In the map form the FP64 and
+ * SINV_FP32X2 results repeat bit for bit (the Horner steps sum in exact fixed
+ * point); the FP32 form and the hash form sum with floating-point atomics, so
+ * their repeated calls agree to rounding. */
 sinv_status sinv_ninv(sinv_handle h, const double *L_val, const double *D_val, int m,
                       sinv_precision prec, double *N_S, void *stream);
+
+/* NInv with the inverse tolerance delta sparsifying the series (Section 2.2:
+ * larger delta, sparser L^inv): the Horner steps run in column form,
+ * W <- I + W E (column j of W from the columns k of struct(j)), and after every
+ * step the off-diagonal entries of W with |w| < delta are set to zero; the product
+ * W^T D^{-1} W is then evaluated exactly on S, as in sinv_ninv.  delta = 0 is
+ * sinv_ninv.  The kernels keep the structural pattern of the full series, so a
+ * larger delta changes the values, not the work.  delta < 0 or NaN:
+ * SINV_ERR_INVALID_ARG.  Everything else as sinv_ninv. */
+sinv_status sinv_ninv_drop(sinv_handle h, const double *L_val, const double *D_val, int m, double delta,
+                           sinv_precision prec, double *N_S, void *stream);
 
 /* NInv on S for every truncation t = 0..m of the series at once (Eq. (6) cut after
  * t terms, then Eq. (8)): N_stack[t * |S_lo| + e] (device, (m+1) x |S_lo| doubles).

@@ -133,27 +133,45 @@ def _Dinv(n, pivot_start, d_diag, d_off):
     return sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
 
 
-def ninv_W(n, L_rowptr, L_col, L_val, m):
-    """W = sum_{t=0}^{m} E_L^t (Eq. (6) truncated after the m-th power)."""
+def _drop_offdiag(W, delta):
+    """Section 2.2's inverse tolerance (reading: after each Horner step, the
+    off-diagonal entries with |w| < delta are dropped)."""
+    W = W.tocoo()
+    keep = (W.row == W.col) | (np.abs(W.data) >= delta)
+    return sp.csr_matrix((W.data[keep], (W.row[keep], W.col[keep])), shape=W.shape)
+
+
+def ninv_W(n, L_rowptr, L_col, L_val, m, delta=0.0):
+    """W = sum_{t=0}^{m} E_L^t (Eq. (6) truncated after the m-th power).
+
+    Horner steps in column form, W_t = I + W_{t-1} E_L: column j of W_t is e_j
+    plus E_kj times column k of W_{t-1} for the rows k of column j of E_L (the
+    identity Z = I + Z E_L of Z = L^{-1}).  Without dropping this is the same sum
+    as I + E_L W_{t-1}; with delta > 0 every step drops its off-diagonal entries
+    below delta, and the two orders differ, so the column form is the reading.
+    """
     E = _E(n, L_rowptr, L_col, L_val)
     I = sp.identity(n, format="csr")
     W = I.copy()
     for _ in range(m):
-        W = (I + E @ W).tocsr()  # Horner: W_t = I + E W_{t-1}
+        W = (I + W @ E).tocsr()  # Horner: W_t = I + W_{t-1} E
+        if delta > 0:
+            W = _drop_offdiag(W, delta)
     W.sort_indices()
     return W
 
 
-def ninv(n, L_rowptr, L_col, L_val, pivot_start, d_diag, d_off, m, S=None, chunk=1 << 20):
+def ninv(n, L_rowptr, L_col, L_val, pivot_start, d_diag, d_off, m, S=None, chunk=1 << 20, delta=0.0):
     """NInv on S: N_ij = (W^T D^{-1} W)_ij for (i, j) in S_lo (Eq. (8)).
 
-    W is the exact truncated series (no value dropping); the product is
+    W is the truncated series, exact for delta = 0, else with each Horner
+    step's off-diagonal entries below delta dropped (ninv_W); the product is
     evaluated exactly on S, entry by entry as the dot product of column i of W
     with column j of D^{-1} W.
     """
     if S is None:
         S = symbolic_S(n, L_rowptr, L_col, pivot_start)
-    W = ninv_W(n, L_rowptr, L_col, L_val, m)
+    W = ninv_W(n, L_rowptr, L_col, L_val, m, delta)
     Y = (_Dinv(n, pivot_start, d_diag, d_off) @ W).tocsr()
     Wt = W.T.tocsr(); Yt = Y.T.tocsr()
     rows, cols = _S_entries(*S)
@@ -164,16 +182,40 @@ def ninv(n, L_rowptr, L_col, L_val, pivot_start, d_diag, d_off, m, S=None, chunk
     return out
 
 
-def ninv_entries_sampled(n, L_rowptr, L_col, L_val, pivot_start, d_diag, d_off, m, pairs):
-    """N_ij for a list of (i, j) pairs, one at a time, at any n.
+def ninv_entries_sampled(n, L_rowptr, L_col, L_val, pivot_start, d_diag, d_off, m, pairs, delta=0.0):
+    """N_ij for a list of (i, j) pairs, one at a time.
 
-    Column c of W is sum_t E^t e_c, built from sparse matrix-vector products.
+    delta = 0 (any n): column c of W is sum_t E^t e_c, built from sparse
+    matrix-vector products.  delta > 0 (small n): the column form of ninv_W,
+    column c of W_t = e_c + sum_{k in struct(c)} E_kc W_{t-1}[:, k] with the
+    off-diagonal entries below delta dropped, by memoised recursion over the
+    columns it reaches.
     """
     E = _E(n, L_rowptr, L_col, L_val).tocsc()
     Dinv = _Dinv(n, pivot_start, d_diag, d_off).tocsc()
 
+    def unit(c):
+        return sp.csc_matrix(([1.0], ([c], [0])), shape=(n, 1))
+
+    memo = {}
+
+    def wcol_drop(c, t):
+        if t == 0:
+            return unit(c)
+        key = (c, t)
+        if key not in memo:
+            w = unit(c)
+            for q in range(E.indptr[c], E.indptr[c + 1]):
+                w = w + E.data[q] * wcol_drop(int(E.indices[q]), t - 1)
+            w = w.tocoo()
+            keep = (w.row == c) | (np.abs(w.data) >= delta)
+            memo[key] = sp.coo_matrix((w.data[keep], (w.row[keep], w.col[keep])), shape=(n, 1)).tocsc()
+        return memo[key]
+
     def wcol(c):
-        e = sp.csc_matrix(([1.0], ([c], [0])), shape=(n, 1))
+        if delta > 0:
+            return wcol_drop(c, m)
+        e = unit(c)
         w = e.copy()
         for _ in range(m):
             w = (e + E @ w).tocsc()

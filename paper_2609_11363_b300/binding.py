@@ -28,7 +28,7 @@ EXPORTS = [
     "sinv_lowrank_correct", "sinv_sync_status", "sinv_get_stats", "sinv_get_supernodes",
     "sinv_status_string", "sinv_last_error", "sinv_destroy", "sinv_debug_wait_timeout",
     "sinv_trace_enable", "sinv_trace_read", "sinv_lowrank_correct_noalloc",
-    "sinv_batch_symbolic", "sinv_batch_layout", "sinv_ninv_stack",
+    "sinv_batch_symbolic", "sinv_batch_layout", "sinv_ninv_stack", "sinv_ninv_drop",
     "sinv_mlp_param_count", "sinv_mlp_create", "sinv_mlp_destroy", "sinv_mlp_get_params", "sinv_mlp_set_params",
     "sinv_mlp_features", "sinv_mlp_targets", "sinv_mlp_grad", "sinv_mlp_train_step", "sinv_mlp_predict",
 ]
@@ -77,6 +77,7 @@ def load_library():
     lib.sinv_get_pattern_host.argtypes = [H, P, P]
     lib.sinv_selinv.argtypes = [H, P, P, ctypes.c_int, P, P]
     lib.sinv_ninv.argtypes = [H, P, P, ctypes.c_int, ctypes.c_int, P, P]
+    lib.sinv_ninv_drop.argtypes = [H, P, P, ctypes.c_int, ctypes.c_double, ctypes.c_int, P, P]
     lib.sinv_mix.argtypes = [H, P, P, D, P, P]
     lib.sinv_lowrank_correct.argtypes = [H, ctypes.c_int, P, P, ctypes.c_int, P, P]
     lib.sinv_sync_status.argtypes = [H, P]
@@ -372,11 +373,17 @@ class Handle:
                                           _check_tensor(out, "G_S", self.nnz_S), _stream_ptr(stream)))
         return out
 
-    def ninv(self, L_val, D_val, m, prec="fp64", out=None, stream=None):
+    def ninv(self, L_val, D_val, m, prec="fp64", out=None, stream=None, delta=0.0):
+        """NInv on S; delta > 0 drops off-diagonal |w| < delta after every Horner step."""
         out = self._out(out)
-        self._check(self._lib.sinv_ninv(self._h, _check_tensor(L_val, "L_val", self.nnz_L),
-                                        _check_tensor(D_val, "D_val", self.nD), int(m), PREC[prec],
-                                        _check_tensor(out, "N_S", self.nnz_S), _stream_ptr(stream)))
+        Lp = _check_tensor(L_val, "L_val", self.nnz_L)
+        Dp = _check_tensor(D_val, "D_val", self.nD)
+        Np = _check_tensor(out, "N_S", self.nnz_S)
+        if delta:
+            st = self._lib.sinv_ninv_drop(self._h, Lp, Dp, int(m), float(delta), PREC[prec], Np, _stream_ptr(stream))
+        else:
+            st = self._lib.sinv_ninv(self._h, Lp, Dp, int(m), PREC[prec], Np, _stream_ptr(stream))
+        self._check(st)
         return out
 
     def mix(self, G, N, eps, out=None, stream=None):

@@ -514,22 +514,28 @@ sinv_status sinv_selinv(sinv_handle h, const double* L_val, const double* D_val,
     return SINV_OK;
 }
 
-static sinv_status ninv_common(sinv_handle h, const double* L_val, const double* D_val, int m, sinv_precision prec,
-                               double* N_S, double* N_stack, void* stream);
+static sinv_status ninv_common(sinv_handle h, const double* L_val, const double* D_val, int m, double delta,
+                               sinv_precision prec, double* N_S, double* N_stack, void* stream);
 
 sinv_status sinv_ninv(sinv_handle h, const double* L_val, const double* D_val, int m, sinv_precision prec,
                       double* N_S, void* stream) {
-    return ninv_common(h, L_val, D_val, m, prec, N_S, nullptr, stream);
+    return ninv_common(h, L_val, D_val, m, 0.0, prec, N_S, nullptr, stream);
+}
+
+sinv_status sinv_ninv_drop(sinv_handle h, const double* L_val, const double* D_val, int m, double delta,
+                           sinv_precision prec, double* N_S, void* stream) {
+    if (!(delta >= 0.0)) return SINV_ERR_INVALID_ARG;  // negative or NaN
+    return ninv_common(h, L_val, D_val, m, delta, prec, N_S, nullptr, stream);
 }
 
 sinv_status sinv_ninv_stack(sinv_handle h, const double* L_val, const double* D_val, int m, sinv_precision prec,
                             double* N_stack, void* stream) {
     if (h && h->P.n > 0 && !N_stack) return SINV_ERR_INVALID_ARG;
-    return ninv_common(h, L_val, D_val, m, prec, nullptr, N_stack, stream);
+    return ninv_common(h, L_val, D_val, m, 0.0, prec, nullptr, N_stack, stream);
 }
 
-static sinv_status ninv_common(sinv_handle h, const double* L_val, const double* D_val, int m, sinv_precision prec,
-                               double* N_S, double* N_stack, void* stream) {
+static sinv_status ninv_common(sinv_handle h, const double* L_val, const double* D_val, int m, double delta,
+                               sinv_precision prec, double* N_S, double* N_stack, void* stream) {
     if (!h || !valid_prec(prec) || m < 0) return SINV_ERR_INVALID_ARG;
     if (!on_device(h)) return SINV_ERR_INVALID_ARG;
     if (m > 30) {
@@ -583,6 +589,7 @@ static sinv_status ninv_common(sinv_handle h, const double* L_val, const double*
     a.nnzS = P.nnzS;
     a.nnzW = h->W.nnzW;
     a.nnzL = P.nnzL;
+    a.delta = delta;
     a.dpos = h->ddpos;
     a.pstart = h->dpstart;
     a.Lval = L_val;

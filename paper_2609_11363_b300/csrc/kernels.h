@@ -83,6 +83,7 @@ struct NinvArgs {
     int64_t nnzS;
     int64_t nnzW;
     int64_t nnzL;
+    double delta;         // after every Horner step, off-diagonal |w| < delta is set to 0 (0: keep all)
     const int32_t* dpos;
     const int8_t* pstart;
     const double* Lval;

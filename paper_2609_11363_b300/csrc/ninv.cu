@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(kThreads) ninv_horner(NinvArgs a, int t, const
         __syncthreads();
         for (int32_t e = threadIdx.x; e < nj; e += kThreads) {
             const int32_t h = table_find(keys, mask, a.Wr[base + e] & kRowMask);
-            Wn[base + e] = acc[h] + (e == 0 ? T(1) : T(0));
+            const T v = acc[h] + (e == 0 ? T(1) : T(0));
+            Wn[base + e] = (e != 0 && fabs((double)v) < a.delta) ? T(0) : v;  // drop below the tolerance
         }
         __syncthreads();
     }

@@ -327,7 +327,10 @@ __global__ void __launch_bounds__(kThreads) hm_step(NinvArgs a, NinvMaps x, Colu
                 [&](uint16_t p, const T& v) { atomicAdd(acc + p, ekj * v); });
         }
         __syncthreads();
-        for (int32_t e = threadIdx.x; e < nt; e += kThreads) Wn[base + e] = acc[e] + (e == 0 ? T(1) : T(0));
+        for (int32_t e = threadIdx.x; e < nt; e += kThreads) {
+            const T v = acc[e] + (e == 0 ? T(1) : T(0));
+            Wn[base + e] = (e != 0 && fabs((double)v) < a.delta) ? T(0) : v;  // drop below the tolerance
+        }
         __syncthreads();
     }
 }
@@ -411,7 +414,8 @@ __global__ void __launch_bounds__(kThreads) hm_step_fx(NinvArgs a, NinvMaps x, C
             const long long iv = (long long)acc[e];
             const unsigned long long av = (unsigned long long)(iv < 0 ? -iv : iv);
             mx = av > mx ? av : mx;
-            const double v = scale_pow2(__ll2double_rn(iv), sc);
+            double v = scale_pow2(__ll2double_rn(iv), sc);
+            if (e != 0 && fabs(v) < a.delta) v = 0.0;  // drop below the tolerance
             Wn[base + e] = v;
             if (Wx) Wx[base + e] = split_pair(v);  // for a product in pairs of floats
         }

@@ -142,6 +142,32 @@ def test_ninv_fp32(case, form):
     assert normwise(out.cpu().numpy(), N) <= 1e-5, name
 
 
+@pytest.mark.parametrize("form", sorted(FORMS))
+@pytest.mark.parametrize("delta", [1e-3, 1e-2, 1e-1])
+def test_ninv_drop(case, delta, form):
+    """NInv with the inverse tolerance (off-diagonal |w| < delta dropped after each
+    Horner step) against the oracle's dropped series, in every precision form."""
+    name, f, m, S, G, N = case
+    Nr = oracle.ninv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, m, S, delta=delta)
+    h = _handle(f, ninv_index_bytes=FORMS[form])
+    Lv, Dv = _dev(f.L_val), _dev(f.D_packed)
+    for prec in ("fp64", "fp32x2", "fp32"):
+        out = h.ninv(Lv, Dv, m, prec, delta=delta).cpu().numpy()
+        h.sync_status()
+        if prec == "fp32":
+            assert normwise(out, Nr) <= 1e-5, (name, delta, form)
+        else:
+            assert sel_rel_err(out, Nr, *S) <= TOL64, (name, delta, form, prec)
+
+
+def test_ninv_drop_rejects_negative_tolerance():
+    from paper_2609_11363_b300 import SinvError
+    f = lap2d_32().factors
+    h = _handle(f)
+    with pytest.raises(SinvError):
+        h.ninv(_dev(f.L_val), _dev(f.D_packed), 2, delta=-1.0)
+
+
 @pytest.mark.parametrize("mm", [0, 1, 3])
 def test_ninv_fp32x2(case, mm):
     """Product on S in pairs of floats: FP64-class, checked at the FP64 tolerance."""

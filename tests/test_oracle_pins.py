@@ -251,6 +251,61 @@ def test_ninv_sampled_matches_full():
     assert np.max(np.abs(Ns - ref)) <= 1e-13 and np.max(np.abs(N[idx] - ref)) <= 1e-13
 
 
+def _drop_case(e10, e21):
+    """3x3 factors with E_10 = e10, E_21 = e21, no L_20 and D = diag(2, 4, 5)."""
+    L = np.array([[1.0, 0.0, 0.0], [-e10, 1.0, 0.0], [0.0, -e21, 1.0]])
+    return _factors_from_dense(L, [2.0, 4.0, 5.0])
+
+
+@pytest.mark.parametrize("e10,e21,delta,want", [
+    # exact series W = I + E + E^2 with W_20 = E_21 E_10 = 0.05
+    (0.5, 0.1, 0.0, [0.5630, 0.126, 0.252, 0.02, 0.2]),
+    # delta = 0.1: the second step drops W_20 = 0.05; 0.1 itself stays (strict test)
+    (0.5, 0.1, 0.1, [0.5625, 0.125, 0.252, 0.02, 0.2]),
+    # delta = 0.2: the first step already drops E_21 = 0.1
+    (0.5, 0.1, 0.2, [0.5625, 0.125, 0.25, 0.0, 0.2]),
+    # the order of the Horner product matters once entries are dropped: the first
+    # step drops W_10 = 0.05, and the column form W_2 = I + W_1 E still forms
+    # W_20 = W_1[2, 1] E_10 = 4 * 0.05 = 0.2 (kept), where I + E W_1 would give 0
+    (0.05, 4.0, 0.0, [0.508625, 0.1725, 3.45, 0.8, 0.2]),
+    (0.05, 4.0, 0.1, [0.508, 0.16, 3.45, 0.8, 0.2]),
+])
+def test_ninv_drop_hand_example(e10, e21, delta, want):
+    """Section 2.2's inverse tolerance, read as: the Horner steps W_t = I + W_{t-1} E
+    (column j from the columns of struct(j)) drop their off-diagonal |w| < delta.
+    N_ij = sum_r W_ri W_rj / d_r by hand on S_lo = {(0,0), (1,0), (1,1), (2,1), (2,2)}."""
+    f = _drop_case(e10, e21)
+    S = _S(f)
+    assert np.array_equal(S[0], [0, 1, 3, 5]) and np.array_equal(S[1], [0, 0, 1, 1, 2])
+    N = oracle.ninv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, 2, S, delta=delta)
+    assert np.allclose(N, want, rtol=0, atol=1e-14)
+    pairs = list(zip(_rows(S[0]), S[1]))
+    Ns = oracle.ninv_entries_sampled(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, 2,
+                                     pairs, delta=delta)
+    assert np.allclose(Ns, want, rtol=0, atol=1e-14)
+
+
+def test_ninv_drop_limits_and_fill():
+    """delta beyond every entry leaves W = I, so N = D^{-1} on S (2x2 blocks too);
+    the fill of W never grows with delta; the column-wise sampled evaluation agrees
+    with the matrix Horner evaluation at every delta."""
+    from workloads.configs import random_factors
+    f = random_factors(150, 0.05, 0.2, 12)
+    Srp, Sc = _S(f)
+    rows = _rows(Srp)
+    Dinv = np.linalg.inv(f.D_dense_blocks().toarray())
+    N = oracle.ninv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, 3, (Srp, Sc), delta=1e30)
+    assert np.max(np.abs(N - Dinv[rows, Sc])) <= 1e-15 * 4
+    fills = [oracle.ninv_W(f.n, f.L_rowptr, f.L_col, f.L_val, 3, d).nnz for d in (0.0, 1e-4, 1e-3, 1e-2, 1e-1, 1.0)]
+    assert all(a >= b for a, b in zip(fills, fills[1:])) and fills[0] > fills[-1]
+    idx = np.arange(0, len(Sc), 7)
+    for d in (1e-3, 1e-2, 1e-1):
+        N = oracle.ninv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, 3, (Srp, Sc), delta=d)
+        Ns = oracle.ninv_entries_sampled(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, 3,
+                                         list(zip(rows[idx], Sc[idx])), delta=d)
+        assert np.max(np.abs(Ns - N[idx])) <= 1e-13 * max(1.0, np.max(np.abs(N)))
+
+
 # -- Mix (Section 2.3) ---------------------------------------------------------------------
 def test_mix_special_cases_and_hand_example():
     G = np.array([0.5, -1e-4, 2e-3, -0.2, 0.0])
