@@ -49,11 +49,15 @@ def parse():
     p.add_argument("--size", type=int, default=64)
     p.add_argument("--ninv-delta", type=float, default=0.0,
                    help="inverse tolerance of NInv: off-diagonal |w| < delta dropped after each Horner step")
-    p.add_argument("--workload", default="diff3d", choices=["diff3d", "batch9pt", "learned", "elastic"],
+    p.add_argument("--workload", default="diff3d", choices=["diff3d", "batch9pt", "learned", "elastic", "covariance"],
                    help="diff3d: the 64^3 step (default); batch9pt: 256 matrices in one graph-captured launch; "
                         "learned: the trained NInv->SelInv correction on 128^3; elastic: the 27-point 3-dof "
-                        "operator (N^3 nodes, --elastic-size N)")
+                        "operator (N^3 nodes, --elastic-size N); covariance: the (1-d/3)^4 covariance-type "
+                        "matrix on an N x N grid (--cov-size N)")
     p.add_argument("--elastic-size", type=int, default=24)
+    p.add_argument("--cov-size", type=int, default=200)
+    p.add_argument("--exact-diag-max-n", type=int, default=10000,
+                   help="covariance: also report err_1 of the diagonals against a dense inverse up to this n")
     p.add_argument("--batch", type=int, default=256, help="matrices of the batch9pt workload")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -577,6 +581,9 @@ def run_extra(args, rank, world):
     if args.workload == "elastic":
         run_elastic(args, rank, world, dev, peaks)
         return
+    if args.workload == "covariance":
+        run_covariance(args, rank, world, dev)
+        return
     # learned correction
     from paper_2609_11363_b300.learned import LearnedCorrection
     torch.cuda.set_device(dev)
@@ -603,11 +610,14 @@ def run_extra(args, rank, world):
     d = lc.prepare(h, Lv, Dv)
     ev = lc.evaluate(d)
 
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
     def timed(fn, reps):
         fn()
         torch.cuda.synchronize()
         out = []
         for _ in range(reps):
+            flush.zero_()  # inputs are smaller than L2: flush it between timed steps
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -677,11 +687,14 @@ def run_elastic(args, rank, world, dev, peaks):
         h.mix(G, N, eps, out=M)
         h.lowrank_correct(Vd, ld, M, "fp32")
 
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
     def timed(fn, reps):
         fn()
         torch.cuda.synchronize()
         out = []
         for _ in range(reps):
+            flush.zero_()  # inputs are smaller than L2: flush it between timed steps
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -711,6 +724,92 @@ def run_elastic(args, rank, world, dev, peaks):
                        "nnz_W": st["nnz_W"], "ninv_form": "map" if st["ninv_index_bytes"] > 0 else "hash",
                        "selinv_fp64_ms": ms_sel64, "selinv_fp32_ms": ms_sel32, "ninv_fp32_ms": ms_ninv,
                        "input_gen_s": t_gen},
+            "gpu_launches": None}
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def run_covariance(args, rank, world, dev):
+    """The paper's covariance-type example, (1 - d/3)^4 on an N x N grid, ILDL tau = 1e-3.
+    One step = SelInv + NInv (m = 3, inverse tolerance --ninv-delta) + Mix in FP64,
+    inputs resident; the phases are timed apart as well."""
+    import torch
+    from paper_2609_11363_b300 import Handle
+    from workloads.configs import covariance
+    torch.cuda.set_device(dev)
+    t0 = time.time()
+    w = covariance(args.cov_size)
+    f = w.factors
+    t_gen = time.time() - t0
+    from paper_2609_11363_b300.autotune import tune_selinv
+    Lv = torch.as_tensor(f.L_val, device=dev)
+    Dv = torch.as_tensor(f.D_packed, device=dev)
+    t0 = time.time()
+    h, best, table = tune_selinv(f, Lv, Dv, prec="fp64", caps=(4, 16, 64), bigs=(1024, 4096), device=dev.index)
+    t_tune = time.time() - t0
+    G = torch.empty(h.nnz_S, dtype=torch.float64, device=dev)
+    N = torch.empty_like(G)
+    M = torch.empty_like(G)
+    h.selinv(Lv, Dv, "fp64", out=G)
+    h.ninv(Lv, Dv, w.m, "fp64", out=N, delta=args.ninv_delta)
+    eps = 1e-3 * float(G.abs().max())  # SPD: the largest |G| is on the diagonal
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        out = []
+        for _ in range(reps):
+            flush.zero_()  # inputs are smaller than L2: flush it between timed steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return float(np.median(out))
+
+    def step():
+        h.selinv(Lv, Dv, "fp64", out=G)
+        h.ninv(Lv, Dv, w.m, "fp64", out=N, delta=args.ninv_delta)
+        h.mix(G, N, eps, out=M)
+
+    for _ in range(args.warmup):
+        step()
+    ms = timed(step, args.steps)
+    ms_sel = timed(lambda: h.selinv(Lv, Dv, "fp64", out=G), args.steps)
+    ms_ninv = timed(lambda: h.ninv(Lv, Dv, w.m, "fp64", out=N, delta=args.ninv_delta), args.steps)
+    h.sync_status()
+    st = h.stats()
+    nS = 2 * h.nnz_S - h.n
+    gn = float(torch.linalg.vector_norm(G))
+    err = {"ninv_vs_selinv": float(torch.linalg.vector_norm(N - G)) / gn,
+           "mix_vs_selinv": float(torch.linalg.vector_norm(M - G)) / gn}
+    if f.n <= args.exact_diag_max_n:
+        # err_1 of the diagonal against diag(A^{-1}) from a dense Cholesky (measurement only)
+        rp, _ = h.pattern_host()
+        dpos = torch.as_tensor(rp[1:] - 1, device=dev)  # the diagonal ends each row of S_lo
+        Ad = torch.as_tensor(w.A.toarray(), device=dev)
+        Ai = torch.cholesky_inverse(torch.linalg.cholesky(Ad))
+        exact = torch.diagonal(Ai)
+        del Ad, Ai
+        en = float(exact.abs().sum())
+        for nm, X in (("selinv", G), ("ninv", N), ("mix", M)):
+            err["err1_diag_%s_vs_exact" % nm] = float((X[dpos] - exact).abs().sum()) / en
+    line = {"metric": METRIC, "value": world * nS / (ms / 1e3), "unit": "entries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "rel_error_on_S_lo": err,
+            "config": {"workload": "covariance: (1 - d/3)^4 on a %d x %d grid (n=%d), ILDL tau=1e-3, SelInv + NInv m=%d "
+                                   "+ Mix, FP64" % (args.cov_size, args.cov_size, f.n, w.m),
+                       "stated_rel_error": STATED_ERROR["fp64"], "ninv_delta": args.ninv_delta,
+                       "nnz_A": int(w.A.nnz), "nnz_L": st["nnz_L"], "S_entries": nS, "levels": st["n_levels"],
+                       "nnz_W": st["nnz_W"], "ninv_form": "map" if st["ninv_index_bytes"] > 0 else "hash",
+                       "selinv_fp64_ms": ms_sel, "ninv_fp64_ms": ms_ninv, "input_gen_s": t_gen,
+                       "l2": "flushed (512 MB write) before each timed step",
+                       "selinv_schedule": best, "tune_table": table, "tune_s": t_tune},
             "gpu_launches": None}
     if rank == 0:
         print(json.dumps(line))

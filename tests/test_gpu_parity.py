@@ -12,7 +12,7 @@ import torch
 
 import oracle
 from tests.helpers import normwise, sel_rel_err
-from workloads.configs import diff3d, elastic3d, lap2d_32, plant_2x2, random_factors, random_lowrank
+from workloads.configs import covariance, diff3d, elastic3d, lap2d_32, plant_2x2, random_factors, random_lowrank
 
 pytestmark = pytest.mark.gpu
 
@@ -44,6 +44,8 @@ CASES = {
     "diff3d_12_planted": lambda: plant_2x2(diff3d(12, m=3).factors, 0.05, 13),
     # 27-point 3-dof elastic-like operator (dense 3x3 blocks, ~100 entries per row of L)
     "elastic3d_8_planted": lambda: plant_2x2(elastic3d(8).factors, 0.05, 17),
+    # the covariance-type example (1 - d/3)^4 on a 24 x 24 grid
+    "covariance_24": lambda: covariance(24).factors,
 }
 
 

@@ -402,3 +402,16 @@ def test_mlp_oracle_gradient_matches_finite_differences():
     t1, m1, v1 = omlp.adam(theta, g, np.zeros_like(g), np.zeros_like(g), 1, 1e-3)
     big = np.abs(g) > 1e-3
     assert np.allclose((theta - t1)[big], 1e-3 * np.sign(g[big]), rtol=1e-4)
+
+
+def test_covariance_generator_matches_definition():
+    """The covariance-type example entry by entry from the grid coordinates (brute
+    force over all pairs), symmetric positive definite."""
+    from workloads import grids
+    N, alpha, beta = 7, 3.0, 4.0
+    C = grids.covariance2d(N, alpha, beta).toarray()
+    xy = np.array([(i % N, i // N) for i in range(N * N)], dtype=float)
+    d = np.sqrt(((xy[:, None, :] - xy[None, :, :]) ** 2).sum(-1))
+    ref = np.where(d <= alpha, np.clip(1.0 - d / alpha, 0.0, None) ** beta, 0.0)
+    assert np.max(np.abs(C - ref)) <= 1e-15
+    assert np.linalg.eigvalsh(C).min() > 0.1

@@ -22,6 +22,9 @@ Recipes (every random number from PCG64 ``numpy.random.default_rng``):
 * ``diff3d_spd``    as ``diff3d`` without the shift (SPD), tau = 1e-3, m = 3:
                     48^3 training seeds 4000..4063, 128^3 inference seed 4999.
 * ``elastic3d``     3D 27-point, 3 dof per node, seed 5, tau = 1e-4, m = 2, k = 64.
+* ``covariance``    covariance-type matrix (1 - d/alpha)^beta on an N x N grid,
+                    alpha = 3, beta = 4 (no random numbers), tau = 1e-3, m = 3:
+                    the paper's second example, N = 100 and 200.
 """
 from __future__ import annotations
 
@@ -110,6 +113,15 @@ def batch9pt_member(seed: int, tau: float = 1e-2, m: int = 3, n_range=(2048, 655
 def elastic3d(N: int = 80, tau: float = 1e-4, m: int = 2, k: int = 64, seed: int = 5) -> Workload:
     A, p = _ordered(grids.elastic3d_27pt(N, N, N, seed), (N, N, N), dof=3)
     return Workload("elastic3d_%d" % N, A, ildl(A, tau), tau, m, k, meta={"shape": (N, N, N), "seed": seed})
+
+
+def covariance(N: int = 200, alpha: float = 3.0, beta: float = 4.0, tau: float = 1e-3, m: int = 3) -> Workload:
+    """The covariance-type example on an N x N grid (N = 100, 200 in the paper,
+    alpha = 3, beta = 4, tau = 1e-3), in nested-dissection order.  m = 3 is a
+    proposed NInv depth (the paper's NInv uses its inverse tolerance instead)."""
+    A, p = _ordered(grids.covariance2d(N, alpha, beta), (N, N))
+    return Workload("covariance_%d_a%g_b%g" % (N, alpha, beta), A, ildl(A, tau), tau, m,
+                    meta={"shape": (N, N), "alpha": alpha, "beta": beta})
 
 
 def random_lowrank(n: int, k: int, seed: int, orthonormal: bool = True):

@@ -166,3 +166,29 @@ def elastic3d_27pt(nx: int, ny: int, nz: int, seed) -> sp.csr_matrix:
             cols.append(3 * np.arange(nn) + c)
             vals.append(dblk[:, r, c])
     return _coo_to_csr(np.concatenate(rows), np.concatenate(cols), np.concatenate(vals), n)
+
+
+def covariance2d(N: int, alpha: float = 3.0, beta: float = 4.0) -> sp.csr_matrix:
+    """Covariance-type matrix on an N x N grid of unit spacing (n = N^2):
+    c_ij = (1 - d(i, j)/alpha)^beta for d(i, j) <= alpha, else 0, with d the
+    Euclidean distance between grid points i and j (the paper's second example,
+    Section 3, after Tang and Saad).  c_ii = 1; entries at d = alpha are 0 and
+    are not stored.  The truncated power (1 - r)_+^beta is positive definite in
+    the plane for beta >= 3/2 (Askey), so C is SPD for beta = 4.  No random numbers.
+    """
+    n = N * N
+    idx = np.arange(n).reshape(N, N)
+    r = int(np.floor(alpha))
+    rows, cols, vals = [], [], []
+    for dy in range(-r, r + 1):
+        for dx in range(-r, r + 1):
+            d = float(np.hypot(dx, dy))
+            if d >= alpha:
+                continue
+            c = (1.0 - d / alpha) ** beta
+            y0, y1 = max(0, -dy), min(N, N - dy)
+            x0, x1 = max(0, -dx), min(N, N - dx)
+            a = idx[y0:y1, x0:x1].ravel()
+            b = idx[y0 + dy:y1 + dy, x0 + dx:x1 + dx].ravel()
+            rows.append(a); cols.append(b); vals.append(np.full(a.size, c))
+    return _coo_to_csr(np.concatenate(rows), np.concatenate(cols), np.concatenate(vals), n)
