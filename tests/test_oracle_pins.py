@@ -415,3 +415,105 @@ def test_covariance_generator_matches_definition():
     ref = np.where(d <= alpha, np.clip(1.0 - d / alpha, 0.0, None) ** beta, 0.0)
     assert np.max(np.abs(C - ref)) <= 1e-15
     assert np.linalg.eigvalsh(C).min() > 0.1
+
+
+# --------------------------------------------------------------------------
+# SPAI refinement (Section 2.4)
+# --------------------------------------------------------------------------
+def _lower_pattern(M):
+    low = sp.tril(sp.csr_matrix(M), format="csr")
+    low.sort_indices()
+    return low.indptr.astype(np.int64), low.indices.astype(np.int32)
+
+
+def _spai_case(n=30, seed=11):
+    """A small sparse SPD A (random symmetric couplings, diagonally dominant)
+    and a pattern S = lower part of pattern(A + A^2 restricted) with the diagonal."""
+    rng = np.random.default_rng(seed)
+    R = sp.random(n, n, density=0.12, random_state=seed, data_rvs=lambda k: rng.uniform(-1, 1, k))
+    A = (R + R.T).tocsr()
+    A = A + sp.diags(np.asarray(abs(A).sum(axis=1)).ravel() + 1.0)
+    P = sp.csr_matrix(A @ A)
+    P.data[:] = 1.0
+    keep = sp.random(n, n, density=0.5, random_state=seed + 1)
+    keep = keep + keep.T
+    S = P.multiply(keep != 0) + sp.identity(n)
+    Srp, Sc = _lower_pattern(S)
+    return sp.csr_matrix(A), Srp, Sc
+
+
+def test_spai_hand_example_2x2():
+    # A = [[2,1],[1,2]], full pattern, start 0.  Normal matrix B = A^T A = [[5,4],[4,5]];
+    # column 0: b = [2,1], z = r/5, p = [0.4,0.2], r.z = 1, Bp = [2.8,2.6], p.Bp = 1.64,
+    # x = p/1.64.  Two steps solve the 2x2 system: the inverse [[2,-1],[-1,2]]/3.
+    A = sp.csr_matrix(np.array([[2.0, 1.0], [1.0, 2.0]]))
+    Srp = np.array([0, 1, 3], dtype=np.int64)
+    Sc = np.array([0, 0, 1], dtype=np.int32)
+    Y1 = oracle.spai_refine(A, Srp, Sc, np.zeros(3), 1)
+    np.testing.assert_allclose(Y1, [0.4 / 1.64, 0.2 / 1.64, 0.4 / 1.64], rtol=1e-15)
+    Y2 = oracle.spai_refine(A, Srp, Sc, np.zeros(3), 2)
+    np.testing.assert_allclose(Y2, [2 / 3, -1 / 3, 2 / 3], rtol=1e-14)
+
+
+def test_spai_converges_to_least_squares_columns():
+    # enough steps: each column is the least-squares minimiser on its pattern (LAPACK gelsd)
+    A, Srp, Sc = _spai_case()
+    n = A.shape[0]
+    cols = oracle.spai_columns(A, Srp, Sc, np.zeros(len(Sc)), 200)
+    Ad = A.toarray()
+    for j, (J, m) in enumerate(cols):
+        e = np.zeros(n)
+        e[j] = 1.0
+        ref = np.linalg.lstsq(Ad[:, J], e, rcond=None)[0]
+        np.testing.assert_allclose(m, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    # and the symmetrised values are the average of the two least-squares columns
+    Y = oracle.spai_refine(A, Srp, Sc, np.zeros(len(Sc)), 200)
+    look = [dict(zip(J.tolist(), m.tolist())) for J, m in cols]
+    rows = _rows(Srp)
+    for p in range(0, len(Sc), 7):
+        i, j = int(rows[p]), int(Sc[p])
+        want = look[j][i] if i == j else 0.5 * (look[j][i] + look[i][j])
+        assert abs(Y[p] - want) <= 1e-13 * max(1.0, abs(want))
+
+
+def test_spai_full_pattern_gives_the_inverse():
+    A, _, _ = _spai_case(n=14, seed=5)
+    Srp, Sc = _lower_pattern(np.ones((14, 14)))
+    Y = oracle.spai_refine(A, Srp, Sc, np.zeros(len(Sc)), 60)
+    inv = np.linalg.inv(A.toarray())
+    np.testing.assert_allclose(Y, inv[_rows(Srp), Sc], rtol=0, atol=1e-12 * np.abs(inv).max())
+
+
+def test_spai_zero_steps_and_diagonal_matrix():
+    A, Srp, Sc = _spai_case(n=20, seed=3)
+    X = np.random.default_rng(0).standard_normal(len(Sc))
+    np.testing.assert_array_equal(oracle.spai_refine(A, Srp, Sc, X, 0), X)
+    # diagonal A: B = diag(a^2) is its own Jacobi preconditioner, so one step reaches
+    # e_j / a_j from any start, and further steps stay there (r.z = 0)
+    a = np.linspace(0.5, 3.0, 20)
+    D = sp.diags(a).tocsr()
+    rows = _rows(Srp)
+    want = np.where(rows == Sc, 1.0 / a[rows], 0.0)
+    for it in (1, 4):
+        np.testing.assert_allclose(oracle.spai_refine(D, Srp, Sc, X, it), want, rtol=1e-15, atol=1e-15)
+
+
+def test_spai_residual_never_grows():
+    # CG minimises the B-norm of the error over growing Krylov spaces, and
+    # ||A_J x - e_j||^2 = ||x - x*||_B^2 + const, so the residual cannot grow
+    A, Srp, Sc = _spai_case(n=40, seed=7)
+    n = A.shape[0]
+    X = 0.05 * np.random.default_rng(1).standard_normal(len(Sc))
+    Ad = A.toarray()
+    prev = None
+    for it in range(7):
+        res = []
+        for j, (J, m) in enumerate(oracle.spai_columns(A, Srp, Sc, X, it)):
+            e = np.zeros(n)
+            e[j] = 1.0
+            res.append(np.linalg.norm(Ad[:, J] @ m - e))
+        res = np.array(res)
+        if prev is not None:
+            assert np.all(res <= prev * (1 + 1e-12) + 1e-15)
+        prev = res
+    assert prev.max() < 0.9  # and it did move
