@@ -56,6 +56,10 @@ def parse():
                         "matrix on an N x N grid (--cov-size N)")
     p.add_argument("--elastic-size", type=int, default=24)
     p.add_argument("--cov-size", type=int, default=200)
+    p.add_argument("--spai-iters", type=int, default=20,
+                   help="covariance: PCG steps of the SPAI refinement of Mix (Mix-SPAI); 0 = leave it out")
+    p.add_argument("--spai-power", type=int, default=2,
+                   help="covariance: SPAI pattern P = S + pairs within this graph distance in A")
     p.add_argument("--exact-diag-max-n", type=int, default=10000,
                    help="covariance: also report err_1 of the diagonals against a dense inverse up to this n")
     p.add_argument("--batch", type=int, default=256, help="matrices of the batch9pt workload")
@@ -771,16 +775,26 @@ def run_covariance(args, rank, world, dev):
             out.append(e0.elapsed_time(e1))
         return float(np.median(out))
 
+    t0 = time.time()
+    Ac = h.spai_analyse(w.A, power=args.spai_power)
+    t_spai_an = time.time() - t0
+    Av = torch.as_tensor(Ac.data, device=dev)
+    Y = torch.empty(h.nnz_P, dtype=torch.float64, device=dev)
+    it = args.spai_iters
+
     def step():
         h.selinv(Lv, Dv, "fp64", out=G)
         h.ninv(Lv, Dv, w.m, "fp64", out=N, delta=args.ninv_delta)
         h.mix(G, N, eps, out=M)
+        if it > 0:
+            h.spai(Av, M, it, out=Y)
 
     for _ in range(args.warmup):
         step()
     ms = timed(step, args.steps)
     ms_sel = timed(lambda: h.selinv(Lv, Dv, "fp64", out=G), args.steps)
     ms_ninv = timed(lambda: h.ninv(Lv, Dv, w.m, "fp64", out=N, delta=args.ninv_delta), args.steps)
+    ms_spai = timed(lambda: h.spai(Av, M, it, out=Y), args.steps) if it > 0 else 0.0
     h.sync_status()
     st = h.stats()
     nS = 2 * h.nnz_S - h.n
@@ -798,12 +812,21 @@ def run_covariance(args, rank, world, dev):
         en = float(exact.abs().sum())
         for nm, X in (("selinv", G), ("ninv", N), ("mix", M)):
             err["err1_diag_%s_vs_exact" % nm] = float((X[dpos] - exact).abs().sum()) / en
+        if it > 0:
+            prp, _ = h.spai_pattern()
+            ppos = torch.as_tensor(prp[1:] - 1, device=dev)
+            err["err1_diag_mix_spai_vs_exact"] = float((Y[ppos] - exact).abs().sum()) / en
     line = {"metric": METRIC, "value": world * nS / (ms / 1e3), "unit": "entries/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "rel_error_on_S_lo": err,
             "config": {"workload": "covariance: (1 - d/3)^4 on a %d x %d grid (n=%d), ILDL tau=1e-3, SelInv + NInv m=%d "
-                                   "+ Mix, FP64" % (args.cov_size, args.cov_size, f.n, w.m),
+                                   "+ Mix%s, FP64" % (args.cov_size, args.cov_size, f.n, w.m,
+                                                      " + SPAI (%d PCG steps on S + distance-%d neighbourhoods of A)"
+                                                      % (it, args.spai_power) if it > 0 else ""),
+                       "spai_iters": it, "spai_power": args.spai_power, "spai_nnz_P_lo": st["spai_nnz_P"],
+                       "spai_fp64_ms": ms_spai, "spai_entries": st["spai_entries"], "spai_analyse_s": t_spai_an,
+                       "spai_cols_warp": st["spai_cols_warp"], "spai_cols_cta": st["spai_cols_cta"],
                        "stated_rel_error": STATED_ERROR["fp64"], "ninv_delta": args.ninv_delta,
                        "nnz_A": int(w.A.nnz), "nnz_L": st["nnz_L"], "S_entries": nS, "levels": st["n_levels"],
                        "nnz_W": st["nnz_W"], "ninv_form": "map" if st["ninv_index_bytes"] > 0 else "hash",

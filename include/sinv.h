@@ -180,6 +180,47 @@ sinv_status sinv_mix(sinv_handle h, const double *G_S, const double *N_S, double
 sinv_status sinv_lowrank_correct(sinv_handle h, int k, const double *V, const double *lambda,
                                  sinv_precision prec, double *X_S, void *stream);
 
+/* SPAI refinement on a fixed pattern P (Section 2.4; Mix-SPAI is this step
+ * applied to the Mix values).  P is S, or S widened to every (i, j) whose
+ * distance in the graph of A is at most `power` (a larger candidate pattern,
+ * which the least-squares fit needs to beat the start values: see the
+ * documentation).  For every column j, with J_j = {i : (i, j) in P}, `iters`
+ * steps of Jacobi-preconditioned conjugate gradients on the normal equations
+ * (A_J^T A_J) m = A_J^T e_j  of  min ||A m - e_j||_2  over m supported on J_j,
+ * started from X on S and zero on the rest of P; then Y = (M + M^T) / 2 on P_lo.
+ * A column stops early only when its preconditioned residual r.z is exactly
+ * zero or the curvature p.Bp is not positive.  FP64 throughout.
+ *
+ * sinv_spai_analyse: the pattern of A, HOST arrays, n x n CSR with
+ *   A_rowptr[n+1] (starts at 0, ends at nnzA) and A_col[nnzA]; rows need not be
+ *   sorted; no duplicates; structurally symmetric.  power >= 0 (0: P = S; at
+ *   most 8).  Builds P, the column lists of P, the entry offsets and the two
+ *   work tiers (a warp per column in shared memory, a CTA per column with a
+ *   global scratch block) and uploads them; it synchronises the device.  On a
+ *   host-only handle it builds the plan and the pattern only.  A new analysis
+ *   replaces the previous one.
+ *   warp_entries: the most entries of A a column may stage to be solved by a warp
+ *   (0 = the default and maximum, 1024; a column also needs |J_j| <= 128); smaller
+ *   values move columns to the CTA tier.
+ *   Errors: SINV_ERR_INVALID_ARG (power < 0, warp_entries < 0), SINV_ERR_PATTERN
+ *   (range, order of rowptr, duplicates, asymmetry), SINV_ERR_UNSUPPORTED
+ *   (power > 8, nnzA or |P_lo| >= 2^31, a column staging >= 2^30 entries),
+ *   SINV_ERR_OOM.
+ * sinv_spai_pattern: copies P_lo (CSR, rows sorted, the diagonal last) into
+ *   host arrays P_rowptr[n+1] and P_col[spai_nnz_P of sinv_get_stats].
+ * sinv_spai: A_val[nnzA] (device, in the order of the analysed A_col; A must be
+ *   symmetric: row k is read as column k), X_S [|S_lo|] and Y_P [|P_lo|]
+ *   (device, must not overlap; X symmetric by construction, given by its lower
+ *   part).  Stream ordered, no allocation, no synchronisation, graph-capturable.
+ *   Y is not bit-reproducible (shared-memory atomics in A_J^T A_J p).
+ *   Errors: SINV_ERR_INVALID_ARG (no analysis on the device, iters < 0,
+ *   X_S == Y_P). */
+sinv_status sinv_spai_analyse(sinv_handle h, int64_t nnzA, const int64_t *A_rowptr, const int32_t *A_col,
+                              int power, int warp_entries);
+sinv_status sinv_spai_pattern(sinv_handle h, int64_t *P_rowptr, int32_t *P_col);
+sinv_status sinv_spai(sinv_handle h, const double *A_val, const double *X_S, int iters, double *Y_P,
+                      void *stream);
+
 /* The FP32 form of sinv_lowrank_correct for callers that cannot allocate device
  * memory -- for instance code that gets all of its device memory from an
  * arena it owns, or that must not call cudaMalloc because it may synchronise
@@ -253,6 +294,12 @@ typedef struct {
     int64_t product_hits;     /* rows shared by W[:, i] and (D^{-1} W)[:, j] over the
                                  entries (i, j) of S_lo: the multiply-adds of the
                                  product (known once the maps exist, else 0)           */
+    int64_t spai_entries;     /* entries of A staged by all columns of the SPAI step
+                                 (one product A_J^T A_J p streams each twice), 0 until
+                                 sinv_spai_analyse ran                                 */
+    int64_t spai_cols_warp;   /* columns solved by a warp in shared memory             */
+    int64_t spai_cols_cta;    /* columns solved by a CTA with a global scratch block   */
+    int64_t spai_nnz_P;       /* |P_lo| of the SPAI pattern, 0 until analysed          */
 } sinv_stats;
 sinv_status sinv_get_stats(sinv_handle h, sinv_stats *out);
 

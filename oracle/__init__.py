@@ -13,9 +13,10 @@ LDL^T Factorization and Spectral Corrections"):
 * ``mix``             -- Mix approximation (Section 2.3)
 * ``lowrank_correct`` -- A^inv + V_k Lambda_k V_k^T on S, Eq. (9); diagonal
                          update formula of Section 2.6
-* ``spai_refine``     -- SPAI refinement on the fixed pattern S by Jacobi-PCG
-                         on each column's normal equations, then (Y + Y^T)/2
-                         (Section 2.4; Mix-SPAI = spai_refine(Mix))
+* ``spai_refine``     -- SPAI refinement on a fixed pattern by Jacobi-PCG on
+                         each column's normal equations, then (Y + Y^T)/2
+                         (Section 2.4; Mix-SPAI = spai_refine(Mix)); the
+                         pattern is S or S widened by ``spai_pattern``
 * ``lanczos_einv``    -- dominant eigenpairs of E_inv = A^{-1} - A^inv
                          (Section 2.5, Algorithm 1 step 5)
 * measures            -- err_1, fill_fact, fill_inv, DoDD (Sections 2.6, 3.2)
@@ -46,4 +47,4 @@ from .core import (  # noqa: F401
     accept_modes,
     build_lib,
 )
-from .spai import spai_columns, spai_refine, pcg_jacobi  # noqa: F401
+from .spai import spai_columns, spai_refine, spai_entries_sampled, spai_pattern, embed, pcg_jacobi  # noqa: F401

@@ -26,6 +26,32 @@ import numpy as np
 import scipy.sparse as sp
 
 
+def spai_pattern(A, Srp, Sc, power):
+    """Lower CSR of P = S united with {(i, j) : dist_A(i, j) <= power}, where
+    dist_A is the distance in the graph of A (power 0: P = S).  Boolean matrix
+    powers: dist_A(i, j) <= p  iff  ((I + B)^p)_ij != 0, B = pattern of A."""
+    n = A.shape[0]
+    B = sp.csr_matrix(A, dtype=np.float64, copy=True)
+    B.data[:] = 1.0
+    R = sp.identity(n, format="csr")
+    step = (B + sp.identity(n, format="csr")).tocsr()
+    for _ in range(power):
+        R = (R @ step).tocsr()
+        R.data[:] = 1.0
+    S = sp.csr_matrix((np.ones(len(Sc)), np.asarray(Sc), np.asarray(Srp)), shape=(n, n))
+    P = sp.tril(S + R, format="csr")
+    P.sort_indices()
+    return P.indptr.astype(np.int64), P.indices.astype(np.int32)
+
+
+def embed(Srp, Sc, X_S, Prp, Pc):
+    """Values on P_lo from values on S_lo (S is a subset of P): X where (i, j) in S, else 0."""
+    n = len(Srp) - 1
+    X = sp.csr_matrix((np.asarray(X_S, dtype=np.float64), np.asarray(Sc), np.asarray(Srp)), shape=(n, n))
+    rows = np.repeat(np.arange(n), np.diff(Prp))
+    return np.asarray(X[rows, np.asarray(Pc)]).ravel()
+
+
 def _full_pattern(n, Srp, Sc):
     """Column lists of the symmetric pattern S (both triangles), sorted."""
     low = sp.csr_matrix((np.ones(len(Sc)), np.asarray(Sc), np.asarray(Srp)), shape=(n, n))
@@ -66,23 +92,49 @@ def pcg_jacobi(B, b, x0, iters):
     return x
 
 
-def spai_columns(A, Srp, Sc, X_S, iters):
-    """Per column j: (J_j, m_j) after ``iters`` PCG steps on the normal
-    equations of min ||A m - e_j|| over the pattern J_j, started from the
-    values of X (symmetric, given by its lower part X_S on S_lo)."""
+def _column_solver(A, Srp, Sc, X_S):
+    """solve(j, iters) -> (J_j, m_j) for one column (see spai_columns)."""
     A = sp.csc_matrix(A, dtype=np.float64)
     Ar = sp.csr_matrix(A)
     n = A.shape[0]
     cp, ri = _full_pattern(n, Srp, Sc)
     X = _sym_values(n, Srp, Sc, X_S)
-    out = []
-    for j in range(n):
+
+    def solve(j, iters):
         J = ri[cp[j]:cp[j + 1]]
         AJ = A[:, J]
         B = (AJ.T @ AJ).toarray()
         b = Ar[j, J].toarray().ravel()          # A_J^T e_j: row j of A on the columns J
         x0 = X[:, [j]].toarray().ravel()[J]
-        out.append((J, pcg_jacobi(B, b, x0, iters)))
+        return J, pcg_jacobi(B, b, x0, iters)
+
+    return solve
+
+
+def spai_columns(A, Srp, Sc, X_S, iters):
+    """Per column j: (J_j, m_j) after ``iters`` PCG steps on the normal
+    equations of min ||A m - e_j|| over the pattern J_j, started from the
+    values of X (symmetric, given by its lower part X_S on S_lo)."""
+    solve = _column_solver(A, Srp, Sc, X_S)
+    return [solve(j, iters) for j in range(A.shape[0])]
+
+
+def spai_entries_sampled(A, Srp, Sc, X_S, iters, pairs):
+    """spai_refine at the given (i, j) in S_lo only (i >= j), solving just the
+    columns those entries need."""
+    solve = _column_solver(A, Srp, Sc, X_S)
+    cache = {}
+
+    def col(j):
+        if j not in cache:
+            J, m = solve(j, iters)
+            cache[j] = dict(zip(J.tolist(), m.tolist()))
+        return cache[j]
+
+    out = np.empty(len(pairs), dtype=np.float64)
+    for e, (i, j) in enumerate(pairs):
+        i, j = int(i), int(j)
+        out[e] = col(j)[i] if i == j else 0.5 * (col(j)[i] + col(i)[j])
     return out
 
 

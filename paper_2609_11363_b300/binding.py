@@ -29,6 +29,7 @@ EXPORTS = [
     "sinv_status_string", "sinv_last_error", "sinv_destroy", "sinv_debug_wait_timeout",
     "sinv_trace_enable", "sinv_trace_read", "sinv_lowrank_correct_noalloc",
     "sinv_batch_symbolic", "sinv_batch_layout", "sinv_ninv_stack", "sinv_ninv_drop",
+    "sinv_spai_analyse", "sinv_spai_pattern", "sinv_spai",
     "sinv_mlp_param_count", "sinv_mlp_create", "sinv_mlp_destroy", "sinv_mlp_get_params", "sinv_mlp_set_params",
     "sinv_mlp_features", "sinv_mlp_targets", "sinv_mlp_grad", "sinv_mlp_train_step", "sinv_mlp_predict",
 ]
@@ -55,7 +56,8 @@ class _Stats(ctypes.Structure):
                                               "n_levels", "max_c", "hit_pairs", "max_width", "nnz_W")] + [
         ("ninv_m", ctypes.c_int32), ("pad", ctypes.c_int32), ("horner_products", ctypes.c_int64),
         ("product_stream", ctypes.c_int64), ("selinv_flops", ctypes.c_int64), ("selinv_bytes", ctypes.c_int64),
-        ("ninv_index_bytes", ctypes.c_int64), ("product_hits", ctypes.c_int64)]
+        ("ninv_index_bytes", ctypes.c_int64), ("product_hits", ctypes.c_int64), ("spai_entries", ctypes.c_int64),
+        ("spai_cols_warp", ctypes.c_int64), ("spai_cols_cta", ctypes.c_int64), ("spai_nnz_P", ctypes.c_int64)]
 
 
 def lib_path() -> str:
@@ -79,6 +81,9 @@ def load_library():
     lib.sinv_ninv.argtypes = [H, P, P, ctypes.c_int, ctypes.c_int, P, P]
     lib.sinv_ninv_drop.argtypes = [H, P, P, ctypes.c_int, ctypes.c_double, ctypes.c_int, P, P]
     lib.sinv_mix.argtypes = [H, P, P, D, P, P]
+    lib.sinv_spai_analyse.argtypes = [H, I64, P, P, ctypes.c_int, ctypes.c_int]
+    lib.sinv_spai_pattern.argtypes = [H, P, P]
+    lib.sinv_spai.argtypes = [H, P, P, ctypes.c_int, P, P]
     lib.sinv_lowrank_correct.argtypes = [H, ctypes.c_int, P, P, ctypes.c_int, P, P]
     lib.sinv_sync_status.argtypes = [H, P]
     lib.sinv_get_stats.argtypes = [H, ctypes.POINTER(_Stats)]
@@ -391,6 +396,40 @@ class Handle:
         self._check(self._lib.sinv_mix(self._h, _check_tensor(G, "G_S", self.nnz_S),
                                        _check_tensor(N, "N_S", self.nnz_S), float(eps),
                                        _check_tensor(out, "M_S", self.nnz_S), _stream_ptr(stream)))
+        return out
+
+    def spai_analyse(self, A, power=0, warp_entries=0):
+        """Analyse the pattern of the symmetric matrix A (scipy sparse) for spai(): the
+        refinement pattern P = S widened to graph distance <= power in A.  Returns the
+        CSR A (int64 rowptr, int32 indices) whose value order spai() takes.
+        warp_entries: cap on the entries of a warp-solved column (0 = default)."""
+        import scipy.sparse as sp
+        A = sp.csr_matrix(A)
+        A.sum_duplicates()
+        rp = np.ascontiguousarray(A.indptr, dtype=np.int64)
+        col = np.ascontiguousarray(A.indices, dtype=np.int32)
+        self._check(self._lib.sinv_spai_analyse(self._h, int(A.nnz), _np_ptr(rp), _np_ptr(col), int(power),
+                                                int(warp_entries)))
+        self._spai_nnzA = int(A.nnz)
+        self.nnz_P = self.stats()["spai_nnz_P"]
+        return sp.csr_matrix((A.data, col, rp), shape=A.shape)
+
+    def spai_pattern(self):
+        """(rowptr int64[n+1], col int32[|P_lo|]) of the SPAI pattern P_lo (host)."""
+        rp = np.empty(self.n + 1, dtype=np.int64)
+        col = np.empty(max(self.nnz_P, 1), dtype=np.int32)
+        self._check(self._lib.sinv_spai_pattern(self._h, _np_ptr(rp), _np_ptr(col)))
+        return rp, col[: self.nnz_P]
+
+    def spai(self, A_val, X, iters, out=None, stream=None):
+        """SPAI refinement of X (on S) over the analysed pattern P: result on P_lo
+        (Mix-SPAI when X is Mix).  A_val in the order of the matrix spai_analyse returned."""
+        nP = getattr(self, "nnz_P", None)
+        if out is None:
+            out = torch.empty(nP or 0, dtype=torch.float64, device=self.device)
+        self._check(self._lib.sinv_spai(self._h, _check_tensor(A_val, "A_val", getattr(self, "_spai_nnzA", None)),
+                                        _check_tensor(X, "X_S", self.nnz_S), int(iters),
+                                        _check_tensor(out, "Y_P", nP), _stream_ptr(stream)))
         return out
 
     def lowrank_correct(self, V, lam, X, prec="fp64", stream=None):

@@ -140,6 +140,16 @@ struct sinv_handle_s {
     int64_t index_budget = 0;   // < 0: never; 0: half the free device memory; > 0: bytes
     int index_tried_m = -1;     // m for which the index was built or found not to fit
     std::string index_note;     // why the hash form runs (empty when the maps are used)
+    // SPAI refinement: analysis of the current pattern of A
+    SpaiPlan Q;
+    bool spai_analysed = false;  // Q holds a plan
+    bool spai_ready = false;     // ... and it is on the device
+    int64_t* dfcp = nullptr;
+    int32_t *dfri = nullptr, *dfpos = nullptr, *dfsrc = nullptr, *dfeo = nullptr, *dfE = nullptr, *dfR = nullptr;
+    int64_t* dArp = nullptr;
+    int32_t *dAcol = nullptr, *dscols_w = nullptr, *dscols_c = nullptr, *dsticket = nullptr;
+    double* dsscratch = nullptr;
+    int64_t spai_cta_bytes = 0;
     std::string last_error;
 };
 
@@ -163,6 +173,21 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
     return e;
 }
 
+void spai_free(sinv_handle h) {
+    void* ptrs[] = {h->dfcp, h->dfri, h->dfpos, h->dfsrc, h->dfeo, h->dfE, h->dfR, h->dArp, h->dAcol, h->dscols_w,
+                    h->dscols_c, h->dsticket, h->dsscratch};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    h->dfcp = nullptr;
+    h->dfri = h->dfpos = h->dfsrc = h->dfeo = h->dfE = h->dfR = nullptr;
+    h->dArp = nullptr;
+    h->dAcol = h->dscols_w = h->dscols_c = h->dsticket = nullptr;
+    h->dsscratch = nullptr;
+    h->spai_ready = false;
+    h->spai_analysed = false;
+    h->Q = SpaiPlan();
+}
+
 void free_all(sinv_handle h) {
     void* ptrs[] = {h->dSrp, h->dSc, h->dSdiag, h->dl2s, h->dLrp, h->dLcp, h->dLri, h->dLcsr, h->ddpos, h->dpstart,
                     h->dsn, h->dorder, h->downer, h->dCrow, h->dLmap, h->dJJl, h->dJJs, h->dhit_ik, h->dhit_pos,
@@ -171,6 +196,7 @@ void free_all(sinv_handle h) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     ninv_maps_free(h->X);
+    spai_free(h);
 }
 
 sinv_status ensure_work(sinv_handle h, size_t bytes) {
@@ -445,6 +471,10 @@ sinv_status sinv_get_stats(sinv_handle h, sinv_stats* s) {
     s->selinv_bytes = P.selinv_bytes;
     s->ninv_index_bytes = h->X.ready ? h->X.bytes : 0;
     s->product_hits = h->X.ready ? h->X.hits : 0;
+    s->spai_entries = h->spai_analysed ? h->Q.entries : 0;
+    s->spai_cols_warp = h->spai_analysed ? (int64_t)h->Q.cols_w.size() : 0;
+    s->spai_cols_cta = h->spai_analysed ? (int64_t)h->Q.cols_c.size() : 0;
+    s->spai_nnz_P = h->spai_analysed ? h->Q.nnzP : 0;
     return SINV_OK;
 }
 
@@ -666,6 +696,140 @@ sinv_status sinv_lowrank_correct(sinv_handle h, int k, const double* V, const do
     if ((e = lowrank_launch(h->P.n, h->dSrp, h->dSc, k, V, lambda, prec == SINV_FP32 ? 1 : 0, h->dwork, X_S,
                             h->num_sms, (cudaStream_t)stream)) != cudaSuccess)
         return cuda_fail(h, e, "lowrank launch");
+    return SINV_OK;
+}
+
+sinv_status sinv_spai_analyse(sinv_handle h, int64_t nnzA, const int64_t* A_rowptr, const int32_t* A_col, int power,
+                              int warp_entries) {
+    if (!h || nnzA < 0 || !A_rowptr || (nnzA > 0 && !A_col) || warp_entries < 0 || power < 0)
+        return SINV_ERR_INVALID_ARG;
+    if (power > 8) {
+        set_err(h, "power > 8 is not supported");
+        return SINV_ERR_UNSUPPORTED;
+    }
+    cudaError_t e = cudaSuccess;
+    if (h->device >= 0) {
+        if ((e = cudaSetDevice(h->device)) != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+        if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(h, e, "synchronize");
+    }
+    spai_free(h);
+    std::string err;
+    try {
+        const int we = warp_entries == 0 ? kSpaiWarpE : std::min(warp_entries, kSpaiWarpE);
+        err = build_spai_plan(h->P, nnzA, A_rowptr, A_col, power, kSpaiWarpJ, we, kSpaiWarpH / 2, h->Q);
+    } catch (const std::bad_alloc&) {
+        h->Q = SpaiPlan();
+        set_err(h, "host allocation failed in the SPAI analysis");
+        return SINV_ERR_OOM;
+    }
+    if (!err.empty()) {
+        h->Q = SpaiPlan();
+        set_err(h, err);
+        return err.find("not supported") != std::string::npos ? SINV_ERR_UNSUPPORTED : SINV_ERR_PATTERN;
+    }
+    h->spai_analysed = true;
+    if (h->device < 0) return SINV_OK;  // host-only handle: the plan and the pattern, no upload
+    const SpaiPlan& Q = h->Q;
+    std::vector<int64_t> Arp(A_rowptr, A_rowptr + h->P.n + 1);
+    std::vector<int32_t> Acol(A_col, A_col + nnzA);
+    std::vector<int32_t> zero2(2, 0);
+#define UPS(dst, src)                                            \
+    do {                                                         \
+        if ((e = upload(&h->dst, src)) != cudaSuccess) {         \
+            spai_free(h);                                        \
+            return cuda_fail(h, e, "upload " #dst);              \
+        }                                                        \
+    } while (0)
+    UPS(dfcp, Q.fcp);
+    UPS(dfri, Q.fri);
+    UPS(dfpos, Q.fpos);
+    UPS(dfsrc, Q.fsrc);
+    UPS(dfeo, Q.feo);
+    UPS(dfE, Q.fE);
+    UPS(dfR, Q.fR);
+    UPS(dArp, Arp);
+    UPS(dAcol, Acol);
+    UPS(dscols_w, Q.cols_w);
+    UPS(dscols_c, Q.cols_c);
+    UPS(dsticket, zero2);
+#undef UPS
+    if ((e = spai_configure()) != cudaSuccess) {
+        spai_free(h);
+        return cuda_fail(h, e, "kernel attributes");
+    }
+    h->spai_cta_bytes = 0;
+    if (!Q.cols_c.empty()) {
+        h->spai_cta_bytes = (int64_t)spai_cta_bytes(Q.cap_nj, Q.cap_E, Q.cap_H);
+        if ((size_t)h->spai_cta_bytes > kSpaiCtaSmemMax) {
+            const size_t bytes = (size_t)h->spai_cta_bytes *
+                                 (size_t)spai_cta_grid(h->num_sms, (int64_t)Q.cols_c.size(), (size_t)h->spai_cta_bytes);
+            if ((e = cudaMalloc((void**)&h->dsscratch, bytes)) != cudaSuccess) {
+                spai_free(h);
+                return cuda_fail(h, e, "SPAI scratch");
+            }
+        }
+    }
+    h->spai_ready = true;
+    return SINV_OK;
+}
+
+sinv_status sinv_spai_pattern(sinv_handle h, int64_t* P_rowptr, int32_t* P_col) {
+    if (!h || !P_rowptr) return SINV_ERR_INVALID_ARG;
+    if (!h->spai_analysed) {
+        set_err(h, "sinv_spai_pattern needs sinv_spai_analyse first");
+        return SINV_ERR_INVALID_ARG;
+    }
+    if (h->Q.nnzP > 0 && !P_col) return SINV_ERR_INVALID_ARG;
+    memcpy(P_rowptr, h->Q.Prp.data(), h->Q.Prp.size() * sizeof(int64_t));
+    if (h->Q.nnzP > 0) memcpy(P_col, h->Q.Pc.data(), h->Q.Pc.size() * sizeof(int32_t));
+    return SINV_OK;
+}
+
+sinv_status sinv_spai(sinv_handle h, const double* A_val, const double* X_S, int iters, double* Y_P, void* stream) {
+    if (!h || iters < 0) return SINV_ERR_INVALID_ARG;
+    if (!on_device(h)) return SINV_ERR_INVALID_ARG;
+    if (!h->spai_ready) {
+        set_err(h, "sinv_spai needs sinv_spai_analyse first");
+        return SINV_ERR_INVALID_ARG;
+    }
+    if (h->Q.nnzP == 0) return SINV_OK;
+    if (!X_S || !Y_P || (!A_val && h->Q.nnzA > 0)) return SINV_ERR_INVALID_ARG;
+    if (X_S == Y_P) {
+        set_err(h, "X_S and Y_P must not overlap");
+        return SINV_ERR_INVALID_ARG;
+    }
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    const SpaiPlan& Q = h->Q;
+    SpaiArgs a;
+    a.fcp = h->dfcp;
+    a.fri = h->dfri;
+    a.fpos = h->dfpos;
+    a.fsrc = h->dfsrc;
+    a.feo = h->dfeo;
+    a.fE = h->dfE;
+    a.fR = h->dfR;
+    a.Arp = h->dArp;
+    a.Acol = h->dAcol;
+    a.Aval = A_val;
+    a.X = X_S;
+    a.Y = Y_P;
+    a.nnzP = h->Q.nnzP;
+    a.iters = iters;
+    a.cols = h->dscols_w;
+    a.ncols = (int64_t)Q.cols_w.size();
+    a.cols_cta = h->dscols_c;
+    a.ncols_cta = (int64_t)Q.cols_c.size();
+    a.ticket = h->dsticket;
+    a.scratch = h->dsscratch;
+    a.cta_bytes = h->spai_cta_bytes;
+    a.cta_in_smem = (size_t)h->spai_cta_bytes <= kSpaiCtaSmemMax ? 1 : 0;
+    a.cap_nj = Q.cap_nj;
+    a.cap_E = Q.cap_E;
+    a.cap_H = Q.cap_H;
+    a.status = h->dstatus;
+    TraceScope trace_scope(h->tracer);
+    if ((e = spai_launch(a, h->num_sms, (cudaStream_t)stream)) != cudaSuccess) return cuda_fail(h, e, "spai launch");
     return SINV_OK;
 }
 

@@ -132,6 +132,42 @@ constexpr int64_t kLowrankStaticFloats = int64_t(1) << 22;  // 4,194,304 floats 
 cudaError_t lowrank_noalloc_launch(int64_t n, const int64_t* Srp, const int32_t* Sc, int k, const double* V,
                                    const double* lambda, double* X, cudaStream_t st);
 
+// ---- SPAI refinement (spai.cu) ----
+constexpr int kSpaiWarpJ = 128;   // tier W: rows of the column
+constexpr int kSpaiWarpE = 1024;  // tier W: staged entries of A
+constexpr int kSpaiWarpH = 512;   // tier W: table slots (a tier-W column has at most kSpaiWarpH/2 rows of A)
+struct SpaiArgs {
+    const int64_t* fcp;   // columns of P (both triangles)
+    const int32_t* fri;
+    const int32_t* fpos;  // P_lo position of each entry
+    const int32_t* fsrc;  // S_lo position of each entry (-1: not in S)
+    const int32_t* feo;   // entry offset of each row inside its column's list
+    const int32_t* fE;    // entries per column
+    const int32_t* fR;    // distinct rows of A per column
+    const int64_t* Arp;   // A (symmetric), CSR
+    const int32_t* Acol;
+    const double* Aval;
+    const double* X;      // start values on S_lo
+    double* Y;            // result on P_lo (zeroed by the launcher)
+    int64_t nnzP;
+    int iters;
+    const int32_t* cols;      // tier W columns
+    int64_t ncols;
+    const int32_t* cols_cta;  // tier C columns
+    int64_t ncols_cta;
+    int32_t* ticket;          // 2 counters, zeroed by the launcher
+    double* scratch;          // tier C: one block of cta_bytes per CTA (unused when it fits shared memory)
+    int64_t cta_bytes;
+    int cta_in_smem;          // tier C arrays in dynamic shared memory
+    int64_t cap_nj, cap_E, cap_H;
+    int32_t* status;
+};
+cudaError_t spai_configure();
+size_t spai_cta_bytes(int64_t cap_nj, int64_t cap_E, int64_t cap_H);
+constexpr size_t kSpaiCtaSmemMax = 200 * 1024;  // tier C blocks up to this size live in shared memory
+int spai_cta_grid(int num_sms, int64_t ncols_cta, size_t cta_bytes);
+cudaError_t spai_launch(const SpaiArgs& a, int num_sms, cudaStream_t st);
+
 cudaError_t debug_wait_launch(uint32_t* flag, int32_t* status, int64_t limit, cudaStream_t st);
 
 // ---- learned correction (mlp.cu) ----

@@ -82,6 +82,31 @@ struct NinvPlan {
     int64_t product_stream = 0;
 };
 
+// SPAI refinement (Section 2.4) on a symmetric pattern P for a given pattern of
+// A.  P = S united with {(i, j) : graph distance between i and j in A <= power}
+// (power 0: P = S), lower part in CSR.  Its columns (both triangles, rows
+// ascending) carry the P_lo position of each entry, the S_lo position the
+// start value comes from (-1: start at 0), and the offset of the entry's row
+// of A inside the column's list of A entries.  Columns are split into two
+// tiers by size.
+struct SpaiPlan {
+    int64_t n = 0, nnzA = 0, nnzP = 0;
+    int power = 0;
+    std::vector<int64_t> Prp;     // P_lo, CSR with sorted rows (the diagonal last)
+    std::vector<int32_t> Pc;
+    std::vector<int64_t> fcp;     // n+1
+    std::vector<int32_t> fri;     // |P|: rows of each column, ascending
+    std::vector<int32_t> fpos;    // |P|: P_lo position of (max, min)
+    std::vector<int32_t> fsrc;    // |P|: S_lo position of (max, min), -1 outside S
+    std::vector<int32_t> feo;     // |P|: sum of nnz(A row) over the earlier rows of the column
+    std::vector<int32_t> fE;      // n: entries of A staged by each column
+    std::vector<int32_t> fR;      // n: distinct rows of A those entries touch (the table y)
+    std::vector<int32_t> cols_w;  // columns a warp solves in shared memory (most entries first)
+    std::vector<int32_t> cols_c;  // the rest: a CTA each, with a global scratch block
+    int64_t cap_nj = 0, cap_E = 0, cap_H = 0;  // largest tier-C column: rows, entries, table (pow2 >= 2R)
+    int64_t entries = 0;          // sum of fE: entries of A streamed by one B product over all columns
+};
+
 // Returns an empty string on success, else the reason the pattern is invalid.
 // big_pairs: supernodes with at least this many pairs are processed by a whole CTA;
 // group: small supernodes per work item (one per warp); levels with fewer than
@@ -90,5 +115,9 @@ std::string build_plan(int64_t n, const int64_t* L_rowptr, const int32_t* L_col,
                        const int8_t* pivot_start, int supernode_cap, int64_t big_pairs, int group,
                        int64_t thin_level, HostPlan& P);
 std::string build_ninv_plan(const HostPlan& P, int m, NinvPlan& W);
+// A: n x n CSR pattern (host), structurally symmetric; warp_j / warp_e / warp_r: the
+// tier-W caps on pattern rows, staged entries and distinct rows of A.
+std::string build_spai_plan(const HostPlan& P, int64_t nnzA, const int64_t* A_rowptr, const int32_t* A_col,
+                            int power, int warp_j, int warp_e, int warp_r, SpaiPlan& X);
 
 }  // namespace sinv

@@ -512,4 +512,143 @@ std::string build_ninv_plan(const HostPlan& P, int m, NinvPlan& W) {
     return "";
 }
 
+std::string build_spai_plan(const HostPlan& P, int64_t nnzA, const int64_t* Arp, const int32_t* Ac, int power,
+                            int warp_j, int warp_e, int warp_r, SpaiPlan& X) {
+    const int64_t n = P.n;
+    X = SpaiPlan();
+    X.n = n;
+    X.nnzA = nnzA;
+    X.power = power;
+    if (Arp[0] != 0 || Arp[n] != nnzA) return "A_rowptr must start at 0 and end at nnzA";
+    for (int64_t i = 0; i < n; ++i)
+        if (Arp[i + 1] < Arp[i]) return "A_rowptr must be non-decreasing";
+    if (nnzA >= ((int64_t)1 << 31)) return "nnzA >= 2^31 is not supported";
+    // rows sorted on a copy: range, duplicates and structural symmetry
+    std::vector<int32_t> sorted(Ac, Ac + nnzA);
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t* b = sorted.data() + Arp[i];
+        int32_t* e = sorted.data() + Arp[i + 1];
+        std::sort(b, e);
+        for (int32_t* c = b; c != e; ++c) {
+            if (*c < 0 || *c >= n) return "A column index out of range";
+            if (c + 1 != e && c[1] == *c) return "A has a duplicate entry";
+        }
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t q = Arp[i]; q < Arp[i + 1]; ++q) {
+            const int32_t k = sorted[q];
+            if (!std::binary_search(sorted.begin() + Arp[k], sorted.begin() + Arp[k + 1], (int32_t)i))
+                return "the pattern of A is not symmetric";
+        }
+    // P_lo row by row: S_lo row i, and every j <= i within `power` steps of i in the graph of A
+    X.Prp.assign(n + 1, 0);
+    std::vector<int64_t> reached(n, -1);
+    std::vector<int32_t> row, frontier, next;
+    std::vector<int32_t> src_of;  // per P_lo entry: S_lo position or -1
+    for (int64_t i = 0; i < n; ++i) {
+        row.assign(P.Sc.begin() + P.Srp[i], P.Sc.begin() + P.Srp[i + 1]);
+        if (power > 0) {
+            reached[i] = i;
+            row.push_back((int32_t)i);
+            frontier.assign(1, (int32_t)i);
+            for (int step = 0; step < power && !frontier.empty(); ++step) {
+                next.clear();
+                for (int32_t u : frontier)
+                    for (int64_t q = Arp[u]; q < Arp[u + 1]; ++q) {
+                        const int32_t v = sorted[q];
+                        if (reached[v] == i) continue;
+                        reached[v] = i;
+                        next.push_back(v);
+                        if (v <= i) row.push_back(v);
+                    }
+                frontier.swap(next);
+            }
+        }
+        std::sort(row.begin(), row.end());
+        row.erase(std::unique(row.begin(), row.end()), row.end());
+        X.Prp[i + 1] = X.Prp[i] + (int64_t)row.size();
+        if (X.Prp[i + 1] >= ((int64_t)1 << 31)) return "the refinement pattern has >= 2^31 entries: not supported";
+        // S positions: S_lo row i is sorted and a subset of the row
+        int64_t p = P.Srp[i];
+        for (int32_t c : row) {
+            X.Pc.push_back(c);
+            if (p < P.Srp[i + 1] && P.Sc[p] == c) src_of.push_back((int32_t)p++);
+            else src_of.push_back(-1);
+        }
+    }
+    X.nnzP = X.Prp[n];
+    // columns of P: row j of P_lo (rows k <= j), then the entries (i, j) of later rows i
+    std::vector<int64_t> cnt(n, 0);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t p = X.Prp[i]; p < X.Prp[i + 1]; ++p) {
+            cnt[i] += 1;
+            if (X.Pc[p] != i) cnt[X.Pc[p]] += 1;
+        }
+    X.fcp.assign(n + 1, 0);
+    for (int64_t j = 0; j < n; ++j) X.fcp[j + 1] = X.fcp[j] + cnt[j];
+    const int64_t nf = X.fcp[n];
+    X.fri.resize(nf);
+    X.fpos.resize(nf);
+    X.fsrc.resize(nf);
+    std::vector<int64_t> cur(n);
+    for (int64_t j = 0; j < n; ++j) {
+        int64_t q = X.fcp[j];
+        for (int64_t p = X.Prp[j]; p < X.Prp[j + 1]; ++p, ++q) {
+            X.fri[q] = X.Pc[p];
+            X.fpos[q] = (int32_t)p;
+            X.fsrc[q] = src_of[p];
+        }
+        cur[j] = q;
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t p = X.Prp[i]; p < X.Prp[i + 1]; ++p) {
+            const int32_t j = X.Pc[p];
+            if (j == i) continue;
+            X.fri[cur[j]] = (int32_t)i;
+            X.fpos[cur[j]] = (int32_t)p;
+            X.fsrc[cur[j]] = src_of[p];
+            ++cur[j];
+        }
+    // entry offsets, distinct rows per column and the two tiers
+    X.feo.resize(nf);
+    X.fE.resize(n);
+    X.fR.resize(n);
+    std::vector<int64_t> seen(n, -1);
+    int64_t cap_R = 0;
+    for (int64_t j = 0; j < n; ++j) {
+        int64_t acc = 0, R = 0;
+        for (int64_t q = X.fcp[j]; q < X.fcp[j + 1]; ++q) {
+            X.feo[q] = (int32_t)acc;
+            const int32_t k = X.fri[q];
+            acc += Arp[k + 1] - Arp[k];
+            if (acc >= ((int64_t)1 << 30)) return "a column of P stages more than 2^30 entries of A: not supported";
+            for (int64_t e = Arp[k]; e < Arp[k + 1]; ++e)
+                if (seen[Ac[e]] != j) {
+                    seen[Ac[e]] = j;
+                    ++R;
+                }
+        }
+        X.fE[j] = (int32_t)acc;
+        X.fR[j] = (int32_t)R;
+        X.entries += acc;
+        const int64_t nj = X.fcp[j + 1] - X.fcp[j];
+        if (nj <= warp_j && acc <= warp_e && R <= warp_r) {
+            X.cols_w.push_back((int32_t)j);
+        } else {
+            X.cols_c.push_back((int32_t)j);
+            X.cap_nj = std::max(X.cap_nj, nj);
+            X.cap_E = std::max(X.cap_E, acc);
+            cap_R = std::max(cap_R, R);
+        }
+    }
+    if (!X.cols_c.empty()) {
+        X.cap_H = 32;
+        while (X.cap_H < 2 * cap_R) X.cap_H <<= 1;
+    }
+    auto by_size = [&](int32_t a, int32_t b) { return X.fE[a] > X.fE[b]; };
+    std::stable_sort(X.cols_w.begin(), X.cols_w.end(), by_size);
+    std::stable_sort(X.cols_c.begin(), X.cols_c.end(), by_size);
+    return "";
+}
+
 }  // namespace sinv

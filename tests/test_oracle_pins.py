@@ -517,3 +517,34 @@ def test_spai_residual_never_grows():
             assert np.all(res <= prev * (1 + 1e-12) + 1e-15)
         prev = res
     assert prev.max() < 0.9  # and it did move
+
+
+def test_spai_sampled_entries_match_the_full_refinement():
+    A, Srp, Sc = _spai_case(n=25, seed=9)
+    X = 0.1 * np.random.default_rng(2).standard_normal(len(Sc))
+    full = oracle.spai_refine(A, Srp, Sc, X, 3)
+    rows = _rows(Srp)
+    idx = np.arange(0, len(Sc), 5)
+    got = oracle.spai_entries_sampled(A, Srp, Sc, X, 3, list(zip(rows[idx], Sc[idx])))
+    np.testing.assert_array_equal(got, full[idx])
+
+
+def test_spai_pattern_by_breadth_first_search():
+    # P = S + {(i, j): graph distance <= p}: brute force by BFS on a small random graph
+    A, Srp, Sc = _spai_case(n=35, seed=4)
+    n = A.shape[0]
+    adj = [set(A[i].indices.tolist()) - {i} for i in range(n)]
+    S = set(zip(_rows(Srp).tolist(), Sc.tolist()))
+    for p in (0, 1, 2, 3):
+        want = set(S)
+        for i in range(n):
+            dist = {i: 0}
+            ring = [i]
+            for d in range(1, p + 1):
+                ring = [v for u in ring for v in adj[u] if v not in dist]
+                for v in ring:
+                    dist.setdefault(v, d)
+            want |= {(i, j) for j in dist if j <= i}
+        Prp, Pc = oracle.spai_pattern(A, Srp, Sc, p)
+        assert set(zip(_rows(Prp).tolist(), Pc.tolist())) == want
+        assert np.all(Pc[Prp[1:] - 1] == np.arange(n))  # the diagonal ends every row

@@ -166,3 +166,47 @@ def test_batch_layout_host(lib):
         s0, r0 = lay["S"][b], lay["n"][b]
         assert np.array_equal(col[s0:lay["S"][b + 1]] - r0, S[1])
         assert np.array_equal(rp[r0:r0 + f.n + 1] - s0, S[0])
+
+
+def _spai_cases():
+    from workloads.configs import covariance
+    w = lap2d_32()
+    c = covariance(12)
+    return {"lap2d": (w.A, w.factors), "covariance_12": (c.A, c.factors)}
+
+
+@pytest.mark.parametrize("power", [0, 1, 2, 3])
+@pytest.mark.parametrize("name", ["lap2d", "covariance_12"])
+def test_spai_pattern_bit_exact_vs_oracle(lib, name, power):
+    A, f = _spai_cases()[name]
+    h = _host_handle(f)
+    h.spai_analyse(A, power=power)
+    rp, col = h.spai_pattern()
+    S = oracle.symbolic_S(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+    want = oracle.spai_pattern(A, S[0], S[1], power)
+    assert np.array_equal(rp, want[0]) and np.array_equal(col, want[1])
+    st = h.stats()
+    assert st["spai_nnz_P"] == len(want[1])
+    assert st["spai_cols_warp"] + st["spai_cols_cta"] == f.n
+    # entries staged per B product: sum over the columns j of P of nnz(A) of their rows
+    full = sp.csr_matrix((np.ones(len(col)), col, rp), shape=(f.n, f.n))
+    full = full + sp.tril(full, k=-1).T
+    annz = np.diff(sp.csr_matrix(A).indptr)
+    assert st["spai_entries"] == int(np.asarray(full.sum(axis=0)).ravel() @ annz)
+
+
+def test_spai_analysis_rejects_bad_patterns(lib):
+    from paper_2609_11363_b300 import SinvError
+    w = lap2d_32()
+    h = _host_handle(w.factors)
+    B = sp.csr_matrix(w.A, copy=True).tolil()
+    B[0, w.factors.n - 1] = 1.0  # one entry without its mirror
+    with pytest.raises(SinvError) as e:
+        h.spai_analyse(B.tocsr())
+    assert e.value.name == "SINV_ERR_PATTERN"
+    with pytest.raises(SinvError) as e:
+        h.spai_analyse(w.A, power=-1)
+    assert e.value.name == "SINV_ERR_INVALID_ARG"
+    with pytest.raises(SinvError) as e:
+        h.spai_analyse(w.A, power=9)
+    assert e.value.name == "SINV_ERR_UNSUPPORTED"
