@@ -34,7 +34,8 @@ struct WarpLayout {
     static constexpr size_t kEa = 0;                                        // double[kE]
     static constexpr size_t kY = kEa + sizeof(double) * kE;                 // double[kH]: y, or keys + ids
     static constexpr size_t kVec = kY + sizeof(double) * kH;                // x r p q dinv: double[5 kJ]
-    static constexpr size_t kSoff = kVec + sizeof(double) * 5 * kJ;         // int32[kH + 1]
+    static constexpr size_t kScal = kVec + sizeof(double) * 5 * kJ;         // double[2]
+    static constexpr size_t kSoff = kScal + sizeof(double) * 2;             // int32[kH + 1]
     static constexpr size_t kEt = kSoff + sizeof(int32_t) * (kH + 1);       // uint16[kE] row run t
     static constexpr size_t kEs = kEt + sizeof(uint16_t) * kE;              // uint16[kE] table id c
     static constexpr size_t kPerm = kEs + sizeof(uint16_t) * kE;            // uint16[kE] entries by id
@@ -72,18 +73,6 @@ struct CtaGroup {
     __device__ static int size() { return kCtaThreads; }
     __device__ static int rank() { return threadIdx.x; }
     __device__ static void sync() { __syncthreads(); }
-    // warp butterflies, then every thread adds the warp totals in the same order
-    __device__ static double sum(double v, double* red) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-        __syncthreads();
-        double s = 0.0;
-#pragma unroll
-        for (int w = 0; w < kW; ++w) s += red[w];
-        __syncthreads();
-        return s;
-    }
     __device__ static int scan_excl(int v, int* tmp, int* total) {
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
         int x = v;
@@ -127,7 +116,16 @@ struct ColumnMem {
     I* es;           // per entry: its table id c
     I* perm;         // entries grouped by table id
     int32_t* eoff;   // nj + 1 entry offsets, one run per pattern row
+    double* scal;    // 2 scalars the vector warp hands to the group (stop flag, r.z)
     int32_t cap_h;   // table size available (power of two)
+};
+
+// One thread's contiguous share [lo, hi) of the staged entries, with the table id and
+// the pattern row its first entry belongs to.  Every product walks the same shares, so
+// each thread does the same number of multiply-adds (a warp's FP64 instruction costs
+// the pipe the same however many of its lanes are active).
+struct Share {
+    int lo, hi, c, t;
 };
 
 __device__ __forceinline__ uint32_t slot_hash(int32_t r, int shift) {
@@ -164,29 +162,48 @@ __device__ int group_scan(int32_t* a, int L, int* tmp) {
     return total;
 }
 
-// q = B v = A_J^T (A_J v) over the staged entries (two gathers)
+// q = B v = A_J^T (A_J v) over the staged entries: each thread sums its share in
+// table-id order into y, then in row order into q, adding a partial sum at every
+// segment end (shared-memory atomics, a few per thread)
 template <class G, class I>
-__device__ void apply_normal(const ColumnMem<I>& m, int nj, int R, const double* v, double* q) {
+__device__ void apply_normal(const ColumnMem<I>& m, int nj, int R, const Share& sh, const double* v, double* q) {
     const int tid = G::rank(), gsz = G::size();
-    for (int c = tid; c < R; c += gsz) {
+    for (int c = tid; c < R; c += gsz) m.y[c] = 0.0;
+    for (int t = tid; t < nj; t += gsz) q[t] = 0.0;
+    G::sync();
+    if (sh.lo < sh.hi) {
+        int c = sh.c, end = m.soff[c];
         double s = 0.0;
-        for (int o2 = c ? m.soff[c - 1] : 0; o2 < m.soff[c]; ++o2) {
+        for (int o2 = sh.lo; o2 < sh.hi; ++o2) {
+            if (o2 == end) {  // every id owns at least one entry
+                atomicAdd(m.y + c, s);
+                s = 0.0;
+                end = m.soff[++c];
+            }
             const int o = m.perm[o2];
-            s += m.ea[o] * v[m.et[o]];
+            s = fma(m.ea[o], v[m.et[o]], s);
         }
-        m.y[c] = s;
+        atomicAdd(m.y + c, s);
     }
     G::sync();
-    for (int t = tid; t < nj; t += gsz) {
+    if (sh.lo < sh.hi) {
+        int t = sh.t, end = m.eoff[t + 1];
         double s = 0.0;
-        for (int o = m.eoff[t]; o < m.eoff[t + 1]; ++o) s += m.ea[o] * m.y[m.es[o]];
-        q[t] = s;
+        for (int o = sh.lo; o < sh.hi; ++o) {
+            while (o == end) {  // rows of A without entries end where they start
+                atomicAdd(q + t, s);
+                s = 0.0;
+                end = m.eoff[++t + 1];
+            }
+            s = fma(m.ea[o], m.y[m.es[o]], s);
+        }
+        atomicAdd(q + t, s);
     }
     G::sync();
 }
 
 template <class G, class I>
-__device__ void solve_column(const SpaiArgs& a, int j, const ColumnMem<I>& m, double* red, int* tmp) {
+__device__ void solve_column(const SpaiArgs& a, int j, const ColumnMem<I>& m, int* tmp) {
     const int tid = G::rank(), gsz = G::size();
     const int64_t c0 = a.fcp[j];
     const int nj = (int)(a.fcp[j + 1] - c0);
@@ -248,37 +265,70 @@ __device__ void solve_column(const SpaiArgs& a, int j, const ColumnMem<I>& m, do
         for (int o = m.eoff[t]; o < m.eoff[t + 1]; ++o) s += m.ea[o] * m.ea[o];
         m.dinv[t] = s != 0.0 ? 1.0 / s : 0.0;  // Jacobi: diag(B)_k = ||A e_k||^2
     }
-    // r = b - B x, z = D^{-1} r, p = z
-    apply_normal<G>(m, nj, R, m.x, m.q);
-    double rz = 0.0;
-    for (int t = tid; t < nj; t += gsz) {
-        const double rt = m.r[t] - m.q[t];
-        const double zt = m.dinv[t] * rt;
-        m.r[t] = rt;
-        m.p[t] = zt;
-        rz += rt * zt;
+    // this thread's share of the entries, with the id and row of its first entry
+    Share sh;
+    {
+        const int chunk = (E + gsz - 1) / gsz;
+        sh.lo = min(E, tid * chunk);
+        sh.hi = min(E, sh.lo + chunk);
+        sh.t = sh.lo < sh.hi ? run_of(m.eoff, nj, sh.lo) : 0;
+        int lo = 0, hi = R - 1;  // smallest c with soff[c] > sh.lo
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (m.soff[mid] > sh.lo) hi = mid; else lo = mid + 1;
+        }
+        sh.c = lo;
     }
-    rz = G::sum(rz, red);
+    // the CG vector work (a few vectors of nj) runs on the group's first warp; its
+    // scalars reach the other threads through m.scal
+    const bool vw = tid < 32;
+    const int lane = tid & 31;
+    // r = b - B x, z = D^{-1} r, p = z
+    apply_normal<G>(m, nj, R, sh, m.x, m.q);
+    if (vw) {
+        double rz = 0.0;
+        for (int t = lane; t < nj; t += 32) {
+            const double rt = m.r[t] - m.q[t];
+            const double zt = m.dinv[t] * rt;
+            m.r[t] = rt;
+            m.p[t] = zt;
+            rz += rt * zt;
+        }
+        rz = WarpGroup::sum(rz, nullptr);
+        if (lane == 0) m.scal[1] = rz;
+    }
+    G::sync();
+    double rz = m.scal[1];
     for (int it = 0; it < a.iters; ++it) {
         if (rz == 0.0) break;
-        G::sync();  // p complete before the gathers read it
-        apply_normal<G>(m, nj, R, m.p, m.q);
-        double pq = 0.0;
-        for (int t = tid; t < nj; t += gsz) pq += m.p[t] * m.q[t];
-        pq = G::sum(pq, red);
-        if (!(pq > 0.0)) break;
-        const double alpha = rz / pq;
-        double rzn = 0.0;
-        for (int t = tid; t < nj; t += gsz) {
-            m.x[t] += alpha * m.p[t];
-            const double rt = m.r[t] - alpha * m.q[t];
-            m.r[t] = rt;
-            rzn += rt * (m.dinv[t] * rt);
+        apply_normal<G>(m, nj, R, sh, m.p, m.q);
+        if (vw) {
+            double pq = 0.0;
+            for (int t = lane; t < nj; t += 32) pq += m.p[t] * m.q[t];
+            pq = WarpGroup::sum(pq, nullptr);
+            double rzn = 0.0;
+            const bool stop = !(pq > 0.0);
+            if (!stop) {
+                const double alpha = rz / pq;
+                for (int t = lane; t < nj; t += 32) {
+                    m.x[t] += alpha * m.p[t];
+                    const double rt = m.r[t] - alpha * m.q[t];
+                    m.r[t] = rt;
+                    rzn += rt * (m.dinv[t] * rt);
+                }
+                rzn = WarpGroup::sum(rzn, nullptr);
+                const double beta = rzn / rz;
+                for (int t = lane; t < nj; t += 32) m.p[t] = m.dinv[t] * m.r[t] + beta * m.p[t];
+            }
+            if (lane == 0) {
+                m.scal[0] = stop ? 1.0 : 0.0;
+                m.scal[1] = rzn;
+            }
         }
-        rzn = G::sum(rzn, red);
-        const double beta = rzn / rz;
-        for (int t = tid; t < nj; t += gsz) m.p[t] = m.dinv[t] * m.r[t] + beta * m.p[t];
-        rz = rzn;
+        G::sync();
+        if (m.scal[0] != 0.0) break;
+        rz = m.scal[1];
+        G::sync();  // every thread has read the scalars before the vector warp rewrites them
     }
     // (Y + Y^T)/2: an off-diagonal entry of P_lo gets exactly two halves (from column j
     // and from column i) added to a zeroed Y, so the result does not depend on their order
@@ -304,6 +354,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) spai_warp_kernel(SpaiArgs a
     m.p = vec + 2 * L::kJ;
     m.q = vec + 3 * L::kJ;
     m.dinv = vec + 4 * L::kJ;
+    m.scal = reinterpret_cast<double*>(base + L::kScal);
     m.soff = reinterpret_cast<int32_t*>(base + L::kSoff);
     m.et = reinterpret_cast<uint16_t*>(base + L::kEt);
     m.es = reinterpret_cast<uint16_t*>(base + L::kEs);
@@ -315,14 +366,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) spai_warp_kernel(SpaiArgs a
         if ((threadIdx.x & 31) == 0) c = atomicAdd(a.ticket, 1);
         c = WarpGroup::broadcast(c, nullptr);
         if (c >= a.ncols) break;
-        solve_column<WarpGroup>(a, a.cols[c], m, nullptr, nullptr);
+        solve_column<WarpGroup>(a, a.cols[c], m, nullptr);
     }
 }
 
 template <bool kSmem>
 __global__ void __launch_bounds__(kCtaThreads) spai_cta_kernel(SpaiArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double red[CtaGroup::kW];
+    __shared__ double scal[2];
     __shared__ int tmp[CtaGroup::kW];
     __shared__ int cell;
     const int64_t cj = a.cap_nj, cE = a.cap_E, cH = a.cap_H;
@@ -341,11 +392,12 @@ __global__ void __launch_bounds__(kCtaThreads) spai_cta_kernel(SpaiArgs a) {
     m.es = m.et + cE;
     m.perm = m.es + cE;
     m.eoff = m.perm + cE;
+    m.scal = scal;
     m.cap_h = (int32_t)cH;
     for (;;) {
         int c = CtaGroup::broadcast(threadIdx.x == 0 ? atomicAdd(a.ticket + 1, 1) : 0, &cell);
         if (c >= a.ncols_cta) break;
-        solve_column<CtaGroup>(a, a.cols_cta[c], m, red, tmp);
+        solve_column<CtaGroup>(a, a.cols_cta[c], m, tmp);
     }
 }
 
