@@ -200,8 +200,8 @@ sinv_status sinv_lowrank_correct(sinv_handle h, int k, const double *V, const do
  *   host-only handle it builds the plan and the pattern only.  A new analysis
  *   replaces the previous one.
  *   warp_entries: the most entries of A a column may stage to be solved by a warp
- *   (0 = the default and maximum, 1024; a column also needs |J_j| <= 128); smaller
- *   values move columns to the CTA tier.
+ *   (0 = the default and maximum, 704; a column also needs |J_j| <= 128 and at
+ *   most 256 distinct rows of A); smaller values move columns to the CTA tier.
  *   Errors: SINV_ERR_INVALID_ARG (power < 0, warp_entries < 0), SINV_ERR_PATTERN
  *   (range, order of rowptr, duplicates, asymmetry), SINV_ERR_UNSUPPORTED
  *   (power > 8, nnzA or |P_lo| >= 2^31, a column staging >= 2^30 entries),
@@ -212,7 +212,8 @@ sinv_status sinv_lowrank_correct(sinv_handle h, int k, const double *V, const do
  *   symmetric: row k is read as column k), X_S [|S_lo|] and Y_P [|P_lo|]
  *   (device, must not overlap; X symmetric by construction, given by its lower
  *   part).  Stream ordered, no allocation, no synchronisation, graph-capturable.
- *   Y is not bit-reproducible (shared-memory atomics in A_J^T A_J p).
+ *   Y is not bit-reproducible (the order of the entries inside a row of the
+ *   products comes from a counting sort with atomics).
  *   Errors: SINV_ERR_INVALID_ARG (no analysis on the device, iters < 0,
  *   X_S == Y_P). */
 sinv_status sinv_spai_analyse(sinv_handle h, int64_t nnzA, const int64_t *A_rowptr, const int32_t *A_col,

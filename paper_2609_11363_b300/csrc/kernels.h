@@ -134,7 +134,7 @@ cudaError_t lowrank_noalloc_launch(int64_t n, const int64_t* Srp, const int32_t*
 
 // ---- SPAI refinement (spai.cu) ----
 constexpr int kSpaiWarpJ = 128;   // tier W: rows of the column
-constexpr int kSpaiWarpE = 1024;  // tier W: staged entries of A
+constexpr int kSpaiWarpE = 704;   // tier W: staged entries of A (4 warps' columns fit twice per SM)
 constexpr int kSpaiWarpH = 512;   // tier W: table slots (a tier-W column has at most kSpaiWarpH/2 rows of A)
 struct SpaiArgs {
     const int64_t* fcp;   // columns of P (both triangles)

@@ -9,7 +9,7 @@
 // a CTA's shared memory or a per-CTA global scratch block (a CTA per column).
 // The normal matrix B = A_J^T A_J is never formed: B v = A_J^T (A_J v) goes
 // through a table y over the rows R = union of struct(A_k), k in J, in two
-// gather passes with no atomics:
+// passes with no floating-point atomics:
 //   y_c = sum over the entries (k, r_c) of the rows k in J of  A_{r_c k} v_k,
 //   q_k = sum over the entries (k, r) of row k of  A_rk y_{c(r)}.
 // The entries (A_rk, k, c(r)) are staged once per column: a hash insert of r,
@@ -32,7 +32,8 @@ struct WarpLayout {
     static constexpr int kJ = kSpaiWarpJ;  // pattern rows of the column
     static constexpr int kH = kSpaiWarpH;  // table slots (>= 2 R for tier-W columns)
     static constexpr size_t kEa = 0;                                        // double[kE]
-    static constexpr size_t kY = kEa + sizeof(double) * kE;                 // double[kH]: y, or keys + ids
+    static constexpr size_t kPart = kEa + sizeof(double) * kE;              // double[kE] partial sums
+    static constexpr size_t kY = kPart + sizeof(double) * kE;               // double[kH]: y, or keys + ids
     static constexpr size_t kVec = kY + sizeof(double) * kH;                // x r p q dinv: double[5 kJ]
     static constexpr size_t kScal = kVec + sizeof(double) * 5 * kJ;         // double[2]
     static constexpr size_t kSoff = kScal + sizeof(double) * 2;             // int32[kH + 1]
@@ -105,6 +106,7 @@ struct CtaGroup {
 template <class I>
 struct ColumnMem {
     double* ea;      // staged A values, in row-run order
+    double* part;    // partial sums of the products, at the last entry of each piece
     double* y;       // row table; while staging, int32 keys[h] then int32 ids[h]
     double* x;
     double* r;
@@ -123,9 +125,12 @@ struct ColumnMem {
 // One thread's contiguous share [lo, hi) of the staged entries, with the table id and
 // the pattern row its first entry belongs to.  Every product walks the same shares, so
 // each thread does the same number of multiply-adds (a warp's FP64 instruction costs
-// the pipe the same however many of its lanes are active).
+// the pipe the same however many of its lanes are active).  A share ends a piece at
+// every segment end and at its own end; the piece sums are stored, not added with
+// atomics, and one thread per segment adds its pieces up in a fixed order.
 struct Share {
     int lo, hi, c, t;
+    int chunk;  // odd, so that the lanes' shares start in different shared-memory banks
 };
 
 __device__ __forceinline__ uint32_t slot_hash(int32_t r, int shift) {
@@ -162,42 +167,54 @@ __device__ int group_scan(int32_t* a, int L, int* tmp) {
     return total;
 }
 
+// the sum of the pieces of the segment [beg, e): the piece at e - 1, plus one at
+// every share end strictly inside (share ends sit at k * chunk - 1)
+__device__ __forceinline__ double piece_sum(const double* part, int beg, int e, int chunk) {
+    double v = part[e - 1];
+    for (int p = (beg + chunk) / chunk * chunk - 1; p < e - 1; p += chunk) v += part[p];
+    return v;
+}
+
 // q = B v = A_J^T (A_J v) over the staged entries: each thread sums its share in
-// table-id order into y, then in row order into q, adding a partial sum at every
-// segment end (shared-memory atomics, a few per thread)
+// table-id order (pieces -> y), then in row order (pieces -> q)
 template <class G, class I>
 __device__ void apply_normal(const ColumnMem<I>& m, int nj, int R, const Share& sh, const double* v, double* q) {
     const int tid = G::rank(), gsz = G::size();
-    for (int c = tid; c < R; c += gsz) m.y[c] = 0.0;
-    for (int t = tid; t < nj; t += gsz) q[t] = 0.0;
-    G::sync();
     if (sh.lo < sh.hi) {
         int c = sh.c, end = m.soff[c];
         double s = 0.0;
         for (int o2 = sh.lo; o2 < sh.hi; ++o2) {
-            if (o2 == end) {  // every id owns at least one entry
-                atomicAdd(m.y + c, s);
-                s = 0.0;
-                end = m.soff[++c];
-            }
             const int o = m.perm[o2];
             s = fma(m.ea[o], v[m.et[o]], s);
+            if (o2 + 1 == end || o2 + 1 == sh.hi) {
+                m.part[o2] = s;
+                s = 0.0;
+                if (o2 + 1 == end && o2 + 1 < sh.hi) end = m.soff[++c];  // every id owns an entry
+            }
         }
-        atomicAdd(m.y + c, s);
     }
+    G::sync();
+    for (int c = tid; c < R; c += gsz) m.y[c] = piece_sum(m.part, c ? m.soff[c - 1] : 0, m.soff[c], sh.chunk);
     G::sync();
     if (sh.lo < sh.hi) {
         int t = sh.t, end = m.eoff[t + 1];
         double s = 0.0;
         for (int o = sh.lo; o < sh.hi; ++o) {
-            while (o == end) {  // rows of A without entries end where they start
-                atomicAdd(q + t, s);
-                s = 0.0;
-                end = m.eoff[++t + 1];
-            }
             s = fma(m.ea[o], m.y[m.es[o]], s);
+            if (o + 1 == end || o + 1 == sh.hi) {
+                m.part[o] = s;
+                s = 0.0;
+                if (o + 1 == end && o + 1 < sh.hi) {
+                    do end = m.eoff[++t + 1];  // rows of A without entries end where they start
+                    while (end == o + 1);
+                }
+            }
         }
-        atomicAdd(q + t, s);
+    }
+    G::sync();
+    for (int t = tid; t < nj; t += gsz) {
+        const int beg = m.eoff[t], e = m.eoff[t + 1];
+        q[t] = beg == e ? 0.0 : piece_sum(m.part, beg, e, sh.chunk);
     }
     G::sync();
 }
@@ -215,7 +232,11 @@ __device__ void solve_column(const SpaiArgs& a, int j, const ColumnMem<I>& m, in
     const int shift = 32 - (31 - __clz(h));
     int32_t* keys = reinterpret_cast<int32_t*>(m.y);
     int32_t* ids = keys + h;
+    // while staging, p holds per pattern row t: (k, start of row k in A) (nnz(A) < 2^31)
+    int2* rowk = reinterpret_cast<int2*>(m.p);
     for (int t = tid; t < nj; t += gsz) {
+        const int k = a.fri[c0 + t];
+        rowk[t] = make_int2(k, (int)a.Arp[k]);
         m.eoff[t] = a.feo[c0 + t];
         const int32_t src = a.fsrc[c0 + t];
         m.x[t] = src >= 0 ? a.X[src] : 0.0;  // start: X on S, zero on the rest of P
@@ -227,8 +248,7 @@ __device__ void solve_column(const SpaiArgs& a, int j, const ColumnMem<I>& m, in
     // stage the entries of rows k in J: value, run t and the table slot of the column index r
     for (int o = tid; o < E; o += gsz) {
         const int t = run_of(m.eoff, nj, o);
-        const int k = a.fri[c0 + t];
-        const int64_t e = a.Arp[k] + (o - m.eoff[t]);
+        const int64_t e = (int64_t)rowk[t].y + (o - m.eoff[t]);
         const int32_t rr = a.Acol[e];
         const double av = a.Aval[e];
         uint32_t s = slot_hash(rr, shift);
@@ -268,7 +288,8 @@ __device__ void solve_column(const SpaiArgs& a, int j, const ColumnMem<I>& m, in
     // this thread's share of the entries, with the id and row of its first entry
     Share sh;
     {
-        const int chunk = (E + gsz - 1) / gsz;
+        const int chunk = ((E + gsz - 1) / gsz) | 1;
+        sh.chunk = chunk;
         sh.lo = min(E, tid * chunk);
         sh.hi = min(E, sh.lo + chunk);
         sh.t = sh.lo < sh.hi ? run_of(m.eoff, nj, sh.lo) : 0;
@@ -347,6 +368,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) spai_warp_kernel(SpaiArgs a
     unsigned char* base = smem + (size_t)(threadIdx.x >> 5) * L::kBytes;
     ColumnMem<uint16_t> m;
     m.ea = reinterpret_cast<double*>(base + L::kEa);
+    m.part = reinterpret_cast<double*>(base + L::kPart);
     m.y = reinterpret_cast<double*>(base + L::kY);
     double* vec = reinterpret_cast<double*>(base + L::kVec);
     m.x = vec;
@@ -381,7 +403,8 @@ __global__ void __launch_bounds__(kCtaThreads) spai_cta_kernel(SpaiArgs a) {
                                 : reinterpret_cast<unsigned char*>(a.scratch) + (size_t)blockIdx.x * (size_t)a.cta_bytes;
     ColumnMem<int32_t> m;
     m.ea = reinterpret_cast<double*>(base);
-    m.y = m.ea + cE;
+    m.part = m.ea + cE;
+    m.y = m.part + cE;
     m.x = m.y + cH;
     m.r = m.x + cj;
     m.p = m.r + cj;
@@ -404,7 +427,7 @@ __global__ void __launch_bounds__(kCtaThreads) spai_cta_kernel(SpaiArgs a) {
 }  // namespace
 
 size_t spai_cta_bytes(int64_t cap_nj, int64_t cap_E, int64_t cap_H) {
-    size_t b = sizeof(double) * (size_t)(cap_E + cap_H + 5 * cap_nj) +
+    size_t b = sizeof(double) * (size_t)(2 * cap_E + cap_H + 5 * cap_nj) +
                sizeof(int32_t) * (size_t)((cap_H + 1) + 3 * cap_E + (cap_nj + 1));
     return (b + 255) / 256 * 256;
 }
