@@ -58,6 +58,9 @@ def parse():
     p.add_argument("--cov-size", type=int, default=200)
     p.add_argument("--spai-iters", type=int, default=20,
                    help="covariance: PCG steps of the SPAI refinement of Mix (Mix-SPAI); 0 = leave it out")
+    p.add_argument("--einv-k", type=int, default=3,
+                   help="covariance: eigenpairs of the spectral check (Lanczos on A^{-1} - Mix); 0 = skip it")
+    p.add_argument("--einv-steps", type=int, default=30, help="covariance: Lanczos steps of the spectral check")
     p.add_argument("--spai-power", type=int, default=2,
                    help="covariance: SPAI pattern P = S + pairs within this graph distance in A")
     p.add_argument("--exact-diag-max-n", type=int, default=10000,
@@ -796,6 +799,24 @@ def run_covariance(args, rank, world, dev):
     ms_ninv = timed(lambda: h.ninv(Lv, Dv, w.m, "fp64", out=N, delta=args.ninv_delta), args.steps)
     ms_spai = timed(lambda: h.spai(Av, M, it, out=Y), args.steps) if it > 0 else 0.0
     h.sync_status()
+    spectral = None
+    if args.einv_k > 0:
+        # the spectral check of the paper's covariance runs: k requested eigenpairs of
+        # E_inv = A^{-1} - Mix, Lanczos with ILDL-preconditioned CG (timed once, synchronous)
+        t0 = time.time()
+        Ae = h.einv_analyse(w.A)
+        t_an = time.time() - t0
+        q0 = torch.as_tensor(np.random.default_rng(0).standard_normal(f.n), device=dev)
+        Aev = torch.as_tensor(Ae.data, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        lam, _, info = h.einv_lanczos(Aev, Lv, Dv, M, q0, args.einv_k, args.einv_steps, cg_tol=1e-10, cg_maxit=500)
+        t_lz = time.time() - t0
+        stE = h.stats()
+        spectral = {"k": args.einv_k, "lanczos_steps": info["steps"], "cg_iterations": info["cg_iterations"],
+                    "cg_unconverged": info["cg_unconverged"], "seconds": t_lz, "analyse_s": t_an,
+                    "ritz_values": [float(x) for x in lam], "solve_levels": [stE["einv_levels_fwd"],
+                                                                             stE["einv_levels_bwd"]]}
     st = h.stats()
     nS = 2 * h.nnz_S - h.n
     gn = float(torch.linalg.vector_norm(G))
@@ -819,7 +840,7 @@ def run_covariance(args, rank, world, dev):
     line = {"metric": METRIC, "value": world * nS / (ms / 1e3), "unit": "entries/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "rel_error_on_S_lo": err,
+            "rel_error_on_S_lo": err, "spectral_check": spectral,
             "config": {"workload": "covariance: (1 - d/3)^4 on a %d x %d grid (n=%d), ILDL tau=1e-3, SelInv + NInv m=%d "
                                    "+ Mix%s, FP64" % (args.cov_size, args.cov_size, f.n, w.m,
                                                       " + SPAI (%d PCG steps on S + distance-%d neighbourhoods of A)"

@@ -222,6 +222,37 @@ sinv_status sinv_spai_pattern(sinv_handle h, int64_t *P_rowptr, int32_t *P_col);
 sinv_status sinv_spai(sinv_handle h, const double *A_val, const double *X_S, int iters, double *Y_P,
                       void *stream);
 
+/* Spectral-correction producer (Section 2.5, Algorithm 1 step 5): the k
+ * dominant eigenpairs (largest |lambda|) of E_inv = A^{-1} - A^inv by Lanczos
+ * with full reorthogonalisation (classical Gram-Schmidt, twice) from the start
+ * vector q0.  Each step applies E_inv: A^{-1} q by conjugate gradients from 0,
+ * preconditioned with the ILDL factors (z = L^{-T} D^{-1} L^{-1} r), stopped
+ * at ||r|| <= cg_tol ||q|| or after cg_maxit iterations; A^inv q is X applied
+ * as the symmetric matrix given by its lower part on S.  Lanczos stops early
+ * when beta < 1e-14 max(1, |alpha|).  The Ritz pairs come from the tridiagonal
+ * matrix by cyclic Jacobi.  FP64 throughout.  A must be symmetric positive
+ * definite for the CG solves (indefinite A: a CG breakdown ends that solve
+ * early and counts in info[2]).
+ *
+ * sinv_einv_analyse: the pattern of A, HOST arrays (the same rules as
+ *   sinv_spai_analyse).  Builds the columns of S and the dependency levels of
+ *   the two triangular solves, uploads them, synchronises the device (on a
+ *   host-only handle: the plan only).
+ *   Errors: SINV_ERR_PATTERN, SINV_ERR_UNSUPPORTED (nnzA >= 2^31), SINV_ERR_OOM.
+ * sinv_einv_lanczos: A_val[nnzA], L_val, D_val (as for sinv_selinv), X_S
+ *   [|S_lo|], q0 [n]: device.  lambda [k]: HOST, the Ritz values, largest |.|
+ *   first; V [n*k] row-major: device, the Ritz vectors (unit norm).  info [3]:
+ *   HOST, (Lanczos steps taken m, total CG iterations, solves that stopped
+ *   before cg_tol).  If m < k, the last k - m values and columns are 0.
+ *   Synchronous on `stream` (every step reads its scalars on the host).
+ *   1 <= k <= steps <= min(n, 256), cg_tol > 0, cg_maxit >= 1.
+ *   Errors: SINV_ERR_INVALID_ARG (no analysis, bad sizes, q0 zero or not
+ *   finite), SINV_ERR_UNSUPPORTED (steps > 256), SINV_ERR_OOM. */
+sinv_status sinv_einv_analyse(sinv_handle h, int64_t nnzA, const int64_t *A_rowptr, const int32_t *A_col);
+sinv_status sinv_einv_lanczos(sinv_handle h, const double *A_val, const double *L_val, const double *D_val,
+                              const double *X_S, const double *q0, int steps, double cg_tol, int cg_maxit, int k,
+                              double *lambda, double *V, int32_t *info, void *stream);
+
 /* The FP32 form of sinv_lowrank_correct for callers that cannot allocate device
  * memory -- for instance code that gets all of its device memory from an
  * arena it owns, or that must not call cudaMalloc because it may synchronise
@@ -301,6 +332,9 @@ typedef struct {
     int64_t spai_cols_warp;   /* columns solved by a warp in shared memory             */
     int64_t spai_cols_cta;    /* columns solved by a CTA with a global scratch block   */
     int64_t spai_nnz_P;       /* |P_lo| of the SPAI pattern, 0 until analysed          */
+    int64_t einv_levels_fwd;  /* dependency levels of the solve with L (one launch each),
+                                 0 until sinv_einv_analyse ran                          */
+    int64_t einv_levels_bwd;  /* dependency levels of the solve with L^T                */
 } sinv_stats;
 sinv_status sinv_get_stats(sinv_handle h, sinv_stats *out);
 

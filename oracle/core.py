@@ -268,7 +268,7 @@ def sym_from_S(n, Srp, Sc, X_S):
     return (low + strict.T).tocsr()
 
 
-def lanczos_einv(A, Ainv_sym, k, steps=None, seed=0, solve=None):
+def lanczos_einv(A, Ainv_sym, k, steps=None, seed=0, solve=None, q0=None):
     """k dominant (largest |lambda|) eigenpairs of E_inv = A^{-1} - A^inv.
 
     Matrix-free as in Section 2.5: E_inv x = A^{-1} x - A^inv x.  The first term
@@ -281,10 +281,10 @@ def lanczos_einv(A, Ainv_sym, k, steps=None, seed=0, solve=None):
         lu = spla.splu(sp.csc_matrix(A))
         solve = lu.solve
     steps = min(n, steps or max(4 * k + 20, 60))
-    rng = np.random.default_rng(seed)
     Q = np.zeros((n, steps + 1))
     alpha = np.zeros(steps); beta = np.zeros(steps)
-    q = rng.standard_normal(n); q /= np.linalg.norm(q)
+    q = np.random.default_rng(seed).standard_normal(n) if q0 is None else np.array(q0, dtype=np.float64)
+    q /= np.linalg.norm(q)
     Q[:, 0] = q
     m = steps
     for it in range(steps):

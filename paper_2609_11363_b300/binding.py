@@ -29,7 +29,7 @@ EXPORTS = [
     "sinv_status_string", "sinv_last_error", "sinv_destroy", "sinv_debug_wait_timeout",
     "sinv_trace_enable", "sinv_trace_read", "sinv_lowrank_correct_noalloc",
     "sinv_batch_symbolic", "sinv_batch_layout", "sinv_ninv_stack", "sinv_ninv_drop",
-    "sinv_spai_analyse", "sinv_spai_pattern", "sinv_spai",
+    "sinv_spai_analyse", "sinv_spai_pattern", "sinv_spai", "sinv_einv_analyse", "sinv_einv_lanczos",
     "sinv_mlp_param_count", "sinv_mlp_create", "sinv_mlp_destroy", "sinv_mlp_get_params", "sinv_mlp_set_params",
     "sinv_mlp_features", "sinv_mlp_targets", "sinv_mlp_grad", "sinv_mlp_train_step", "sinv_mlp_predict",
 ]
@@ -57,7 +57,8 @@ class _Stats(ctypes.Structure):
         ("ninv_m", ctypes.c_int32), ("pad", ctypes.c_int32), ("horner_products", ctypes.c_int64),
         ("product_stream", ctypes.c_int64), ("selinv_flops", ctypes.c_int64), ("selinv_bytes", ctypes.c_int64),
         ("ninv_index_bytes", ctypes.c_int64), ("product_hits", ctypes.c_int64), ("spai_entries", ctypes.c_int64),
-        ("spai_cols_warp", ctypes.c_int64), ("spai_cols_cta", ctypes.c_int64), ("spai_nnz_P", ctypes.c_int64)]
+        ("spai_cols_warp", ctypes.c_int64), ("spai_cols_cta", ctypes.c_int64), ("spai_nnz_P", ctypes.c_int64),
+        ("einv_levels_fwd", ctypes.c_int64), ("einv_levels_bwd", ctypes.c_int64)]
 
 
 def lib_path() -> str:
@@ -83,6 +84,8 @@ def load_library():
     lib.sinv_mix.argtypes = [H, P, P, D, P, P]
     lib.sinv_spai_analyse.argtypes = [H, I64, P, P, ctypes.c_int, ctypes.c_int]
     lib.sinv_spai_pattern.argtypes = [H, P, P]
+    lib.sinv_einv_analyse.argtypes = [H, I64, P, P]
+    lib.sinv_einv_lanczos.argtypes = [H, P, P, P, P, P, ctypes.c_int, D, ctypes.c_int, ctypes.c_int, P, P, P, P]
     lib.sinv_spai.argtypes = [H, P, P, ctypes.c_int, P, P]
     lib.sinv_lowrank_correct.argtypes = [H, ctypes.c_int, P, P, ctypes.c_int, P, P]
     lib.sinv_sync_status.argtypes = [H, P]
@@ -431,6 +434,32 @@ class Handle:
                                         _check_tensor(X, "X_S", self.nnz_S), int(iters),
                                         _check_tensor(out, "Y_P", nP), _stream_ptr(stream)))
         return out
+
+    def einv_analyse(self, A):
+        """Analyse the pattern of the symmetric matrix A (scipy sparse) for einv_lanczos();
+        returns the CSR A whose value order einv_lanczos() takes."""
+        import scipy.sparse as sp
+        A = sp.csr_matrix(A)
+        A.sum_duplicates()
+        rp = np.ascontiguousarray(A.indptr, dtype=np.int64)
+        col = np.ascontiguousarray(A.indices, dtype=np.int32)
+        self._check(self._lib.sinv_einv_analyse(self._h, int(A.nnz), _np_ptr(rp), _np_ptr(col)))
+        self._einv_nnzA = int(A.nnz)
+        return sp.csr_matrix((A.data, col, rp), shape=A.shape)
+
+    def einv_lanczos(self, A_val, L_val, D_val, X, q0, k, steps, cg_tol=1e-12, cg_maxit=1000, stream=None):
+        """k dominant eigenpairs of E_inv = A^{-1} - A^inv (A^inv = X on S): returns
+        (lambda numpy[k], V tensor [n, k], info dict)."""
+        lam = np.zeros(int(k), dtype=np.float64)
+        info = np.zeros(3, dtype=np.int32)
+        V = torch.empty((self.n, int(k)), dtype=torch.float64, device=self.device)
+        self._check(self._lib.sinv_einv_lanczos(
+            self._h, _check_tensor(A_val, "A_val", getattr(self, "_einv_nnzA", None)),
+            _check_tensor(L_val, "L_val", self.nnz_L), _check_tensor(D_val, "D_val", self.nD),
+            _check_tensor(X, "X_S", self.nnz_S), _check_tensor(q0, "q0", self.n), int(steps), float(cg_tol),
+            int(cg_maxit), int(k), _np_ptr(lam), _check_tensor(V, "V", self.n * int(k)), _np_ptr(info),
+            _stream_ptr(stream)))
+        return lam, V, {"steps": int(info[0]), "cg_iterations": int(info[1]), "cg_unconverged": int(info[2])}
 
     def lowrank_correct(self, V, lam, X, prec="fp64", stream=None):
         k = int(lam.numel())

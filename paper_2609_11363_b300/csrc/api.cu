@@ -2,6 +2,8 @@
 // symbolic analysis upload and the numeric entry points.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -150,6 +152,15 @@ struct sinv_handle_s {
     int32_t *dAcol = nullptr, *dscols_w = nullptr, *dscols_c = nullptr, *dsticket = nullptr;
     double* dsscratch = nullptr;
     int64_t spai_cta_bytes = 0;
+    // spectral-correction producer: analysis of the current pattern of A
+    EinvPlan E;
+    bool einv_analysed = false;  // E holds a plan
+    bool einv_ready = false;     // ... and it is on the device
+    int64_t *deArp = nullptr, *deLrp = nullptr, *defcp = nullptr;
+    int32_t *deAcol = nullptr, *deLcol = nullptr, *defri = nullptr, *defpos = nullptr, *defwd = nullptr,
+            *debwd = nullptr;
+    void* dework = nullptr;
+    size_t ework_bytes = 0;
     std::string last_error;
 };
 
@@ -188,6 +199,20 @@ void spai_free(sinv_handle h) {
     h->Q = SpaiPlan();
 }
 
+void einv_free(sinv_handle h) {
+    void* ptrs[] = {h->deArp, h->deLrp, h->defcp, h->deAcol, h->deLcol, h->defri, h->defpos, h->defwd, h->debwd,
+                    h->dework};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    h->deArp = h->deLrp = h->defcp = nullptr;
+    h->deAcol = h->deLcol = h->defri = h->defpos = h->defwd = h->debwd = nullptr;
+    h->dework = nullptr;
+    h->ework_bytes = 0;
+    h->einv_ready = false;
+    h->einv_analysed = false;
+    h->E = EinvPlan();
+}
+
 void free_all(sinv_handle h) {
     void* ptrs[] = {h->dSrp, h->dSc, h->dSdiag, h->dl2s, h->dLrp, h->dLcp, h->dLri, h->dLcsr, h->ddpos, h->dpstart,
                     h->dsn, h->dorder, h->downer, h->dCrow, h->dLmap, h->dJJl, h->dJJs, h->dhit_ik, h->dhit_pos,
@@ -197,6 +222,7 @@ void free_all(sinv_handle h) {
         if (p) cudaFree(p);
     ninv_maps_free(h->X);
     spai_free(h);
+    einv_free(h);
 }
 
 sinv_status ensure_work(sinv_handle h, size_t bytes) {
@@ -475,6 +501,8 @@ sinv_status sinv_get_stats(sinv_handle h, sinv_stats* s) {
     s->spai_cols_warp = h->spai_analysed ? (int64_t)h->Q.cols_w.size() : 0;
     s->spai_cols_cta = h->spai_analysed ? (int64_t)h->Q.cols_c.size() : 0;
     s->spai_nnz_P = h->spai_analysed ? h->Q.nnzP : 0;
+    s->einv_levels_fwd = h->einv_analysed && !h->E.fwd_ptr.empty() ? (int64_t)h->E.fwd_ptr.size() - 1 : 0;
+    s->einv_levels_bwd = h->einv_analysed && !h->E.bwd_ptr.empty() ? (int64_t)h->E.bwd_ptr.size() - 1 : 0;
     return SINV_OK;
 }
 
@@ -830,6 +858,231 @@ sinv_status sinv_spai(sinv_handle h, const double* A_val, const double* X_S, int
     a.status = h->dstatus;
     TraceScope trace_scope(h->tracer);
     if ((e = spai_launch(a, h->num_sms, (cudaStream_t)stream)) != cudaSuccess) return cuda_fail(h, e, "spai launch");
+    return SINV_OK;
+}
+
+sinv_status sinv_einv_analyse(sinv_handle h, int64_t nnzA, const int64_t* A_rowptr, const int32_t* A_col) {
+    if (!h || nnzA < 0 || !A_rowptr || (nnzA > 0 && !A_col)) return SINV_ERR_INVALID_ARG;
+    cudaError_t e = cudaSuccess;
+    if (h->device >= 0) {
+        if ((e = cudaSetDevice(h->device)) != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+        if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(h, e, "synchronize");
+    }
+    einv_free(h);
+    std::string err;
+    try {
+        err = build_einv_plan(h->P, nnzA, A_rowptr, A_col, h->E);
+    } catch (const std::bad_alloc&) {
+        h->E = EinvPlan();
+        set_err(h, "host allocation failed in the Lanczos analysis");
+        return SINV_ERR_OOM;
+    }
+    if (!err.empty()) {
+        h->E = EinvPlan();
+        set_err(h, err);
+        return err.find("not supported") != std::string::npos ? SINV_ERR_UNSUPPORTED : SINV_ERR_PATTERN;
+    }
+    h->einv_analysed = true;
+    if (h->device < 0) return SINV_OK;  // host-only handle: the plan only
+    const EinvPlan& E = h->E;
+    std::vector<int64_t> Arp(A_rowptr, A_rowptr + h->P.n + 1);
+    std::vector<int32_t> Acol(A_col, A_col + nnzA);
+    std::vector<int64_t> Lrp(h->P.n + 1, 0);
+    for (int64_t q = 0; q < h->P.nnzL; ++q) Lrp[h->P.Lri[q] + 1] += 1;
+    for (int64_t i = 0; i < h->P.n; ++i) Lrp[i + 1] += Lrp[i];
+#define UPE(dst, src)                                            \
+    do {                                                         \
+        if ((e = upload(&h->dst, src)) != cudaSuccess) {         \
+            einv_free(h);                                        \
+            return cuda_fail(h, e, "upload " #dst);              \
+        }                                                        \
+    } while (0)
+    UPE(deArp, Arp);
+    UPE(deAcol, Acol);
+    UPE(deLrp, Lrp);
+    UPE(deLcol, E.Lcol);
+    UPE(defcp, E.fcp);
+    UPE(defri, E.fri);
+    UPE(defpos, E.fpos);
+    UPE(defwd, E.fwd_rows);
+    UPE(debwd, E.bwd_cols);
+#undef UPE
+    h->einv_ready = true;
+    return SINV_OK;
+}
+
+sinv_status sinv_einv_lanczos(sinv_handle h, const double* A_val, const double* L_val, const double* D_val,
+                              const double* X_S, const double* q0, int steps, double cg_tol, int cg_maxit, int k,
+                              double* lambda, double* V, int32_t* info, void* stream) {
+    if (!h) return SINV_ERR_INVALID_ARG;
+    if (!on_device(h)) return SINV_ERR_INVALID_ARG;
+    if (!h->einv_ready) {
+        set_err(h, "sinv_einv_lanczos needs sinv_einv_analyse first");
+        return SINV_ERR_INVALID_ARG;
+    }
+    const int64_t n = h->P.n;
+    if (k < 1 || steps < k || steps > n || !(cg_tol > 0.0) || cg_maxit < 1 || !lambda || !V || !info || !q0 ||
+        !X_S || !D_val || (!A_val && h->E.nnzA > 0) || (!L_val && h->P.nnzL > 0)) {
+        set_err(h, "invalid argument: need 1 <= k <= steps <= n, cg_tol > 0, cg_maxit >= 1 and all buffers");
+        return SINV_ERR_INVALID_ARG;
+    }
+    if (steps > kEinvMaxSteps) {
+        set_err(h, "steps > 256 is not supported");
+        return SINV_ERR_UNSUPPORTED;
+    }
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    TraceScope trace_scope(h->tracer);
+    const int nb = einv_dot_blocks(h->num_sms);
+    // workspace: 8 vectors, Q, D^{-1} rows, partial sums, scalars, T, U, sel, lam
+    const size_t nv = (size_t)n, sq = (size_t)steps * steps;
+    const size_t doubles = 8 * nv + (size_t)(steps + 1) * nv + 2 * nv + nb + 8 + (steps + 1) + 2 * sq + k;
+    const size_t bytes = doubles * sizeof(double) + (nv + k + 8) * sizeof(int32_t) + 256;
+    if (bytes > h->ework_bytes) {
+        if (h->dework) cudaFree(h->dework);
+        h->dework = nullptr;
+        h->ework_bytes = 0;
+        if ((e = cudaMalloc(&h->dework, bytes)) != cudaSuccess) return cuda_fail(h, e, "Lanczos workspace");
+        h->ework_bytes = bytes;
+    }
+    double* base = reinterpret_cast<double*>(h->dework);
+    double *x = base, *r = x + nv, *z = r + nv, *p = z + nv, *qv = p + nv, *y = qv + nv, *w = y + nv, *v = w + nv;
+    double* Q = v + nv;
+    double* dr = Q + (size_t)(steps + 1) * nv;
+    double* dp = dr + nv;
+    double* partial = dp + nv;
+    double* scal = partial + nb;
+    double* cvec = scal + 8;
+    double* T = cvec + (steps + 1);
+    double* U = T + sq;
+    double* lamd = U + sq;
+    int32_t* part = reinterpret_cast<int32_t*>(lamd + k);
+    int32_t* sel = part + nv;
+
+    const EinvPlan& E = h->E;
+    EinvArgs a;
+    a.n = n;
+    a.num_sms = h->num_sms;
+    a.Arp = h->deArp;
+    a.Acol = h->deAcol;
+    a.Aval = A_val;
+    a.fcp = h->defcp;
+    a.fri = h->defri;
+    a.fpos = h->defpos;
+    a.X = X_S;
+    a.Lrp = h->deLrp;
+    a.Lcol = h->deLcol;
+    a.Lcp = h->dLcp;
+    a.Lri = h->dLri;
+    a.Lcsr = h->dLcsr;
+    a.Lval = L_val;
+    a.dr = dr;
+    a.dp = dp;
+    a.part = part;
+    a.fwd_rows = h->defwd;
+    a.fwd_ptr_h = E.fwd_ptr.data();
+    a.nlev_fwd = E.fwd_ptr.empty() ? 0 : (int)E.fwd_ptr.size() - 1;
+    a.bwd_cols = h->debwd;
+    a.bwd_ptr_h = E.bwd_ptr.data();
+    a.nlev_bwd = E.bwd_ptr.empty() ? 0 : (int)E.bwd_ptr.size() - 1;
+
+    NinvArgs na{};
+    na.n = n;
+    na.dpos = h->ddpos;
+    na.pstart = h->dpstart;
+    na.Dval = D_val;
+    na.num_sms = h->num_sms;
+    na.status = h->dstatus;
+    ninv_dinv_launch(na, dr, dp, part, st);
+
+    bool fail = false;
+    auto chk = [&](cudaError_t err) {
+        if (err != cudaSuccess && !fail) {
+            fail = true;
+            e = err;
+        }
+    };
+    auto dot = [&](const double* u1, const double* u2) -> double {
+        double hv = 0.0;
+        chk(einv_dot(a, u1, u2, partial, scal, st));
+        chk(cudaMemcpyAsync(&hv, scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+        chk(cudaStreamSynchronize(st));
+        return hv;
+    };
+    // q_0 = q0 / ||q0||
+    const double n0 = std::sqrt(dot(q0, q0));
+    if (fail) return cuda_fail(h, e, "Lanczos start");
+    if (!(n0 > 0.0) || !std::isfinite(n0)) {
+        set_err(h, "the start vector q0 must be finite and nonzero");
+        return SINV_ERR_INVALID_ARG;
+    }
+    chk(einv_axpby(a, 1.0 / n0, q0, 0.0, q0, Q, st));
+    std::vector<double> alph(steps, 0.0), beta(steps, 0.0);
+    int m = steps;
+    int64_t cg_total = 0;
+    int cg_unconverged = 0;
+    for (int it = 0; it < steps && !fail; ++it) {
+        const double* qi = Q + (size_t)it * nv;
+        // x = A^{-1} q_i by CG preconditioned with L^{-T} D^{-1} L^{-1}, from x = 0
+        chk(cudaMemsetAsync(x, 0, nv * sizeof(double), st));
+        chk(einv_axpby(a, 1.0, qi, 0.0, qi, r, st));
+        const double bn = std::sqrt(dot(r, r));
+        chk(einv_precond(a, r, y, w, z, st));
+        chk(einv_axpby(a, 1.0, z, 0.0, z, p, st));
+        double rz = dot(r, z);
+        bool conv = false;
+        for (int ci = 0; ci < cg_maxit && !fail; ++ci) {
+            chk(einv_spmv_A(a, p, qv, st));
+            const double pq = dot(p, qv);
+            if (!(pq > 0.0)) break;
+            const double al = rz / pq;
+            chk(einv_cg_xr(a, al, p, qv, x, r, st));
+            ++cg_total;
+            if (std::sqrt(dot(r, r)) <= cg_tol * bn) {
+                conv = true;
+                break;
+            }
+            chk(einv_precond(a, r, y, w, z, st));
+            const double rzn = dot(r, z);
+            chk(einv_cg_p(a, rzn / rz, z, p, st));
+            rz = rzn;
+        }
+        if (!conv) ++cg_unconverged;
+        // v = A^{-1} q_i - A^inv q_i, alpha_i = q_i . v, then v orthogonalised twice against q_0..q_i
+        chk(einv_symv_X(a, qi, y, st));
+        chk(einv_axpby(a, 1.0, x, -1.0, y, v, st));
+        alph[it] = dot(qi, v);
+        chk(einv_reorth(a, Q, it + 1, cvec, v, st));
+        chk(einv_reorth(a, Q, it + 1, cvec, v, st));
+        const double b = std::sqrt(dot(v, v));
+        beta[it] = b;
+        if (b < 1e-14 * std::max(1.0, std::fabs(alph[it]))) {
+            m = it + 1;
+            break;
+        }
+        chk(einv_axpby(a, 1.0 / b, v, 0.0, v, Q + (size_t)(it + 1) * nv, st));
+    }
+    if (fail) return cuda_fail(h, e, "Lanczos iteration");
+    // Ritz pairs of the tridiagonal T (m x m): the k of largest |theta|
+    std::vector<double> Th((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i) {
+        Th[(size_t)i * m + i] = alph[i];
+        if (i + 1 < m) Th[(size_t)i * m + i + 1] = Th[(size_t)(i + 1) * m + i] = beta[i];
+    }
+    const int kk = std::min(k, m);
+    chk(cudaMemcpyAsync(T, Th.data(), Th.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    chk(einv_eig(m, T, U, kk, sel, lamd, st));
+    chk(cudaMemsetAsync(V, 0, nv * k * sizeof(double), st));
+    chk(einv_ritz(a, m, kk, k, Q, U, sel, V, st));
+    std::vector<double> lh(kk);
+    chk(cudaMemcpyAsync(lh.data(), lamd, kk * sizeof(double), cudaMemcpyDeviceToHost, st));
+    chk(cudaStreamSynchronize(st));
+    if (fail) return cuda_fail(h, e, "Ritz pairs");
+    for (int l = 0; l < k; ++l) lambda[l] = l < kk ? lh[l] : 0.0;
+    info[0] = m;
+    info[1] = (int32_t)std::min<int64_t>(cg_total, INT32_MAX);
+    info[2] = cg_unconverged;
     return SINV_OK;
 }
 

@@ -168,6 +168,54 @@ constexpr size_t kSpaiCtaSmemMax = 200 * 1024;  // tier C blocks up to this size
 int spai_cta_grid(int num_sms, int64_t ncols_cta, size_t cta_bytes);
 cudaError_t spai_launch(const SpaiArgs& a, int num_sms, cudaStream_t st);
 
+// ---- spectral-correction producer (einv.cu) ----
+struct EinvArgs {
+    int64_t n;
+    int num_sms;
+    const int64_t* Arp;   // A (symmetric), CSR
+    const int32_t* Acol;
+    const double* Aval;
+    const int64_t* fcp;   // columns of S and the S_lo position of each entry
+    const int32_t* fri;
+    const int32_t* fpos;
+    const double* X;      // A^inv on S_lo
+    const int64_t* Lrp;   // L by rows
+    const int32_t* Lcol;
+    const int64_t* Lcp;   // L by columns, with the CSR position of each entry
+    const int32_t* Lri;
+    const int32_t* Lcsr;
+    const double* Lval;
+    const double* dr;     // D^{-1} per row: diagonal, partner coefficient, partner (-1: 1x1)
+    const double* dp;
+    const int32_t* part;
+    const int32_t* fwd_rows;  // rows by level of L y = b (device), level starts on the host
+    const int32_t* fwd_ptr_h;
+    int nlev_fwd;
+    const int32_t* bwd_cols;  // columns by level of L^T x = w
+    const int32_t* bwd_ptr_h;
+    int nlev_bwd;
+};
+constexpr int kEinvMaxSteps = 256;  // Lanczos steps (the tridiagonal eigenproblem runs in one CTA)
+int einv_dot_blocks(int num_sms);
+cudaError_t einv_spmv_A(const EinvArgs& a, const double* x, double* y, cudaStream_t st);
+cudaError_t einv_symv_X(const EinvArgs& a, const double* x, double* y, cudaStream_t st);
+// z = L^{-T} D^{-1} L^{-1} r (y, w: work vectors)
+cudaError_t einv_precond(const EinvArgs& a, const double* r, double* y, double* w, double* z, cudaStream_t st);
+cudaError_t einv_dot(const EinvArgs& a, const double* x, const double* y, double* partial, double* out,
+                     cudaStream_t st);
+cudaError_t einv_cg_xr(const EinvArgs& a, double alpha, const double* p, const double* q, double* x, double* r,
+                       cudaStream_t st);
+cudaError_t einv_cg_p(const EinvArgs& a, double beta, const double* z, double* p, cudaStream_t st);
+cudaError_t einv_axpby(const EinvArgs& a, double alpha, const double* x, double beta, const double* y, double* out,
+                       cudaStream_t st);
+// v -= Q[:, :ncols] (Q[:, :ncols]^T v)   (c: ncols work scalars)
+cudaError_t einv_reorth(const EinvArgs& a, const double* Q, int ncols, double* c, double* v, cudaStream_t st);
+// eigen-decomposition of the m x m symmetric T (overwritten), eigenvectors in U; the k
+// eigenvalues of largest modulus and their columns into lam / sel
+cudaError_t einv_eig(int m, double* T, double* U, int k, int32_t* sel, double* lam, cudaStream_t st);
+cudaError_t einv_ritz(const EinvArgs& a, int m, int k, int ldv, const double* Q, const double* U,
+                      const int32_t* sel, double* V, cudaStream_t st);
+
 cudaError_t debug_wait_launch(uint32_t* flag, int32_t* status, int64_t limit, cudaStream_t st);
 
 // ---- learned correction (mlp.cu) ----

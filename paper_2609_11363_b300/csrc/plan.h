@@ -107,6 +107,21 @@ struct SpaiPlan {
     int64_t entries = 0;          // sum of fE: entries of A streamed by one B product over all columns
 };
 
+// Spectral-correction producer (Section 2.5): what the Lanczos iteration on
+// E_inv = A^{-1} - A^inv needs besides the plan of S.  The columns of S (both
+// triangles) apply A^inv, given on S_lo; the rows of L grouped by dependency
+// level drive the forward solve with L, the columns grouped the same way the
+// solve with L^T (the two triangular factors of the ILDL preconditioner).
+struct EinvPlan {
+    int64_t n = 0, nnzA = 0;
+    std::vector<int64_t> fcp;      // n+1: columns of S
+    std::vector<int32_t> fri;      // rows of each column
+    std::vector<int32_t> fpos;     // S_lo position of each entry
+    std::vector<int32_t> Lcol;     // nnz(L): column of every CSR entry of L
+    std::vector<int32_t> fwd_rows, fwd_ptr;  // rows of level l: fwd_rows[fwd_ptr[l] .. fwd_ptr[l+1])
+    std::vector<int32_t> bwd_cols, bwd_ptr;  // columns of level l of the solve with L^T
+};
+
 // Returns an empty string on success, else the reason the pattern is invalid.
 // big_pairs: supernodes with at least this many pairs are processed by a whole CTA;
 // group: small supernodes per work item (one per warp); levels with fewer than
@@ -119,5 +134,8 @@ std::string build_ninv_plan(const HostPlan& P, int m, NinvPlan& W);
 // tier-W caps on pattern rows, staged entries and distinct rows of A.
 std::string build_spai_plan(const HostPlan& P, int64_t nnzA, const int64_t* A_rowptr, const int32_t* A_col,
                             int power, int warp_j, int warp_e, int warp_r, SpaiPlan& X);
+// A: n x n CSR pattern (host), structurally symmetric (the same checks as above).
+std::string build_einv_plan(const HostPlan& P, int64_t nnzA, const int64_t* A_rowptr, const int32_t* A_col,
+                            EinvPlan& X);
 
 }  // namespace sinv

@@ -512,19 +512,17 @@ std::string build_ninv_plan(const HostPlan& P, int m, NinvPlan& W) {
     return "";
 }
 
-std::string build_spai_plan(const HostPlan& P, int64_t nnzA, const int64_t* Arp, const int32_t* Ac, int power,
-                            int warp_j, int warp_e, int warp_r, SpaiPlan& X) {
-    const int64_t n = P.n;
-    X = SpaiPlan();
-    X.n = n;
-    X.nnzA = nnzA;
-    X.power = power;
+namespace {
+
+// Checks of a symmetric matrix's CSR pattern; `sorted` receives the rows sorted.
+std::string check_symmetric_pattern(int64_t n, int64_t nnzA, const int64_t* Arp, const int32_t* Ac,
+                                    std::vector<int32_t>& sorted) {
     if (Arp[0] != 0 || Arp[n] != nnzA) return "A_rowptr must start at 0 and end at nnzA";
     for (int64_t i = 0; i < n; ++i)
         if (Arp[i + 1] < Arp[i]) return "A_rowptr must be non-decreasing";
     if (nnzA >= ((int64_t)1 << 31)) return "nnzA >= 2^31 is not supported";
     // rows sorted on a copy: range, duplicates and structural symmetry
-    std::vector<int32_t> sorted(Ac, Ac + nnzA);
+    sorted.assign(Ac, Ac + nnzA);
     for (int64_t i = 0; i < n; ++i) {
         int32_t* b = sorted.data() + Arp[i];
         int32_t* e = sorted.data() + Arp[i + 1];
@@ -540,6 +538,21 @@ std::string build_spai_plan(const HostPlan& P, int64_t nnzA, const int64_t* Arp,
             if (!std::binary_search(sorted.begin() + Arp[k], sorted.begin() + Arp[k + 1], (int32_t)i))
                 return "the pattern of A is not symmetric";
         }
+    return "";
+}
+
+}  // namespace
+
+std::string build_spai_plan(const HostPlan& P, int64_t nnzA, const int64_t* Arp, const int32_t* Ac, int power,
+                            int warp_j, int warp_e, int warp_r, SpaiPlan& X) {
+    const int64_t n = P.n;
+    X = SpaiPlan();
+    X.n = n;
+    X.nnzA = nnzA;
+    X.power = power;
+    std::vector<int32_t> sorted;
+    std::string err = check_symmetric_pattern(n, nnzA, Arp, Ac, sorted);
+    if (!err.empty()) return err;
     // P_lo row by row: S_lo row i, and every j <= i within `power` steps of i in the graph of A
     X.Prp.assign(n + 1, 0);
     std::vector<int64_t> reached(n, -1);
@@ -648,6 +661,79 @@ std::string build_spai_plan(const HostPlan& P, int64_t nnzA, const int64_t* Arp,
     auto by_size = [&](int32_t a, int32_t b) { return X.fE[a] > X.fE[b]; };
     std::stable_sort(X.cols_w.begin(), X.cols_w.end(), by_size);
     std::stable_sort(X.cols_c.begin(), X.cols_c.end(), by_size);
+    return "";
+}
+
+std::string build_einv_plan(const HostPlan& P, int64_t nnzA, const int64_t* Arp, const int32_t* Ac, EinvPlan& X) {
+    const int64_t n = P.n;
+    X = EinvPlan();
+    X.n = n;
+    X.nnzA = nnzA;
+    std::vector<int32_t> sorted;
+    std::string err = check_symmetric_pattern(n, nnzA, Arp, Ac, sorted);
+    if (!err.empty()) return err;
+    // columns of S: row j of S_lo (rows k <= j), then the entries (i, j) of later rows i
+    std::vector<int64_t> cnt(n, 0);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t p = P.Srp[i]; p < P.Srp[i + 1]; ++p) {
+            cnt[i] += 1;
+            if (P.Sc[p] != i) cnt[P.Sc[p]] += 1;
+        }
+    X.fcp.assign(n + 1, 0);
+    for (int64_t j = 0; j < n; ++j) X.fcp[j + 1] = X.fcp[j] + cnt[j];
+    X.fri.resize(X.fcp[n]);
+    X.fpos.resize(X.fcp[n]);
+    std::vector<int64_t> cur(n);
+    for (int64_t j = 0; j < n; ++j) {
+        int64_t q = X.fcp[j];
+        for (int64_t p = P.Srp[j]; p < P.Srp[j + 1]; ++p, ++q) {
+            X.fri[q] = P.Sc[p];
+            X.fpos[q] = (int32_t)p;
+        }
+        cur[j] = q;
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t p = P.Srp[i]; p < P.Srp[i + 1]; ++p) {
+            const int32_t j = P.Sc[p];
+            if (j == i) continue;
+            X.fri[cur[j]] = (int32_t)i;
+            X.fpos[cur[j]] = (int32_t)p;
+            ++cur[j];
+        }
+    // L by rows: the column of every CSR entry, from the CSC copy and its CSR positions
+    X.Lcol.assign(P.nnzL, 0);
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t q = P.Lcp[j]; q < P.Lcp[j + 1]; ++q) X.Lcol[P.Lcsr[q]] = (int32_t)j;
+    std::vector<int64_t> rcnt(n + 1, 0);
+    for (int64_t q = 0; q < P.nnzL; ++q) rcnt[P.Lri[q] + 1] += 1;
+    for (int64_t i = 0; i < n; ++i) rcnt[i + 1] += rcnt[i];  // CSR row starts of L
+    // levels: row i of L y = b needs the rows j of its entries; column j of L^T x = z
+    // needs the rows i > j of column j
+    std::vector<int32_t> lev(n, 0);
+    int32_t nlev = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t l = 0;
+        for (int64_t q = rcnt[i]; q < rcnt[i + 1]; ++q) l = std::max(l, lev[X.Lcol[q]] + 1);
+        lev[i] = l;
+        nlev = std::max(nlev, l + 1);
+    }
+    auto group = [&](std::vector<int32_t>& items, std::vector<int32_t>& ptr) {
+        ptr.assign(nlev + 1, 0);
+        for (int64_t i = 0; i < n; ++i) ptr[lev[i] + 1] += 1;
+        for (int32_t l = 0; l < nlev; ++l) ptr[l + 1] += ptr[l];
+        items.resize(n);
+        std::vector<int32_t> at(ptr.begin(), ptr.end() - 1);
+        for (int64_t i = 0; i < n; ++i) items[at[lev[i]]++] = (int32_t)i;
+    };
+    if (n > 0) group(X.fwd_rows, X.fwd_ptr);
+    nlev = 0;
+    for (int64_t j = n - 1; j >= 0; --j) {
+        int32_t l = 0;
+        for (int64_t q = P.Lcp[j]; q < P.Lcp[j + 1]; ++q) l = std::max(l, lev[P.Lri[q]] + 1);
+        lev[j] = l;
+        nlev = std::max(nlev, l + 1);
+    }
+    if (n > 0) group(X.bwd_cols, X.bwd_ptr);
     return "";
 }
 

@@ -210,3 +210,25 @@ def test_spai_analysis_rejects_bad_patterns(lib):
     with pytest.raises(SinvError) as e:
         h.spai_analyse(w.A, power=9)
     assert e.value.name == "SINV_ERR_UNSUPPORTED"
+
+
+@pytest.mark.parametrize("name", ["lap2d", "covariance_12"])
+def test_einv_solve_levels_vs_brute_force(lib, name):
+    # levels of L y = b: 1 + the deepest row a row reads; of L^T x = w: 1 + the deepest
+    # later row of its column
+    A, f = _spai_cases()[name]
+    h = _host_handle(f)
+    h.einv_analyse(A)
+    st = h.stats()
+    L = f.L_csr()
+    n = f.n
+    fwd = np.zeros(n, dtype=int)
+    for i in range(n):
+        c = L.indices[L.indptr[i]:L.indptr[i + 1]]
+        fwd[i] = fwd[c].max() + 1 if len(c) else 0
+    Lc = L.tocsc()
+    bwd = np.zeros(n, dtype=int)
+    for j in range(n - 1, -1, -1):
+        r = Lc.indices[Lc.indptr[j]:Lc.indptr[j + 1]]
+        bwd[j] = bwd[r].max() + 1 if len(r) else 0
+    assert st["einv_levels_fwd"] == fwd.max() + 1 and st["einv_levels_bwd"] == bwd.max() + 1
