@@ -27,8 +27,11 @@ def _handle(f):
 
 
 def _ldlt(f):
+    """L D L^T, symmetrised as (M + M^T)/2: the sparse product drops exact cancellations,
+    which rounding can make differ between the two triangles."""
     L = f.L_csr() + sp.identity(f.n, format="csr")
-    A = sp.csr_matrix(L @ f.D_dense_blocks() @ L.T)
+    M = sp.csr_matrix(L @ f.D_dense_blocks() @ L.T)
+    A = sp.csr_matrix(0.5 * (M + M.T))
     A.sum_duplicates()
     A.sort_indices()
     return A
