@@ -354,6 +354,22 @@ def test_lanczos_eigenpairs_and_eckart_young():
     assert abs(np.linalg.norm(R, "fro") ** 2 - np.sum(ev[k:] ** 2)) <= 1e-8 * np.sum(ev ** 2)
 
 
+def test_lanczos_start_vector_is_an_input():
+    # a given start vector reproduces the seeded run exactly, and a scaled one gives the
+    # same Ritz pairs (the first Lanczos vector is normalised)
+    A = sp.csr_matrix(grids.laplace2d_5pt(8, 8, 0.1))
+    f = ildl(A, 5e-2)
+    Srp, Sc = _S(f)
+    Gs = oracle.core.sym_from_S(f.n, Srp, Sc, _selinv(f, (Srp, Sc)))
+    q = np.random.default_rng(3).standard_normal(f.n)
+    lam1, V1 = oracle.lanczos_einv(A, Gs, 2, steps=20, seed=3)
+    lam2, V2 = oracle.lanczos_einv(A, Gs, 2, steps=20, q0=q)
+    np.testing.assert_array_equal(lam1, lam2)
+    np.testing.assert_array_equal(V1, V2)
+    lam3, V3 = oracle.lanczos_einv(A, Gs, 2, steps=20, q0=7.5 * q)
+    np.testing.assert_allclose(lam3, lam1, rtol=1e-13)
+
+
 def test_acceptance_keeps_only_improving_modes():
     d = np.array([1.0, 2.0, 3.0])
     d_hat = np.array([0.9, 2.0, 3.0])
