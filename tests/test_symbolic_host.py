@@ -232,3 +232,27 @@ def test_einv_solve_levels_vs_brute_force(lib, name):
         r = Lc.indices[Lc.indptr[j]:Lc.indptr[j + 1]]
         bwd[j] = bwd[r].max() + 1 if len(r) else 0
     assert st["einv_levels_fwd"] == fwd.max() + 1 and st["einv_levels_bwd"] == bwd.max() + 1
+
+
+def test_spai_and_lanczos_errors_through_the_abi(lib):
+    # documented error returns that need no device: calls on a host-only handle, a pattern
+    # query before any analysis, bad analysis arguments
+    w = lap2d_32()
+    h = _host_handle(w.factors)
+    rp = np.zeros(w.factors.n + 1, dtype=np.int64)
+    col = np.zeros(max(1, h.nnz_S), dtype=np.int32)
+    P = ctypes.c_void_p
+    assert lib.sinv_spai_pattern(h._h, rp.ctypes.data_as(P), col.ctypes.data_as(P)) == 1
+    assert lib.sinv_spai(h._h, None, None, 3, None, None) == 1
+    lam = np.zeros(2)
+    info = np.zeros(3, dtype=np.int32)
+    assert lib.sinv_einv_lanczos(h._h, None, None, None, None, None, 4, 1e-10, 10, 2,
+                                 lam.ctypes.data_as(P), None, info.ctypes.data_as(P), None) == 1
+    A = sp.csr_matrix(w.A)
+    arp = A.indptr.astype(np.int64)
+    acol = A.indices.astype(np.int32)
+    assert lib.sinv_spai_analyse(h._h, A.nnz, arp.ctypes.data_as(P), acol.ctypes.data_as(P), 0, -1) == 1
+    assert lib.sinv_einv_analyse(h._h, -1, arp.ctypes.data_as(P), acol.ctypes.data_as(P)) == 1
+    bad = arp.copy()
+    bad[-1] += 1  # rowptr does not end at nnzA
+    assert lib.sinv_einv_analyse(h._h, A.nnz, bad.ctypes.data_as(P), acol.ctypes.data_as(P)) == 2
