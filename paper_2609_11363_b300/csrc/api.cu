@@ -175,8 +175,8 @@ sinv_status cuda_fail(sinv_handle h, cudaError_t e, const char* where) {
     return e == cudaErrorMemoryAllocation ? SINV_ERR_OOM : SINV_ERR_CUDA;
 }
 
-template <class T>
-cudaError_t upload(T** dst, const std::vector<T>& src) {
+template <class T, class Alloc>
+cudaError_t upload(T** dst, const std::vector<T, Alloc>& src) {
     size_t bytes = std::max<size_t>(src.size(), 1) * sizeof(T);
     cudaError_t e = cudaMalloc((void**)dst, bytes);
     if (e != cudaSuccess) return e;

@@ -1,10 +1,37 @@
 // Internal data layout shared by the host symbolic analysis and the kernels.
 #pragma once
 #include <cstdint>
+#include <memory>
+#include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 namespace sinv {
+
+// An allocator whose resize() leaves new elements of trivial types uninitialised:
+// for the largest arrays of the plan, which a parallel pass fills completely right
+// after sizing them (zeroing them first took a single thread as long as the pass).
+template <class T>
+struct NoInitAlloc : std::allocator<T> {
+    template <class U>
+    struct rebind {
+        using other = NoInitAlloc<U>;
+    };
+    NoInitAlloc() = default;
+    template <class U>
+    NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+    template <class U>
+    void construct(U* p) noexcept {
+        ::new ((void*)p) U;
+    }
+    template <class U, class... A>
+    void construct(U* p, A&&... a) {
+        ::new ((void*)p) U(std::forward<A>(a)...);
+    }
+};
+template <class T>
+using FillVec = std::vector<T, NoInitAlloc<T>>;
 
 // One supernode: consecutive pivot blocks [s0, s0 + w) processed as one dense
 // step of the Takahashi recurrence.  C is the sorted set of rows below the
@@ -51,8 +78,8 @@ struct HostPlan {
     std::vector<int32_t> owner;      // supernode of each column
     std::vector<int32_t> order;      // processing order (level-major)
     std::vector<int32_t> Crow, Lmap, JJl, JJs;
-    std::vector<uint32_t> hit_ik;    // (i << 16) | k
-    std::vector<int32_t> hit_pos;    // S_lo position of (max, min) of (C[i], C[k])
+    FillVec<uint32_t> hit_ik;        // (i << 16) | k
+    FillVec<int32_t> hit_pos;        // S_lo position of (max, min) of (C[i], C[k])
     std::vector<int32_t> hrow;       // per supernode c+1 row starts
     std::vector<WorkItem> items;
     // supernodes split over several CTAs: offset of their c*w partial-sum block (-1: not split)
@@ -73,7 +100,7 @@ struct NinvPlan {
     int m = -1;
     int64_t nnzW = 0;
     std::vector<int64_t> Wcp;
-    std::vector<int32_t> Wr;
+    FillVec<int32_t> Wr;
     std::vector<int32_t> grp;
     int64_t max_col = 0;
     // algorithmic work: products E_kj W_{t-1}[r,k] of all m Horner steps, and the

@@ -3,6 +3,7 @@
 // (Section 2.1, Fig. 2), dependency levels and the index maps of the numeric
 // kernels.  Everything here is integer work and is deterministic.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <thread>
 
@@ -31,6 +32,29 @@ void parallel_for(int64_t count, F f) {
         if (a >= b) break;
         th.emplace_back([=, &f] { f(a, b); });
     }
+    for (auto& x : th) x.join();
+}
+
+// The same, with items handed out in chunks of `grain` from a shared counter: for
+// loops whose per-item cost varies a lot (supernodes near the root of the tree are
+// the largest).  Each item must write only its own outputs.
+template <class F>
+void parallel_for_dynamic(int64_t count, int64_t grain, F f) {
+    int T = n_threads();
+    if (count < 4096 || T == 1) {
+        f(0, count);
+        return;
+    }
+    std::atomic<int64_t> next(0);
+    std::vector<std::thread> th;
+    for (int t = 0; t < T; ++t)
+        th.emplace_back([&] {
+            for (;;) {
+                const int64_t a = next.fetch_add(grain);
+                if (a >= count) break;
+                f(a, std::min(count, a + grain));
+            }
+        });
     for (auto& x : th) x.join();
 }
 
@@ -305,7 +329,7 @@ std::string build_plan(int64_t n, const int64_t* Lrp, const int32_t* Lc, const i
         if (fill) hrow[c] = (int32_t)cnt;
         return cnt;
     };
-    parallel_for(ns, [&](int64_t a, int64_t b) {
+    parallel_for_dynamic(ns, 256, [&](int64_t a, int64_t b) {
         for (int64_t s = a; s < b; ++s) hits[s] = pairs(s, false, nullptr, nullptr, nullptr);
     });
     int64_t hoff = 0, roff = 0;
@@ -326,7 +350,7 @@ std::string build_plan(int64_t n, const int64_t* Lrp, const int32_t* Lc, const i
     P.hit_ik.resize(hoff);
     P.hit_pos.resize(hoff);
     P.hrow.resize(roff);
-    parallel_for(ns, [&](int64_t a, int64_t b) {
+    parallel_for_dynamic(ns, 256, [&](int64_t a, int64_t b) {
         for (int64_t s = a; s < b; ++s) {
             SnInfo& I = P.sn[s];
             pairs(s, true, P.hit_ik.data() + I.hit_off, P.hit_pos.data() + I.hit_off, P.hrow.data() + I.hrow_off);
@@ -426,50 +450,56 @@ std::string build_ninv_plan(const HostPlan& P, int m, NinvPlan& W) {
     W.m = m;
     const int64_t* Lcp = P.Lcp.data();
     const int32_t* Lri = P.Lri.data();
-    // dist-tagged columns, built per power: cur[j] = rows of R_t(j) sorted, with tag
-    std::vector<std::vector<int32_t>> rows(n), tags(n);
+    // dist-tagged columns, built per power: rows[j] = R_t(j) sorted, tags[j] = the
+    // fewest steps that reach each row.  R_t(j) = {j} + the union over k in struct(j)
+    // of R_{t-1}(k), and the union of the R_{t-2}(k) is already in R_{t-1}(j), so round
+    // t only propagates front[k], the rows that entered R_{t-1}(k) in round t-1; the
+    // rows it adds to R_t(j) have tag t.
+    std::vector<std::vector<int32_t>> rows(n), tags(n), front(n);
     for (int64_t j = 0; j < n; ++j) {
         rows[j].push_back((int32_t)j);
         tags[j].push_back(0);
+        front[j].push_back((int32_t)j);
     }
     for (int t = 1; t <= m; ++t) {
-        std::vector<std::vector<int32_t>> nrows(n), ntags(n);
-        parallel_for(n, [&](int64_t a, int64_t b) {
+        std::vector<std::vector<int32_t>> nrows(n), ntags(n), nfront(n);
+        parallel_for_dynamic(n, 512, [&](int64_t a, int64_t b) {
             // per-thread dense markers: mark[r] == j when row r is already in R_t(j)
-            std::vector<int32_t> mark(n, -1), best(n, 0), list;
+            std::vector<int32_t> mark(n, -1), fresh;
             for (int64_t j = a; j < b; ++j) {
-                list.clear();
-                auto add = [&](int32_t r, int32_t tg) {
-                    if (mark[r] != (int32_t)j) {
-                        mark[r] = (int32_t)j;
-                        best[r] = tg;
-                        list.push_back(r);
-                    } else if (tg < best[r]) {
-                        best[r] = tg;
-                    }
-                };
-                for (size_t e = 0; e < rows[j].size(); ++e) add(rows[j][e], tags[j][e]);
-                for (int64_t q = Lcp[j]; q < Lcp[j + 1]; ++q) {
-                    int32_t k = Lri[q];
-                    // rows reached from k within t-1 steps are reached from j within t
-                    const auto& rk = rows[k];
-                    const auto& tk = tags[k];
-                    for (size_t e = 0; e < rk.size(); ++e)
-                        if (tk[e] <= t - 1) add(rk[e], tk[e] + 1);
-                }
-                std::sort(list.begin(), list.end());
+                for (int32_t r : rows[j]) mark[r] = (int32_t)j;
+                fresh.clear();
+                for (int64_t q = Lcp[j]; q < Lcp[j + 1]; ++q)
+                    for (int32_t r : front[Lri[q]])
+                        if (mark[r] != (int32_t)j) {
+                            mark[r] = (int32_t)j;
+                            fresh.push_back(r);
+                        }
+                std::sort(fresh.begin(), fresh.end());
+                // merge the sorted old rows (their tags kept) with the new ones (tag t)
+                const auto& R0 = rows[j];
+                const auto& T0 = tags[j];
                 auto& R = nrows[j];
                 auto& T = ntags[j];
-                R.resize(list.size());
-                T.resize(list.size());
-                for (size_t e = 0; e < list.size(); ++e) {
-                    R[e] = list[e];
-                    T[e] = best[list[e]];
+                R.resize(R0.size() + fresh.size());
+                T.resize(R.size());
+                size_t x = 0, y = 0, o = 0;
+                while (x < R0.size() || y < fresh.size()) {
+                    if (y == fresh.size() || (x < R0.size() && R0[x] < fresh[y])) {
+                        R[o] = R0[x];
+                        T[o++] = T0[x++];
+                    } else {
+                        R[o] = fresh[y++];
+                        T[o++] = t;
+                    }
                 }
+                nfront[j].swap(fresh);
+                fresh.clear();
             }
         });
         rows.swap(nrows);
         tags.swap(ntags);
+        front.swap(nfront);
     }
     W.Wcp.assign(n + 1, 0);
     for (int64_t j = 0; j < n; ++j) W.Wcp[j + 1] = W.Wcp[j] + (int64_t)rows[j].size();
@@ -477,22 +507,24 @@ std::string build_ninv_plan(const HostPlan& P, int m, NinvPlan& W) {
     if (W.nnzW > INT32_MAX) return "pattern of the truncated Neumann series has >= 2^31 entries";
     W.Wr.resize(W.nnzW);
     W.grp.assign((size_t)n * (m + 2), 0);
-    parallel_for(n, [&](int64_t a, int64_t b) {
-        std::vector<std::pair<int32_t, int32_t>> buf;
+    // column j of W: its rows grouped by tag, ascending inside each group (the rows are
+    // already sorted, so a stable split by tag gives that order)
+    parallel_for_dynamic(n, 512, [&](int64_t a, int64_t b) {
+        std::vector<int32_t> at(m + 2);
         for (int64_t j = a; j < b; ++j) {
-            buf.clear();
-            for (size_t e = 0; e < rows[j].size(); ++e) buf.push_back({tags[j][e], rows[j][e]});
-            std::sort(buf.begin(), buf.end());
-            int64_t base = W.Wcp[j];
+            const auto& R = rows[j];
+            const auto& T = tags[j];
             int32_t* g = W.grp.data() + (size_t)j * (m + 2);
-            int t = 0;
-            for (size_t e = 0; e < buf.size(); ++e) {
-                while (t <= buf[e].first) g[t++] = (int32_t)e;
-                const int32_t r = buf[e].second;
+            std::fill(at.begin(), at.end(), 0);
+            for (int32_t tg : T) ++at[tg + 1];
+            for (int t = 0; t <= m; ++t) at[t + 1] += at[t];
+            for (int t = 0; t <= m + 1; ++t) g[t] = at[t];  // group starts, then the end
+            int32_t* out = W.Wr.data() + W.Wcp[j];
+            for (size_t e = 0; e < R.size(); ++e) {
+                const int32_t r = R[e];
                 const bool two = !P.pstart[r] || (r + 1 < n && !P.pstart[r + 1]);
-                W.Wr[base + e] = two ? (int32_t)((uint32_t)r | 0x80000000u) : r;
+                out[at[T[e]]++] = two ? (int32_t)((uint32_t)r | 0x80000000u) : r;
             }
-            while (t <= m + 1) g[t++] = (int32_t)buf.size();
         }
     });
     for (int64_t j = 0; j < n; ++j) W.max_col = std::max<int64_t>(W.max_col, W.Wcp[j + 1] - W.Wcp[j]);
