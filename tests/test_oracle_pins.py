@@ -564,3 +564,16 @@ def test_spai_pattern_by_breadth_first_search():
         Prp, Pc = oracle.spai_pattern(A, Srp, Sc, p)
         assert set(zip(_rows(Prp).tolist(), Pc.tolist())) == want
         assert np.all(Pc[Prp[1:] - 1] == np.arange(n))  # the diagonal ends every row
+
+
+def test_spai_embed_places_values_on_the_wider_pattern():
+    # X on S moved onto P = S + distance-1 pairs: the same values where (i, j) is in S, 0 elsewhere
+    A, Srp, Sc = _spai_case(n=18, seed=12)
+    X = np.random.default_rng(4).standard_normal(len(Sc))
+    np.testing.assert_array_equal(oracle.embed(Srp, Sc, X, Srp, Sc), X)
+    Prp, Pc = oracle.spai_pattern(A, Srp, Sc, 1)
+    Y = oracle.embed(Srp, Sc, X, Prp, Pc)
+    onS = dict(zip(zip(_rows(Srp).tolist(), Sc.tolist()), X.tolist()))
+    for (i, j), y in zip(zip(_rows(Prp).tolist(), Pc.tolist()), Y.tolist()):
+        assert y == onS.get((i, j), 0.0)
+    assert len(Pc) > len(Sc)
