@@ -262,11 +262,17 @@ sinv_status sinv_einv_lanczos(sinv_handle h, const double *A_val, const double *
  * no counterpart; this is a deployment variant of the correction above.
  *   S_rowptr [n+1], S_col [|S_lo|]: the pattern S_lo on the device (for example
  *   from sinv_get_pattern); V [n*k] row-major, lambda [k], X_S in/out: device.
- *   Limit: n*k + k <= 4,194,304, else SINV_ERR_UNSUPPORTED (nothing is launched).
- *   The first call on a device looks up the array's device address; make that
- *   first call before any stream capture.  All calls on a device share the
- *   array: calls that overlap on the GPU (other streams, other threads) race,
- *   so order them on one stream.  Errors of the launch: SINV_ERR_CUDA. */
+ *   Limits: 1 <= k <= 256 (lambda .* V_i is staged in a 256-entry shared row)
+ *   and n*k + k <= 4,194,304 (the array's size).  All pointers must belong to
+ *   the current device.  The first call on a device looks up the array's
+ *   device address; make that first call before any stream capture.  All
+ *   calls on a device share the array: calls that overlap on the GPU (other
+ *   streams, other threads) race, so order them on one stream.
+ *   Returns: SINV_OK (also for n == 0 or k == 0, with nothing launched);
+ *   SINV_ERR_INVALID_ARG for n < 0, k < 0 or a null pointer;
+ *   SINV_ERR_UNSUPPORTED for k > 256 or n*k + k > 4,194,304 (checked before
+ *   anything else is read, nothing is launched); SINV_ERR_CUDA when the device
+ *   lookup or a launch fails. */
 sinv_status sinv_lowrank_correct_noalloc(int64_t n, const int64_t *S_rowptr, const int32_t *S_col, int k,
                                          const double *V, const double *lambda, double *X_S, void *stream);
 

@@ -231,6 +231,7 @@ class Mlp:
 
 
 LOWRANK_NOALLOC_MAX = 1 << 22  # n*k + k floats of the library's built-in working array
+LOWRANK_NOALLOC_KMAX = 256     # largest rank k of the low-rank correction
 
 
 def lowrank_correct_noalloc(S_rowptr, S_col, V, lam, X, stream=None):
@@ -239,18 +240,28 @@ def lowrank_correct_noalloc(S_rowptr, S_col, V, lam, X, stream=None):
     For callers that cannot allocate device memory: no handle, the working copy
     lives in the library's fixed 16 MiB array.  S_rowptr (int64, n+1) and S_col
     (int32) are the pattern on the device; V (n x k, float64), lam (k) and the
-    in/out X (float64) are CUDA tensors.  Raises SinvError(SINV_ERR_UNSUPPORTED)
-    when n*k + k exceeds LOWRANK_NOALLOC_MAX.
+    in/out X (float64) are CUDA tensors, all on one device; the call runs with
+    that device current.  Raises SinvError(SINV_ERR_UNSUPPORTED) when k > 256 or
+    n*k + k exceeds LOWRANK_NOALLOC_MAX.
     """
     lib = load_library()
+    tensors = (S_rowptr, S_col, V, lam, X)
+    dev = V.device
+    if dev.type != "cuda" or any(t.device != dev for t in tensors):
+        raise ValueError("S_rowptr, S_col, V, lam and X must be CUDA tensors on one device")
     n = int(S_rowptr.numel()) - 1
     k = int(lam.numel())
-    st = lib.sinv_lowrank_correct_noalloc(
-        n, _check_tensor(S_rowptr, "S_rowptr", n + 1, torch.int64), _check_tensor(S_col, "S_col", None, torch.int32),
-        k, _check_tensor(V, "V", n * k), _check_tensor(lam, "lambda", k), _check_tensor(X, "X_S", int(S_col.numel())),
-        _stream_ptr(stream))
+    with torch.cuda.device(dev):
+        st = lib.sinv_lowrank_correct_noalloc(
+            n, _check_tensor(S_rowptr, "S_rowptr", n + 1, torch.int64),
+            _check_tensor(S_col, "S_col", None, torch.int32), k, _check_tensor(V, "V", n * k),
+            _check_tensor(lam, "lambda", k), _check_tensor(X, "X_S", int(S_col.numel())), _stream_ptr(stream))
     if st != 0:
-        msg = "n*k + k = %d exceeds %d" % (n * k + k, LOWRANK_NOALLOC_MAX) if st == 7 else "launch failed"
+        if st == 7:
+            msg = "k = %d (limit %d) or n*k + k = %d (limit %d) too large" % (
+                k, LOWRANK_NOALLOC_KMAX, n * k + k, LOWRANK_NOALLOC_MAX)
+        else:
+            msg = "invalid argument" if st == 1 else "launch failed"
         raise SinvError(st, msg)
     return X
 

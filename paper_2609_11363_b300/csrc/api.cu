@@ -708,7 +708,7 @@ sinv_status sinv_lowrank_correct(sinv_handle h, int k, const double* V, const do
                                  double* X_S, void* stream) {
     if (!h || k < 0 || !valid_prec(prec)) return SINV_ERR_INVALID_ARG;
     if (!on_device(h)) return SINV_ERR_INVALID_ARG;
-    if (k > 256) {
+    if (k > kLowrankKMax) {
         set_err(h, "k > 256 is not supported");
         return SINV_ERR_UNSUPPORTED;
     }
@@ -1125,8 +1125,8 @@ sinv_status sinv_debug_wait_timeout(sinv_handle h, void* stream) {
 sinv_status sinv_lowrank_correct_noalloc(int64_t n, const int64_t* S_rowptr, const int32_t* S_col, int k,
                                          const double* V, const double* lambda, double* X_S, void* stream) {
     if (n < 0 || k < 0) return SINV_ERR_INVALID_ARG;
+    if (k > kLowrankKMax || n * (int64_t)k + k > kLowrankStaticFloats) return SINV_ERR_UNSUPPORTED;
     if (n == 0 || k == 0) return SINV_OK;
-    if (n * (int64_t)k + k > kLowrankStaticFloats) return SINV_ERR_UNSUPPORTED;
     if (!S_rowptr || !S_col || !V || !lambda || !X_S) return SINV_ERR_INVALID_ARG;
     cudaError_t e = lowrank_noalloc_launch(n, S_rowptr, S_col, k, V, lambda, X_S, (cudaStream_t)stream);
     return e == cudaSuccess ? SINV_OK : SINV_ERR_CUDA;

@@ -36,7 +36,7 @@ __global__ void mix_kernel(const double* __restrict__ G, const double* __restric
 }
 
 constexpr int kLrWarps = 8;
-constexpr int kKMax = 256;
+constexpr int kKMax = kLowrankKMax;
 
 // One warp per row i of S_lo: u = lambda .* V_i staged in shared memory, then
 // every entry (i, j) of the row adds u . V_j.  R is the product type.
@@ -151,7 +151,7 @@ static cudaError_t lowrank_static_scratch(float** out) {
 cudaError_t lowrank_noalloc_launch(int64_t n, const int64_t* Srp, const int32_t* Sc, int k, const double* V,
                                    const double* lambda, double* X, cudaStream_t st) {
     if (n == 0 || k == 0) return cudaSuccess;
-    if (n * (int64_t)k + k > kLowrankStaticFloats) return cudaErrorInvalidValue;
+    if (k < 0 || k > kKMax || n * (int64_t)k + k > kLowrankStaticFloats) return cudaErrorInvalidValue;
     float* Vf = nullptr;
     cudaError_t e = lowrank_static_scratch(&Vf);
     if (e != cudaSuccess) return e;

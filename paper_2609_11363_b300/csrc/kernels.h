@@ -126,8 +126,12 @@ size_t ninv_work_bytes(const NinvArgs& a, int prec);
 cudaError_t ninv_launch(const NinvArgs& a, int prec, void* work, double* N_out, cudaStream_t st,
                         double* N_stack = nullptr);
 
+// Largest rank k of the low-rank correction: lowrank_kernel stages lambda .* V_i
+// in a shared row of this many values per warp.
+constexpr int kLowrankKMax = 256;
+
 // FP32 low-rank correction with its working copy in a file-scope device array
-// (no allocation); n*k + k must not exceed kLowrankStaticFloats.
+// (no allocation); k <= kLowrankKMax and n*k + k <= kLowrankStaticFloats.
 constexpr int64_t kLowrankStaticFloats = int64_t(1) << 22;  // 4,194,304 floats = 16 MiB
 cudaError_t lowrank_noalloc_launch(int64_t n, const int64_t* Srp, const int32_t* Sc, int k, const double* V,
                                    const double* lambda, double* X, cudaStream_t st);

@@ -64,6 +64,71 @@ def test_mlp_gradient_matches_oracle_and_adam_step():
     assert np.max(np.abs(th1 - want)) <= 1e-6
 
 
+def _predict_ref(theta_bf16, Xr, N, sc):
+    """N + s * f(x) with the oracle network on the BF16-rounded weights and features."""
+    return N + sc.astype(np.float64) * omlp.forward(theta_bf16, Xr, F, H)
+
+
+def _assert_predict_close(got, N, sc, theta_bf16, Xr):
+    """Entry by entry.  f is evaluated with FP32 sums: three layers of at most 64
+    terms each, so its error is bounded by a few units of 2^-24 times the sum of
+    the magnitudes of the terms (|h|.|W|, taken from the oracle in FP64)."""
+    W1, b1, W2, b2, W3, b3 = omlp.split(theta_bf16, F, H)
+    h1 = np.maximum(Xr @ W1 + b1, 0.0)
+    h2 = np.maximum(h1 @ W2 + b2, 0.0)
+    aW2, aW3 = np.abs(W2), np.abs(W3)
+    mag = ((np.abs(Xr) @ np.abs(W1) + np.abs(b1)) @ aW2) @ aW3      # layer-1 sums carried through
+    mag += (np.abs(h1) @ aW2 + np.abs(b2)) @ aW3                      # layer-2 sums
+    mag += np.abs(h2) @ aW3 + abs(b3[0])                              # output sum
+    f_ref = h2 @ W3 + b3[0]
+    f_got = (got - N) / sc.astype(np.float64)
+    bound = 2 * (H + 1) * 2.0 ** -24 * mag + 1e-30
+    assert np.all(np.abs(f_got - f_ref) <= bound), float(np.max(np.abs(f_got - f_ref) / bound))
+    want = _predict_ref(theta_bf16, Xr, N, sc)
+    assert np.all(np.abs(got - want) <= sc * bound + 4 * np.finfo(float).eps * np.abs(want))
+
+
+@pytest.mark.parametrize("count", [1, 127, 128, 1000, 4099])
+def test_mlp_predict_matches_oracle_entry_by_entry(count):
+    """sinv_mlp_predict against N + s * oracle.mlp.forward(bf16(theta), bf16(X)) on
+    random features and weights: every entry, full tiles and a ragged tail."""
+    from paper_2609_11363_b300 import Mlp
+    rng = np.random.default_rng(11 + count)
+    net = Mlp(seed=3, max_batch=4096)
+    th = rng.standard_normal(net.n_params).astype(np.float32) * 0.3
+    net.set_params(th)
+    Xb = torch.as_tensor(rng.standard_normal((count, F)).astype(np.float32)).to(torch.bfloat16).cuda()
+    sc = rng.uniform(0.5, 2.0, count).astype(np.float32)
+    N = rng.standard_normal(count)
+    got = net.predict(Xb, _dev(sc), _dev(N)).cpu().numpy()
+    Xr = Xb.float().cpu().numpy().astype(np.float64)
+    _assert_predict_close(got, N, sc, _bf16_round(th), Xr)
+
+
+def test_mlp_predict_on_diffusion_features():
+    """The same comparison on the features of a 3D diffusion case (the inputs the
+    learned correction sees), after a few training steps so the weights are not
+    the initial ones."""
+    from paper_2609_11363_b300 import Handle, Mlp
+    f = plant_2x2(diff3d(9, shifted=False, m=3).factors, 0.05, 8)
+    h = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+    Lv, Dv = _dev(f.L_val), _dev(f.D_packed)
+    st = h.ninv_stack(Lv, Dv, 3)
+    X, sc = h.mlp_features(st, 3, Lv, Dv)
+    G = h.selinv(Lv, Dv)
+    net = Mlp(seed=5, max_batch=1 << 15)
+    y = net.targets(G, st[3].contiguous(), sc)
+    idx = torch.arange(min(X.shape[0], 1 << 15), dtype=torch.int64, device="cuda")
+    for _ in range(5):
+        net.train_step(X, y, idx, 3e-3)
+    N = st[3].contiguous()
+    got = net.predict(X, sc, N).cpu().numpy()
+    h.sync_status()
+    th = _bf16_round(net.get_params())
+    Xr = X.float().cpu().numpy().astype(np.float64)
+    _assert_predict_close(got, N.cpu().numpy(), sc.cpu().numpy(), th, Xr)
+
+
 def test_features_match_their_definition():
     from paper_2609_11363_b300 import Handle
     f = plant_2x2(diff3d(8, shifted=False, m=3).factors, 0.1, 5)
@@ -115,7 +180,9 @@ def test_full_size_128_ninv_stack_sampled():
     Lv, Dv = _dev(f.L_val), _dev(f.D_packed)
     st = h.ninv_stack(Lv, Dv, 3).cpu().numpy()
     h.sync_status()
-    S = (h.pattern_host()[0], h.pattern_host()[1])
+    S = oracle.symbolic_S(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+    rp_h, col_h = h.pattern_host()
+    assert np.array_equal(rp_h, S[0]) and np.array_equal(col_h, S[1])
     rng = np.random.default_rng(3)
     idx = rng.choice(len(S[1]), 24, replace=False)
     rows = np.repeat(np.arange(f.n), np.diff(S[0]))

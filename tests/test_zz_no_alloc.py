@@ -58,3 +58,43 @@ def test_noalloc_rejects_oversized_request():
         lowrank_correct_noalloc(_dev(rp), _dev(col), V, lam, X)
     assert ei.value.name == "SINV_ERR_UNSUPPORTED"
     assert torch.count_nonzero(X).item() == 0
+
+
+def test_noalloc_rejects_rank_above_256_before_reading_pointers():
+    """k > 256 does not fit the kernel's shared row of lambda .* V_i: the entry
+    point must refuse it before it looks at any pointer, so NULL pointers give
+    SINV_ERR_UNSUPPORTED (a regression would give SINV_ERR_INVALID_ARG) and
+    nothing reaches a GPU.  Runs without a GPU."""
+    from paper_2609_11363_b300.binding import LOWRANK_NOALLOC_KMAX, load_library
+
+    lib = load_library()
+    for n, k in ((100, 257), (1024, 300), (100, 1000), (0, 257)):
+        assert lib.sinv_lowrank_correct_noalloc(n, None, None, k, None, None, None, None) == 7, (n, k)
+    assert LOWRANK_NOALLOC_KMAX == 256
+    # within both limits, NULL pointers are an invalid argument, not a launch
+    assert lib.sinv_lowrank_correct_noalloc(100, None, None, 256, None, None, None, None) == 1
+    assert lib.sinv_lowrank_correct_noalloc(-1, None, None, 4, None, None, None, None) == 1
+
+
+@pytest.mark.gpu
+def test_noalloc_rank_257_leaves_X_unchanged():
+    from paper_2609_11363_b300 import Handle, SinvError, lowrank_correct_noalloc
+    from paper_2609_11363_b300.binding import load_library
+
+    # the same request with NULL pointers first: if the rank check ever went
+    # missing this returns SINV_ERR_INVALID_ARG and the test stops here, before
+    # a kernel could be launched with a rank its shared row cannot hold
+    assert load_library().sinv_lowrank_correct_noalloc(1024, None, None, 257, None, None, None, None) == 7
+    f = lap2d_32().factors
+    h = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+    rp, col = h.pattern_host()
+    k = 257
+    assert f.n * k + k <= 1 << 22   # inside the array: only the rank limit applies
+    V, lam = random_lowrank(f.n, k, seed=9)
+    X0 = np.random.default_rng(3).standard_normal(h.nnz_S)
+    X = _dev(X0)
+    with pytest.raises(SinvError) as ei:
+        lowrank_correct_noalloc(_dev(rp), _dev(col), _dev(V), _dev(lam), X)
+    assert ei.value.name == "SINV_ERR_UNSUPPORTED"
+    torch.cuda.synchronize()
+    assert np.array_equal(X.cpu().numpy(), X0)
