@@ -20,6 +20,10 @@ LDL^T Factorization and Spectral Corrections"):
 * ``lanczos_einv``    -- dominant eigenpairs of E_inv = A^{-1} - A^inv
                          (Section 2.5, Algorithm 1 step 5)
 * measures            -- err_1, fill_fact, fill_inv, DoDD (Sections 2.6, 3.2)
+* ``selinv_levels``, ``ninv_threads`` -- the same SelInv and NInv on every
+                         host thread (OpenMP over level sets / independent
+                         columns and entries; C, csrc/): the all-cores CPU
+                         baseline, checked against ``selinv`` and ``ninv``
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA
@@ -46,5 +50,8 @@ from .core import (  # noqa: F401
     dodd,
     accept_modes,
     build_lib,
+    selinv_levels,
+    ninv_threads,
+    host_threads,
 )
 from .spai import spai_columns, spai_refine, spai_entries_sampled, spai_pattern, embed, pcg_jacobi  # noqa: F401

@@ -18,16 +18,18 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "csrc", "selinv_ref.c")
+_SRCS = [os.path.join(_HERE, "csrc", f) for f in ("selinv_ref.c", "ninv_ref.c")]
 _LIB = os.path.join(_HERE, "_selinv_ref.so")
 _lib = None
 
 
 def build_lib(force: bool = False) -> str:
-    """Compile the C part of the oracle in place (gcc -O2)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile the C part of the oracle in place (gcc -O2, OpenMP for the
+    all-threads baseline variants)."""
+    newest = max(os.path.getmtime(f) for f in _SRCS + [__file__])
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + ".tmp.%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-fopenmp", "-shared", "-o", tmp] + _SRCS)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -39,8 +41,19 @@ def _load():
         P = ctypes.c_void_p
         lib.oracle_selinv.argtypes = [ctypes.c_int64, P, P, P, P, P, P, P, P, P, ctypes.c_int64]
         lib.oracle_selinv.restype = ctypes.c_int
+        lib.oracle_selinv_levels.argtypes = [ctypes.c_int64, P, P, P, P, P, P, P, P, P, P]
+        lib.oracle_selinv_levels.restype = ctypes.c_int
+        lib.oracle_ninv_threads.argtypes = [ctypes.c_int64, P, P, P, P, P, P, ctypes.c_int, P, P, P]
+        lib.oracle_ninv_threads.restype = ctypes.c_int
+        lib.oracle_threads.argtypes = []
+        lib.oracle_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
+
+
+def host_threads() -> int:
+    """Threads the all-threads variants use (OpenMP's default: every host core)."""
+    return int(_load().oracle_threads())
 
 
 def _p(a):
@@ -106,6 +119,57 @@ def selinv(n, L_rowptr, L_col, L_val, pivot_start, d_diag, d_off, S=None, stop_c
     if rc != 0:
         raise MemoryError("oracle_selinv failed")
     return G
+
+
+def _csc_L(n, L_rowptr, L_col, L_val):
+    Lcsc = sp.csr_matrix((np.asarray(L_val, dtype=np.float64), L_col, L_rowptr), shape=(n, n)).tocsc()
+    Lcsc.sort_indices()
+    return Lcsc.indptr.astype(np.int64), Lcsc.indices.astype(np.int32), Lcsc.data.astype(np.float64)
+
+
+def selinv_levels(n, L_rowptr, L_col, L_val, pivot_start, d_diag, d_off, S=None):
+    """``selinv`` scheduled by level sets over every host thread (the survey's
+    CPU baseline variant (ii)).  Each pivot block does the same arithmetic as
+    in ``selinv``, so the result is identical to it.  Returns (G, levels)."""
+    lib = _load()
+    if S is None:
+        S = symbolic_S(n, L_rowptr, L_col, pivot_start)
+    cp, r, v = _csc_L(n, L_rowptr, L_col, L_val)
+    ps = np.ascontiguousarray(pivot_start, dtype=np.int8)
+    dd = np.ascontiguousarray(d_diag, dtype=np.float64)
+    do = np.ascontiguousarray(d_off, dtype=np.float64)
+    Srp = np.ascontiguousarray(S[0], dtype=np.int64); Sc = np.ascontiguousarray(S[1], dtype=np.int32)
+    G = np.zeros(len(Sc))
+    nlev = np.zeros(1, dtype=np.int64)
+    rc = lib.oracle_selinv_levels(n, _p(cp), _p(r), _p(v), _p(ps), _p(dd), _p(do), _p(Srp), _p(Sc), _p(G),
+                                  _p(nlev))
+    if rc == -2:
+        raise ZeroDivisionError("singular pivot block")
+    if rc != 0:
+        raise MemoryError("oracle_selinv_levels failed")
+    return G, int(nlev[0])
+
+
+def ninv_threads(n, L_rowptr, L_col, L_val, pivot_start, d_diag, d_off, m, S=None):
+    """``ninv`` (delta = 0) in plain C over every host thread: the Horner
+    columns and the entries of the product are independent (the survey's CPU
+    baseline variant (ii)).  Agrees with ``ninv`` to rounding."""
+    lib = _load()
+    if S is None:
+        S = symbolic_S(n, L_rowptr, L_col, pivot_start)
+    cp, r, v = _csc_L(n, L_rowptr, L_col, L_val)
+    ps = np.ascontiguousarray(pivot_start, dtype=np.int8)
+    dd = np.ascontiguousarray(d_diag, dtype=np.float64)
+    do = np.ascontiguousarray(d_off, dtype=np.float64)
+    Srp = np.ascontiguousarray(S[0], dtype=np.int64); Sc = np.ascontiguousarray(S[1], dtype=np.int32)
+    N = np.zeros(len(Sc))
+    rc = lib.oracle_ninv_threads(n, _p(cp), _p(r), _p(v), _p(ps), _p(dd), _p(do), int(m), _p(Srp), _p(Sc),
+                                 _p(N))
+    if rc == -2:
+        raise ZeroDivisionError("singular pivot block")
+    if rc != 0:
+        raise MemoryError("oracle_ninv_threads failed")
+    return N
 
 
 # --------------------------------------------------------------------------

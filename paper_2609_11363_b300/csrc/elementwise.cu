@@ -9,7 +9,7 @@ namespace sinv {
 
 namespace {
 
-// (A_Mix)_ij = G_ij if |G_ij| > eps else N_ij.  Streams 3 x 8 B in, 8 B out per entry.
+// (A_Mix)_ij = G_ij if |G_ij| > eps else N_ij.  Streams 2 x 8 B in, 8 B out per entry.
 __global__ void mix_kernel(const double* __restrict__ G, const double* __restrict__ N, double eps,
                            double* __restrict__ M, int64_t nnz) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
