@@ -31,10 +31,25 @@ def n_params(F, H):
     return F * H + H + H * H + H + H + 1
 
 
-def forward(theta, X, F, H):
-    """f(x) for every row of X (shape [B, F])."""
+def bf16_round(a):
+    """Round to the nearest BF16 value (8 significant bits, ties to even), by way
+    of FP32 as a device does it; returned as float64."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward(theta, X, F, H, act_bf16=False):
+    """f(x) for every row of X (shape [B, F]).
+
+    act_bf16: the first hidden layer is stored in BF16 before the second layer
+    reads it -- the reading of inference on tensor cores, whose operands of the
+    64 x 64 layer are BF16 (the network is defined with BF16 weights and
+    features already; sums stay exact here)."""
     W1, b1, W2, b2, W3, b3 = split(theta, F, H)
     h1 = np.maximum(X @ W1 + b1, 0.0)
+    if act_bf16:
+        h1 = bf16_round(h1)
     h2 = np.maximum(h1 @ W2 + b2, 0.0)
     return h2 @ W3 + b3[0]
 

@@ -420,6 +420,25 @@ def test_mlp_oracle_gradient_matches_finite_differences():
     assert np.allclose((theta - t1)[big], 1e-3 * np.sign(g[big]), rtol=1e-4)
 
 
+def test_mlp_bf16_rounding_hand_values_and_library():
+    """The BF16 rounding of the hidden layer (inference on tensor cores): ties go
+    to the even neighbour, and every value agrees with torch's own conversion."""
+    import torch
+    from oracle import mlp as omlp
+    hand = np.array([1.0, 1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, 1 + 2.0 ** -7, 1 + 2.0 ** -8 + 2.0 ** -20, -3.0, 0.0])
+    want = np.array([1.0, 1.0, 1 + 2.0 ** -6, 1 + 2.0 ** -7, 1 + 2.0 ** -7, -3.0, 0.0])
+    assert np.array_equal(omlp.bf16_round(hand), want)
+    x = np.random.default_rng(4).standard_normal(10000) * 10.0 ** np.random.default_rng(5).integers(-8, 8, 10000)
+    lib = torch.as_tensor(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(omlp.bf16_round(x), lib)
+    rng = np.random.default_rng(6)
+    theta = rng.standard_normal(omlp.n_params(16, 64)) * 0.3
+    X = rng.standard_normal((50, 16))
+    a = omlp.forward(theta, X, 16, 64)
+    b = omlp.forward(theta, X, 16, 64, act_bf16=True)
+    assert 0 < np.max(np.abs(a - b)) <= 2.0 ** -7 * np.max(np.abs(a)) + 1e-3
+
+
 def test_covariance_generator_matches_definition():
     """The covariance-type example entry by entry from the grid coordinates (brute
     force over all pairs), symmetric positive definite."""
