@@ -309,9 +309,17 @@ sinv_status sinv_mlp_grad(sinv_mlp m, const void *X, const float *y, const int64
 /* sinv_mlp_grad followed by one Adam step (beta 0.9 / 0.999, eps 1e-8) with rate lr. */
 sinv_status sinv_mlp_train_step(sinv_mlp m, const void *X, const float *y, const int64_t *idx, int64_t count,
                                 float lr, float *loss, void *stream);
-/* out[e] = N[e] + scale[e] f(X[e]) for count entries (device). */
+/* out[e] = N[e] + scale[e] f(X[e]) for count entries (device).  Runs on the
+ * tensor cores (tcgen05, BF16 operands, FP32 accumulators in tensor memory);
+ * the first hidden layer is rounded to BF16 as the operand of the second.  X
+ * must be 16-byte aligned (SINV_ERR_INVALID_ARG otherwise).  A completion wait
+ * that runs out of polls is recorded for sinv_mlp_sync_status. */
 sinv_status sinv_mlp_predict(sinv_mlp m, const void *X, const float *scale, const double *N, int64_t count,
                              double *out, void *stream);
+/* Synchronizes `stream` and returns the first device error of the network's
+ * asynchronous calls since the last check (SINV_ERR_TIMEOUT for a tensor-core
+ * completion wait that ran out of polls), then clears it. */
+sinv_status sinv_mlp_sync_status(sinv_mlp m, void *stream);
 
 /* Wait for the handle's queued work on `stream` and return the first device
  * error recorded since the last call (then clear it). */

@@ -32,6 +32,7 @@ EXPORTS = [
     "sinv_spai_analyse", "sinv_spai_pattern", "sinv_spai", "sinv_einv_analyse", "sinv_einv_lanczos",
     "sinv_mlp_param_count", "sinv_mlp_create", "sinv_mlp_destroy", "sinv_mlp_get_params", "sinv_mlp_set_params",
     "sinv_mlp_features", "sinv_mlp_targets", "sinv_mlp_grad", "sinv_mlp_train_step", "sinv_mlp_predict",
+    "sinv_mlp_sync_status",
 ]
 
 
@@ -107,6 +108,7 @@ def load_library():
     lib.sinv_mlp_grad.argtypes = [H, P, P, P, I64, P, P, P]
     lib.sinv_mlp_train_step.argtypes = [H, P, P, P, I64, ctypes.c_float, P, P]
     lib.sinv_mlp_predict.argtypes = [H, P, P, P, I64, P, P]
+    lib.sinv_mlp_sync_status.argtypes = [H, P]
     lib.sinv_batch_symbolic.argtypes = [ctypes.c_int32, P, P, P, P, ctypes.POINTER(_Opts), ctypes.POINTER(H)]
     lib.sinv_batch_layout.argtypes = [H, ctypes.POINTER(ctypes.c_int32), P, P, P, P]
     lib.sinv_lowrank_correct_noalloc.argtypes = [I64, P, P, ctypes.c_int, P, P, P, P]
@@ -228,6 +230,10 @@ class Mlp:
                                              _check_tensor(N, "N"), int(N.numel()), _check_tensor(out, "out"),
                                              _stream_ptr(stream)), "predict")
         return out
+
+    def sync_status(self, stream=None):
+        """Synchronize and raise on a device error of the asynchronous calls."""
+        self._chk(self._lib.sinv_mlp_sync_status(self._m, _stream_ptr(stream)), "sync_status")
 
 
 LOWRANK_NOALLOC_MAX = 1 << 22  # n*k + k floats of the library's built-in working array

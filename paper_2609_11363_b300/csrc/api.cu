@@ -1144,6 +1144,7 @@ struct sinv_mlp_s {
     float* grad = nullptr;
     float* partial = nullptr;
     float* loss_partial = nullptr;
+    int32_t* dstatus = nullptr;  // first device error of the asynchronous calls (bounded waits)
 };
 
 static uint64_t splitmix64(uint64_t x) {
@@ -1159,7 +1160,7 @@ void sinv_mlp_destroy(sinv_mlp m) {
     if (!m) return;
     cudaSetDevice(m->device);
     for (void* p : {(void*)m->theta, (void*)m->mom1, (void*)m->mom2, (void*)m->grad, (void*)m->partial,
-                    (void*)m->loss_partial})
+                    (void*)m->loss_partial, (void*)m->dstatus})
         if (p) cudaFree(p);
     delete m;
 }
@@ -1181,6 +1182,8 @@ sinv_status sinv_mlp_create(int32_t device, uint64_t seed, int64_t max_batch, si
     if (e == cudaSuccess) e = cudaMalloc((void**)&m->grad, P);
     if (e == cudaSuccess) e = cudaMalloc((void**)&m->partial, (size_t)nblk * P);
     if (e == cudaSuccess) e = cudaMalloc((void**)&m->loss_partial, (size_t)nblk * sizeof(float) + 16);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->dstatus, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(m->dstatus, 0, sizeof(int32_t));
     if (e == cudaSuccess) e = mlp_configure();
     if (e != cudaSuccess) {
         sinv_mlp_destroy(m);
@@ -1271,10 +1274,26 @@ sinv_status sinv_mlp_train_step(sinv_mlp m, const void* X, const float* y, const
 sinv_status sinv_mlp_predict(sinv_mlp m, const void* X, const float* scale, const double* N, int64_t count, double* out,
                              void* stream) {
     if (!m || count < 0 || (count > 0 && (!X || !scale || !N || !out))) return SINV_ERR_INVALID_ARG;
+    if (((uintptr_t)X & 15) != 0) return SINV_ERR_INVALID_ARG;  // rows are read as 16-byte vectors
     cudaSetDevice(m->device);
-    return mlp_predict_launch(X, scale, N, count, m->theta, out, m->num_sms, (cudaStream_t)stream) == cudaSuccess
+    return mlp_predict_launch(X, scale, N, count, m->theta, out, m->dstatus, kMlpWaitLimit, m->num_sms,
+                              (cudaStream_t)stream) == cudaSuccess
                ? SINV_OK
                : SINV_ERR_CUDA;
+}
+
+sinv_status sinv_mlp_sync_status(sinv_mlp m, void* stream) {
+    if (!m) return SINV_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(m->device);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    int32_t st = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&st, m->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return SINV_ERR_CUDA;
+    if (st != 0) {
+        cudaMemset(m->dstatus, 0, sizeof(int32_t));
+        return st == SINV_ERR_TIMEOUT ? SINV_ERR_TIMEOUT : SINV_ERR_CUDA;
+    }
+    return SINV_OK;
 }
 
 sinv_status sinv_trace_enable(sinv_handle h, int enable) {

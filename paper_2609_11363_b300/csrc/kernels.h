@@ -232,6 +232,8 @@ constexpr int kOffB2 = kOffW2 + kMlpH * kMlpH;
 constexpr int kOffW3 = kOffB2 + kMlpH;
 constexpr int kOffB3 = kOffW3 + kMlpH;
 constexpr int kMlpParams = kOffB3 + 1;
+// polls of a tensor-core completion wait before the kernel records SINV_ERR_TIMEOUT
+constexpr int64_t kMlpWaitLimit = int64_t(1) << 24;
 cudaError_t mlp_configure();
 int mlp_train_blocks(int64_t count);
 cudaError_t mlp_features_launch(int64_t n, const int64_t* Srp, const int32_t* Sc, const int64_t* Lrp,
@@ -244,6 +246,6 @@ cudaError_t mlp_grad_launch(const void* X, const float* y, const int64_t* idx, i
                             float* partial, float* loss_partial, float* grad, float* loss, cudaStream_t st);
 cudaError_t mlp_adam_launch(float* theta, float* m, float* v, const float* g, float lr, int step, cudaStream_t st);
 cudaError_t mlp_predict_launch(const void* X, const float* scale, const double* N, int64_t count, const float* theta,
-                               double* out, int num_sms, cudaStream_t st);
+                               double* out, int32_t* status, int64_t wait_limit, int num_sms, cudaStream_t st);
 
 }  // namespace sinv

@@ -13,6 +13,7 @@
 
 #include "device.cuh"
 #include "kernels.h"
+#include "tc.cuh"
 
 namespace sinv {
 
@@ -282,19 +283,153 @@ __global__ void adam_kernel(float* __restrict__ theta, float* __restrict__ m, fl
     }
 }
 
-__global__ void __launch_bounds__(kB) predict_kernel(const __nv_bfloat16* __restrict__ X, const float* __restrict__ scale,
-                                                     const double* __restrict__ N, int64_t count,
-                                                     const float* __restrict__ theta, double* __restrict__ out) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Weights& w = *reinterpret_cast<Weights*>(smem_raw);
-    load_weights(w, theta);
-    __syncthreads();
-    float x[kMlpF], h1[kMlpH], h2[kMlpH];
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
-        load_x(X, e, x);
-        const float f = mlp_eval(w, x, h1, h2);
-        out[e] = N[e] + (double)scale[e] * (double)f;
+// ---- inference on the tensor cores ---------------------------------------------------
+// A CTA of four warps (thread t owns row t of a tile of 128 entries) loops over
+// tiles.  Layer 1 (128 x 16 features times W1, K = 16) and layer 2 (128 x 64 hidden
+// times W2, K = 64) are tcgen05 MMAs with BF16 operands in shared memory and FP32
+// accumulators in tensor memory (columns 0-63: layer 1, 64-127: layer 2).  The
+// epilogues read the accumulators back (tcgen05.ld), add the bias and apply ReLU;
+// the first hidden layer is rounded to BF16 as the operand of layer 2, the second
+// stays FP32 for the output layer's dot product.
+constexpr int kTcRows = 128;
+constexpr int kTcCols = 128;   // TMEM columns per CTA
+// dynamic shared memory per CTA: sized so that at most four CTAs share an SM,
+// whose 512 TMEM columns then hold all four allocations
+constexpr int kPredictSmem = 52 * 1024;
+constexpr uint32_t kIdescL = tc::instr_desc(tc::kFmtBF16, 128, kMlpH);
+
+struct __align__(128) PredictSmem {
+    uint8_t w1t[kMlpH * kMlpF * 2];     // B of layer 1: row j = output unit, K = 16 inputs (2 chunks)
+    uint8_t w2t[kMlpH * kMlpH * 2];     // B of layer 2: K = 64 (8 chunks)
+    uint8_t xa[kTcRows * kMlpF * 2];    // A of layer 1
+    uint8_t ha[kTcRows * kMlpH * 2];    // A of layer 2
+    float b1[kMlpH], b2[kMlpH], w3[kMlpH];
+    float b3;
+    uint32_t tmem;
+    uint64_t mbar;
+};
+
+__device__ __forceinline__ void st_bf16x8(uint8_t* dst, const float* v) {
+    __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) h[i] = __float2bfloat16(v[i]);
+    *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(h);
+}
+
+__global__ void __launch_bounds__(kTcRows) predict_tc_kernel(const __nv_bfloat16* __restrict__ X,
+                                                             const float* __restrict__ scale,
+                                                             const double* __restrict__ N, int64_t count,
+                                                             const float* __restrict__ theta,
+                                                             double* __restrict__ out, int32_t* status,
+                                                             int64_t wait_limit) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    PredictSmem& S = *reinterpret_cast<PredictSmem*>(smem_raw);
+    const int t = threadIdx.x, warp = t >> 5;
+    // weights: B operands in the K-major layout (element (j, k) = W[k][j]), BF16
+    for (int p = t; p < kMlpH * kMlpF; p += kTcRows) {
+        const int j = p / kMlpF, k = p % kMlpF;
+        *reinterpret_cast<__nv_bfloat16*>(S.w1t + tc::kmajor_offset(j, k, kMlpF / 8, 2)) =
+            __float2bfloat16(theta[kOffW1 + k * kMlpH + j]);
     }
+    for (int p = t; p < kMlpH * kMlpH; p += kTcRows) {
+        const int j = p / kMlpH, k = p % kMlpH;
+        *reinterpret_cast<__nv_bfloat16*>(S.w2t + tc::kmajor_offset(j, k, kMlpH / 8, 2)) =
+            __float2bfloat16(theta[kOffW2 + k * kMlpH + j]);
+    }
+    if (t < kMlpH) {
+        S.b1[t] = bf(theta[kOffB1 + t]);
+        S.b2[t] = bf(theta[kOffB2 + t]);
+        S.w3[t] = bf(theta[kOffW3 + t]);
+    }
+    if (t == 0) {
+        S.b3 = bf(theta[kOffB3]);
+        tc::mbar_init(&S.mbar, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(&S.tmem, kTcCols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = S.tmem;
+    const uint32_t d1 = tmem, d2 = tmem + kMlpH;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const uint64_t dw1 = tc::smem_desc(tc::smem_u32(S.w1t), 128, (kMlpF / 8) * 128);
+    const uint64_t dx = tc::smem_desc(tc::smem_u32(S.xa), 128, (kMlpF / 8) * 128);
+    uint32_t phase = 0;
+    bool ok = true;
+    const int64_t ntiles = (count + kTcRows - 1) / kTcRows;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int64_t e = tile * kTcRows + t;
+        const bool valid = e < count;
+        // features of row t into the A tile of layer 1
+        uint4 xa0 = make_uint4(0, 0, 0, 0), xa1 = xa0;
+        if (valid) {
+            const uint4* p = reinterpret_cast<const uint4*>(X + e * kMlpF);
+            xa0 = __ldcs(p);
+            xa1 = __ldcs(p + 1);
+        }
+        *reinterpret_cast<uint4*>(S.xa + tc::kmajor_offset(t, 0, kMlpF / 8, 2)) = xa0;
+        *reinterpret_cast<uint4*>(S.xa + tc::kmajor_offset(t, 8, kMlpF / 8, 2)) = xa1;
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (t == 0) {
+            tc::fence_after_sync();
+            tc::mma_bf16(d1, dx, dw1, kIdescL, false);
+            tc::commit(&S.mbar);
+        }
+        const double n_e = valid ? __ldcs(N + e) : 0.0;
+        const float s_e = valid ? __ldcs(scale + e) : 0.f;
+        ok = tc::mbar_wait(&S.mbar, phase, status, wait_limit);
+        phase ^= 1u;
+        tc::fence_after_sync();
+        // layer-1 epilogue: bias, ReLU, BF16 into the A tile of layer 2
+#pragma unroll
+        for (int c0 = 0; c0 < kMlpH; c0 += 16) {
+            float v[16];
+            tc::ld16(d1 + lane_base + c0, v);
+            tc::ld_wait();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + S.b1[c0 + i], 0.f);
+            st_bf16x8(S.ha + tc::kmajor_offset(t, c0, kMlpH / 8, 2), v);
+            st_bf16x8(S.ha + tc::kmajor_offset(t, c0 + 8, kMlpH / 8, 2), v + 8);
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (t == 0) {
+            tc::fence_after_sync();
+#pragma unroll
+            for (int kk = 0; kk < kMlpH / 16; ++kk) {
+                const uint64_t da = tc::smem_desc(tc::smem_u32(S.ha) + kk * 256, 128, (kMlpH / 8) * 128);
+                const uint64_t db = tc::smem_desc(tc::smem_u32(S.w2t) + kk * 256, 128, (kMlpH / 8) * 128);
+                tc::mma_bf16(d2, da, db, kIdescL, kk > 0);
+            }
+            tc::commit(&S.mbar);
+        }
+        ok = tc::mbar_wait(&S.mbar, phase, status, wait_limit) && ok;
+        phase ^= 1u;
+        tc::fence_after_sync();
+        // layer-2 epilogue and the output unit
+        float o = S.b3;
+#pragma unroll
+        for (int c0 = 0; c0 < kMlpH; c0 += 16) {
+            float v[16];
+            tc::ld16(d2 + lane_base + c0, v);
+            tc::ld_wait();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) o = fmaf(fmaxf(v[i] + S.b2[c0 + i], 0.f), S.w3[c0 + i], o);
+        }
+        if (valid) __stcs(out + e, n_e + (double)s_e * (double)o);
+        tc::fence_before_sync();
+        // every thread leaves a tile only after the MMAs have finished with its
+        // operand tiles and accumulators (the waits above), so they can be reused
+        ok = __syncthreads_and(ok) != 0;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, kTcCols);
 }
 
 }  // namespace
@@ -302,7 +437,8 @@ __global__ void __launch_bounds__(kB) predict_kernel(const __nv_bfloat16* __rest
 cudaError_t mlp_configure() {
     cudaError_t e = cudaFuncSetAttribute(fwd_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(predict_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Weights));
+    static_assert(sizeof(PredictSmem) <= kPredictSmem, "predict shared memory");
+    return cudaFuncSetAttribute(predict_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPredictSmem);
 }
 
 int mlp_train_blocks(int64_t count) { return (int)((count + kB - 1) / kB); }
@@ -350,11 +486,14 @@ cudaError_t mlp_adam_launch(float* theta, float* m, float* v, const float* g, fl
 }
 
 cudaError_t mlp_predict_launch(const void* X, const float* scale, const double* N, int64_t count, const float* theta,
-                               double* out, int num_sms, cudaStream_t st) {
+                               double* out, int32_t* status, int64_t wait_limit, int num_sms, cudaStream_t st) {
     if (count == 0) return cudaSuccess;
+    const int64_t tiles = (count + kTcRows - 1) / kTcRows;
+    // four CTAs per SM: their 128 TMEM columns each fill the SM's 512
+    const int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms * 4);
     trace_begin("mlp_predict", st);
-    predict_kernel<<<num_sms * 8, kB, sizeof(Weights), st>>>(reinterpret_cast<const __nv_bfloat16*>(X), scale, N, count,
-                                                             theta, out);
+    predict_tc_kernel<<<grid, kTcRows, kPredictSmem, st>>>(
+        reinterpret_cast<const __nv_bfloat16*>(X), scale, N, count, theta, out, status, wait_limit);
     trace_end(st);
     return cudaGetLastError();
 }

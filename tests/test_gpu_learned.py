@@ -64,31 +64,34 @@ def test_mlp_gradient_matches_oracle_and_adam_step():
     assert np.max(np.abs(th1 - want)) <= 1e-6
 
 
-def _predict_ref(theta_bf16, Xr, N, sc):
-    """N + s * f(x) with the oracle network on the BF16-rounded weights and features."""
-    return N + sc.astype(np.float64) * omlp.forward(theta_bf16, Xr, F, H)
-
-
 def _assert_predict_close(got, N, sc, theta_bf16, Xr):
-    """Entry by entry.  f is evaluated with FP32 sums: three layers of at most 64
-    terms each, so its error is bounded by a few units of 2^-24 times the sum of
-    the magnitudes of the terms (|h|.|W|, taken from the oracle in FP64)."""
+    """Entry by entry against N + s * oracle.mlp.forward(theta, X, act_bf16=True):
+    BF16 weights and features, the first hidden layer rounded to BF16 (the
+    operand of the tensor-core layer).  The sums are FP32 (tensor-core
+    accumulators and the output dot product): three layers of at most 65 terms,
+    so f is off by at most a few units of 2^-24 times the sum of the magnitudes
+    of the terms (|h|.|W|, from the oracle in FP64) -- the tight bound.  Where the
+    device's FP32 sum and the exact one straddle a BF16 rounding boundary, the two
+    sides round that hidden unit one BF16 unit (2^-8 relative) apart: the loose
+    bound allows that for every unit; at most 2 % of the entries may need it."""
     W1, b1, W2, b2, W3, b3 = omlp.split(theta_bf16, F, H)
-    h1 = np.maximum(Xr @ W1 + b1, 0.0)
+    h1 = omlp.bf16_round(np.maximum(Xr @ W1 + b1, 0.0))
     h2 = np.maximum(h1 @ W2 + b2, 0.0)
+    f_ref = h2 @ W3 + b3[0]
+    assert np.array_equal(f_ref, omlp.forward(theta_bf16, Xr, F, H, act_bf16=True))
     aW2, aW3 = np.abs(W2), np.abs(W3)
     mag = ((np.abs(Xr) @ np.abs(W1) + np.abs(b1)) @ aW2) @ aW3      # layer-1 sums carried through
     mag += (np.abs(h1) @ aW2 + np.abs(b2)) @ aW3                      # layer-2 sums
     mag += np.abs(h2) @ aW3 + abs(b3[0])                              # output sum
-    f_ref = h2 @ W3 + b3[0]
+    tight = 2 * (H + 1) * 2.0 ** -24 * mag + 1e-30
+    loose = tight + 2.0 ** -8 * (np.abs(h1) @ aW2) @ aW3
     f_got = (got - N) / sc.astype(np.float64)
-    bound = 2 * (H + 1) * 2.0 ** -24 * mag + 1e-30
-    assert np.all(np.abs(f_got - f_ref) <= bound), float(np.max(np.abs(f_got - f_ref) / bound))
-    want = _predict_ref(theta_bf16, Xr, N, sc)
-    assert np.all(np.abs(got - want) <= sc * bound + 4 * np.finfo(float).eps * np.abs(want))
+    err = np.abs(f_got - f_ref)
+    assert np.all(err <= loose), float(np.max(err / loose))
+    assert np.mean(err <= tight) >= 0.98, float(np.mean(err <= tight))
 
 
-@pytest.mark.parametrize("count", [1, 127, 128, 1000, 4099])
+@pytest.mark.parametrize("count", [1, 127, 128, 1000, 4099, 300001])
 def test_mlp_predict_matches_oracle_entry_by_entry(count):
     """sinv_mlp_predict against N + s * oracle.mlp.forward(bf16(theta), bf16(X)) on
     random features and weights: every entry, full tiles and a ragged tail."""
@@ -101,6 +104,7 @@ def test_mlp_predict_matches_oracle_entry_by_entry(count):
     sc = rng.uniform(0.5, 2.0, count).astype(np.float32)
     N = rng.standard_normal(count)
     got = net.predict(Xb, _dev(sc), _dev(N)).cpu().numpy()
+    net.sync_status()
     Xr = Xb.float().cpu().numpy().astype(np.float64)
     _assert_predict_close(got, N, sc, _bf16_round(th), Xr)
 
@@ -124,6 +128,7 @@ def test_mlp_predict_on_diffusion_features():
     N = st[3].contiguous()
     got = net.predict(X, sc, N).cpu().numpy()
     h.sync_status()
+    net.sync_status()
     th = _bf16_round(net.get_params())
     Xr = X.float().cpu().numpy().astype(np.float64)
     _assert_predict_close(got, N.cpu().numpy(), sc.cpu().numpy(), th, Xr)
