@@ -57,7 +57,7 @@ typedef enum {
     SINV_FP64 = 0,      /* native FP64 throughout                                  */
     SINV_FP32 = 1,      /* FP32 products and sums; pivot inverses and the diagonal
                            accumulation of each pivot block in FP64                */
-    SINV_FP32X2 = 2     /* FP64-class results with the NInv product on S run on the
+    SINV_FP32X2 = 2,    /* FP64-class results with the NInv product on S run on the
                            FP32 pipes: every FP64 operand is split into an FP32
                            high part and an FP32 low part, a product keeps the
                            high-by-high product exactly plus both cross terms, and
@@ -69,6 +69,19 @@ typedef enum {
                            Values of W or D^{-1}W at or above 2^100 in magnitude
                            are reported as SINV_ERR_UNSUPPORTED by the next
                            sinv_sync_status.                                       */
+    SINV_TF32_FP32ACC = 3,  /* sinv_selinv only (Section 2.1, Eqs. (4)-(5)): the
+                           supernodes of the leading levels whose row set C is a
+                           contiguous range of rows run on the tensor cores
+                           (tcgen05): G~_CC L_CJ with every operand split into a
+                           TF32 high and a TF32 low part, the high-by-high
+                           products and the cross terms in two FP32 accumulators
+                           added in FP64; L_JJ^{-1}, the pivot inverses, the sum
+                           of L_CJ^T G~ L_CJ over C and G_JJ in FP64.  The other
+                           supernodes run SINV_FP64.  Stated error: normwise
+                           1e-6 against the FP64 oracle.  Other calls return
+                           SINV_ERR_UNSUPPORTED (no dense contraction there).   */
+    SINV_BF16_FP32ACC = 4   /* the same with BF16 high and low parts; stated error:
+                           normwise 1e-5.                                          */
 } sinv_precision;
 
 typedef struct sinv_handle_s *sinv_handle;
@@ -349,6 +362,10 @@ typedef struct {
     int64_t einv_levels_fwd;  /* dependency levels of the solve with L (one launch each),
                                  0 until sinv_einv_analyse ran                          */
     int64_t einv_levels_bwd;  /* dependency levels of the solve with L^T                */
+    int64_t tc_levels;        /* leading levels run by the tensor-core forms of SelInv  */
+    int64_t tc_supernodes;    /* supernodes in them                                     */
+    int64_t tc_pairs;         /* sum of |C|^2 over them (the contraction's size)        */
+    int64_t tc_mirror_bytes;  /* their symmetric band copy of G                         */
 } sinv_stats;
 sinv_status sinv_get_stats(sinv_handle h, sinv_stats *out);
 
@@ -370,6 +387,19 @@ typedef struct {
     double total_ms;
 } sinv_kernel_time;
 sinv_status sinv_trace_enable(sinv_handle h, int enable);
+/* Per-supernode timeline of sinv_selinv, for the analysis of its dependency
+ * chain (Section 2.1: a supernode starts when the supernodes owning its rows C
+ * have finished).  While enabled, every sinv_selinv records device timestamps
+ * (globaltimer, nanoseconds) for each supernode J; sinv_timeline_read writes
+ * four per supernode into stamps[4J .. 4J+3] (host array of 4 * n_supernodes,
+ * n_supernodes as in sinv_get_stats): the earliest start of any of its work
+ * items, the latest moment a part saw its dependencies published, the latest
+ * end of a part's contraction, and its publication.  Unset stamps read 0 (the
+ * first one all ones).  The read synchronizes `stream`.  Recording adds atomic
+ * operations to the kernels: time the path with the timeline disabled.
+ * Errors: SINV_ERR_INVALID_ARG (not enabled, wrong count), SINV_ERR_OOM. */
+sinv_status sinv_timeline_enable(sinv_handle h, int enable);
+sinv_status sinv_timeline_read(sinv_handle h, uint64_t *stamps, int64_t n_supernodes, void *stream);
 sinv_status sinv_trace_read(sinv_handle h, sinv_kernel_time *out, int max_entries, int *count, int reset);
 
 const char *sinv_status_string(sinv_status s);

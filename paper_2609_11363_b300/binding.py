@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libsinv.so")
 _lib = None
 
-PREC = {"fp64": 0, "fp32": 1, "fp32x2": 2}
+PREC = {"fp64": 0, "fp32": 1, "fp32x2": 2, "tf32": 3, "bf16": 4}
 STATUS = {
     0: "SINV_OK", 1: "SINV_ERR_INVALID_ARG", 2: "SINV_ERR_PATTERN", 3: "SINV_ERR_SINGULAR_PIVOT",
     4: "SINV_ERR_OOM", 5: "SINV_ERR_CUDA", 6: "SINV_ERR_TIMEOUT", 7: "SINV_ERR_UNSUPPORTED",
@@ -32,7 +32,7 @@ EXPORTS = [
     "sinv_spai_analyse", "sinv_spai_pattern", "sinv_spai", "sinv_einv_analyse", "sinv_einv_lanczos",
     "sinv_mlp_param_count", "sinv_mlp_create", "sinv_mlp_destroy", "sinv_mlp_get_params", "sinv_mlp_set_params",
     "sinv_mlp_features", "sinv_mlp_targets", "sinv_mlp_grad", "sinv_mlp_train_step", "sinv_mlp_predict",
-    "sinv_mlp_sync_status",
+    "sinv_mlp_sync_status", "sinv_timeline_enable", "sinv_timeline_read",
 ]
 
 
@@ -59,7 +59,8 @@ class _Stats(ctypes.Structure):
         ("product_stream", ctypes.c_int64), ("selinv_flops", ctypes.c_int64), ("selinv_bytes", ctypes.c_int64),
         ("ninv_index_bytes", ctypes.c_int64), ("product_hits", ctypes.c_int64), ("spai_entries", ctypes.c_int64),
         ("spai_cols_warp", ctypes.c_int64), ("spai_cols_cta", ctypes.c_int64), ("spai_nnz_P", ctypes.c_int64),
-        ("einv_levels_fwd", ctypes.c_int64), ("einv_levels_bwd", ctypes.c_int64)]
+        ("einv_levels_fwd", ctypes.c_int64), ("einv_levels_bwd", ctypes.c_int64), ("tc_levels", ctypes.c_int64),
+        ("tc_supernodes", ctypes.c_int64), ("tc_pairs", ctypes.c_int64), ("tc_mirror_bytes", ctypes.c_int64)]
 
 
 def lib_path() -> str:
@@ -109,6 +110,8 @@ def load_library():
     lib.sinv_mlp_train_step.argtypes = [H, P, P, P, I64, ctypes.c_float, P, P]
     lib.sinv_mlp_predict.argtypes = [H, P, P, P, I64, P, P]
     lib.sinv_mlp_sync_status.argtypes = [H, P]
+    lib.sinv_timeline_enable.argtypes = [H, ctypes.c_int]
+    lib.sinv_timeline_read.argtypes = [H, P, I64, P]
     lib.sinv_batch_symbolic.argtypes = [ctypes.c_int32, P, P, P, P, ctypes.POINTER(_Opts), ctypes.POINTER(H)]
     lib.sinv_batch_layout.argtypes = [H, ctypes.POINTER(ctypes.c_int32), P, P, P, P]
     lib.sinv_lowrank_correct_noalloc.argtypes = [I64, P, P, ctypes.c_int, P, P, P, P]
@@ -519,6 +522,18 @@ class Handle:
         cnt = ctypes.c_int()
         self._check(self._lib.sinv_trace_read(self._h, buf, 64, ctypes.byref(cnt), int(bool(reset))))
         return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(cnt.value)}
+
+    def timeline(self, enable=True):
+        """Record the per-supernode timeline of the following selinv calls."""
+        self._check(self._lib.sinv_timeline_enable(self._h, 1 if enable else 0))
+
+    def timeline_read(self, stream=None) -> np.ndarray:
+        """[n_supernodes, 4] uint64 globaltimer stamps (ns) of the last selinv: start,
+        dependencies published, contraction done, published."""
+        ns = int(self.stats()["n_supernodes"])
+        out = np.zeros((ns, 4), dtype=np.uint64)
+        self._check(self._lib.sinv_timeline_read(self._h, _np_ptr(out), ns, _stream_ptr(stream)))
+        return out
 
     def debug_wait_timeout(self, stream=None) -> int:
         return int(self._lib.sinv_debug_wait_timeout(self._h, _stream_ptr(stream)))

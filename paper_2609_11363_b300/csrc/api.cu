@@ -127,6 +127,18 @@ struct sinv_handle_s {
     int32_t* dstatus = nullptr;
     uint32_t* ddebug_flag = nullptr;
     double* dscratch = nullptr;
+    // tensor-core tier of SelInv (allocated by the first call of a tensor-core form)
+    WorkItem* dtc_items = nullptr;
+    int32_t* dtc_map = nullptr;
+    int32_t* dtc_deps = nullptr;
+    int32_t* dtc_ticket = nullptr;
+    double* dtc_mirror = nullptr;
+    uint32_t* dtc_arrive_t = nullptr;
+    double* dtc_z = nullptr;
+    bool tc_ready = false;
+    // per-supernode timeline of SelInv (allocated while enabled)
+    unsigned long long* dtl_first = nullptr;
+    unsigned long long* dtl_last = nullptr;
     void* dwork = nullptr;
     size_t work_bytes = 0;
     int grid = 0;
@@ -217,7 +229,8 @@ void free_all(sinv_handle h) {
     void* ptrs[] = {h->dSrp, h->dSc, h->dSdiag, h->dl2s, h->dLrp, h->dLcp, h->dLri, h->dLcsr, h->ddpos, h->dpstart,
                     h->dsn, h->dorder, h->downer, h->dCrow, h->dLmap, h->dJJl, h->dJJs, h->dhit_ik, h->dhit_pos,
                     h->dhrow, h->ditems, h->dxsum_off, h->dxsum, h->darrive, h->ddone, h->depoch, h->dticket, h->dstatus, h->ddebug_flag, h->dscratch, h->dwork, h->dWcp,
-                    h->dWr, h->dgrp};
+                    h->dWr, h->dgrp, h->dtc_items, h->dtc_map, h->dtc_deps, h->dtc_ticket, h->dtc_mirror, h->dtc_arrive_t,
+                    h->dtc_z, h->dtl_first, h->dtl_last};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     ninv_maps_free(h->X);
@@ -237,6 +250,7 @@ sinv_status ensure_work(sinv_handle h, size_t bytes) {
 }
 
 bool valid_prec(int p) { return p == SINV_FP64 || p == SINV_FP32 || p == SINV_FP32X2; }
+bool tc_prec(int p) { return p == SINV_TF32_FP32ACC || p == SINV_BF16_FP32ACC; }
 
 // numeric calls need a handle that lives on a device
 bool on_device(sinv_handle h) {
@@ -371,7 +385,8 @@ sinv_status sinv_symbolic(int64_t n, const int64_t* L_rowptr, const int32_t* L_c
         *out = h;
         return cuda_fail(h, e, "device state");
     }
-    if ((e = selinv_configure()) != cudaSuccess || (e = ninv_configure()) != cudaSuccess ||
+    if ((e = selinv_configure()) != cudaSuccess || (e = selinv_tc_configure()) != cudaSuccess ||
+        (e = ninv_configure()) != cudaSuccess ||
         (e = ninv_maps_configure()) != cudaSuccess) {
         *out = h;
         return cuda_fail(h, e, "kernel attributes");
@@ -503,6 +518,10 @@ sinv_status sinv_get_stats(sinv_handle h, sinv_stats* s) {
     s->spai_nnz_P = h->spai_analysed ? h->Q.nnzP : 0;
     s->einv_levels_fwd = h->einv_analysed && !h->E.fwd_ptr.empty() ? (int64_t)h->E.fwd_ptr.size() - 1 : 0;
     s->einv_levels_bwd = h->einv_analysed && !h->E.bwd_ptr.empty() ? (int64_t)h->E.bwd_ptr.size() - 1 : 0;
+    s->tc_levels = P.tc_levels;
+    s->tc_supernodes = P.tc_sn;
+    s->tc_pairs = P.tc_pairs;
+    s->tc_mirror_bytes = P.tc_levels > 0 ? (P.n - P.tc_row0) * P.tc_width * (int64_t)sizeof(double) : 0;
     return SINV_OK;
 }
 
@@ -514,9 +533,34 @@ sinv_status sinv_get_supernodes(sinv_handle h, const int32_t** sn_start, const i
     return SINV_OK;
 }
 
+// device state of the tensor-core tier: its work items, ticket, mirror and partial sums
+static sinv_status ensure_tc(sinv_handle h) {
+    if (h->tc_ready) return SINV_OK;
+    const HostPlan& P = h->P;
+    cudaError_t e = upload(&h->dtc_items, P.tc_items);
+    if (e == cudaSuccess) e = upload(&h->dtc_map, P.tc_map);
+    if (e == cudaSuccess) e = upload(&h->dtc_deps, P.tc_deps);
+    const size_t mirror = (size_t)(P.n - P.tc_row0) * (size_t)P.tc_width;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->dtc_ticket, 64);
+    if (e == cudaSuccess) e = cudaMemset(h->dtc_ticket, 0, 64);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->dtc_mirror, std::max<size_t>(mirror, 1) * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMalloc((void**)&h->dtc_arrive_t, std::max<int64_t>(P.tc_t_total, 1) * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->dtc_z, std::max<int64_t>(P.tc_z_total, 1) * sizeof(double));
+    if (e != cudaSuccess) {
+        if (e == cudaErrorMemoryAllocation) {
+            set_err(h, "device allocation of the tensor-core tier failed");
+            return SINV_ERR_OOM;
+        }
+        return cuda_fail(h, e, "tensor-core tier state");
+    }
+    h->tc_ready = true;
+    return SINV_OK;
+}
+
 sinv_status sinv_selinv(sinv_handle h, const double* L_val, const double* D_val, sinv_precision prec, double* G_S,
                         void* stream) {
-    if (!h || !valid_prec(prec)) return SINV_ERR_INVALID_ARG;
+    if (!h || !(valid_prec(prec) || tc_prec(prec))) return SINV_ERR_INVALID_ARG;
     if (!on_device(h)) return SINV_ERR_INVALID_ARG;
     const HostPlan& P = h->P;
     if (P.n == 0) return SINV_OK;
@@ -562,11 +606,48 @@ sinv_status sinv_selinv(sinv_handle h, const double* L_val, const double* D_val,
     a.xsum_off = h->dxsum_off;
     a.xsum = h->dxsum;
     a.arrive = h->darrive;
-    if ((e = selinv_prepare(h->depoch, h->dticket, st)) != cudaSuccess) return cuda_fail(h, e, "selinv prepare");
-    if (P.xsum_total > 0 &&  // partial sums and arrival counts of the supernodes split over CTAs
+    a.item0 = 0;
+    a.tl.first = h->dtl_first;
+    a.tl.last = h->dtl_last;
+    if (h->dtl_first &&
+        ((e = cudaMemsetAsync(h->dtl_first, 0xFF, P.sn.size() * sizeof(unsigned long long), st)) != cudaSuccess ||
+         (e = cudaMemsetAsync(h->dtl_last, 0, 3 * P.sn.size() * sizeof(unsigned long long), st)) != cudaSuccess))
+        return cuda_fail(h, e, "selinv timeline");
+    const bool tc = tc_prec(prec) && P.tc_levels > 0;
+    if (tc) {
+        sinv_status s = ensure_tc(h);
+        if (s != SINV_OK) return s;
+    }
+    if ((e = selinv_prepare(h->depoch, h->dticket, st, tc ? h->dtc_ticket : nullptr)) != cudaSuccess)
+        return cuda_fail(h, e, "selinv prepare");
+    if ((P.xsum_total > 0 || tc) &&  // partial sums and arrival counts of the supernodes split over CTAs
         ((e = cudaMemsetAsync(h->dxsum, 0, (size_t)P.xsum_total * sizeof(double), st)) != cudaSuccess ||
          (e = cudaMemsetAsync(h->darrive, 0, P.sn.size() * sizeof(uint32_t), st)) != cudaSuccess))
         return cuda_fail(h, e, "selinv prepare");
+    if (tc) {
+        // the leading levels on the tensor cores, then the rest in FP64 from item rest_first
+        const size_t mirror = (size_t)(P.n - P.tc_row0) * (size_t)P.tc_width;
+        if ((e = cudaMemsetAsync(h->dtc_mirror, 0, mirror * sizeof(double), st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(h->dtc_arrive_t, 0, (size_t)P.tc_t_total * sizeof(uint32_t), st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(h->dtc_z, 0, (size_t)P.tc_z_total * sizeof(double), st)) != cudaSuccess)
+            return cuda_fail(h, e, "selinv tensor-core prepare");
+        TcArgs t;
+        t.tcmap = h->dtc_map;
+        t.deps = h->dtc_deps;
+        t.items = h->dtc_items;
+        t.nitems = (int32_t)P.tc_items.size();
+        t.ticket = h->dtc_ticket;
+        t.mirror = h->dtc_mirror;
+        t.row0 = P.tc_row0;
+        t.band = P.tc_band;
+        t.width = P.tc_width;
+        t.arrive_t = h->dtc_arrive_t;
+        t.zacc = h->dtc_z;
+        if ((e = selinv_tc_launch(a, t, prec == SINV_TF32_FP32ACC ? 2 : 1, G_S, st)) != cudaSuccess)
+            return cuda_fail(h, e, "selinv tensor-core launch");
+        a.item0 = (int32_t)P.rest_first;
+        if (P.rest_first >= (int64_t)P.items.size()) return SINV_OK;
+    }
     if ((e = selinv_launch(a, prec == SINV_FP32 ? 1 : 0, h->dwork, G_S, st, h->grid)) != cudaSuccess)
         return cuda_fail(h, e, "selinv launch");
     return SINV_OK;
@@ -594,6 +675,10 @@ sinv_status sinv_ninv_stack(sinv_handle h, const double* L_val, const double* D_
 
 static sinv_status ninv_common(sinv_handle h, const double* L_val, const double* D_val, int m, double delta,
                                sinv_precision prec, double* N_S, double* N_stack, void* stream) {
+    if (h && tc_prec(prec)) {
+        set_err(h, "the tensor-core forms apply to sinv_selinv only");
+        return SINV_ERR_UNSUPPORTED;
+    }
     if (!h || !valid_prec(prec) || m < 0) return SINV_ERR_INVALID_ARG;
     if (!on_device(h)) return SINV_ERR_INVALID_ARG;
     if (m > 30) {
@@ -706,6 +791,10 @@ sinv_status sinv_mix(sinv_handle h, const double* G_S, const double* N_S, double
 
 sinv_status sinv_lowrank_correct(sinv_handle h, int k, const double* V, const double* lambda, sinv_precision prec,
                                  double* X_S, void* stream) {
+    if (h && tc_prec(prec)) {
+        set_err(h, "the tensor-core forms apply to sinv_selinv only");
+        return SINV_ERR_UNSUPPORTED;
+    }
     if (!h || k < 0 || !valid_prec(prec)) return SINV_ERR_INVALID_ARG;
     if (!on_device(h)) return SINV_ERR_INVALID_ARG;
     if (k > kLowrankKMax) {
@@ -1327,6 +1416,54 @@ sinv_status sinv_trace_read(sinv_handle h, sinv_kernel_time* out, int max_entrie
     }
     *count = std::min(c, max_entries);
     if (reset) h->tracer->agg.clear();
+    return SINV_OK;
+}
+
+sinv_status sinv_timeline_enable(sinv_handle h, int enable) {
+    if (!h) return SINV_ERR_INVALID_ARG;
+    if (!on_device(h)) return SINV_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    const size_t ns = std::max<size_t>(h->P.sn.size(), 1);
+    if (enable && !h->dtl_first) {
+        if ((e = cudaMalloc((void**)&h->dtl_first, ns * sizeof(unsigned long long))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&h->dtl_last, 3 * ns * sizeof(unsigned long long))) != cudaSuccess ||
+            (e = cudaMemset(h->dtl_first, 0xFF, ns * sizeof(unsigned long long))) != cudaSuccess ||
+            (e = cudaMemset(h->dtl_last, 0, 3 * ns * sizeof(unsigned long long))) != cudaSuccess) {
+            if (h->dtl_first) cudaFree(h->dtl_first);
+            if (h->dtl_last) cudaFree(h->dtl_last);
+            h->dtl_first = nullptr;
+            h->dtl_last = nullptr;
+            return e == cudaErrorMemoryAllocation ? SINV_ERR_OOM : cuda_fail(h, e, "timeline");
+        }
+    }
+    if (!enable && h->dtl_first) {
+        cudaFree(h->dtl_first);
+        cudaFree(h->dtl_last);
+        h->dtl_first = nullptr;
+        h->dtl_last = nullptr;
+    }
+    return SINV_OK;
+}
+
+sinv_status sinv_timeline_read(sinv_handle h, uint64_t* stamps, int64_t n_supernodes, void* stream) {
+    if (!h || !stamps || n_supernodes != (int64_t)h->P.sn.size()) return SINV_ERR_INVALID_ARG;
+    if (!h->dtl_first) {
+        set_err(h, "the timeline is not enabled");
+        return SINV_ERR_INVALID_ARG;
+    }
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    std::vector<unsigned long long> f(n_supernodes), l(3 * n_supernodes);
+    if (e == cudaSuccess && n_supernodes > 0)
+        e = cudaMemcpy(f.data(), h->dtl_first, f.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && n_supernodes > 0)
+        e = cudaMemcpy(l.data(), h->dtl_last, l.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "timeline read");
+    for (int64_t J = 0; J < n_supernodes; ++J) {
+        stamps[4 * J] = f[J];
+        for (int k = 0; k < 3; ++k) stamps[4 * J + 1 + k] = l[3 * J + k];
+    }
     return SINV_OK;
 }
 

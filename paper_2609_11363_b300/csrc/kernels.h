@@ -4,6 +4,7 @@
 #include <string>
 #include <cuda_runtime.h>
 
+#include "device.cuh"
 #include "plan.h"
 
 namespace sinv {
@@ -47,11 +48,31 @@ struct SelinvArgs {
     const int64_t* xsum_off;  // per supernode: its partial-sum block when split over CTAs, else -1
     double* xsum;             // the blocks (zeroed before every launch)
     uint32_t* arrive;         // per supernode: parts arrived in this call (zeroed before every launch)
+    int32_t item0;            // first work item of this launch (the tensor-core tier runs the ones before)
+    Timeline tl;              // per-supernode stamps, or nulls
 };
 
+// The tensor-core tier of SelInv (selinv_tc.cu): items over (supernode, row tile,
+// part of C) of the leading levels whose C is contiguous.
+struct TcArgs {
+    const int32_t* tcmap;  // per supernode tc_c x w: CSR position of L(R[o], s0+t) or -1
+    const int32_t* deps;   // per supernode: the distinct supernodes owning rows of C
+    const WorkItem* items;
+    int32_t nitems;
+    int32_t* ticket;
+    double* mirror;      // symmetric band copy of G for rows [row0, n), zeroed before every call
+    int64_t row0, band, width;
+    uint32_t* arrive_t;  // per row tile: parts arrived (zeroed)
+    double* zacc;        // per supernode w x w: Z summed over the tiles (zeroed)
+};
+cudaError_t selinv_tc_configure();
+// fmt: 2 = TF32, 1 = BF16 (the tcgen05 input type of the split operands)
+cudaError_t selinv_tc_launch(const SelinvArgs& a, const TcArgs& t, int fmt, double* G, cudaStream_t st);
+
 cudaError_t selinv_configure();
-// epoch += 1 (skipping 0) and ticket = 0, in stream order: keeps the launch graph-capturable
-cudaError_t selinv_prepare(uint32_t* epoch, int32_t* ticket, cudaStream_t st);
+// epoch += 1 (skipping 0) and ticket = 0 (and ticket2 = 0 if given), in stream order:
+// keeps the launch graph-capturable
+cudaError_t selinv_prepare(uint32_t* epoch, int32_t* ticket, cudaStream_t st, int32_t* ticket2 = nullptr);
 int selinv_grid(int num_sms);
 int selinv_max_width();
 int selinv_cw_smem();

@@ -45,6 +45,18 @@ struct SnInfo {
     int64_t hit_cnt;   // pairs (i, k) of C x C (both triangles and the diagonal) with
                        // (C[i], C[k]) in S, sorted by (i, k)
     int64_t hrow_off;  // hrow[hrow_off .. +c+1): start of row i's pairs, relative to hit_off
+    // tensor-core tier (supernodes of the leading levels whose C fills most of the
+    // range of rows [C[0], C[c-1]]; -1 / 0 elsewhere).  The tier works on the whole
+    // range R (tc_c rows): rows of R outside C have no entry in L_CJ, so they add
+    // nothing to Y's rows in C nor to Z, and their X is never stored.
+    int32_t tc_c;      // |R|
+    int32_t tc_tiles;  // row tiles of 128 rows of R (at least 1)
+    int32_t tc_ks;     // parts of the contraction over R per row tile
+    int32_t tc_ndep;     // distinct supernodes owning rows of C (the ones to wait for)
+    int64_t tc_map_off;  // tc_map[tc_map_off .. + tc_c * w): CSR position of L(R[o], s0+t), or -1
+    int64_t tc_dep_off;  // tc_deps[tc_dep_off .. + tc_ndep): those supernodes, latest first
+    int64_t tc_t_off;  // arrival counters of the row tiles
+    int64_t tc_z_off;  // Z block of w x w doubles (sum over the row tiles)
 };
 
 // A unit of the persistent SelInv schedule: either one large supernode that a
@@ -85,6 +97,18 @@ struct HostPlan {
     // supernodes split over several CTAs: offset of their c*w partial-sum block (-1: not split)
     std::vector<int64_t> xsum_off;
     int64_t xsum_total = 0;
+    // tensor-core tier: the leading tc_levels levels, whose supernodes all have a
+    // nearly contiguous C and width <= kTcWMax.  tc_items: one per (supernode, row tile,
+    // part of the contraction) in processing order; items[rest_first ..] are the
+    // supernodes of the later levels.  The tier reads G~ from a symmetric band
+    // copy ("mirror") of rows [tc_row0, n), columns row - tc_band .. row + tc_band
+    // with a margin of 64 both ways, tc_width values per row.
+    int64_t tc_levels = 0, rest_first = 0, tc_sn = 0, tc_pairs = 0;
+    std::vector<WorkItem> tc_items;
+    int64_t tc_t_total = 0, tc_z_total = 0;
+    int64_t tc_row0 = 0, tc_band = 0, tc_width = 0;
+    std::vector<int32_t> tc_map;
+    std::vector<int32_t> tc_deps;
     int64_t n_levels = 0, max_c = 0, max_w = 0, max_cw = 0, hit_pairs = 0;
     // algorithmic work of one SelInv: 2 w flops per pair of C x C in S, 2 c w^2 for
     // the diagonal block; bytes: each entry of S in C x C once (8 B) and L_CJ in, X out
@@ -148,6 +172,10 @@ struct EinvPlan {
     std::vector<int32_t> fwd_rows, fwd_ptr;  // rows of level l: fwd_rows[fwd_ptr[l] .. fwd_ptr[l+1])
     std::vector<int32_t> bwd_cols, bwd_ptr;  // columns of level l of the solve with L^T
 };
+
+constexpr int kTcWMax = 32;     // widest supernode of the tensor-core tier
+constexpr int kTcRowsTile = 128;  // rows of C per tensor-core tile (the MMA's M)
+constexpr int kTcMaxChunks = 8;   // 32-column chunks of one part of the contraction
 
 // Returns an empty string on success, else the reason the pattern is invalid.
 // big_pairs: supernodes with at least this many pairs are processed by a whole CTA;

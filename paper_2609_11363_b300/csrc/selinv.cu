@@ -163,6 +163,7 @@ __device__ bool process(const SelinvArgs& a, typename Form::G* Gw, int J, uint32
     const SnInfo I = a.sn[J];
     const int c = I.c, w = I.w, cw = c * w;
     const int tid = Gr::rank(), gsz = Gr::size(), lane = threadIdx.x & 31;
+    if (tid == 0) tl_start(a.tl, J);
     const int32_t* Crow = a.Crow + I.crow_off;
     const int32_t* Lmap = a.Lmap + I.cw_off;
 
@@ -296,10 +297,12 @@ __device__ bool process(const SelinvArgs& a, typename Form::G* Gw, int J, uint32
     // the acquire loads above, followed by the group barrier inside any(), order
     // every thread's reads of G after the producers' release stores
     if (Gr::any(!ok)) return false;
+    if (tid == 0) tl_mark(a.tl, J, 0);
 
     // ---- phase C ---------------------------------------------------------------------
     accumulate_pairs<Form>(pr, hik, hpos, Gw, lh, x, w, lane);
     Gr::sync();
+    if (tid == 0) tl_mark(a.tl, J, 1);
     if (kCta && nparts > 1) {
         double* blk = a.xsum + a.xsum_off[J];
         for (int e = tid; e < cw; e += gsz) {
@@ -353,7 +356,10 @@ __device__ bool process(const SelinvArgs& a, typename Form::G* Gw, int J, uint32
     // the barrier orders every thread's writes before thread 0's release store,
     // which publishes them (release is cumulative over the barrier)
     Gr::sync();
-    if (tid == 0) st_release(a.done + J, epoch);
+    if (tid == 0) {
+        st_release(a.done + J, epoch);
+        tl_mark(a.tl, J, 2);
+    }
     return true;
 }
 
@@ -367,7 +373,7 @@ __global__ void __launch_bounds__(kWarps * 32) selinv_persistent(SelinvArgs a, t
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
-            cs.item = atomicAdd(a.ticket, 1);
+            cs.item = a.item0 + atomicAdd(a.ticket, 1);
             cs.stop = ld_volatile(a.status) != ST_OK;
         }
         __syncthreads();
@@ -386,10 +392,11 @@ __global__ void __launch_bounds__(kWarps * 32) selinv_persistent(SelinvArgs a, t
     }
 }
 
-__global__ void prepare_kernel(uint32_t* epoch, int32_t* ticket) {
+__global__ void prepare_kernel(uint32_t* epoch, int32_t* ticket, int32_t* ticket2) {
     uint32_t e = *epoch + 1;
     *epoch = e == 0 ? 1 : e;
     *ticket = 0;
+    if (ticket2) *ticket2 = 0;
 }
 
 template <class Form>
@@ -417,9 +424,9 @@ cudaError_t launch_form(const SelinvArgs& a, typename Form::G* Gw, double* G_out
 
 }  // namespace
 
-cudaError_t selinv_prepare(uint32_t* epoch, int32_t* ticket, cudaStream_t st) {
+cudaError_t selinv_prepare(uint32_t* epoch, int32_t* ticket, cudaStream_t st, int32_t* ticket2) {
     trace_begin("selinv_prepare", st);
-    prepare_kernel<<<1, 1, 0, st>>>(epoch, ticket);
+    prepare_kernel<<<1, 1, 0, st>>>(epoch, ticket, ticket2);
     trace_end(st);
     return cudaGetLastError();
 }

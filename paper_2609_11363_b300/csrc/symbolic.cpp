@@ -393,6 +393,103 @@ std::string build_plan(int64_t n, const int64_t* Lrp, const int32_t* Lc, const i
         if (P.sn[a].level != P.sn[b].level) return P.sn[a].level < P.sn[b].level;
         return P.sn[a].hit_cnt > P.sn[b].hit_cnt;
     });
+    // tensor-core tier: the leading levels in which every supernode has a contiguous C
+    // (and width <= kTcWMax).  Its G~ reads go to a symmetric band copy of G whose
+    // half-width covers every |row - column| the tier touches; the tier is cut back
+    // to fewer levels while that copy would exceed kTcMirrorMax bytes.
+    {
+        constexpr int64_t kTcMirrorMax = int64_t(8) << 30;
+        int64_t D = P.n_levels;
+        for (int64_t s = 0; s < ns; ++s) {
+            const auto& C = Cs[s];
+            const SnInfo& I = P.sn[s];
+            const int64_t range = C.empty() ? 0 : (int64_t)C.back() - C.front() + 1;
+            const int64_t c = (int64_t)C.size();
+            const bool ok = I.w <= kTcWMax && range <= c + std::max<int64_t>(16, c / 8);
+            if (!ok) D = std::min<int64_t>(D, I.level);
+        }
+        // levels in processing order; shrink D until the mirror fits
+        auto mirror_shape = [&](int64_t lv_end, int64_t& row0, int64_t& band) {
+            row0 = n;
+            band = 0;
+            for (int64_t s = 0; s < ns; ++s) {
+                if (P.sn[s].level >= lv_end) continue;
+                const auto& C = Cs[s];
+                row0 = std::min<int64_t>(row0, P.sn[s].s0);
+                band = std::max<int64_t>(band, C.empty() ? P.sn[s].w - 1 : (int64_t)C.back() - P.sn[s].s0);
+            }
+        };
+        int64_t row0 = n, band = 0;
+        while (D > 0) {
+            mirror_shape(D, row0, band);
+            const int64_t width = ((2 * band + 136) + 3) / 4 * 4;
+            if ((n - row0) * width * 8 <= kTcMirrorMax) break;
+            --D;
+        }
+        P.tc_levels = D;
+        for (int64_t s = 0; s < ns; ++s) {
+            SnInfo& I = P.sn[s];
+            I.tc_c = 0;
+            I.tc_tiles = 0;
+            I.tc_ks = 0;
+            I.tc_ndep = 0;
+            I.tc_t_off = I.tc_z_off = I.tc_map_off = I.tc_dep_off = -1;
+        }
+        if (D > 0) {
+            P.tc_row0 = row0;
+            P.tc_band = band;
+            P.tc_width = ((2 * band + 136) + 3) / 4 * 4;
+            for (int64_t t = 0; t < ns; ++t) {
+                const int32_t sidx = P.order[t];
+                SnInfo& I = P.sn[sidx];
+                if (I.level >= D) break;  // the order is level-major
+                const auto& C = Cs[sidx];
+                const int64_t c = C.empty() ? 0 : (int64_t)C.back() - C.front() + 1;  // the range R
+                const int64_t tiles = std::max<int64_t>(1, (c + kTcRowsTile - 1) / kTcRowsTile);
+                const int64_t k0 = c > 0 ? (Cs[sidx].front() >> 2) << 2 : 0;
+                const int64_t nch = c > 0 ? (Cs[sidx].front() + c - k0 + 31) / 32 : 0;
+                // parts of at least 64 columns of R (two chunks) and at most kTcMaxChunks
+                // chunks (their B tiles are staged at once), at most 16 parts unless needed
+                int64_t ks = std::max<int64_t>(1, std::min<int64_t>({c / 64, 16, std::max<int64_t>(nch, 1)}));
+                ks = std::max<int64_t>(ks, (nch + kTcMaxChunks - 1) / kTcMaxChunks);
+                // the distinct supernodes owning rows of C, the latest in processing order first
+                {
+                    std::vector<int32_t> dep;
+                    for (int32_t r : C) dep.push_back(P.owner[r]);
+                    std::sort(dep.begin(), dep.end());
+                    dep.erase(std::unique(dep.begin(), dep.end()), dep.end());
+                    std::sort(dep.begin(), dep.end(), [&](int32_t x, int32_t y) {
+                        return P.sn[x].level > P.sn[y].level || (P.sn[x].level == P.sn[y].level && x < y);
+                    });
+                    I.tc_dep_off = (int64_t)P.tc_deps.size();
+                    I.tc_ndep = (int32_t)dep.size();
+                    P.tc_deps.insert(P.tc_deps.end(), dep.begin(), dep.end());
+                }
+                I.tc_c = (int32_t)c;
+                I.tc_map_off = (int64_t)P.tc_map.size();
+                P.tc_map.resize(P.tc_map.size() + c * I.w, -1);
+                for (int64_t i = 0; i < (int64_t)C.size(); ++i) {
+                    const int64_t o = C[i] - C.front();
+                    for (int32_t tt = 0; tt < I.w; ++tt)
+                        P.tc_map[I.tc_map_off + o * I.w + tt] = P.Lmap[I.cw_off + i * I.w + tt];
+                }
+                I.tc_tiles = (int32_t)tiles;
+                I.tc_ks = (int32_t)ks;
+                I.tc_t_off = P.tc_t_total; P.tc_t_total += tiles;
+                I.tc_z_off = P.tc_z_total; P.tc_z_total += (int64_t)I.w * I.w;
+                P.tc_sn += 1;
+                P.tc_pairs += c * c;
+                for (int64_t q = 0; q < tiles * ks; ++q) {
+                    WorkItem it;
+                    it.first = (int32_t)t;
+                    it.count = (int32_t)(tiles * ks);
+                    it.big = 3;
+                    it.part = (int32_t)q;
+                    P.tc_items.push_back(it);
+                }
+            }
+        }
+    }
     // work items: a large supernode alone (whole CTA), else up to `group` consecutive ones.
     // Levels with fewer supernodes than thin_level sit on the critical path of the
     // dependency chain: each of their supernodes gets a whole CTA to shorten it.  A
@@ -430,8 +527,11 @@ std::string build_plan(int64_t n, const int64_t* Lrp, const int32_t* Lc, const i
             ++t;
         } else {
             int64_t e = t;
+            // a group never mixes the tensor-core levels with the later ones
+            const bool tc_side = I.level < P.tc_levels;
             while (e < ns && e - t < group && P.sn[P.order[e]].hit_cnt < big_pairs &&
-                   level_size[P.sn[P.order[e]].level] >= thin_level)
+                   level_size[P.sn[P.order[e]].level] >= thin_level &&
+                   (P.sn[P.order[e]].level < P.tc_levels) == tc_side)
                 ++e;
             it.count = (int32_t)(e - t);
             it.big = 0;
@@ -439,6 +539,12 @@ std::string build_plan(int64_t n, const int64_t* Lrp, const int32_t* Lc, const i
         }
         P.items.push_back(it);
     }
+    P.rest_first = (int64_t)P.items.size();
+    for (int64_t q = 0; q < (int64_t)P.items.size(); ++q)
+        if (P.sn[P.order[P.items[q].first]].level >= P.tc_levels) {
+            P.rest_first = q;
+            break;
+        }
     return "";
 }
 

@@ -25,6 +25,10 @@ Recipes (every random number from PCG64 ``numpy.random.default_rng``):
 * ``covariance``    covariance-type matrix (1 - d/alpha)^beta on an N x N grid,
                     alpha = 3, beta = 4 (no random numbers), tau = 1e-3, m = 3:
                     the paper's second example, N = 100 and 200.
+* ``band``          dense band of half-bandwidth b, DoDD 1.8, seed 6, in its
+                    natural order (a band needs no reordering: its factor has
+                    no fill), tau = 1e-6: the paper's dense-row microbenchmark
+                    shape, n = 12,288 (b = 1024) and 24,576.
 """
 from __future__ import annotations
 
@@ -122,6 +126,14 @@ def covariance(N: int = 200, alpha: float = 3.0, beta: float = 4.0, tau: float =
     A, p = _ordered(grids.covariance2d(N, alpha, beta), (N, N))
     return Workload("covariance_%d_a%g_b%g" % (N, alpha, beta), A, ildl(A, tau), tau, m,
                     meta={"shape": (N, N), "alpha": alpha, "beta": beta})
+
+
+def band(n: int = 12288, b: int = 1024, tau: float = 1e-6, dodd: float = 1.8, seed: int = 6, m: int = 3) -> Workload:
+    """The dense-row microbenchmark shape of the paper (its n12 / n24 matrices:
+    n = 12,288 / 24,576, half-bandwidth 1024, DoDD 1.8, best tau = 1e-6) in
+    natural order."""
+    A = grids.band_dd(n, b, dodd, seed)
+    return Workload("band_%d_b%d" % (n, b), A, ildl(A, tau), tau, m, meta={"n": n, "b": b, "dodd": dodd, "seed": seed})
 
 
 def random_lowrank(n: int, k: int, seed: int, orthonormal: bool = True):
