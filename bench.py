@@ -49,11 +49,16 @@ def parse():
     p.add_argument("--size", type=int, default=64)
     p.add_argument("--ninv-delta", type=float, default=0.0,
                    help="inverse tolerance of NInv: off-diagonal |w| < delta dropped after each Horner step")
-    p.add_argument("--workload", default="diff3d", choices=["diff3d", "batch9pt", "learned", "elastic", "covariance"],
+    p.add_argument("--workload", default="diff3d",
+                   choices=["diff3d", "batch9pt", "learned", "elastic", "covariance", "band"],
                    help="diff3d: the 64^3 step (default); batch9pt: 256 matrices in one graph-captured launch; "
                         "learned: the trained NInv->SelInv correction on 128^3; elastic: the 27-point 3-dof "
                         "operator (N^3 nodes, --elastic-size N); covariance: the (1-d/3)^4 covariance-type "
-                        "matrix on an N x N grid (--cov-size N)")
+                        "matrix on an N x N grid (--cov-size N); band: the dense-row microbenchmark shape "
+                        "(--band-n, --band-b, --band-tau), SelInv FP64 vs the tensor-core forms")
+    p.add_argument("--band-n", type=int, default=12288)
+    p.add_argument("--band-b", type=int, default=1024)
+    p.add_argument("--band-tau", type=float, default=1e-6)
     p.add_argument("--elastic-size", type=int, default=24)
     p.add_argument("--cov-size", type=int, default=200)
     p.add_argument("--spai-iters", type=int, default=20,
@@ -627,6 +632,10 @@ def run_extra(args, rank, world):
     if args.workload == "elastic":
         run_elastic(args, rank, world, dev, peaks)
         return
+    if args.workload == "band":
+        torch.cuda.set_device(dev)
+        run_band(args, rank, world, dev, peaks)
+        return
     if args.workload == "covariance":
         run_covariance(args, rank, world, dev)
         return
@@ -700,6 +709,91 @@ def run_extra(args, rank, world):
             "gpu_launches": None}
     if rank == 0:
         print(json.dumps(line))
+
+
+def run_band(args, rank, world, dev, peaks):
+    """The dense-row microbenchmark shape of the paper (n = 12,288, half-bandwidth
+    1024, DoDD 1.8, tau = 1e-6 by default): SelInv in FP64 and in the tensor-core
+    forms (TF32 / BF16 split operands), entries of S per second, the normwise
+    difference from the FP64 result (itself parity-tested against the oracle) and
+    the critical-path split of the tensor-core call."""
+    import torch
+    from paper_2609_11363_b300 import Handle
+    from paper_2609_11363_b300.timeline import critical_path, dependencies
+    from workloads.configs import band
+    t0 = time.time()
+    f = band(args.band_n, args.band_b, tau=args.band_tau).factors
+    t_gen = time.time() - t0
+    t0 = time.time()
+    h = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start, device=dev.index, supernode_cap=16)
+    t_sym = time.time() - t0
+    st = h.stats()
+    Lv = torch.as_tensor(f.L_val, device=dev)
+    Dv = torch.as_tensor(f.D_packed, device=dev)
+    nS = 2 * h.nnz_S - f.n
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res, outs = {}, {}
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    for prec in ("fp64", "tf32", "bf16"):
+        G = torch.empty(h.nnz_S, dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            h.selinv(Lv, Dv, prec, out=G)
+        h.sync_status()
+        h.trace(True)
+        ms = []
+        steps = args.steps if prec != "fp64" else max(1, min(args.steps, 3))
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            h.selinv(Lv, Dv, prec, out=G)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        tr = h.trace_read()
+        h.trace(False)
+        h.sync_status()
+        outs[prec] = G.cpu().numpy()
+        res[prec] = {"ms": float(np.median(ms)), "entries_per_s": nS / (float(np.median(ms)) / 1e3),
+                     "kernels": {k: {"launches_per_step": c / steps, "ms_per_step": t / steps} for k, (c, t) in tr.items()}}
+    clk = clocks.stop()
+    ref = outs["fp64"]
+    for prec in ("tf32", "bf16"):
+        res[prec]["normwise_vs_fp64"] = float(np.linalg.norm(outs[prec] - ref) / np.linalg.norm(ref))
+        res[prec]["speedup_vs_fp64"] = res["fp64"]["ms"] / res[prec]["ms"]
+    # critical path of the TF32 call (a separate, recorded call)
+    h.timeline(True)
+    G = torch.empty(h.nnz_S, dtype=torch.float64, device=dev)
+    h.selinv(Lv, Dv, "tf32", out=G)
+    h.sync_status()
+    stamps = h.timeline_read()
+    h.timeline(False)
+    sn_start, sn_level = h.supernodes()
+    cp = critical_path(stamps, dependencies(f.n, f.L_rowptr, f.L_col, sn_start), sn_level)
+    # work of the contraction: per supernode 3 split products of 2 |R|^2 w flops
+    tc_flops = 3 * 2.0 * st["tc_pairs"] * 16
+    tc_ms = res["tf32"]["kernels"].get("selinv_tc_tf32", {}).get("ms_per_step", res["tf32"]["ms"])
+    line = {"metric": METRIC, "workload": "band", "value": res["tf32"]["entries_per_s"], "unit": "entries/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["tf32"]["ms"],
+            "higher_is_better": True, "dtype": "tf32 split operands, f32 accumulators, f64 pivots and G_JJ",
+            "data": "synthetic",
+            "config": {"workload": "band_%d_b%d_tau%g: dense band, half-bandwidth %d, DoDD 1.8, seed 6, natural "
+                                   "order; SelInv" % (f.n, args.band_b, args.band_tau, args.band_b),
+                       "n": f.n, "nnz_L": st["nnz_L"], "S_entries": nS, "supernodes": st["n_supernodes"],
+                       "levels": st["n_levels"], "tc_levels": st["tc_levels"], "tc_pairs": st["tc_pairs"],
+                       "tc_mirror_bytes": st["tc_mirror_bytes"], "input_gen_s": t_gen, "symbolic_s": t_sym,
+                       "l2": "flushed between timed calls (512 MB write)",
+                       "stated_rel_error": {"tf32": "normwise 1e-6", "bf16": "normwise 1e-5"}},
+            "forms": res, "critical_path_tf32": cp,
+            "tensor_roofline": {"bound": "latency of the level chain", "flops_per_call": tc_flops,
+                                "achieved_tflops": tc_flops / (tc_ms * 1e-3) / 1e12,
+                                "peak_tflops_tf32": 0.5 * float(peaks.get("bf16_tflops", 1800.0)),
+                                "peak_source": "MEASURED_PEAKS.json bf16 x 1/2 (nominal TF32:BF16 ratio)"},
+            "clocks": clk}
+    line["tensor_roofline"]["frac"] = line["tensor_roofline"]["achieved_tflops"] / line["tensor_roofline"]["peak_tflops_tf32"]
+    print(json.dumps(line))
 
 
 def run_elastic(args, rank, world, dev, peaks):

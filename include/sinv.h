@@ -132,6 +132,29 @@ sinv_status sinv_batch_symbolic(int32_t nmat, const int64_t *n, const int64_t *c
 sinv_status sinv_batch_layout(sinv_handle h, int32_t *nmat, int64_t *n_off, int64_t *L_off, int64_t *D_off,
                               int64_t *S_off);
 
+/* One call over all matrices of a batch handle, with every matrix in its own
+ * buffers: the persistent, graph-capturable batched run of Section 2.1 (SelInv)
+ * and Section 2.2 (NInv) over many matrices of uneven size.  The matrices'
+ * L and D values are gathered into the handle's concatenated layout (one
+ * launch each), SelInv runs as one persistent launch over the supernodes of all
+ * matrices (level by level), NInv as one set of launches, and the results are
+ * scattered back (one launch each).  Every step is a kernel launch on `stream`;
+ * the per-matrix pointers travel as kernel arguments, so the whole call can be
+ * captured in a CUDA graph and replayed.
+ *   h: from sinv_batch_symbolic with nmat matrices.  L_vals[b], D_vals[b]: host
+ *   arrays of nmat device pointers to matrix b's own L values (CSR order) and
+ *   packed D.  G_outs: host array of nmat device pointers (|S_lo| of matrix b,
+ *   S_lo order), or NULL to skip SelInv; an entry may be NULL to skip that
+ *   matrix's copy.  m, N_outs: NInv with m terms into N_outs the same way, or
+ *   N_outs NULL to skip it.  prec as for sinv_selinv (the tensor-core forms
+ *   apply to SelInv only; NInv then returns SINV_ERR_UNSUPPORTED).
+ *   The first call allocates the concatenated buffers (|L| + |D| + 2 |S_lo|
+ *   doubles, handle-owned): make it before any stream capture.
+ *   Errors: SINV_ERR_INVALID_ARG (not a batch handle, nmat mismatch, missing
+ *   pointers), SINV_ERR_OOM, and those of sinv_selinv / sinv_ninv. */
+sinv_status sinv_batch_run(sinv_handle h, int32_t nmat, const double *const *L_vals, const double *const *D_vals,
+                           sinv_precision prec, double *const *G_outs, int m, double *const *N_outs, void *stream);
+
 /* S_lo on the device (handle-owned, valid until sinv_destroy) and its size. */
 sinv_status sinv_get_pattern(sinv_handle h, const int64_t **S_rowptr, const int32_t **S_col,
                              int64_t *nnzS_lo);
@@ -262,6 +285,17 @@ sinv_status sinv_spai(sinv_handle h, const double *A_val, const double *X_S, int
  *   Errors: SINV_ERR_INVALID_ARG (no analysis, bad sizes, q0 zero or not
  *   finite), SINV_ERR_UNSUPPORTED (steps > 256), SINV_ERR_OOM. */
 sinv_status sinv_einv_analyse(sinv_handle h, int64_t nnzA, const int64_t *A_rowptr, const int32_t *A_col);
+/* The inner solver of sinv_einv_lanczos for A^{-1} q (Section 2.5 solves these
+ * with ILDL-preconditioned Krylov methods, sQMR for indefinite A):
+ *   0 (default): conjugate gradients with M = L D L^T -- needs A and D positive
+ *     definite;
+ *   1: MINRES (Paige & Saunders) with the SPD preconditioner M = L |D| L^T, |D|
+ *     the absolute value of every 1x1 / 2x2 pivot block -- for indefinite A.
+ * Both apply M^{-1} with two persistent triangular solves (one launch each
+ * over all dependency levels).  cg_tol of sinv_einv_lanczos is then the
+ * relative residual in the norm of M^{-1} that MINRES estimates, and cg_maxit
+ * its iteration limit.  Errors: SINV_ERR_INVALID_ARG (unknown solver). */
+sinv_status sinv_einv_set_solver(sinv_handle h, int32_t solver);
 sinv_status sinv_einv_lanczos(sinv_handle h, const double *A_val, const double *L_val, const double *D_val,
                               const double *X_S, const double *q0, int steps, double cg_tol, int cg_maxit, int k,
                               double *lambda, double *V, int32_t *info, void *stream);

@@ -32,7 +32,8 @@ EXPORTS = [
     "sinv_spai_analyse", "sinv_spai_pattern", "sinv_spai", "sinv_einv_analyse", "sinv_einv_lanczos",
     "sinv_mlp_param_count", "sinv_mlp_create", "sinv_mlp_destroy", "sinv_mlp_get_params", "sinv_mlp_set_params",
     "sinv_mlp_features", "sinv_mlp_targets", "sinv_mlp_grad", "sinv_mlp_train_step", "sinv_mlp_predict",
-    "sinv_mlp_sync_status", "sinv_timeline_enable", "sinv_timeline_read",
+    "sinv_mlp_sync_status", "sinv_timeline_enable", "sinv_timeline_read", "sinv_batch_run",
+    "sinv_einv_set_solver",
 ]
 
 
@@ -112,6 +113,8 @@ def load_library():
     lib.sinv_mlp_sync_status.argtypes = [H, P]
     lib.sinv_timeline_enable.argtypes = [H, ctypes.c_int]
     lib.sinv_timeline_read.argtypes = [H, P, I64, P]
+    lib.sinv_batch_run.argtypes = [H, ctypes.c_int32, P, P, ctypes.c_int, P, ctypes.c_int, P, P]
+    lib.sinv_einv_set_solver.argtypes = [H, ctypes.c_int32]
     lib.sinv_batch_symbolic.argtypes = [ctypes.c_int32, P, P, P, P, ctypes.POINTER(_Opts), ctypes.POINTER(H)]
     lib.sinv_batch_layout.argtypes = [H, ctypes.POINTER(ctypes.c_int32), P, P, P, P]
     lib.sinv_lowrank_correct_noalloc.argtypes = [I64, P, P, ctypes.c_int, P, P, P, P]
@@ -341,6 +344,22 @@ class Handle:
         self._check(self._lib.sinv_batch_layout(self._h, ctypes.byref(nmat), *[_np_ptr(a) for a in arrs]))
         return dict(zip(("n", "L", "D", "S"), arrs))
 
+    def batch_run(self, L_vals, D_vals, prec="fp64", G_outs=None, m=0, N_outs=None, stream=None):
+        """sinv_batch_run: SelInv (into G_outs) and / or NInv with m terms (into N_outs)
+        for every matrix of a batch handle, each in its own CUDA tensors."""
+        k = len(L_vals)
+
+        def ptrs(ts, name, dtype=torch.float64):
+            arr = (ctypes.c_void_p * k)()
+            for b, t in enumerate(ts):
+                arr[b] = _check_tensor(t, name, None, dtype).value if t is not None else None
+            return arr
+
+        Lp, Dp = ptrs(L_vals, "L_val"), ptrs(D_vals, "D_val")
+        Gp = ptrs(G_outs, "G_out") if G_outs is not None else None
+        Np = ptrs(N_outs, "N_out") if N_outs is not None else None
+        self._check(self._lib.sinv_batch_run(self._h, k, Lp, Dp, PREC[prec], Gp, int(m), Np, _stream_ptr(stream)))
+
     # -- helpers -----------------------------------------------------------
     def last_error(self) -> str:
         if not self._h:
@@ -466,6 +485,10 @@ class Handle:
         self._check(self._lib.sinv_einv_analyse(self._h, int(A.nnz), _np_ptr(rp), _np_ptr(col)))
         self._einv_nnzA = int(A.nnz)
         return sp.csr_matrix((A.data, col, rp), shape=A.shape)
+
+    def einv_set_solver(self, solver):
+        """Inner solver of einv_lanczos: "cg" (A SPD) or "minres" (L |D| L^T, indefinite A)."""
+        self._check(self._lib.sinv_einv_set_solver(self._h, {"cg": 0, "minres": 1}[solver]))
 
     def einv_lanczos(self, A_val, L_val, D_val, X, q0, k, steps, cg_tol=1e-12, cg_maxit=1000, stream=None):
         """k dominant eigenpairs of E_inv = A^{-1} - A^inv (A^inv = X on S): returns

@@ -146,6 +146,14 @@ struct sinv_handle_s {
     NinvPlan W;
     // batch layout (block-diagonal concatenation of several matrices), nmat+1 offsets each
     std::vector<int64_t> b_n_off, b_L_off, b_D_off, b_S_off;
+    // sinv_batch_run: device offsets and the concatenated value / output buffers
+    int64_t* db_L_off = nullptr;
+    int64_t* db_D_off = nullptr;
+    int64_t* db_S_off = nullptr;
+    double* db_L = nullptr;
+    double* db_D = nullptr;
+    double* db_G = nullptr;
+    double* db_N = nullptr;
     int64_t* dWcp = nullptr;
     int32_t* dWr = nullptr;
     int32_t* dgrp = nullptr;
@@ -172,6 +180,9 @@ struct sinv_handle_s {
     int32_t *deAcol = nullptr, *deLcol = nullptr, *defri = nullptr, *defpos = nullptr, *defwd = nullptr,
             *debwd = nullptr;
     void* dework = nullptr;
+    // persistent triangular solves: per-row flags of each solve, epoch and tickets (zeroed once)
+    uint32_t* detrsv = nullptr;
+    int32_t einv_solver = 0;  // 0: CG with L D L^T (A SPD), 1: MINRES with L |D| L^T
     size_t ework_bytes = 0;
     std::string last_error;
 };
@@ -213,12 +224,13 @@ void spai_free(sinv_handle h) {
 
 void einv_free(sinv_handle h) {
     void* ptrs[] = {h->deArp, h->deLrp, h->defcp, h->deAcol, h->deLcol, h->defri, h->defpos, h->defwd, h->debwd,
-                    h->dework};
+                    h->dework, h->detrsv};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     h->deArp = h->deLrp = h->defcp = nullptr;
     h->deAcol = h->deLcol = h->defri = h->defpos = h->defwd = h->debwd = nullptr;
     h->dework = nullptr;
+    h->detrsv = nullptr;
     h->ework_bytes = 0;
     h->einv_ready = false;
     h->einv_analysed = false;
@@ -230,7 +242,8 @@ void free_all(sinv_handle h) {
                     h->dsn, h->dorder, h->downer, h->dCrow, h->dLmap, h->dJJl, h->dJJs, h->dhit_ik, h->dhit_pos,
                     h->dhrow, h->ditems, h->dxsum_off, h->dxsum, h->darrive, h->ddone, h->depoch, h->dticket, h->dstatus, h->ddebug_flag, h->dscratch, h->dwork, h->dWcp,
                     h->dWr, h->dgrp, h->dtc_items, h->dtc_map, h->dtc_deps, h->dtc_ticket, h->dtc_mirror, h->dtc_arrive_t,
-                    h->dtc_z, h->dtl_first, h->dtl_last};
+                    h->dtc_z, h->dtl_first, h->dtl_last, h->db_L_off, h->db_D_off, h->db_S_off, h->db_L, h->db_D,
+                    h->db_G, h->db_N};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     ninv_maps_free(h->X);
@@ -996,7 +1009,20 @@ sinv_status sinv_einv_analyse(sinv_handle h, int64_t nnzA, const int64_t* A_rowp
     UPE(defwd, E.fwd_rows);
     UPE(debwd, E.bwd_cols);
 #undef UPE
+    // flags of the two solves (n each), then the epoch and two tickets
+    const size_t nflag = 2 * (size_t)h->P.n + 64;
+    if ((e = cudaMalloc((void**)&h->detrsv, nflag * sizeof(uint32_t))) != cudaSuccess ||
+        (e = cudaMemset(h->detrsv, 0, nflag * sizeof(uint32_t))) != cudaSuccess) {
+        einv_free(h);
+        return cuda_fail(h, e, "triangular-solve flags");
+    }
     h->einv_ready = true;
+    return SINV_OK;
+}
+
+sinv_status sinv_einv_set_solver(sinv_handle h, int32_t solver) {
+    if (!h || (solver != 0 && solver != 1)) return SINV_ERR_INVALID_ARG;
+    h->einv_solver = solver;
     return SINV_OK;
 }
 
@@ -1024,9 +1050,9 @@ sinv_status sinv_einv_lanczos(sinv_handle h, const double* A_val, const double* 
     cudaStream_t st = (cudaStream_t)stream;
     TraceScope trace_scope(h->tracer);
     const int nb = einv_dot_blocks(h->num_sms);
-    // workspace: 8 vectors, Q, D^{-1} rows, partial sums, scalars, T, U, sel, lam
+    // workspace: 10 vectors, Q, D^{-1} rows, partial sums, scalars, T, U, sel, lam
     const size_t nv = (size_t)n, sq = (size_t)steps * steps;
-    const size_t doubles = 8 * nv + (size_t)(steps + 1) * nv + 2 * nv + nb + 8 + (steps + 1) + 2 * sq + k;
+    const size_t doubles = 10 * nv + (size_t)(steps + 1) * nv + 2 * nv + nb + 8 + (steps + 1) + 2 * sq + k;
     const size_t bytes = doubles * sizeof(double) + (nv + k + 8) * sizeof(int32_t) + 256;
     if (bytes > h->ework_bytes) {
         if (h->dework) cudaFree(h->dework);
@@ -1037,7 +1063,8 @@ sinv_status sinv_einv_lanczos(sinv_handle h, const double* A_val, const double* 
     }
     double* base = reinterpret_cast<double*>(h->dework);
     double *x = base, *r = x + nv, *z = r + nv, *p = z + nv, *qv = p + nv, *y = qv + nv, *w = y + nv, *v = w + nv;
-    double* Q = v + nv;
+    double *u1 = v + nv, *u2 = u1 + nv;  // two more work vectors (MINRES)
+    double* Q = u2 + nv;
     double* dr = Q + (size_t)(steps + 1) * nv;
     double* dp = dr + nv;
     double* partial = dp + nv;
@@ -1070,11 +1097,13 @@ sinv_status sinv_einv_lanczos(sinv_handle h, const double* A_val, const double* 
     a.dp = dp;
     a.part = part;
     a.fwd_rows = h->defwd;
-    a.fwd_ptr_h = E.fwd_ptr.data();
-    a.nlev_fwd = E.fwd_ptr.empty() ? 0 : (int)E.fwd_ptr.size() - 1;
     a.bwd_cols = h->debwd;
-    a.bwd_ptr_h = E.bwd_ptr.data();
-    a.nlev_bwd = E.bwd_ptr.empty() ? 0 : (int)E.bwd_ptr.size() - 1;
+    a.fwd_flags = h->detrsv;
+    a.bwd_flags = h->detrsv + n;
+    a.tepoch = h->detrsv + 2 * n;
+    a.tickets = reinterpret_cast<int32_t*>(h->detrsv + 2 * n + 16);
+    a.status = h->dstatus;
+    a.wait_limit = h->wait_limit;
 
     NinvArgs na{};
     na.n = n;
@@ -1083,7 +1112,11 @@ sinv_status sinv_einv_lanczos(sinv_handle h, const double* A_val, const double* 
     na.Dval = D_val;
     na.num_sms = h->num_sms;
     na.status = h->dstatus;
-    ninv_dinv_launch(na, dr, dp, part, st);
+    // D^{-1} (CG) or |D|^{-1} (MINRES: the SPD preconditioner L |D| L^T)
+    if (h->einv_solver == 1)
+        einv_absdinv(a, h->ddpos, h->dpstart, D_val, dr, dp, part, st);
+    else
+        ninv_dinv_launch(na, dr, dp, part, st);
 
     bool fail = false;
     auto chk = [&](cudaError_t err) {
@@ -1111,31 +1144,89 @@ sinv_status sinv_einv_lanczos(sinv_handle h, const double* A_val, const double* 
     int m = steps;
     int64_t cg_total = 0;
     int cg_unconverged = 0;
+    // x = A^{-1} b by preconditioned MINRES (Paige & Saunders) from x = 0 with the SPD
+    // preconditioner L |D| L^T; converged when the estimate of the residual in the
+    // preconditioner's inverse norm falls below tol times its start.  Returns true then.
+    auto minres = [&](const double* b, double tol, int maxit) -> bool {
+        double* r1 = r;
+        double* r2 = z;
+        double* yv = p;
+        double* wv = qv;
+        double* w1v = u1;
+        double* w2v = u2;
+        chk(cudaMemsetAsync(x, 0, nv * sizeof(double), st));
+        chk(cudaMemsetAsync(wv, 0, nv * sizeof(double), st));
+        chk(cudaMemsetAsync(w2v, 0, nv * sizeof(double), st));
+        chk(einv_axpby(a, 1.0, b, 0.0, b, r1, st));
+        chk(einv_axpby(a, 1.0, b, 0.0, b, r2, st));
+        chk(einv_precond_persistent(a, r1, y, yv, st));
+        const double bb = dot(r1, yv);
+        if (!(bb > 0.0)) return bb == 0.0;
+        const double beta1 = std::sqrt(bb);
+        double oldb = 0.0, beta = beta1, dbar = 0.0, epsln = 0.0, phibar = beta1, cs = -1.0, sn = 0.0;
+        for (int itn = 1; itn <= maxit && !fail; ++itn) {
+            chk(einv_axpby(a, 1.0 / beta, yv, 0.0, yv, v, st));                  // v = y / beta
+            chk(einv_spmv_A(a, v, yv, st));                                      // y = A v
+            if (itn >= 2) chk(einv_axpby(a, 1.0, yv, -beta / oldb, r1, yv, st)); // y -= (beta/oldb) r1
+            const double alfa = dot(v, yv);
+            chk(einv_axpby(a, 1.0, yv, -alfa / beta, r2, yv, st));               // y -= (alfa/beta) r2
+            std::swap(r1, r2);                                                   // r1 <- r2
+            std::swap(r2, yv);                                                   // r2 <- y
+            chk(einv_precond_persistent(a, r2, y, yv, st));                      // y = M^{-1} r2
+            ++cg_total;
+            oldb = beta;
+            const double b2 = dot(r2, yv);
+            if (!(b2 >= 0.0)) return false;  // the preconditioner lost definiteness
+            beta = std::sqrt(b2);
+            const double oldeps = epsln;
+            const double delta = cs * dbar + sn * alfa;
+            const double gbar = sn * dbar - cs * alfa;
+            epsln = sn * beta;
+            dbar = -cs * beta;
+            const double gamma = std::max(std::sqrt(gbar * gbar + beta * beta), 1e-300);
+            cs = gbar / gamma;
+            sn = beta / gamma;
+            const double phi = cs * phibar;
+            phibar = sn * phibar;
+            // w1 <- w2, w2 <- w, w = (v - oldeps w1 - delta w2) / gamma
+            std::swap(w1v, w2v);
+            std::swap(w2v, wv);
+            chk(einv_axpby(a, 1.0 / gamma, v, -oldeps / gamma, w1v, wv, st));
+            chk(einv_axpby(a, 1.0, wv, -delta / gamma, w2v, wv, st));
+            chk(einv_axpby(a, 1.0, x, phi, wv, x, st));                          // x += phi w
+            if (phibar <= tol * beta1 || beta == 0.0) return true;
+        }
+        return false;
+    };
     for (int it = 0; it < steps && !fail; ++it) {
         const double* qi = Q + (size_t)it * nv;
-        // x = A^{-1} q_i by CG preconditioned with L^{-T} D^{-1} L^{-1}, from x = 0
-        chk(cudaMemsetAsync(x, 0, nv * sizeof(double), st));
-        chk(einv_axpby(a, 1.0, qi, 0.0, qi, r, st));
-        const double bn = std::sqrt(dot(r, r));
-        chk(einv_precond(a, r, y, w, z, st));
-        chk(einv_axpby(a, 1.0, z, 0.0, z, p, st));
-        double rz = dot(r, z);
         bool conv = false;
-        for (int ci = 0; ci < cg_maxit && !fail; ++ci) {
-            chk(einv_spmv_A(a, p, qv, st));
-            const double pq = dot(p, qv);
-            if (!(pq > 0.0)) break;
-            const double al = rz / pq;
-            chk(einv_cg_xr(a, al, p, qv, x, r, st));
-            ++cg_total;
-            if (std::sqrt(dot(r, r)) <= cg_tol * bn) {
-                conv = true;
-                break;
+        if (h->einv_solver == 1) {
+            conv = minres(qi, cg_tol, cg_maxit);
+        } else {
+            // x = A^{-1} q_i by CG preconditioned with L^{-T} D^{-1} L^{-1}, from x = 0
+            chk(cudaMemsetAsync(x, 0, nv * sizeof(double), st));
+            chk(einv_axpby(a, 1.0, qi, 0.0, qi, r, st));
+            const double bn = std::sqrt(dot(r, r));
+            chk(einv_precond_persistent(a, r, y, z, st));
+            chk(einv_axpby(a, 1.0, z, 0.0, z, p, st));
+            double rz = dot(r, z);
+            for (int ci = 0; ci < cg_maxit && !fail; ++ci) {
+                chk(einv_spmv_A(a, p, qv, st));
+                const double pq = dot(p, qv);
+                if (!(pq > 0.0)) break;
+                const double al = rz / pq;
+                chk(einv_cg_xr(a, al, p, qv, x, r, st));
+                ++cg_total;
+                if (std::sqrt(dot(r, r)) <= cg_tol * bn) {
+                    conv = true;
+                    break;
+                }
+                chk(einv_precond_persistent(a, r, y, z, st));
+                const double rzn = dot(r, z);
+                chk(einv_cg_p(a, rzn / rz, z, p, st));
+                rz = rzn;
             }
-            chk(einv_precond(a, r, y, w, z, st));
-            const double rzn = dot(r, z);
-            chk(einv_cg_p(a, rzn / rz, z, p, st));
-            rz = rzn;
         }
         if (!conv) ++cg_unconverged;
         // v = A^{-1} q_i - A^inv q_i, alpha_i = q_i . v, then v orthogonalised twice against q_0..q_i
@@ -1416,6 +1507,58 @@ sinv_status sinv_trace_read(sinv_handle h, sinv_kernel_time* out, int max_entrie
     }
     *count = std::min(c, max_entries);
     if (reset) h->tracer->agg.clear();
+    return SINV_OK;
+}
+
+sinv_status sinv_batch_run(sinv_handle h, int32_t nmat, const double* const* L_vals, const double* const* D_vals,
+                           sinv_precision prec, double* const* G_outs, int m, double* const* N_outs, void* stream) {
+    if (!h || nmat < 0) return SINV_ERR_INVALID_ARG;
+    if (!on_device(h)) return SINV_ERR_INVALID_ARG;
+    const int32_t nb = h->b_n_off.empty() ? 0 : (int32_t)h->b_n_off.size() - 1;
+    if (nb == 0 || nmat != nb) {
+        set_err(h, "sinv_batch_run needs a handle from sinv_batch_symbolic with the same number of matrices");
+        return SINV_ERR_INVALID_ARG;
+    }
+    if (!L_vals || !D_vals || (N_outs && m < 0)) return SINV_ERR_INVALID_ARG;
+    for (int32_t b = 0; b < nb; ++b) {
+        const bool has_L = h->b_L_off[b + 1] > h->b_L_off[b];
+        if ((has_L && !L_vals[b]) || !D_vals[b]) return SINV_ERR_INVALID_ARG;
+    }
+    const HostPlan& P = h->P;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if (!h->db_L) {  // the first call allocates; later calls (and graph captures) do not
+        if ((e = upload(&h->db_L_off, h->b_L_off)) != cudaSuccess || (e = upload(&h->db_D_off, h->b_D_off)) != cudaSuccess ||
+            (e = upload(&h->db_S_off, h->b_S_off)) != cudaSuccess ||
+            (e = cudaMalloc((void**)&h->db_L, std::max<int64_t>(P.nnzL, 1) * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&h->db_D, std::max<int64_t>(P.nD, 1) * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&h->db_G, std::max<int64_t>(P.nnzS, 1) * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&h->db_N, std::max<int64_t>(P.nnzS, 1) * sizeof(double))) != cudaSuccess) {
+            if (e == cudaErrorMemoryAllocation) {
+                set_err(h, "device allocation of the batch buffers failed");
+                return SINV_ERR_OOM;
+            }
+            return cuda_fail(h, e, "batch buffers");
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((e = batch_copy_launch(nb, L_vals, h->db_L_off, 1, h->db_L, h->num_sms, st)) != cudaSuccess ||
+        (e = batch_copy_launch(nb, D_vals, h->db_D_off, 1, h->db_D, h->num_sms, st)) != cudaSuccess)
+        return cuda_fail(h, e, "batch gather");
+    if (G_outs) {
+        sinv_status s = sinv_selinv(h, h->db_L, h->db_D, prec, h->db_G, stream);
+        if (s != SINV_OK) return s;
+        if ((e = batch_copy_launch(nb, const_cast<const double* const*>(G_outs), h->db_S_off, 0, h->db_G, h->num_sms,
+                                   st)) != cudaSuccess)
+            return cuda_fail(h, e, "batch scatter");
+    }
+    if (N_outs) {
+        sinv_status s = ninv_common(h, h->db_L, h->db_D, m, 0.0, prec, h->db_N, nullptr, stream);
+        if (s != SINV_OK) return s;
+        if ((e = batch_copy_launch(nb, const_cast<const double* const*>(N_outs), h->db_S_off, 0, h->db_N, h->num_sms,
+                                   st)) != cudaSuccess)
+            return cuda_fail(h, e, "batch scatter");
+    }
     return SINV_OK;
 }
 

@@ -49,40 +49,6 @@ __global__ void symv_S(int64_t n, const int64_t* __restrict__ fcp, const int32_t
     }
 }
 
-// one level of L y = b (unit lower): the rows of the level, each reading rows of earlier levels
-__global__ void trsv_fwd_level(const int32_t* __restrict__ rows, int count, const int64_t* __restrict__ Lrp,
-                               const int32_t* __restrict__ Lcol, const double* __restrict__ Lval,
-                               const double* __restrict__ b, double* __restrict__ y) {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= count) return;
-    const int i = rows[u];
-    double s = b[i];
-    for (int64_t q = Lrp[i]; q < Lrp[i + 1]; ++q) s = fma(-Lval[q], y[Lcol[q]], s);
-    y[i] = s;
-}
-
-// one level of L^T x = w: column j reads x at the rows i > j of column j of L
-__global__ void trsv_bwd_level(const int32_t* __restrict__ cols, int count, const int64_t* __restrict__ Lcp,
-                               const int32_t* __restrict__ Lri, const int32_t* __restrict__ Lcsr,
-                               const double* __restrict__ Lval, const double* __restrict__ w,
-                               double* __restrict__ x) {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= count) return;
-    const int j = cols[u];
-    double s = w[j];
-    for (int64_t q = Lcp[j]; q < Lcp[j + 1]; ++q) s = fma(-Lval[Lcsr[q]], x[Lri[q]], s);
-    x[j] = s;
-}
-
-// w = D^{-1} y with the per-row diagonal, partner coefficient and partner of D^{-1}
-__global__ void dinv_apply(int64_t n, const double* __restrict__ dr, const double* __restrict__ dp,
-                           const int32_t* __restrict__ part, const double* __restrict__ y, double* __restrict__ w) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t p = part[i];
-        w[i] = p >= 0 ? fma(dr[i], y[i], dp[i] * y[p]) : dr[i] * y[i];
-    }
-}
-
 // per-block partial sums of a . b (a fixed grid: the sum is reproducible)
 __global__ void dot_partial(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
                             double* __restrict__ partial) {
@@ -233,6 +199,136 @@ __global__ void ritz_vectors(int64_t n, int m, int k, int ldv, const double* __r
         }
 }
 
+// ---- persistent triangular solves -----------------------------------------------------
+// One launch per solve instead of one per dependency level: a warp takes the next row
+// (column) in level order from a ticket, waits (bounded) until every row it reads has
+// been published with this call's epoch, computes its value and publishes it with a
+// release store.  A row only waits for rows of earlier levels, handed out before its
+// own ticket to warps that are running, so the schedule cannot deadlock.
+
+__global__ void trsv_prepare(uint32_t* epoch, int32_t* tickets) {
+    uint32_t e = *epoch + 1;
+    *epoch = e == 0 ? 1 : e;
+    tickets[0] = 0;
+    tickets[1] = 0;
+}
+
+// y = L^{-1} b (L unit lower, by rows)
+__global__ void trsv_fwd_persistent(int64_t n, const int32_t* __restrict__ rows, const int64_t* __restrict__ Lrp,
+                                    const int32_t* __restrict__ Lcol, const double* __restrict__ Lval,
+                                    const double* __restrict__ b, double* __restrict__ y, uint32_t* flags,
+                                    const uint32_t* epoch_p, int32_t* ticket, int32_t* status, int64_t limit) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t epoch = *epoch_p;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(ticket, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= n) break;
+        const int i = rows[t];
+        double s = 0.0;
+        bool ok = true;
+        for (int64_t q = Lrp[i] + lane; q < Lrp[i + 1]; q += 32) {
+            const int c = Lcol[q];
+            if (!wait_flag(flags + c, epoch, status, limit)) {
+                ok = false;
+                break;
+            }
+            s = fma(Lval[q], __ldcg(y + c), s);
+        }
+        if (!__all_sync(0xffffffffu, ok)) break;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            __stcg(y + i, b[i] - s);
+            st_release(flags + i, epoch);
+        }
+    }
+}
+
+// x = L^{-T} w with w = D^{-1} y formed on the fly (D^{-1} by rows: diagonal, partner
+// coefficient, partner), L by columns
+__global__ void trsv_bwd_persistent(int64_t n, const int32_t* __restrict__ cols, const int64_t* __restrict__ Lcp,
+                                    const int32_t* __restrict__ Lri, const int32_t* __restrict__ Lcsr,
+                                    const double* __restrict__ Lval, const double* __restrict__ dr,
+                                    const double* __restrict__ dp, const int32_t* __restrict__ part,
+                                    const double* __restrict__ y, double* __restrict__ x, uint32_t* flags,
+                                    const uint32_t* epoch_p, int32_t* ticket, int32_t* status, int64_t limit) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t epoch = *epoch_p;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(ticket, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= n) break;
+        const int j = cols[t];
+        double s = 0.0;
+        bool ok = true;
+        for (int64_t q = Lcp[j] + lane; q < Lcp[j + 1]; q += 32) {
+            const int r = Lri[q];
+            if (!wait_flag(flags + r, epoch, status, limit)) {
+                ok = false;
+                break;
+            }
+            s = fma(Lval[Lcsr[q]], __ldcg(x + r), s);
+        }
+        if (!__all_sync(0xffffffffu, ok)) break;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            const int32_t p = part[j];
+            const double wj = p >= 0 ? fma(dr[j], y[j], dp[j] * y[p]) : dr[j] * y[j];
+            __stcg(x + j, wj - s);
+            st_release(flags + j, epoch);
+        }
+    }
+}
+
+// |D|^{-1} by rows, from D itself: for a 1x1 pivot 1/|d|; for a 2x2 block [a b; b d]
+// with eigenpairs (l_k, u_k) (the closed form of a symmetric 2x2), sum_k u_k u_k^T /
+// |l_k| -- the inverse of the block's absolute value, so that L |D| L^T is an SPD
+// preconditioner.  Written as diagonal, partner coefficient and partner per row, like
+// D^{-1} (part = -1 for a 1x1 pivot).
+__global__ void absdinv_rows(int64_t n, const int32_t* __restrict__ dpos, const int8_t* __restrict__ pstart,
+                             const double* __restrict__ Dval, double* __restrict__ dr, double* __restrict__ dp,
+                             int32_t* __restrict__ part, int32_t* status) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const bool first = pstart[r] != 0;
+        const bool two = first ? (r + 1 < n && pstart[r + 1] == 0) : true;
+        const double* dv = Dval + dpos[r];
+        if (!two) {
+            if (dv[0] == 0.0) set_status(status, ST_SINGULAR);
+            dr[r] = 1.0 / fabs(dv[0]);
+            dp[r] = 0.0;
+            part[r] = -1;
+            continue;
+        }
+        const double a = dv[0], b = dv[1], d = dv[2];
+        const double mean = 0.5 * (a + d), rad = sqrt(0.25 * (a - d) * (a - d) + b * b);
+        const double l1 = mean + rad, l2 = mean - rad;
+        if (l1 == 0.0 || l2 == 0.0) set_status(status, ST_SINGULAR);
+        // unit eigenvector u of l1: (b, l1 - a) or (l1 - d, b), the larger of the two
+        double u0 = b, u1 = l1 - a;
+        if (fabs(l1 - d) > fabs(l1 - a)) {
+            u0 = l1 - d;
+            u1 = b;
+        }
+        const double nu = sqrt(u0 * u0 + u1 * u1);
+        if (nu > 0.0) {
+            u0 /= nu;
+            u1 /= nu;
+        } else {  // b = 0 and a = d: any basis
+            u0 = 1.0;
+            u1 = 0.0;
+        }
+        // |D|^{-1} = u u^T / |l1| + v v^T / |l2|, v = (-u1, u0)
+        const double i1 = 1.0 / fabs(l1), i2 = 1.0 / fabs(l2);
+        dr[r] = first ? u0 * u0 * i1 + u1 * u1 * i2 : u1 * u1 * i1 + u0 * u0 * i2;
+        dp[r] = u0 * u1 * (i1 - i2);
+        part[r] = (int32_t)(first ? r + 1 : r - 1);
+    }
+}
+
 int grid_for(int64_t n, int num_sms) {
     const int64_t g = (n + kThreads - 1) / kThreads;
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)num_sms * 8));
@@ -252,18 +348,19 @@ cudaError_t einv_symv_X(const EinvArgs& a, const double* x, double* y, cudaStrea
     return cudaGetLastError();
 }
 
-cudaError_t einv_precond(const EinvArgs& a, const double* r, double* y, double* w, double* z, cudaStream_t st) {
-    for (int l = 0; l < a.nlev_fwd; ++l) {
-        const int c = a.fwd_ptr_h[l + 1] - a.fwd_ptr_h[l];
-        trsv_fwd_level<<<(c + kThreads - 1) / kThreads, kThreads, 0, st>>>(a.fwd_rows + a.fwd_ptr_h[l], c, a.Lrp,
-                                                                            a.Lcol, a.Lval, r, y);
-    }
-    dinv_apply<<<grid_for(a.n, a.num_sms), kThreads, 0, st>>>(a.n, a.dr, a.dp, a.part, y, w);
-    for (int l = 0; l < a.nlev_bwd; ++l) {
-        const int c = a.bwd_ptr_h[l + 1] - a.bwd_ptr_h[l];
-        trsv_bwd_level<<<(c + kThreads - 1) / kThreads, kThreads, 0, st>>>(a.bwd_cols + a.bwd_ptr_h[l], c, a.Lcp,
-                                                                            a.Lri, a.Lcsr, a.Lval, w, z);
-    }
+cudaError_t einv_precond_persistent(const EinvArgs& a, const double* r, double* y, double* z, cudaStream_t st) {
+    trsv_prepare<<<1, 1, 0, st>>>(a.tepoch, a.tickets);
+    const int grid = a.num_sms * 8;  // 8 warps of 32 per CTA, 8 CTAs per SM
+    trsv_fwd_persistent<<<grid, 256, 0, st>>>(a.n, a.fwd_rows, a.Lrp, a.Lcol, a.Lval, r, y, a.fwd_flags, a.tepoch,
+                                              a.tickets, a.status, a.wait_limit);
+    trsv_bwd_persistent<<<grid, 256, 0, st>>>(a.n, a.bwd_cols, a.Lcp, a.Lri, a.Lcsr, a.Lval, a.dr, a.dp, a.part, y, z,
+                                              a.bwd_flags, a.tepoch, a.tickets + 1, a.status, a.wait_limit);
+    return cudaGetLastError();
+}
+
+cudaError_t einv_absdinv(const EinvArgs& a, const int32_t* dpos, const int8_t* pstart, const double* Dval, double* dr,
+                         double* dp, int32_t* part, cudaStream_t st) {
+    absdinv_rows<<<grid_for(a.n, a.num_sms), kThreads, 0, st>>>(a.n, dpos, pstart, Dval, dr, dp, part, a.status);
     return cudaGetLastError();
 }
 

@@ -173,3 +173,41 @@ cudaError_t debug_wait_launch(uint32_t* flag, int32_t* status, int64_t limit, cu
 }
 
 }  // namespace sinv
+
+// ---- batched runs: per-matrix buffers <-> the batch handle's concatenated layout ----
+namespace sinv {
+namespace {
+
+// blockIdx.y = matrix of this launch's slice; the pointers travel as a kernel argument,
+// so a captured graph replays with the same buffers and no host work
+__global__ void batch_copy_kernel(BatchPtrs ptrs, const int64_t* __restrict__ off, int32_t first, int to_cat,
+                                  double* __restrict__ cat) {
+    const int b = blockIdx.y;
+    const int64_t o0 = off[first + b], len = off[first + b + 1] - o0;
+    double* mine = const_cast<double*>(ptrs.p[b]);
+    if (!mine) return;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+        if (to_cat)
+            cat[o0 + e] = __ldg(mine + e);
+        else
+            mine[e] = cat[o0 + e];
+    }
+}
+
+}  // namespace
+
+cudaError_t batch_copy_launch(int32_t nmat, const double* const* ptrs, const int64_t* d_off, int to_cat, double* cat,
+                              int num_sms, cudaStream_t st) {
+    for (int32_t b0 = 0; b0 < nmat; b0 += kBatchPtrs) {
+        BatchPtrs bp;
+        const int32_t cnt = std::min<int32_t>(kBatchPtrs, nmat - b0);
+        for (int32_t b = 0; b < kBatchPtrs; ++b) bp.p[b] = b < cnt ? ptrs[b0 + b] : nullptr;
+        dim3 grid((unsigned)std::max(1, 2 * num_sms / std::max(1, (int)std::min(cnt, 64))), (unsigned)cnt);
+        batch_copy_kernel<<<grid, 256, 0, st>>>(bp, d_off, b0, to_cat, cat);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace sinv

@@ -83,6 +83,16 @@ cudaError_t selinv_launch(const SelinvArgs& a, int prec, void* work, double* G_o
 cudaError_t mix_launch(const double* G, const double* N, double eps, double* M, int64_t nnz, int num_sms,
                        cudaStream_t st);
 
+// per-matrix device pointers of one batched copy launch (a kernel argument)
+constexpr int kBatchPtrs = 256;
+struct BatchPtrs {
+    const double* p[kBatchPtrs];
+};
+// to_cat = 1: every matrix's buffer into its range [off[b], off[b+1]) of cat; 0: back.
+// A null pointer skips its matrix.  d_off: nmat+1 offsets on the device.
+cudaError_t batch_copy_launch(int32_t nmat, const double* const* ptrs, const int64_t* d_off, int to_cat, double* cat,
+                              int num_sms, cudaStream_t st);
+
 // X_S += sum_l lambda_l V_il V_jl on S_lo.  prec 0: FP64; 1: FP32 products (V converted
 // once into `work`, n*k floats), FP64 accumulation into X.
 cudaError_t lowrank_launch(int64_t n, const int64_t* Srp, const int32_t* Sc, int k, const double* V,
@@ -213,19 +223,27 @@ struct EinvArgs {
     const double* dr;     // D^{-1} per row: diagonal, partner coefficient, partner (-1: 1x1)
     const double* dp;
     const int32_t* part;
-    const int32_t* fwd_rows;  // rows by level of L y = b (device), level starts on the host
-    const int32_t* fwd_ptr_h;
-    int nlev_fwd;
-    const int32_t* bwd_cols;  // columns by level of L^T x = w
-    const int32_t* bwd_ptr_h;
-    int nlev_bwd;
+    const int32_t* fwd_rows;  // rows of L y = b in level order (device)
+    const int32_t* bwd_cols;  // columns of L^T x = w in level order
+    // persistent solves: per-row flags of each solve, their epoch, two tickets
+    uint32_t* fwd_flags;
+    uint32_t* bwd_flags;
+    uint32_t* tepoch;
+    int32_t* tickets;
+    int32_t* status;
+    int64_t wait_limit;
 };
 constexpr int kEinvMaxSteps = 256;  // Lanczos steps (the tridiagonal eigenproblem runs in one CTA)
 int einv_dot_blocks(int num_sms);
 cudaError_t einv_spmv_A(const EinvArgs& a, const double* x, double* y, cudaStream_t st);
 cudaError_t einv_symv_X(const EinvArgs& a, const double* x, double* y, cudaStream_t st);
-// z = L^{-T} D^{-1} L^{-1} r (y, w: work vectors)
-cudaError_t einv_precond(const EinvArgs& a, const double* r, double* y, double* w, double* z, cudaStream_t st);
+// z = L^{-T} D^{-1} L^{-1} r in three launches: y = L^{-1} r, then z = L^{-T} (D^{-1} y), each
+// one persistent launch over all dependency levels (D^{-1}: the dr / dp / part rows given)
+cudaError_t einv_precond_persistent(const EinvArgs& a, const double* r, double* y, double* z, cudaStream_t st);
+// |D|^{-1} per row (diagonal, partner coefficient, partner) from D: the SPD preconditioner
+// L |D| L^T of MINRES
+cudaError_t einv_absdinv(const EinvArgs& a, const int32_t* dpos, const int8_t* pstart, const double* Dval, double* dr,
+                         double* dp, int32_t* part, cudaStream_t st);
 cudaError_t einv_dot(const EinvArgs& a, const double* x, const double* y, double* partial, double* out,
                      cudaStream_t st);
 cudaError_t einv_cg_xr(const EinvArgs& a, double alpha, const double* p, const double* q, double* x, double* r,

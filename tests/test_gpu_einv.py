@@ -120,3 +120,68 @@ def test_lanczos_errors():
     with pytest.raises(SinvError) as e:
         h.einv_lanczos(Av, Lv, Dv, X, torch.zeros_like(q0), 2, 4)
     assert e.value.name == "SINV_ERR_INVALID_ARG"
+
+
+def _indefinite_exact():
+    """A = L D L^T exactly with an indefinite D: negated 1x1 pivots and 2x2 blocks,
+    one of them indefinite (negative determinant)."""
+    import dataclasses
+    f = plant_2x2(lap2d_32().factors, 0.3, 11)
+    dd, do = f.d_diag.copy(), f.d_off.copy()
+    rng = np.random.default_rng(7)
+    ones = np.nonzero((f.pivot_start == 1) & (np.r_[f.pivot_start[1:], 1] == 1))[0]
+    dd[rng.choice(ones, len(ones) // 5, replace=False)] *= -1.0
+    twos = np.nonzero((f.pivot_start == 1) & (np.r_[f.pivot_start[1:], 1] == 0))[0]
+    assert len(twos) >= 2
+    b = twos[0]
+    dd[b + 1] = -abs(dd[b + 1])        # det = a d - b^2 < 0
+    g = dataclasses.replace(f, d_diag=dd, d_off=do)
+    return _ldlt(g), g
+
+
+def _run_solver(A, f, k, steps, solver, seed=0):
+    S = oracle.symbolic_S(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+    G = oracle.selinv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, S)
+    q0 = np.random.default_rng(seed).standard_normal(f.n)
+    h = _handle(f)
+    Ac = h.einv_analyse(A)
+    h.einv_set_solver(solver)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    lam, V, info = h.einv_lanczos(dev(Ac.data), dev(f.L_val), dev(f.D_packed), dev(G), dev(q0), k, steps,
+                                  cg_tol=1e-13, cg_maxit=3000)
+    h.sync_status()
+    return lam, V.cpu().numpy(), info, oracle.core.sym_from_S(f.n, S[0], S[1], G), q0
+
+
+def test_minres_exact_indefinite_factors_converge_in_two_steps():
+    """With A = L D L^T and M = L |D| L^T, M^{-1} A has the eigenvalues +1 and -1 only,
+    so every MINRES solve ends after two iterations: a check of |D|^{-1} (2x2 blocks,
+    one indefinite, included) and of the persistent triangular solves."""
+    A, f = _indefinite_exact()
+    ev = np.linalg.eigvalsh(A.toarray())
+    assert ev.min() < 0 < ev.max()
+    lam, V, info, Xs, q0 = _run_solver(A, f, 2, 10, "minres")
+    assert info["cg_unconverged"] == 0 and info["cg_iterations"] <= 2 * 10
+    lo, Vo = oracle.lanczos_einv(A, Xs, 2, steps=10, q0=q0)
+    np.testing.assert_allclose(lam, lo, rtol=0, atol=1e-9 * np.abs(lo).max())
+
+
+@pytest.mark.parametrize("name", ["diff3d_shifted", "lap2d"])
+def test_minres_lanczos_parity(name):
+    """Indefinite A (3D diffusion shifted into its first spectral gap, planted 2x2
+    pivots) and an SPD case, MINRES inner solves against the oracle's exact ones."""
+    from workloads.configs import diff3d
+    if name == "lap2d":
+        w = lap2d_32()
+        A, f = w.A, w.factors
+    else:
+        w = diff3d(10, m=3)
+        A, f = w.A, plant_2x2(w.factors, 0.05, 13)
+    k, steps = 3, 30
+    lam, V, info, Xs, q0 = _run_solver(A, f, k, steps, "minres")
+    lo, Vo = oracle.lanczos_einv(A, Xs, k, steps=steps, q0=q0)
+    assert info["steps"] == steps and info["cg_unconverged"] == 0
+    np.testing.assert_allclose(lam, lo, rtol=0, atol=1e-8 * np.abs(lo).max())
+    for l in range(k):
+        c = abs(V[:, l] @ Vo[:, l]) / (np.linalg.norm(V[:, l]) * np.linalg.norm(Vo[:, l]))
+        assert c >= 1 - 1e-7, (l, c)
