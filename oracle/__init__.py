@@ -20,6 +20,9 @@ LDL^T Factorization and Spectral Corrections"):
 * ``lanczos_einv``    -- dominant eigenpairs of E_inv = A^{-1} - A^inv
                          (Section 2.5, Algorithm 1 step 5)
 * measures            -- err_1, fill_fact, fill_inv, DoDD (Sections 2.6, 3.2)
+* ``selinv_blocks``, ``ninv_W_columns`` -- the same recurrence on a list of
+                         pivot blocks, and the series on a set of columns
+                         given the columns they read (to check a partition)
 * ``selinv_levels``, ``ninv_threads`` -- the same SelInv and NInv on every
                          host thread (OpenMP over level sets / independent
                          columns and entries; C, csrc/): the all-cores CPU
@@ -53,5 +56,7 @@ from .core import (  # noqa: F401
     selinv_levels,
     ninv_threads,
     host_threads,
+    selinv_blocks,
+    ninv_W_columns,
 )
 from .spai import spai_columns, spai_refine, spai_entries_sampled, spai_pattern, embed, pcg_jacobi  # noqa: F401

@@ -45,6 +45,8 @@ def _load():
         lib.oracle_selinv_levels.restype = ctypes.c_int
         lib.oracle_ninv_threads.argtypes = [ctypes.c_int64, P, P, P, P, P, P, ctypes.c_int, P, P, P]
         lib.oracle_ninv_threads.restype = ctypes.c_int
+        lib.oracle_selinv_blocks.argtypes = [ctypes.c_int64, P, P, P, P, P, P, P, P, P, P, ctypes.c_int64]
+        lib.oracle_selinv_blocks.restype = ctypes.c_int
         lib.oracle_threads.argtypes = []
         lib.oracle_threads.restype = ctypes.c_int
         _lib = lib
@@ -148,6 +150,57 @@ def selinv_levels(n, L_rowptr, L_col, L_val, pivot_start, d_diag, d_off, S=None)
     if rc != 0:
         raise MemoryError("oracle_selinv_levels failed")
     return G, int(nlev[0])
+
+
+def selinv_blocks(n, L_rowptr, L_col, L_val, pivot_start, d_diag, d_off, S, G, blocks):
+    """The scalar recurrence of ``selinv`` on the listed pivot blocks only (each by
+    its first column), in the order given, on G in place (S_lo order): the entries
+    the listed blocks read must already be in G.  For checking a partition of the
+    recurrence."""
+    lib = _load()
+    cp, r, v = _csc_L(n, L_rowptr, L_col, L_val)
+    ps = np.ascontiguousarray(pivot_start, dtype=np.int8)
+    dd = np.ascontiguousarray(d_diag, dtype=np.float64)
+    do = np.ascontiguousarray(d_off, dtype=np.float64)
+    Srp = np.ascontiguousarray(S[0], dtype=np.int64); Sc = np.ascontiguousarray(S[1], dtype=np.int32)
+    bl = np.ascontiguousarray(blocks, dtype=np.int64)
+    assert G.dtype == np.float64 and G.flags.c_contiguous and len(G) == len(Sc)
+    rc = lib.oracle_selinv_blocks(n, _p(cp), _p(r), _p(v), _p(ps), _p(dd), _p(do), _p(Srp), _p(Sc), _p(G),
+                                  _p(bl), len(bl))
+    if rc == -2:
+        raise ZeroDivisionError("singular pivot block")
+    if rc != 0:
+        raise MemoryError("oracle_selinv_blocks failed")
+    return G
+
+
+def ninv_W_columns(n, L_rowptr, L_col, L_val, m, cols, W_known=None):
+    """Columns ``cols`` of W = sum_{t<=m} E^t (no dropping) by the column form of
+    the Horner steps, W_t[:, j] = e_j + sum_{k in struct(j)} E_kj W_{t-1}[:, k]
+    (Eq. (6)).  The columns it reads but does not compute come from ``W_known``:
+    {column: {t: {row: value}}} for every step t = 0..m.  Plain dictionaries,
+    small n.  Returns {t: {column: {row: value}}} for the computed and the known
+    columns."""
+    E = _E(n, L_rowptr, L_col, L_val).tocsc()
+    cols = sorted(set(int(c) for c in cols), reverse=True)
+    steps = {0: {}}
+    known = W_known or {}
+    for t in range(m + 1):
+        steps.setdefault(t, {})
+        for j, per_t in known.items():
+            steps[t][j] = dict(per_t[t])
+    for j in cols:
+        steps[0][j] = {j: 1.0}
+    for t in range(1, m + 1):
+        for j in cols:   # a column reads columns k > j of the previous step only
+            col = {j: 1.0}
+            for q in range(E.indptr[j], E.indptr[j + 1]):
+                k = int(E.indices[q])
+                e = float(E.data[q])
+                for r, w in steps[t - 1][k].items():
+                    col[r] = col.get(r, 0.0) + e * w
+            steps[t][j] = col
+    return steps
 
 
 def ninv_threads(n, L_rowptr, L_col, L_val, pivot_start, d_diag, d_off, m, S=None):

@@ -260,3 +260,22 @@ out:
     free(blk_of); free(level); free(order); free(lstart);
     return rc;
 }
+
+/* The recurrence on a given list of pivot blocks, in the order listed (each block
+ * by its first column), reading and writing G in place: the blocks whose G entries
+ * a listed block reads must already be in G.  Used to check a partition of the
+ * recurrence (some blocks computed elsewhere and copied into G first).  Returns 0,
+ * -1 (allocation) or -2 (singular pivot block). */
+int oracle_selinv_blocks(int64_t n, const int64_t *Lcp, const int32_t *Lr, const double *Lv,
+                         const int8_t *pivot_start, const double *d_diag, const double *d_off,
+                         const int64_t *Srp, const int32_t *Sc, double *G, const int64_t *blocks, int64_t nblocks) {
+    block_scratch ws;
+    int rc = scratch_alloc(&ws, n);
+    for (int64_t e = 0; e < nblocks && rc == 0; ++e) {
+        int64_t b = blocks[e];
+        int64_t j = (b + 1 < n && !pivot_start[b + 1]) ? b + 1 : b;
+        rc = selinv_block(b, j, Lcp, Lr, Lv, d_diag, d_off, Srp, Sc, G, &ws);
+    }
+    scratch_free(&ws);
+    return rc;
+}
