@@ -10,6 +10,8 @@ LDL^T Factorization and Spectral Corrections"):
                          restriction to S of Section 2.1       (C, csrc/selinv_ref.c)
 * ``ninv``            -- truncated Neumann series L^{-1} ~ sum_{t<=m} E_L^t,
                          Eq. (6), and (L^inv)^T D^{-1} L^inv, Eq. (8), on S
+* ``ninv_own``        -- the same with the inverse tolerance delta on its own
+                         pattern (the product's fill controlled by delta too)
 * ``mix``             -- Mix approximation (Section 2.3)
 * ``lowrank_correct`` -- A^inv + V_k Lambda_k V_k^T on S, Eq. (9); diagonal
                          update formula of Section 2.6
@@ -42,6 +44,7 @@ from .core import (  # noqa: F401
     selinv,
     ninv,
     ninv_W,
+    ninv_own,
     ninv_entries_sampled,
     mix,
     lowrank_correct,

@@ -299,6 +299,24 @@ def ninv(n, L_rowptr, L_col, L_val, pivot_start, d_diag, d_off, m, S=None, chunk
     return out
 
 
+def ninv_own(n, L_rowptr, L_col, L_val, pivot_start, d_diag, d_off, m, delta):
+    """NInv on its own pattern (Section 2.2, Eq. (8)): W = ninv_W(m, delta) (the
+    series with off-diagonal |w| < delta dropped after every Horner step), then
+    N = W^T D^{-1} W, whose fill delta also controls.  Reading of the product's
+    drop: an off-diagonal entry is dropped when |N_ij| < delta sqrt(|N_ii N_jj|)
+    (relative to the diagonal, as N carries D^{-1}'s scale); the diagonal is
+    always kept.  Returns the lower triangle (i >= j) as a CSC matrix with
+    sorted rows."""
+    W = ninv_W(n, L_rowptr, L_col, L_val, m, delta)
+    Y = (_Dinv(n, pivot_start, d_diag, d_off) @ W).tocsc()
+    N = sp.tril((W.T @ Y).tocsc()).tocoo()
+    d = np.asarray((W.T @ Y).diagonal())
+    keep = (N.row == N.col) | (np.abs(N.data) >= delta * np.sqrt(np.abs(d[N.row] * d[N.col])))
+    out = sp.csc_matrix((N.data[keep], (N.row[keep], N.col[keep])), shape=(n, n))
+    out.sort_indices()
+    return out
+
+
 def ninv_entries_sampled(n, L_rowptr, L_col, L_val, pivot_start, d_diag, d_off, m, pairs, delta=0.0):
     """N_ij for a list of (i, j) pairs, one at a time.
 

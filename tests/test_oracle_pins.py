@@ -10,7 +10,7 @@ import scipy.sparse as sp
 
 import oracle
 from workloads import grids
-from workloads.configs import diff3d, lap2d_32
+from workloads.configs import diff3d, lap2d_32, plant_2x2
 from workloads.factor import Factors, ildl
 from workloads.nd import nd_perm
 
@@ -236,6 +236,47 @@ def test_ninv_exact_when_m_reaches_depth():
     assert np.max(np.abs(N - Ainv[_rows(Srp), Sc])) <= 1e-11
     E = -f.L_csr().toarray()
     assert not np.any(np.linalg.matrix_power(E, m + 1))
+
+
+def test_ninv_own_pattern_hand_example():
+    """L = [[1,0,0],[0.5,1,0],[0,0.1,1]], D = I, m = 2, delta = 0.1, worked by hand:
+    the Horner steps in column form give W = [[1,0,0],[-0.5,1,0],[0,-0.1,1]] (the
+    second step's 0.05 in column 0 falls below delta; -0.1 is not below it), then
+    N = W^T W: N_00 = 1.25, N_10 = -0.5, N_11 = 1.01, N_21 = -0.1, N_22 = 1, and the
+    product's drop removes N_21 (0.1 < 0.1 sqrt(1.01)) but keeps N_10."""
+    from workloads.factor import Factors
+    f = Factors(n=3, L_rowptr=np.array([0, 0, 1, 2], dtype=np.int64), L_col=np.array([0, 1], dtype=np.int32),
+                L_val=np.array([0.5, 0.1]), pivot_start=np.ones(3, dtype=np.int8), d_diag=np.ones(3),
+                d_off=np.zeros(3))
+    N = oracle.ninv_own(3, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, 2, 0.1).toarray()
+    want = np.array([[1.25, 0, 0], [-0.5, 1.01, 0], [0, 0, 1.0]])
+    assert np.allclose(N, want, rtol=0, atol=1e-15)
+    W = oracle.ninv_W(3, f.L_rowptr, f.L_col, f.L_val, 2, 0.1).toarray()
+    assert np.allclose(W, [[1, 0, 0], [-0.5, 1, 0], [0, -0.1, 1]], rtol=0, atol=1e-15)
+    # with a smaller tolerance the product keeps N_21 and W keeps the 0.05
+    N2 = oracle.ninv_own(3, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, 2, 0.04).toarray()
+    assert np.isclose(N2[2, 1], -0.1) and np.isclose(N2[2, 0], 0.05)
+
+
+def test_ninv_own_limits():
+    """delta = 0 with m >= depth and exact factors: the whole lower triangle of
+    inv(A); delta huge: W = I and only the diagonal of D^{-1} is left."""
+    w = lap2d_32(tau=0.0)
+    f = w.factors
+    Lc = f.L_csr().tocsc()
+    depth = np.zeros(f.n, int)
+    for j in range(f.n - 1, -1, -1):
+        r = Lc.indices[Lc.indptr[j]:Lc.indptr[j + 1]]
+        if len(r):
+            depth[j] = 1 + depth[r].max()
+    N = oracle.ninv_own(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, int(depth.max()), 0.0)
+    Ainv = np.tril(np.linalg.inv(w.A.toarray()))
+    assert np.max(np.abs(N.toarray() - Ainv)) <= 1e-11
+    assert N.nnz == np.count_nonzero(np.abs(Ainv) > 1e-300)
+    g = plant_2x2(lap2d_32().factors, 0.2, 1)
+    N = oracle.ninv_own(g.n, g.L_rowptr, g.L_col, g.L_val, g.pivot_start, g.d_diag, g.d_off, 3, 1e30)
+    Dinv = oracle.core._Dinv(g.n, g.pivot_start, g.d_diag, g.d_off).diagonal()
+    assert N.nnz == g.n and np.allclose(N.diagonal(), Dinv, rtol=1e-15)
 
 
 def test_ninv_sampled_matches_full():
