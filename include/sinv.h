@@ -204,6 +204,28 @@ sinv_status sinv_ninv_drop(sinv_handle h, const double *L_val, const double *D_v
 sinv_status sinv_ninv_stack(sinv_handle h, const double *L_val, const double *D_val, int m,
                             sinv_precision prec, double *N_stack, void *stream);
 
+/* NInv on its own pattern (Section 2.2, Eqs. (6) and (8)): the inverse
+ * tolerance delta sparsifies both W = L^inv and the product W^T D^{-1} W, so
+ * the result is a sparse approximate inverse whose pattern depends only on the
+ * sizes of the entries (not on S).  W is built by the m Horner steps of
+ * sinv_ninv_drop (off-diagonal |w| < delta dropped after every step), each
+ * step compacted so the next one only streams the survivors; the product is
+ * formed by columns through the rows of W and keeps the diagonal and the
+ * entries with |N_ij| >= delta sqrt(|N_ii N_jj|) (the reading of "delta
+ * controls the sparsity of the product").  The result is the lower triangle
+ * N_lo in CSC (column j: rows i >= j, in no particular order), kept by the
+ * handle until the next call: sinv_ninv_own_size gives its size and the size
+ * of W after every step (nnz_W_steps[t], t = 0..m), sinv_ninv_own_copy copies
+ * it into caller-owned device buffers (colptr n+1, rows and values nnz).
+ * Synchronous on `stream` (sizes are read back after every step).
+ * delta = 0 keeps every structural entry (the product's pattern then grows
+ * like (L^{-1})^T L^{-1}).  Errors: SINV_ERR_INVALID_ARG (m < 0, delta < 0),
+ * SINV_ERR_UNSUPPORTED (m > 30), SINV_ERR_OOM (the product's bound too large). */
+sinv_status sinv_ninv_own(sinv_handle h, const double *L_val, const double *D_val, int m, double delta,
+                          void *stream);
+sinv_status sinv_ninv_own_size(sinv_handle h, int64_t *nnz_N_lo, int64_t *nnz_W_steps, int32_t max_steps);
+sinv_status sinv_ninv_own_copy(sinv_handle h, int64_t *N_colptr, int32_t *N_row, double *N_val, void *stream);
+
 /* Mix (Section 2.3): M_ij = G_ij where |G_ij| > eps, else N_ij, on S.
  *   G_S, N_S, M_S [|S_lo|]: device (M_S may alias G_S or N_S). */
 sinv_status sinv_mix(sinv_handle h, const double *G_S, const double *N_S, double eps,

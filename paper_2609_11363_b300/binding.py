@@ -33,7 +33,7 @@ EXPORTS = [
     "sinv_mlp_param_count", "sinv_mlp_create", "sinv_mlp_destroy", "sinv_mlp_get_params", "sinv_mlp_set_params",
     "sinv_mlp_features", "sinv_mlp_targets", "sinv_mlp_grad", "sinv_mlp_train_step", "sinv_mlp_predict",
     "sinv_mlp_sync_status", "sinv_timeline_enable", "sinv_timeline_read", "sinv_batch_run",
-    "sinv_einv_set_solver",
+    "sinv_einv_set_solver", "sinv_ninv_own", "sinv_ninv_own_size", "sinv_ninv_own_copy",
 ]
 
 
@@ -115,6 +115,9 @@ def load_library():
     lib.sinv_timeline_read.argtypes = [H, P, I64, P]
     lib.sinv_batch_run.argtypes = [H, ctypes.c_int32, P, P, ctypes.c_int, P, ctypes.c_int, P, P]
     lib.sinv_einv_set_solver.argtypes = [H, ctypes.c_int32]
+    lib.sinv_ninv_own.argtypes = [H, P, P, ctypes.c_int, ctypes.c_double, P]
+    lib.sinv_ninv_own_size.argtypes = [H, ctypes.POINTER(I64), P, ctypes.c_int32]
+    lib.sinv_ninv_own_copy.argtypes = [H, P, P, P, P]
     lib.sinv_batch_symbolic.argtypes = [ctypes.c_int32, P, P, P, P, ctypes.POINTER(_Opts), ctypes.POINTER(H)]
     lib.sinv_batch_layout.argtypes = [H, ctypes.POINTER(ctypes.c_int32), P, P, P, P]
     lib.sinv_lowrank_correct_noalloc.argtypes = [I64, P, P, ctypes.c_int, P, P, P, P]
@@ -510,6 +513,22 @@ class Handle:
                                                    _check_tensor(lam, "lambda", k), PREC[prec],
                                                    _check_tensor(X, "X_S", self.nnz_S), _stream_ptr(stream)))
         return X
+
+    def ninv_own(self, L_val, D_val, m, delta, stream=None):
+        """NInv on its own pattern: (colptr, rows, values) of the lower triangle in CSC
+        (CUDA tensors) and the nnz of W after every Horner step."""
+        self._check(self._lib.sinv_ninv_own(self._h, _check_tensor(L_val, "L_val"), _check_tensor(D_val, "D_val"),
+                                            int(m), float(delta), _stream_ptr(stream)))
+        nnz = ctypes.c_int64()
+        steps = np.zeros(int(m) + 1, dtype=np.int64)
+        self._check(self._lib.sinv_ninv_own_size(self._h, ctypes.byref(nnz), _np_ptr(steps), int(m) + 1))
+        cp = torch.empty(self.n + 1, dtype=torch.int64, device=self.device)
+        rows = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=self.device)
+        vals = torch.empty(max(nnz.value, 1), dtype=torch.float64, device=self.device)
+        self._check(self._lib.sinv_ninv_own_copy(self._h, _check_tensor(cp, "colptr", None, torch.int64),
+                                                 _check_tensor(rows, "rows", None, torch.int32),
+                                                 _check_tensor(vals, "vals"), _stream_ptr(stream)))
+        return cp, rows[:nnz.value], vals[:nnz.value], steps
 
     def ninv_stack(self, L_val, D_val, m, prec="fp64", out=None, stream=None):
         """NInv on S for the truncations after 0..m terms: tensor [(m+1), |S_lo|]."""

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT = os.path.join(HERE, "libsinv.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "selinv.cu", "selinv_tc.cu", "ninv.cu", "ninv_map.cu", "elementwise.cu", "mlp.cu", "spai.cu", "einv.cu", "symbolic.cpp"]
+SOURCES = ["api.cu", "selinv.cu", "selinv_tc.cu", "ninv.cu", "ninv_map.cu", "ninv_own.cu", "elementwise.cu", "mlp.cu", "spai.cu", "einv.cu", "symbolic.cpp"]
 HEADERS = ["plan.h", "kernels.h", "device.cuh", "hash.cuh", "tc.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

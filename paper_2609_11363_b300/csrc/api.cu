@@ -136,6 +136,12 @@ struct sinv_handle_s {
     uint32_t* dtc_arrive_t = nullptr;
     double* dtc_z = nullptr;
     bool tc_ready = false;
+    // NInv on its own pattern: result (CSC of N_lo) and the sizes of the last call
+    int64_t* down_cp = nullptr;
+    int32_t* down_r = nullptr;
+    double* down_v = nullptr;
+    int64_t own_nnz = 0, own_nnzW = 0;
+    std::vector<int64_t> own_nnzW_steps;
     // per-supernode timeline of SelInv (allocated while enabled)
     unsigned long long* dtl_first = nullptr;
     unsigned long long* dtl_last = nullptr;
@@ -242,7 +248,7 @@ void free_all(sinv_handle h) {
                     h->dsn, h->dorder, h->downer, h->dCrow, h->dLmap, h->dJJl, h->dJJs, h->dhit_ik, h->dhit_pos,
                     h->dhrow, h->ditems, h->dxsum_off, h->dxsum, h->darrive, h->ddone, h->depoch, h->dticket, h->dstatus, h->ddebug_flag, h->dscratch, h->dwork, h->dWcp,
                     h->dWr, h->dgrp, h->dtc_items, h->dtc_map, h->dtc_deps, h->dtc_ticket, h->dtc_mirror, h->dtc_arrive_t,
-                    h->dtc_z, h->dtl_first, h->dtl_last, h->db_L_off, h->db_D_off, h->db_S_off, h->db_L, h->db_D,
+                    h->dtc_z, h->dtl_first, h->dtl_last, h->down_cp, h->down_r, h->down_v, h->db_L_off, h->db_D_off, h->db_S_off, h->db_L, h->db_D,
                     h->db_G, h->db_N};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -261,6 +267,19 @@ sinv_status ensure_work(sinv_handle h, size_t bytes) {
     h->work_bytes = bytes;
     return SINV_OK;
 }
+
+// a device buffer freed at scope exit (the own-pattern call's temporaries)
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    template <class T>
+    T* as() {
+        return reinterpret_cast<T*>(p);
+    }
+};
+cudaError_t dev_alloc(DevBuf& b, size_t bytes) { return cudaMalloc(&b.p, std::max<size_t>(bytes, 8)); }
 
 bool valid_prec(int p) { return p == SINV_FP64 || p == SINV_FP32 || p == SINV_FP32X2; }
 bool tc_prec(int p) { return p == SINV_TF32_FP32ACC || p == SINV_BF16_FP32ACC; }
@@ -1560,6 +1579,212 @@ sinv_status sinv_batch_run(sinv_handle h, int32_t nmat, const double* const* L_v
             return cuda_fail(h, e, "batch scatter");
     }
     return SINV_OK;
+}
+
+sinv_status sinv_ninv_own(sinv_handle h, const double* L_val, const double* D_val, int m, double delta, void* stream) {
+    if (!h || m < 0 || !(delta >= 0.0)) return SINV_ERR_INVALID_ARG;
+    if (!on_device(h)) return SINV_ERR_INVALID_ARG;
+    if (m > 30) {
+        set_err(h, "m > 30 is not supported");
+        return SINV_ERR_UNSUPPORTED;
+    }
+    const HostPlan& P = h->P;
+    const int64_t n = P.n;
+    if (n == 0) return SINV_OK;
+    if (!D_val || (P.nnzL > 0 && !L_val)) return SINV_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    // the structural pattern of the series for m: capacities of the Horner steps
+    if (h->W.m != m) {
+        std::string err;
+        try {
+            err = build_ninv_plan(P, m, h->W);
+        } catch (const std::bad_alloc&) {
+            set_err(h, "host allocation failed building the Neumann pattern");
+            return SINV_ERR_OOM;
+        }
+        if (!err.empty()) {
+            h->W.m = -1;
+            set_err(h, err);
+            return SINV_ERR_UNSUPPORTED;
+        }
+        ninv_maps_free(h->X);
+        h->index_tried_m = -1;
+        if (h->dWcp) cudaFree(h->dWcp);
+        if (h->dWr) cudaFree(h->dWr);
+        if (h->dgrp) cudaFree(h->dgrp);
+        h->dWcp = nullptr; h->dWr = nullptr; h->dgrp = nullptr;
+        if ((e = upload(&h->dWcp, h->W.Wcp)) != cudaSuccess || (e = upload(&h->dWr, h->W.Wr)) != cudaSuccess ||
+            (e = upload(&h->dgrp, h->W.grp)) != cudaSuccess) {
+            h->W.m = -1;
+            return cuda_fail(h, e, "upload Neumann pattern");
+        }
+    }
+    TraceScope trace_scope(h->tracer);
+    const int64_t cap = std::max<int64_t>(h->W.nnzW, n);
+    const int grid = own_grid_ctas(h->num_sms);
+    auto fail = [&](cudaError_t err, const char* what) -> sinv_status {
+        if (err == cudaErrorMemoryAllocation) {
+            set_err(h, std::string("device allocation failed: ") + what);
+            return SINV_ERR_OOM;
+        }
+        return cuda_fail(h, err, what);
+    };
+    DevBuf cpA, rA, vA, cpB, rB, vB, rS, vS, cnt, dr, dp, part, ticket, gk, gv;
+    int64_t gslice = own_table_slots(2 * std::max<int64_t>(h->W.max_col, 1));
+    if ((e = dev_alloc(cpA, (n + 1) * 8)) != cudaSuccess || (e = dev_alloc(rA, cap * 4)) != cudaSuccess ||
+        (e = dev_alloc(vA, cap * 8)) != cudaSuccess || (e = dev_alloc(cpB, (n + 1) * 8)) != cudaSuccess ||
+        (e = dev_alloc(rB, cap * 4)) != cudaSuccess || (e = dev_alloc(vB, cap * 8)) != cudaSuccess ||
+        (e = dev_alloc(rS, cap * 4)) != cudaSuccess || (e = dev_alloc(vS, cap * 8)) != cudaSuccess ||
+        (e = dev_alloc(cnt, (n + 1) * 8)) != cudaSuccess || (e = dev_alloc(dr, n * 8)) != cudaSuccess ||
+        (e = dev_alloc(dp, n * 8)) != cudaSuccess || (e = dev_alloc(part, n * 4)) != cudaSuccess ||
+        (e = dev_alloc(ticket, 64)) != cudaSuccess || (e = dev_alloc(gk, (size_t)grid * gslice * 4)) != cudaSuccess ||
+        (e = dev_alloc(gv, (size_t)grid * gslice * 8)) != cudaSuccess)
+        return fail(e, "NInv own-pattern work");
+    NinvArgs na{};
+    na.n = n;
+    na.dpos = h->ddpos;
+    na.pstart = h->dpstart;
+    na.Dval = D_val;
+    na.num_sms = h->num_sms;
+    na.status = h->dstatus;
+    ninv_dinv_launch(na, dr.as<double>(), dp.as<double>(), part.as<int32_t>(), st);
+    OwnArgs a;
+    a.n = n;
+    a.num_sms = h->num_sms;
+    a.Lcp = h->dLcp;
+    a.Lri = h->dLri;
+    a.Lcsr = h->dLcsr;
+    a.Lval = L_val;
+    a.Wcp = h->dWcp;
+    a.delta = delta;
+    a.dr = dr.as<double>();
+    a.dp = dp.as<double>();
+    a.part = part.as<int32_t>();
+    a.gkeys = gk.as<int32_t>();
+    a.gvals = gv.as<double>();
+    a.gslice = gslice;
+    a.ticket = ticket.as<int32_t>();
+    // W_0 = I, then m Horner steps, each compacted
+    h->own_nnzW_steps.assign(1, n);
+    if ((e = own_identity_launch(n, cpA.as<int64_t>(), rA.as<int32_t>(), vA.as<double>(), h->num_sms, st)) !=
+        cudaSuccess)
+        return fail(e, "NInv own-pattern identity");
+    for (int t = 1; t <= m; ++t) {
+        if ((e = own_horner_launch(a, t, cpA.as<int64_t>(), rA.as<int32_t>(), vA.as<double>(), rS.as<int32_t>(),
+                                   vS.as<double>(), cnt.as<int64_t>(), st)) != cudaSuccess ||
+            (e = own_scan_launch(n, cnt.as<int64_t>(), cpB.as<int64_t>(), st)) != cudaSuccess ||
+            (e = own_compact_launch(n, h->dWcp, cpB.as<int64_t>(), rS.as<int32_t>(), vS.as<double>(),
+                                    rB.as<int32_t>(), vB.as<double>(), h->num_sms, st)) != cudaSuccess)
+            return fail(e, "NInv own-pattern Horner step");
+        std::swap(cpA.p, cpB.p);
+        std::swap(rA.p, rB.p);
+        std::swap(vA.p, vB.p);
+        int64_t nz = 0;
+        if ((e = cudaMemcpyAsync(&nz, cpA.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return fail(e, "NInv own-pattern sizes");
+        h->own_nnzW_steps.push_back(nz);
+    }
+    const int64_t nnzW = h->own_nnzW_steps.back();
+    // W by rows, the diagonal of N and the bound of every column of N
+    DevBuf rowcnt, rp, fill, rc, rv, diag, bound, off;
+    if ((e = dev_alloc(rowcnt, (n + 1) * 8)) != cudaSuccess || (e = dev_alloc(rp, (n + 1) * 8)) != cudaSuccess ||
+        (e = dev_alloc(fill, (n + 1) * 8)) != cudaSuccess || (e = dev_alloc(rc, nnzW * 4)) != cudaSuccess ||
+        (e = dev_alloc(rv, nnzW * 8)) != cudaSuccess || (e = dev_alloc(diag, n * 8)) != cudaSuccess ||
+        (e = dev_alloc(bound, (n + 1) * 8)) != cudaSuccess || (e = dev_alloc(off, (n + 1) * 8)) != cudaSuccess)
+        return fail(e, "NInv own-pattern product work");
+    if ((e = own_transpose_launch(n, nnzW, cpA.as<int64_t>(), rA.as<int32_t>(), vA.as<double>(), rowcnt.as<int64_t>(),
+                                  rp.as<int64_t>(), fill.as<int64_t>(), rc.as<int32_t>(), rv.as<double>(), h->num_sms,
+                                  st)) != cudaSuccess ||
+        (e = own_diag_launch(a, cpA.as<int64_t>(), rA.as<int32_t>(), vA.as<double>(), rp.as<int64_t>(),
+                             diag.as<double>(), bound.as<int64_t>(), st)) != cudaSuccess ||
+        (e = own_scan_launch(n, bound.as<int64_t>(), off.as<int64_t>(), st)) != cudaSuccess)
+        return fail(e, "NInv own-pattern diagonal");
+    int64_t total = 0;
+    std::vector<int64_t> hb(n);
+    if ((e = cudaMemcpyAsync(&total, off.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(hb.data(), bound.as<int64_t>(), n * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return fail(e, "NInv own-pattern bounds");
+    const int64_t maxb = hb.empty() ? 1 : *std::max_element(hb.begin(), hb.end());
+    // the product's tables: Y[:, j] in the first half of a CTA's slice, N's column in the second
+    const int64_t half = std::max<int64_t>(own_table_slots(2 * std::max<int64_t>(h->W.max_col, 1)),
+                                           own_table_slots(std::max<int64_t>(maxb, 1)));
+    if (2 * half > gslice) {
+        gslice = 2 * half;
+        cudaFree(gk.p);
+        cudaFree(gv.p);
+        gk.p = gv.p = nullptr;
+        if ((e = dev_alloc(gk, (size_t)grid * gslice * 4)) != cudaSuccess ||
+            (e = dev_alloc(gv, (size_t)grid * gslice * 8)) != cudaSuccess)
+            return fail(e, "NInv own-pattern product tables");
+        a.gkeys = gk.as<int32_t>();
+        a.gvals = gv.as<double>();
+        a.gslice = gslice;
+    }
+    DevBuf nrS, nvS;
+    if ((e = dev_alloc(nrS, total * 4)) != cudaSuccess || (e = dev_alloc(nvS, total * 8)) != cudaSuccess)
+        return fail(e, "NInv own-pattern product slots");
+    if ((e = own_product_launch(a, cpA.as<int64_t>(), rA.as<int32_t>(), vA.as<double>(), rp.as<int64_t>(),
+                                rc.as<int32_t>(), rv.as<double>(), diag.as<double>(), off.as<int64_t>(),
+                                bound.as<int64_t>(), nrS.as<int32_t>(), nvS.as<double>(), cnt.as<int64_t>(), st)) !=
+            cudaSuccess ||
+        (e = own_scan_launch(n, cnt.as<int64_t>(), cpB.as<int64_t>(), st)) != cudaSuccess)
+        return fail(e, "NInv own-pattern product");
+    int64_t nnzN = 0;
+    if ((e = cudaMemcpyAsync(&nnzN, cpB.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return fail(e, "NInv own-pattern size");
+    // the result, owned by the handle
+    if (h->down_cp) cudaFree(h->down_cp);
+    if (h->down_r) cudaFree(h->down_r);
+    if (h->down_v) cudaFree(h->down_v);
+    h->down_cp = nullptr;
+    h->down_r = nullptr;
+    h->down_v = nullptr;
+    if ((e = cudaMalloc((void**)&h->down_cp, (n + 1) * 8)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&h->down_r, std::max<int64_t>(nnzN, 1) * 4)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&h->down_v, std::max<int64_t>(nnzN, 1) * 8)) != cudaSuccess)
+        return fail(e, "NInv own-pattern result");
+    if ((e = cudaMemcpyAsync(h->down_cp, cpB.p, (n + 1) * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+        (e = own_compact_launch(n, off.as<int64_t>(), h->down_cp, nrS.as<int32_t>(), nvS.as<double>(), h->down_r,
+                                h->down_v, h->num_sms, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return fail(e, "NInv own-pattern compaction");
+    h->own_nnz = nnzN;
+    h->own_nnzW = nnzW;
+    return SINV_OK;
+}
+
+sinv_status sinv_ninv_own_size(sinv_handle h, int64_t* nnz_N_lo, int64_t* nnz_W_steps, int32_t max_steps) {
+    if (!h || !nnz_N_lo || max_steps < 0 || (max_steps > 0 && !nnz_W_steps)) return SINV_ERR_INVALID_ARG;
+    if (!h->down_cp) {
+        set_err(h, "sinv_ninv_own has not run");
+        return SINV_ERR_INVALID_ARG;
+    }
+    *nnz_N_lo = h->own_nnz;
+    for (int32_t t = 0; t < max_steps; ++t)
+        nnz_W_steps[t] = t < (int32_t)h->own_nnzW_steps.size() ? h->own_nnzW_steps[t] : 0;
+    return SINV_OK;
+}
+
+sinv_status sinv_ninv_own_copy(sinv_handle h, int64_t* N_colptr, int32_t* N_row, double* N_val, void* stream) {
+    if (!h || !N_colptr || !N_row || !N_val) return SINV_ERR_INVALID_ARG;
+    if (!h->down_cp) {
+        set_err(h, "sinv_ninv_own has not run");
+        return SINV_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(N_colptr, h->down_cp, (h->P.n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && h->own_nnz > 0)
+        e = cudaMemcpyAsync(N_row, h->down_r, h->own_nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && h->own_nnz > 0)
+        e = cudaMemcpyAsync(N_val, h->down_v, h->own_nnz * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? SINV_OK : cuda_fail(h, e, "NInv own-pattern copy");
 }
 
 sinv_status sinv_timeline_enable(sinv_handle h, int enable) {

@@ -1,0 +1,75 @@
+"""NInv on its own pattern (Section 2.2: delta sparsifies W = L^inv and the
+product W^T D^{-1} W) against the oracle's ninv_own.
+
+The pattern is decided in FP64 on both sides from sums in different orders, so
+an entry whose magnitude sits at its drop threshold (within 1e-9 relative) may
+fall either way; every other entry of the two patterns must agree, and the values
+on the common pattern agree within 1e-10 (scaled by |N_ij| + sqrt|N_ii N_jj|, as
+the other FP64 NInv tests)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import torch
+
+import oracle
+from workloads.configs import diff3d, lap2d_32, plant_2x2, random_factors
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def _cases():
+    return [("lap2d", lap2d_32().factors), ("diff3d_2x2", plant_2x2(diff3d(10, m=3).factors, 0.05, 13)),
+            ("random_2x2", random_factors(400, 0.02, 0.1, 5))]
+
+
+def _gpu(h, f, m, delta):
+    cp, rows, vals, steps = h.ninv_own(_dev(f.L_val), _dev(f.D_packed), m, delta)
+    h.sync_status()
+    cp, rows, vals = cp.cpu().numpy(), rows.cpu().numpy(), vals.cpu().numpy()
+    N = sp.csc_matrix((vals, rows, cp), shape=(f.n, f.n))
+    N.sort_indices()
+    return N, steps
+
+
+@pytest.mark.parametrize("name,f", _cases(), ids=[c[0] for c in _cases()])
+@pytest.mark.parametrize("delta", [1e-1, 1e-2, 1e-3])
+def test_ninv_own_matches_oracle(name, f, delta):
+    from paper_2609_11363_b300 import Handle
+    m = 3
+    h = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+    N, steps = _gpu(h, f, m, delta)
+    R = oracle.ninv_own(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, m, delta)
+    W = oracle.ninv_W(f.n, f.L_rowptr, f.L_col, f.L_val, m, delta)
+    assert steps[0] == f.n and steps[m] == W.nnz
+    d = R.diagonal()
+    Rc, Nc = R.tocoo(), N.tocoo()
+    ref = {(int(i), int(j)): v for i, j, v in zip(Rc.row, Rc.col, Rc.data)}
+    got = {(int(i), int(j)): v for i, j, v in zip(Nc.row, Nc.col, Nc.data)}
+    assert all(i >= j for i, j in got)
+    for key in set(ref) ^ set(got):      # only entries at the threshold may differ
+        v = ref.get(key, got.get(key))
+        thr = delta * np.sqrt(abs(d[key[0]] * d[key[1]]))
+        assert abs(abs(v) - thr) <= 1e-9 * thr, (key, v, thr)
+    common = set(ref) & set(got)
+    assert len(common) >= 0.999 * len(ref)
+    worst = max(abs(got[k] - ref[k]) / (abs(ref[k]) + np.sqrt(abs(d[k[0]] * d[k[1]]))) for k in common)
+    assert worst <= 1e-10, worst
+
+
+def test_fill_falls_with_delta():
+    """Fewer entries in W and in the product as delta grows (the paper's fill
+    behaviour), and the diagonal is always there."""
+    from paper_2609_11363_b300 import Handle
+    f = plant_2x2(diff3d(12, m=3).factors, 0.05, 13)
+    h = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+    sizes = []
+    for delta in (1e-3, 1e-2, 1e-1):
+        N, steps = _gpu(h, f, 3, delta)
+        assert np.all(N.diagonal() != 0)
+        sizes.append((steps[3], N.nnz))
+    assert sizes[0][0] > sizes[1][0] > sizes[2][0]
+    assert sizes[0][1] > sizes[1][1] > sizes[2][1] >= f.n
