@@ -50,12 +50,14 @@ def parse():
     p.add_argument("--ninv-delta", type=float, default=0.0,
                    help="inverse tolerance of NInv: off-diagonal |w| < delta dropped after each Horner step")
     p.add_argument("--workload", default="diff3d",
-                   choices=["diff3d", "batch9pt", "learned", "elastic", "covariance", "band"],
+                   choices=["diff3d", "batch9pt", "learned", "elastic", "covariance", "band", "ninv_own"],
                    help="diff3d: the 64^3 step (default); batch9pt: 256 matrices in one graph-captured launch; "
                         "learned: the trained NInv->SelInv correction on 128^3; elastic: the 27-point 3-dof "
                         "operator (N^3 nodes, --elastic-size N); covariance: the (1-d/3)^4 covariance-type "
                         "matrix on an N x N grid (--cov-size N); band: the dense-row microbenchmark shape "
-                        "(--band-n, --band-b, --band-tau), SelInv FP64 vs the tensor-core forms")
+                        "(--band-n, --band-b, --band-tau), SelInv FP64 vs the tensor-core forms; ninv_own: NInv "
+                        "on its own delta-sparsified pattern on the 64^3 factors (--own-deltas)")
+    p.add_argument("--own-deltas", default="1e-1,1e-2", help="ninv_own: inverse tolerances to time")
     p.add_argument("--band-n", type=int, default=12288)
     p.add_argument("--band-b", type=int, default=1024)
     p.add_argument("--band-tau", type=float, default=1e-6)
@@ -639,6 +641,10 @@ def run_extra(args, rank, world):
     if args.workload == "covariance":
         run_covariance(args, rank, world, dev)
         return
+    if args.workload == "ninv_own":
+        torch.cuda.set_device(dev)
+        run_ninv_own(args, rank, world, dev)
+        return
     # learned correction
     from paper_2609_11363_b300.learned import LearnedCorrection
     torch.cuda.set_device(dev)
@@ -794,6 +800,60 @@ def run_band(args, rank, world, dev, peaks):
             "clocks": clk}
     line["tensor_roofline"]["frac"] = line["tensor_roofline"]["achieved_tflops"] / line["tensor_roofline"]["peak_tflops_tf32"]
     print(json.dumps(line))
+
+
+def run_ninv_own(args, rank, world, dev):
+    """NInv on its own pattern (Section 2.2): delta sparsifies the series W and the
+    product W^T D^{-1} W, so fill and time fall as delta grows.  The 64^3 benchmark
+    factors, m = 4; per delta: the call's wall time (it sizes its outputs on the host
+    between steps, so it synchronises), the kernel times, the fill of W and of the
+    product, against NInv on S."""
+    import torch
+    from paper_2609_11363_b300 import Handle
+    w, f, _, _, t_gen = build_workload(args.size)
+    h = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start, device=dev.index)
+    Lv = torch.as_tensor(f.L_val, device=dev)
+    Dv = torch.as_tensor(f.D_packed, device=dev)
+    N = torch.empty(h.nnz_S, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        out = []
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            out.append((time.perf_counter() - t0) * 1e3)
+        return float(np.median(out))
+
+    rows = []
+    for delta in [float(x) for x in args.own_deltas.split(",")]:
+        ms = timed(lambda: h.ninv_own(Lv, Dv, w.m, delta), args.steps)
+        h.trace(True)
+        cp, r, v, steps = h.ninv_own(Lv, Dv, w.m, delta)
+        torch.cuda.synchronize()
+        kern = h.trace_read()
+        h.trace(False)
+        h.sync_status()
+        rows.append({"delta": delta, "ms": ms, "nnz_W_by_step": [int(x) for x in steps],
+                     "nnz_N_lo": int(r.numel()), "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kern.items()}})
+    del cp, r, v
+    ms_on_S = timed(lambda: h.ninv(Lv, Dv, w.m, "fp64", out=N), args.steps)  # after: its maps take HBM
+    line = {"metric": METRIC, "value": None, "unit": "entries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "ninv_own: " + workload_name(args.size, f, w.m, w.k).split(";")[0]
+                                   + "; NInv m=%d on its own delta-sparsified pattern" % w.m,
+                       "S_lo": int(h.nnz_S), "ninv_on_S_ms": ms_on_S, "by_delta": rows,
+                       "timing": "host wall time per call after a device synchronisation, L2 flushed before each",
+                       "input_gen_s": t_gen},
+            "gpu_launches": None}
+    if rank == 0:
+        print(json.dumps(line))
 
 
 def run_elastic(args, rank, world, dev, peaks):
