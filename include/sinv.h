@@ -101,6 +101,13 @@ typedef struct {
                                < 0 = never.  Without maps (also when a column of the
                                pattern is too long for them) the hash form runs:
                                same results, slower                                  */
+    int64_t selinv_pair_bytes; /* memory the SelInv pair lists may take (8 B for every
+                               pair of C_J x C_J in S, over all supernodes J): 0 = 8 GB,
+                               > 0 = this many bytes, < 0 = none.  Past it the scan
+                               form runs: every supernode reads G~_CC by scanning its
+                               rows of S_lo from the diagonal down to the first row of
+                               C_J, looking each column up in a hash table of C_J.
+                               Same arithmetic per pair; the plan then holds O(nnz L). */
 } sinv_symbolic_opts;
 
 /* Symbolic analysis (host).  Validates the pattern of L and the pivot layout,
@@ -422,6 +429,10 @@ typedef struct {
     int64_t tc_supernodes;    /* supernodes in them                                     */
     int64_t tc_pairs;         /* sum of |C|^2 over them (the contraction's size)        */
     int64_t tc_mirror_bytes;  /* their symmetric band copy of G                         */
+    int64_t selinv_scan;      /* 1: SelInv reads C x C by scanning rows of S (scan form:
+                                 no pair lists; see selinv_pair_bytes), 0: pair lists  */
+    int64_t scan_rows_total;  /* sum over supernodes J of the lengths of the rows C_J of
+                                 S_lo (an upper bound of the scan form's lookups)      */
 } sinv_stats;
 sinv_status sinv_get_stats(sinv_handle h, sinv_stats *out);
 
@@ -456,6 +467,11 @@ sinv_status sinv_trace_enable(sinv_handle h, int enable);
  * Errors: SINV_ERR_INVALID_ARG (not enabled, wrong count), SINV_ERR_OOM. */
 sinv_status sinv_timeline_enable(sinv_handle h, int enable);
 sinv_status sinv_timeline_read(sinv_handle h, uint64_t *stamps, int64_t n_supernodes, void *stream);
+/* Scan form only: the lookups (row entries of S_lo examined) and the pairs of
+ * C_J x C_J in S found by the last sinv_selinv made while the timeline was enabled
+ * (both 0 for a handle with pair lists, or without such a call).  Synchronises
+ * `stream` first. */
+sinv_status sinv_selinv_scan_counts(sinv_handle h, int64_t *lookups, int64_t *pairs, void *stream);
 sinv_status sinv_trace_read(sinv_handle h, sinv_kernel_time *out, int max_entries, int *count, int reset);
 
 const char *sinv_status_string(sinv_status s);

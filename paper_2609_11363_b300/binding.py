@@ -34,6 +34,7 @@ EXPORTS = [
     "sinv_mlp_features", "sinv_mlp_targets", "sinv_mlp_grad", "sinv_mlp_train_step", "sinv_mlp_predict",
     "sinv_mlp_sync_status", "sinv_timeline_enable", "sinv_timeline_read", "sinv_batch_run",
     "sinv_einv_set_solver", "sinv_ninv_own", "sinv_ninv_own_size", "sinv_ninv_own_copy",
+    "sinv_selinv_scan_counts",
 ]
 
 
@@ -46,7 +47,8 @@ class SinvError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("supernode_cap", ctypes.c_int32), ("device", ctypes.c_int32), ("wait_limit", ctypes.c_int64),
-                ("big_pairs", ctypes.c_int64), ("ninv_index_bytes", ctypes.c_int64)]
+                ("big_pairs", ctypes.c_int64), ("ninv_index_bytes", ctypes.c_int64),
+                ("selinv_pair_bytes", ctypes.c_int64)]
 
 
 class _KTime(ctypes.Structure):
@@ -61,7 +63,8 @@ class _Stats(ctypes.Structure):
         ("ninv_index_bytes", ctypes.c_int64), ("product_hits", ctypes.c_int64), ("spai_entries", ctypes.c_int64),
         ("spai_cols_warp", ctypes.c_int64), ("spai_cols_cta", ctypes.c_int64), ("spai_nnz_P", ctypes.c_int64),
         ("einv_levels_fwd", ctypes.c_int64), ("einv_levels_bwd", ctypes.c_int64), ("tc_levels", ctypes.c_int64),
-        ("tc_supernodes", ctypes.c_int64), ("tc_pairs", ctypes.c_int64), ("tc_mirror_bytes", ctypes.c_int64)]
+        ("tc_supernodes", ctypes.c_int64), ("tc_pairs", ctypes.c_int64), ("tc_mirror_bytes", ctypes.c_int64),
+        ("selinv_scan", ctypes.c_int64), ("scan_rows_total", ctypes.c_int64)]
 
 
 def lib_path() -> str:
@@ -113,6 +116,7 @@ def load_library():
     lib.sinv_mlp_sync_status.argtypes = [H, P]
     lib.sinv_timeline_enable.argtypes = [H, ctypes.c_int]
     lib.sinv_timeline_read.argtypes = [H, P, I64, P]
+    lib.sinv_selinv_scan_counts.argtypes = [H, ctypes.POINTER(I64), ctypes.POINTER(I64), P]
     lib.sinv_batch_run.argtypes = [H, ctypes.c_int32, P, P, ctypes.c_int, P, ctypes.c_int, P, P]
     lib.sinv_einv_set_solver.argtypes = [H, ctypes.c_int32]
     lib.sinv_ninv_own.argtypes = [H, P, P, ctypes.c_int, ctypes.c_double, P]
@@ -289,10 +293,11 @@ class Handle:
     """
 
     def __init__(self, n, L_rowptr, L_col, pivot_start, supernode_cap=0, device=0, wait_limit=0, big_pairs=0,
-                 ninv_index_bytes=0, _batch=None):
+                 ninv_index_bytes=0, selinv_pair_bytes=0, _batch=None):
         self._lib = load_library()
         self._h = ctypes.c_void_p()
-        opts = _Opts(int(supernode_cap), int(device), int(wait_limit), int(big_pairs), int(ninv_index_bytes))
+        opts = _Opts(int(supernode_cap), int(device), int(wait_limit), int(big_pairs), int(ninv_index_bytes),
+                     int(selinv_pair_bytes))
         self.device = torch.device("cuda", int(device)) if int(device) >= 0 else None
         if _batch is None:
             self.n = int(n)
@@ -576,6 +581,13 @@ class Handle:
         out = np.zeros((ns, 4), dtype=np.uint64)
         self._check(self._lib.sinv_timeline_read(self._h, _np_ptr(out), ns, _stream_ptr(stream)))
         return out
+
+    def selinv_scan_counts(self, stream=None):
+        """(lookups, pairs) of the last selinv run with the timeline enabled (scan form)."""
+        lk, pr = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self._lib.sinv_selinv_scan_counts(self._h, ctypes.byref(lk), ctypes.byref(pr),
+                                                      _stream_ptr(stream)))
+        return int(lk.value), int(pr.value)
 
     def debug_wait_timeout(self, stream=None) -> int:
         return int(self._lib.sinv_debug_wait_timeout(self._h, _stream_ptr(stream)))

@@ -145,6 +145,10 @@ struct sinv_handle_s {
     // per-supernode timeline of SelInv (allocated while enabled)
     unsigned long long* dtl_first = nullptr;
     unsigned long long* dtl_last = nullptr;
+    unsigned long long* dscan_counts = nullptr;  // lookups and pairs of the scan form (with the timeline)
+    // scan form of SelInv: hash tables of C in global memory for groups whose C is too large
+    int32_t* dgtab = nullptr;
+    int64_t gtab_slots = 0;
     void* dwork = nullptr;
     size_t work_bytes = 0;
     int grid = 0;
@@ -248,7 +252,7 @@ void free_all(sinv_handle h) {
                     h->dsn, h->dorder, h->downer, h->dCrow, h->dLmap, h->dJJl, h->dJJs, h->dhit_ik, h->dhit_pos,
                     h->dhrow, h->ditems, h->dxsum_off, h->dxsum, h->darrive, h->ddone, h->depoch, h->dticket, h->dstatus, h->ddebug_flag, h->dscratch, h->dwork, h->dWcp,
                     h->dWr, h->dgrp, h->dtc_items, h->dtc_map, h->dtc_deps, h->dtc_ticket, h->dtc_mirror, h->dtc_arrive_t,
-                    h->dtc_z, h->dtl_first, h->dtl_last, h->down_cp, h->down_r, h->down_v, h->db_L_off, h->db_D_off, h->db_S_off, h->db_L, h->db_D,
+                    h->dtc_z, h->dtl_first, h->dtl_last, h->dscan_counts, h->dgtab, h->down_cp, h->down_r, h->down_v, h->db_L_off, h->db_D_off, h->db_S_off, h->db_L, h->db_D,
                     h->db_G, h->db_N};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -327,12 +331,14 @@ sinv_status sinv_symbolic(int64_t n, const int64_t* L_rowptr, const int32_t* L_c
     if (!h) return SINV_ERR_OOM;
     int cap = 4;
     int64_t big_pairs = 1024;
+    int64_t pair_bytes = 0;
     if (opts) {
         if (opts->supernode_cap > 0) cap = opts->supernode_cap;
         if (opts->big_pairs > 0) big_pairs = opts->big_pairs;
         h->device = opts->device;
         if (opts->wait_limit > 0) h->wait_limit = opts->wait_limit;
         h->index_budget = opts->ninv_index_bytes;
+        pair_bytes = opts->selinv_pair_bytes;
     }
     cap = std::min(cap, selinv_max_width());
     const bool host_only = h->device < 0;
@@ -349,7 +355,7 @@ sinv_status sinv_symbolic(int64_t n, const int64_t* L_rowptr, const int32_t* L_c
     std::string err;
     try {
         err = build_plan(n, L_rowptr, L_col, pivot_start, cap, big_pairs, selinv_warps_per_cta(), thin_level,
-                         h->P);
+                         h->P, pair_bytes);
     } catch (const std::bad_alloc&) {
         set_err(h, "host allocation failed in the symbolic analysis");
         *out = h;
@@ -423,12 +429,23 @@ sinv_status sinv_symbolic(int64_t n, const int64_t* L_rowptr, const int32_t* L_c
         *out = h;
         return cuda_fail(h, e, "kernel attributes");
     }
-    h->grid = selinv_grid(h->num_sms);
+    h->grid = selinv_grid(h->num_sms, P.scan != 0);
     if (P.max_cw > selinv_cw_smem()) {
         size_t bytes = (size_t)h->grid * selinv_warps_per_cta() * 3 * (size_t)P.max_cw * sizeof(double);
         if ((e = cudaMalloc((void**)&h->dscratch, bytes)) != cudaSuccess) {
             *out = h;
             return cuda_fail(h, e, "selinv scratch");
+        }
+    }
+    if (P.scan && 2 * P.max_c > selinv_scan_table_smem()) {
+        // hash tables of C for the groups whose C exceeds their shared slots
+        int64_t slots = 32;
+        while (slots < 2 * P.max_c) slots <<= 1;
+        h->gtab_slots = slots;
+        size_t bytes = (size_t)h->grid * selinv_warps_per_cta() * 2 * (size_t)slots * sizeof(int32_t);
+        if ((e = cudaMalloc((void**)&h->dgtab, bytes)) != cudaSuccess) {
+            *out = h;
+            return cuda_fail(h, e, "selinv scan tables");
         }
     }
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
@@ -554,6 +571,8 @@ sinv_status sinv_get_stats(sinv_handle h, sinv_stats* s) {
     s->tc_supernodes = P.tc_sn;
     s->tc_pairs = P.tc_pairs;
     s->tc_mirror_bytes = P.tc_levels > 0 ? (P.n - P.tc_row0) * P.tc_width * (int64_t)sizeof(double) : 0;
+    s->selinv_scan = P.scan;
+    s->scan_rows_total = P.scan_rows_total;
     return SINV_OK;
 }
 
@@ -641,6 +660,14 @@ sinv_status sinv_selinv(sinv_handle h, const double* L_val, const double* D_val,
     a.item0 = 0;
     a.tl.first = h->dtl_first;
     a.tl.last = h->dtl_last;
+    a.scan = P.scan;
+    a.Srp = h->dSrp;
+    a.Sc = h->dSc;
+    a.gtab = h->dgtab;
+    a.gtab_slots = h->gtab_slots;
+    a.counts = h->dtl_first ? h->dscan_counts : nullptr;
+    if (a.counts && (e = cudaMemsetAsync(h->dscan_counts, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess)
+        return cuda_fail(h, e, "selinv counters");
     if (h->dtl_first &&
         ((e = cudaMemsetAsync(h->dtl_first, 0xFF, P.sn.size() * sizeof(unsigned long long), st)) != cudaSuccess ||
          (e = cudaMemsetAsync(h->dtl_last, 0, 3 * P.sn.size() * sizeof(unsigned long long), st)) != cudaSuccess))
@@ -1797,20 +1824,42 @@ sinv_status sinv_timeline_enable(sinv_handle h, int enable) {
         if ((e = cudaMalloc((void**)&h->dtl_first, ns * sizeof(unsigned long long))) != cudaSuccess ||
             (e = cudaMalloc((void**)&h->dtl_last, 3 * ns * sizeof(unsigned long long))) != cudaSuccess ||
             (e = cudaMemset(h->dtl_first, 0xFF, ns * sizeof(unsigned long long))) != cudaSuccess ||
-            (e = cudaMemset(h->dtl_last, 0, 3 * ns * sizeof(unsigned long long))) != cudaSuccess) {
+            (e = cudaMemset(h->dtl_last, 0, 3 * ns * sizeof(unsigned long long))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&h->dscan_counts, 2 * sizeof(unsigned long long))) != cudaSuccess ||
+            (e = cudaMemset(h->dscan_counts, 0, 2 * sizeof(unsigned long long))) != cudaSuccess) {
             if (h->dtl_first) cudaFree(h->dtl_first);
             if (h->dtl_last) cudaFree(h->dtl_last);
+            if (h->dscan_counts) cudaFree(h->dscan_counts);
             h->dtl_first = nullptr;
             h->dtl_last = nullptr;
+            h->dscan_counts = nullptr;
             return e == cudaErrorMemoryAllocation ? SINV_ERR_OOM : cuda_fail(h, e, "timeline");
         }
     }
     if (!enable && h->dtl_first) {
         cudaFree(h->dtl_first);
         cudaFree(h->dtl_last);
+        cudaFree(h->dscan_counts);
         h->dtl_first = nullptr;
         h->dtl_last = nullptr;
+        h->dscan_counts = nullptr;
     }
+    return SINV_OK;
+}
+
+sinv_status sinv_selinv_scan_counts(sinv_handle h, int64_t* lookups, int64_t* pairs, void* stream) {
+    if (!h || !lookups || !pairs) return SINV_ERR_INVALID_ARG;
+    *lookups = 0;
+    *pairs = 0;
+    if (!on_device(h)) return SINV_ERR_INVALID_ARG;
+    if (!h->dscan_counts) return SINV_OK;
+    cudaError_t e = cudaSetDevice(h->device);
+    unsigned long long c[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemcpy(c, h->dscan_counts, sizeof(c), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "scan counters");
+    *lookups = (int64_t)c[0];
+    *pairs = (int64_t)c[1];
     return SINV_OK;
 }
 

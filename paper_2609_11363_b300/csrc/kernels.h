@@ -50,6 +50,15 @@ struct SelinvArgs {
     uint32_t* arrive;         // per supernode: parts arrived in this call (zeroed before every launch)
     int32_t item0;            // first work item of this launch (the tensor-core tier runs the ones before)
     Timeline tl;              // per-supernode stamps, or nulls
+    // scan form (no pair lists): S_lo rows, per-group hash tables of C for groups whose
+    // C exceeds shared memory (2 x gtab_slots int32 per group slot: keys, then local
+    // indices), and, when not null, the call's lookups and pairs found (2 counters)
+    int32_t scan;
+    const int64_t* Srp;
+    const int32_t* Sc;
+    int32_t* gtab;
+    int64_t gtab_slots;
+    unsigned long long* counts;
 };
 
 // The tensor-core tier of SelInv (selinv_tc.cu): items over (supernode, row tile,
@@ -73,7 +82,8 @@ cudaError_t selinv_configure();
 // epoch += 1 (skipping 0) and ticket = 0 (and ticket2 = 0 if given), in stream order:
 // keeps the launch graph-capturable
 cudaError_t selinv_prepare(uint32_t* epoch, int32_t* ticket, cudaStream_t st, int32_t* ticket2 = nullptr);
-int selinv_grid(int num_sms);
+int selinv_grid(int num_sms, bool scan);
+int selinv_scan_table_smem();  // hash slots of C per warp in shared memory (scan form)
 int selinv_max_width();
 int selinv_cw_smem();
 int selinv_warps_per_cta();

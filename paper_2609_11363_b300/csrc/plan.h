@@ -110,6 +110,15 @@ struct HostPlan {
     std::vector<int32_t> tc_map;
     std::vector<int32_t> tc_deps;
     int64_t n_levels = 0, max_c = 0, max_w = 0, max_cw = 0, hit_pairs = 0;
+    // scan form: no pair lists are stored; every supernode reads G~_CC by scanning
+    // the rows C of S_lo backwards from the diagonal to C[0] and looking each column
+    // up in a hash table of C.  hrow then holds, per supernode, the prefix over its
+    // rows of the row lengths of S_lo (the work measure that splits rows over CTAs),
+    // and hit_cnt a third of its total (the same scale as a pair count).
+    // scan_rows_total: sum over supernodes of those lengths (an upper bound of the
+    // lookups; the kernel counts the exact ones on request).
+    int32_t scan = 0;
+    int64_t scan_rows_total = 0;
     // algorithmic work of one SelInv: 2 w flops per pair of C x C in S, 2 c w^2 for
     // the diagonal block; bytes: each entry of S in C x C once (8 B) and L_CJ in, X out
     int64_t selinv_flops = 0, selinv_bytes = 0;
@@ -181,9 +190,11 @@ constexpr int kTcMaxChunks = 8;   // 32-column chunks of one part of the contrac
 // big_pairs: supernodes with at least this many pairs are processed by a whole CTA;
 // group: small supernodes per work item (one per warp); levels with fewer than
 // thin_level supernodes give every supernode a whole CTA.
+// pair_bytes: bytes the pair lists may take (> 0), 0 for the default 8 GB, < 0 to
+// take the scan form whatever the size.
 std::string build_plan(int64_t n, const int64_t* L_rowptr, const int32_t* L_col,
                        const int8_t* pivot_start, int supernode_cap, int64_t big_pairs, int group,
-                       int64_t thin_level, HostPlan& P);
+                       int64_t thin_level, HostPlan& P, int64_t pair_bytes = 0);
 std::string build_ninv_plan(const HostPlan& P, int m, NinvPlan& W);
 // A: n x n CSR pattern (host), structurally symmetric; warp_j / warp_e / warp_r: the
 // tier-W caps on pattern rows, staged entries and distinct rows of A.

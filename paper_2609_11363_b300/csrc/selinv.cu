@@ -12,6 +12,13 @@
 // touched.  The pairs are accumulated with shared-memory atomic adds into
 // distinct rows per instruction (see accumulate_pairs).
 //
+// Scan form (for factors whose pair lists would not fit in memory): no list is
+// stored.  A warp walks each row r = C[i] of S_lo backwards from the diagonal to
+// the column C[0], looks every column up in a hash table of C built in phase A,
+// and for each entry (r, C[k]) in C x C adds G(r, C[k]) Lh[i][:] into X[k] and
+// G(r, C[k]) Lh[k][:] into X[i] (the symmetric pair), the latter summed over the
+// warp first.  Reads of S_lo are contiguous; the plan holds nothing per pair.
+//
 // Scheduling: a CTA takes the next work item from a global ticket counter in
 // level-major order.  An item is either one large supernode (the whole CTA
 // works on it, rows split among the warps) or up to eight small ones (one per
@@ -31,6 +38,7 @@ constexpr int kWarps = 8;          // warps per CTA
 constexpr int kCW = 256;           // per-warp shared capacity for c*w values (Lh, X, output positions)
 constexpr int kWMax = 16;          // supernode width limit of this kernel
 constexpr int kBatch = 4;          // chunks of 32 pairs whose G loads are in flight together
+constexpr int kTabW = 256;         // scan form: hash slots of C per warp in shared memory (CTA: all warps')
 
 struct F64 {
     using G = double;
@@ -147,6 +155,120 @@ __device__ __forceinline__ void accumulate_pairs(PairRange& pr, const uint32_t* 
     }
 }
 
+// ---- scan form --------------------------------------------------------------------
+__device__ __forceinline__ uint32_t c_hash(int32_t r, uint32_t mask) { return ((uint32_t)r * 2654435761u) & mask; }
+
+// local index of global row r in the table of C, or -1 (the table holds at most
+// half as many keys as slots, so a free slot ends every probe)
+__device__ __forceinline__ int c_find(const int32_t* keys, const int32_t* vals, uint32_t mask, int32_t r) {
+    uint32_t h = c_hash(r, mask);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const int32_t k = keys[h];
+        if (k == r) return vals[h];
+        if (k < 0) return -1;
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+template <class Gr>
+__device__ __forceinline__ void c_build(int32_t* keys, int32_t* vals, uint32_t mask, const int32_t* Crow, int c) {
+    const int tid = Gr::rank(), gsz = Gr::size();
+    for (uint32_t s = tid; s <= mask; s += gsz) keys[s] = -1;
+    Gr::sync();
+    for (int i = tid; i < c; i += gsz) {
+        const int32_t r = Crow[i];
+        uint32_t h = c_hash(r, mask);
+        while (atomicCAS(keys + h, -1, r) != -1) h = (h + 1) & mask;  // rows of C are distinct
+        vals[h] = i;
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// X -= G~_CC Lh for the rows [i0, i1) of C taken by this warp (row i0 + v, then every
+// nw-th): row r = C[i] of S_lo is read from its diagonal backwards in batches of
+// kBatch x 32 entries while the columns stay >= C[0]; an entry whose column is C[k]
+// adds G Lh[i][:] into X[k] (distinct k within an instruction) and G Lh[k][:] into
+// X[i] (summed over the warp, one atomic add per column of the supernode).
+template <class Form>
+__device__ __forceinline__ void scan_rows(const SelinvArgs& a, const typename Form::G* Gw, const int32_t* Crow, int c,
+                                          int i0, int i1, int v, int nw, const int32_t* keys, const int32_t* vals,
+                                          uint32_t mask, const typename Form::R* lh, typename Form::R* x, int w,
+                                          int lane) {
+    using R = typename Form::R;
+    const int32_t c0 = c > 0 ? Crow[0] : 0;
+    unsigned long long n_look = 0, n_hit = 0;
+    for (int i = i0 + v; i < i1; i += nw) {
+        const int32_t r = Crow[i];
+        const int64_t rs = a.Srp[r];
+        const int64_t pd = a.Sdiag[r];
+        for (int64_t hi = pd;;) {
+            int32_t col[kBatch];
+            int kk[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int64_t p = hi - 1 - lane - 32 * u;
+                col[u] = p >= rs ? __ldg(a.Sc + p) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) kk[u] = col[u] >= c0 ? c_find(keys, vals, mask, col[u]) : -1;
+            R g[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) g[u] = kk[u] >= 0 ? Form::ld(Gw + (hi - 1 - lane - 32 * u)) : R(0);
+            bool any = false;
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                if (kk[u] < 0) continue;
+                any = true;
+                for (int q = 0; q < w; ++q) atomicAdd(x + kk[u] * w + q, -g[u] * lh[i * w + q]);
+            }
+            if (__any_sync(0xffffffffu, any)) {
+                for (int q = 0; q < w; ++q) {
+                    R s = R(0);
+#pragma unroll
+                    for (int u = 0; u < kBatch; ++u)
+                        if (kk[u] >= 0) s += g[u] * lh[kk[u] * w + q];
+                    s = warp_sum(s);
+                    if (lane == 0) atomicAdd(x + i * w + q, -s);
+                }
+            }
+            if (a.counts) {
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    n_look += col[u] >= c0;
+                    n_hit += kk[u] >= 0;
+                }
+            }
+            // go on while the batch's smallest column (lane 31, last chunk) is still in range
+            const int32_t last = __shfl_sync(0xffffffffu, col[kBatch - 1], 31);
+            hi -= 32 * kBatch;
+            if (hi <= rs || last < c0) break;
+        }
+        if (lane == 0) {
+            const R gd = Form::ld(Gw + pd);
+            for (int q = 0; q < w; ++q) atomicAdd(x + i * w + q, -gd * lh[i * w + q]);
+        }
+    }
+    if (a.counts) {
+        n_look = (unsigned long long)warp_sum((double)n_look);
+        n_hit = (unsigned long long)warp_sum((double)n_hit);
+        if (lane == 0) {
+            atomicAdd(a.counts, n_look);
+            atomicAdd(a.counts + 1, n_hit);
+        }
+    }
+}
+
 // One supernode on a group (warp or CTA).  Returns false when a wait gave up.
 // Phase A reads only the inputs and the plan (it overlaps the producers of C);
 // phase B waits for them; phase C reads G, forms X and G_JJ and publishes.
@@ -155,9 +277,9 @@ __device__ __forceinline__ void accumulate_pairs(PairRange& pr, const uint32_t* 
 // global block with device atomics, and the last part to arrive (an arrival count,
 // no waiting) reads the complete X back and finishes the supernode.  Blocks and
 // counts are zeroed in stream order before every launch.
-template <class Form, bool kCta>
+template <class Form, bool kCta, bool kScan>
 __device__ bool process(const SelinvArgs& a, typename Form::G* Gw, int J, uint32_t epoch, WarpSmem* ws,
-                        CtaShared* cs, int64_t gslot, int part = 0, int nparts = 1) {
+                        CtaShared* cs, int64_t gslot, int32_t* tab, int part = 0, int nparts = 1) {
     using R = typename Form::R;
     using Gr = Group<kCta>;
     const SnInfo I = a.sn[J];
@@ -209,7 +331,40 @@ __device__ bool process(const SelinvArgs& a, typename Form::G* Gw, int J, uint32
     PairRange pr;
     pr.e0 = 0;
     pr.e1 = I.hit_cnt;
-    if (kCta) {
+    // scan form: the table of C (this warp's or the CTA's shared slots, else a global
+    // slice) and this part's rows, balanced by the row lengths of S
+    int32_t* tkeys = nullptr;
+    int32_t* tvals = nullptr;
+    uint32_t tmask = 0;
+    int r0 = 0, r1 = c;
+    if (kScan) {
+        uint32_t slots = 32;
+        while ((int64_t)slots < 2 * (int64_t)c) slots <<= 1;
+        const uint32_t avail = kCta ? kTabW * kWarps : kTabW;
+        if (slots <= avail) {
+            tkeys = kCta ? tab : tab + (threadIdx.x >> 5) * kTabW;
+            tvals = tkeys + kTabW * kWarps;
+        } else {
+            tkeys = a.gtab + gslot * 2 * a.gtab_slots;
+            tvals = tkeys + a.gtab_slots;
+        }
+        tmask = slots - 1;
+        if (kCta && nparts > 1) {
+            const int32_t* hrow = a.hrow + I.hrow_off;
+            const int64_t E = hrow[c];
+            auto row_at = [&](int64_t target) -> int {
+                int lo = 0, hi = c;
+                while (lo < hi) {
+                    int mid = (lo + hi) >> 1;
+                    if (hrow[mid] < target) lo = mid + 1; else hi = mid;
+                }
+                return lo;
+            };
+            r0 = part == 0 ? 0 : row_at(E * part / nparts);
+            r1 = part == nparts - 1 ? c : row_at(E * (part + 1) / nparts);
+        }
+        c_build<Gr>(tkeys, tvals, tmask, Crow, c);
+    } else if (kCta) {
         const int32_t* hrow = a.hrow + I.hrow_off;
         const int64_t E = I.hit_cnt;
         const int v = Gr::warp();
@@ -228,7 +383,7 @@ __device__ bool process(const SelinvArgs& a, typename Form::G* Gw, int J, uint32
         pr.e1 = v == kWarps - 1 ? p1 : row_start_at(p0 + (p1 - p0) * (v + 1) / kWarps);
         if (pr.e1 < pr.e0) pr.e1 = pr.e0;
     }
-    load_pairs(hik, hpos, pr.e0, pr.e1, lane, pr.ik, pr.pos);
+    if (!kScan) load_pairs(hik, hpos, pr.e0, pr.e1, lane, pr.ik, pr.pos);
     Gr::sync();
     // Lh = L_CJ L_JJ^{-1}: row by row, columns from the last to the first
     if (w > 1) {
@@ -300,7 +455,10 @@ __device__ bool process(const SelinvArgs& a, typename Form::G* Gw, int J, uint32
     if (tid == 0) tl_mark(a.tl, J, 0);
 
     // ---- phase C ---------------------------------------------------------------------
-    accumulate_pairs<Form>(pr, hik, hpos, Gw, lh, x, w, lane);
+    if (kScan)
+        scan_rows<Form>(a, Gw, Crow, c, r0, r1, Gr::warp(), Gr::nwarps(), tkeys, tvals, tmask, lh, x, w, lane);
+    else
+        accumulate_pairs<Form>(pr, hik, hpos, Gw, lh, x, w, lane);
     Gr::sync();
     if (tid == 0) tl_mark(a.tl, J, 1);
     if (kCta && nparts > 1) {
@@ -363,11 +521,13 @@ __device__ bool process(const SelinvArgs& a, typename Form::G* Gw, int J, uint32
     return true;
 }
 
-template <class Form>
+template <class Form, bool kScan>
 __global__ void __launch_bounds__(kWarps * 32) selinv_persistent(SelinvArgs a, typename Form::G* Gw) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ CtaShared cs;
     WarpSmem* ws = reinterpret_cast<WarpSmem*>(smem_raw) + (threadIdx.x >> 5);
+    // scan form: kWarps x kTabW keys, then as many values, after the warps' regions
+    int32_t* tab = reinterpret_cast<int32_t*>(reinterpret_cast<WarpSmem*>(smem_raw) + kWarps);
     const int warp = threadIdx.x >> 5;
     const uint32_t epoch = *a.epoch;
     for (;;) {
@@ -381,13 +541,13 @@ __global__ void __launch_bounds__(kWarps * 32) selinv_persistent(SelinvArgs a, t
         if (item >= a.nitems || cs.stop) break;
         const WorkItem it = a.items[item];
         if (it.big == 2) {
-            process<Form, true>(a, Gw, a.order[it.first], epoch, ws, &cs, (int64_t)blockIdx.x * kWarps, it.part,
-                                it.count);
+            process<Form, true, kScan>(a, Gw, a.order[it.first], epoch, ws, &cs, (int64_t)blockIdx.x * kWarps, tab,
+                                       it.part, it.count);
         } else if (it.big) {
-            process<Form, true>(a, Gw, a.order[it.first], epoch, ws, &cs, (int64_t)blockIdx.x * kWarps);
+            process<Form, true, kScan>(a, Gw, a.order[it.first], epoch, ws, &cs, (int64_t)blockIdx.x * kWarps, tab);
         } else if (warp < it.count) {
-            process<Form, false>(a, Gw, a.order[it.first + warp], epoch, ws, &cs,
-                                 (int64_t)blockIdx.x * kWarps + warp);
+            process<Form, false, kScan>(a, Gw, a.order[it.first + warp], epoch, ws, &cs,
+                                        (int64_t)blockIdx.x * kWarps + warp, tab);
         }
     }
 }
@@ -405,11 +565,17 @@ __global__ void widen_to_double(const typename Form::G* __restrict__ src, double
         dst[i] = Form::to_d(src[i]);
 }
 
+size_t smem_bytes(bool scan) { return sizeof(WarpSmem) * kWarps + (scan ? 2 * sizeof(int32_t) * kWarps * kTabW : 0); }
+
 template <class Form>
 cudaError_t launch_form(const SelinvArgs& a, typename Form::G* Gw, double* G_out, cudaStream_t st, int grid) {
-    size_t smem = sizeof(WarpSmem) * kWarps;
-    trace_begin("selinv_persistent", st);
-    selinv_persistent<Form><<<grid, kWarps * 32, smem, st>>>(a, Gw);
+    if (a.scan) {
+        trace_begin("selinv_scan", st);
+        selinv_persistent<Form, true><<<grid, kWarps * 32, smem_bytes(true), st>>>(a, Gw);
+    } else {
+        trace_begin("selinv_persistent", st);
+        selinv_persistent<Form, false><<<grid, kWarps * 32, smem_bytes(false), st>>>(a, Gw);
+    }
     trace_end(st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -436,20 +602,29 @@ int selinv_cw_smem() { return kCW; }
 int selinv_warps_per_cta() { return kWarps; }
 
 cudaError_t selinv_configure() {
-    size_t smem = sizeof(WarpSmem) * kWarps;
-    cudaError_t e = cudaFuncSetAttribute(selinv_persistent<F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(selinv_persistent<F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int s0 = (int)smem_bytes(false), s1 = (int)smem_bytes(true);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(selinv_persistent<F64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s0)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(selinv_persistent<F32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s0)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(selinv_persistent<F64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1)) !=
+            cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(selinv_persistent<F32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
 }
 
-int selinv_grid(int num_sms) {
+int selinv_grid(int num_sms, bool scan) {
     int per_sm = 0;
-    size_t smem = sizeof(WarpSmem) * kWarps;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, selinv_persistent<F64>, kWarps * 32, smem) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
+    cudaError_t e = scan ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, selinv_persistent<F64, true>,
+                                                                         kWarps * 32, smem_bytes(true))
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, selinv_persistent<F64, false>,
+                                                                         kWarps * 32, smem_bytes(false));
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     return per_sm * num_sms;
 }
+
+int selinv_scan_table_smem() { return kTabW; }
 
 cudaError_t selinv_launch(const SelinvArgs& a, int prec, void* work, double* G_out, cudaStream_t st, int grid) {
     if (prec == 0) return launch_form<F64>(a, G_out, G_out, st, grid);

@@ -73,7 +73,7 @@ bool subset_except(const int32_t* a, int64_t na, const int32_t* b, int64_t nb, i
 }  // namespace
 
 std::string build_plan(int64_t n, const int64_t* Lrp, const int32_t* Lc, const int8_t* ps, int cap,
-                       int64_t big_pairs, int group, int64_t thin_level, HostPlan& P) {
+                       int64_t big_pairs, int group, int64_t thin_level, HostPlan& P, int64_t pair_bytes) {
     if (n < 0) return "negative n";
     if (n > INT32_MAX - 1) return "n does not fit int32 column indices";
     if (cap <= 0) cap = 16;
@@ -329,33 +329,82 @@ std::string build_plan(int64_t n, const int64_t* Lrp, const int32_t* Lc, const i
         if (fill) hrow[c] = (int32_t)cnt;
         return cnt;
     };
-    parallel_for_dynamic(ns, 256, [&](int64_t a, int64_t b) {
-        for (int64_t s = a; s < b; ++s) hits[s] = pairs(s, false, nullptr, nullptr, nullptr);
-    });
-    int64_t hoff = 0, roff = 0;
-    for (int64_t s = 0; s < ns; ++s) {
-        P.sn[s].hit_off = hoff;
-        P.sn[s].hit_cnt = hits[s];
-        P.sn[s].hrow_off = roff;
-        hoff += hits[s];
-        roff += P.sn[s].c + 1;
-        if (hits[s] > INT32_MAX) return "a supernode has >= 2^31 pairs: unsupported";
-    }
-    P.hit_pairs = hoff;
-    for (int64_t s = 0; s < ns; ++s) {
-        const SnInfo& I = P.sn[s];
-        P.selinv_flops += 2 * I.w * hits[s] + 2 * (int64_t)I.c * I.w * I.w;
-        P.selinv_bytes += 8 * ((hits[s] + I.c) / 2) + 16 * (int64_t)I.c * I.w;
-    }
-    P.hit_ik.resize(hoff);
-    P.hit_pos.resize(hoff);
-    P.hrow.resize(roff);
-    parallel_for_dynamic(ns, 256, [&](int64_t a, int64_t b) {
+    // The pair lists take 8 B per pair.  Their number is bounded by the row lengths of
+    // S over C (each lower pair is an entry of a row of C, counted once per side), and
+    // measured at about a third of them on 3D factors: when even a quarter of that
+    // bound would pass the budget, the lists are not built (counting them costs as
+    // much as building them), else they are counted and the budget decides.
+    const int64_t budget = pair_bytes > 0 ? pair_bytes : (int64_t(8) << 30);
+    std::vector<int64_t> rowsum(ns, 0);
+    parallel_for(ns, [&](int64_t a, int64_t b) {
         for (int64_t s = a; s < b; ++s) {
-            SnInfo& I = P.sn[s];
-            pairs(s, true, P.hit_ik.data() + I.hit_off, P.hit_pos.data() + I.hit_off, P.hrow.data() + I.hrow_off);
+            int64_t t = 0;
+            for (int32_t r : Cs[s]) t += P.Srp[r + 1] - P.Srp[r];
+            rowsum[s] = t;
         }
     });
+    int64_t rows_total = 0;
+    for (int64_t s = 0; s < ns; ++s) rows_total += rowsum[s];
+    P.scan_rows_total = rows_total;
+    bool scan = pair_bytes < 0 || 8 * (rows_total / 4) > budget;
+    if (!scan) {
+        parallel_for_dynamic(ns, 256, [&](int64_t a, int64_t b) {
+            for (int64_t s = a; s < b; ++s) hits[s] = pairs(s, false, nullptr, nullptr, nullptr);
+        });
+        int64_t tot = 0;
+        for (int64_t s = 0; s < ns; ++s) tot += hits[s];
+        scan = 8 * tot > budget;
+    }
+    P.scan = scan ? 1 : 0;
+    int64_t hoff = 0, roff = 0;
+    for (int64_t s = 0; s < ns; ++s) {
+        SnInfo& I = P.sn[s];
+        I.hit_off = scan ? 0 : hoff;
+        I.hit_cnt = scan ? rowsum[s] / 3 + I.c : hits[s];
+        I.hrow_off = roff;
+        if (!scan) hoff += hits[s];
+        roff += I.c + 1;
+        if (I.hit_cnt > INT32_MAX || rowsum[s] > INT32_MAX)
+            return "a supernode has >= 2^31 pairs: unsupported";
+    }
+    P.hit_pairs = scan ? 0 : hoff;
+    P.hrow.resize(roff);
+    if (scan) {
+        // work estimate: a third of the row lengths are pairs (see above); each
+        // lookup reads a 4 B column index, each pair an 8 B value
+        for (int64_t s = 0; s < ns; ++s) {
+            const SnInfo& I = P.sn[s];
+            P.selinv_flops += 2 * I.w * (rowsum[s] / 3 + I.c) + 2 * (int64_t)I.c * I.w * I.w;
+            P.selinv_bytes += 4 * (rowsum[s] / 2) + 8 * ((rowsum[s] / 3 + I.c) / 2) + 16 * (int64_t)I.c * I.w;
+        }
+        parallel_for(ns, [&](int64_t a, int64_t b) {
+            for (int64_t s = a; s < b; ++s) {
+                int32_t* hr = P.hrow.data() + P.sn[s].hrow_off;
+                int64_t t = 0;
+                const auto& C = Cs[s];
+                for (size_t i = 0; i < C.size(); ++i) {
+                    hr[i] = (int32_t)t;
+                    t += P.Srp[C[i] + 1] - P.Srp[C[i]];
+                }
+                hr[C.size()] = (int32_t)t;
+            }
+        });
+    } else {
+        for (int64_t s = 0; s < ns; ++s) {
+            const SnInfo& I = P.sn[s];
+            P.selinv_flops += 2 * I.w * hits[s] + 2 * (int64_t)I.c * I.w * I.w;
+            P.selinv_bytes += 8 * ((hits[s] + I.c) / 2) + 16 * (int64_t)I.c * I.w;
+        }
+        P.hit_ik.resize(hoff);
+        P.hit_pos.resize(hoff);
+        parallel_for_dynamic(ns, 256, [&](int64_t a, int64_t b) {
+            for (int64_t s = a; s < b; ++s) {
+                SnInfo& I = P.sn[s];
+                pairs(s, true, P.hit_ik.data() + I.hit_off, P.hit_pos.data() + I.hit_off,
+                      P.hrow.data() + I.hrow_off);
+            }
+        });
+    }
     parallel_for(ns, [&](int64_t a, int64_t b) {
         for (int64_t s = a; s < b; ++s) {
             SnInfo& I = P.sn[s];

@@ -108,6 +108,68 @@ def test_selinv_fp32(case):
     assert normwise(out.cpu().numpy(), G) <= 1e-5, name
 
 
+def _sum_c(f, sn_start):
+    """sum over supernodes J of |C_J| (rows of L below J in J's columns)."""
+    L = sp.csr_matrix((np.ones(len(f.L_col)), f.L_col, f.L_rowptr), shape=(f.n, f.n)).tocsc()
+    tot = 0
+    for J in range(len(sn_start) - 1):
+        s0, s1 = int(sn_start[J]), int(sn_start[J + 1])
+        rows = np.unique(L.indices[L.indptr[s0]:L.indptr[s1]])
+        tot += int((rows >= s1).sum())
+    return tot
+
+
+@pytest.mark.parametrize("cap,big", [(1, 0), (16, 0), (4, 64)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_selinv_scan_form(case, cap, big, prec):
+    """The scan form (no pair lists: every supernode scans its rows of S_lo against
+    a hash table of C) gives the oracle's values, with whole-CTA, per-warp and split
+    supernodes; the pairs it finds are exactly the pair lists' (each lower pair
+    counted once: lists = 2 x pairs + the diagonals of C)."""
+    name, f, m, S, G, N = case
+    h = _handle(f, supernode_cap=cap, big_pairs=big, selinv_pair_bytes=-1)
+    st = h.stats()
+    assert st["selinv_scan"] == 1 and st["hit_pairs"] == 0
+    Lv, Dv = _dev(f.L_val), _dev(f.D_packed)
+    h.timeline(True)
+    for _ in range(2):
+        out = h.selinv(Lv, Dv, prec).cpu().numpy()
+        h.sync_status()
+        if prec == "fp64":
+            assert sel_rel_err(out, G, *S) <= TOL64, name
+        else:
+            assert normwise(out, G) <= 1e-5, name
+    look, pairs = h.selinv_scan_counts()
+    h.timeline(False)
+    ref = _handle(f, supernode_cap=cap, big_pairs=big)
+    assert ref.stats()["selinv_scan"] == 0
+    sn_start, _ = ref.supernodes()
+    assert 2 * pairs + _sum_c(f, sn_start) == ref.stats()["hit_pairs"], name
+    assert pairs <= look <= st["scan_rows_total"]
+
+
+def test_selinv_scan_form_large_C():
+    """Rows C of up to ~1,100 per supernode on a dense band: hash tables of C in
+    global memory (beyond the shared slots of a warp and of a CTA), global X and Lh."""
+    from workloads.configs import band
+    f = band(4096, 1100).factors
+    S = oracle.symbolic_S(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+    G = oracle.selinv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, S)
+    for cap in (1, 16):
+        h = _handle(f, supernode_cap=cap, selinv_pair_bytes=-1)
+        assert h.stats()["max_c"] > 1024
+        out = h.selinv(_dev(f.L_val), _dev(f.D_packed), "fp64").cpu().numpy()
+        h.sync_status()
+        assert sel_rel_err(out, G, *S) <= TOL64, cap
+
+
+def test_selinv_pair_budget_switches_to_scan_form():
+    """A pair budget below the lists' size takes the scan form; the default keeps them."""
+    f = lap2d_32().factors
+    assert _handle(f).stats()["selinv_scan"] == 0
+    assert _handle(f, selinv_pair_bytes=1024).stats()["selinv_scan"] == 1
+
+
 # NInv runs in map form (maps built by the first call of an m, the default) or in
 # hash form (no maps); both are checked against the oracle
 FORMS = {"map": 0, "hash": -1}

@@ -94,3 +94,16 @@ def test_tensor_core_forms_only_for_selinv():
         with pytest.raises(SinvError) as ei:
             h.ninv(Lv, Dv, 2, prec)
         assert ei.value.name == "SINV_ERR_UNSUPPORTED"
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_tensor_core_tier_over_the_scan_form(prec):
+    """The tier's levels, then the scan form of FP64 SelInv (no pair lists) for the rest."""
+    from paper_2609_11363_b300 import Handle
+    f = plant_2x2(diff3d(12, m=3).factors, 0.05, 13)
+    S, G_ref = _ref("diff3d12_2x2", f)
+    h = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start, supernode_cap=4, selinv_pair_bytes=-1)
+    assert h.stats()["selinv_scan"] == 1 and h.stats()["tc_levels"] >= 1
+    G = h.selinv(_dev(f.L_val), _dev(f.D_packed), prec).cpu().numpy()
+    h.sync_status()
+    assert normwise(G, G_ref) <= STATED_SHIFTED[prec]

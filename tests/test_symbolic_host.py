@@ -99,6 +99,28 @@ def test_supernode_and_level_invariants(lib, name, cap):
         assert level[s] == want
 
 
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_scan_form_plan(lib, name):
+    """The scan form of SelInv keeps the supernodes and levels, stores no pair list,
+    and its work measure is the sum over supernodes of the S_lo row lengths of C."""
+    f = CASES[name]()
+    a = _host_handle(f)
+    b = _host_handle(f, selinv_pair_bytes=-1)
+    sa, sb = a.stats(), b.stats()
+    assert sa["selinv_scan"] == 0 and sb["selinv_scan"] == 1 and sb["hit_pairs"] == 0
+    for x, y in zip(a.supernodes(), b.supernodes()):
+        assert np.array_equal(x, y)
+    rp, _ = b.pattern_host()
+    rowlen = np.diff(rp)
+    start, _ = b.supernodes()
+    st = _structs(f)
+    want = 0
+    for s_ in range(len(start) - 1):
+        C = set().union(*[st[c] for c in range(start[s_], start[s_ + 1])])
+        want += int(sum(rowlen[r] for r in C if r >= start[s_ + 1]))
+    assert sb["scan_rows_total"] == want == sa["scan_rows_total"]
+
+
 def _expect_pattern_error(n, rp, col, ps):
     from paper_2609_11363_b300 import Handle, SinvError
     with pytest.raises(SinvError) as ei:
