@@ -142,6 +142,7 @@ struct sinv_handle_s {
     double* down_v = nullptr;
     int64_t own_nnz = 0, own_nnzW = 0;
     std::vector<int64_t> own_nnzW_steps;
+    std::vector<int64_t> own_hint;  // output sizes of the last call's steps (first guesses of the next)
     // per-supernode timeline of SelInv (allocated while enabled)
     unsigned long long* dtl_first = nullptr;
     unsigned long long* dtl_last = nullptr;
@@ -1622,35 +1623,7 @@ sinv_status sinv_ninv_own(sinv_handle h, const double* L_val, const double* D_va
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
-    // the structural pattern of the series for m: capacities of the Horner steps
-    if (h->W.m != m) {
-        std::string err;
-        try {
-            err = build_ninv_plan(P, m, h->W);
-        } catch (const std::bad_alloc&) {
-            set_err(h, "host allocation failed building the Neumann pattern");
-            return SINV_ERR_OOM;
-        }
-        if (!err.empty()) {
-            h->W.m = -1;
-            set_err(h, err);
-            return SINV_ERR_UNSUPPORTED;
-        }
-        ninv_maps_free(h->X);
-        h->index_tried_m = -1;
-        if (h->dWcp) cudaFree(h->dWcp);
-        if (h->dWr) cudaFree(h->dWr);
-        if (h->dgrp) cudaFree(h->dgrp);
-        h->dWcp = nullptr; h->dWr = nullptr; h->dgrp = nullptr;
-        if ((e = upload(&h->dWcp, h->W.Wcp)) != cudaSuccess || (e = upload(&h->dWr, h->W.Wr)) != cudaSuccess ||
-            (e = upload(&h->dgrp, h->W.grp)) != cudaSuccess) {
-            h->W.m = -1;
-            return cuda_fail(h, e, "upload Neumann pattern");
-        }
-    }
     TraceScope trace_scope(h->tracer);
-    const int64_t cap = std::max<int64_t>(h->W.nnzW, n);
-    const int grid = own_grid_ctas(h->num_sms);
     auto fail = [&](cudaError_t err, const char* what) -> sinv_status {
         if (err == cudaErrorMemoryAllocation) {
             set_err(h, std::string("device allocation failed: ") + what);
@@ -1658,17 +1631,30 @@ sinv_status sinv_ninv_own(sinv_handle h, const double* L_val, const double* D_va
         }
         return cuda_fail(h, err, what);
     };
-    DevBuf cpA, rA, vA, cpB, rB, vB, rS, vS, cnt, dr, dp, part, ticket, gk, gv;
-    int64_t gslice = own_table_slots(2 * std::max<int64_t>(h->W.max_col, 1));
-    if ((e = dev_alloc(cpA, (n + 1) * 8)) != cudaSuccess || (e = dev_alloc(rA, cap * 4)) != cudaSuccess ||
-        (e = dev_alloc(vA, cap * 8)) != cudaSuccess || (e = dev_alloc(cpB, (n + 1) * 8)) != cudaSuccess ||
-        (e = dev_alloc(rB, cap * 4)) != cudaSuccess || (e = dev_alloc(vB, cap * 8)) != cudaSuccess ||
-        (e = dev_alloc(rS, cap * 4)) != cudaSuccess || (e = dev_alloc(vS, cap * 8)) != cudaSuccess ||
-        (e = dev_alloc(cnt, (n + 1) * 8)) != cudaSuccess || (e = dev_alloc(dr, n * 8)) != cudaSuccess ||
-        (e = dev_alloc(dp, n * 8)) != cudaSuccess || (e = dev_alloc(part, n * 4)) != cudaSuccess ||
-        (e = dev_alloc(ticket, 64)) != cudaSuccess || (e = dev_alloc(gk, (size_t)grid * gslice * 4)) != cudaSuccess ||
-        (e = dev_alloc(gv, (size_t)grid * gslice * 8)) != cudaSuccess)
+    // a buffer that only grows
+    auto ensure = [](DevBuf& b, int64_t& have, int64_t need, size_t esize) -> cudaError_t {
+        if (need <= have && b.p) return cudaSuccess;
+        if (b.p) cudaFree(b.p);
+        b.p = nullptr;
+        have = 0;
+        cudaError_t err = dev_alloc(b, (size_t)std::max<int64_t>(need, 1) * esize);
+        if (err == cudaSuccess) have = need;
+        return err;
+    };
+    auto read64 = [&](const void* dptr, int64_t* out) -> cudaError_t {
+        cudaError_t err = cudaMemcpyAsync(out, dptr, 8, cudaMemcpyDeviceToHost, st);
+        return err == cudaSuccess ? cudaStreamSynchronize(st) : err;
+    };
+    DevBuf dr, dp, part, ticket, scal, stA, ctA, stB, ctB, rA, vA, rB, vB, gk, gv;
+    int64_t capA = 0, capB = 0, have_gk = 0, have_gv = 0;
+    if ((e = dev_alloc(dr, n * 8)) != cudaSuccess || (e = dev_alloc(dp, n * 8)) != cudaSuccess ||
+        (e = dev_alloc(part, n * 4)) != cudaSuccess || (e = dev_alloc(ticket, 64)) != cudaSuccess ||
+        (e = dev_alloc(scal, 64)) != cudaSuccess || (e = dev_alloc(stA, n * 8)) != cudaSuccess ||
+        (e = dev_alloc(ctA, n * 8)) != cudaSuccess || (e = dev_alloc(stB, n * 8)) != cudaSuccess ||
+        (e = dev_alloc(ctB, n * 8)) != cudaSuccess || (e = ensure(rA, capA, n, 4)) != cudaSuccess ||
+        (e = dev_alloc(vA, n * 8)) != cudaSuccess)
         return fail(e, "NInv own-pattern work");
+    int64_t* d_max = scal.as<int64_t>();
     NinvArgs na{};
     na.n = n;
     na.dpos = h->ddpos;
@@ -1680,91 +1666,130 @@ sinv_status sinv_ninv_own(sinv_handle h, const double* L_val, const double* D_va
     OwnArgs a;
     a.n = n;
     a.num_sms = h->num_sms;
+    a.grid = own_grid_ctas(h->num_sms);
     a.Lcp = h->dLcp;
     a.Lri = h->dLri;
     a.Lcsr = h->dLcsr;
     a.Lval = L_val;
-    a.Wcp = h->dWcp;
     a.delta = delta;
     a.dr = dr.as<double>();
     a.dp = dp.as<double>();
     a.part = part.as<int32_t>();
-    a.gkeys = gk.as<int32_t>();
-    a.gvals = gv.as<double>();
-    a.gslice = gslice;
+    a.gkeys = nullptr;
+    a.gvals = nullptr;
+    a.gslice = 0;
     a.ticket = ticket.as<int32_t>();
-    // W_0 = I, then m Horner steps, each compacted
+    a.cursor = reinterpret_cast<unsigned long long*>(scal.as<int64_t>() + 1);
+    // global hash tables of `slots` slots per CTA when shared memory is too small;
+    // fewer CTAs when all of them would pass the table budget
+    const int64_t table_budget = int64_t(8) << 30;
+    auto tables = [&](int64_t slots, bool fits) -> cudaError_t {
+        a.grid = own_grid_ctas(h->num_sms);
+        a.gslice = 0;
+        if (fits) return cudaSuccess;
+        a.gslice = slots;
+        const int64_t per = slots * (int64_t)(sizeof(int32_t) + sizeof(double));
+        a.grid = (int)std::max<int64_t>(1, std::min<int64_t>(a.grid, table_budget / per));
+        cudaError_t err;
+        if ((err = ensure(gk, have_gk, (int64_t)a.grid * slots, 4)) != cudaSuccess ||
+            (err = ensure(gv, have_gv, (int64_t)a.grid * slots, 8)) != cudaSuccess)
+            return err;
+        a.gkeys = gk.as<int32_t>();
+        a.gvals = gv.as<double>();
+        return cudaSuccess;
+    };
+    // W_0 = I, then m Horner steps; an output that overflows is grown to the exact
+    // count the cursor reports and the step runs again
     h->own_nnzW_steps.assign(1, n);
-    if ((e = own_identity_launch(n, cpA.as<int64_t>(), rA.as<int32_t>(), vA.as<double>(), h->num_sms, st)) !=
-        cudaSuccess)
+    if ((e = own_identity_launch(n, stA.as<int64_t>(), ctA.as<int64_t>(), rA.as<int32_t>(), vA.as<double>(),
+                                 h->num_sms, st)) != cudaSuccess)
         return fail(e, "NInv own-pattern identity");
+    int64_t nnz_prev = n, vcapB = 0;
     for (int t = 1; t <= m; ++t) {
-        if ((e = own_horner_launch(a, t, cpA.as<int64_t>(), rA.as<int32_t>(), vA.as<double>(), rS.as<int32_t>(),
-                                   vS.as<double>(), cnt.as<int64_t>(), st)) != cudaSuccess ||
-            (e = own_scan_launch(n, cnt.as<int64_t>(), cpB.as<int64_t>(), st)) != cudaSuccess ||
-            (e = own_compact_launch(n, h->dWcp, cpB.as<int64_t>(), rS.as<int32_t>(), vS.as<double>(),
-                                    rB.as<int32_t>(), vB.as<double>(), h->num_sms, st)) != cudaSuccess)
-            return fail(e, "NInv own-pattern Horner step");
-        std::swap(cpA.p, cpB.p);
+        int64_t maxb = 0;
+        if ((e = own_bound_launch(n, h->dLcp, h->dLri, ctA.as<int64_t>(), d_max, h->num_sms, st)) != cudaSuccess ||
+            (e = read64(d_max, &maxb)) != cudaSuccess ||
+            (e = tables(own_table_slots(maxb), own_table_slots(maxb) <= own_smem_slots())) != cudaSuccess)
+            return fail(e, "NInv own-pattern Horner tables");
+        int64_t want = std::max<int64_t>(capB, 2 * nnz_prev + n);
+        if ((int64_t)h->own_hint.size() > t) want = std::max<int64_t>(want, h->own_hint[t] + h->own_hint[t] / 32);
+        for (int attempt = 0;; ++attempt) {
+            if ((e = ensure(rB, capB, want, 4)) != cudaSuccess || (e = ensure(vB, vcapB, want, 8)) != cudaSuccess)
+                return fail(e, "NInv own-pattern Horner output");
+            int64_t tot = 0;
+            if ((e = own_horner_launch(a, stA.as<int64_t>(), ctA.as<int64_t>(), rA.as<int32_t>(), vA.as<double>(),
+                                       rB.as<int32_t>(), vB.as<double>(), stB.as<int64_t>(), ctB.as<int64_t>(),
+                                       std::min(capB, vcapB), st)) != cudaSuccess ||
+                (e = read64(a.cursor, &tot)) != cudaSuccess)
+                return fail(e, "NInv own-pattern Horner step");
+            if (tot <= std::min(capB, vcapB)) {
+                nnz_prev = tot;
+                break;
+            }
+            if (attempt > 0) {
+                set_err(h, "NInv own-pattern Horner step: output count changed between runs");
+                return SINV_ERR_CUDA;
+            }
+            // room for entries at the drop threshold that another summation order keeps
+            want = tot + tot / 32 + 1024;
+        }
+        std::swap(stA.p, stB.p);
+        std::swap(ctA.p, ctB.p);
         std::swap(rA.p, rB.p);
         std::swap(vA.p, vB.p);
-        int64_t nz = 0;
-        if ((e = cudaMemcpyAsync(&nz, cpA.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-            (e = cudaStreamSynchronize(st)) != cudaSuccess)
-            return fail(e, "NInv own-pattern sizes");
-        h->own_nnzW_steps.push_back(nz);
+        std::swap(capA, capB);
+        vcapB = capB;  // the buffers swapped: r and v have the same capacity in each pair from here on
+        h->own_nnzW_steps.push_back(nnz_prev);
     }
-    const int64_t nnzW = h->own_nnzW_steps.back();
+    const int64_t nnzW = nnz_prev;
     // W by rows, the diagonal of N and the bound of every column of N
-    DevBuf rowcnt, rp, fill, rc, rv, diag, bound, off;
+    DevBuf rowcnt, rp, fill, rc, rv, diag, bound;
     if ((e = dev_alloc(rowcnt, (n + 1) * 8)) != cudaSuccess || (e = dev_alloc(rp, (n + 1) * 8)) != cudaSuccess ||
         (e = dev_alloc(fill, (n + 1) * 8)) != cudaSuccess || (e = dev_alloc(rc, nnzW * 4)) != cudaSuccess ||
         (e = dev_alloc(rv, nnzW * 8)) != cudaSuccess || (e = dev_alloc(diag, n * 8)) != cudaSuccess ||
-        (e = dev_alloc(bound, (n + 1) * 8)) != cudaSuccess || (e = dev_alloc(off, (n + 1) * 8)) != cudaSuccess)
+        (e = dev_alloc(bound, (n + 1) * 8)) != cudaSuccess)
         return fail(e, "NInv own-pattern product work");
-    if ((e = own_transpose_launch(n, nnzW, cpA.as<int64_t>(), rA.as<int32_t>(), vA.as<double>(), rowcnt.as<int64_t>(),
-                                  rp.as<int64_t>(), fill.as<int64_t>(), rc.as<int32_t>(), rv.as<double>(), h->num_sms,
-                                  st)) != cudaSuccess ||
-        (e = own_diag_launch(a, cpA.as<int64_t>(), rA.as<int32_t>(), vA.as<double>(), rp.as<int64_t>(),
-                             diag.as<double>(), bound.as<int64_t>(), st)) != cudaSuccess ||
-        (e = own_scan_launch(n, bound.as<int64_t>(), off.as<int64_t>(), st)) != cudaSuccess)
+    int64_t maxct = 0, maxbound = 0;
+    if ((e = own_transpose_launch(n, nnzW, stA.as<int64_t>(), ctA.as<int64_t>(), rA.as<int32_t>(), vA.as<double>(),
+                                  rowcnt.as<int64_t>(), rp.as<int64_t>(), fill.as<int64_t>(), rc.as<int32_t>(),
+                                  rv.as<double>(), h->num_sms, st)) != cudaSuccess ||
+        (e = own_max_launch(n, ctA.as<int64_t>(), d_max, h->num_sms, st)) != cudaSuccess ||
+        (e = read64(d_max, &maxct)) != cudaSuccess ||
+        (e = tables(own_table_slots(2 * maxct), own_table_slots(2 * maxct) <= own_smem_slots())) != cudaSuccess ||
+        (e = own_diag_launch(a, stA.as<int64_t>(), ctA.as<int64_t>(), rA.as<int32_t>(), vA.as<double>(),
+                             rp.as<int64_t>(), diag.as<double>(), bound.as<int64_t>(), d_max, st)) != cudaSuccess ||
+        (e = read64(d_max, &maxbound)) != cudaSuccess)
         return fail(e, "NInv own-pattern diagonal");
-    int64_t total = 0;
-    std::vector<int64_t> hb(n);
-    if ((e = cudaMemcpyAsync(&total, off.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(hb.data(), bound.as<int64_t>(), n * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess)
-        return fail(e, "NInv own-pattern bounds");
-    const int64_t maxb = hb.empty() ? 1 : *std::max_element(hb.begin(), hb.end());
     // the product's tables: Y[:, j] in the first half of a CTA's slice, N's column in the second
-    const int64_t half = std::max<int64_t>(own_table_slots(2 * std::max<int64_t>(h->W.max_col, 1)),
-                                           own_table_slots(std::max<int64_t>(maxb, 1)));
-    if (2 * half > gslice) {
-        gslice = 2 * half;
-        cudaFree(gk.p);
-        cudaFree(gv.p);
-        gk.p = gv.p = nullptr;
-        if ((e = dev_alloc(gk, (size_t)grid * gslice * 4)) != cudaSuccess ||
-            (e = dev_alloc(gv, (size_t)grid * gslice * 8)) != cudaSuccess)
+    {
+        const int64_t half = std::max<int64_t>(own_table_slots(2 * maxct), own_table_slots(std::max<int64_t>(maxbound, 1)));
+        if ((e = tables(2 * half, half <= own_smem_slots() / 2)) != cudaSuccess)
             return fail(e, "NInv own-pattern product tables");
-        a.gkeys = gk.as<int32_t>();
-        a.gvals = gv.as<double>();
-        a.gslice = gslice;
     }
-    DevBuf nrS, nvS;
-    if ((e = dev_alloc(nrS, total * 4)) != cudaSuccess || (e = dev_alloc(nvS, total * 8)) != cudaSuccess)
-        return fail(e, "NInv own-pattern product slots");
-    if ((e = own_product_launch(a, cpA.as<int64_t>(), rA.as<int32_t>(), vA.as<double>(), rp.as<int64_t>(),
-                                rc.as<int32_t>(), rv.as<double>(), diag.as<double>(), off.as<int64_t>(),
-                                bound.as<int64_t>(), nrS.as<int32_t>(), nvS.as<double>(), cnt.as<int64_t>(), st)) !=
-            cudaSuccess ||
-        (e = own_scan_launch(n, cnt.as<int64_t>(), cpB.as<int64_t>(), st)) != cudaSuccess)
-        return fail(e, "NInv own-pattern product");
-    int64_t nnzN = 0;
-    if ((e = cudaMemcpyAsync(&nnzN, cpB.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess)
-        return fail(e, "NInv own-pattern size");
-    // the result, owned by the handle
+    DevBuf nr, nv, stN, ctN, cpN;
+    int64_t capN = 0, vcapN = 0;
+    if ((e = dev_alloc(stN, n * 8)) != cudaSuccess || (e = dev_alloc(ctN, n * 8)) != cudaSuccess ||
+        (e = dev_alloc(cpN, (n + 1) * 8)) != cudaSuccess)
+        return fail(e, "NInv own-pattern product work");
+    int64_t nnzN = 0, want = std::max<int64_t>(2 * nnzW, 2 * n);
+    if ((int64_t)h->own_hint.size() > m + 1) want = std::max<int64_t>(want, h->own_hint[m + 1] + h->own_hint[m + 1] / 32);
+    for (int attempt = 0;; ++attempt) {
+        if ((e = ensure(nr, capN, want, 4)) != cudaSuccess || (e = ensure(nv, vcapN, want, 8)) != cudaSuccess)
+            return fail(e, "NInv own-pattern product output");
+        if ((e = own_product_launch(a, stA.as<int64_t>(), ctA.as<int64_t>(), rA.as<int32_t>(), vA.as<double>(),
+                                    rp.as<int64_t>(), rc.as<int32_t>(), rv.as<double>(), diag.as<double>(),
+                                    bound.as<int64_t>(), nr.as<int32_t>(), nv.as<double>(), stN.as<int64_t>(),
+                                    ctN.as<int64_t>(), std::min(capN, vcapN), st)) != cudaSuccess ||
+            (e = read64(a.cursor, &nnzN)) != cudaSuccess)
+            return fail(e, "NInv own-pattern product");
+        if (nnzN <= std::min(capN, vcapN)) break;
+        if (attempt > 0) {
+            set_err(h, "NInv own-pattern product: output count changed between runs");
+            return SINV_ERR_CUDA;
+        }
+        want = nnzN + nnzN / 32 + 1024;
+    }
+    // the result, owned by the handle: CSC of the lower triangle
     if (h->down_cp) cudaFree(h->down_cp);
     if (h->down_r) cudaFree(h->down_r);
     if (h->down_v) cudaFree(h->down_v);
@@ -1775,13 +1800,15 @@ sinv_status sinv_ninv_own(sinv_handle h, const double* L_val, const double* D_va
         (e = cudaMalloc((void**)&h->down_r, std::max<int64_t>(nnzN, 1) * 4)) != cudaSuccess ||
         (e = cudaMalloc((void**)&h->down_v, std::max<int64_t>(nnzN, 1) * 8)) != cudaSuccess)
         return fail(e, "NInv own-pattern result");
-    if ((e = cudaMemcpyAsync(h->down_cp, cpB.p, (n + 1) * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
-        (e = own_compact_launch(n, off.as<int64_t>(), h->down_cp, nrS.as<int32_t>(), nvS.as<double>(), h->down_r,
+    if ((e = own_scan_launch(n, ctN.as<int64_t>(), h->down_cp, st)) != cudaSuccess ||
+        (e = own_compact_launch(n, stN.as<int64_t>(), h->down_cp, nr.as<int32_t>(), nv.as<double>(), h->down_r,
                                 h->down_v, h->num_sms, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return fail(e, "NInv own-pattern compaction");
     h->own_nnz = nnzN;
     h->own_nnzW = nnzW;
+    h->own_hint = h->own_nnzW_steps;
+    h->own_hint.push_back(nnzN);
     return SINV_OK;
 }
 

@@ -161,36 +161,44 @@ cudaError_t ninv_map_launch(const NinvArgs& a, const NinvMaps& x, int prec, void
 struct OwnArgs {
     int64_t n;
     int num_sms;
+    int grid;             // CTAs of the column kernels
     const int64_t* Lcp;   // E by columns: rows and CSR positions of the L values
     const int32_t* Lri;
     const int32_t* Lcsr;
     const double* Lval;
-    const int64_t* Wcp;   // column starts of the structural pattern P_W (slot capacities)
     double delta;
     const double* dr;     // D^{-1} by rows: diagonal, partner coefficient, partner
     const double* dp;
     const int32_t* part;
     int32_t* gkeys;       // per-CTA hash tables in global memory for long columns
     double* gvals;
-    int64_t gslice;
+    int64_t gslice;       // slots per CTA
     int32_t* ticket;
+    unsigned long long* cursor;  // append position of the current kernel's output
 };
-cudaError_t own_identity_launch(int64_t n, int64_t* cp, int32_t* r, double* v, int num_sms, cudaStream_t st);
-cudaError_t own_horner_launch(const OwnArgs& a, int t, const int64_t* cpIn, const int32_t* rIn, const double* vIn,
-                              int32_t* rOut, double* vOut, int64_t* cnt, cudaStream_t st);
-cudaError_t own_scan_launch(int64_t n, const int64_t* cnt, int64_t* out, cudaStream_t st);
+// W columns as segments: column j = entries [st[j], st[j] + ct[j]) of (r, v)
+cudaError_t own_identity_launch(int64_t n, int64_t* st, int64_t* ct, int32_t* r, double* v, int num_sms,
+                                cudaStream_t s);
+cudaError_t own_bound_launch(int64_t n, const int64_t* Lcp, const int32_t* Lri, const int64_t* ctIn, int64_t* maxb,
+                             int num_sms, cudaStream_t s);
+cudaError_t own_max_launch(int64_t n, const int64_t* x, int64_t* out, int num_sms, cudaStream_t s);
+cudaError_t own_horner_launch(const OwnArgs& a, const int64_t* stIn, const int64_t* ctIn, const int32_t* rIn,
+                              const double* vIn, int32_t* rOut, double* vOut, int64_t* stOut, int64_t* ctOut,
+                              int64_t cap, cudaStream_t s);
+cudaError_t own_scan_launch(int64_t n, const int64_t* cnt, int64_t* out, cudaStream_t s);
 cudaError_t own_compact_launch(int64_t n, const int64_t* off, const int64_t* cp, const int32_t* rs, const double* vs,
-                               int32_t* rd, double* vd, int num_sms, cudaStream_t st);
-cudaError_t own_transpose_launch(int64_t n, int64_t nnz, const int64_t* cp, const int32_t* r, const double* v,
-                                 int64_t* rowcnt, int64_t* rp, int64_t* fill, int32_t* rc, double* rv, int num_sms,
-                                 cudaStream_t st);
-cudaError_t own_diag_launch(const OwnArgs& a, const int64_t* cp, const int32_t* r, const double* v, const int64_t* rp,
-                            double* diag, int64_t* bound, cudaStream_t st);
-cudaError_t own_product_launch(const OwnArgs& a, const int64_t* cp, const int32_t* r, const double* v,
-                               const int64_t* rp, const int32_t* rc, const double* rv, const double* diag,
-                               const int64_t* off, const int64_t* bound, int32_t* nr, double* nv, int64_t* cnt,
-                               cudaStream_t st);
+                               int32_t* rd, double* vd, int num_sms, cudaStream_t s);
+cudaError_t own_transpose_launch(int64_t n, int64_t nnz, const int64_t* st, const int64_t* ct, const int32_t* r,
+                                 const double* v, int64_t* rowcnt, int64_t* rp, int64_t* fill, int32_t* rc,
+                                 double* rv, int num_sms, cudaStream_t s);
+cudaError_t own_diag_launch(const OwnArgs& a, const int64_t* st, const int64_t* ct, const int32_t* r, const double* v,
+                            const int64_t* rp, double* diag, int64_t* bound, int64_t* maxb, cudaStream_t s);
+cudaError_t own_product_launch(const OwnArgs& a, const int64_t* st, const int64_t* ct, const int32_t* r,
+                               const double* v, const int64_t* rp, const int32_t* rc, const double* rv,
+                               const double* diag, const int64_t* bound, int32_t* nr, double* nv, int64_t* stN,
+                               int64_t* ctN, int64_t cap, cudaStream_t s);
 int own_table_slots(int64_t entries);
+int own_smem_slots();
 int own_grid_ctas(int num_sms);
 
 // D^{-1} per row (ninv.cu): diagonal, off-diagonal of its 2x2 block, partner row (-1: 1x1)

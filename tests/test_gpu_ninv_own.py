@@ -12,7 +12,7 @@ import scipy.sparse as sp
 import torch
 
 import oracle
-from workloads.configs import diff3d, lap2d_32, plant_2x2, random_factors
+from workloads.configs import band, diff3d, lap2d_32, plant_2x2, random_factors
 
 pytestmark = pytest.mark.gpu
 
@@ -24,6 +24,25 @@ def _dev(a):
 def _cases():
     return [("lap2d", lap2d_32().factors), ("diff3d_2x2", plant_2x2(diff3d(10, m=3).factors, 0.05, 13)),
             ("random_2x2", random_factors(400, 0.02, 0.1, 5))]
+
+
+def _compare(f, m, delta, N, steps):
+    R = oracle.ninv_own(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, m, delta)
+    W = oracle.ninv_W(f.n, f.L_rowptr, f.L_col, f.L_val, m, delta)
+    assert steps[0] == f.n and steps[m] == W.nnz
+    d = R.diagonal()
+    Rc, Nc = R.tocoo(), N.tocoo()
+    ref = {(int(i), int(j)): v for i, j, v in zip(Rc.row, Rc.col, Rc.data)}
+    got = {(int(i), int(j)): v for i, j, v in zip(Nc.row, Nc.col, Nc.data)}
+    assert all(i >= j for i, j in got)
+    for key in set(ref) ^ set(got):      # only entries at the threshold may differ
+        v = ref.get(key, got.get(key))
+        thr = delta * np.sqrt(abs(d[key[0]] * d[key[1]]))
+        assert abs(abs(v) - thr) <= 1e-9 * thr, (key, v, thr)
+    common = set(ref) & set(got)
+    assert len(common) >= 0.999 * len(ref)
+    worst = max(abs(got[k] - ref[k]) / (abs(ref[k]) + np.sqrt(abs(d[k[0]] * d[k[1]]))) for k in common)
+    assert worst <= 1e-10, worst
 
 
 def _gpu(h, f, m, delta):
@@ -42,22 +61,30 @@ def test_ninv_own_matches_oracle(name, f, delta):
     m = 3
     h = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start)
     N, steps = _gpu(h, f, m, delta)
-    R = oracle.ninv_own(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, m, delta)
-    W = oracle.ninv_W(f.n, f.L_rowptr, f.L_col, f.L_val, m, delta)
-    assert steps[0] == f.n and steps[m] == W.nnz
-    d = R.diagonal()
-    Rc, Nc = R.tocoo(), N.tocoo()
-    ref = {(int(i), int(j)): v for i, j, v in zip(Rc.row, Rc.col, Rc.data)}
-    got = {(int(i), int(j)): v for i, j, v in zip(Nc.row, Nc.col, Nc.data)}
-    assert all(i >= j for i, j in got)
-    for key in set(ref) ^ set(got):      # only entries at the threshold may differ
-        v = ref.get(key, got.get(key))
-        thr = delta * np.sqrt(abs(d[key[0]] * d[key[1]]))
-        assert abs(abs(v) - thr) <= 1e-9 * thr, (key, v, thr)
-    common = set(ref) & set(got)
-    assert len(common) >= 0.999 * len(ref)
-    worst = max(abs(got[k] - ref[k]) / (abs(ref[k]) + np.sqrt(abs(d[k[0]] * d[k[1]]))) for k in common)
-    assert worst <= 1e-10, worst
+    _compare(f, m, delta, N, steps)
+
+
+def test_ninv_own_exact_series_grows_its_buffers():
+    """delta = 0 on exact factors: W and the product fill in far beyond the first
+    guesses of their output sizes, so every step overflows once, is grown to the
+    counted size and runs again."""
+    from paper_2609_11363_b300 import Handle
+    f = lap2d_32(tau=0.0).factors
+    h = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+    N, steps = _gpu(h, f, 3, 0.0)
+    assert steps[1] > 3 * f.n
+    _compare(f, 3, 0.0, N, steps)
+
+
+def test_ninv_own_long_columns_use_global_tables():
+    """A dense band of half-width 256: Horner bounds and product columns beyond the
+    shared-memory tables (global slices per CTA)."""
+    from paper_2609_11363_b300 import Handle
+    f = band(2048, 256).factors
+    h = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+    for delta in (1e-3, 1e-1):
+        N, steps = _gpu(h, f, 2, delta)
+        _compare(f, 2, delta, N, steps)
 
 
 def test_fill_falls_with_delta():
