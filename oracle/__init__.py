@@ -12,7 +12,9 @@ LDL^T Factorization and Spectral Corrections"):
                          Eq. (6), and (L^inv)^T D^{-1} L^inv, Eq. (8), on S
 * ``ninv_own``        -- the same with the inverse tolerance delta on its own
                          pattern (the product's fill controlled by delta too)
-* ``mix``             -- Mix approximation (Section 2.3)
+* ``mix``             -- Mix approximation (Section 2.3), on S
+* ``mix_own``         -- the same on NInv's own pattern: the union of that
+                         pattern and S_eps
 * ``lowrank_correct`` -- A^inv + V_k Lambda_k V_k^T on S, Eq. (9); diagonal
                          update formula of Section 2.6
 * ``spai_refine``     -- SPAI refinement on a fixed pattern by Jacobi-PCG on
@@ -47,6 +49,7 @@ from .core import (  # noqa: F401
     ninv_own,
     ninv_entries_sampled,
     mix,
+    mix_own,
     lowrank_correct,
     lowrank_diag,
     lanczos_einv,

@@ -372,6 +372,30 @@ def mix(G_S, N_S, eps):
     return np.where(np.abs(G_S) > eps, G_S, N_S)
 
 
+def mix_own(n, Srp, Sc, G_S, N_lo, eps):
+    """Mix on NInv's own pattern (Section 2.3): S_eps = {(i, j) in S_lo : |G_ij| > eps};
+    (A_Mix)_ij = G_ij on S_eps and N_ij elsewhere on N's pattern, so the pattern
+    is the union of N's pattern and S_eps.  G_S: values on S_lo (CSR order of
+    Srp, Sc); N_lo: the lower triangle of NInv on its own pattern (any sparse
+    format).  Returns the lower triangle as a CSC matrix with sorted rows;
+    entries are kept as stored (an explicit zero of N stays an entry)."""
+    G_S = np.asarray(G_S, dtype=np.float64)
+    rows, cols = _S_entries(Srp, Sc)
+    sel = np.abs(G_S) > eps
+    Nc = sp.coo_matrix(N_lo)
+    out = {}
+    for i, j, v in zip(Nc.row.tolist(), Nc.col.tolist(), Nc.data.tolist()):
+        out[(i, j)] = v
+    for i, j, g in zip(rows[sel].tolist(), cols[sel].tolist(), G_S[sel].tolist()):
+        out[(i, j)] = g
+    if not out:
+        return sp.csc_matrix((n, n))
+    ij = np.array(list(out.keys()), dtype=np.int64)
+    M = sp.csc_matrix((np.array(list(out.values())), (ij[:, 0], ij[:, 1])), shape=(n, n))
+    M.sort_indices()
+    return M
+
+
 def lowrank_correct(Srp, Sc, X_S, V, lam):
     """(A^inv + V diag(lam) V^T)_ij for (i, j) in S_lo (Eq. (9))."""
     rows, cols = _S_entries(Srp, Sc)

@@ -258,6 +258,42 @@ def test_ninv_own_pattern_hand_example():
     assert np.isclose(N2[2, 1], -0.1) and np.isclose(N2[2, 0], 0.05)
 
 
+def test_mix_own_hand_example():
+    """S_lo = {(0,0), (1,0), (1,1), (2,1), (2,2)} with SelInv values 2, -0.004, 1.5,
+    0.3, 1; NInv on its own pattern {(0,0): 1.25, (1,0): -0.5, (1,1): 1.01,
+    (2,0): 0.05, (2,2): 1}; eps = 0.01.  By hand (Section 2.3): S_eps = {(0,0),
+    (1,1), (2,1), (2,2)} (|-0.004| is not above eps), so Mix = G there, N at (1,0)
+    and at (2,0) (outside S), and (2,1) joins the pattern from S_eps."""
+    Srp = np.array([0, 1, 3, 5], dtype=np.int64)
+    Sc = np.array([0, 0, 1, 1, 2], dtype=np.int32)
+    G = np.array([2.0, -0.004, 1.5, 0.3, 1.0])
+    N = sp.csc_matrix(([1.25, -0.5, 0.05, 1.01, 1.0], ([0, 1, 2, 1, 2], [0, 0, 0, 1, 2])), shape=(3, 3))
+    M = oracle.mix_own(3, Srp, Sc, G, N, 0.01)
+    assert M.nnz == 6
+    assert np.array_equal(M.toarray(), [[2.0, 0, 0], [-0.5, 1.5, 0], [0.05, 0.3, 1.0]])
+    # eps = +inf: NInv unchanged; eps < 0: SelInv on all of S, NInv off S
+    assert np.array_equal(oracle.mix_own(3, Srp, Sc, G, N, np.inf).toarray(), N.toarray())
+    Mneg = oracle.mix_own(3, Srp, Sc, G, N, -1.0)
+    assert Mneg.nnz == 6
+    assert np.array_equal(Mneg.toarray(), [[2.0, 0, 0], [-0.004, 1.5, 0], [0.05, 0.3, 1.0]])
+
+
+def test_mix_own_on_S_reduces_to_mix():
+    """With NInv given on exactly the pattern S, Mix on the own pattern is the Mix of
+    Section 2.3 on S, entry by entry, for every eps rule."""
+    f = plant_2x2(lap2d_32().factors, 0.3, 11)
+    Srp, Sc = oracle.symbolic_S(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+    rng = np.random.default_rng(3)
+    G = rng.standard_normal(len(Sc)) * np.exp(rng.standard_normal(len(Sc)) * 3)
+    Nv = rng.standard_normal(len(Sc))
+    rows = np.repeat(np.arange(f.n), np.diff(Srp))
+    N = sp.csc_matrix((Nv, (rows, Sc)), shape=(f.n, f.n))
+    for eps in (1e-3 * np.abs(G).max(), 0.0, -1.0, np.inf):
+        M = oracle.mix_own(f.n, Srp, Sc, G, N, eps)
+        assert M.nnz == len(Sc)
+        assert np.array_equal(np.asarray(M[rows, Sc]).ravel(), oracle.mix(G, Nv, eps))
+
+
 def test_ninv_own_limits():
     """delta = 0 with m >= depth and exact factors: the whole lower triangle of
     inv(A); delta huge: W = I and only the diagonal of D^{-1} is left."""
