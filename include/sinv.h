@@ -233,6 +233,46 @@ sinv_status sinv_ninv_own(sinv_handle h, const double *L_val, const double *D_va
 sinv_status sinv_ninv_own_size(sinv_handle h, int64_t *nnz_N_lo, int64_t *nnz_W_steps, int32_t max_steps);
 sinv_status sinv_ninv_own_copy(sinv_handle h, int64_t *N_colptr, int32_t *N_row, double *N_val, void *stream);
 
+/* Mix on NInv's own pattern (Section 2.3): with S_eps = {(i, j) in S_lo : |G_ij| >
+ * eps}, the result is G on S_eps and the last sinv_ninv_own result N elsewhere on
+ * N's pattern, so its pattern is the union of N's and S_eps (lower triangle, CSC,
+ * rows of a column in no particular order: N's rows first, then the rows of S_eps
+ * that N lacks).  The paper computes N for Mix with a loose inverse tolerance
+ * (delta = 1e-1), so the result has about NInv's fill and SelInv's large entries.
+ *   G_S [|S_lo|]: device, SelInv on S_lo (S_lo CSR order).  eps: any value but NaN
+ *   (+inf gives N, a negative value all of S).  Synchronous on `stream` (the result
+ *   is sized on the host); the result is handle-owned until the next call:
+ *   sinv_mix_own_size gives its number of entries, sinv_mix_own_copy copies it to
+ *   caller-owned device arrays (n+1 column pointers, then rows and values).
+ *   Errors: SINV_ERR_INVALID_ARG (no sinv_ninv_own result, null G_S, NaN eps),
+ *   SINV_ERR_OOM, SINV_ERR_CUDA. */
+sinv_status sinv_mix_own(sinv_handle h, const double *G_S, double eps, void *stream);
+sinv_status sinv_mix_own_size(sinv_handle h, int64_t *nnz);
+sinv_status sinv_mix_own_copy(sinv_handle h, int64_t *M_colptr, int32_t *M_row, double *M_val, void *stream);
+/* The rank-k correction of Eq. (9) added in place to the handle-owned result of
+ * sinv_mix_own: M_ij += sum_l lambda_l V_il V_jl on its pattern.  Arguments, forms
+ * and limits as for sinv_lowrank_correct (V [n x k] row-major and lambda [k] on
+ * the device, 0 <= k <= 256, SINV_FP64 or SINV_FP32).
+ *   Errors: SINV_ERR_INVALID_ARG (no sinv_mix_own result, bad arguments),
+ *   SINV_ERR_UNSUPPORTED (k > 256, tensor-core forms), SINV_ERR_OOM, SINV_ERR_CUDA. */
+sinv_status sinv_lowrank_correct_mix_own(sinv_handle h, int k, const double *V, const double *lambda,
+                                         sinv_precision prec, void *stream);
+
+/* Mix-SPAI on the Mix pattern (Section 2.4: the refinement keeps the pattern of
+ * the Mix built on NInv's loose-tolerance pattern).  sinv_spai_analyse_mix_own
+ * replaces the handle's SPAI plan by one on the pattern of the current
+ * sinv_mix_own result (read back to the host; A as for sinv_spai_analyse, HOST
+ * arrays), and sinv_spai_mix_own runs the refinement, writing Y_P [|P_lo|]
+ * (device) in the order of sinv_spai_pattern.  X_M: start values on the Mix
+ * pattern in the order of sinv_mix_own_copy (device), or NULL for the handle's
+ * current Mix values.  Other arguments and errors as for sinv_spai_analyse /
+ * sinv_spai; sinv_spai_mix_own also returns SINV_ERR_INVALID_ARG when the plan was
+ * not built from the current Mix result. */
+sinv_status sinv_spai_analyse_mix_own(sinv_handle h, int64_t nnzA, const int64_t *A_rowptr, const int32_t *A_col,
+                                      int warp_entries);
+sinv_status sinv_spai_mix_own(sinv_handle h, const double *A_val, const double *X_M, int iters, double *Y_P,
+                              void *stream);
+
 /* Mix (Section 2.3): M_ij = G_ij where |G_ij| > eps, else N_ij, on S.
  *   G_S, N_S, M_S [|S_lo|]: device (M_S may alias G_S or N_S). */
 sinv_status sinv_mix(sinv_handle h, const double *G_S, const double *N_S, double eps,

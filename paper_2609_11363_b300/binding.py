@@ -34,7 +34,8 @@ EXPORTS = [
     "sinv_mlp_features", "sinv_mlp_targets", "sinv_mlp_grad", "sinv_mlp_train_step", "sinv_mlp_predict",
     "sinv_mlp_sync_status", "sinv_timeline_enable", "sinv_timeline_read", "sinv_batch_run",
     "sinv_einv_set_solver", "sinv_ninv_own", "sinv_ninv_own_size", "sinv_ninv_own_copy",
-    "sinv_selinv_scan_counts",
+    "sinv_selinv_scan_counts", "sinv_mix_own", "sinv_mix_own_size", "sinv_mix_own_copy",
+    "sinv_lowrank_correct_mix_own", "sinv_spai_analyse_mix_own", "sinv_spai_mix_own",
 ]
 
 
@@ -122,6 +123,12 @@ def load_library():
     lib.sinv_ninv_own.argtypes = [H, P, P, ctypes.c_int, ctypes.c_double, P]
     lib.sinv_ninv_own_size.argtypes = [H, ctypes.POINTER(I64), P, ctypes.c_int32]
     lib.sinv_ninv_own_copy.argtypes = [H, P, P, P, P]
+    lib.sinv_mix_own.argtypes = [H, P, ctypes.c_double, P]
+    lib.sinv_mix_own_size.argtypes = [H, ctypes.POINTER(I64)]
+    lib.sinv_mix_own_copy.argtypes = [H, P, P, P, P]
+    lib.sinv_lowrank_correct_mix_own.argtypes = [H, ctypes.c_int, P, P, ctypes.c_int, P]
+    lib.sinv_spai_analyse_mix_own.argtypes = [H, I64, P, P, ctypes.c_int]
+    lib.sinv_spai_mix_own.argtypes = [H, P, P, ctypes.c_int, P, P]
     lib.sinv_batch_symbolic.argtypes = [ctypes.c_int32, P, P, P, P, ctypes.POINTER(_Opts), ctypes.POINTER(H)]
     lib.sinv_batch_layout.argtypes = [H, ctypes.POINTER(ctypes.c_int32), P, P, P, P]
     lib.sinv_lowrank_correct_noalloc.argtypes = [I64, P, P, ctypes.c_int, P, P, P, P]
@@ -482,6 +489,32 @@ class Handle:
                                         _check_tensor(out, "Y_P", nP), _stream_ptr(stream)))
         return out
 
+    def spai_analyse_mix_own(self, A, warp_entries=0):
+        """Analyse A (scipy sparse) for spai_mix_own(): the refinement pattern is the one
+        of the current mix_own result.  Returns the CSR A whose value order it takes."""
+        import scipy.sparse as sp
+        A = sp.csr_matrix(A)
+        A.sum_duplicates()
+        rp = np.ascontiguousarray(A.indptr, dtype=np.int64)
+        col = np.ascontiguousarray(A.indices, dtype=np.int32)
+        self._check(self._lib.sinv_spai_analyse_mix_own(self._h, int(A.nnz), _np_ptr(rp), _np_ptr(col),
+                                                        int(warp_entries)))
+        self._spai_nnzA = int(A.nnz)
+        self.nnz_P = self.stats()["spai_nnz_P"]
+        return sp.csr_matrix((A.data, col, rp), shape=A.shape)
+
+    def spai_mix_own(self, A_val, iters, X=None, out=None, stream=None):
+        """Mix-SPAI over the pattern of the current mix_own result, from its values (or
+        from X, given in the order of mix_own_result): result on P_lo."""
+        nP = getattr(self, "nnz_P", None)
+        if out is None:
+            out = torch.empty(nP or 0, dtype=torch.float64, device=self.device)
+        xp = None if X is None else _check_tensor(X, "X_M")
+        self._check(self._lib.sinv_spai_mix_own(self._h, _check_tensor(A_val, "A_val",
+                                                                       getattr(self, "_spai_nnzA", None)),
+                                                xp, int(iters), _check_tensor(out, "Y_P", nP), _stream_ptr(stream)))
+        return out
+
     def einv_analyse(self, A):
         """Analyse the pattern of the symmetric matrix A (scipy sparse) for einv_lanczos();
         returns the CSR A whose value order einv_lanczos() takes."""
@@ -534,6 +567,32 @@ class Handle:
                                                  _check_tensor(rows, "rows", None, torch.int32),
                                                  _check_tensor(vals, "vals"), _stream_ptr(stream)))
         return cp, rows[:nnz.value], vals[:nnz.value], steps
+
+    def mix_own(self, G, eps, stream=None):
+        """Mix on the pattern of the last ninv_own: (colptr, rows, values) of the lower
+        triangle in CSC (CUDA tensors)."""
+        self._check(self._lib.sinv_mix_own(self._h, _check_tensor(G, "G", self.nnz_S), float(eps),
+                                           _stream_ptr(stream)))
+        return self.mix_own_result(stream)
+
+    def mix_own_result(self, stream=None):
+        """The handle's current Mix on the own pattern (copies): (colptr, rows, values)."""
+        nnz = ctypes.c_int64()
+        self._check(self._lib.sinv_mix_own_size(self._h, ctypes.byref(nnz)))
+        cp = torch.empty(self.n + 1, dtype=torch.int64, device=self.device)
+        rows = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=self.device)
+        vals = torch.empty(max(nnz.value, 1), dtype=torch.float64, device=self.device)
+        self._check(self._lib.sinv_mix_own_copy(self._h, _check_tensor(cp, "colptr", None, torch.int64),
+                                                _check_tensor(rows, "rows", None, torch.int32),
+                                                _check_tensor(vals, "vals"), _stream_ptr(stream)))
+        return cp, rows[:nnz.value], vals[:nnz.value]
+
+    def lowrank_correct_mix_own(self, V, lam, prec="fp64", stream=None):
+        """Add V diag(lam) V^T on the pattern of the last mix_own result (in place)."""
+        k = int(lam.numel())
+        self._check(self._lib.sinv_lowrank_correct_mix_own(self._h, k, _check_tensor(V, "V", self.n * k),
+                                                           _check_tensor(lam, "lambda", k), PREC[prec],
+                                                           _stream_ptr(stream)))
 
     def ninv_stack(self, L_val, D_val, m, prec="fp64", out=None, stream=None):
         """NInv on S for the truncations after 0..m terms: tensor [(m+1), |S_lo|]."""

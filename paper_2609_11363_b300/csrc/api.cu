@@ -143,6 +143,13 @@ struct sinv_handle_s {
     int64_t own_nnz = 0, own_nnzW = 0;
     std::vector<int64_t> own_nnzW_steps;
     std::vector<int64_t> own_hint;  // output sizes of the last call's steps (first guesses of the next)
+    // Mix on the own pattern (handle-owned CSC of the lower triangle)
+    int64_t* dmix_cp = nullptr;
+    int32_t* dmix_r = nullptr;
+    double* dmix_v = nullptr;
+    int64_t mix_nnz = -1;
+    int64_t mix_gen = 0;       // bumped by every sinv_mix_own
+    int64_t spai_mix_gen = -1; // the mix_gen the SPAI plan was built from (-1: not from a Mix)
     // per-supernode timeline of SelInv (allocated while enabled)
     unsigned long long* dtl_first = nullptr;
     unsigned long long* dtl_last = nullptr;
@@ -253,7 +260,7 @@ void free_all(sinv_handle h) {
                     h->dsn, h->dorder, h->downer, h->dCrow, h->dLmap, h->dJJl, h->dJJs, h->dhit_ik, h->dhit_pos,
                     h->dhrow, h->ditems, h->dxsum_off, h->dxsum, h->darrive, h->ddone, h->depoch, h->dticket, h->dstatus, h->ddebug_flag, h->dscratch, h->dwork, h->dWcp,
                     h->dWr, h->dgrp, h->dtc_items, h->dtc_map, h->dtc_deps, h->dtc_ticket, h->dtc_mirror, h->dtc_arrive_t,
-                    h->dtc_z, h->dtl_first, h->dtl_last, h->dscan_counts, h->dgtab, h->down_cp, h->down_r, h->down_v, h->db_L_off, h->db_D_off, h->db_S_off, h->db_L, h->db_D,
+                    h->dtc_z, h->dtl_first, h->dtl_last, h->dscan_counts, h->dgtab, h->dmix_cp, h->dmix_r, h->dmix_v, h->down_cp, h->down_r, h->down_v, h->db_L_off, h->db_D_off, h->db_S_off, h->db_L, h->db_D,
                     h->db_G, h->db_N};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -876,6 +883,10 @@ sinv_status sinv_lowrank_correct(sinv_handle h, int k, const double* V, const do
     return SINV_OK;
 }
 
+static sinv_status spai_analyse_common(sinv_handle h, int64_t nnzA, const int64_t* A_rowptr, const int32_t* A_col,
+                                       int power, int warp_entries, const int64_t* Prp, const int32_t* Pc,
+                                       const int32_t* src);
+
 sinv_status sinv_spai_analyse(sinv_handle h, int64_t nnzA, const int64_t* A_rowptr, const int32_t* A_col, int power,
                               int warp_entries) {
     if (!h || nnzA < 0 || !A_rowptr || (nnzA > 0 && !A_col) || warp_entries < 0 || power < 0)
@@ -884,16 +895,24 @@ sinv_status sinv_spai_analyse(sinv_handle h, int64_t nnzA, const int64_t* A_rowp
         set_err(h, "power > 8 is not supported");
         return SINV_ERR_UNSUPPORTED;
     }
+    return spai_analyse_common(h, nnzA, A_rowptr, A_col, power, warp_entries, nullptr, nullptr, nullptr);
+}
+
+// the SPAI plan (from S widened by `power`, or the given pattern) and its upload
+static sinv_status spai_analyse_common(sinv_handle h, int64_t nnzA, const int64_t* A_rowptr, const int32_t* A_col,
+                                       int power, int warp_entries, const int64_t* Prp, const int32_t* Pc,
+                                       const int32_t* src) {
     cudaError_t e = cudaSuccess;
     if (h->device >= 0) {
         if ((e = cudaSetDevice(h->device)) != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
         if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(h, e, "synchronize");
     }
     spai_free(h);
+    h->spai_mix_gen = -1;
     std::string err;
     try {
         const int we = warp_entries == 0 ? kSpaiWarpE : std::min(warp_entries, kSpaiWarpE);
-        err = build_spai_plan(h->P, nnzA, A_rowptr, A_col, power, kSpaiWarpJ, we, kSpaiWarpH / 2, h->Q);
+        err = build_spai_plan(h->P, nnzA, A_rowptr, A_col, power, kSpaiWarpJ, we, kSpaiWarpH / 2, h->Q, Prp, Pc, src);
     } catch (const std::bad_alloc&) {
         h->Q = SpaiPlan();
         set_err(h, "host allocation failed in the SPAI analysis");
@@ -1839,6 +1858,199 @@ sinv_status sinv_ninv_own_copy(sinv_handle h, int64_t* N_colptr, int32_t* N_row,
     if (e == cudaSuccess && h->own_nnz > 0)
         e = cudaMemcpyAsync(N_val, h->down_v, h->own_nnz * sizeof(double), cudaMemcpyDeviceToDevice, st);
     return e == cudaSuccess ? SINV_OK : cuda_fail(h, e, "NInv own-pattern copy");
+}
+
+sinv_status sinv_mix_own(sinv_handle h, const double* G_S, double eps, void* stream) {
+    if (!h || !G_S || eps != eps) return SINV_ERR_INVALID_ARG;
+    if (!on_device(h)) return SINV_ERR_INVALID_ARG;
+    if (!h->down_cp) {
+        set_err(h, "sinv_ninv_own has not run");
+        return SINV_ERR_INVALID_ARG;
+    }
+    const HostPlan& P = h->P;
+    const int64_t n = P.n;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    TraceScope trace_scope(h->tracer);
+    auto fail = [&](cudaError_t err, const char* what) -> sinv_status {
+        if (err == cudaErrorMemoryAllocation) {
+            set_err(h, std::string("device allocation failed: ") + what);
+            return SINV_ERR_OOM;
+        }
+        return cuda_fail(h, err, what);
+    };
+    DevBuf ticket, scal, cnt, gk;
+    int64_t maxlen = 0;
+    if ((e = dev_alloc(ticket, 64)) != cudaSuccess || (e = dev_alloc(scal, 64)) != cudaSuccess ||
+        (e = dev_alloc(cnt, (n + 1) * 8)) != cudaSuccess ||
+        (e = own_max_col_launch(n, h->down_cp, scal.as<int64_t>(), h->num_sms, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&maxlen, scal.p, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return fail(e, "Mix own-pattern work");
+    MixOwnArgs a;
+    a.n = n;
+    a.grid = own_grid_ctas(h->num_sms);
+    a.Ncp = h->down_cp;
+    a.Nr = h->down_r;
+    a.Nv = h->down_v;
+    a.Srp = h->dSrp;
+    a.Sdiag = h->dSdiag;
+    a.Lcp = h->dLcp;
+    a.Lri = h->dLri;
+    a.Lcsr = h->dLcsr;
+    a.l2s = h->dl2s;
+    a.pstart = h->dpstart;
+    a.G = G_S;
+    a.eps = eps;
+    a.gkeys = nullptr;
+    a.gslice = 0;
+    a.ticket = ticket.as<int32_t>();
+    const int64_t slots = own_table_slots(maxlen);
+    if (slots > own_smem_slots()) {
+        // keys and positions of N's longest column per CTA, in global memory
+        a.gslice = slots;
+        a.grid = (int)std::max<int64_t>(1, std::min<int64_t>(a.grid, (int64_t(4) << 30) / (8 * slots)));
+        if ((e = dev_alloc(gk, (size_t)a.grid * 2 * slots * sizeof(int32_t))) != cudaSuccess)
+            return fail(e, "Mix own-pattern tables");
+        a.gkeys = gk.as<int32_t>();
+    }
+    int64_t total = 0;
+    if (h->dmix_cp) cudaFree(h->dmix_cp);
+    h->dmix_cp = nullptr;
+    h->mix_nnz = -1;
+    if ((e = cudaMalloc((void**)&h->dmix_cp, (n + 1) * 8)) != cudaSuccess ||
+        (e = mix_own_launch(a, false, cnt.as<int64_t>(), nullptr, nullptr, st)) != cudaSuccess ||
+        (e = own_scan_launch(n, cnt.as<int64_t>(), h->dmix_cp, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&total, h->dmix_cp + n, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return fail(e, "Mix own-pattern count");
+    if (h->dmix_r) cudaFree(h->dmix_r);
+    if (h->dmix_v) cudaFree(h->dmix_v);
+    h->dmix_r = nullptr;
+    h->dmix_v = nullptr;
+    if ((e = cudaMalloc((void**)&h->dmix_r, std::max<int64_t>(total, 1) * 4)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&h->dmix_v, std::max<int64_t>(total, 1) * 8)) != cudaSuccess ||
+        (e = mix_own_launch(a, true, h->dmix_cp, h->dmix_r, h->dmix_v, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return fail(e, "Mix own-pattern fill");
+    h->mix_nnz = total;
+    h->mix_gen += 1;
+    return SINV_OK;
+}
+
+sinv_status sinv_spai_analyse_mix_own(sinv_handle h, int64_t nnzA, const int64_t* A_rowptr, const int32_t* A_col,
+                                      int warp_entries) {
+    if (!h || nnzA < 0 || !A_rowptr || (nnzA > 0 && !A_col) || warp_entries < 0) return SINV_ERR_INVALID_ARG;
+    if (!on_device(h)) return SINV_ERR_INVALID_ARG;
+    if (h->mix_nnz < 0) {
+        set_err(h, "sinv_mix_own has not run");
+        return SINV_ERR_INVALID_ARG;
+    }
+    const int64_t n = h->P.n;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    // the Mix pattern by rows (lower triangle, sorted rows) and, per entry, its index
+    // in the Mix value array
+    std::vector<int64_t> cp(n + 1), Prp(n + 1, 0);
+    std::vector<int32_t> rows(std::max<int64_t>(h->mix_nnz, 1)), Pc, src;
+    try {
+        if ((e = cudaMemcpy(cp.data(), h->dmix_cp, (n + 1) * 8, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+            (h->mix_nnz > 0 &&
+             (e = cudaMemcpy(rows.data(), h->dmix_r, h->mix_nnz * 4, cudaMemcpyDeviceToHost)) != cudaSuccess))
+            return cuda_fail(h, e, "Mix pattern read");
+        for (int64_t q = 0; q < h->mix_nnz; ++q) Prp[rows[q] + 1]++;
+        for (int64_t i = 0; i < n; ++i) Prp[i + 1] += Prp[i];
+        Pc.resize(h->mix_nnz);
+        src.resize(h->mix_nnz);
+        std::vector<int64_t> fill(Prp.begin(), Prp.end() - 1);
+        for (int64_t j = 0; j < n; ++j)  // columns in increasing order: every row comes out sorted
+            for (int64_t q = cp[j]; q < cp[j + 1]; ++q) {
+                const int64_t d = fill[rows[q]]++;
+                Pc[d] = (int32_t)j;
+                src[d] = (int32_t)q;
+            }
+    } catch (const std::bad_alloc&) {
+        set_err(h, "host allocation failed in the SPAI analysis");
+        return SINV_ERR_OOM;
+    }
+    if (h->mix_nnz >= ((int64_t)1 << 31)) {
+        set_err(h, "the Mix pattern has >= 2^31 entries: not supported");
+        return SINV_ERR_UNSUPPORTED;
+    }
+    sinv_status s = spai_analyse_common(h, nnzA, A_rowptr, A_col, 0, warp_entries, Prp.data(), Pc.data(), src.data());
+    if (s == SINV_OK) h->spai_mix_gen = h->mix_gen;
+    return s;
+}
+
+sinv_status sinv_spai_mix_own(sinv_handle h, const double* A_val, const double* X_M, int iters, double* Y_P,
+                              void* stream) {
+    if (!h) return SINV_ERR_INVALID_ARG;
+    if (h->spai_mix_gen < 0 || h->spai_mix_gen != h->mix_gen) {
+        set_err(h, "sinv_spai_mix_own needs sinv_spai_analyse_mix_own on the current Mix result");
+        return SINV_ERR_INVALID_ARG;
+    }
+    return sinv_spai(h, A_val, X_M ? X_M : h->dmix_v, iters, Y_P, stream);
+}
+
+sinv_status sinv_lowrank_correct_mix_own(sinv_handle h, int k, const double* V, const double* lambda,
+                                         sinv_precision prec, void* stream) {
+    if (h && tc_prec(prec)) {
+        set_err(h, "the tensor-core forms apply to sinv_selinv only");
+        return SINV_ERR_UNSUPPORTED;
+    }
+    if (!h || k < 0 || !valid_prec(prec)) return SINV_ERR_INVALID_ARG;
+    if (!on_device(h)) return SINV_ERR_INVALID_ARG;
+    if (h->mix_nnz < 0) {
+        set_err(h, "sinv_mix_own has not run");
+        return SINV_ERR_INVALID_ARG;
+    }
+    if (k > kLowrankKMax) {
+        set_err(h, "k > 256 is not supported");
+        return SINV_ERR_UNSUPPORTED;
+    }
+    if (k == 0 || h->P.n == 0) return SINV_OK;
+    if (!V || !lambda) return SINV_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if (prec == SINV_FP32) {
+        sinv_status s = ensure_work(h, ((size_t)h->P.n * k + k) * sizeof(float) + 256);
+        if (s != SINV_OK) return s;
+    }
+    TraceScope trace_scope(h->tracer);
+    // the correction is symmetric in (i, j): the CSC of the lower triangle serves as
+    // the CSR of the upper one
+    if ((e = lowrank_launch(h->P.n, h->dmix_cp, h->dmix_r, k, V, lambda, prec == SINV_FP32 ? 1 : 0, h->dwork,
+                            h->dmix_v, h->num_sms, (cudaStream_t)stream)) != cudaSuccess)
+        return cuda_fail(h, e, "lowrank launch");
+    return SINV_OK;
+}
+
+sinv_status sinv_mix_own_size(sinv_handle h, int64_t* nnz) {
+    if (!h || !nnz) return SINV_ERR_INVALID_ARG;
+    if (h->mix_nnz < 0) {
+        set_err(h, "sinv_mix_own has not run");
+        return SINV_ERR_INVALID_ARG;
+    }
+    *nnz = h->mix_nnz;
+    return SINV_OK;
+}
+
+sinv_status sinv_mix_own_copy(sinv_handle h, int64_t* M_colptr, int32_t* M_row, double* M_val, void* stream) {
+    if (!h || !M_colptr || !M_row || !M_val) return SINV_ERR_INVALID_ARG;
+    if (h->mix_nnz < 0) {
+        set_err(h, "sinv_mix_own has not run");
+        return SINV_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(M_colptr, h->dmix_cp, (h->P.n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && h->mix_nnz > 0)
+        e = cudaMemcpyAsync(M_row, h->dmix_r, h->mix_nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && h->mix_nnz > 0)
+        e = cudaMemcpyAsync(M_val, h->dmix_v, h->mix_nnz * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? SINV_OK : cuda_fail(h, e, "Mix own-pattern copy");
 }
 
 sinv_status sinv_timeline_enable(sinv_handle h, int enable) {

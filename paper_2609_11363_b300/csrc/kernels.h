@@ -197,6 +197,31 @@ cudaError_t own_product_launch(const OwnArgs& a, const int64_t* st, const int64_
                                const double* v, const int64_t* rp, const int32_t* rc, const double* rv,
                                const double* diag, const int64_t* bound, int32_t* nr, double* nv, int64_t* stN,
                                int64_t* ctN, int64_t cap, cudaStream_t s);
+// Mix on the own pattern: N (CSC of the lower triangle) and S_lo with L by columns
+struct MixOwnArgs {
+    int64_t n;
+    int grid;
+    const int64_t* Ncp;
+    const int32_t* Nr;
+    const double* Nv;
+    const int64_t* Srp;
+    const int32_t* Sdiag;
+    const int64_t* Lcp;
+    const int32_t* Lri;
+    const int32_t* Lcsr;
+    const int32_t* l2s;
+    const int8_t* pstart;
+    const double* G;
+    double eps;
+    int32_t* gkeys;  // per CTA: gslice keys then gslice positions, for columns beyond shared memory
+    int64_t gslice;
+    int32_t* ticket;
+};
+// fill = false: counts of every result column into cnt_or_cp; fill = true: the
+// columns at the offsets cnt_or_cp (the scan of the counts)
+cudaError_t mix_own_launch(const MixOwnArgs& a, bool fill, int64_t* cnt_or_cp, int32_t* outR, double* outV,
+                           cudaStream_t s);
+cudaError_t own_max_col_launch(int64_t n, const int64_t* cp, int64_t* out, int num_sms, cudaStream_t s);
 int own_table_slots(int64_t entries);
 int own_smem_slots();
 int own_grid_ctas(int num_sms);

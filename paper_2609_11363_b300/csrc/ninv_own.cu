@@ -374,7 +374,149 @@ __global__ void own_compact(int64_t n, const int64_t* __restrict__ off, const in
     }
 }
 
+// ---- Mix on NInv's own pattern (Section 2.3) ------------------------------------
+// Column j of the result: the rows of N's column j (values of N), then the rows
+// of S_eps in column j that N's column lacks; where a row of S_eps is in N's
+// column its value is G's.  An int table maps the rows of N's column to their
+// positions in it.
+__device__ __forceinline__ uint32_t mix_hash(int32_t r, uint32_t mask) { return ((uint32_t)r * 2654435761u) & mask; }
+
+// the entries of column j of S_lo: u = 0 the diagonal, u = 1 the 2x2 partner row
+// j + 1 when j opens a 2x2 block, then the rows of L's column j
+__device__ __forceinline__ void s_col_entry(int64_t j, int64_t u, bool partner, const int64_t* Srp,
+                                            const int32_t* Sdiag, const int64_t* Lcp, const int32_t* Lri,
+                                            const int32_t* Lcsr, const int32_t* l2s, int32_t& i, int64_t& p) {
+    if (u == 0) {
+        i = (int32_t)j;
+        p = Sdiag[j];
+    } else if (partner && u == 1) {
+        i = (int32_t)(j + 1);
+        p = Srp[j + 2] - 2;
+    } else {
+        const int64_t q = Lcp[j] + u - 1 - (partner ? 1 : 0);
+        i = Lri[q];
+        p = l2s[Lcsr[q]];
+    }
+}
+
+template <bool kFill>
+__global__ void __launch_bounds__(kOwnThreads) mix_own_kernel(int64_t n, const int64_t* __restrict__ Ncp,
+                                                              const int32_t* __restrict__ Nr,
+                                                              const double* __restrict__ Nv,
+                                                              const int64_t* __restrict__ Srp,
+                                                              const int32_t* __restrict__ Sdiag,
+                                                              const int64_t* __restrict__ Lcp,
+                                                              const int32_t* __restrict__ Lri,
+                                                              const int32_t* __restrict__ Lcsr,
+                                                              const int32_t* __restrict__ l2s,
+                                                              const int8_t* __restrict__ pstart,
+                                                              const double* __restrict__ G, double eps,
+                                                              int64_t* __restrict__ cnt_or_cp, int32_t* __restrict__ outR,
+                                                              double* __restrict__ outV, int32_t* gkeys,
+                                                              int64_t gslice, int32_t* ticket) {
+    __shared__ int32_t skeys[kSmemSlots];
+    __shared__ int32_t sidx[kSmemSlots];
+    __shared__ int64_t s_j;
+    __shared__ int32_t s_extra;
+    int32_t* gk = gkeys + (int64_t)blockIdx.x * 2 * gslice;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_j = atomicAdd(ticket, 1);
+            s_extra = 0;
+        }
+        __syncthreads();
+        const int64_t j = s_j;
+        if (j >= n) break;
+        const int64_t c0 = Ncp[j], len = Ncp[j + 1] - c0;
+        const uint32_t mask = table_mask(len);
+        int32_t* keys = (int64_t)mask + 1 <= kSmemSlots ? skeys : gk;
+        int32_t* idx = (int64_t)mask + 1 <= kSmemSlots ? sidx : gk + gslice;
+        for (uint32_t s = threadIdx.x; s <= mask; s += blockDim.x) keys[s] = -1;
+        __syncthreads();
+        for (int64_t e = threadIdx.x; e < len; e += blockDim.x) {
+            const int32_t r = Nr[c0 + e];
+            uint32_t h = mix_hash(r, mask);
+            while (atomicCAS(keys + h, -1, r) != -1) h = (h + 1) & mask;  // the rows of a column are distinct
+            idx[h] = (int32_t)e;
+        }
+        const int64_t o = kFill ? cnt_or_cp[j] : 0;
+        if (kFill)
+            for (int64_t e = threadIdx.x; e < len; e += blockDim.x) {
+                outR[o + e] = Nr[c0 + e];
+                outV[o + e] = Nv[c0 + e];
+            }
+        __syncthreads();
+        const bool partner = pstart[j] != 0 && j + 1 < n && pstart[j + 1] == 0;
+        const int64_t ns = 1 + (partner ? 1 : 0) + (Lcp[j + 1] - Lcp[j]);
+        for (int64_t u = threadIdx.x; u < ns; u += blockDim.x) {
+            int32_t i;
+            int64_t p;
+            s_col_entry(j, u, partner, Srp, Sdiag, Lcp, Lri, Lcsr, l2s, i, p);
+            const double g = G[p];
+            if (!(fabs(g) > eps)) continue;
+            // the row in N's column, or -1
+            int32_t k = -1;
+            uint32_t h = mix_hash(i, mask);
+            for (uint32_t probe = 0; probe <= mask; ++probe) {
+                const int32_t key = keys[h];
+                if (key == i) {
+                    k = idx[h];
+                    break;
+                }
+                if (key < 0) break;
+                h = (h + 1) & mask;
+            }
+            if (k >= 0) {
+                if (kFill) outV[o + k] = g;
+            } else {
+                const int32_t x = atomicAdd(&s_extra, 1);
+                if (kFill) {
+                    outR[o + len + x] = i;
+                    outV[o + len + x] = g;
+                }
+            }
+        }
+        __syncthreads();
+        if (!kFill && threadIdx.x == 0) cnt_or_cp[j] = len + s_extra;
+        __syncthreads();
+    }
+}
+
+// the longest column of a CSC pointer array
+__global__ void own_max_col(int64_t n, const int64_t* __restrict__ cp, int64_t* __restrict__ out) {
+    int64_t m = 0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, cp[j + 1] - cp[j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_i64(out, m);
+}
+
 }  // namespace
+
+cudaError_t own_max_col_launch(int64_t n, const int64_t* cp, int64_t* out, int num_sms, cudaStream_t s) {
+    cudaMemsetAsync(out, 0, sizeof(int64_t), s);
+    own_max_col<<<num_sms * 4, 256, 0, s>>>(n, cp, out);
+    return cudaGetLastError();
+}
+
+cudaError_t mix_own_launch(const MixOwnArgs& a, bool fill, int64_t* cnt_or_cp, int32_t* outR, double* outV,
+                           cudaStream_t s) {
+    cudaMemsetAsync(a.ticket, 0, sizeof(int32_t), s);
+    if (fill) {
+        trace_begin("mix_own_fill", s);
+        mix_own_kernel<true><<<a.grid, kOwnThreads, 0, s>>>(a.n, a.Ncp, a.Nr, a.Nv, a.Srp, a.Sdiag, a.Lcp, a.Lri,
+                                                            a.Lcsr, a.l2s, a.pstart, a.G, a.eps, cnt_or_cp, outR,
+                                                            outV, a.gkeys, a.gslice, a.ticket);
+    } else {
+        trace_begin("mix_own_count", s);
+        mix_own_kernel<false><<<a.grid, kOwnThreads, 0, s>>>(a.n, a.Ncp, a.Nr, a.Nv, a.Srp, a.Sdiag, a.Lcp, a.Lri,
+                                                             a.Lcsr, a.l2s, a.pstart, a.G, a.eps, cnt_or_cp, outR,
+                                                             outV, a.gkeys, a.gslice, a.ticket);
+    }
+    trace_end(s);
+    return cudaGetLastError();
+}
 
 cudaError_t own_identity_launch(int64_t n, int64_t* st, int64_t* ct, int32_t* r, double* v, int num_sms,
                                 cudaStream_t s) {

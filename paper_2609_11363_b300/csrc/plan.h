@@ -198,8 +198,12 @@ std::string build_plan(int64_t n, const int64_t* L_rowptr, const int32_t* L_col,
 std::string build_ninv_plan(const HostPlan& P, int m, NinvPlan& W);
 // A: n x n CSR pattern (host), structurally symmetric; warp_j / warp_e / warp_r: the
 // tier-W caps on pattern rows, staged entries and distinct rows of A.
+// Prp_given / Pc_given / src_given (optional): the pattern P_lo itself (CSR, sorted
+// rows, the diagonal last) and, per entry, the index of its start value.
 std::string build_spai_plan(const HostPlan& P, int64_t nnzA, const int64_t* A_rowptr, const int32_t* A_col,
-                            int power, int warp_j, int warp_e, int warp_r, SpaiPlan& X);
+                            int power, int warp_j, int warp_e, int warp_r, SpaiPlan& X,
+                            const int64_t* Prp_given = nullptr, const int32_t* Pc_given = nullptr,
+                            const int32_t* src_given = nullptr);
 // A: n x n CSR pattern (host), structurally symmetric (the same checks as above).
 std::string build_einv_plan(const HostPlan& P, int64_t nnzA, const int64_t* A_rowptr, const int32_t* A_col,
                             EinvPlan& X);

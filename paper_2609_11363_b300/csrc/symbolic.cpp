@@ -731,7 +731,8 @@ std::string check_symmetric_pattern(int64_t n, int64_t nnzA, const int64_t* Arp,
 }  // namespace
 
 std::string build_spai_plan(const HostPlan& P, int64_t nnzA, const int64_t* Arp, const int32_t* Ac, int power,
-                            int warp_j, int warp_e, int warp_r, SpaiPlan& X) {
+                            int warp_j, int warp_e, int warp_r, SpaiPlan& X, const int64_t* Prp_given,
+                            const int32_t* Pc_given, const int32_t* src_given) {
     const int64_t n = P.n;
     X = SpaiPlan();
     X.n = n;
@@ -741,11 +742,27 @@ std::string build_spai_plan(const HostPlan& P, int64_t nnzA, const int64_t* Arp,
     std::string err = check_symmetric_pattern(n, nnzA, Arp, Ac, sorted);
     if (!err.empty()) return err;
     // P_lo row by row: S_lo row i, and every j <= i within `power` steps of i in the graph of A
+    // (or the given pattern, whose start values are read at src_given)
     X.Prp.assign(n + 1, 0);
     std::vector<int64_t> reached(n, -1);
     std::vector<int32_t> row, frontier, next;
-    std::vector<int32_t> src_of;  // per P_lo entry: S_lo position or -1
-    for (int64_t i = 0; i < n; ++i) {
+    std::vector<int32_t> src_of;  // per P_lo entry: S_lo position or -1 (given: the caller's index)
+    if (Prp_given) {
+        if (Prp_given[0] != 0) return "the refinement pattern's row pointers do not start at 0";
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t a0 = Prp_given[i], a1 = Prp_given[i + 1];
+            if (a1 <= a0 || Pc_given[a1 - 1] != i)
+                return "row " + std::to_string(i) + " of the refinement pattern lacks its diagonal";
+            for (int64_t p = a0 + 1; p < a1; ++p)
+                if (Pc_given[p - 1] >= Pc_given[p]) return "the refinement pattern's rows are not sorted";
+            if (Pc_given[a0] < 0) return "a column index of the refinement pattern is negative";
+        }
+        if (Prp_given[n] >= ((int64_t)1 << 31)) return "the refinement pattern has >= 2^31 entries: not supported";
+        X.Prp.assign(Prp_given, Prp_given + n + 1);
+        X.Pc.assign(Pc_given, Pc_given + Prp_given[n]);
+        src_of.assign(src_given, src_given + Prp_given[n]);
+    }
+    for (int64_t i = 0; i < n && !Prp_given; ++i) {
         row.assign(P.Sc.begin() + P.Srp[i], P.Sc.begin() + P.Srp[i + 1]);
         if (power > 0) {
             reached[i] = i;

@@ -286,3 +286,47 @@ def test_full_size_64_spai_sampled():
     sigma = np.max(np.abs(pert - ref) / scale)
     got = Y.cpu().numpy()[idx]
     assert np.max(np.abs(got - ref) / scale) <= max(TOL64, 64.0 * sigma), sigma
+
+
+@pytest.mark.parametrize("name", ["covariance_24", "lap2d", "diff3d_10_planted"])
+@pytest.mark.parametrize("iters", [0, 3, 20])
+def test_mix_spai_on_mix_own_pattern(name, iters):
+    """Mix-SPAI on the pattern of Mix built on NInv's own loose-tolerance pattern
+    (delta = 1e-1; Sections 2.3-2.4).  The GPU's Mix pattern must be the oracle's
+    (these cases have no entry at a drop threshold); the refinement then starts from
+    the oracle's Mix values (given in the GPU's Mix order) and is held to the SPAI
+    tolerance; from the handle's own Mix values, zero steps return those values."""
+    A, f = CASES[name]()
+    S = oracle.symbolic_S(f.n, f.L_rowptr, f.L_col, f.pivot_start)
+    G = oracle.selinv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, S)
+    eps, m, delta = 1e-3 * np.abs(G).max(), 3, 1e-1
+    h = _handle(f)
+    Lv = torch.as_tensor(f.L_val, device="cuda")
+    Dv = torch.as_tensor(f.D_packed, device="cuda")
+    h.ninv_own(Lv, Dv, m, delta)
+    cp, rows, vals = h.mix_own(torch.as_tensor(G, device="cuda"), eps)
+    cp, rows, vals = cp.cpu().numpy().copy(), rows.cpu().numpy().copy(), vals.cpu().numpy().copy()
+    Nref = oracle.ninv_own(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, m, delta)
+    R = oracle.mix_own(f.n, S[0], S[1], G, Nref, eps).tocsr()
+    R.sort_indices()
+    cols = np.repeat(np.arange(f.n), np.diff(cp))
+    gpu_keys = set(zip(rows.tolist(), cols.tolist()))
+    Rc = R.tocoo()
+    assert gpu_keys == set(zip(Rc.row.tolist(), Rc.col.tolist())), name
+    Ac = h.spai_analyse_mix_own(A)
+    rp, col = h.spai_pattern()
+    assert np.array_equal(rp, R.indptr) and np.array_equal(col, R.indices)
+    Av = torch.as_tensor(Ac.data, device="cuda")
+    # the oracle's Mix values in the GPU's Mix order
+    X = np.asarray(R[rows, cols]).ravel()
+    Y = h.spai_mix_own(Av, iters, X=torch.as_tensor(X, device="cuda")).cpu().numpy()
+    h.sync_status()
+    ref = oracle.spai_refine(A, R.indptr, R.indices, R.data, iters)
+    tol, sigma = _tolerance(A, (R.indptr, R.indices), R.data, iters, ref) if iters > 4 else (TOL64, 0.0)
+    err = sel_rel_err(Y, ref, R.indptr, R.indices)
+    assert err <= tol, (name, iters, err, sigma)
+    if iters == 0:
+        Y0 = h.spai_mix_own(Av, 0).cpu().numpy()
+        M = sp.csc_matrix((vals, rows, cp), shape=(f.n, f.n)).tocsr()
+        M.sort_indices()
+        np.testing.assert_array_equal(Y0, M.data)
