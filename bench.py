@@ -857,10 +857,14 @@ def run_ninv_own(args, rank, world, dev):
 
 
 def run_elastic(args, rank, world, dev, peaks):
-    """27-point 3-dof elastic-like operator (the 80^3-node configuration's structure,
-    at N^3 nodes: its host ILDL at tau = 1e-4 grows to tens of minutes at 80^3).
-    One step = SelInv (FP32 form) + NInv m = 2 (FP32) + Mix + rank-64 correction
-    (FP32), inputs resident; FP64 SelInv is timed beside it."""
+    """27-point 3-dof elastic-like operator on N^3 nodes (n = 3 N^3; the configuration
+    is 80^3 nodes, n = 1,536,000), ILDL tau = 1e-4.  One step, inputs resident:
+    SelInv in the BF16 tensor-core form (the leading levels on tcgen05 with split
+    operands, the rest FP64; pivots and G_JJ FP64) + NInv on its own pattern (m = 2,
+    delta = 1e-1, the paper's loose tolerance for Mix) + Mix on that pattern + the
+    rank-64 correction on the Mix pattern.  FP64 and FP32 SelInv are timed beside it,
+    with the BF16 form's normwise difference from FP64.  At this size the SelInv
+    plan is the scan form (no pair lists)."""
     import torch
     from paper_2609_11363_b300 import Handle
     from workloads.configs import elastic3d, random_lowrank
@@ -870,22 +874,25 @@ def run_elastic(args, rank, world, dev, peaks):
     f = w.factors
     V, lam = random_lowrank(f.n, w.k, seed=5)
     t_gen = time.time() - t0
+    t0 = time.time()
     h = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start, device=dev.index)
+    t_sym = time.time() - t0
     Lv = torch.as_tensor(f.L_val, device=dev)
     Dv = torch.as_tensor(f.D_packed, device=dev)
     Vd = torch.as_tensor(V, device=dev)
     ld = torch.as_tensor(lam, device=dev)
     G = torch.empty(h.nnz_S, dtype=torch.float64, device=dev)
-    N = torch.empty_like(G)
-    M = torch.empty_like(G)
-    h.selinv(Lv, Dv, "fp64", out=G)
-    eps = 1e-3 * float(G.abs().max())  # the diagonal dominates |G| on this SPD operator
+    G64 = torch.empty_like(G)
+    h.selinv(Lv, Dv, "fp64", out=G64)
+    h.sync_status()
+    eps = 1e-3 * float(G64.abs().max())  # the diagonal dominates |G| on this SPD operator
+    delta, prec = 0.1, "bf16"
 
     def step():
-        h.selinv(Lv, Dv, "fp32", out=G)
-        h.ninv(Lv, Dv, w.m, "fp32", out=N)
-        h.mix(G, N, eps, out=M)
-        h.lowrank_correct(Vd, ld, M, "fp32")
+        h.selinv(Lv, Dv, prec, out=G)
+        h.ninv_own(Lv, Dv, w.m, delta, copy=False)
+        h.mix_own(G, eps, copy=False)
+        h.lowrank_correct_mix_own(Vd, ld, "fp64")
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -894,7 +901,7 @@ def run_elastic(args, rank, world, dev, peaks):
         torch.cuda.synchronize()
         out = []
         for _ in range(reps):
-            flush.zero_()  # inputs are smaller than L2: flush it between timed steps
+            flush.zero_()  # L2 flushed between timed steps
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -906,25 +913,51 @@ def run_elastic(args, rank, world, dev, peaks):
 
     for _ in range(args.warmup):
         step()
+    clk = ClockSampler(dev.index)
+    clk.start()
     ms = timed(step, args.steps)
-    ms_sel64 = timed(lambda: h.selinv(Lv, Dv, "fp64", out=G), args.steps)
-    ms_sel32 = timed(lambda: h.selinv(Lv, Dv, "fp32", out=G), args.steps)
-    ms_ninv = timed(lambda: h.ninv(Lv, Dv, w.m, "fp32", out=N), args.steps)
+    clocks = clk.stop()
+    phases = {"selinv_" + p: timed(lambda p=p: h.selinv(Lv, Dv, p, out=G), args.steps)
+              for p in ("fp64", "fp32", "bf16", "tf32")}
+    h.selinv(Lv, Dv, prec, out=G)
+    diff_bf16 = float(torch.linalg.norm(G - G64) / torch.linalg.norm(G64))
+    phases["ninv_own"] = timed(lambda: h.ninv_own(Lv, Dv, w.m, delta, copy=False), args.steps)
+    _, _, _, wsteps = h.ninv_own(Lv, Dv, w.m, delta, copy=False)
+    phases["mix_own"] = timed(lambda: h.mix_own(G, eps, copy=False), args.steps)
+    phases["lowrank_mix"] = timed(lambda: h.lowrank_correct_mix_own(Vd, ld, "fp64"), args.steps)
+    # one step traced, and the scan form's exact lookups and pairs of one FP64 SelInv
+    h.trace(True)
+    step()
+    torch.cuda.synchronize()
+    kern = h.trace_read()
+    h.trace(False)
+    h.timeline(True)
+    h.selinv(Lv, Dv, "fp64", out=G)
+    look, pairs = h.selinv_scan_counts()
+    h.timeline(False)
     h.sync_status()
     st = h.stats()
     nS = 2 * h.nnz_S - h.n
     line = {"metric": METRIC, "value": world * nS / (ms / 1e3), "unit": "entries/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "elastic: 27-point 3-dof lattice-spring operator %d^3 nodes (n=%d), ILDL tau=1e-4, "
-                                   "SelInv + NInv m=%d + Mix + rank-%d correction, FP32 form"
-                                   % (args.elastic_size, f.n, w.m, w.k),
-                       "stated_rel_error": STATED_ERROR["fp32"], "nnz_L": st["nnz_L"], "S_entries": nS,
-                       "supernodes": st["n_supernodes"], "max_width": st["max_width"], "levels": st["n_levels"],
-                       "nnz_W": st["nnz_W"], "ninv_form": "map" if st["ninv_index_bytes"] > 0 else "hash",
-                       "selinv_fp64_ms": ms_sel64, "selinv_fp32_ms": ms_sel32, "ninv_fp32_ms": ms_ninv,
-                       "input_gen_s": t_gen},
-            "gpu_launches": None}
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 split operands + f64", "data": "synthetic",
+            "config": {"workload": "elastic: 27-point 3-dof lattice-spring operator %d^3 nodes (n=%d), ILDL tau=1e-4; "
+                                   "SelInv BF16/FP32-acc + FP64 pivots, NInv m=%d on its own pattern (delta=%g), "
+                                   "Mix on that pattern, rank-%d correction on the Mix pattern"
+                                   % (args.elastic_size, f.n, w.m, delta, w.k),
+                       "stated_rel_error": {"selinv_bf16": "normwise 1e-5 vs FP64 oracle",
+                                            "ninv_mix_lowrank": STATED_ERROR["fp64"]},
+                       "selinv_bf16_normwise_vs_fp64": diff_bf16,
+                       "nnz_L": st["nnz_L"], "S_entries": nS, "supernodes": st["n_supernodes"],
+                       "max_width": st["max_width"], "levels": st["n_levels"], "max_c": st["max_c"],
+                       "selinv_form": "scan" if st["selinv_scan"] else "pair lists",
+                       "scan_lookups": look, "scan_pairs_lower": pairs, "tc_levels": st["tc_levels"],
+                       "tc_supernodes": st["tc_supernodes"], "nnz_W_by_step": [int(x) for x in wsteps],
+                       "nnz_N_lo": getattr(h, "own_nnz", None), "nnz_mix_lo": h.mix_own_nnz(), "eps": eps,
+                       "phases_ms": phases,
+                       "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kern.items()},
+                       "input_gen_s": t_gen, "symbolic_s": t_sym, "l2": "flushed between timed steps (512 MB write)"},
+            "clocks": clocks, "gpu_launches": int(sum(v[0] for v in kern.values()))}
     if rank == 0:
         print(json.dumps(line))
 

@@ -552,14 +552,18 @@ class Handle:
                                                    _check_tensor(X, "X_S", self.nnz_S), _stream_ptr(stream)))
         return X
 
-    def ninv_own(self, L_val, D_val, m, delta, stream=None):
+    def ninv_own(self, L_val, D_val, m, delta, stream=None, copy=True):
         """NInv on its own pattern: (colptr, rows, values) of the lower triangle in CSC
-        (CUDA tensors) and the nnz of W after every Horner step."""
+        (CUDA tensors) and the nnz of W after every Horner step; copy=False leaves the
+        result in the handle and returns (None, None, None, steps)."""
         self._check(self._lib.sinv_ninv_own(self._h, _check_tensor(L_val, "L_val"), _check_tensor(D_val, "D_val"),
                                             int(m), float(delta), _stream_ptr(stream)))
         nnz = ctypes.c_int64()
         steps = np.zeros(int(m) + 1, dtype=np.int64)
         self._check(self._lib.sinv_ninv_own_size(self._h, ctypes.byref(nnz), _np_ptr(steps), int(m) + 1))
+        if not copy:
+            self.own_nnz = int(nnz.value)
+            return None, None, None, steps
         cp = torch.empty(self.n + 1, dtype=torch.int64, device=self.device)
         rows = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=self.device)
         vals = torch.empty(max(nnz.value, 1), dtype=torch.float64, device=self.device)
@@ -568,12 +572,17 @@ class Handle:
                                                  _check_tensor(vals, "vals"), _stream_ptr(stream)))
         return cp, rows[:nnz.value], vals[:nnz.value], steps
 
-    def mix_own(self, G, eps, stream=None):
+    def mix_own(self, G, eps, stream=None, copy=True):
         """Mix on the pattern of the last ninv_own: (colptr, rows, values) of the lower
-        triangle in CSC (CUDA tensors)."""
+        triangle in CSC (CUDA tensors); copy=False leaves the result in the handle."""
         self._check(self._lib.sinv_mix_own(self._h, _check_tensor(G, "G", self.nnz_S), float(eps),
                                            _stream_ptr(stream)))
-        return self.mix_own_result(stream)
+        return self.mix_own_result(stream) if copy else None
+
+    def mix_own_nnz(self) -> int:
+        nnz = ctypes.c_int64()
+        self._check(self._lib.sinv_mix_own_size(self._h, ctypes.byref(nnz)))
+        return int(nnz.value)
 
     def mix_own_result(self, stream=None):
         """The handle's current Mix on the own pattern (copies): (colptr, rows, values)."""
