@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--band-b", type=int, default=1024)
     p.add_argument("--band-tau", type=float, default=1e-6)
     p.add_argument("--elastic-size", type=int, default=24)
+    p.add_argument("--factor-cache", default=None,
+                   help="elastic: directory of the on-disk factor cache (the ILDL at 80^3 nodes takes minutes)")
     p.add_argument("--cov-size", type=int, default=200)
     p.add_argument("--spai-iters", type=int, default=20,
                    help="covariance: PCG steps of the SPAI refinement of Mix (Mix-SPAI); 0 = leave it out")
@@ -870,7 +872,7 @@ def run_elastic(args, rank, world, dev, peaks):
     from workloads.configs import elastic3d, random_lowrank
     torch.cuda.set_device(dev)
     t0 = time.time()
-    w = elastic3d(args.elastic_size)
+    w = elastic3d(args.elastic_size, cache_dir=args.factor_cache)
     f = w.factors
     V, lam = random_lowrank(f.n, w.k, seed=5)
     t_gen = time.time() - t0

@@ -195,11 +195,19 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// X -= G~_CC Lh for the rows [i0, i1) of C taken by this warp (row i0 + v, then every
-// nw-th): row r = C[i] of S_lo is read from its diagonal backwards in batches of
-// kBatch x 32 entries while the columns stay >= C[0]; an entry whose column is C[k]
-// adds G Lh[i][:] into X[k] (distinct k within an instruction) and G Lh[k][:] into
-// X[i] (summed over the warp, one atomic add per column of the supernode).
+// X -= G~_CC Lh for the rows [i0, i1) of C taken by this warp (rows i0 + v, then
+// every nw-th).  Row r = C[i] of S_lo is read from its diagonal backwards in batches
+// of kBatch x 32 entries while the columns stay >= C[0]; an entry whose column is
+// C[k] adds G Lh[i][:] into X[k] (distinct k within an instruction) and G Lh[k][:]
+// into X[i] (summed over the warp, one atomic add per column of the supernode).
+// The warp keeps two rows in flight (two slots): the loads of both are issued
+// before either is used, so one row's memory latency hides behind the other's.
+struct ScanSlot {
+    int i;        // local row, -1 when the slot is idle
+    int64_t rs;   // first entry of the row in S_lo
+    int64_t hi;   // one past the next batch's last entry
+};
+
 template <class Form>
 __device__ __forceinline__ void scan_rows(const SelinvArgs& a, const typename Form::G* Gw, const int32_t* Crow, int c,
                                           int i0, int i1, int v, int nw, const int32_t* keys, const int32_t* vals,
@@ -208,36 +216,59 @@ __device__ __forceinline__ void scan_rows(const SelinvArgs& a, const typename Fo
     using R = typename Form::R;
     const int32_t c0 = c > 0 ? Crow[0] : 0;
     unsigned long long n_look = 0, n_hit = 0;
-    for (int i = i0 + v; i < i1; i += nw) {
-        const int32_t r = Crow[i];
-        const int64_t rs = a.Srp[r];
-        const int64_t pd = a.Sdiag[r];
-        for (int64_t hi = pd;;) {
-            int32_t col[kBatch];
-            int kk[kBatch];
+    int next = i0 + v;
+    auto start = [&](ScanSlot& sl) {
+        if (next < i1) {
+            const int32_t r = Crow[next];
+            sl.i = next;
+            sl.rs = a.Srp[r];
+            sl.hi = a.Sdiag[r];
+            next += nw;
+        } else {
+            sl.i = -1;
+        }
+    };
+    ScanSlot sl[2];
+    start(sl[0]);
+    start(sl[1]);
+    while (sl[0].i >= 0 || sl[1].i >= 0) {
+        int32_t col[2][kBatch];
+        int kk[2][kBatch];
+        R g[2][kBatch];
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) {
-                const int64_t p = hi - 1 - lane - 32 * u;
-                col[u] = p >= rs ? __ldg(a.Sc + p) : -1;
+                const int64_t p = sl[t].hi - 1 - lane - 32 * u;
+                col[t][u] = (sl[t].i >= 0 && p >= sl[t].rs) ? __ldg(a.Sc + p) : -1;
             }
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u) kk[u] = col[u] >= c0 ? c_find(keys, vals, mask, col[u]) : -1;
-            R g[kBatch];
+        for (int t = 0; t < 2; ++t)
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u) g[u] = kk[u] >= 0 ? Form::ld(Gw + (hi - 1 - lane - 32 * u)) : R(0);
+            for (int u = 0; u < kBatch; ++u)
+                kk[t][u] = col[t][u] >= c0 ? c_find(keys, vals, mask, col[t][u]) : -1;
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u)
+                g[t][u] = kk[t][u] >= 0 ? Form::ld(Gw + (sl[t].hi - 1 - lane - 32 * u)) : R(0);
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            if (sl[t].i < 0) continue;
+            const int i = sl[t].i;
             bool any = false;
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) {
-                if (kk[u] < 0) continue;
+                if (kk[t][u] < 0) continue;
                 any = true;
-                for (int q = 0; q < w; ++q) atomicAdd(x + kk[u] * w + q, -g[u] * lh[i * w + q]);
+                for (int q = 0; q < w; ++q) atomicAdd(x + kk[t][u] * w + q, -g[t][u] * lh[i * w + q]);
             }
             if (__any_sync(0xffffffffu, any)) {
                 for (int q = 0; q < w; ++q) {
                     R s = R(0);
 #pragma unroll
                     for (int u = 0; u < kBatch; ++u)
-                        if (kk[u] >= 0) s += g[u] * lh[kk[u] * w + q];
+                        if (kk[t][u] >= 0) s += g[t][u] * lh[kk[t][u] * w + q];
                     s = warp_sum(s);
                     if (lane == 0) atomicAdd(x + i * w + q, -s);
                 }
@@ -245,18 +276,21 @@ __device__ __forceinline__ void scan_rows(const SelinvArgs& a, const typename Fo
             if (a.counts) {
 #pragma unroll
                 for (int u = 0; u < kBatch; ++u) {
-                    n_look += col[u] >= c0;
-                    n_hit += kk[u] >= 0;
+                    n_look += col[t][u] >= c0;
+                    n_hit += kk[t][u] >= 0;
                 }
             }
             // go on while the batch's smallest column (lane 31, last chunk) is still in range
-            const int32_t last = __shfl_sync(0xffffffffu, col[kBatch - 1], 31);
-            hi -= 32 * kBatch;
-            if (hi <= rs || last < c0) break;
-        }
-        if (lane == 0) {
-            const R gd = Form::ld(Gw + pd);
-            for (int q = 0; q < w; ++q) atomicAdd(x + i * w + q, -gd * lh[i * w + q]);
+            const int32_t last = __shfl_sync(0xffffffffu, col[t][kBatch - 1], 31);
+            sl[t].hi -= 32 * kBatch;
+            if (sl[t].hi <= sl[t].rs || last < c0) {
+                if (lane == 0) {
+                    const int64_t pd = a.Sdiag[Crow[i]];
+                    const R gd = Form::ld(Gw + pd);
+                    for (int q = 0; q < w; ++q) atomicAdd(x + i * w + q, -gd * lh[i * w + q]);
+                }
+                start(sl[t]);
+            }
         }
     }
     if (a.counts) {

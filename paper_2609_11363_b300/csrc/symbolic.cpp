@@ -545,8 +545,10 @@ std::string build_plan(int64_t n, const int64_t* Lrp, const int32_t* Lc, const i
     // supernode with more than 4 big_pairs pairs is split by rows into parts of about
     // that size (at most kMaxParts), one CTA each: the parts add their share of X into
     // a global block and the last part to arrive finishes the supernode.
-    constexpr int64_t kMaxParts = 16;
-    const int64_t part_pairs = 4 * big_pairs;
+    // the scan form costs more per pair (each row's lookups wait on its loads): its
+    // large supernodes take smaller parts and more CTAs
+    const int64_t kMaxParts = P.scan ? 32 : 16;
+    const int64_t part_pairs = P.scan ? big_pairs : 4 * big_pairs;
     std::vector<int64_t> level_size(P.n_levels, 0);
     for (int64_t s = 0; s < ns; ++s) level_size[P.sn[s].level]++;
     P.items.clear();

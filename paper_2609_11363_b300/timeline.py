@@ -97,11 +97,13 @@ def main(argv=None):
     p.add_argument("--tau", type=float, default=1e-6)
     p.add_argument("--cap", type=int, default=0)
     p.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "tf32", "bf16"])
+    p.add_argument("--pair-bytes", type=int, default=0,
+                   help="memory the SelInv pair lists may take (0: default, < 0: the scan form)")
     args = p.parse_args(argv)
     import torch
     from paper_2609_11363_b300 import Handle
     f = _workload(args)
-    h = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start, supernode_cap=args.cap)
+    h = Handle(f.n, f.L_rowptr, f.L_col, f.pivot_start, supernode_cap=args.cap, selinv_pair_bytes=args.pair_bytes)
     Lv = torch.as_tensor(f.L_val, device="cuda")
     Dv = torch.as_tensor(f.D_packed, device="cuda")
     G = torch.empty(h.nnz_S, dtype=torch.float64, device="cuda")
@@ -124,7 +126,8 @@ def main(argv=None):
     deps = dependencies(f.n, f.L_rowptr, f.L_col, sn_start)
     out = critical_path(stamps, deps, sn_level)
     out.update(workload=args.workload, prec=args.prec, n=f.n, cap=args.cap, ms_without_timeline=ms_plain,
-               stats={k: v for k, v in h.stats().items() if k in ("n_supernodes", "n_levels", "tc_levels")})
+               stats={k: v for k, v in h.stats().items()
+                      if k in ("n_supernodes", "n_levels", "tc_levels", "selinv_scan", "max_c")})
     print(json.dumps(out))
     return 0
 

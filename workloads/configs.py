@@ -114,9 +114,50 @@ def batch9pt_member(seed: int, tau: float = 1e-2, m: int = 3, n_range=(2048, 655
     return Workload("9pt_%d" % seed, A, ildl(A, tau), tau, m, meta={"shape": (nx, ny), "seed": seed})
 
 
-def elastic3d(N: int = 80, tau: float = 1e-4, m: int = 2, k: int = 64, seed: int = 5) -> Workload:
-    A, p = _ordered(grids.elastic3d_27pt(N, N, N, seed), (N, N, N), dof=3)
-    return Workload("elastic3d_%d" % N, A, ildl(A, tau), tau, m, k, meta={"shape": (N, N, N), "seed": seed})
+def elastic3d(N: int = 80, tau: float = 1e-4, m: int = 2, k: int = 64, seed: int = 5,
+              cache_dir: str | None = None) -> Workload:
+    """cache_dir: keep the ordered matrix and its factors in a file there, keyed by
+    the generator, N, tau and seed (the ILDL of 80^3 nodes takes minutes on one core),
+    and load them from it when present."""
+    key = "elastic3d_N%d_tau%g_seed%d" % (N, tau, seed)
+    cached = load_cached(cache_dir, key)
+    if cached is not None:
+        A, f = cached
+    else:
+        A, p = _ordered(grids.elastic3d_27pt(N, N, N, seed), (N, N, N), dof=3)
+        f = ildl(A, tau)
+        store_cached(cache_dir, key, A, f)
+    return Workload("elastic3d_%d" % N, A, f, tau, m, k, meta={"shape": (N, N, N), "seed": seed})
+
+
+def load_cached(cache_dir, key):
+    """(A, factors) from cache_dir/key.npz, or None (no directory or no file)."""
+    import os
+    if not cache_dir:
+        return None
+    path = os.path.join(cache_dir, key + ".npz")
+    if not os.path.exists(path):
+        return None
+    z = np.load(path)
+    n = int(z["n"])
+    A = sp.csr_matrix((z["A_val"], z["A_col"], z["A_rp"]), shape=(n, n))
+    f = Factors(n=n, L_rowptr=z["L_rp"], L_col=z["L_col"], L_val=z["L_val"], pivot_start=z["ps"],
+                d_diag=z["dd"], d_off=z["do"], stats={"cache": path})
+    return A, f
+
+
+def store_cached(cache_dir, key, A, f):
+    """Write (A, factors) to cache_dir/key.npz (uncompressed; written to a temporary
+    name first, so a reader never sees a partial file)."""
+    import os
+    if not cache_dir:
+        return
+    os.makedirs(cache_dir, exist_ok=True)
+    A = sp.csr_matrix(A)
+    tmp = os.path.join(cache_dir, key + ".partial.npz")
+    np.savez(tmp, n=f.n, A_rp=A.indptr, A_col=A.indices, A_val=A.data, L_rp=f.L_rowptr, L_col=f.L_col,
+             L_val=f.L_val, ps=f.pivot_start, dd=f.d_diag, do=f.d_off)
+    os.replace(tmp, os.path.join(cache_dir, key + ".npz"))
 
 
 def covariance(N: int = 200, alpha: float = 3.0, beta: float = 4.0, tau: float = 1e-3, m: int = 3) -> Workload:
