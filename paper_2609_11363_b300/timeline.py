@@ -84,7 +84,7 @@ def _workload(args):
     if args.workload == "band":
         return band(args.n, args.b, tau=args.tau).factors
     if args.workload == "elastic":
-        return elastic3d(args.size).factors
+        return elastic3d(args.size, cache_dir=args.factor_cache).factors
     return plant_2x2(diff3d(args.size).factors, 0.02, 2)
 
 
@@ -97,6 +97,7 @@ def main(argv=None):
     p.add_argument("--tau", type=float, default=1e-6)
     p.add_argument("--cap", type=int, default=0)
     p.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "tf32", "bf16"])
+    p.add_argument("--factor-cache", default=None, help="elastic: directory of the on-disk factor cache")
     p.add_argument("--pair-bytes", type=int, default=0,
                    help="memory the SelInv pair lists may take (0: default, < 0: the scan form)")
     args = p.parse_args(argv)
