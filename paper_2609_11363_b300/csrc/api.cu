@@ -432,7 +432,7 @@ sinv_status sinv_symbolic(int64_t n, const int64_t* L_rowptr, const int32_t* L_c
         return cuda_fail(h, e, "device state");
     }
     if ((e = selinv_configure()) != cudaSuccess || (e = selinv_tc_configure()) != cudaSuccess ||
-        (e = ninv_configure()) != cudaSuccess ||
+        (e = ninv_configure()) != cudaSuccess || (e = own_configure()) != cudaSuccess ||
         (e = ninv_maps_configure()) != cudaSuccess) {
         *out = h;
         return cuda_fail(h, e, "kernel attributes");
@@ -1728,7 +1728,7 @@ sinv_status sinv_ninv_own(sinv_handle h, const double* L_val, const double* D_va
         int64_t maxb = 0;
         if ((e = own_bound_launch(n, h->dLcp, h->dLri, ctA.as<int64_t>(), d_max, h->num_sms, st)) != cudaSuccess ||
             (e = read64(d_max, &maxb)) != cudaSuccess ||
-            (e = tables(own_table_slots(maxb), own_table_slots(maxb) <= own_smem_slots())) != cudaSuccess)
+            (e = tables(own_table_slots(maxb), own_table_slots(maxb) <= own_horner_slots())) != cudaSuccess)
             return fail(e, "NInv own-pattern Horner tables");
         int64_t want = std::max<int64_t>(capB, 2 * nnz_prev + n);
         if ((int64_t)h->own_hint.size() > t) want = std::max<int64_t>(want, h->own_hint[t] + h->own_hint[t] / 32);
@@ -1782,7 +1782,7 @@ sinv_status sinv_ninv_own(sinv_handle h, const double* L_val, const double* D_va
     // the product's tables: Y[:, j] in the first half of a CTA's slice, N's column in the second
     {
         const int64_t half = std::max<int64_t>(own_table_slots(2 * maxct), own_table_slots(std::max<int64_t>(maxbound, 1)));
-        if ((e = tables(2 * half, half <= own_smem_slots() / 2)) != cudaSuccess)
+        if ((e = tables(2 * half, half <= own_prod_slots())) != cudaSuccess)
             return fail(e, "NInv own-pattern product tables");
     }
     DevBuf nr, nv, stN, ctN, cpN;

@@ -224,6 +224,9 @@ cudaError_t mix_own_launch(const MixOwnArgs& a, bool fill, int64_t* cnt_or_cp, i
 cudaError_t own_max_col_launch(int64_t n, const int64_t* cp, int64_t* out, int num_sms, cudaStream_t s);
 int own_table_slots(int64_t entries);
 int own_smem_slots();
+int own_horner_slots();
+int own_prod_slots();
+cudaError_t own_configure();
 int own_grid_ctas(int num_sms);
 
 // D^{-1} per row (ninv.cu): diagonal, off-diagonal of its 2x2 block, partner row (-1: 1x1)

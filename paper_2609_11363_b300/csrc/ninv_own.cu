@@ -32,7 +32,9 @@ namespace {
 
 constexpr int kOwnThreads = 256;
 constexpr int kOwnWarps = kOwnThreads / 32;
-constexpr int kSmemSlots = 2048;  // keys + FP64 values in shared memory: 24 KB
+constexpr int kSmemSlots = 2048;    // keys + FP64 values in shared memory: 24 KB (diagonal pass, Mix)
+constexpr int kHornerSlots = 4096;  // Horner step: 48 KB of dynamic shared memory
+constexpr int kProdSlots = 2048;    // product: two tables (Y and N's column), 48 KB in all
 
 // per-CTA table: shared memory when it fits, else the given global slice
 struct Table {
@@ -62,6 +64,29 @@ __device__ __forceinline__ Table make_table(int64_t entries, int32_t* skeys, dou
 __device__ __forceinline__ void table_add(Table& t, int32_t r, double v) {
     const uint32_t s = table_insert(t.keys, t.mask, r);
     atomicAdd(t.vals + s, v);
+}
+
+// The same into a shared-memory table that may be too small: the distinct rows it
+// takes are counted, and past `limit` (half its slots) the column is marked for a
+// second pass with a table sized by its bound; nothing is added after the mark.
+__device__ __forceinline__ void table_add_opt(Table& t, int32_t r, double v, int32_t* n_keys, int32_t limit,
+                                              volatile int32_t* over) {
+    if (*over) return;
+    uint32_t h = hash_row(r, t.mask);
+    for (uint32_t probe = 0; probe <= t.mask; ++probe) {
+        const int32_t old = atomicCAS(t.keys + h, -1, r);
+        if (old == -1) {
+            if (atomicAdd(n_keys, 1) >= limit) *over = 1;
+            atomicAdd(t.vals + h, v);
+            return;
+        }
+        if (old == r) {
+            atomicAdd(t.vals + h, v);
+            return;
+        }
+        h = (h + 1) & t.mask;
+    }
+    *over = 1;
 }
 
 __device__ __forceinline__ void atomic_max_i64(int64_t* p, int64_t v) {
@@ -142,11 +167,12 @@ __global__ void __launch_bounds__(kOwnThreads) own_horner(int64_t n, const int64
                                                           int64_t* __restrict__ stOut, int64_t* __restrict__ ctOut,
                                                           int64_t cap, unsigned long long* cursor, int32_t* gkeys,
                                                           double* gvals, int64_t gslice, int32_t* ticket) {
-    __shared__ int32_t skeys[kSmemSlots];
-    __shared__ double svals[kSmemSlots];
+    extern __shared__ __align__(16) unsigned char own_dyn[];
+    int32_t* skeys = reinterpret_cast<int32_t*>(own_dyn);
+    double* svals = reinterpret_cast<double*>(own_dyn + kHornerSlots * sizeof(int32_t));
     __shared__ int64_t s_j, s_base;
     __shared__ unsigned long long s_b;
-    __shared__ int32_t s_cnt;
+    __shared__ int32_t s_cnt, s_keys, s_over;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int32_t* gk = gkeys + (int64_t)blockIdx.x * gslice;
     double* gv = gvals + (int64_t)blockIdx.x * gslice;
@@ -155,6 +181,8 @@ __global__ void __launch_bounds__(kOwnThreads) own_horner(int64_t n, const int64
             s_j = atomicAdd(ticket, 1);
             s_cnt = 0;
             s_b = 0ull;
+            s_keys = 0;
+            s_over = 0;
         }
         __syncthreads();
         const int64_t j = s_j;
@@ -165,16 +193,31 @@ __global__ void __launch_bounds__(kOwnThreads) own_horner(int64_t n, const int64
         atomicAdd(&s_b, b);
         __syncthreads();
         const int64_t bound = min((int64_t)s_b + 1, n - j);
-        Table t = make_table(bound, skeys, svals, kSmemSlots, gk, gv);
+        // a bound past shared memory first tries the shared table (the bound counts a
+        // row once per column it comes from; the distinct rows are usually far fewer)
+        const bool opt = (int64_t)table_mask(bound) + 1 > kHornerSlots;
+        Table t = make_table(opt ? kHornerSlots / 2 : bound, skeys, svals, kHornerSlots, gk, gv);
         __syncthreads();
-        if (threadIdx.x == 0) table_add(t, (int32_t)j, 1.0);
-        for (int64_t q = Lcp[j] + wid; q < Lcp[j + 1]; q += kOwnWarps) {
-            const int32_t k = Lri[q];
-            const double e = -Lval[Lcsr[q]];
-            const int64_t p0 = stIn[k], p1 = p0 + ctIn[k];
-            for (int64_t p = p0 + lane; p < p1; p += 32) table_add(t, rIn[p], e * vIn[p]);
+        for (int pass = 0; pass < 2; ++pass) {
+            const bool o = opt && pass == 0;
+            if (threadIdx.x == 0) {
+                if (o) table_add_opt(t, (int32_t)j, 1.0, &s_keys, kHornerSlots / 2, &s_over);
+                else table_add(t, (int32_t)j, 1.0);
+            }
+            for (int64_t q = Lcp[j] + wid; q < Lcp[j + 1]; q += kOwnWarps) {
+                const int32_t k = Lri[q];
+                const double e = -Lval[Lcsr[q]];
+                const int64_t p0 = stIn[k], p1 = p0 + ctIn[k];
+                for (int64_t p = p0 + lane; p < p1; p += 32) {
+                    if (o) table_add_opt(t, rIn[p], e * vIn[p], &s_keys, kHornerSlots / 2, &s_over);
+                    else table_add(t, rIn[p], e * vIn[p]);
+                }
+            }
+            __syncthreads();
+            if (!(o && s_over)) break;
+            t = make_table(bound, skeys, svals, kHornerSlots, gk, gv);  // the second pass: sized by the bound
+            __syncthreads();
         }
-        __syncthreads();
         const int32_t jj = (int32_t)j;
         append_kept(t, [&](int32_t r, double v) { return r == jj || fabs(v) >= delta; }, j, rOut, vOut, stOut, ctOut,
                     cap, cursor, &s_cnt, &s_base);
@@ -281,12 +324,13 @@ __global__ void __launch_bounds__(kOwnThreads) own_product(int64_t n, const int6
                                                            int64_t* __restrict__ stN, int64_t* __restrict__ ctN,
                                                            int64_t cap, unsigned long long* cursor, int32_t* gkeys,
                                                            double* gvals, int64_t gslice, int32_t* ticket) {
-    __shared__ int32_t skeys[kSmemSlots / 2];
-    __shared__ double svals[kSmemSlots / 2];
-    __shared__ int32_t skeys2[kSmemSlots / 2];
-    __shared__ double svals2[kSmemSlots / 2];
+    extern __shared__ __align__(16) unsigned char own_dyn[];
+    int32_t* skeys = reinterpret_cast<int32_t*>(own_dyn);
+    int32_t* skeys2 = skeys + kProdSlots;
+    double* svals = reinterpret_cast<double*>(own_dyn + 2 * kProdSlots * sizeof(int32_t));
+    double* svals2 = svals + kProdSlots;
     __shared__ int64_t s_j, s_base;
-    __shared__ int32_t s_cnt;
+    __shared__ int32_t s_cnt, s_keys, s_over;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     // Y[:, j] in the first half of the CTA's slice, N's column in the second
     int32_t* gk = gkeys + (int64_t)blockIdx.x * gslice;
@@ -295,26 +339,39 @@ __global__ void __launch_bounds__(kOwnThreads) own_product(int64_t n, const int6
         if (threadIdx.x == 0) {
             s_j = atomicAdd(ticket, 1);
             s_cnt = 0;
+            s_keys = 0;
+            s_over = 0;
         }
         __syncthreads();
         const int64_t j = s_j;
         if (j >= n) break;
-        Table ty = make_table(2 * ct[j], skeys, svals, kSmemSlots / 2, gk, gv);
-        Table tn = make_table(bound[j], skeys2, svals2, kSmemSlots / 2, gk + gslice / 2, gv + gslice / 2);
+        // N's column: a bound past shared memory first tries the shared table
+        const bool opt = (int64_t)table_mask(bound[j]) + 1 > kProdSlots;
+        Table ty = make_table(2 * ct[j], skeys, svals, kProdSlots, gk, gv);
+        Table tn = make_table(opt ? kProdSlots / 2 : bound[j], skeys2, svals2, kProdSlots, gk + gslice / 2,
+                              gv + gslice / 2);
         __syncthreads();
         fill_y(ty, st, ct, r, v, j, dr, dp, part);
         __syncthreads();
         // N[i, j] += W[c, i] Y[c, j] over the rows c of Y[:, j] and the entries of row c of W
-        for (uint32_t s = wid; s <= ty.mask; s += kOwnWarps) {
-            const int32_t c = ty.keys[s];
-            if (c < 0) continue;
-            const double y = ty.vals[s];
-            for (int64_t p = rp[c] + lane; p < rp[c + 1]; p += 32) {
-                const int32_t i = rc[p];
-                if (i >= j) table_add(tn, i, rv[p] * y);
+        for (int pass = 0; pass < 2; ++pass) {
+            const bool o = opt && pass == 0;
+            for (uint32_t s = wid; s <= ty.mask; s += kOwnWarps) {
+                const int32_t c = ty.keys[s];
+                if (c < 0) continue;
+                const double y = ty.vals[s];
+                for (int64_t p = rp[c] + lane; p < rp[c + 1]; p += 32) {
+                    const int32_t i = rc[p];
+                    if (i < j) continue;
+                    if (o) table_add_opt(tn, i, rv[p] * y, &s_keys, kProdSlots / 2, &s_over);
+                    else table_add(tn, i, rv[p] * y);
+                }
             }
+            __syncthreads();
+            if (!(o && s_over)) break;
+            tn = make_table(bound[j], skeys2, svals2, kProdSlots, gk + gslice / 2, gv + gslice / 2);
+            __syncthreads();
         }
-        __syncthreads();
         const double djj = diag[j];
         const int32_t jj = (int32_t)j;
         append_kept(tn, [&](int32_t i, double x) { return i == jj || fabs(x) >= delta * sqrt(fabs(diag[i] * djj)); },
@@ -543,7 +600,7 @@ cudaError_t own_horner_launch(const OwnArgs& a, const int64_t* stIn, const int64
     cudaMemsetAsync(a.ticket, 0, sizeof(int32_t), s);
     cudaMemsetAsync(a.cursor, 0, sizeof(unsigned long long), s);
     trace_begin("ninv_own_horner", s);
-    own_horner<<<a.grid, kOwnThreads, 0, s>>>(a.n, a.Lcp, a.Lri, a.Lcsr, a.Lval, stIn, ctIn, rIn, vIn, a.delta, rOut,
+    own_horner<<<a.grid, kOwnThreads, kHornerSlots * (sizeof(int32_t) + sizeof(double)), s>>>(a.n, a.Lcp, a.Lri, a.Lcsr, a.Lval, stIn, ctIn, rIn, vIn, a.delta, rOut,
                                               vOut, stOut, ctOut, cap, a.cursor, a.gkeys, a.gvals, a.gslice, a.ticket);
     trace_end(s);
     return cudaGetLastError();
@@ -589,7 +646,7 @@ cudaError_t own_product_launch(const OwnArgs& a, const int64_t* st, const int64_
     cudaMemsetAsync(a.ticket, 0, sizeof(int32_t), s);
     cudaMemsetAsync(a.cursor, 0, sizeof(unsigned long long), s);
     trace_begin("ninv_own_product", s);
-    own_product<<<a.grid, kOwnThreads, 0, s>>>(a.n, st, ct, r, v, rp, rc, rv, a.dr, a.dp, a.part, diag, bound,
+    own_product<<<a.grid, kOwnThreads, 2 * kProdSlots * (sizeof(int32_t) + sizeof(double)), s>>>(a.n, st, ct, r, v, rp, rc, rv, a.dr, a.dp, a.part, diag, bound,
                                                a.delta, nr, nv, stN, ctN, cap, a.cursor, a.gkeys, a.gvals, a.gslice,
                                                a.ticket);
     trace_end(s);
@@ -598,6 +655,16 @@ cudaError_t own_product_launch(const OwnArgs& a, const int64_t* st, const int64_
 
 int own_table_slots(int64_t entries) { return (int)table_mask(entries) + 1; }
 int own_smem_slots() { return kSmemSlots; }
+int own_horner_slots() { return kHornerSlots; }
+int own_prod_slots() { return kProdSlots; }
+
+cudaError_t own_configure() {
+    cudaError_t e = cudaFuncSetAttribute(own_horner, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kHornerSlots * (sizeof(int32_t) + sizeof(double))));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(own_product, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(2 * kProdSlots * (sizeof(int32_t) + sizeof(double))));
+}
 int own_grid_ctas(int num_sms) { return num_sms * 4; }
 
 }  // namespace sinv

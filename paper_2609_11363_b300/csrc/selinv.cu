@@ -556,7 +556,7 @@ __device__ bool process(const SelinvArgs& a, typename Form::G* Gw, int J, uint32
 }
 
 template <class Form, bool kScan>
-__global__ void __launch_bounds__(kWarps * 32) selinv_persistent(SelinvArgs a, typename Form::G* Gw) {
+__global__ void __launch_bounds__(kWarps * 32, kScan ? 3 : 2) selinv_persistent(SelinvArgs a, typename Form::G* Gw) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ CtaShared cs;
     WarpSmem* ws = reinterpret_cast<WarpSmem*>(smem_raw) + (threadIdx.x >> 5);
