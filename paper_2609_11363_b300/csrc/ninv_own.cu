@@ -35,7 +35,6 @@ constexpr int kOwnWarps = kOwnThreads / 32;
 constexpr int kSmemSlots = 2048;    // keys + FP64 values in shared memory: 24 KB (diagonal pass, Mix)
 constexpr int kHornerSlots = 4096;  // Horner step: 48 KB of dynamic shared memory
 constexpr int kProdSlots = 2048;    // product: two tables (Y and N's column), 48 KB in all
-constexpr int kShort = 16;          // a column (row) of W up to this length goes to one thread
 
 // per-CTA table: shared memory when it fits, else the given global slice
 struct Table {
@@ -205,25 +204,10 @@ __global__ void __launch_bounds__(kOwnThreads) own_horner(int64_t n, const int64
                 if (o) table_add_opt(t, (int32_t)j, 1.0, &s_keys, kHornerSlots / 2, &s_over);
                 else table_add(t, (int32_t)j, 1.0);
             }
-            // short columns k (the usual case with a loose tolerance): one thread each,
-            // so the loads of many columns are in flight together; long ones: a warp each
-            for (int64_t q = Lcp[j] + threadIdx.x; q < Lcp[j + 1]; q += blockDim.x) {
-                const int32_t k = Lri[q];
-                const int64_t len = ctIn[k];
-                if (len > kShort) continue;
-                const double e = -Lval[Lcsr[q]];
-                const int64_t p0 = stIn[k];
-                for (int64_t p = p0; p < p0 + len; ++p) {
-                    if (o) table_add_opt(t, rIn[p], e * vIn[p], &s_keys, kHornerSlots / 2, &s_over);
-                    else table_add(t, rIn[p], e * vIn[p]);
-                }
-            }
             for (int64_t q = Lcp[j] + wid; q < Lcp[j + 1]; q += kOwnWarps) {
                 const int32_t k = Lri[q];
-                const int64_t len = ctIn[k];
-                if (len <= kShort) continue;
                 const double e = -Lval[Lcsr[q]];
-                const int64_t p0 = stIn[k], p1 = p0 + len;
+                const int64_t p0 = stIn[k], p1 = p0 + ctIn[k];
                 for (int64_t p = p0 + lane; p < p1; p += 32) {
                     if (o) table_add_opt(t, rIn[p], e * vIn[p], &s_keys, kHornerSlots / 2, &s_over);
                     else table_add(t, rIn[p], e * vIn[p]);
@@ -372,21 +356,9 @@ __global__ void __launch_bounds__(kOwnThreads) own_product(int64_t n, const int6
         // N[i, j] += W[c, i] Y[c, j] over the rows c of Y[:, j] and the entries of row c of W
         for (int pass = 0; pass < 2; ++pass) {
             const bool o = opt && pass == 0;
-            // short rows of W (one thread each) and long ones (a warp each), as in the Horner step
-            for (uint32_t s = threadIdx.x; s <= ty.mask; s += blockDim.x) {
-                const int32_t c = ty.keys[s];
-                if (c < 0 || rp[c + 1] - rp[c] > kShort) continue;
-                const double y = ty.vals[s];
-                for (int64_t p = rp[c]; p < rp[c + 1]; ++p) {
-                    const int32_t i = rc[p];
-                    if (i < j) continue;
-                    if (o) table_add_opt(tn, i, rv[p] * y, &s_keys, kProdSlots / 2, &s_over);
-                    else table_add(tn, i, rv[p] * y);
-                }
-            }
             for (uint32_t s = wid; s <= ty.mask; s += kOwnWarps) {
                 const int32_t c = ty.keys[s];
-                if (c < 0 || rp[c + 1] - rp[c] <= kShort) continue;
+                if (c < 0) continue;
                 const double y = ty.vals[s];
                 for (int64_t p = rp[c] + lane; p < rp[c + 1]; p += 32) {
                     const int32_t i = rc[p];
