@@ -524,6 +524,14 @@ void sinv_destroy(sinv_handle h);
  * sets, and returns the status that wait reports (SINV_ERR_TIMEOUT expected). */
 sinv_status sinv_debug_wait_timeout(sinv_handle h, void *stream);
 
+/* Test support for the checked build (libsinv_checked.so, compiled with
+ * -DSINV_CHECKED): points one stored SelInv pair position past the end of S_lo, so
+ * that the next sinv_selinv meets an out-of-range index; the checked kernels skip
+ * that access and sinv_sync_status reports SINV_ERR_CUDA ("index out of range").
+ * The regular build returns SINV_ERR_UNSUPPORTED and changes nothing (its kernels
+ * do not check).  SINV_ERR_UNSUPPORTED also when the handle has no pair lists. */
+sinv_status sinv_debug_corrupt_plan(sinv_handle h);
+
 #ifdef __cplusplus
 }
 #endif

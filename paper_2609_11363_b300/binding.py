@@ -16,6 +16,16 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libsinv.so")
 _lib = None
 
+
+def use_checked_library():
+    """Load the checked build (libsinv_checked.so: out-of-range plan or map indices
+    are reported as SINV_ERR_CUDA 'index out of range' instead of being used) in
+    place of the regular one; call before anything loads the library."""
+    global _LIB_PATH
+    if _lib is not None:
+        raise RuntimeError("the library is already loaded")
+    _LIB_PATH = os.path.join(_HERE, "libsinv_checked.so")
+
 PREC = {"fp64": 0, "fp32": 1, "fp32x2": 2, "tf32": 3, "bf16": 4}
 STATUS = {
     0: "SINV_OK", 1: "SINV_ERR_INVALID_ARG", 2: "SINV_ERR_PATTERN", 3: "SINV_ERR_SINGULAR_PIVOT",
@@ -35,7 +45,7 @@ EXPORTS = [
     "sinv_mlp_sync_status", "sinv_timeline_enable", "sinv_timeline_read", "sinv_batch_run",
     "sinv_einv_set_solver", "sinv_ninv_own", "sinv_ninv_own_size", "sinv_ninv_own_copy",
     "sinv_selinv_scan_counts", "sinv_mix_own", "sinv_mix_own_size", "sinv_mix_own_copy",
-    "sinv_lowrank_correct_mix_own", "sinv_spai_analyse_mix_own", "sinv_spai_mix_own",
+    "sinv_lowrank_correct_mix_own", "sinv_spai_analyse_mix_own", "sinv_spai_mix_own", "sinv_debug_corrupt_plan",
 ]
 
 
@@ -118,6 +128,7 @@ def load_library():
     lib.sinv_timeline_enable.argtypes = [H, ctypes.c_int]
     lib.sinv_timeline_read.argtypes = [H, P, I64, P]
     lib.sinv_selinv_scan_counts.argtypes = [H, ctypes.POINTER(I64), ctypes.POINTER(I64), P]
+    lib.sinv_debug_corrupt_plan.argtypes = [H]
     lib.sinv_batch_run.argtypes = [H, ctypes.c_int32, P, P, ctypes.c_int, P, ctypes.c_int, P, P]
     lib.sinv_einv_set_solver.argtypes = [H, ctypes.c_int32]
     lib.sinv_ninv_own.argtypes = [H, P, P, ctypes.c_int, ctypes.c_double, P]
@@ -656,6 +667,10 @@ class Handle:
         self._check(self._lib.sinv_selinv_scan_counts(self._h, ctypes.byref(lk), ctypes.byref(pr),
                                                       _stream_ptr(stream)))
         return int(lk.value), int(pr.value)
+
+    def debug_corrupt_plan(self) -> int:
+        """Checked build only: plant an out-of-range SelInv pair position (status code)."""
+        return int(self._lib.sinv_debug_corrupt_plan(self._h))
 
     def debug_wait_timeout(self, stream=None) -> int:
         return int(self._lib.sinv_debug_wait_timeout(self._h, _stream_ptr(stream)))

@@ -1351,10 +1351,39 @@ sinv_status sinv_sync_status(sinv_handle h, void* stream) {
             set_err(h, "a pivot block of D is singular");
             return SINV_ERR_SINGULAR_PIVOT;
         }
+        if (st == ST_BOUNDS) {
+            set_err(h, "index out of range (checked build): a plan or map entry points outside its array");
+            return SINV_ERR_CUDA;
+        }
         set_err(h, "internal device error " + std::to_string(st));
         return SINV_ERR_CUDA;
     }
     return SINV_OK;
+}
+
+sinv_status sinv_debug_corrupt_plan(sinv_handle h) {
+    if (!h) return SINV_ERR_INVALID_ARG;
+#ifndef SINV_CHECKED
+    set_err(h, "sinv_debug_corrupt_plan exists in the checked build only");
+    return SINV_ERR_UNSUPPORTED;
+#else
+    if (!on_device(h)) return SINV_ERR_INVALID_ARG;
+    if (h->P.hit_pairs == 0 || h->P.nnzS > INT32_MAX - 1024) {
+        set_err(h, "no pair lists to corrupt");
+        return SINV_ERR_UNSUPPORTED;
+    }
+    cudaError_t e = cudaSetDevice(h->device);
+    // the first pair of the first supernode that has pairs points past the end of S_lo
+    int64_t at = -1;
+    for (const SnInfo& I : h->P.sn)
+        if (I.hit_cnt > 0) {
+            at = I.hit_off;
+            break;
+        }
+    const int32_t bad = (int32_t)(h->P.nnzS + 1000);
+    if (e == cudaSuccess && at >= 0) e = cudaMemcpy(h->dhit_pos + at, &bad, sizeof(bad), cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? SINV_OK : cuda_fail(h, e, "corrupt plan");
+#endif
 }
 
 sinv_status sinv_debug_wait_timeout(sinv_handle h, void* stream) {

@@ -7,7 +7,7 @@
 namespace sinv {
 
 // must match sinv_status in include/sinv.h
-enum : int32_t { ST_OK = 0, ST_SINGULAR = 3, ST_TIMEOUT = 6, ST_UNSUPPORTED = 7, ST_INTERNAL = 100 };
+enum : int32_t { ST_OK = 0, ST_SINGULAR = 3, ST_TIMEOUT = 6, ST_UNSUPPORTED = 7, ST_INTERNAL = 100, ST_BOUNDS = 101 };
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
     uint32_t v;
@@ -29,6 +29,19 @@ __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
 
 // Record the first error of a call (later errors are dropped).
 __device__ __forceinline__ void set_status(int32_t* status, int32_t code) { atomicCAS(status, 0, code); }
+
+// Bounds checks of the checked build (-DSINV_CHECKED): an index read from the plan
+// or the maps that falls outside its array records ST_BOUNDS in the status word
+// and the access is skipped (nothing traps).  The regular build compiles them out.
+#ifdef SINV_CHECKED
+__device__ __forceinline__ bool in_range(int32_t* status, int64_t idx, int64_t lo, int64_t hi) {
+    if (idx >= lo && idx < hi) return true;
+    set_status(status, ST_BOUNDS);
+    return false;
+}
+#else
+__device__ __forceinline__ bool in_range(int32_t*, int64_t, int64_t, int64_t) { return true; }
+#endif
 
 // Spin until *flag == want, with a poll limit.  Returns false (and records
 // ST_TIMEOUT) when the limit ran out, or when another warp already recorded an

@@ -324,7 +324,9 @@ __global__ void __launch_bounds__(kThreads) hm_step(NinvArgs a, NinvMaps x, Colu
                     p = mp[e];
                     v = wk[e];
                 },
-                [&](uint16_t p, const T& v) { atomicAdd(acc + p, ekj * v); });
+                [&](uint16_t p, const T& v) {
+                    if (in_range(a.status, p, 0, nt)) atomicAdd(acc + p, ekj * v);
+                });
         }
         __syncthreads();
         for (int32_t e = threadIdx.x; e < nt; e += kThreads) {
@@ -405,7 +407,7 @@ __global__ void __launch_bounds__(kThreads) hm_step_fx(NinvArgs a, NinvMaps x, C
                 },
                 [&](uint16_t p, const double& v) {
                     const long long q = __double_as_longlong(fma(ekj, v, kRoundMagic)) - magic;
-                    atomicAdd(acc + p, (unsigned long long)q);
+                    if (in_range(a.status, p, 0, nt)) atomicAdd(acc + p, (unsigned long long)q);
                 });
         }
         __syncthreads();
@@ -461,7 +463,8 @@ __global__ void __launch_bounds__(kThreads) pm_product(NinvArgs a, NinvMaps x, C
             const int32_t r = rf & kRowMask;
             const double w = (double)W[base + e];
             atomicAdd(y + e, T(dr[r] * w));
-            if (rf & kTwoFlag) atomicAdd(y + x.ypart[base + e], T(dp[r] * w));
+            if ((rf & kTwoFlag) && in_range(a.status, x.ypart[base + e], 0, ny))
+                atomicAdd(y + x.ypart[base + e], T(dp[r] * w));
         }
         __syncthreads();
         const bool two_first = a.pstart[j] != 0 && j + 1 < a.n && a.pstart[j + 1] == 0;
@@ -488,12 +491,14 @@ __global__ void __launch_bounds__(kThreads) pm_product(NinvArgs a, NinvMaps x, C
                 p = mp[e];
                 v = wi[e];
             };
-            auto apply = [&](uint16_t p, const T& v) { s = fma_m<T>(v, y[p], s); };
+            auto apply = [&](uint16_t p, const T& v) {
+                if (in_range(a.status, p, 0, ny)) s = fma_m<T>(v, y[p], s);
+            };
             if constexpr (std::is_same<T, float>::value) stream_column_pred<T>(ni, lane, load, apply);
             else stream_column<T>(ni, lane, load, apply);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) N[spos] = (double)s;
+            if (lane == 0 && in_range(a.status, spos, 0, a.nnzS)) N[spos] = (double)s;
         }
         __syncthreads();
     }

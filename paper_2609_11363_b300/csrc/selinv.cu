@@ -127,12 +127,14 @@ __device__ __forceinline__ void load_pairs(const uint32_t* __restrict__ hik, con
 template <class Form>
 __device__ __forceinline__ void accumulate_pairs(PairRange& pr, const uint32_t* __restrict__ hik,
                                                  const int32_t* __restrict__ hpos, const typename Form::G* Gw,
-                                                 const typename Form::R* lh, typename Form::R* x, int w, int lane) {
+                                                 const typename Form::R* lh, typename Form::R* x, int w, int lane,
+                                                 int c, int64_t nnzS, int32_t* status) {
     using R = typename Form::R;
     for (int64_t base = pr.e0; base < pr.e1; base += 32 * kBatch) {
         R g[kBatch];
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) g[u] = pr.pos[u] >= 0 ? Form::ld(Gw + pr.pos[u]) : R(0);
+        for (int u = 0; u < kBatch; ++u)
+            g[u] = (pr.pos[u] >= 0 && in_range(status, pr.pos[u], 0, nnzS)) ? Form::ld(Gw + pr.pos[u]) : R(0);
         uint32_t ik_n[kBatch];
         int32_t pos_n[kBatch];
         load_pairs(hik, hpos, base + 32 * kBatch, pr.e1, lane, ik_n, pos_n);
@@ -141,6 +143,7 @@ __device__ __forceinline__ void accumulate_pairs(PairRange& pr, const uint32_t* 
             if (pr.pos[u] < 0) continue;
             const int i = (int)(pr.ik[u] >> 16);
             const int k = (int)(pr.ik[u] & 0xffff);
+            if (!in_range(status, i, 0, c) || !in_range(status, k, 0, c)) continue;
             if (w == 1) {
                 atomicAdd(x + k, -g[u] * lh[i]);
             } else {
@@ -247,6 +250,11 @@ __device__ __forceinline__ void scan_rows(const SelinvArgs& a, const typename Fo
 #pragma unroll
             for (int u = 0; u < kBatch; ++u)
                 kk[t][u] = col[t][u] >= c0 ? c_find(keys, vals, mask, col[t][u]) : -1;
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u)
+                if (kk[t][u] >= c && !in_range(a.status, kk[t][u], 0, c)) kk[t][u] = -1;
 #pragma unroll
         for (int t = 0; t < 2; ++t)
 #pragma unroll
@@ -492,7 +500,7 @@ __device__ bool process(const SelinvArgs& a, typename Form::G* Gw, int J, uint32
     if (kScan)
         scan_rows<Form>(a, Gw, Crow, c, r0, r1, Gr::warp(), Gr::nwarps(), tkeys, tvals, tmask, lh, x, w, lane);
     else
-        accumulate_pairs<Form>(pr, hik, hpos, Gw, lh, x, w, lane);
+        accumulate_pairs<Form>(pr, hik, hpos, Gw, lh, x, w, lane, c, a.nnzS, a.status);
     Gr::sync();
     if (tid == 0) tl_mark(a.tl, J, 1);
     if (kCta && nparts > 1) {
@@ -513,7 +521,7 @@ __device__ bool process(const SelinvArgs& a, typename Form::G* Gw, int J, uint32
     }
     for (int e = tid; e < cw; e += gsz) {
         const int p = xpos[e];
-        if (p >= 0) Form::st(Gw + p, x[e]);
+        if (p >= 0 && in_range(a.status, p, 0, a.nnzS)) Form::st(Gw + p, x[e]);
     }
     // G_JJ[r][b] = (M^T T)[r][b] - sum_i Lh[i][r] X[i][b]   (r >= b): FP64 accumulation
     const int npair = w * (w + 1) / 2;
@@ -543,7 +551,7 @@ __device__ bool process(const SelinvArgs& a, typename Form::G* Gw, int J, uint32
         double m = 0.0;
         for (int p = 0; p < w; ++p) m += jj[p * w + r] * tt[p * w + b];
         const int sp = a.JJs[I.ww_off + r * w + b];
-        if (sp >= 0) Form::st(Gw + sp, Form::from_d(m - s));
+        if (sp >= 0 && in_range(a.status, sp, 0, a.nnzS)) Form::st(Gw + sp, Form::from_d(m - s));
     }
     // the barrier orders every thread's writes before thread 0's release store,
     // which publishes them (release is cumulative over the barrier)

@@ -39,6 +39,18 @@ def test_library_exports_every_declared_symbol(lib):
     assert sorted(EXPORTS) == names
 
 
+def test_checked_library_exports_every_declared_symbol(lib):
+    """The bounds-checked build (-DSINV_CHECKED) has the same ABI."""
+    import ctypes
+    from paper_2609_11363_b300.binding import EXPORTS
+    from paper_2609_11363_b300.build import build_lib
+    path = build_lib(checked=True)
+    assert path.endswith("libsinv_checked.so")
+    clib = ctypes.CDLL(path)
+    for nm in EXPORTS:
+        assert hasattr(clib, nm), nm
+
+
 CASES = {
     "lap2d": lambda: lap2d_32().factors,
     "lap2d_exact": lambda: lap2d_32(tau=0.0).factors,
