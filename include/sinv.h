@@ -360,10 +360,13 @@ sinv_status sinv_einv_analyse(sinv_handle h, int64_t nnzA, const int64_t *A_rowp
  *     definite;
  *   1: MINRES (Paige & Saunders) with the SPD preconditioner M = L |D| L^T, |D|
  *     the absolute value of every 1x1 / 2x2 pivot block -- for indefinite A.
- * Both apply M^{-1} with two persistent triangular solves (one launch each
- * over all dependency levels).  cg_tol of sinv_einv_lanczos is then the
- * relative residual in the norm of M^{-1} that MINRES estimates, and cg_maxit
- * its iteration limit.  Errors: SINV_ERR_INVALID_ARG (unknown solver). */
+ * Both apply M^{-1} with two triangular solves over the dependency levels:
+ * one CTA walking the levels with a barrier between them when they hold fewer
+ * than 64 rows on average, else a persistent grid with per-row flags (one
+ * launch each); adding 2 to `solver` forces the persistent grid.  cg_tol of
+ * sinv_einv_lanczos is then the relative residual in the norm of M^{-1} that
+ * MINRES estimates, and cg_maxit its iteration limit.  Errors:
+ * SINV_ERR_INVALID_ARG (unknown solver). */
 sinv_status sinv_einv_set_solver(sinv_handle h, int32_t solver);
 sinv_status sinv_einv_lanczos(sinv_handle h, const double *A_val, const double *L_val, const double *D_val,
                               const double *X_S, const double *q0, int steps, double cg_tol, int cg_maxit, int k,

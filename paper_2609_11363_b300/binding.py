@@ -538,9 +538,10 @@ class Handle:
         self._einv_nnzA = int(A.nnz)
         return sp.csr_matrix((A.data, col, rp), shape=A.shape)
 
-    def einv_set_solver(self, solver):
-        """Inner solver of einv_lanczos: "cg" (A SPD) or "minres" (L |D| L^T, indefinite A)."""
-        self._check(self._lib.sinv_einv_set_solver(self._h, {"cg": 0, "minres": 1}[solver]))
+    def einv_set_solver(self, solver, grid_solve=False):
+        """Inner solver of einv_lanczos: "cg" (A SPD) or "minres" (L |D| L^T, indefinite A);
+        grid_solve forces the persistent multi-CTA triangular solves."""
+        self._check(self._lib.sinv_einv_set_solver(self._h, {"cg": 0, "minres": 1}[solver] | (2 if grid_solve else 0)))
 
     def einv_lanczos(self, A_val, L_val, D_val, X, q0, k, steps, cg_tol=1e-12, cg_maxit=1000, stream=None):
         """k dominant eigenpairs of E_inv = A^{-1} - A^inv (A^inv = X on S): returns

@@ -196,11 +196,12 @@ struct sinv_handle_s {
     bool einv_ready = false;     // ... and it is on the device
     int64_t *deArp = nullptr, *deLrp = nullptr, *defcp = nullptr;
     int32_t *deAcol = nullptr, *deLcol = nullptr, *defri = nullptr, *defpos = nullptr, *defwd = nullptr,
-            *debwd = nullptr;
+            *debwd = nullptr, *defwdp = nullptr, *debwdp = nullptr;
     void* dework = nullptr;
     // persistent triangular solves: per-row flags of each solve, epoch and tickets (zeroed once)
     uint32_t* detrsv = nullptr;
     int32_t einv_solver = 0;  // 0: CG with L D L^T (A SPD), 1: MINRES with L |D| L^T
+    bool einv_grid_solve = false;  // the persistent grid solves even where one CTA would walk the levels
     size_t ework_bytes = 0;
     std::string last_error;
 };
@@ -242,11 +243,11 @@ void spai_free(sinv_handle h) {
 
 void einv_free(sinv_handle h) {
     void* ptrs[] = {h->deArp, h->deLrp, h->defcp, h->deAcol, h->deLcol, h->defri, h->defpos, h->defwd, h->debwd,
-                    h->dework, h->detrsv};
+                    h->defwdp, h->debwdp, h->dework, h->detrsv};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     h->deArp = h->deLrp = h->defcp = nullptr;
-    h->deAcol = h->deLcol = h->defri = h->defpos = h->defwd = h->debwd = nullptr;
+    h->deAcol = h->deLcol = h->defri = h->defpos = h->defwd = h->debwd = h->defwdp = h->debwdp = nullptr;
     h->dework = nullptr;
     h->detrsv = nullptr;
     h->ework_bytes = 0;
@@ -1074,6 +1075,8 @@ sinv_status sinv_einv_analyse(sinv_handle h, int64_t nnzA, const int64_t* A_rowp
     UPE(defpos, E.fpos);
     UPE(defwd, E.fwd_rows);
     UPE(debwd, E.bwd_cols);
+    UPE(defwdp, E.fwd_ptr);
+    UPE(debwdp, E.bwd_ptr);
 #undef UPE
     // flags of the two solves (n each), then the epoch and two tickets
     const size_t nflag = 2 * (size_t)h->P.n + 64;
@@ -1087,8 +1090,9 @@ sinv_status sinv_einv_analyse(sinv_handle h, int64_t nnzA, const int64_t* A_rowp
 }
 
 sinv_status sinv_einv_set_solver(sinv_handle h, int32_t solver) {
-    if (!h || (solver != 0 && solver != 1)) return SINV_ERR_INVALID_ARG;
-    h->einv_solver = solver;
+    if (!h || (solver & ~3) != 0) return SINV_ERR_INVALID_ARG;
+    h->einv_solver = solver & 1;
+    h->einv_grid_solve = (solver & 2) != 0;
     return SINV_OK;
 }
 
@@ -1164,6 +1168,14 @@ sinv_status sinv_einv_lanczos(sinv_handle h, const double* A_val, const double* 
     a.part = part;
     a.fwd_rows = h->defwd;
     a.bwd_cols = h->debwd;
+    a.fwd_ptr = h->defwdp;
+    a.bwd_ptr = h->debwdp;
+    a.nlev_fwd = h->E.fwd_ptr.empty() ? 0 : (int32_t)h->E.fwd_ptr.size() - 1;
+    a.nlev_bwd = h->E.bwd_ptr.empty() ? 0 : (int32_t)h->E.bwd_ptr.size() - 1;
+    // levels of fewer than 64 rows on average: one CTA walks them (a barrier per level
+    // costs less than the hand-off between SMs); wider levels: the persistent grid
+    a.cta_solve = (!h->einv_grid_solve && a.nlev_fwd > 0 && a.nlev_bwd > 0 &&
+                   n < (int64_t)64 * std::min(a.nlev_fwd, a.nlev_bwd)) ? 1 : 0;
     a.fwd_flags = h->detrsv;
     a.bwd_flags = h->detrsv + n;
     a.tepoch = h->detrsv + 2 * n;

@@ -284,6 +284,101 @@ __global__ void trsv_bwd_persistent(int64_t n, const int32_t* __restrict__ cols,
     }
 }
 
+// ---- single-CTA level-synchronous triangular solves ------------------------------------
+// For factors whose levels hold few rows (the covariance example: about 12 rows per
+// level over 3,289 levels), the hand-off between SMs costs more than the rows: one
+// CTA walks the levels with a barrier between them.  A warp takes a row of the level;
+// the row's bounds and its entries of L (which do not depend on the solution) for the
+// next level are loaded before the barrier, so after it only the solution values are
+// read.  Rows beyond 32 entries are read in a loop.
+constexpr int kCtaSolve = 1024;
+
+struct RowPre {
+    int i;         // row (column), -1 when the warp has none in the level
+    int64_t q0, q1;
+    int c;         // this lane's first entry: column (row) and value, c = -1 when none
+    double v;
+};
+
+__device__ __forceinline__ RowPre row_pre_fwd(int t, int t1, const int32_t* rows, const int64_t* Lrp,
+                                               const int32_t* Lcol, const double* Lval, int lane) {
+    RowPre p;
+    p.i = t < t1 ? rows[t] : -1;
+    p.q0 = p.i >= 0 ? Lrp[p.i] : 0;
+    p.q1 = p.i >= 0 ? Lrp[p.i + 1] : 0;
+    p.c = p.q0 + lane < p.q1 ? Lcol[p.q0 + lane] : -1;
+    p.v = p.c >= 0 ? Lval[p.q0 + lane] : 0.0;
+    return p;
+}
+
+__device__ __forceinline__ RowPre row_pre_bwd(int t, int t1, const int32_t* cols, const int64_t* Lcp,
+                                               const int32_t* Lri, const int32_t* Lcsr, const double* Lval,
+                                               int lane) {
+    RowPre p;
+    p.i = t < t1 ? cols[t] : -1;
+    p.q0 = p.i >= 0 ? Lcp[p.i] : 0;
+    p.q1 = p.i >= 0 ? Lcp[p.i + 1] : 0;
+    p.c = p.q0 + lane < p.q1 ? Lri[p.q0 + lane] : -1;
+    p.v = p.c >= 0 ? Lval[Lcsr[p.q0 + lane]] : 0.0;
+    return p;
+}
+
+// y = L^{-1} b, levels [0, nlev) of the rows in level order (ptr[l] .. ptr[l+1])
+__global__ void __launch_bounds__(kCtaSolve) trsv_fwd_cta(int nlev, const int32_t* __restrict__ ptr,
+                                                          const int32_t* __restrict__ rows,
+                                                          const int64_t* __restrict__ Lrp,
+                                                          const int32_t* __restrict__ Lcol,
+                                                          const double* __restrict__ Lval,
+                                                          const double* __restrict__ b, double* y) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = kCtaSolve / 32;
+    RowPre pre = row_pre_fwd(ptr[0] + wid, ptr[1], rows, Lrp, Lcol, Lval, lane);
+    for (int l = 0; l < nlev; ++l) {
+        const int t0 = ptr[l], t1 = ptr[l + 1];
+        for (int t = t0 + wid; t < t1; t += nw) {
+            const RowPre r = t == t0 + wid ? pre : row_pre_fwd(t, t1, rows, Lrp, Lcol, Lval, lane);
+            double s = r.c >= 0 ? r.v * y[r.c] : 0.0;
+            for (int64_t q = r.q0 + 32 + lane; q < r.q1; q += 32) s = fma(Lval[q], y[Lcol[q]], s);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) y[r.i] = b[r.i] - s;
+        }
+        if (l + 1 < nlev) pre = row_pre_fwd(ptr[l + 1] + wid, ptr[l + 2], rows, Lrp, Lcol, Lval, lane);
+        __syncthreads();  // the level's values are visible to the whole CTA
+    }
+}
+
+// x = L^{-T} w with w = D^{-1} y on the fly, L by columns, levels of the solve with L^T
+__global__ void __launch_bounds__(kCtaSolve) trsv_bwd_cta(int nlev, const int32_t* __restrict__ ptr,
+                                                          const int32_t* __restrict__ cols,
+                                                          const int64_t* __restrict__ Lcp,
+                                                          const int32_t* __restrict__ Lri,
+                                                          const int32_t* __restrict__ Lcsr,
+                                                          const double* __restrict__ Lval,
+                                                          const double* __restrict__ dr, const double* __restrict__ dp,
+                                                          const int32_t* __restrict__ part,
+                                                          const double* __restrict__ y, double* x) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = kCtaSolve / 32;
+    RowPre pre = row_pre_bwd(ptr[0] + wid, ptr[1], cols, Lcp, Lri, Lcsr, Lval, lane);
+    for (int l = 0; l < nlev; ++l) {
+        const int t0 = ptr[l], t1 = ptr[l + 1];
+        for (int t = t0 + wid; t < t1; t += nw) {
+            const RowPre r = t == t0 + wid ? pre : row_pre_bwd(t, t1, cols, Lcp, Lri, Lcsr, Lval, lane);
+            double s = r.c >= 0 ? r.v * x[r.c] : 0.0;
+            for (int64_t q = r.q0 + 32 + lane; q < r.q1; q += 32) s = fma(Lval[Lcsr[q]], x[Lri[q]], s);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) {
+                const int j = r.i;
+                const int32_t p = part[j];
+                const double wj = p >= 0 ? fma(dr[j], y[j], dp[j] * y[p]) : dr[j] * y[j];
+                x[j] = wj - s;
+            }
+        }
+        if (l + 1 < nlev) pre = row_pre_bwd(ptr[l + 1] + wid, ptr[l + 2], cols, Lcp, Lri, Lcsr, Lval, lane);
+        __syncthreads();
+    }
+}
+
 // |D|^{-1} by rows, from D itself: for a 1x1 pivot 1/|d|; for a 2x2 block [a b; b d]
 // with eigenpairs (l_k, u_k) (the closed form of a symmetric 2x2), sum_k u_k u_k^T /
 // |l_k| -- the inverse of the block's absolute value, so that L |D| L^T is an SPD
@@ -349,6 +444,12 @@ cudaError_t einv_symv_X(const EinvArgs& a, const double* x, double* y, cudaStrea
 }
 
 cudaError_t einv_precond_persistent(const EinvArgs& a, const double* r, double* y, double* z, cudaStream_t st) {
+    if (a.cta_solve) {
+        trsv_fwd_cta<<<1, kCtaSolve, 0, st>>>(a.nlev_fwd, a.fwd_ptr, a.fwd_rows, a.Lrp, a.Lcol, a.Lval, r, y);
+        trsv_bwd_cta<<<1, kCtaSolve, 0, st>>>(a.nlev_bwd, a.bwd_ptr, a.bwd_cols, a.Lcp, a.Lri, a.Lcsr, a.Lval, a.dr,
+                                              a.dp, a.part, y, z);
+        return cudaGetLastError();
+    }
     trsv_prepare<<<1, 1, 0, st>>>(a.tepoch, a.tickets);
     const int grid = a.num_sms * 8;  // 8 warps of 32 per CTA, 8 CTAs per SM
     trsv_fwd_persistent<<<grid, 256, 0, st>>>(a.n, a.fwd_rows, a.Lrp, a.Lcol, a.Lval, r, y, a.fwd_flags, a.tepoch,

@@ -307,6 +307,10 @@ struct EinvArgs {
     const int32_t* part;
     const int32_t* fwd_rows;  // rows of L y = b in level order (device)
     const int32_t* bwd_cols;  // columns of L^T x = w in level order
+    const int32_t* fwd_ptr;   // level starts in fwd_rows / bwd_cols (nlev + 1 each)
+    const int32_t* bwd_ptr;
+    int32_t nlev_fwd, nlev_bwd;
+    int32_t cta_solve;        // 1: one CTA walks the levels (few rows per level), 0: persistent grid
     // persistent solves: per-row flags of each solve, their epoch, two tickets
     uint32_t* fwd_flags;
     uint32_t* bwd_flags;

@@ -49,12 +49,13 @@ def _case(name):
     return _ldlt(f), f
 
 
-def _run(A, f, k, steps, seed=0):
+def _run(A, f, k, steps, seed=0, grid_solve=False):
     S = oracle.symbolic_S(f.n, f.L_rowptr, f.L_col, f.pivot_start)
     G = oracle.selinv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, S)
     q0 = np.random.default_rng(seed).standard_normal(f.n)
     h = _handle(f)
     Ac = h.einv_analyse(A)
+    h.einv_set_solver("cg", grid_solve=grid_solve)
     lam, V, info = h.einv_lanczos(torch.as_tensor(Ac.data, device="cuda"), torch.as_tensor(f.L_val, device="cuda"),
                                   torch.as_tensor(f.D_packed, device="cuda"), torch.as_tensor(G, device="cuda"),
                                   torch.as_tensor(q0, device="cuda"), k, steps, cg_tol=1e-13, cg_maxit=3000)
@@ -63,11 +64,14 @@ def _run(A, f, k, steps, seed=0):
     return lam, V.cpu().numpy(), info, S, G, Xs, q0
 
 
+@pytest.mark.parametrize("grid_solve", [False, True], ids=["cta_solve", "grid_solve"])
 @pytest.mark.parametrize("name", ["lap2d", "covariance_24", "exact_2x2"])
-def test_lanczos_parity(name):
+def test_lanczos_parity(name, grid_solve):
+    """Both triangular solves: one CTA walking the levels (the choice for these
+    factors, whose levels hold few rows) and the persistent grid."""
     A, f = _case(name)
     k, steps = 4, 40
-    lam, V, info, S, G, Xs, q0 = _run(A, f, k, steps)
+    lam, V, info, S, G, Xs, q0 = _run(A, f, k, steps, grid_solve=grid_solve)
     lo, Vo = oracle.lanczos_einv(A, Xs, k, steps=steps, q0=q0)
     assert info["steps"] == steps and info["cg_unconverged"] == 0
     scale = np.abs(lo).max()
@@ -139,13 +143,13 @@ def _indefinite_exact():
     return _ldlt(g), g
 
 
-def _run_solver(A, f, k, steps, solver, seed=0):
+def _run_solver(A, f, k, steps, solver, seed=0, grid_solve=False):
     S = oracle.symbolic_S(f.n, f.L_rowptr, f.L_col, f.pivot_start)
     G = oracle.selinv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, S)
     q0 = np.random.default_rng(seed).standard_normal(f.n)
     h = _handle(f)
     Ac = h.einv_analyse(A)
-    h.einv_set_solver(solver)
+    h.einv_set_solver(solver, grid_solve=grid_solve)
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
     lam, V, info = h.einv_lanczos(dev(Ac.data), dev(f.L_val), dev(f.D_packed), dev(G), dev(q0), k, steps,
                                   cg_tol=1e-13, cg_maxit=3000)
@@ -166,8 +170,9 @@ def test_minres_exact_indefinite_factors_converge_in_two_steps():
     np.testing.assert_allclose(lam, lo, rtol=0, atol=1e-9 * np.abs(lo).max())
 
 
+@pytest.mark.parametrize("grid_solve", [False, True], ids=["cta_solve", "grid_solve"])
 @pytest.mark.parametrize("name", ["diff3d_shifted", "lap2d"])
-def test_minres_lanczos_parity(name):
+def test_minres_lanczos_parity(name, grid_solve):
     """Indefinite A (3D diffusion shifted into its first spectral gap, planted 2x2
     pivots) and an SPD case, MINRES inner solves against the oracle's exact ones."""
     from workloads.configs import diff3d
@@ -178,7 +183,7 @@ def test_minres_lanczos_parity(name):
         w = diff3d(10, m=3)
         A, f = w.A, plant_2x2(w.factors, 0.05, 13)
     k, steps = 3, 30
-    lam, V, info, Xs, q0 = _run_solver(A, f, k, steps, "minres")
+    lam, V, info, Xs, q0 = _run_solver(A, f, k, steps, "minres", grid_solve=grid_solve)
     lo, Vo = oracle.lanczos_einv(A, Xs, k, steps=steps, q0=q0)
     assert info["steps"] == steps and info["cg_unconverged"] == 0
     np.testing.assert_allclose(lam, lo, rtol=0, atol=1e-8 * np.abs(lo).max())
