@@ -79,6 +79,21 @@ def critical_path(stamps, deps, levels=None):
     return out
 
 
+def totals(stamps):
+    """Sums over all supernodes (microseconds): waiting for dependencies after the
+    first work item started (ready - start), contraction (done - ready) and finish
+    (published - done); with the span, what the CTAs spent on each.  For a supernode
+    split over several CTAs the stamps cover all its parts."""
+    st = np.asarray(stamps, dtype=np.float64)
+    ok = (st[:, 3] > 0) & (st[:, 0] < 1.8e19)
+    st = st[ok]
+    t0, t1 = float(st[:, 0].min()), float(st[:, 3].max())
+    return {"supernodes": int(st.shape[0]), "span_us": (t1 - t0) / 1e3,
+            "wait_us": float((st[:, 1] - st[:, 0]).sum()) / 1e3,
+            "contraction_us": float((st[:, 2] - st[:, 1]).sum()) / 1e3,
+            "finish_us": float((st[:, 3] - st[:, 2]).sum()) / 1e3}
+
+
 def _workload(args):
     from workloads.configs import band, diff3d, elastic3d, plant_2x2
     if args.workload == "band":
@@ -97,6 +112,8 @@ def main(argv=None):
     p.add_argument("--tau", type=float, default=1e-6)
     p.add_argument("--cap", type=int, default=0)
     p.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "tf32", "bf16"])
+    p.add_argument("--totals-only", action="store_true",
+                   help="only the sums over all supernodes (no dependency walk: fast at any size)")
     p.add_argument("--factor-cache", default=None, help="elastic: directory of the on-disk factor cache")
     p.add_argument("--pair-bytes", type=int, default=0,
                    help="memory the SelInv pair lists may take (0: default, < 0: the scan form)")
@@ -123,9 +140,13 @@ def main(argv=None):
     h.sync_status()
     stamps = h.timeline_read()
     h.timeline(False)
-    sn_start, sn_level = h.supernodes()
-    deps = dependencies(f.n, f.L_rowptr, f.L_col, sn_start)
-    out = critical_path(stamps, deps, sn_level)
+    if args.totals_only:
+        out = {"totals": totals(stamps)}
+    else:
+        sn_start, sn_level = h.supernodes()
+        deps = dependencies(f.n, f.L_rowptr, f.L_col, sn_start)
+        out = critical_path(stamps, deps, sn_level)
+        out["totals"] = totals(stamps)
     out.update(workload=args.workload, prec=args.prec, n=f.n, cap=args.cap, ms_without_timeline=ms_plain,
                stats={k: v for k, v in h.stats().items()
                       if k in ("n_supernodes", "n_levels", "tc_levels", "selinv_scan", "max_c")})

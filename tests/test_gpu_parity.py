@@ -155,7 +155,7 @@ def test_selinv_scan_form_large_C():
     f = band(4096, 1100).factors
     S = oracle.symbolic_S(f.n, f.L_rowptr, f.L_col, f.pivot_start)
     G = oracle.selinv(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, S)
-    for cap in (1, 16):
+    for cap in (1, 4, 16):   # C x w within the shared regions (cap 1, 4) and beyond them (16)
         h = _handle(f, supernode_cap=cap, selinv_pair_bytes=-1)
         assert h.stats()["max_c"] > 1024
         out = h.selinv(_dev(f.L_val), _dev(f.D_packed), "fp64").cpu().numpy()

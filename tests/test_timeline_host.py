@@ -35,3 +35,14 @@ def test_critical_path_on_a_hand_timeline():
     assert np.isclose(out["handoff_us"], (0 + 500 + 1000) / 1e3)
     assert np.isclose(out["contraction_us"], (3000 + 1500 + 3000) / 1e3)
     assert np.isclose(out["finish_us"], (1000 + 1000 + 1000) / 1e3)
+
+
+def test_totals_sum_the_phases_of_every_supernode():
+    import numpy as np
+    from paper_2609_11363_b300.timeline import totals
+    st = np.array([[0, 10, 30, 35], [5, 40, 50, 60], [2**64 - 1, 0, 0, 0]], dtype=np.uint64)  # the last never ran
+    t = totals(st)
+    assert t["supernodes"] == 2
+    assert abs(t["span_us"] - 0.060) < 1e-12
+    assert abs(t["wait_us"] - 0.045) < 1e-12 and abs(t["contraction_us"] - 0.030) < 1e-12
+    assert abs(t["finish_us"] - 0.015) < 1e-12
