@@ -216,7 +216,10 @@ sinv_status sinv_ninv_stack(sinv_handle h, const double *L_val, const double *D_
  * the result is a sparse approximate inverse whose pattern depends only on the
  * sizes of the entries (not on S).  W is built by the m Horner steps of
  * sinv_ninv_drop (off-diagonal |w| < delta dropped after every step), each
- * step compacted so the next one only streams the survivors; the product is
+ * step's survivors appended per column (no structural pattern of the series is
+ * built: a step whose output passes its first size guess is rerun into a
+ * buffer of the size it counted), so the next step only streams the
+ * survivors; the product is
  * formed by columns through the rows of W and keeps the diagonal and the
  * entries with |N_ij| >= delta sqrt(|N_ii N_jj|) (the reading of "delta
  * controls the sparsity of the product").  The result is the lower triangle
@@ -226,8 +229,9 @@ sinv_status sinv_ninv_stack(sinv_handle h, const double *L_val, const double *D_
  * it into caller-owned device buffers (colptr n+1, rows and values nnz).
  * Synchronous on `stream` (sizes are read back after every step).
  * delta = 0 keeps every structural entry (the product's pattern then grows
- * like (L^{-1})^T L^{-1}).  Errors: SINV_ERR_INVALID_ARG (m < 0, delta < 0),
- * SINV_ERR_UNSUPPORTED (m > 30), SINV_ERR_OOM (the product's bound too large). */
+ * like (L^{-1})^T L^{-1}).  Errors: SINV_ERR_INVALID_ARG (m < 0, delta < 0,
+ * NaN), SINV_ERR_UNSUPPORTED (m > 30), SINV_ERR_OOM (device memory for the
+ * series, its hash tables or the product), SINV_ERR_CUDA. */
 sinv_status sinv_ninv_own(sinv_handle h, const double *L_val, const double *D_val, int m, double delta,
                           void *stream);
 sinv_status sinv_ninv_own_size(sinv_handle h, int64_t *nnz_N_lo, int64_t *nnz_W_steps, int32_t max_steps);
