@@ -404,7 +404,7 @@ sinv_status sinv_lowrank_correct_noalloc(int64_t n, const int64_t *S_rowptr, con
  * of S to a correction: N^_ij = N_ij + s_ij f(x_ij), s_ij = sqrt|N_ii N_jj|.  It is
  * trained on pairs the method itself produces (target (SelInv_ij - N_ij) / s_ij),
  * with BF16 weights and features, FP32 sums and Adam, by the library's own
- * forward, backward and optimiser kernels.  SelInv stays the judge: callers keep
+ * forward, backward and optimiser kernels.  SelInv stays the reference: callers keep
  * the correction only where it lowers the error on held-out matrices.
  * Parameter vector (FP32, sinv_mlp_param_count() entries): W1[16x64], b1[64],
  * W2[64x64], b2[64], W3[64], b3. */

@@ -130,8 +130,8 @@ def _csc_L(n, L_rowptr, L_col, L_val):
 
 
 def selinv_levels(n, L_rowptr, L_col, L_val, pivot_start, d_diag, d_off, S=None):
-    """``selinv`` scheduled by level sets over every host thread (the survey's
-    CPU baseline variant (ii)).  Each pivot block does the same arithmetic as
+    """``selinv`` scheduled by level sets over every host thread (the all-cores
+    CPU baseline).  Each pivot block does the same arithmetic as
     in ``selinv``, so the result is identical to it.  Returns (G, levels)."""
     lib = _load()
     if S is None:
@@ -205,8 +205,8 @@ def ninv_W_columns(n, L_rowptr, L_col, L_val, m, cols, W_known=None):
 
 def ninv_threads(n, L_rowptr, L_col, L_val, pivot_start, d_diag, d_off, m, S=None):
     """``ninv`` (delta = 0) in plain C over every host thread: the Horner
-    columns and the entries of the product are independent (the survey's CPU
-    baseline variant (ii)).  Agrees with ``ninv`` to rounding."""
+    columns and the entries of the product are independent (the all-cores CPU
+    baseline).  Agrees with ``ninv`` to rounding."""
     lib = _load()
     if S is None:
         S = symbolic_S(n, L_rowptr, L_col, pivot_start)

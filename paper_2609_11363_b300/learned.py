@@ -7,7 +7,7 @@ truncation stack (``sinv_selinv``, ``sinv_ninv_stack``), the features
 module only orders the calls: it concatenates training sets, draws the
 mini-batch order with ``torch.randperm`` and reports errors.
 
-SelInv is the judge: ``evaluate`` measures ||N - G||_F / ||G||_F on S for plain
+SelInv is the reference: ``evaluate`` measures ||N - G||_F / ||G||_F on S for plain
 NInv and for the corrected NInv, and ``choose`` keeps the corrected values only
 when they beat NInv by the requested margin on held-out matrices (otherwise the
 caller uses SelInv, the method the network imitates).

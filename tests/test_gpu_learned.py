@@ -1,6 +1,6 @@
 """Learned correction: NInv truncation stack, BF16 MLP gradients against the FP64
 oracle, one Adam step, and the gain of a trained network over plain NInv on a
-held-out matrix (SelInv as the judge)."""
+held-out matrix (SelInv as the reference)."""
 import numpy as np
 import pytest
 import torch
