@@ -71,6 +71,13 @@ struct WarpSmem {
 // a CTA-cooperative supernode lays Lh, X and the positions out over all warps' regions
 static_assert(sizeof(WarpSmem) * kWarps >= (2 * sizeof(double) + sizeof(int32_t)) * kCW * kWarps, "layout");
 
+// scan form, whole CTA: a second place for the table of C, in the warps' shared
+// regions after Lh, X and the X positions of a supernode whose C x w fits them
+constexpr int kCtaTabOff = kCW * kWarps * (2 * (int)sizeof(double) + (int)sizeof(int32_t));
+constexpr int kCtaTabSlots = 4096;
+static_assert(kCtaTabOff + 2 * kCtaTabSlots * (int)sizeof(int32_t) <= (int)sizeof(WarpSmem) * kWarps,
+              "the table fits the warps' regions");
+
 struct CtaShared {
     int item;
     int stop;
@@ -386,6 +393,12 @@ __device__ bool process(const SelinvArgs& a, typename Form::G* Gw, int J, uint32
         if (slots <= avail) {
             tkeys = kCta ? tab : tab + (threadIdx.x >> 5) * kTabW;
             tvals = tkeys + kTabW * kWarps;
+        } else if (kCta && slots <= kCtaTabSlots) {
+            // a whole-CTA supernode with C up to kCtaTabSlots / 2 rows: the table in the
+            // warps' shared regions past Lh, X and their positions
+            unsigned char* base = reinterpret_cast<unsigned char*>(ws - (threadIdx.x >> 5));
+            tkeys = reinterpret_cast<int32_t*>(base + kCtaTabOff);
+            tvals = tkeys + kCtaTabSlots;
         } else {
             tkeys = a.gtab + gslot * 2 * a.gtab_slots;
             tvals = tkeys + a.gtab_slots;
