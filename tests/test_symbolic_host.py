@@ -290,3 +290,36 @@ def test_spai_and_lanczos_errors_through_the_abi(lib):
     bad = arp.copy()
     bad[-1] += 1  # rowptr does not end at nnzA
     assert lib.sinv_einv_analyse(h._h, A.nnz, bad.ctypes.data_as(P), acol.ctypes.data_as(P)) == 2
+
+
+def test_new_entry_points_report_errors_without_a_device(lib):
+    """Documented error returns of the calls for NInv / Mix on the own pattern, the
+    scan counters, the timeline and the checked-build test hook: a NULL handle, a
+    host-only handle, or a call before the one it needs (no device is touched)."""
+    P = ctypes.c_void_p
+    I64 = ctypes.c_int64
+    nnz, steps = I64(), np.zeros(4, dtype=np.int64)
+    # NULL handle
+    assert lib.sinv_ninv_own(None, None, None, 2, ctypes.c_double(0.1), None) == 1
+    assert lib.sinv_mix_own(None, None, ctypes.c_double(0.0), None) == 1
+    assert lib.sinv_mix_own_size(None, ctypes.byref(nnz)) == 1
+    assert lib.sinv_lowrank_correct_mix_own(None, 4, None, None, 0, None) == 1
+    assert lib.sinv_spai_mix_own(None, None, None, 3, None, None) == 1
+    assert lib.sinv_selinv_scan_counts(None, ctypes.byref(nnz), ctypes.byref(nnz), None) == 1
+    assert lib.sinv_debug_corrupt_plan(None) == 1
+    # a host-only handle: numeric calls are refused, the results of calls that never ran too
+    w = lap2d_32()
+    h = _host_handle(w.factors)
+    assert lib.sinv_ninv_own(h._h, None, None, 2, ctypes.c_double(0.1), None) == 1
+    assert lib.sinv_ninv_own(h._h, None, None, -1, ctypes.c_double(0.1), None) == 1
+    assert lib.sinv_ninv_own(h._h, None, None, 2, ctypes.c_double(-1.0), None) == 1
+    assert lib.sinv_ninv_own_size(h._h, ctypes.byref(nnz), steps.ctypes.data_as(P), 4) == 1
+    assert lib.sinv_mix_own(h._h, None, ctypes.c_double(float("nan")), None) == 1
+    assert lib.sinv_mix_own_size(h._h, ctypes.byref(nnz)) == 1
+    assert lib.sinv_lowrank_correct_mix_own(h._h, 300, None, None, 0, None) == 1
+    assert lib.sinv_spai_mix_own(h._h, None, None, 3, None, None) == 1
+    A = sp.csr_matrix(w.A)
+    arp, acol = A.indptr.astype(np.int64), A.indices.astype(np.int32)
+    assert lib.sinv_spai_analyse_mix_own(h._h, A.nnz, arp.ctypes.data_as(P), acol.ctypes.data_as(P), 0) == 1
+    assert lib.sinv_timeline_enable(h._h, 1) == 1
+    assert lib.sinv_debug_corrupt_plan(h._h) == 7   # the regular build never plants it
