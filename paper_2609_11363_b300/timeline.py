@@ -37,11 +37,11 @@ def dependencies(n, L_rowptr, L_col, sn_start):
     cols = np.asarray(L_col, dtype=np.int64)
     js = owner[cols]
     below = rows >= sn_start[js + 1]
-    pairs = np.unique(np.stack([js[below], owner[rows[below]]], axis=1), axis=0)
-    deps = [[] for _ in range(ns)]
-    for j, k in pairs:
-        deps[int(j)].append(int(k))
-    return deps
+    # distinct (J, K) pairs, sorted by J then K, as one int64 key per pair
+    key = np.unique(js[below].astype(np.int64) * ns + owner[rows[below]].astype(np.int64))
+    J, K = key // ns, key % ns
+    cuts = np.searchsorted(J, np.arange(1, ns))
+    return [a.tolist() for a in np.split(K, cuts)]
 
 
 def critical_path(stamps, deps, levels=None):
