@@ -229,7 +229,8 @@ sinv_status sinv_ninv_stack(sinv_handle h, const double *L_val, const double *D_
  * it into caller-owned device buffers (colptr n+1, rows and values nnz).
  * Synchronous on `stream` (sizes are read back after every step).
  * delta = 0 keeps every structural entry (the product's pattern then grows
- * like (L^{-1})^T L^{-1}).  Errors: SINV_ERR_INVALID_ARG (m < 0, delta < 0,
+ * like (L^{-1})^T L^{-1}).  For n = 0 the result is empty (colptr {0}, every
+ * nnz_W_steps[t] = 0) and L_val, D_val may be NULL.  Errors: SINV_ERR_INVALID_ARG (m < 0, delta < 0,
  * NaN), SINV_ERR_UNSUPPORTED (m > 30), SINV_ERR_OOM (device memory for the
  * series, its hash tables or the product), SINV_ERR_CUDA. */
 sinv_status sinv_ninv_own(sinv_handle h, const double *L_val, const double *D_val, int m, double delta,
@@ -248,6 +249,7 @@ sinv_status sinv_ninv_own_copy(sinv_handle h, int64_t *N_colptr, int32_t *N_row,
  *   is sized on the host); the result is handle-owned until the next call:
  *   sinv_mix_own_size gives its number of entries, sinv_mix_own_copy copies it to
  *   caller-owned device arrays (n+1 column pointers, then rows and values).
+ *   G_S may be NULL when S is empty (n = 0; the result is then empty).
  *   Errors: SINV_ERR_INVALID_ARG (no sinv_ninv_own result, null G_S, NaN eps),
  *   SINV_ERR_OOM, SINV_ERR_CUDA. */
 sinv_status sinv_mix_own(sinv_handle h, const double *G_S, double eps, void *stream);

@@ -294,6 +294,19 @@ struct DevBuf {
 };
 cudaError_t dev_alloc(DevBuf& b, size_t bytes) { return cudaMalloc(&b.p, std::max<size_t>(bytes, 8)); }
 
+// a handle-owned CSC result of the empty matrix: colptr = {0}, no rows or values
+cudaError_t empty_csc(int64_t** cp, int32_t** rows, double** vals, cudaStream_t st) {
+    if (*cp) cudaFree(*cp);
+    if (*rows) cudaFree(*rows);
+    if (*vals) cudaFree(*vals);
+    *cp = nullptr;
+    *rows = nullptr;
+    *vals = nullptr;
+    cudaError_t e = cudaMalloc((void**)cp, sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(*cp, 0, sizeof(int64_t), st);
+    return e == cudaSuccess ? cudaStreamSynchronize(st) : e;
+}
+
 bool valid_prec(int p) { return p == SINV_FP64 || p == SINV_FP32 || p == SINV_FP32X2; }
 bool tc_prec(int p) { return p == SINV_TF32_FP32ACC || p == SINV_BF16_FP32ACC; }
 
@@ -1678,11 +1691,18 @@ sinv_status sinv_ninv_own(sinv_handle h, const double* L_val, const double* D_va
     }
     const HostPlan& P = h->P;
     const int64_t n = P.n;
-    if (n == 0) return SINV_OK;
-    if (!D_val || (P.nnzL > 0 && !L_val)) return SINV_ERR_INVALID_ARG;
+    if (n > 0 && (!D_val || (P.nnzL > 0 && !L_val))) return SINV_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if (n == 0) {  // the empty matrix: an empty result (colptr {0}) that the size, copy and Mix calls accept
+        if ((e = empty_csc(&h->down_cp, &h->down_r, &h->down_v, st)) != cudaSuccess)
+            return cuda_fail(h, e, "NInv own-pattern result");
+        h->own_nnz = h->own_nnzW = 0;
+        h->own_nnzW_steps.assign(m + 1, 0);
+        h->own_hint.clear();
+        return SINV_OK;
+    }
     TraceScope trace_scope(h->tracer);
     auto fail = [&](cudaError_t err, const char* what) -> sinv_status {
         if (err == cudaErrorMemoryAllocation) {
@@ -1902,7 +1922,7 @@ sinv_status sinv_ninv_own_copy(sinv_handle h, int64_t* N_colptr, int32_t* N_row,
 }
 
 sinv_status sinv_mix_own(sinv_handle h, const double* G_S, double eps, void* stream) {
-    if (!h || !G_S || eps != eps) return SINV_ERR_INVALID_ARG;
+    if (!h || eps != eps || (!G_S && h->P.nnzS > 0)) return SINV_ERR_INVALID_ARG;
     if (!on_device(h)) return SINV_ERR_INVALID_ARG;
     if (!h->down_cp) {
         set_err(h, "sinv_ninv_own has not run");
@@ -1913,6 +1933,14 @@ sinv_status sinv_mix_own(sinv_handle h, const double* G_S, double eps, void* str
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if (n == 0) {  // the empty matrix: an empty result
+        h->mix_nnz = -1;
+        if ((e = empty_csc(&h->dmix_cp, &h->dmix_r, &h->dmix_v, st)) != cudaSuccess)
+            return cuda_fail(h, e, "Mix own-pattern result");
+        h->mix_nnz = 0;
+        h->mix_gen += 1;
+        return SINV_OK;
+    }
     TraceScope trace_scope(h->tracer);
     auto fail = [&](cudaError_t err, const char* what) -> sinv_status {
         if (err == cudaErrorMemoryAllocation) {
@@ -1988,6 +2016,10 @@ sinv_status sinv_spai_analyse_mix_own(sinv_handle h, int64_t nnzA, const int64_t
         set_err(h, "sinv_mix_own has not run");
         return SINV_ERR_INVALID_ARG;
     }
+    if (h->mix_nnz >= ((int64_t)1 << 31)) {
+        set_err(h, "the Mix pattern has >= 2^31 entries: not supported");
+        return SINV_ERR_UNSUPPORTED;
+    }
     const int64_t n = h->P.n;
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
@@ -2014,10 +2046,6 @@ sinv_status sinv_spai_analyse_mix_own(sinv_handle h, int64_t nnzA, const int64_t
     } catch (const std::bad_alloc&) {
         set_err(h, "host allocation failed in the SPAI analysis");
         return SINV_ERR_OOM;
-    }
-    if (h->mix_nnz >= ((int64_t)1 << 31)) {
-        set_err(h, "the Mix pattern has >= 2^31 entries: not supported");
-        return SINV_ERR_UNSUPPORTED;
     }
     sinv_status s = spai_analyse_common(h, nnzA, A_rowptr, A_col, 0, warp_entries, Prp.data(), Pc.data(), src.data());
     if (s == SINV_OK) h->spai_mix_gen = h->mix_gen;

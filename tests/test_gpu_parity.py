@@ -393,6 +393,35 @@ def test_empty_and_tiny():
     assert abs(out.item() - G[0]) <= 1e-15 * abs(G[0])
 
 
+def test_empty_matrix_every_entry_point():
+    """n = 0 through every numeric call of the path: each returns without an error
+    and every result is empty (the own-pattern results are the CSC of the empty
+    matrix, colptr {0})."""
+    from paper_2609_11363_b300 import Handle
+    h = Handle(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int8))
+    e = torch.zeros(0, dtype=torch.float64, device="cuda")
+    lam = torch.ones(4, dtype=torch.float64, device="cuda")
+    for prec in ("fp64", "fp32", "fp32x2", "tf32", "bf16"):
+        assert h.selinv(e, e, prec).numel() == 0
+    for prec in ("fp64", "fp32", "fp32x2"):
+        assert h.ninv(e, e, 3, prec).numel() == 0
+        assert h.ninv(e, e, 3, prec, delta=1e-2).numel() == 0
+        h.lowrank_correct(e, lam, e, prec)
+    assert h.ninv_stack(e, e, 2).numel() == 0
+    assert h.mix(e, e, 0.5).numel() == 0
+    cp, rows, vals, steps = h.ninv_own(e, e, 3, 1e-1)
+    assert cp.tolist() == [0] and rows.numel() == 0 and vals.numel() == 0 and steps.tolist() == [0] * 4
+    cp, rows, vals = h.mix_own(e, 1e-3)
+    assert cp.tolist() == [0] and rows.numel() == 0 and vals.numel() == 0 and h.mix_own_nnz() == 0
+    h.lowrank_correct_mix_own(e, lam)
+    A = sp.csr_matrix((0, 0))
+    h.spai_analyse(A)
+    assert h.spai(e, e, 3).numel() == 0
+    h.spai_analyse_mix_own(A)
+    assert h.spai_mix_own(e, 3).numel() == 0
+    h.sync_status()
+
+
 @pytest.mark.slow
 def test_full_size_diff3d_64():
     """The 64^3 shifted diffusion workload at full size, in the benchmark's launch

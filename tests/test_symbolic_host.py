@@ -323,3 +323,20 @@ def test_new_entry_points_report_errors_without_a_device(lib):
     assert lib.sinv_spai_analyse_mix_own(h._h, A.nnz, arp.ctypes.data_as(P), acol.ctypes.data_as(P), 0) == 1
     assert lib.sinv_timeline_enable(h._h, 1) == 1
     assert lib.sinv_debug_corrupt_plan(h._h) == 7   # the regular build never plants it
+
+
+def test_empty_matrix_host_analyses(lib):
+    """n = 0: the symbolic analysis, the SPAI pattern (S widened by any power) and
+    the Lanczos solve levels are all empty, and no call reports an error."""
+    from paper_2609_11363_b300 import Handle
+    h = Handle(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int8), device=-1)
+    st = h.stats()
+    assert h.nnz_S == 0 and st["n_supernodes"] == 0
+    A = sp.csr_matrix((0, 0))
+    for power in (0, 2):
+        h.spai_analyse(A, power=power)
+        rp, col = h.spai_pattern()
+        assert rp.tolist() == [0] and len(col) == 0 and h.stats()["spai_nnz_P"] == 0
+    h.einv_analyse(A)
+    st = h.stats()
+    assert st["einv_levels_fwd"] == 0 and st["einv_levels_bwd"] == 0
