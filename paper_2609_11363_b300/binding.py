@@ -159,11 +159,13 @@ def _np_ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def _check_tensor(t, name, numel=None, dtype=torch.float64):
+def _check_tensor(t, name, numel=None, dtype=torch.float64, device=None):
     if not isinstance(t, torch.Tensor):
         raise TypeError("%s must be a torch tensor" % name)
     if not t.is_cuda:
         raise ValueError("%s must be a CUDA tensor" % name)
+    if device is not None and t.device != device:
+        raise ValueError("%s is on %s, the handle on %s" % (name, t.device, device))
     if t.dtype != dtype:
         raise TypeError("%s must be %s" % (name, dtype))
     if not t.is_contiguous():
@@ -173,11 +175,13 @@ def _check_tensor(t, name, numel=None, dtype=torch.float64):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def _stream_ptr(stream):
+def _stream_ptr(stream, device=None):
     if stream is None:
         if not torch.cuda.is_available():
             return ctypes.c_void_p(0)  # host-only handles: the library rejects the call itself
-        stream = torch.cuda.current_stream()
+        stream = torch.cuda.current_stream(device)
+    elif device is not None and stream.device != device:
+        raise ValueError("the stream is on %s, the handle on %s" % (stream.device, device))
     return ctypes.c_void_p(stream.cuda_stream)
 
 
@@ -198,6 +202,14 @@ class Mlp:
             raise SinvError(st, "sinv_mlp_create")
         self.n_params = int(self._lib.sinv_mlp_param_count())
         self._loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+
+    def _t(self, t, name, numel=None, dtype=torch.float64):
+        """A CUDA tensor of this object's device (else ValueError), as a pointer."""
+        return _check_tensor(t, name, numel, dtype, self.device)
+
+    def _s(self, stream):
+        """The given stream (on this object's device) or that device's current one."""
+        return _stream_ptr(stream, self.device)
 
     def close(self):
         if getattr(self, "_m", None):
@@ -226,9 +238,9 @@ class Mlp:
 
     def targets(self, G, N, scale, stream=None):
         y = torch.empty(G.numel(), dtype=torch.float32, device=self.device)
-        self._chk(self._lib.sinv_mlp_targets(self._m, G.numel(), _check_tensor(G, "G"), _check_tensor(N, "N"),
-                                             _check_tensor(scale, "scale", None, torch.float32),
-                                             _check_tensor(y, "y", None, torch.float32), _stream_ptr(stream)),
+        self._chk(self._lib.sinv_mlp_targets(self._m, G.numel(), self._t(G, "G"), self._t(N, "N"),
+                                             self._t(scale, "scale", None, torch.float32),
+                                             self._t(y, "y", None, torch.float32), self._s(stream)),
                   "targets")
         return y
 
@@ -236,35 +248,35 @@ class Mlp:
         """(gradient [n_params] float32 tensor, loss tensor) over the entries idx (or all)."""
         count = int(idx.numel()) if idx is not None else int(X.shape[0])
         g = torch.empty(self.n_params, dtype=torch.float32, device=self.device)
-        self._chk(self._lib.sinv_mlp_grad(self._m, _check_tensor(X, "X", None, torch.bfloat16),
-                                          _check_tensor(y, "y", None, torch.float32),
-                                          _check_tensor(idx, "idx", None, torch.int64) if idx is not None else None,
-                                          count, _check_tensor(g, "grad", None, torch.float32),
-                                          _check_tensor(self._loss, "loss", None, torch.float32), _stream_ptr(stream)),
+        self._chk(self._lib.sinv_mlp_grad(self._m, self._t(X, "X", None, torch.bfloat16),
+                                          self._t(y, "y", None, torch.float32),
+                                          self._t(idx, "idx", None, torch.int64) if idx is not None else None,
+                                          count, self._t(g, "grad", None, torch.float32),
+                                          self._t(self._loss, "loss", None, torch.float32), self._s(stream)),
                   "grad")
         return g, self._loss
 
     def train_step(self, X, y, idx, lr, stream=None):
-        self._chk(self._lib.sinv_mlp_train_step(self._m, _check_tensor(X, "X", None, torch.bfloat16),
-                                                _check_tensor(y, "y", None, torch.float32),
-                                                _check_tensor(idx, "idx", None, torch.int64), int(idx.numel()),
-                                                ctypes.c_float(lr), _check_tensor(self._loss, "loss", None,
+        self._chk(self._lib.sinv_mlp_train_step(self._m, self._t(X, "X", None, torch.bfloat16),
+                                                self._t(y, "y", None, torch.float32),
+                                                self._t(idx, "idx", None, torch.int64), int(idx.numel()),
+                                                ctypes.c_float(lr), self._t(self._loss, "loss", None,
                                                                                   torch.float32),
-                                                _stream_ptr(stream)), "train_step")
+                                                self._s(stream)), "train_step")
         return self._loss
 
     def predict(self, X, scale, N, out=None, stream=None):
         if out is None:
             out = torch.empty_like(N)
-        self._chk(self._lib.sinv_mlp_predict(self._m, _check_tensor(X, "X", None, torch.bfloat16),
-                                             _check_tensor(scale, "scale", None, torch.float32),
-                                             _check_tensor(N, "N"), int(N.numel()), _check_tensor(out, "out"),
-                                             _stream_ptr(stream)), "predict")
+        self._chk(self._lib.sinv_mlp_predict(self._m, self._t(X, "X", None, torch.bfloat16),
+                                             self._t(scale, "scale", None, torch.float32),
+                                             self._t(N, "N"), int(N.numel()), self._t(out, "out"),
+                                             self._s(stream)), "predict")
         return out
 
     def sync_status(self, stream=None):
         """Synchronize and raise on a device error of the asynchronous calls."""
-        self._chk(self._lib.sinv_mlp_sync_status(self._m, _stream_ptr(stream)), "sync_status")
+        self._chk(self._lib.sinv_mlp_sync_status(self._m, self._s(stream)), "sync_status")
 
 
 LOWRANK_NOALLOC_MAX = 1 << 22  # n*k + k floats of the library's built-in working array
@@ -378,13 +390,13 @@ class Handle:
         def ptrs(ts, name, dtype=torch.float64):
             arr = (ctypes.c_void_p * k)()
             for b, t in enumerate(ts):
-                arr[b] = _check_tensor(t, name, None, dtype).value if t is not None else None
+                arr[b] = self._t(t, name, None, dtype).value if t is not None else None
             return arr
 
         Lp, Dp = ptrs(L_vals, "L_val"), ptrs(D_vals, "D_val")
         Gp = ptrs(G_outs, "G_out") if G_outs is not None else None
         Np = ptrs(N_outs, "N_out") if N_outs is not None else None
-        self._check(self._lib.sinv_batch_run(self._h, k, Lp, Dp, PREC[prec], Gp, int(m), Np, _stream_ptr(stream)))
+        self._check(self._lib.sinv_batch_run(self._h, k, Lp, Dp, PREC[prec], Gp, int(m), Np, self._s(stream)))
 
     # -- helpers -----------------------------------------------------------
     def last_error(self) -> str:
@@ -397,6 +409,14 @@ class Handle:
     def _check(self, st):
         if st != 0:
             raise SinvError(st, self.last_error())
+
+    def _t(self, t, name, numel=None, dtype=torch.float64):
+        """A CUDA tensor of this object's device (else ValueError), as a pointer."""
+        return _check_tensor(t, name, numel, dtype, self.device)
+
+    def _s(self, stream):
+        """The given stream (on this object's device) or that device's current one."""
+        return _stream_ptr(stream, self.device)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -441,29 +461,29 @@ class Handle:
     # -- numeric calls -----------------------------------------------------
     def selinv(self, L_val, D_val, prec="fp64", out=None, stream=None):
         out = self._out(out)
-        self._check(self._lib.sinv_selinv(self._h, _check_tensor(L_val, "L_val", self.nnz_L),
-                                          _check_tensor(D_val, "D_val", self.nD), PREC[prec],
-                                          _check_tensor(out, "G_S", self.nnz_S), _stream_ptr(stream)))
+        self._check(self._lib.sinv_selinv(self._h, self._t(L_val, "L_val", self.nnz_L),
+                                          self._t(D_val, "D_val", self.nD), PREC[prec],
+                                          self._t(out, "G_S", self.nnz_S), self._s(stream)))
         return out
 
     def ninv(self, L_val, D_val, m, prec="fp64", out=None, stream=None, delta=0.0):
         """NInv on S; delta > 0 drops off-diagonal |w| < delta after every Horner step."""
         out = self._out(out)
-        Lp = _check_tensor(L_val, "L_val", self.nnz_L)
-        Dp = _check_tensor(D_val, "D_val", self.nD)
-        Np = _check_tensor(out, "N_S", self.nnz_S)
+        Lp = self._t(L_val, "L_val", self.nnz_L)
+        Dp = self._t(D_val, "D_val", self.nD)
+        Np = self._t(out, "N_S", self.nnz_S)
         if delta:
-            st = self._lib.sinv_ninv_drop(self._h, Lp, Dp, int(m), float(delta), PREC[prec], Np, _stream_ptr(stream))
+            st = self._lib.sinv_ninv_drop(self._h, Lp, Dp, int(m), float(delta), PREC[prec], Np, self._s(stream))
         else:
-            st = self._lib.sinv_ninv(self._h, Lp, Dp, int(m), PREC[prec], Np, _stream_ptr(stream))
+            st = self._lib.sinv_ninv(self._h, Lp, Dp, int(m), PREC[prec], Np, self._s(stream))
         self._check(st)
         return out
 
     def mix(self, G, N, eps, out=None, stream=None):
         out = self._out(out)
-        self._check(self._lib.sinv_mix(self._h, _check_tensor(G, "G_S", self.nnz_S),
-                                       _check_tensor(N, "N_S", self.nnz_S), float(eps),
-                                       _check_tensor(out, "M_S", self.nnz_S), _stream_ptr(stream)))
+        self._check(self._lib.sinv_mix(self._h, self._t(G, "G_S", self.nnz_S),
+                                       self._t(N, "N_S", self.nnz_S), float(eps),
+                                       self._t(out, "M_S", self.nnz_S), self._s(stream)))
         return out
 
     def spai_analyse(self, A, power=0, warp_entries=0):
@@ -495,9 +515,9 @@ class Handle:
         nP = getattr(self, "nnz_P", None)
         if out is None:
             out = torch.empty(nP or 0, dtype=torch.float64, device=self.device)
-        self._check(self._lib.sinv_spai(self._h, _check_tensor(A_val, "A_val", getattr(self, "_spai_nnzA", None)),
-                                        _check_tensor(X, "X_S", self.nnz_S), int(iters),
-                                        _check_tensor(out, "Y_P", nP), _stream_ptr(stream)))
+        self._check(self._lib.sinv_spai(self._h, self._t(A_val, "A_val", getattr(self, "_spai_nnzA", None)),
+                                        self._t(X, "X_S", self.nnz_S), int(iters),
+                                        self._t(out, "Y_P", nP), self._s(stream)))
         return out
 
     def spai_analyse_mix_own(self, A, warp_entries=0):
@@ -520,10 +540,10 @@ class Handle:
         nP = getattr(self, "nnz_P", None)
         if out is None:
             out = torch.empty(nP or 0, dtype=torch.float64, device=self.device)
-        xp = None if X is None else _check_tensor(X, "X_M")
-        self._check(self._lib.sinv_spai_mix_own(self._h, _check_tensor(A_val, "A_val",
+        xp = None if X is None else self._t(X, "X_M")
+        self._check(self._lib.sinv_spai_mix_own(self._h, self._t(A_val, "A_val",
                                                                        getattr(self, "_spai_nnzA", None)),
-                                                xp, int(iters), _check_tensor(out, "Y_P", nP), _stream_ptr(stream)))
+                                                xp, int(iters), self._t(out, "Y_P", nP), self._s(stream)))
         return out
 
     def einv_analyse(self, A):
@@ -550,26 +570,26 @@ class Handle:
         info = np.zeros(3, dtype=np.int32)
         V = torch.empty((self.n, int(k)), dtype=torch.float64, device=self.device)
         self._check(self._lib.sinv_einv_lanczos(
-            self._h, _check_tensor(A_val, "A_val", getattr(self, "_einv_nnzA", None)),
-            _check_tensor(L_val, "L_val", self.nnz_L), _check_tensor(D_val, "D_val", self.nD),
-            _check_tensor(X, "X_S", self.nnz_S), _check_tensor(q0, "q0", self.n), int(steps), float(cg_tol),
-            int(cg_maxit), int(k), _np_ptr(lam), _check_tensor(V, "V", self.n * int(k)), _np_ptr(info),
-            _stream_ptr(stream)))
+            self._h, self._t(A_val, "A_val", getattr(self, "_einv_nnzA", None)),
+            self._t(L_val, "L_val", self.nnz_L), self._t(D_val, "D_val", self.nD),
+            self._t(X, "X_S", self.nnz_S), self._t(q0, "q0", self.n), int(steps), float(cg_tol),
+            int(cg_maxit), int(k), _np_ptr(lam), self._t(V, "V", self.n * int(k)), _np_ptr(info),
+            self._s(stream)))
         return lam, V, {"steps": int(info[0]), "cg_iterations": int(info[1]), "cg_unconverged": int(info[2])}
 
     def lowrank_correct(self, V, lam, X, prec="fp64", stream=None):
         k = int(lam.numel())
-        self._check(self._lib.sinv_lowrank_correct(self._h, k, _check_tensor(V, "V", self.n * k),
-                                                   _check_tensor(lam, "lambda", k), PREC[prec],
-                                                   _check_tensor(X, "X_S", self.nnz_S), _stream_ptr(stream)))
+        self._check(self._lib.sinv_lowrank_correct(self._h, k, self._t(V, "V", self.n * k),
+                                                   self._t(lam, "lambda", k), PREC[prec],
+                                                   self._t(X, "X_S", self.nnz_S), self._s(stream)))
         return X
 
     def ninv_own(self, L_val, D_val, m, delta, stream=None, copy=True):
         """NInv on its own pattern: (colptr, rows, values) of the lower triangle in CSC
         (CUDA tensors) and the nnz of W after every Horner step; copy=False leaves the
         result in the handle and returns (None, None, None, steps)."""
-        self._check(self._lib.sinv_ninv_own(self._h, _check_tensor(L_val, "L_val"), _check_tensor(D_val, "D_val"),
-                                            int(m), float(delta), _stream_ptr(stream)))
+        self._check(self._lib.sinv_ninv_own(self._h, self._t(L_val, "L_val"), self._t(D_val, "D_val"),
+                                            int(m), float(delta), self._s(stream)))
         nnz = ctypes.c_int64()
         steps = np.zeros(int(m) + 1, dtype=np.int64)
         self._check(self._lib.sinv_ninv_own_size(self._h, ctypes.byref(nnz), _np_ptr(steps), int(m) + 1))
@@ -579,16 +599,16 @@ class Handle:
         cp = torch.empty(self.n + 1, dtype=torch.int64, device=self.device)
         rows = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=self.device)
         vals = torch.empty(max(nnz.value, 1), dtype=torch.float64, device=self.device)
-        self._check(self._lib.sinv_ninv_own_copy(self._h, _check_tensor(cp, "colptr", None, torch.int64),
-                                                 _check_tensor(rows, "rows", None, torch.int32),
-                                                 _check_tensor(vals, "vals"), _stream_ptr(stream)))
+        self._check(self._lib.sinv_ninv_own_copy(self._h, self._t(cp, "colptr", None, torch.int64),
+                                                 self._t(rows, "rows", None, torch.int32),
+                                                 self._t(vals, "vals"), self._s(stream)))
         return cp, rows[:nnz.value], vals[:nnz.value], steps
 
     def mix_own(self, G, eps, stream=None, copy=True):
         """Mix on the pattern of the last ninv_own: (colptr, rows, values) of the lower
         triangle in CSC (CUDA tensors); copy=False leaves the result in the handle."""
-        self._check(self._lib.sinv_mix_own(self._h, _check_tensor(G, "G", self.nnz_S), float(eps),
-                                           _stream_ptr(stream)))
+        self._check(self._lib.sinv_mix_own(self._h, self._t(G, "G", self.nnz_S), float(eps),
+                                           self._s(stream)))
         return self.mix_own_result(stream) if copy else None
 
     def mix_own_nnz(self) -> int:
@@ -603,26 +623,26 @@ class Handle:
         cp = torch.empty(self.n + 1, dtype=torch.int64, device=self.device)
         rows = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=self.device)
         vals = torch.empty(max(nnz.value, 1), dtype=torch.float64, device=self.device)
-        self._check(self._lib.sinv_mix_own_copy(self._h, _check_tensor(cp, "colptr", None, torch.int64),
-                                                _check_tensor(rows, "rows", None, torch.int32),
-                                                _check_tensor(vals, "vals"), _stream_ptr(stream)))
+        self._check(self._lib.sinv_mix_own_copy(self._h, self._t(cp, "colptr", None, torch.int64),
+                                                self._t(rows, "rows", None, torch.int32),
+                                                self._t(vals, "vals"), self._s(stream)))
         return cp, rows[:nnz.value], vals[:nnz.value]
 
     def lowrank_correct_mix_own(self, V, lam, prec="fp64", stream=None):
         """Add V diag(lam) V^T on the pattern of the last mix_own result (in place)."""
         k = int(lam.numel())
-        self._check(self._lib.sinv_lowrank_correct_mix_own(self._h, k, _check_tensor(V, "V", self.n * k),
-                                                           _check_tensor(lam, "lambda", k), PREC[prec],
-                                                           _stream_ptr(stream)))
+        self._check(self._lib.sinv_lowrank_correct_mix_own(self._h, k, self._t(V, "V", self.n * k),
+                                                           self._t(lam, "lambda", k), PREC[prec],
+                                                           self._s(stream)))
 
     def ninv_stack(self, L_val, D_val, m, prec="fp64", out=None, stream=None):
         """NInv on S for the truncations after 0..m terms: tensor [(m+1), |S_lo|]."""
         if out is None:
             out = torch.empty((m + 1) * self.nnz_S, dtype=torch.float64, device=self.device)
-        self._check(self._lib.sinv_ninv_stack(self._h, _check_tensor(L_val, "L_val", self.nnz_L),
-                                              _check_tensor(D_val, "D_val", self.nD), int(m), PREC[prec],
-                                              _check_tensor(out, "N_stack", (m + 1) * self.nnz_S),
-                                              _stream_ptr(stream)))
+        self._check(self._lib.sinv_ninv_stack(self._h, self._t(L_val, "L_val", self.nnz_L),
+                                              self._t(D_val, "D_val", self.nD), int(m), PREC[prec],
+                                              self._t(out, "N_stack", (m + 1) * self.nnz_S),
+                                              self._s(stream)))
         return out.view(m + 1, self.nnz_S)
 
     def mlp_features(self, N_stack, m, L_val, D_val, stream=None):
@@ -630,14 +650,14 @@ class Handle:
         X = torch.empty((self.nnz_S, MLP_F), dtype=torch.bfloat16, device=self.device)
         sc = torch.empty(self.nnz_S, dtype=torch.float32, device=self.device)
         self._check(self._lib.sinv_mlp_features(
-            self._h, _check_tensor(N_stack.reshape(-1), "N_stack", (m + 1) * self.nnz_S), int(m),
-            _check_tensor(L_val, "L_val", self.nnz_L), _check_tensor(D_val, "D_val", self.nD),
-            _check_tensor(X, "X", None, torch.bfloat16), _check_tensor(sc, "scale", None, torch.float32),
-            _stream_ptr(stream)))
+            self._h, self._t(N_stack.reshape(-1), "N_stack", (m + 1) * self.nnz_S), int(m),
+            self._t(L_val, "L_val", self.nnz_L), self._t(D_val, "D_val", self.nD),
+            self._t(X, "X", None, torch.bfloat16), self._t(sc, "scale", None, torch.float32),
+            self._s(stream)))
         return X, sc
 
     def sync_status(self, stream=None):
-        self._check(self._lib.sinv_sync_status(self._h, _stream_ptr(stream)))
+        self._check(self._lib.sinv_sync_status(self._h, self._s(stream)))
 
     def trace(self, enable=True):
         """Turn per-kernel event timing on or off."""
@@ -659,14 +679,14 @@ class Handle:
         dependencies published, contraction done, published."""
         ns = int(self.stats()["n_supernodes"])
         out = np.zeros((ns, 4), dtype=np.uint64)
-        self._check(self._lib.sinv_timeline_read(self._h, _np_ptr(out), ns, _stream_ptr(stream)))
+        self._check(self._lib.sinv_timeline_read(self._h, _np_ptr(out), ns, self._s(stream)))
         return out
 
     def selinv_scan_counts(self, stream=None):
         """(lookups, pairs) of the last selinv run with the timeline enabled (scan form)."""
         lk, pr = ctypes.c_int64(), ctypes.c_int64()
         self._check(self._lib.sinv_selinv_scan_counts(self._h, ctypes.byref(lk), ctypes.byref(pr),
-                                                      _stream_ptr(stream)))
+                                                      self._s(stream)))
         return int(lk.value), int(pr.value)
 
     def debug_corrupt_plan(self) -> int:
@@ -674,4 +694,4 @@ class Handle:
         return int(self._lib.sinv_debug_corrupt_plan(self._h))
 
     def debug_wait_timeout(self, stream=None) -> int:
-        return int(self._lib.sinv_debug_wait_timeout(self._h, _stream_ptr(stream)))
+        return int(self._lib.sinv_debug_wait_timeout(self._h, self._s(stream)))
