@@ -23,7 +23,9 @@
  *    "on S" (G_S, N_S, M_S, X_S) has |S_lo| entries in this CSR order.
  *  - Numeric calls take DEVICE pointers, are asynchronous on the given stream,
  *    and keep no pointer after their stream work completes.  The caller owns
- *    every buffer it passes; the handle owns everything it allocates.
+ *    every buffer it passes; the handle owns everything it allocates.  Every
+ *    pointer and the stream belong to the handle's device (the `device` of
+ *    sinv_symbolic_opts); the call makes that device current itself.
  *  - Every call returns a status and never aborts or throws across the ABI.
  *    Errors found on the device (a singular pivot, a wait that timed out) are
  *    recorded in a handle-owned status word and returned (and cleared) by
