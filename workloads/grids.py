@@ -172,7 +172,7 @@ def covariance2d(N: int, alpha: float = 3.0, beta: float = 4.0) -> sp.csr_matrix
     """Covariance-type matrix on an N x N grid of unit spacing (n = N^2):
     c_ij = (1 - d(i, j)/alpha)^beta for d(i, j) <= alpha, else 0, with d the
     Euclidean distance between grid points i and j (the paper's second example,
-    Section 3, after Tang and Saad).  c_ii = 1; entries at d = alpha are 0 and
+    Section 3.6, after Tang and Saad).  c_ii = 1; entries at d = alpha are 0 and
     are not stored.  The truncated power (1 - r)_+^beta is positive definite in
     the plane for beta >= 3/2 (Askey), so C is SPD for beta = 4.  No random numbers.
     """
