@@ -1098,8 +1098,12 @@ def run_reference(args, world):
     trailing block of the workload's factors, sized during the warm-up so that
     the whole run stays within a few minutes."""
     w, f, V, lam, t_gen = build_workload(args.size)
-    budget_s = 150.0  # the timed steps together
-    b, t_cal, nS_b, _ = calibrated_block(f, V, lam, w.m, target_s=budget_s / max(args.steps, 1))
+    # the timed steps together take about 150 s at most, and one step 15 s at most:
+    # the oracle's memory grows faster than its time with the block (about 34 GB
+    # at n' = 24,576 of the 64^3 workload), so a few long steps must not buy a
+    # larger block
+    budget_s = 150.0
+    b, t_cal, nS_b, _ = calibrated_block(f, V, lam, w.m, target_s=min(budget_s / max(args.steps, 1), 15.0))
     for _ in range(max(args.warmup - 1, 0)):
         oracle_step(b, lam, w.m)
     times, parts = [], None
