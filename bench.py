@@ -11,6 +11,9 @@ With --gpus N > 1 (under torchrun) every rank runs its own replica of the
 workload: the path has no exchange step between matrices (weak scaling, no
 collective on the data path).  ``--impl reference`` times the FP64 CPU oracle on
 the host cores instead (the baseline arm: the paper ships no code).
+After the FP64 timed region the same step also runs in the mixed-precision
+forms (FP32X2, FP32) on the same inputs: ``forms`` holds their step times and
+their error against the FP64 step's result (``--no-forms`` leaves this out).
 """
 from __future__ import annotations
 
@@ -76,6 +79,8 @@ def parse():
                    help="covariance: also report err_1 of the diagonals against a dense inverse up to this n")
     p.add_argument("--batch", type=int, default=256, help="matrices of the batch9pt workload")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-forms", action="store_true",
+                   help="leave out the FP32X2 and FP32 steps timed after the FP64 line's timed region")
     return p.parse_args()
 
 
@@ -308,13 +313,67 @@ def run_ours(args, rank, world):
         step_ms.append(ev[0].elapsed_time(ev[4]))
     ms_per_step, value = aggregate_ranks(float(np.sum(step_ms)), nS, args.steps, world, dev)
 
-    e2e = None
+    e2e = forms = None
     if rank == 0:
+        M64 = M.clone()  # the last timed FP64 step's corrected result
         e2e = measure_e2e(h, f, V, lam, m, eps, prec, dev, args)
+        if prec == "fp64" and not args.no_forms:
+            forms = measure_forms(h, Lv, Dv, Vd, lamd, m, eps, M64, nS, flush, stream, dev, args,
+                                  float(np.sum(step_ms)) / args.steps)
     launches = int(sum(c for c, _ in trace.values()))
     return dict(w=w, f=f, h=h, nS=nS, nS_lo=nS_lo, t_gen=t_gen, t_sym=t_sym, t_sym_ninv=t_sym_ninv,
                 ms_per_step=ms_per_step, value=value, clocks=clk, eps=eps, e2e=e2e, m=m, k=k, V=V, lam=lam,
-                phase_ms={p: float(np.median(v)) for p, v in per_phase.items()}, trace=trace, launches=launches)
+                phase_ms={p: float(np.median(v)) for p, v in per_phase.items()}, trace=trace, launches=launches,
+                forms=forms)
+
+
+def measure_forms(h, Lv, Dv, Vd, lamd, m, eps, M64, nS, flush, stream, dev, args, fp64_ms):
+    """The same step in the mixed-precision forms, after the FP64 timed region and on
+    the same inputs: event-timed steps with L2 flushed between them, and the error
+    of each form's corrected result against the FP64 step's, in the measure of the
+    form's stated error (entrywise scaled for the pair form, normwise for FP32)."""
+    import torch
+    rp, col = h.pattern_host()
+    rows = torch.as_tensor(np.repeat(np.arange(h.n, dtype=np.int64), np.diff(rp)), device=dev)
+    cols = torch.as_tensor(np.asarray(col, dtype=np.int64), device=dev)
+    dia = M64[torch.as_tensor(rp[1:] - 1, device=dev)].abs()
+    G, N, M = torch.empty_like(M64), torch.empty_like(M64), torch.empty_like(M64)
+    out = {}
+    for form in ("fp32x2", "fp32"):
+        try:
+            def step():
+                h.selinv(Lv, Dv, form, out=G)
+                h.ninv(Lv, Dv, m, form, out=N, delta=args.ninv_delta)
+                h.mix(G, N, eps, out=M)
+                h.lowrank_correct(Vd, lamd, M, form)
+
+            for _ in range(max(args.warmup, 1)):
+                step()
+            h.sync_status()
+            K = max(1, min(args.steps, 5))
+            evs = []
+            for _ in range(K):
+                flush.zero_()
+                e = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                e[0].record(stream)
+                step()
+                e[1].record(stream)
+                evs.append(e)
+            torch.cuda.synchronize()
+            h.sync_status()
+            ms = [a.elapsed_time(b) for a, b in evs]
+            if form == "fp32x2":
+                err = float(((M - M64).abs() / (M64.abs() + torch.sqrt(dia[rows] * dia[cols]))).max())
+                measure = "entrywise max |x-r| / (|r| + sqrt|r_ii r_jj|), r = the FP64 step's result"
+            else:
+                err = float(torch.linalg.norm(M - M64) / torch.linalg.norm(M64))
+                measure = "normwise ||x-r||_F / ||r||_F, r = the FP64 step's result"
+            out[form] = {"ms_per_step": float(np.mean(ms)), "value": nS * K / (float(np.sum(ms)) / 1e3),
+                         "unit": "entries/s", "speedup_vs_fp64": fp64_ms / float(np.mean(ms)), "steps": K,
+                         "stated_rel_error": STATED_ERROR[form], "error_vs_fp64": err, "error_measure": measure}
+        except Exception as exc:  # the FP64 line stands whatever happens here
+            out[form] = {"failed": repr(exc)}
+    return out
 
 
 def measure_e2e(h, f, V, lam, m, eps, prec, dev, args):
@@ -500,6 +559,7 @@ def main():
                        "input_gen_s": res["t_gen"], "peaks": peak_kind,
                        "parallelism": "replicas" if world > 1 else "single"},
             "phase_ms": res["phase_ms"],
+            "forms": res["forms"],
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": res["e2e"],
