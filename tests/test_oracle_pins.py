@@ -673,3 +673,72 @@ def test_spai_embed_places_values_on_the_wider_pattern():
     for (i, j), y in zip(zip(_rows(Prp).tolist(), Pc.tolist()), Y.tolist()):
         assert y == onS.get((i, j), 0.0)
     assert len(Pc) > len(Sc)
+
+
+def test_selinv_blocks_top_down_over_every_block_is_selinv():
+    """The recurrence restricted to listed pivot blocks, given every block from the
+    last to the first, is the whole recurrence (bit for bit); a block left out keeps
+    its entries untouched (the partition of the elimination DAG relies on both)."""
+    from workloads.configs import random_factors
+    for f in (plant_2x2(lap2d_32().factors, 0.3, 11), random_factors(300, 0.05, 0.15, 5)):
+        S = _S(f)
+        G = _selinv(f, S)
+        starts = np.flatnonzero(np.asarray(f.pivot_start) != 0)
+        Gb = np.zeros(len(S[1]))
+        oracle.selinv_blocks(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, S, Gb,
+                             starts[::-1])
+        assert np.array_equal(Gb, G)
+        # leave out the first block: its rows of S_lo (and only they) stay zero
+        Gc = np.zeros(len(S[1]))
+        oracle.selinv_blocks(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, S, Gc,
+                             starts[::-1][:-1])
+        first = starts[1] if len(starts) > 1 else f.n      # columns of the first block
+        col = np.asarray(S[1])
+        assert np.all(Gc[col < first] == 0.0) and np.array_equal(Gc[col >= first], G[col >= first])
+
+
+def test_ninv_W_columns_is_the_dense_truncated_series():
+    """Columns of W_t = sum_{s<=t} E^t (E = I - L) by the column Horner steps equal
+    the dense truncated series at every t; columns computed from W_known columns
+    given for the rest agree with computing everything."""
+    from workloads.configs import random_factors
+    f = random_factors(60, 0.08, 0.1, 3)
+    n, m = f.n, 3
+    E = -f.L_csr().toarray()
+    dense = [np.eye(n)]
+    for t in range(1, m + 1):
+        dense.append(np.eye(n) + E @ dense[-1])
+    W = oracle.ninv_W_columns(n, f.L_rowptr, f.L_col, f.L_val, m, range(n))
+    for t in range(m + 1):
+        for j in range(n):
+            col = np.zeros(n)
+            for r, v in W[t][j].items():
+                col[r] = v
+            assert np.allclose(col, dense[t][:, j], rtol=0, atol=1e-13), (t, j)
+    top = list(range(n // 2, n))
+    known = {j: {t: W[t][j] for t in range(m + 1)} for j in top}
+    W2 = oracle.ninv_W_columns(n, f.L_rowptr, f.L_col, f.L_val, m, range(n // 2), W_known=known)
+    for t in range(m + 1):
+        for j in range(n // 2):
+            assert W2[t][j] == W[t][j]
+
+
+def test_pcg_jacobi_reaches_the_solution():
+    """Jacobi-PCG: n steps solve an SPD system to rounding (CG's finite termination),
+    one step is exact for a diagonal matrix, and zero steps return the start."""
+    from oracle.spai import pcg_jacobi
+    rng = np.random.default_rng(4)
+    n = 12
+    Q = rng.standard_normal((n, n))
+    B = Q @ Q.T + n * np.eye(n)
+    b = rng.standard_normal(n)
+    x = pcg_jacobi(B, b, np.zeros(n), n)
+    assert np.linalg.norm(x - np.linalg.solve(B, b)) <= 1e-10 * np.linalg.norm(np.linalg.solve(B, b))
+    Dg = np.diag(rng.uniform(1.0, 5.0, n))
+    assert np.allclose(pcg_jacobi(Dg, b, np.zeros(n), 1), b / np.diag(Dg), rtol=1e-15, atol=0)
+    x0 = rng.standard_normal(n)
+    assert np.array_equal(pcg_jacobi(B, b, x0, 0), x0)
+
+
+def test_fill_ratios_hand_values():
+    assert oracle.fill_inv(30, 10) == 3.0 and oracle.fill_fact(25, 10) == 2.5
