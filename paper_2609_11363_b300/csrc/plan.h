@@ -72,13 +72,13 @@ struct HostPlan {
     int64_t n = 0, nnzL = 0, nnzS = 0;
     // S_lo
     std::vector<int64_t> Srp;
-    std::vector<int32_t> Sc;
+    FillVec<int32_t> Sc;
     std::vector<int32_t> Sdiag;   // position of (i, i) in S_lo
-    std::vector<int32_t> l2s;     // S_lo position of each L entry (CSR order)
+    FillVec<int32_t> l2s;         // S_lo position of each L entry (CSR order)
     // L by columns (struct(j)), with the CSR position of each entry
     std::vector<int64_t> Lcp;
-    std::vector<int32_t> Lri;
-    std::vector<int32_t> Lcsr;
+    FillVec<int32_t> Lri;
+    FillVec<int32_t> Lcsr;
     // pivot blocks
     std::vector<int8_t> pstart;
     std::vector<int32_t> dpos;    // per column: offset of its block's first value in D_val

@@ -58,6 +58,69 @@ void parallel_for_dynamic(int64_t count, int64_t grain, F f) {
     for (auto& x : th) x.join();
 }
 
+// f(t) for every t in [0, T), one thread each
+template <class F>
+void run_chunks(int T, F f) {
+    if (T <= 1) {
+        f(0);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < T; ++t) th.emplace_back([=, &f] { f(t); });
+    for (auto& x : th) x.join();
+}
+
+// CSR (rows 0..n-1, columns < n) to CSC, with every column's rows in increasing
+// order and the CSR position of each entry: the rows are cut into T chunks of about
+// equal entries; each chunk counts its entries per column, the counts become start
+// positions ordered by (column, chunk), and each chunk places its own entries.  The
+// result is the one a serial counting sort gives.
+template <class IdxVec>
+void csr_to_csc(int64_t n, const int64_t* rp, const int32_t* col, std::vector<int64_t>& cp, IdxVec& ri,
+                IdxVec& pos) {
+    const int64_t nnz = rp[n];
+    cp.assign(n + 1, 0);
+    ri.resize(nnz);
+    pos.resize(nnz);
+    int T = (int)std::min<int64_t>(n_threads(), std::max<int64_t>(1, nnz >> 20));
+    if ((int64_t)T * n > (int64_t(1) << 30)) T = 1;  // the per-chunk counts must stay small
+    std::vector<int64_t> rb(T + 1);
+    for (int t = 0; t <= T; ++t)  // first row of chunk t: the first row starting at or past t nnz / T
+        rb[t] = t == T ? n : std::lower_bound(rp, rp + n, (int64_t)((__int128)nnz * t / T)) - rp;
+    std::vector<int64_t> start((size_t)T * n, 0);  // entries of chunk t in column j, then their start
+    run_chunks(T, [&](int t) {
+        int64_t* c = start.data() + (size_t)t * n;
+        for (int64_t q = rp[rb[t]]; q < rp[rb[t + 1]]; ++q) c[col[q]]++;
+    });
+    parallel_for(n, [&](int64_t a, int64_t b) {
+        for (int64_t j = a; j < b; ++j) {
+            int64_t tot = 0;
+            for (int t = 0; t < T; ++t) tot += start[(size_t)t * n + j];
+            cp[j + 1] = tot;
+        }
+    });
+    for (int64_t j = 0; j < n; ++j) cp[j + 1] += cp[j];
+    parallel_for(n, [&](int64_t a, int64_t b) {
+        for (int64_t j = a; j < b; ++j) {
+            int64_t run = cp[j];
+            for (int t = 0; t < T; ++t) {
+                const int64_t c = start[(size_t)t * n + j];
+                start[(size_t)t * n + j] = run;
+                run += c;
+            }
+        }
+    });
+    run_chunks(T, [&](int t) {
+        int64_t* c = start.data() + (size_t)t * n;
+        for (int64_t i = rb[t]; i < rb[t + 1]; ++i)
+            for (int64_t q = rp[i]; q < rp[i + 1]; ++q) {
+                const int64_t d = c[col[q]]++;
+                ri[d] = (int32_t)i;
+                pos[d] = (int32_t)q;
+            }
+    });
+}
+
 // is sorted list a (minus the values in [ex0, ex1)) a subset of sorted list b?
 bool subset_except(const int32_t* a, int64_t na, const int32_t* b, int64_t nb, int32_t ex0, int32_t ex1) {
     int64_t j = 0;
@@ -92,7 +155,26 @@ std::string build_plan(int64_t n, const int64_t* Lrp, const int32_t* Lc, const i
     int64_t nnzL = Lrp[n];
     P.nnzL = nnzL;
     if (nnzL > INT32_MAX) return "nnz(L) >= 2^31 not supported";
-    for (int64_t i = 0; i < n; ++i) {
+    // rows are checked in parallel for the first bad one, whose message comes from
+    // the same check in row order
+    auto row_ok = [&](int64_t i) {
+        for (int64_t q = Lrp[i]; q < Lrp[i + 1]; ++q) {
+            const int32_t c = Lc[q];
+            if (c < 0 || c >= i || (q > Lrp[i] && Lc[q - 1] >= c)) return false;
+        }
+        return true;
+    };
+    std::atomic<int64_t> first_bad(n);
+    parallel_for(n, [&](int64_t a, int64_t b) {
+        for (int64_t i = a; i < b; ++i)
+            if (!row_ok(i)) {
+                int64_t cur = first_bad.load();
+                while (i < cur && !first_bad.compare_exchange_weak(cur, i)) {
+                }
+                return;
+            }
+    });
+    for (int64_t i = first_bad.load(); i < n; ++i) {
         for (int64_t q = Lrp[i]; q < Lrp[i + 1]; ++q) {
             int32_t c = Lc[q];
             if (c < 0 || c >= i) return "L entry out of the strictly lower triangle at row " + std::to_string(i);
@@ -144,31 +226,20 @@ std::string build_plan(int64_t n, const int64_t* Lrp, const int32_t* Lc, const i
     P.Sc.resize(P.nnzS);
     P.Sdiag.resize(n);
     P.l2s.resize(nnzL);
-    for (int64_t i = 0; i < n; ++i) {
-        int64_t s = P.Srp[i];
-        for (int64_t q = Lrp[i]; q < Lrp[i + 1]; ++q) {
-            P.l2s[q] = (int32_t)s;
-            P.Sc[s++] = Lc[q];
-        }
-        if (i > 0 && ps[i] == 0) P.Sc[s++] = (int32_t)(i - 1);
-        P.Sdiag[i] = (int32_t)s;
-        P.Sc[s++] = (int32_t)i;
-    }
-    // L by columns
-    P.Lcp.assign(n + 1, 0);
-    for (int64_t q = 0; q < nnzL; ++q) P.Lcp[Lc[q] + 1]++;
-    for (int64_t j = 0; j < n; ++j) P.Lcp[j + 1] += P.Lcp[j];
-    P.Lri.resize(nnzL);
-    P.Lcsr.resize(nnzL);
-    {
-        std::vector<int64_t> fill(P.Lcp.begin(), P.Lcp.end() - 1);
-        for (int64_t i = 0; i < n; ++i)
+    parallel_for(n, [&](int64_t a, int64_t b) {
+        for (int64_t i = a; i < b; ++i) {
+            int64_t s = P.Srp[i];
             for (int64_t q = Lrp[i]; q < Lrp[i + 1]; ++q) {
-                int64_t d = fill[Lc[q]]++;
-                P.Lri[d] = (int32_t)i;
-                P.Lcsr[d] = (int32_t)q;
+                P.l2s[q] = (int32_t)s;
+                P.Sc[s++] = Lc[q];
             }
-    }
+            if (i > 0 && ps[i] == 0) P.Sc[s++] = (int32_t)(i - 1);
+            P.Sdiag[i] = (int32_t)s;
+            P.Sc[s++] = (int32_t)i;
+        }
+    });
+    // L by columns
+    csr_to_csc(n, Lrp, Lc, P.Lcp, P.Lri, P.Lcsr);
     const int64_t* Lcp = P.Lcp.data();
     const int32_t* Lri = P.Lri.data();
 

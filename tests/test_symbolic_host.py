@@ -57,6 +57,8 @@ CASES = {
     "lap2d_2x2": lambda: plant_2x2(lap2d_32().factors, 0.4, 3),
     "rand": lambda: random_factors(400, 0.03, 0.2, 8),
     "diff3d_10": lambda: plant_2x2(diff3d(10).factors, 0.05, 4),
+    # 3.4 M entries of L: the analysis transposes L in several row chunks
+    "rand_dense_3k": lambda: random_factors(3000, 0.75, 0.1, 9),
 }
 
 
@@ -119,7 +121,11 @@ def test_scan_form_plan(lib, name):
     a = _host_handle(f)
     b = _host_handle(f, selinv_pair_bytes=-1)
     sa, sb = a.stats(), b.stats()
-    assert sa["selinv_scan"] == 0 and sb["selinv_scan"] == 1 and sb["hit_pairs"] == 0
+    assert sb["selinv_scan"] == 1 and sb["hit_pairs"] == 0
+    # by default the pair lists, unless they would pass the memory budget (the dense
+    # random case: its rows of C hold 5.0 G entries of S, so even a quarter of them
+    # as 8-byte pairs passes the default 8 GB)
+    assert sa["selinv_scan"] == (1 if name == "rand_dense_3k" else 0)
     for x, y in zip(a.supernodes(), b.supernodes()):
         assert np.array_equal(x, y)
     rp, _ = b.pattern_host()
