@@ -678,25 +678,29 @@ std::string build_ninv_plan(const HostPlan& P, int m, NinvPlan& W) {
     W.m = m;
     const int64_t* Lcp = P.Lcp.data();
     const int32_t* Lri = P.Lri.data();
-    // dist-tagged columns, built per power: rows[j] = R_t(j) sorted, tags[j] = the
-    // fewest steps that reach each row.  R_t(j) = {j} + the union over k in struct(j)
-    // of R_{t-1}(k), and the union of the R_{t-2}(k) is already in R_{t-1}(j), so round
-    // t only propagates front[k], the rows that entered R_{t-1}(k) in round t-1; the
-    // rows it adds to R_t(j) have tag t.
-    std::vector<std::vector<int32_t>> rows(n), tags(n), front(n);
+    // Column j of the pattern, built by powers: R_t(j) = {j} + the union over k in
+    // struct(j) of R_{t-1}(k).  The union of the R_{t-2}(k) is already in R_{t-1}(j), so
+    // round t only propagates front[k], the rows that entered R_{t-1}(k) in round t-1,
+    // and the rows it adds to column j are the group of tag t (the fewest steps that
+    // reach them).  rows[j] keeps the groups one after another, each sorted, which is
+    // the layout of W (grp[j] holds the group starts).
+    const int G = m + 2;
+    std::vector<std::vector<int32_t>> rows(n), front(n);
+    W.grp.assign((size_t)n * G, 0);
     for (int64_t j = 0; j < n; ++j) {
         rows[j].push_back((int32_t)j);
-        tags[j].push_back(0);
         front[j].push_back((int32_t)j);
+        W.grp[(size_t)j * G + 1] = 1;  // group 0 = {j}
     }
     for (int t = 1; t <= m; ++t) {
-        std::vector<std::vector<int32_t>> nrows(n), ntags(n), nfront(n);
+        std::vector<std::vector<int32_t>> nfront(n);
         parallel_for_dynamic(n, 512, [&](int64_t a, int64_t b) {
             // per-thread dense markers: mark[r] == j when row r is already in R_t(j)
-            std::vector<int32_t> mark(n, -1), fresh;
+            std::vector<int32_t> mark(n, -1);
             for (int64_t j = a; j < b; ++j) {
-                for (int32_t r : rows[j]) mark[r] = (int32_t)j;
-                fresh.clear();
+                auto& R = rows[j];
+                for (int32_t r : R) mark[r] = (int32_t)j;
+                auto& fresh = nfront[j];
                 for (int64_t q = Lcp[j]; q < Lcp[j + 1]; ++q)
                     for (int32_t r : front[Lri[q]])
                         if (mark[r] != (int32_t)j) {
@@ -704,60 +708,32 @@ std::string build_ninv_plan(const HostPlan& P, int m, NinvPlan& W) {
                             fresh.push_back(r);
                         }
                 std::sort(fresh.begin(), fresh.end());
-                // merge the sorted old rows (their tags kept) with the new ones (tag t)
-                const auto& R0 = rows[j];
-                const auto& T0 = tags[j];
-                auto& R = nrows[j];
-                auto& T = ntags[j];
-                R.resize(R0.size() + fresh.size());
-                T.resize(R.size());
-                size_t x = 0, y = 0, o = 0;
-                while (x < R0.size() || y < fresh.size()) {
-                    if (y == fresh.size() || (x < R0.size() && R0[x] < fresh[y])) {
-                        R[o] = R0[x];
-                        T[o++] = T0[x++];
-                    } else {
-                        R[o] = fresh[y++];
-                        T[o++] = t;
-                    }
-                }
-                nfront[j].swap(fresh);
-                fresh.clear();
+                R.insert(R.end(), fresh.begin(), fresh.end());
+                W.grp[(size_t)j * G + t + 1] = (int32_t)R.size();
             }
         });
-        rows.swap(nrows);
-        tags.swap(ntags);
         front.swap(nfront);
     }
+    front = std::vector<std::vector<int32_t>>();
     W.Wcp.assign(n + 1, 0);
     for (int64_t j = 0; j < n; ++j) W.Wcp[j + 1] = W.Wcp[j] + (int64_t)rows[j].size();
     W.nnzW = W.Wcp[n];
     if (W.nnzW > INT32_MAX) return "pattern of the truncated Neumann series has >= 2^31 entries";
     W.Wr.resize(W.nnzW);
-    W.grp.assign((size_t)n * (m + 2), 0);
-    // column j of W: its rows grouped by tag, ascending inside each group (the rows are
-    // already sorted, so a stable split by tag gives that order)
+    // rows of 2x2 blocks carry a flag bit
     parallel_for_dynamic(n, 512, [&](int64_t a, int64_t b) {
-        std::vector<int32_t> at(m + 2);
         for (int64_t j = a; j < b; ++j) {
-            const auto& R = rows[j];
-            const auto& T = tags[j];
-            int32_t* g = W.grp.data() + (size_t)j * (m + 2);
-            std::fill(at.begin(), at.end(), 0);
-            for (int32_t tg : T) ++at[tg + 1];
-            for (int t = 0; t <= m; ++t) at[t + 1] += at[t];
-            for (int t = 0; t <= m + 1; ++t) g[t] = at[t];  // group starts, then the end
             int32_t* out = W.Wr.data() + W.Wcp[j];
+            const auto& R = rows[j];
             for (size_t e = 0; e < R.size(); ++e) {
                 const int32_t r = R[e];
                 const bool two = !P.pstart[r] || (r + 1 < n && !P.pstart[r + 1]);
-                out[at[T[e]]++] = two ? (int32_t)((uint32_t)r | 0x80000000u) : r;
+                out[e] = two ? (int32_t)((uint32_t)r | 0x80000000u) : r;
             }
         }
     });
     for (int64_t j = 0; j < n; ++j) W.max_col = std::max<int64_t>(W.max_col, W.Wcp[j + 1] - W.Wcp[j]);
     // work counts: step t reads groups 0..t-1 of every k in struct(j)
-    const int G = m + 2;
     for (int64_t j = 0; j < n; ++j) {
         for (int64_t q = Lcp[j]; q < Lcp[j + 1]; ++q) {
             const int64_t k = Lri[q];
