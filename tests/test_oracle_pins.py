@@ -190,6 +190,54 @@ def test_selinv_closed_random_pattern_equals_inverse():
     assert np.max(np.abs(G - exact[_rows(Srp), Sc])) <= 1e-11 * np.max(np.abs(exact))
 
 
+def _dense_masked_selinv(f, S):
+    """The recurrence of Eqs. (4)-(5) on dense arrays, written apart from the oracle:
+    pivot blocks J from the last to the first; C = the rows below J stored in L's
+    columns of J; X = -G_CC L_CJ with G_CC read from the dense array, where only
+    entries of S were ever written (zero off S); G_JJ = D_J^{-1} - L_CJ^T X; then only
+    the entries of S kept."""
+    n = f.n
+    Lc = f.L_csr()
+    stored = np.zeros((n, n), dtype=bool)
+    stored[_rows(Lc.indptr), Lc.indices] = True
+    L = Lc.toarray()
+    D = f.D_dense_blocks().toarray()
+    inS = np.zeros((n, n), dtype=bool)
+    inS[_rows(S[0]), S[1]] = True
+    inS |= inS.T
+    G = np.zeros((n, n))
+    starts = [j for j in range(n) if f.pivot_start[j]] + [n]
+    for b in range(len(starts) - 2, -1, -1):
+        J = list(range(starts[b], starts[b + 1]))
+        C = [r for r in range(starts[b + 1], n) if stored[r, J].any()]
+        LCJ = L[np.ix_(C, J)]
+        X = -G[np.ix_(C, C)] @ LCJ
+        GJJ = np.linalg.inv(D[np.ix_(J, J)]) - LCJ.T @ X
+        for a, r in enumerate(C):
+            for c_, c in enumerate(J):
+                if inS[r, c]:
+                    G[r, c] = G[c, r] = X[a, c_]
+        for a, r in enumerate(J):
+            for c_, c in enumerate(J):
+                G[r, c] = GJJ[a, c_]
+    return G[_rows(S[0]), S[1]]
+
+
+@pytest.mark.parametrize("seed", [3, 8, 21])
+def test_selinv_matches_a_dense_masked_recurrence(seed):
+    """Incomplete (non-closed) random factors with 2x2 pivots: the oracle's sparse
+    recurrence equals the same recurrence run on dense arrays, entry by entry."""
+    from workloads.configs import random_factors
+    f = random_factors(70, 0.08, 0.2, seed)
+    S = _S(f)
+    G = _selinv(f, S)
+    ref = _dense_masked_selinv(f, S)
+    assert np.max(np.abs(G - ref)) <= 1e-12 * np.max(np.abs(ref))
+    # the pattern is not closed: the result differs from the true inverse on S
+    exact = np.linalg.inv(_dense_LDLt(f))
+    assert np.max(np.abs(G - exact[_rows(S[0]), S[1]])) > 1e-6 * np.max(np.abs(exact))
+
+
 # -- NInv (Section 2.2) ------------------------------------------------------------------
 def _brute_ninv(f, m):
     n = f.n
