@@ -346,3 +346,25 @@ def test_empty_matrix_host_analyses(lib):
     h.einv_analyse(A)
     st = h.stats()
     assert st["einv_levels_fwd"] == 0 and st["einv_levels_bwd"] == 0
+
+
+@pytest.mark.parametrize("name", ["lap2d_exact", "diff3d_8_exact"])
+def test_levels_of_exact_factors_are_elimination_tree_depths(lib, name):
+    """For exact factors (a closed pattern) and one column per supernode, a column's
+    level is its depth in the elimination tree (parent(j) = the first row of
+    struct(j); the root has depth 0): every row of struct(j) is an ancestor of j and
+    the parent is the deepest of them."""
+    from workloads.configs import diff3d
+    f = {"lap2d_exact": lambda: lap2d_32(tau=0.0).factors,
+         "diff3d_8_exact": lambda: diff3d(8, tau=0.0, shifted=False).factors}[name]()
+    assert np.all(f.pivot_start == 1)
+    h = _host_handle(f, supernode_cap=1)
+    start, level = h.supernodes()
+    assert np.array_equal(start, np.arange(f.n + 1))
+    Lc = f.L_csr().tocsc()
+    Lc.sort_indices()
+    depth = np.zeros(f.n, dtype=np.int64)
+    for j in range(f.n - 1, -1, -1):
+        rows = Lc.indices[Lc.indptr[j]:Lc.indptr[j + 1]]
+        depth[j] = 0 if len(rows) == 0 else depth[rows[0]] + 1
+    assert np.array_equal(np.asarray(level), depth)
