@@ -421,6 +421,16 @@ void sinv_mlp_destroy(sinv_mlp m);
 /* Host copies of the FP32 master weights; set also resets the Adam state. */
 sinv_status sinv_mlp_get_params(sinv_mlp m, float *theta);
 sinv_status sinv_mlp_set_params(sinv_mlp m, const float *theta);
+/* The whole training state, for a checkpoint: the FP32 weights, Adam's two moment
+ * vectors (host arrays of sinv_mlp_param_count() floats each) and the number of
+ * Adam steps taken.  Both calls first wait for the device's queued work.  After
+ * sinv_mlp_set_state training continues exactly as it would have from the saved
+ * network (the same inputs give the same weights bit for bit).
+ *   Errors: SINV_ERR_INVALID_ARG (a NULL pointer, step < 0 or >= 2^31),
+ *   SINV_ERR_CUDA. */
+sinv_status sinv_mlp_get_state(sinv_mlp m, float *theta, float *mom1, float *mom2, int64_t *step);
+sinv_status sinv_mlp_set_state(sinv_mlp m, const float *theta, const float *mom1, const float *mom2,
+                               int64_t step);
 /* Features of every S_lo entry from the NInv stack of sinv_ninv_stack (m <= 9):
  * X [|S_lo| x 16] BF16, scale [|S_lo|] FP32 (s_ij); all device. */
 sinv_status sinv_mlp_features(sinv_handle h, const double *N_stack, int m, const double *L_val,

@@ -46,6 +46,7 @@ EXPORTS = [
     "sinv_einv_set_solver", "sinv_ninv_own", "sinv_ninv_own_size", "sinv_ninv_own_copy",
     "sinv_selinv_scan_counts", "sinv_mix_own", "sinv_mix_own_size", "sinv_mix_own_copy",
     "sinv_lowrank_correct_mix_own", "sinv_spai_analyse_mix_own", "sinv_spai_mix_own", "sinv_debug_corrupt_plan",
+    "sinv_mlp_get_state", "sinv_mlp_set_state",
 ]
 
 
@@ -119,6 +120,8 @@ def load_library():
     lib.sinv_mlp_destroy.argtypes = [H]
     lib.sinv_mlp_get_params.argtypes = [H, P]
     lib.sinv_mlp_set_params.argtypes = [H, P]
+    lib.sinv_mlp_get_state.argtypes = [H, P, P, P, ctypes.POINTER(I64)]
+    lib.sinv_mlp_set_state.argtypes = [H, P, P, P, I64]
     lib.sinv_mlp_features.argtypes = [H, P, ctypes.c_int, P, P, P, P, P]
     lib.sinv_mlp_targets.argtypes = [H, I64, P, P, P, P, P]
     lib.sinv_mlp_grad.argtypes = [H, P, P, P, I64, P, P, P]
@@ -235,6 +238,32 @@ class Mlp:
         th = np.ascontiguousarray(theta, dtype=np.float32)
         assert th.size == self.n_params
         self._chk(self._lib.sinv_mlp_set_params(self._m, _np_ptr(th)), "set_params")
+
+    def get_state(self) -> dict:
+        """The training state (weights, Adam moments, step count) as host arrays."""
+        th, m1, m2 = (np.empty(self.n_params, dtype=np.float32) for _ in range(3))
+        step = ctypes.c_int64()
+        self._chk(self._lib.sinv_mlp_get_state(self._m, _np_ptr(th), _np_ptr(m1), _np_ptr(m2), ctypes.byref(step)),
+                  "get_state")
+        return {"theta": th, "mom1": m1, "mom2": m2, "step": int(step.value)}
+
+    def set_state(self, state):
+        """Restore a state from get_state: training continues where it stopped."""
+        arrs = [np.ascontiguousarray(state[k], dtype=np.float32) for k in ("theta", "mom1", "mom2")]
+        if any(a.size != self.n_params for a in arrs):
+            raise ValueError("a state holds %d floats per array" % self.n_params)
+        self._chk(self._lib.sinv_mlp_set_state(self._m, *[_np_ptr(a) for a in arrs], int(state["step"])),
+                  "set_state")
+
+    def save(self, path):
+        """Checkpoint the training state to an .npz file."""
+        st = self.get_state()
+        np.savez(path, theta=st["theta"], mom1=st["mom1"], mom2=st["mom2"], step=np.int64(st["step"]))
+
+    def load(self, path):
+        """Restore a checkpoint written by save()."""
+        with np.load(path) as z:
+            self.set_state({"theta": z["theta"], "mom1": z["mom1"], "mom2": z["mom2"], "step": int(z["step"])})
 
     def targets(self, G, N, scale, stream=None):
         y = torch.empty(G.numel(), dtype=torch.float32, device=self.device)

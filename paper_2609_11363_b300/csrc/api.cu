@@ -1524,6 +1524,30 @@ sinv_status sinv_mlp_set_params(sinv_mlp m, const float* theta) {
     return SINV_OK;
 }
 
+sinv_status sinv_mlp_get_state(sinv_mlp m, float* theta, float* mom1, float* mom2, int64_t* step) {
+    if (!m || !theta || !mom1 || !mom2 || !step) return SINV_ERR_INVALID_ARG;
+    const size_t P = kMlpParams * sizeof(float);
+    if (cudaSetDevice(m->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(theta, m->theta, P, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(mom1, m->mom1, P, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(mom2, m->mom2, P, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SINV_ERR_CUDA;
+    *step = m->step;
+    return SINV_OK;
+}
+
+sinv_status sinv_mlp_set_state(sinv_mlp m, const float* theta, const float* mom1, const float* mom2, int64_t step) {
+    if (!m || !theta || !mom1 || !mom2 || step < 0 || step > INT32_MAX) return SINV_ERR_INVALID_ARG;
+    const size_t P = kMlpParams * sizeof(float);
+    if (cudaSetDevice(m->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(m->theta, theta, P, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m->mom1, mom1, P, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m->mom2, mom2, P, cudaMemcpyHostToDevice) != cudaSuccess)
+        return SINV_ERR_CUDA;
+    m->step = (int)step;
+    return SINV_OK;
+}
+
 sinv_status sinv_mlp_features(sinv_handle h, const double* N_stack, int m, const double* L_val, const double* D_val,
                               void* X, float* scale, void* stream) {
     if (!h || m < 0) return SINV_ERR_INVALID_ARG;

@@ -59,6 +59,14 @@ class LearnedCorrection:
         torch.cuda.synchronize()
         return {"steps": step, "seconds": time.time() - t0, "entries": total}
 
+    def save(self, path):
+        """Checkpoint the network's training state (weights, Adam moments, steps)."""
+        self.mlp.save(path)
+
+    def load(self, path):
+        """Resume from a checkpoint written by save()."""
+        self.mlp.load(path)
+
     def predict(self, d) -> torch.Tensor:
         return self.mlp.predict(d["X"], d["scale"], d["N"])
 

@@ -37,6 +37,36 @@ def test_ninv_stack_matches_each_truncation(index_bytes, prec):
         assert sel_rel_err(st[t], ref, *S) <= 1e-10, t
 
 
+def test_mlp_checkpoint_resumes_training_bit_for_bit(tmp_path):
+    """A checkpoint holds the whole training state: a network restored from it (built
+    with other initial weights) and the original, trained on with the same
+    mini-batches, end with the same weights bit for bit (the gradient sums run in a
+    fixed order); a restart from the weights alone, with Adam's moments reset, does
+    not."""
+    from paper_2609_11363_b300 import Mlp
+    rng = np.random.default_rng(11)
+    B = 2048
+    X = torch.as_tensor(rng.standard_normal((B, F)).astype(np.float32)).to(torch.bfloat16).cuda()
+    y = _dev(rng.standard_normal(B).astype(np.float32))
+    idx = torch.arange(B, dtype=torch.int64, device="cuda")
+    a = Mlp(seed=3, max_batch=B)
+    for _ in range(3):
+        a.train_step(X, y, idx, 1e-3)
+    path = str(tmp_path / "mlp_state.npz")
+    a.save(path)
+    b = Mlp(seed=99, max_batch=B)
+    b.load(path)
+    c = Mlp(seed=99, max_batch=B)
+    c.set_params(a.get_params())
+    for _ in range(2):
+        for net in (a, b, c):
+            net.train_step(X, y, idx, 1e-3)
+    torch.cuda.synchronize()
+    assert np.array_equal(a.get_params(), b.get_params())
+    assert not np.array_equal(a.get_params(), c.get_params())
+    assert a.get_state()["step"] == b.get_state()["step"] == 5 and c.get_state()["step"] == 2
+
+
 def test_mlp_gradient_matches_oracle_and_adam_step():
     from paper_2609_11363_b300 import Mlp
     rng = np.random.default_rng(0)

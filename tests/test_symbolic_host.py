@@ -329,6 +329,12 @@ def test_new_entry_points_report_errors_without_a_device(lib):
     assert lib.sinv_spai_analyse_mix_own(h._h, A.nnz, arp.ctypes.data_as(P), acol.ctypes.data_as(P), 0) == 1
     assert lib.sinv_timeline_enable(h._h, 1) == 1
     assert lib.sinv_debug_corrupt_plan(h._h) == 7   # the regular build never plants it
+    # the network's checkpoint calls: a NULL network or buffer is refused before any device call
+    buf = np.zeros(lib.sinv_mlp_param_count(), dtype=np.float32)
+    bp = buf.ctypes.data_as(P)
+    step = I64()
+    assert lib.sinv_mlp_get_state(None, bp, bp, bp, ctypes.byref(step)) == 1
+    assert lib.sinv_mlp_set_state(None, bp, bp, bp, 0) == 1
 
 
 def test_empty_matrix_host_analyses(lib):
