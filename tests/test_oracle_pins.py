@@ -363,6 +363,19 @@ def test_ninv_own_limits():
     assert N.nnz == g.n and np.allclose(N.diagonal(), Dinv, rtol=1e-15)
 
 
+@pytest.mark.parametrize("m", [1, 3])
+def test_ninv_own_without_dropping_is_the_dense_product(m):
+    """delta = 0 on incomplete random factors with 2x2 pivots: nothing is dropped, so
+    NInv on its own pattern is the lower triangle of the dense W^T D^{-1} W with
+    W = sum_{t<=m} E^t, every nonzero of it present."""
+    from workloads.configs import random_factors
+    f = random_factors(90, 0.06, 0.2, 4)
+    N = oracle.ninv_own(f.n, f.L_rowptr, f.L_col, f.L_val, f.pivot_start, f.d_diag, f.d_off, m, 0.0).toarray()
+    ref = np.tril(_brute_ninv(f, m))
+    assert np.max(np.abs(N - ref)) <= 1e-13 * np.max(np.abs(ref))
+    assert np.all(N[np.abs(ref) > 1e-12 * np.max(np.abs(ref))] != 0)
+
+
 def test_ninv_sampled_matches_full():
     w = lap2d_32()
     f = w.factors
