@@ -144,3 +144,16 @@ def test_partition_closure(case, nranks):
     assert np.array_equal(np.sort(pos), np.arange(len(S[1])))
     if case in ("diff3d", "lap2d"):
         assert sum(len(p.supernodes) > 0 for p in P.parts[1:]) == nranks
+
+
+@pytest.mark.parametrize("nranks", [1, 3, 8, 64])
+def test_partition_any_rank_count(nranks):
+    """One rank (everything in its bin), an odd count, and more ranks than there are
+    independent subtrees (some bins stay empty): the parts still cover every column
+    and S entry once and pass the closure check."""
+    from workloads.configs import lap2d_32, random_factors
+    for f in (lap2d_32().factors, random_factors(5, 0.3, 0.0, 1)):
+        S, P = _plan(f, nranks)
+        assert P.validate() and len(P.parts) == nranks + 1
+        assert np.array_equal(np.sort(np.concatenate([p.columns for p in P.parts])), np.arange(f.n))
+        assert np.array_equal(np.sort(np.concatenate([p.s_positions for p in P.parts])), np.arange(len(S[1])))
