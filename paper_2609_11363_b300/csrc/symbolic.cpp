@@ -418,28 +418,67 @@ std::string build_plan(int64_t n, const int64_t* Lrp, const int32_t* Lc, const i
     for (int64_t s = 0; s < ns; ++s) rows_total += rowsum[s];
     P.scan_rows_total = rows_total;
     bool scan = pair_bytes < 0 || 8 * (rows_total / 4) > budget;
+    int64_t roff = 0;
+    for (int64_t s = 0; s < ns; ++s) {
+        P.sn[s].hrow_off = roff;
+        roff += P.sn[s].c + 1;
+    }
+    P.hrow.resize(roff);
+    // The lists are built in one pass, into a buffer per chunk of kChunk consecutive
+    // supernodes sized by an upper bound of its pairs (no-init: only the filled part
+    // is touched), and then copied into place: a chunk's pairs form one contiguous
+    // block of the final lists.  The pass stops once the pairs pass the budget.
+    constexpr int64_t kChunk = 256;
+    std::vector<FillVec<uint32_t>> chunk_ik;
+    std::vector<FillVec<int32_t>> chunk_pos;
     if (!scan) {
-        parallel_for_dynamic(ns, 256, [&](int64_t a, int64_t b) {
-            for (int64_t s = a; s < b; ++s) hits[s] = pairs(s, false, nullptr, nullptr, nullptr);
+        const int64_t nchunks = (ns + kChunk - 1) / kChunk;
+        chunk_ik.resize(nchunks);
+        chunk_pos.resize(nchunks);
+        std::atomic<int64_t> total(0);
+        // pairs of row i of C: at most min(i, its S_lo row length - 1) below the
+        // diagonal, the diagonal, and min(c - 1 - i, |struct| + 1) above it
+        auto bound = [&](int64_t s) {
+            const auto& C = Cs[s];
+            const int64_t c = (int64_t)C.size();
+            int64_t b = 0;
+            for (int64_t i = 0; i < c; ++i) {
+                const int32_t r = C[i];
+                b += std::min<int64_t>(i, P.Srp[r + 1] - P.Srp[r] - 1) + 1 +
+                     std::min<int64_t>(c - 1 - i, Lcp[r + 1] - Lcp[r] + 1);
+            }
+            return b;
+        };
+        parallel_for_dynamic(ns, kChunk, [&](int64_t a, int64_t b) {
+            for (int64_t s0 = a; s0 < b; s0 += kChunk) {
+                if (8 * total.load(std::memory_order_relaxed) > budget) return;
+                const int64_t ch = s0 / kChunk, s1 = std::min(b, s0 + kChunk);
+                int64_t cap = 0;
+                for (int64_t s = s0; s < s1; ++s) cap += bound(s);
+                chunk_ik[ch].resize(cap);
+                chunk_pos[ch].resize(cap);
+                int64_t off = 0;
+                for (int64_t s = s0; s < s1; ++s) {
+                    hits[s] = pairs(s, true, chunk_ik[ch].data() + off, chunk_pos[ch].data() + off,
+                                    P.hrow.data() + P.sn[s].hrow_off);
+                    off += hits[s];
+                }
+                total.fetch_add(off, std::memory_order_relaxed);
+            }
         });
-        int64_t tot = 0;
-        for (int64_t s = 0; s < ns; ++s) tot += hits[s];
-        scan = 8 * tot > budget;
+        scan = 8 * total.load() > budget;
     }
     P.scan = scan ? 1 : 0;
-    int64_t hoff = 0, roff = 0;
+    int64_t hoff = 0;
     for (int64_t s = 0; s < ns; ++s) {
         SnInfo& I = P.sn[s];
         I.hit_off = scan ? 0 : hoff;
         I.hit_cnt = scan ? rowsum[s] / 3 + I.c : hits[s];
-        I.hrow_off = roff;
         if (!scan) hoff += hits[s];
-        roff += I.c + 1;
         if (I.hit_cnt > INT32_MAX || rowsum[s] > INT32_MAX)
             return "a supernode has >= 2^31 pairs: unsupported";
     }
     P.hit_pairs = scan ? 0 : hoff;
-    P.hrow.resize(roff);
     if (scan) {
         // work estimate: a third of the row lengths are pairs (see above); each
         // lookup reads a 4 B column index, each pair an 8 B value
@@ -468,11 +507,20 @@ std::string build_plan(int64_t n, const int64_t* Lrp, const int32_t* Lc, const i
         }
         P.hit_ik.resize(hoff);
         P.hit_pos.resize(hoff);
-        parallel_for_dynamic(ns, 256, [&](int64_t a, int64_t b) {
-            for (int64_t s = a; s < b; ++s) {
-                SnInfo& I = P.sn[s];
-                pairs(s, true, P.hit_ik.data() + I.hit_off, P.hit_pos.data() + I.hit_off,
-                      P.hrow.data() + I.hrow_off);
+        const int64_t nchunks = (int64_t)chunk_ik.size();
+        std::atomic<int64_t> next(0);
+        run_chunks((int)std::min<int64_t>(n_threads(), nchunks), [&](int) {
+            for (;;) {
+                const int64_t ch = next.fetch_add(1);
+                if (ch >= nchunks) break;
+                const int64_t s0 = ch * kChunk, s1 = std::min(ns, s0 + kChunk);
+                const int64_t cnt = P.sn[s1 - 1].hit_off + hits[s1 - 1] - P.sn[s0].hit_off;
+                if (cnt > 0) {
+                    std::memcpy(P.hit_ik.data() + P.sn[s0].hit_off, chunk_ik[ch].data(), cnt * sizeof(uint32_t));
+                    std::memcpy(P.hit_pos.data() + P.sn[s0].hit_off, chunk_pos[ch].data(), cnt * sizeof(int32_t));
+                }
+                FillVec<uint32_t>().swap(chunk_ik[ch]);
+                FillVec<int32_t>().swap(chunk_pos[ch]);
             }
         });
     }

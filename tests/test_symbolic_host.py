@@ -374,3 +374,26 @@ def test_levels_of_exact_factors_are_elimination_tree_depths(lib, name):
         rows = Lc.indices[Lc.indptr[j]:Lc.indptr[j + 1]]
         depth[j] = 0 if len(rows) == 0 else depth[rows[0]] + 1
     assert np.array_equal(np.asarray(level), depth)
+
+
+@pytest.mark.parametrize("name", ["diff3d_10", "lap2d_2x2"])
+def test_pair_budget_passed_while_building_gives_the_scan_form(lib, name):
+    """A budget between the quick bound (a quarter of the row lengths as 8-byte
+    pairs) and the real size of the lists: the lists are started, pass the budget
+    while being built, and the scan form results, with the same supernodes and
+    work measure as when it is asked for."""
+    f = CASES[name]()
+    a = _host_handle(f)
+    sa = a.stats()
+    lo, hi = 8 * (sa["scan_rows_total"] // 4), 8 * sa["hit_pairs"]
+    assert sa["selinv_scan"] == 0 and lo < hi
+    b = _host_handle(f, selinv_pair_bytes=(lo + hi) // 2)
+    c = _host_handle(f, selinv_pair_bytes=-1)
+    sb, sc = b.stats(), c.stats()
+    assert sb["selinv_scan"] == 1 and sb["hit_pairs"] == 0
+    assert sb["scan_rows_total"] == sc["scan_rows_total"] and sb["selinv_flops"] == sc["selinv_flops"]
+    for x, y in zip(b.supernodes(), c.supernodes()):
+        assert np.array_equal(x, y)
+    # and a budget just above the lists keeps them
+    d = _host_handle(f, selinv_pair_bytes=hi)
+    assert d.stats()["selinv_scan"] == 0 and d.stats()["hit_pairs"] == sa["hit_pairs"]
