@@ -427,7 +427,8 @@ std::string build_plan(int64_t n, const int64_t* Lrp, const int32_t* Lc, const i
     // The lists are built in one pass, into a buffer per chunk of kChunk consecutive
     // supernodes sized by an upper bound of its pairs (no-init: only the filled part
     // is touched), and then copied into place: a chunk's pairs form one contiguous
-    // block of the final lists.  The pass stops once the pairs pass the budget.
+    // block of the final lists (so the lists briefly exist twice in host memory:
+    // twice the budget at most).  The pass stops once the pairs pass the budget.
     constexpr int64_t kChunk = 256;
     std::vector<FillVec<uint32_t>> chunk_ik;
     std::vector<FillVec<int32_t>> chunk_pos;
