@@ -397,3 +397,24 @@ def test_pair_budget_passed_while_building_gives_the_scan_form(lib, name):
     # and a budget just above the lists keeps them
     d = _host_handle(f, selinv_pair_bytes=hi)
     assert d.stats()["selinv_scan"] == 0 and d.stats()["hit_pairs"] == sa["hit_pairs"]
+
+
+def test_mlp_checkpoint_file_round_trip(tmp_path):
+    """Mlp.save / Mlp.load carry the whole state (weights, both Adam moments, the
+    step count) through an .npz file unchanged (the device calls are stood in for)."""
+    from paper_2609_11363_b300 import Mlp
+    rng = np.random.default_rng(0)
+    m = Mlp.__new__(Mlp)   # no device: only the file format is under test
+    m.n_params = 37
+    state = {k: rng.standard_normal(37).astype(np.float32) for k in ("theta", "mom1", "mom2")}
+    state["step"] = 12345
+    m.get_state = lambda: state
+    got = {}
+    m.set_state = got.update
+    path = str(tmp_path / "state.npz")
+    m.save(path)
+    m.load(path)
+    assert got["step"] == 12345 and isinstance(got["step"], int)
+    for k in ("theta", "mom1", "mom2"):
+        assert got[k].dtype == np.float32 and np.array_equal(got[k], state[k])
+    m._m = None   # nothing to free at exit
